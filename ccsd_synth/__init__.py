@@ -37,9 +37,12 @@ A k point is the integer triple (k1, k2, k3), 0 <= kd < nd, flattened as
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
 
 import numpy as np
+import scipy.fft as sfft
 
 __all__ = [
     "SynthSpec", "CONFIGS", "spec_for", "generate", "generate_fock",
@@ -150,19 +153,40 @@ def _scale(spec: SynthSpec) -> float:
 
 
 def _gk(spec: SynthSpec, cls: str) -> np.ndarray:
-    """Bloch transform of the raw class tensor: (N, N, N, n_p, n_q, n_r, n_s)."""
+    """Bloch transform of the raw class tensor: (N, N, N, n_p, n_q, n_r, n_s).
+
+    The three cell sums are 3D discrete Fourier transforms on the grid:
+    exp(-i k.R) for R1 and R2 (forward FFT), exp(+i k.R) for R3 (unnormalized
+    inverse FFT), times 1/N."""
     n = {"o": spec.nocc, "v": spec.nvir}
     N = spec.nk
-    phi = _phase(spec.grid)
+    g3 = tuple(spec.grid)
     out = np.empty((N, N, N, n[cls[0]], n[cls[1]], n[cls[2]], n[cls[3]]), np.complex128)
-    for p in range(n[cls[0]]):
+
+    def one(p):
         g = _draw_slice(spec, cls, p)                        # (R1, q, R2, r, R3, s)
-        x = np.tensordot(phi, g, axes=([1], [0]))            # (kp, q, R2, r, R3, s)
-        x = np.tensordot(phi, x, axes=([1], [2]))            # (kq, kp, q, r, R3, s)
-        x = np.tensordot(phi.conj(), x, axes=([1], [4]))     # (kr, kq, kp, q, r, s)
-        out[:, :, :, p] = x.transpose(2, 1, 0, 3, 4, 5)
+        nq, nr, ns = g.shape[1], g.shape[3], g.shape[5]
+        x = g.reshape(g3 + (nq,) + g3 + (nr,) + g3 + (ns,))
+        x = sfft.fftn(x, axes=(0, 1, 2, 4, 5, 6), workers=1)
+        x = sfft.ifftn(x, axes=(8, 9, 10), norm="forward", workers=1, overwrite_x=True)
+        x = x.reshape(N, nq, N, nr, N, ns)
+        out[:, :, :, p] = x.transpose(0, 2, 4, 1, 3, 5)
+
+    _pmap(one, range(n[cls[0]]))
     out *= 1.0 / N
     return out
+
+
+def _pmap(fn, items):
+    items = list(items)
+    workers = min(len(items), os.cpu_count() or 1, 16)
+    if workers <= 1:
+        for x in items:
+            fn(x)
+        return
+    with ThreadPoolExecutor(workers) as ex:
+        for _ in ex.map(fn, items):
+            pass
 
 
 def _swap(cls, perm):
@@ -181,14 +205,17 @@ def _antisym(spec, cls, gk_cache, ks):
     gk_ = g(_swap(cls, (0, 1, 3, 2)))
     gbk = g(_swap(cls, (1, 0, 3, 2)))
     A = np.empty_like(g0)
-    kk = np.arange(N)
-    for kp in range(N):
-        KQ, KR = np.meshgrid(kk, kk, indexing="ij")
-        KS = ks[kp][KQ, KR]
-        A[kp] = g0[kp]
-        A[kp] -= gb[KQ, kp, KR].transpose(0, 1, 3, 2, 4, 5)
-        A[kp] -= gk_[kp][KQ, KS].transpose(0, 1, 2, 3, 5, 4)
-        A[kp] += gbk[KQ, kp, KS].transpose(0, 1, 3, 2, 5, 4)
+
+    def one(kp):
+        for kq in range(N):
+            for kr in range(N):
+                kz = ks[kp, kq, kr]
+                a = g0[kp, kq, kr] - gb[kq, kp, kr].transpose(1, 0, 2, 3)
+                a -= gk_[kp, kq, kz].transpose(0, 1, 3, 2)
+                a += gbk[kq, kp, kz].transpose(1, 0, 3, 2)
+                A[kp, kq, kr] = a
+
+    _pmap(one, range(N))
     return A
 
 
@@ -200,14 +227,19 @@ def _block(spec: SynthSpec, cls: str, ks) -> np.ndarray:
     cache.clear()
     N = spec.nk
     H = np.empty_like(A)
-    kk = np.arange(N)
-    for kp in range(N):
-        KQ, KR = np.meshgrid(kk, kk, indexing="ij")
-        KS = ks[kp][KQ, KR]
-        # conj(A_h[kr, ks, kp](r, s, p, q)) arranged as [p, q, r, s]
-        H[kp] = A[kp] + np.conj(Ah[KR, KS, kp]).transpose(0, 1, 4, 5, 2, 3)
+    sc = 0.5 * _scale(spec)
+
+    def one(kp):
+        for kq in range(N):
+            for kr in range(N):
+                kz = ks[kp, kq, kr]
+                # conj(A_h[kr, ks, kp](r, s, p, q)) arranged as [p, q, r, s]
+                h = A[kp, kq, kr] + np.conj(Ah[kr, kz, kp]).transpose(2, 3, 0, 1)
+                h *= sc
+                H[kp, kq, kr] = h
+
+    _pmap(one, range(N))
     del A, Ah
-    H *= 0.5 * _scale(spec)
     return H
 
 

@@ -1,0 +1,130 @@
+/*
+ * ccsd.h -- C ABI of the GB300 library for periodic spin-orbital CCSD
+ * (Yamashita, Kosugi, Matsushita, Sakurai, "A Parallel Computing Method for
+ * the Coupled-Cluster Singles and Doubles", arXiv:1911.00242).
+ *
+ * The library evaluates the T1/T2 residuals of the paper's Eqs. (ori_EqSingle)
+ * and (ori_EqDouble) -- equivalently the rearranged Eqs. (EqSingle) and
+ * (EqDouble) of Sec. 3.3 -- and performs the amplitude update of Sec. 4.4 on
+ * one GPU.  The paper's N_k^2 process grid (Sec. 3.1-3.2) becomes the batch
+ * index of grouped complex GEMM kernels.
+ *
+ * Data layout (row-major, last index fastest, complex = interleaved re,im):
+ *   k point: integer triple (k1,k2,k3), 0 <= kd < nd, flat index
+ *            (k1*n2 + k2)*n3 + k3; momentum sums are componentwise mod nd
+ *            (paper Sec. 3.2.5).  N = n1*n2*n3.
+ *   f_oo[k][i][j], f_vv[k][a][b], f_ov[k][i][a]   Fock blocks, complex128,
+ *            f_ov[k][i][a] = <i k|f|a k>                        (Sec. 2)
+ *   B[kp][kq][kr][p][q][r][s]  antisymmetrized integrals <p kp q kq||r kr s ks>
+ *            with ks = kp + kq - kr, for B in oooo, ooov, oovv, ovvo, ovvv,
+ *            vvvv (every other class follows from the symmetries of Sec. 3.3)
+ *   t1[k][i][a], t2[ki][kj][ka][i][j][a][b] (kb = ki + kj - ka), complex128
+ *
+ * Errors: every entry point returns 0 (CCSD_OK) or a negative CCSD_ERR_* code;
+ * ccsd_strerror() names it.  No exception crosses the ABI.  After a
+ * CCSD_ERR_CUDA the handle should be destroyed.
+ * Threading: one handle must not be used from two host threads at once.  All
+ * device work is enqueued on the stream given at creation; calls that return
+ * host scalars synchronize that stream.
+ */
+#ifndef CCSD_GB300_H
+#define CCSD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CCSD_OK                 0
+#define CCSD_ERR_INVALID      (-1)  /* bad shape, null pointer, dtype, config   */
+#define CCSD_ERR_OOM          (-2)  /* device allocation or admission refused   */
+#define CCSD_ERR_CUDA         (-3)  /* a CUDA runtime call failed               */
+#define CCSD_ERR_NOT_CONVERGED (-4) /* max_iter reached; results still readable */
+#define CCSD_ERR_DIVERGED     (-5)  /* non-finite residual                       */
+#define CCSD_ERR_TIMEOUT      (-6)  /* a bounded device wait gave up             */
+
+#define CCSD_FP64   0   /* every contraction in FP64 (DFMA)                    */
+
+#define CCSD_C128   0   /* integral blocks complex128                          */
+
+typedef struct ccsd_ctx* ccsd_t;
+
+typedef struct {
+    int    nk_dims[3];    /* k grid (n1, n2, n3), each >= 1                     */
+    int    nocc, nvir;    /* occupied / virtual spin orbitals per k, >= 1       */
+    int    precision;     /* CCSD_FP64                                          */
+    int    diis_depth;    /* 0 = plain successive substitution (paper Sec. 4.4.12);
+                             2..8 = Pulay DIIS over that many updates            */
+    int    max_iter;      /* used by ccsd_solve                                 */
+    double conv_tol;      /* max|R1| and max|R2| threshold, Eqs. (criterion_single,
+                             criterion_double)                                   */
+} ccsd_config;
+
+typedef struct {
+    /* Fock blocks and the six integral blocks in the layout above.  Each
+     * pointer may be device memory (borrowed: it must stay valid and unchanged
+     * until ccsd_destroy) or host memory (copied into library-owned device
+     * memory during ccsd_create; pinned host memory copies fastest). */
+    const void *f_oo, *f_vv, *f_ov;
+    const void *oooo, *ooov, *oovv, *ovvo, *ovvv, *vvvv;
+    int int_dtype;        /* CCSD_C128                                          */
+} ccsd_inputs;
+
+/* Creates a solver for one problem.  `stream` is a cudaStream_t (NULL = the
+ * legacy default stream) on the current device.  The amplitudes start at zero,
+ * so the first update produces t0 = f(0) (paper Sec. 3.2.2).  Allocates all
+ * work memory up front; returns CCSD_ERR_OOM if it does not fit. */
+int ccsd_create(const ccsd_config* cfg, const ccsd_inputs* in, void* stream, ccsd_t* out);
+
+/* Bytes of device memory ccsd_create would allocate for this config when
+ * `inputs_on_device` is 1 (borrowed inputs) or 0 (copied inputs). */
+int ccsd_footprint(const ccsd_config* cfg, int inputs_on_device, size_t* bytes);
+
+/* Builds the launch plan of this config on the host only (no GPU, no device
+ * memory) and checks that every element each launch can touch lies inside
+ * its buffer.  *n_launches receives the kernel launches of one residual
+ * evaluation, *table_bytes the size of the plan's index tables. */
+int ccsd_plan_check(const ccsd_config* cfg, long long* n_launches, size_t* table_bytes);
+
+/* One residual evaluation R(t) (paper Eqs. ori_EqSingle, ori_EqDouble with the
+ * full Fock matrix inside F~): t1, t2 are read and r1, r2 written, all device
+ * pointers in the layout above (r1 like t1, r2 like t2).  Does not touch the
+ * handle's amplitudes. */
+int ccsd_residual(ccsd_t h, const void* t1, const void* t2, void* r1, void* r2);
+
+/* Up to n_iter iterations on the handle's amplitudes.  Each computes R(t);
+ * if max(max|R1|, max|R2|) < conv_tol it sets *done = 1 and stops without
+ * updating; otherwise t <- t + R/D (paper Sec. 4.4.13, D from the Fock
+ * diagonal), followed by DIIS extrapolation when diis_depth > 0.
+ * *max_resid receives the last max|R| (may be NULL).  Returns
+ * CCSD_ERR_DIVERGED if R is not finite. */
+int ccsd_iterate(ccsd_t h, int n_iter, int* done, double* max_resid);
+
+/* Iterates until convergence or cfg->max_iter updates; CCSD_ERR_NOT_CONVERGED
+ * when the limit is reached (the amplitudes remain readable). */
+int ccsd_solve(ccsd_t h, int* iterations, double* max_resid);
+
+/* Correlation energy of the current amplitudes per unit cell (supercell
+ * total / N_k): sum f_ia t_i^a + 1/4 sum <ij||ab> t_ij^ab
+ * + 1/2 sum <ij||ab> t_i^a t_j^b.  The paper states no energy expression; this
+ * is the standard spin-orbital one.  e_imag is zero for time-reversal
+ * symmetric inputs. */
+int ccsd_energy(ccsd_t h, double* e_real, double* e_imag);
+
+/* Copy the amplitudes out of / into the handle; host or device pointers. */
+int ccsd_get_amplitudes(ccsd_t h, void* t1, void* t2);
+int ccsd_set_amplitudes(ccsd_t h, const void* t1, const void* t2);
+
+/* Number of kernel launches the last ccsd_iterate/ccsd_residual call made. */
+int ccsd_last_launch_count(ccsd_t h, long long* launches);
+
+int ccsd_destroy(ccsd_t h);
+
+const char* ccsd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCSD_GB300_H */

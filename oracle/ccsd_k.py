@@ -17,7 +17,9 @@ import numpy as np
 from .integrals import Integrals
 from .kmesh import KMesh
 
-ein = np.einsum
+def ein(*args):
+    # BLAS-backed einsum (numpy picks the pairwise contraction order)
+    return np.einsum(*args, optimize=True)
 
 
 class Problem:

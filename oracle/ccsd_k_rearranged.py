@@ -21,7 +21,9 @@ import numpy as np
 
 from .ccsd_k import Problem  # noqa: F401  (same input container)
 
-ein = np.einsum
+def ein(*args):
+    # BLAS-backed einsum (numpy picks the pairwise contraction order)
+    return np.einsum(*args, optimize=True)
 
 
 def _k_tilde(P, t1):

@@ -12,7 +12,9 @@ supercell.
 """
 import numpy as np
 
-ein = np.einsum
+def ein(*args):
+    # BLAS-backed einsum (numpy picks the pairwise contraction order)
+    return np.einsum(*args, optimize=True)
 
 
 class Dense:

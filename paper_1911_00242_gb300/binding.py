@@ -1,0 +1,169 @@
+"""ctypes binding of libccsd_gb300.so (argument marshalling only).
+
+Every function of include/ccsd.h is exposed under the same name on the object
+returned by `load()`.  `Solver` wraps a handle for torch tensors or numpy
+arrays: device tensors are borrowed by pointer, host arrays are copied by the
+library.  There is no CPU fallback: without the built library every call raises.
+"""
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libccsd_gb300.so")
+
+CCSD_OK = 0
+CCSD_ERR_INVALID = -1
+CCSD_ERR_OOM = -2
+CCSD_ERR_CUDA = -3
+CCSD_ERR_NOT_CONVERGED = -4
+CCSD_ERR_DIVERGED = -5
+CCSD_ERR_TIMEOUT = -6
+CCSD_FP64 = 0
+CCSD_C128 = 0
+
+BLOCKS = ("oooo", "ooov", "oovv", "ovvo", "ovvv", "vvvv")
+
+
+class ccsd_config(ctypes.Structure):
+    _fields_ = [("nk_dims", ctypes.c_int * 3), ("nocc", ctypes.c_int), ("nvir", ctypes.c_int),
+                ("precision", ctypes.c_int), ("diis_depth", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("conv_tol", ctypes.c_double)]
+
+
+class ccsd_inputs(ctypes.Structure):
+    _fields_ = [("f_oo", ctypes.c_void_p), ("f_vv", ctypes.c_void_p), ("f_ov", ctypes.c_void_p),
+                ("oooo", ctypes.c_void_p), ("ooov", ctypes.c_void_p), ("oovv", ctypes.c_void_p),
+                ("ovvo", ctypes.c_void_p), ("ovvv", ctypes.c_void_p), ("vvvv", ctypes.c_void_p),
+                ("int_dtype", ctypes.c_int)]
+
+
+SYMBOLS = {
+    "ccsd_create": ([ctypes.POINTER(ccsd_config), ctypes.POINTER(ccsd_inputs), ctypes.c_void_p,
+                     ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "ccsd_footprint": ([ctypes.POINTER(ccsd_config), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "ccsd_plan_check": ([ctypes.POINTER(ccsd_config), ctypes.POINTER(ctypes.c_longlong),
+                         ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "ccsd_residual": ([ctypes.c_void_p] * 5, ctypes.c_int),
+    "ccsd_iterate": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                      ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "ccsd_solve": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "ccsd_energy": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "ccsd_get_amplitudes": ([ctypes.c_void_p] * 3, ctypes.c_int),
+    "ccsd_set_amplitudes": ([ctypes.c_void_p] * 3, ctypes.c_int),
+    "ccsd_last_launch_count": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+    "ccsd_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "ccsd_strerror": ([ctypes.c_int], ctypes.c_char_p),
+}
+
+_lib = None
+
+
+class CCSDError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _lib.ccsd_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg} ({code})")
+
+
+def load(path=LIB_PATH):
+    """Load the library and declare every exported signature; raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in SYMBOLS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def check(code, where):
+    if code != CCSD_OK:
+        raise CCSDError(code, where)
+    return code
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor or numpy array (must be contiguous)."""
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    assert x.flags.c_contiguous
+    return x.ctypes.data
+
+
+def make_config(grid, nocc, nvir, precision=CCSD_FP64, diis_depth=0, max_iter=100, conv_tol=1e-8):
+    c = ccsd_config()
+    c.nk_dims[0], c.nk_dims[1], c.nk_dims[2] = grid
+    c.nocc, c.nvir, c.precision = nocc, nvir, precision
+    c.diis_depth, c.max_iter, c.conv_tol = diis_depth, max_iter, conv_tol
+    return c
+
+
+class Solver:
+    """One CCSD problem held by a library handle.
+
+    `arrays` maps f_oo, f_vv, f_ov and the six block names to contiguous
+    complex128 torch tensors (device: borrowed, kept referenced here) or numpy
+    arrays (host: copied by the library during creation)."""
+
+    def __init__(self, grid, nocc, nvir, arrays, stream=None, **cfg):
+        self.lib = load()
+        self.cfg = make_config(grid, nocc, nvir, **cfg)
+        self._keep = dict(arrays)
+        inp = ccsd_inputs()
+        for name in ("f_oo", "f_vv", "f_ov") + BLOCKS:
+            setattr(inp, name, _ptr(arrays[name]))
+        inp.int_dtype = CCSD_C128
+        h = ctypes.c_void_p()
+        check(self.lib.ccsd_create(ctypes.byref(self.cfg), ctypes.byref(inp), stream, ctypes.byref(h)), "ccsd_create")
+        self.h = h
+
+    def residual(self, t1, t2, r1, r2):
+        check(self.lib.ccsd_residual(self.h, _ptr(t1), _ptr(t2), _ptr(r1), _ptr(r2)), "ccsd_residual")
+
+    def iterate(self, n=1):
+        done = ctypes.c_int(0)
+        mr = ctypes.c_double(0.0)
+        check(self.lib.ccsd_iterate(self.h, n, ctypes.byref(done), ctypes.byref(mr)), "ccsd_iterate")
+        return bool(done.value), mr.value
+
+    def solve(self):
+        it = ctypes.c_int(0)
+        mr = ctypes.c_double(0.0)
+        code = self.lib.ccsd_solve(self.h, ctypes.byref(it), ctypes.byref(mr))
+        if code not in (CCSD_OK, CCSD_ERR_NOT_CONVERGED):
+            check(code, "ccsd_solve")
+        return code == CCSD_OK, it.value, mr.value
+
+    def energy(self):
+        er = ctypes.c_double(0.0)
+        ei = ctypes.c_double(0.0)
+        check(self.lib.ccsd_energy(self.h, ctypes.byref(er), ctypes.byref(ei)), "ccsd_energy")
+        return complex(er.value, ei.value)
+
+    def get_amplitudes(self, t1, t2):
+        check(self.lib.ccsd_get_amplitudes(self.h, _ptr(t1), _ptr(t2)), "ccsd_get_amplitudes")
+
+    def set_amplitudes(self, t1, t2):
+        check(self.lib.ccsd_set_amplitudes(self.h, _ptr(t1), _ptr(t2)), "ccsd_set_amplitudes")
+
+    def launches(self):
+        n = ctypes.c_longlong(0)
+        check(self.lib.ccsd_last_launch_count(self.h, ctypes.byref(n)), "ccsd_last_launch_count")
+        return n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ccsd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

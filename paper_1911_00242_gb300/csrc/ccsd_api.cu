@@ -1,0 +1,1123 @@
+// C ABI of the GB300 periodic-CCSD library: handle, plans, iteration driver.
+//
+// One residual evaluation is the sequence below (FP64 form).  Each
+// contraction is one launch of the k-blocked complex GEMM (zgemm_kb.cuh); the
+// batch index enumerates the two or three free momenta that the paper maps to
+// process numbers (Sec. 3.1), the chunk index the contracted momentum that the
+// paper's shifted SEND/RECV loop "Sum_88" walks (Sec. 4.3.4).
+//
+//   tau, tau~                                    Sec. 2 (tau definitions)
+//   F~_ov, F~_oo, F~_vv                          Eqs. ori_F_ov, ori_F_oo, ori_F_vv
+//   R1                                           Eq. ori_EqSingle
+//   R2 = <ab||ij>
+//      + 1/2 tau_mn^ab (W'_mnij + 1/2 X_mnij)    hole-hole: W~_mnij without its tau term
+//                                                plus the 1/4 tau <mn||ef> part of W~^abef
+//      + 1/2 tau_ij^ef W'^abef                   ladder: W~^abef without that part
+//      + P(ij)P(ab) [t_in^af W~_jn^bf - t t <ov||vo>]   ring, Eq. Def_Woovv
+//      + P(ab) F'vv t2 - P(ij) F'oo t2 + P(ij) <ab||cj> t - P(ab) t <rb||ij>
+//   (X_mnij = sum tau_ij^ef <mn||ef>; both W~ factorizations are the
+//    paper's Eq. ori_EqDouble regrouped, so R2 is unchanged)
+// and the update t <- t + R/D with convergence test and energy (Sec. 4.4).
+#include "../../include/ccsd.h"
+#include "ccsd_kernels.cuh"
+#include "zgemm_kb.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace ccsdk;
+
+namespace {
+
+// ------------------------------------------------------------ k grid (host)
+struct KGrid {
+    int n[3] = {1, 1, 1};
+    int N = 1;
+    std::vector<int> c0, c1, c2;
+    void init(const int* d) {
+        n[0] = d[0]; n[1] = d[1]; n[2] = d[2];
+        N = n[0] * n[1] * n[2];
+        c0.resize(N); c1.resize(N); c2.resize(N);
+        for (int k = 0; k < N; ++k) { c0[k] = k / (n[1] * n[2]); c1[k] = (k / n[2]) % n[1]; c2[k] = k % n[2]; }
+    }
+    static int md(int x, int m) { x %= m; return x < 0 ? x + m : x; }
+    int flat(int a, int b, int c) const { return (md(a, n[0]) * n[1] + md(b, n[1])) * n[2] + md(c, n[2]); }
+    // k1 + k2 - k3 (momentum conservation k1 + k2 = k3 + k4, paper Sec. 3.2.5)
+    int k4(int k1, int k2, int k3) const {
+        return flat(c0[k1] + c0[k2] - c0[k3], c1[k1] + c1[k2] - c1[k3], c2[k1] + c2[k2] - c2[k3]);
+    }
+};
+
+enum Buf {
+    B_FOO_IN, B_FVV_IN, B_FOV_IN, B_OOOO, B_OOOV, B_OOVV, B_OVVO, B_OVVV, B_VVVV,
+    B_T1, B_T2, B_R1, B_R2, B_TAU, B_TAUT,
+    B_FOV, B_FOO, B_FVV, B_FOOP, B_FVVP,
+    B_WHH, B_WAB, B_WRING, B_Q, B_TT, B_ZAB, B_ZIJ, B_ZR,
+    NBUF
+};
+
+struct GemmPlan {
+    int a, b, c;
+    GemmArgs args;      // device tables filled; A/B/C pointers resolved at launch
+    int cfg;            // tile configuration
+    int blocks;
+};
+
+struct CopyPlan {       // dst = (conj) src, n elements
+    int dst, src; long long n; int conj;
+};
+
+struct PermPlan {
+    int dst, src; Perm4 p;
+};
+
+struct Step {           // one element of the launch sequence
+    int kind;           // 0 gemm, 1 copy, 2 perm, 3 tau, 4 antisym
+    int idx;
+};
+
+}  // namespace
+
+struct ccsd_ctx {
+    ccsd_config cfg;
+    KGrid kg;
+    int N = 0, o = 0, v = 0;
+    long long n1 = 0, n2 = 0;       // elements of t1 and t2
+    cudaStream_t st = nullptr;
+    double2* buf[NBUF] = {};
+    long long bufsize[NBUF] = {};   // elements, for plan bound checks
+    std::vector<void*> owned;        // device allocations to free
+    size_t owned_bytes = 0;
+    double2* amp = nullptr;          // [t1 | t2]
+    double2* res = nullptr;          // [R1 | R2]
+    double* eo = nullptr;            // Fock diagonal eo[k][i]
+    double* ev = nullptr;            // ev[k][a]
+    int* kb_of = nullptr;            // fourth momentum of doubles blocks
+    double2* work = nullptr;         // split-K partials
+    double* red = nullptr;           // reduction partials
+    double* red_out = nullptr;       // scalars
+    double2* cred = nullptr;
+    double2* cred_out = nullptr;
+    std::vector<double2*> hx, he;    // DIIS history
+    std::vector<std::vector<double>> gram;
+    int diis_count = 0, diis_next = 0;
+    std::vector<GemmPlan> gemms;
+    std::vector<CopyPlan> copies;
+    std::vector<PermPlan> perms;
+    std::vector<Step> seq;
+    long long launches = 0;
+    int red_blocks = 0;
+};
+
+namespace {
+
+#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { last_err(e_); return CCSD_ERR_CUDA; } } while (0)
+thread_local char g_errbuf[256];
+void last_err(cudaError_t e) { snprintf(g_errbuf, sizeof g_errbuf, "%s", cudaGetErrorString(e)); }
+
+struct Alloc {
+    ccsd_ctx* h;
+    int err = 0;
+    bool dry = false;     // plan validation only: no device memory, no copies
+    void* get(size_t bytes) {
+        if (err) return nullptr;
+        void* p = nullptr;
+        if (bytes == 0) bytes = 16;
+        if (dry) { h->owned_bytes += bytes; return (void*)(uintptr_t)256; }
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) { cudaGetLastError(); err = (e == cudaErrorMemoryAllocation) ? CCSD_ERR_OOM : CCSD_ERR_CUDA; return nullptr; }
+        h->owned.push_back(p);
+        h->owned_bytes += bytes;
+        return p;
+    }
+};
+
+template <class T>
+T* upload(Alloc& al, const std::vector<T>& v, cudaStream_t st) {
+    T* d = (T*)al.get(v.size() * sizeof(T));
+    if (!d) return nullptr;
+    if (al.dry) return d;
+    if (cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st) != cudaSuccess) { al.err = CCSD_ERR_CUDA; return nullptr; }
+    if (cudaStreamSynchronize(st) != cudaSuccess) { al.err = CCSD_ERR_CUDA; return nullptr; }
+    return d;
+}
+
+// Table helpers: idx(x) for x over a product of index ranges with strides.
+std::vector<int> tab(std::initializer_list<std::pair<int, long long>> dims) {
+    std::vector<std::pair<int, long long>> d(dims);
+    long long total = 1;
+    for (auto& p : d) total *= p.first;
+    std::vector<int> out((size_t)total);
+    for (long long x = 0; x < total; ++x) {
+        long long r = x, off = 0;
+        for (int i = (int)d.size() - 1; i >= 0; --i) { off += (r % d[i].first) * d[i].second; r /= d[i].first; }
+        out[(size_t)x] = (int)off;
+    }
+    return out;
+}
+
+struct GemmSpec {
+    int a, b, c;
+    int M, N, K, nbatch, nchunk;
+    std::vector<long long> offA, offB, offC;
+    std::vector<int> rowA, colA, rowB, colB, rowC, colC;
+    bool conjA = false, conjB = false, acc = true;
+    double ar = 1.0, ai = 0.0;
+};
+
+// Tile configurations: (BM, BN, BK, TM, TN), 256 threads each.
+enum { CFG_64x64 = 0, CFG_64x32 = 1, CFG_128x16 = 2, CFG_16x16 = 3 };
+const int CFG_BM[4] = {64, 64, 128, 16};
+const int CFG_BN[4] = {64, 32, 16, 16};
+
+const int kSMs = 152;
+
+int finalize_gemm(ccsd_ctx* h, Alloc& al, GemmSpec s, size_t& work_need) {
+    // Put the larger output dimension on M (C^T = B^T A^T swaps the operands).
+    if (s.N > s.M) {
+        std::swap(s.M, s.N);
+        std::swap(s.a, s.b);
+        std::swap(s.offA, s.offB);
+        std::swap(s.conjA, s.conjB);
+        std::vector<int> ra = s.colB, ca = s.rowB, rb = s.colA, cb = s.rowA;
+        s.rowA = ra; s.colA = ca; s.rowB = rb; s.colB = cb;
+        std::swap(s.rowC, s.colC);
+    }
+    // Every element a launch can touch must lie inside its buffer.
+    auto span = [](const std::vector<long long>& off, const std::vector<int>& r, const std::vector<int>& c) {
+        long long lo = 0, hi = 0;
+        if (off.empty() || r.empty() || c.empty()) return std::make_pair(-1LL, -1LL);
+        lo = *std::min_element(off.begin(), off.end()) + *std::min_element(r.begin(), r.end()) + *std::min_element(c.begin(), c.end());
+        hi = *std::max_element(off.begin(), off.end()) + *std::max_element(r.begin(), r.end()) + *std::max_element(c.begin(), c.end());
+        return std::make_pair(lo, hi);
+    };
+    if ((long long)s.offA.size() != (long long)s.nbatch * s.nchunk || (long long)s.offB.size() != (long long)s.nbatch * s.nchunk ||
+        (long long)s.offC.size() != s.nbatch || (int)s.rowA.size() != s.M || (int)s.colA.size() != s.K ||
+        (int)s.rowB.size() != s.K || (int)s.colB.size() != s.N || (int)s.rowC.size() != s.M || (int)s.colC.size() != s.N)
+        return CCSD_ERR_INVALID;
+    const std::pair<long long, long long> sa = span(s.offA, s.rowA, s.colA), sb = span(s.offB, s.rowB, s.colB),
+                                          sc = span(s.offC, s.rowC, s.colC);
+    if (sa.first < 0 || sa.second >= h->bufsize[s.a] || sb.first < 0 || sb.second >= h->bufsize[s.b] ||
+        sc.first < 0 || sc.second >= h->bufsize[s.c]) {
+        snprintf(g_errbuf, sizeof g_errbuf, "plan %zu out of bounds", h->gemms.size());
+        return CCSD_ERR_INVALID;
+    }
+    GemmPlan p{};
+    p.a = s.a; p.b = s.b; p.c = s.c;
+    if (s.N >= 48) p.cfg = CFG_64x64;
+    else if (s.N > 16) p.cfg = CFG_64x32;
+    else if (s.M > 16) p.cfg = CFG_128x16;
+    else p.cfg = CFG_16x16;
+    GemmArgs& g = p.args;
+    g.M = s.M; g.N = s.N; g.K = s.K; g.nbatch = s.nbatch; g.nchunk = s.nchunk;
+    g.conjA = s.conjA; g.conjB = s.conjB; g.accumulate = s.acc ? 1 : 0;
+    g.alpha_re = s.ar; g.alpha_im = s.ai;
+    g.tiles_m = (s.M + CFG_BM[p.cfg] - 1) / CFG_BM[p.cfg];
+    g.tiles_n = (s.N + CFG_BN[p.cfg] - 1) / CFG_BN[p.cfg];
+    const long long ctas = (long long)g.tiles_m * g.tiles_n * s.nbatch;
+    int nsplit = 1;
+    if (ctas < 2 * kSMs && s.nchunk > 1) {
+        nsplit = (int)std::min<long long>(s.nchunk, (2 * kSMs + ctas - 1) / ctas);
+    }
+    g.chunks_per_split = (s.nchunk + nsplit - 1) / nsplit;
+    g.nsplit = (s.nchunk + g.chunks_per_split - 1) / g.chunks_per_split;
+    if (g.nsplit > 1) work_need = std::max(work_need, (size_t)g.nsplit * s.nbatch * s.M * s.N);
+    p.blocks = (int)ctas;
+    g.offA = upload(al, s.offA, h->st); g.offB = upload(al, s.offB, h->st); g.offC = upload(al, s.offC, h->st);
+    g.rowA = upload(al, s.rowA, h->st); g.colA = upload(al, s.colA, h->st);
+    g.rowB = upload(al, s.rowB, h->st); g.colB = upload(al, s.colB, h->st);
+    g.rowC = upload(al, s.rowC, h->st); g.colC = upload(al, s.colC, h->st);
+    if (al.err) return al.err;
+    h->gemms.push_back(p);
+    h->seq.push_back({0, (int)h->gemms.size() - 1});
+    return 0;
+}
+
+int add_copy(ccsd_ctx* h, int dst, int src, long long n, int conj) {
+    if (n > h->bufsize[dst] || n > h->bufsize[src]) return CCSD_ERR_INVALID;
+    h->copies.push_back({dst, src, n, conj});
+    h->seq.push_back({1, (int)h->copies.size() - 1});
+    return 0;
+}
+
+int add_perm(ccsd_ctx* h, Alloc& al, int dst, int src, int n0, int n1, int n2, int n3,
+             int d0, int d1, int d2, int d3, int s0, int s1, int s2, int s3,
+             const std::vector<long long>& offD, const std::vector<long long>& offS) {
+    {
+        const long long dmax = (long long)(n0 - 1) * d0 + (long long)(n1 - 1) * d1 + (long long)(n2 - 1) * d2 + (long long)(n3 - 1) * d3;
+        const long long smax = (long long)(n0 - 1) * s0 + (long long)(n1 - 1) * s1 + (long long)(n2 - 1) * s2 + (long long)(n3 - 1) * s3;
+        for (size_t i = 0; i < offD.size(); ++i)
+            if (offD[i] < 0 || offS[i] < 0 || offD[i] + dmax >= h->bufsize[dst] || offS[i] + smax >= h->bufsize[src]) return CCSD_ERR_INVALID;
+    }
+    PermPlan pp{};
+    pp.dst = dst; pp.src = src;
+    pp.p.n0 = n0; pp.p.n1 = n1; pp.p.n2 = n2; pp.p.n3 = n3;
+    pp.p.d0 = d0; pp.p.d1 = d1; pp.p.d2 = d2; pp.p.d3 = d3;
+    pp.p.s0 = s0; pp.p.s1 = s1; pp.p.s2 = s2; pp.p.s3 = s3;
+    pp.p.nbatch = (int)offD.size();
+    pp.p.offD = upload(al, offD, h->st);
+    pp.p.offS = upload(al, offS, h->st);
+    if (al.err) return al.err;
+    h->perms.push_back(pp);
+    h->seq.push_back({2, (int)h->perms.size() - 1});
+    return 0;
+}
+
+// Build the full residual plan.
+int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
+    const KGrid& kg = h->kg;
+    const int N = h->N, o = h->o, v = h->v;
+    const long long ov = (long long)o * v, oo = (long long)o * o, vv = (long long)v * v;
+    const long long S2 = oo * vv;                     // t2 / oovv / ovvo block
+    const long long Soooo = oo * oo, Sooov = oo * ov, Sovvv = ov * vv, Svvvv = vv * vv;
+    auto kk3 = [&](int a, int b, int c) { return ((long long)a * N + b) * N + c; };
+    auto blk = [&](long long S, int a, int b, int c) { return kk3(a, b, c) * S; };
+    int rc;
+    auto G = [&](GemmSpec& s) { return finalize_gemm(h, al, s, work_need); };
+
+    // ---------------- tau, tau~
+    h->seq.push_back({3, 0});
+
+    // ---------------- F~_ov (Eq. ori_F_ov): f_ov + sum t_r^c <p k r k^||g k c k^>
+    if ((rc = add_copy(h, B_FOV, B_FOV_IN, (long long)N * ov, 0))) return rc;
+    {
+        GemmSpec s; s.a = B_OOVV; s.b = B_T1; s.c = B_FOV;
+        s.M = (int)ov; s.N = 1; s.K = (int)ov; s.nbatch = N; s.nchunk = N;
+        for (int k = 0; k < N; ++k) {
+            for (int kh = 0; kh < N; ++kh) { s.offA.push_back(blk(S2, k, kh, k)); s.offB.push_back(kh * ov); }
+            s.offC.push_back(k * ov);
+        }
+        s.rowA = tab({{o, ov * v}, {v, v}}); s.colA = tab({{o, vv}, {v, 1}});
+        s.rowB = tab({{(int)ov, 1}}); s.colB = {0};
+        s.rowC = tab({{(int)ov, 1}}); s.colC = {0};
+        if ((rc = G(s))) return rc;
+    }
+    // ---------------- F~_oo (Eq. ori_F_oo)
+    if ((rc = add_copy(h, B_FOO, B_FOO_IN, (long long)N * oo, 0))) return rc;
+    {   // + 1/2 sum_c f_p^c t_q^c
+        GemmSpec s; s.a = B_FOV_IN; s.b = B_T1; s.c = B_FOO;
+        s.M = o; s.N = o; s.K = v; s.nbatch = N; s.nchunk = 1; s.ar = 0.5;
+        for (int k = 0; k < N; ++k) { s.offA.push_back(k * ov); s.offB.push_back(k * ov); s.offC.push_back(k * oo); }
+        s.rowA = tab({{o, v}}); s.colA = tab({{v, 1}});
+        s.rowB = tab({{v, 1}}); s.colB = tab({{o, v}});
+        s.rowC = tab({{o, o}}); s.colC = tab({{o, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // + sum t_r^c(k^) <p k r k^||q k c k^>
+        GemmSpec s; s.a = B_OOOV; s.b = B_T1; s.c = B_FOO;
+        s.M = (int)oo; s.N = 1; s.K = (int)ov; s.nbatch = N; s.nchunk = N;
+        for (int k = 0; k < N; ++k) {
+            for (int kh = 0; kh < N; ++kh) { s.offA.push_back(blk(Sooov, k, kh, k)); s.offB.push_back(kh * ov); }
+            s.offC.push_back(k * oo);
+        }
+        s.rowA = tab({{o, oo * v}, {o, v}}); s.colA = tab({{o, ov}, {v, 1}});
+        s.rowB = tab({{(int)ov, 1}}); s.colB = {0};
+        s.rowC = tab({{(int)oo, 1}}); s.colC = {0};
+        if ((rc = G(s))) return rc;
+    }
+    {   // + 1/2 sum tau~_{q n}^{e f} <p n||e f>
+        GemmSpec s; s.a = B_OOVV; s.b = B_TAUT; s.c = B_FOO;
+        s.M = o; s.N = o; s.K = (int)(o * vv); s.nbatch = N; s.nchunk = N * N; s.ar = 0.5;
+        for (int k = 0; k < N; ++k) {
+            for (int kn = 0; kn < N; ++kn)
+                for (int ke = 0; ke < N; ++ke) { s.offA.push_back(blk(S2, k, kn, ke)); s.offB.push_back(blk(S2, k, kn, ke)); }
+            s.offC.push_back(k * oo);
+        }
+        s.rowA = tab({{o, o * vv}}); s.colA = tab({{(int)(o * vv), 1}});
+        s.rowB = tab({{(int)(o * vv), 1}}); s.colB = tab({{o, o * vv}});
+        s.rowC = tab({{o, o}}); s.colC = tab({{o, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    // ---------------- F~_vv (Eq. ori_F_vv)
+    if ((rc = add_copy(h, B_FVV, B_FVV_IN, (long long)N * vv, 0))) return rc;
+    {   // - 1/2 sum_r f_r^h t_r^g
+        GemmSpec s; s.a = B_T1; s.b = B_FOV_IN; s.c = B_FVV;
+        s.M = v; s.N = v; s.K = o; s.nbatch = N; s.nchunk = 1; s.ar = -0.5;
+        for (int k = 0; k < N; ++k) { s.offA.push_back(k * ov); s.offB.push_back(k * ov); s.offC.push_back(k * vv); }
+        s.rowA = tab({{v, 1}}); s.colA = tab({{o, v}});
+        s.rowB = tab({{o, v}}); s.colB = tab({{v, 1}});
+        s.rowC = tab({{v, v}}); s.colC = tab({{v, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // + sum t_r^c(k^) <g k r k^||h k c k^> = ovvv[k^,k,k^](r,g,c,h)
+        GemmSpec s; s.a = B_OVVV; s.b = B_T1; s.c = B_FVV;
+        s.M = (int)vv; s.N = 1; s.K = (int)ov; s.nbatch = N; s.nchunk = N;
+        for (int k = 0; k < N; ++k) {
+            for (int kh = 0; kh < N; ++kh) { s.offA.push_back(blk(Sovvv, kh, k, kh)); s.offB.push_back(kh * ov); }
+            s.offC.push_back(k * vv);
+        }
+        s.rowA = tab({{v, vv}, {v, 1}}); s.colA = tab({{o, vv * v}, {v, v}});
+        s.rowB = tab({{(int)ov, 1}}); s.colB = {0};
+        s.rowC = tab({{(int)vv, 1}}); s.colC = {0};
+        if ((rc = G(s))) return rc;
+    }
+    {   // - 1/2 sum tau~_{mn}^{g f} <m n||h f>
+        GemmSpec s; s.a = B_TAUT; s.b = B_OOVV; s.c = B_FVV;
+        s.M = v; s.N = v; s.K = (int)(oo * v); s.nbatch = N; s.nchunk = N * N; s.ar = -0.5;
+        for (int k = 0; k < N; ++k) {
+            for (int km = 0; km < N; ++km)
+                for (int kn = 0; kn < N; ++kn) { s.offA.push_back(blk(S2, km, kn, k)); s.offB.push_back(blk(S2, km, kn, k)); }
+            s.offC.push_back(k * vv);
+        }
+        s.rowA = tab({{v, v}}); s.colA = tab({{(int)oo, vv}, {v, 1}});
+        s.rowB = tab({{(int)oo, vv}, {v, 1}}); s.colB = tab({{v, v}});
+        s.rowC = tab({{v, v}}); s.colC = tab({{v, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    // ---------------- F' combinations used by T2
+    if ((rc = add_copy(h, B_FVVP, B_FVV, (long long)N * vv, 0))) return rc;
+    {   // F~^bf - 1/2 sum_r t_r^b F~_r^f
+        GemmSpec s; s.a = B_T1; s.b = B_FOV; s.c = B_FVVP;
+        s.M = v; s.N = v; s.K = o; s.nbatch = N; s.nchunk = 1; s.ar = -0.5;
+        for (int k = 0; k < N; ++k) { s.offA.push_back(k * ov); s.offB.push_back(k * ov); s.offC.push_back(k * vv); }
+        s.rowA = tab({{v, 1}}); s.colA = tab({{o, v}});
+        s.rowB = tab({{o, v}}); s.colB = tab({{v, 1}});
+        s.rowC = tab({{v, v}}); s.colC = tab({{v, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    if ((rc = add_copy(h, B_FOOP, B_FOO, (long long)N * oo, 0))) return rc;
+    {   // F~_nj + 1/2 sum_c t_j^c F~_n^c
+        GemmSpec s; s.a = B_FOV; s.b = B_T1; s.c = B_FOOP;
+        s.M = o; s.N = o; s.K = v; s.nbatch = N; s.nchunk = 1; s.ar = 0.5;
+        for (int k = 0; k < N; ++k) { s.offA.push_back(k * ov); s.offB.push_back(k * ov); s.offC.push_back(k * oo); }
+        s.rowA = tab({{o, v}}); s.colA = tab({{v, 1}});
+        s.rowB = tab({{v, 1}}); s.colB = tab({{o, v}});
+        s.rowC = tab({{o, o}}); s.colC = tab({{o, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    // ---------------- R1 (Eq. ori_EqSingle); driver <a|f|i> = f_ov^*
+    if ((rc = add_copy(h, B_R1, B_FOV_IN, (long long)N * ov, 1))) return rc;
+    {   // + sum_c F~^{ac} t_i^c
+        GemmSpec s; s.a = B_T1; s.b = B_FVV; s.c = B_R1;
+        s.M = o; s.N = v; s.K = v; s.nbatch = N; s.nchunk = 1;
+        for (int k = 0; k < N; ++k) { s.offA.push_back(k * ov); s.offB.push_back(k * vv); s.offC.push_back(k * ov); }
+        s.rowA = tab({{o, v}}); s.colA = tab({{v, 1}});
+        s.rowB = tab({{v, 1}}); s.colB = tab({{v, v}});
+        s.rowC = tab({{o, v}}); s.colC = tab({{v, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // - sum_r t_r^a F~_{ri}
+        GemmSpec s; s.a = B_FOO; s.b = B_T1; s.c = B_R1;
+        s.M = o; s.N = v; s.K = o; s.nbatch = N; s.nchunk = 1; s.ar = -1.0;
+        for (int k = 0; k < N; ++k) { s.offA.push_back(k * oo); s.offB.push_back(k * ov); s.offC.push_back(k * ov); }
+        s.rowA = tab({{o, 1}}); s.colA = tab({{o, o}});
+        s.rowB = tab({{o, v}}); s.colB = tab({{v, 1}});
+        s.rowC = tab({{o, v}}); s.colC = tab({{v, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // + sum F~_n^f(k^) t_{i k n k^}^{a k f k^}
+        GemmSpec s; s.a = B_T2; s.b = B_FOV; s.c = B_R1;
+        s.M = (int)ov; s.N = 1; s.K = (int)ov; s.nbatch = N; s.nchunk = N;
+        for (int k = 0; k < N; ++k) {
+            for (int kh = 0; kh < N; ++kh) { s.offA.push_back(blk(S2, k, kh, k)); s.offB.push_back(kh * ov); }
+            s.offC.push_back(k * ov);
+        }
+        s.rowA = tab({{o, o * vv}, {v, v}}); s.colA = tab({{o, vv}, {v, 1}});
+        s.rowB = tab({{(int)ov, 1}}); s.colB = {0};
+        s.rowC = tab({{(int)ov, 1}}); s.colC = {0};
+        if ((rc = G(s))) return rc;
+    }
+    {   // + sum t_r^c(k^) <a k r k^||i k c k^> = ovvo[k^,k,k^](r,a,c,i)
+        GemmSpec s; s.a = B_OVVO; s.b = B_T1; s.c = B_R1;
+        s.M = (int)ov; s.N = 1; s.K = (int)ov; s.nbatch = N; s.nchunk = N;
+        for (int k = 0; k < N; ++k) {
+            for (int kh = 0; kh < N; ++kh) { s.offA.push_back(blk(S2, kh, k, kh)); s.offB.push_back(kh * ov); }
+            s.offC.push_back(k * ov);
+        }
+        s.rowA = tab({{o, 1}, {v, v * o}}); s.colA = tab({{o, vv * o}, {v, o}});
+        s.rowB = tab({{(int)ov, 1}}); s.colB = {0};
+        s.rowC = tab({{(int)ov, 1}}); s.colC = {0};
+        if ((rc = G(s))) return rc;
+    }
+    {   // - 1/2 sum t_{mn}^{a f} <m n||i f>
+        GemmSpec s; s.a = B_OOOV; s.b = B_T2; s.c = B_R1;
+        s.M = o; s.N = v; s.K = (int)(oo * v); s.nbatch = N; s.nchunk = N * N; s.ar = -0.5;
+        for (int k = 0; k < N; ++k) {
+            for (int km = 0; km < N; ++km)
+                for (int kn = 0; kn < N; ++kn) { s.offA.push_back(blk(Sooov, km, kn, k)); s.offB.push_back(blk(S2, km, kn, k)); }
+            s.offC.push_back(k * ov);
+        }
+        s.rowA = tab({{o, v}}); s.colA = tab({{(int)oo, ov}, {v, 1}});
+        s.rowB = tab({{(int)oo, vv}, {v, 1}}); s.colB = tab({{v, v}});
+        s.rowC = tab({{o, v}}); s.colC = tab({{v, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // + 1/2 sum t_{i n}^{e f} <a n||e f> = - 1/2 sum t_in^ef ovvv[kn,k,ke](n,a,e,f)
+        GemmSpec s; s.a = B_T2; s.b = B_OVVV; s.c = B_R1;
+        s.M = o; s.N = v; s.K = (int)(o * vv); s.nbatch = N; s.nchunk = N * N; s.ar = -0.5;
+        for (int k = 0; k < N; ++k) {
+            for (int kn = 0; kn < N; ++kn)
+                for (int ke = 0; ke < N; ++ke) { s.offA.push_back(blk(S2, k, kn, ke)); s.offB.push_back(blk(Sovvv, kn, k, ke)); }
+            s.offC.push_back(k * ov);
+        }
+        s.rowA = tab({{o, o * vv}}); s.colA = tab({{o, vv}, {(int)vv, 1}});
+        s.rowB = tab({{o, vv * v}, {(int)vv, 1}}); s.colB = tab({{v, vv}});
+        s.rowC = tab({{o, v}}); s.colC = tab({{v, 1}});
+        if ((rc = G(s))) return rc;
+    }
+
+    // ---------------- R2 (Eq. ori_EqDouble); driver <ab||ij> = <ij||ab>^*
+    if ((rc = add_copy(h, B_R2, B_OOVV, (long long)N * N * N * S2, 1))) return rc;
+    const int N3 = N * N * N;
+    // hole-hole: Whh = <mn||ij> + P(ij) t_j^c <mn||ic> + 1/2 tau_ij^ef <mn||ef>
+    if ((rc = add_copy(h, B_WHH, B_OOOO, (long long)N3 * Soooo, 0))) return rc;
+    {
+        GemmSpec s; s.a = B_OOOV; s.b = B_T1; s.c = B_WHH;
+        s.M = (int)(oo * o); s.N = o; s.K = v; s.nbatch = N3; s.nchunk = 1;
+        for (int km = 0; km < N; ++km) for (int kn = 0; kn < N; ++kn) for (int ki = 0; ki < N; ++ki) {
+            const int kj = kg.k4(km, kn, ki);
+            s.offA.push_back(blk(Sooov, km, kn, ki)); s.offB.push_back(kj * ov); s.offC.push_back(blk(Soooo, km, kn, ki));
+        }
+        s.rowA = tab({{(int)(oo * o), v}}); s.colA = tab({{v, 1}});
+        s.rowB = tab({{v, 1}}); s.colB = tab({{o, v}});
+        s.rowC = tab({{(int)(oo * o), o}}); s.colC = tab({{o, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    {
+        GemmSpec s; s.a = B_OOOV; s.b = B_T1; s.c = B_WHH; s.ar = -1.0;
+        s.M = (int)(oo * o); s.N = o; s.K = v; s.nbatch = N3; s.nchunk = 1;
+        for (int km = 0; km < N; ++km) for (int kn = 0; kn < N; ++kn) for (int ki = 0; ki < N; ++ki) {
+            const int kj = kg.k4(km, kn, ki);
+            s.offA.push_back(blk(Sooov, km, kn, kj)); s.offB.push_back(ki * ov); s.offC.push_back(blk(Soooo, km, kn, ki));
+        }
+        s.rowA = tab({{(int)(oo * o), v}}); s.colA = tab({{v, 1}});
+        s.rowB = tab({{v, 1}}); s.colB = tab({{o, v}});
+        s.rowC = tab({{(int)oo, oo}, {o, 1}}); s.colC = tab({{o, o}});
+        if ((rc = G(s))) return rc;
+    }
+    {
+        GemmSpec s; s.a = B_OOVV; s.b = B_TAU; s.c = B_WHH; s.ar = 0.5;
+        s.M = (int)oo; s.N = (int)oo; s.K = (int)vv; s.nbatch = N3; s.nchunk = N;
+        for (int km = 0; km < N; ++km) for (int kn = 0; kn < N; ++kn) for (int ki = 0; ki < N; ++ki) {
+            const int kj = kg.k4(km, kn, ki);
+            for (int ke = 0; ke < N; ++ke) { s.offA.push_back(blk(S2, km, kn, ke)); s.offB.push_back(blk(S2, ki, kj, ke)); }
+            s.offC.push_back(blk(Soooo, km, kn, ki));
+        }
+        s.rowA = tab({{(int)oo, vv}}); s.colA = tab({{(int)vv, 1}});
+        s.rowB = tab({{(int)vv, 1}}); s.colB = tab({{(int)oo, vv}});
+        s.rowC = tab({{(int)oo, oo}}); s.colC = tab({{(int)oo, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // R2 += 1/2 sum_km tau_{mn}^{ab} Whh_{mnij}
+        GemmSpec s; s.a = B_WHH; s.b = B_TAU; s.c = B_R2; s.ar = 0.5;
+        s.M = (int)oo; s.N = (int)vv; s.K = (int)oo; s.nbatch = N3; s.nchunk = N;
+        for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
+            for (int km = 0; km < N; ++km) {
+                const int kn = kg.k4(ki, kj, km);
+                s.offA.push_back(blk(Soooo, km, kn, ki)); s.offB.push_back(blk(S2, km, kn, ka));
+            }
+            s.offC.push_back(blk(S2, ki, kj, ka));
+        }
+        s.rowA = tab({{(int)oo, 1}}); s.colA = tab({{(int)oo, oo}});
+        s.rowB = tab({{(int)oo, vv}}); s.colB = tab({{(int)vv, 1}});
+        s.rowC = tab({{(int)oo, vv}}); s.colC = tab({{(int)vv, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    // ladder: Wab = <ab||ef> - P(ab) t_r^b <a r||e f>
+    if ((rc = add_copy(h, B_WAB, B_VVVV, (long long)N3 * Svvvv, 0))) return rc;
+    {   // + sum_r t_r^b(kb) ovvv[kb,ka,ke](r,a,e,f)
+        GemmSpec s; s.a = B_OVVV; s.b = B_T1; s.c = B_WAB;
+        s.M = (int)(vv * v); s.N = v; s.K = o; s.nbatch = N3; s.nchunk = 1;
+        for (int ka = 0; ka < N; ++ka) for (int kb = 0; kb < N; ++kb) for (int ke = 0; ke < N; ++ke) {
+            s.offA.push_back(blk(Sovvv, kb, ka, ke)); s.offB.push_back(kb * ov); s.offC.push_back(blk(Svvvv, ka, kb, ke));
+        }
+        s.rowA = tab({{(int)(vv * v), 1}}); s.colA = tab({{o, vv * v}});
+        s.rowB = tab({{o, v}}); s.colB = tab({{v, 1}});
+        s.rowC = tab({{v, vv * v}, {(int)vv, 1}}); s.colC = tab({{v, vv}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // - sum_r t_r^a(ka) ovvv[ka,kb,ke](r,b,e,f)
+        GemmSpec s; s.a = B_OVVV; s.b = B_T1; s.c = B_WAB; s.ar = -1.0;
+        s.M = (int)(vv * v); s.N = v; s.K = o; s.nbatch = N3; s.nchunk = 1;
+        for (int ka = 0; ka < N; ++ka) for (int kb = 0; kb < N; ++kb) for (int ke = 0; ke < N; ++ke) {
+            s.offA.push_back(blk(Sovvv, ka, kb, ke)); s.offB.push_back(ka * ov); s.offC.push_back(blk(Svvvv, ka, kb, ke));
+        }
+        s.rowA = tab({{(int)(vv * v), 1}}); s.colA = tab({{o, vv * v}});
+        s.rowB = tab({{o, v}}); s.colB = tab({{v, 1}});
+        s.rowC = tab({{v, vv}, {(int)vv, 1}}); s.colC = tab({{v, vv * v}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // R2 += 1/2 sum_ke tau_ij^ef Wab^{abef}; batches grouped by (ka, kb) for L2 reuse
+        GemmSpec s; s.a = B_TAU; s.b = B_WAB; s.c = B_R2; s.ar = 0.5;
+        s.M = (int)oo; s.N = (int)vv; s.K = (int)vv; s.nbatch = N3; s.nchunk = N;
+        for (int ka = 0; ka < N; ++ka) for (int kb = 0; kb < N; ++kb) for (int ki = 0; ki < N; ++ki) {
+            const int kj = kg.k4(ka, kb, ki);
+            for (int ke = 0; ke < N; ++ke) { s.offA.push_back(blk(S2, ki, kj, ke)); s.offB.push_back(blk(Svvvv, ka, kb, ke)); }
+            s.offC.push_back(blk(S2, ki, kj, ka));
+        }
+        s.rowA = tab({{(int)oo, vv}}); s.colA = tab({{(int)vv, 1}});
+        s.rowB = tab({{(int)vv, 1}}); s.colB = tab({{(int)vv, vv}});
+        s.rowC = tab({{(int)oo, vv}}); s.colC = tab({{(int)vv, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    // ring: W~_jn^bf (Eq. Def_Woovv), stored [kj,kn,kb](j,n,b,f), kf = kn + kb - kj
+    {
+        std::vector<long long> offD, offS;
+        for (int kj = 0; kj < N; ++kj) for (int kn = 0; kn < N; ++kn) for (int kb = 0; kb < N; ++kb) {
+            const int kf = kg.k4(kn, kb, kj);
+            offD.push_back(blk(S2, kj, kn, kb)); offS.push_back(blk(S2, kn, kb, kf));
+        }
+        // W(j,n,b,f) = ovvo(n,b,f,j)
+        if ((rc = add_perm(h, al, B_WRING, B_OVVO, o, o, v, v, (int)(o * vv), (int)vv, v, 1,
+                           1, (int)(vv * o), (int)(v * o), o, offD, offS))) return rc;
+    }
+    {   // + sum_c t_j^c <n b||f c>
+        GemmSpec s; s.a = B_T1; s.b = B_OVVV; s.c = B_WRING;
+        s.M = o; s.N = (int)(o * vv); s.K = v; s.nbatch = N3; s.nchunk = 1;
+        for (int kj = 0; kj < N; ++kj) for (int kn = 0; kn < N; ++kn) for (int kb = 0; kb < N; ++kb) {
+            const int kf = kg.k4(kn, kb, kj);
+            s.offA.push_back(kj * ov); s.offB.push_back(blk(Sovvv, kn, kb, kf)); s.offC.push_back(blk(S2, kj, kn, kb));
+        }
+        s.rowA = tab({{o, v}}); s.colA = tab({{v, 1}});
+        s.rowB = tab({{v, 1}}); s.colB = tab({{(int)(o * vv), v}});
+        s.rowC = tab({{o, o * vv}}); s.colC = tab({{(int)(o * vv), 1}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // Q(n,r,j,f) = ooov[kn,kb,kj](n,r,j,f) - sum_c oovv[kn,kb,kf](n,r,f,c) t_j^c
+        std::vector<long long> offD, offS;
+        for (int kj = 0; kj < N; ++kj) for (int kn = 0; kn < N; ++kn) for (int kb = 0; kb < N; ++kb) {
+            offD.push_back(blk(Sooov, kj, kn, kb)); offS.push_back(blk(Sooov, kn, kb, kj));
+        }
+        if ((rc = add_perm(h, al, B_Q, B_OOOV, o, o, o, v, (int)(oo * v), (int)ov, v, 1,
+                           (int)(oo * v), (int)ov, v, 1, offD, offS))) return rc;
+        GemmSpec s; s.a = B_OOVV; s.b = B_T1; s.c = B_Q; s.ar = -1.0;
+        s.M = (int)(oo * v); s.N = o; s.K = v; s.nbatch = N3; s.nchunk = 1;
+        for (int kj = 0; kj < N; ++kj) for (int kn = 0; kn < N; ++kn) for (int kb = 0; kb < N; ++kb) {
+            const int kf = kg.k4(kn, kb, kj);
+            s.offA.push_back(blk(S2, kn, kb, kf)); s.offB.push_back(kj * ov); s.offC.push_back(blk(Sooov, kj, kn, kb));
+        }
+        s.rowA = tab({{(int)oo, vv}, {v, v}}); s.colA = tab({{v, 1}});
+        s.rowB = tab({{v, 1}}); s.colB = tab({{o, v}});
+        s.rowC = tab({{(int)oo, ov}, {v, 1}}); s.colC = tab({{o, v}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // W += sum_r t_r^b Q(n,r,j,f)   (= -t_r^b <n r||f j> - t_j^c t_r^b <n r||f c>)
+        GemmSpec s; s.a = B_T1; s.b = B_Q; s.c = B_WRING;
+        s.M = v; s.N = (int)(oo * v); s.K = o; s.nbatch = N3; s.nchunk = 1;
+        for (int kj = 0; kj < N; ++kj) for (int kn = 0; kn < N; ++kn) for (int kb = 0; kb < N; ++kb) {
+            s.offA.push_back(kb * ov); s.offB.push_back(blk(Sooov, kj, kn, kb)); s.offC.push_back(blk(S2, kj, kn, kb));
+        }
+        s.rowA = tab({{v, 1}}); s.colA = tab({{o, v}});
+        s.rowB = tab({{o, ov}}); s.colB = tab({{o, oo * v}, {o, v}, {v, 1}});
+        s.rowC = tab({{v, v}}); s.colC = tab({{o, vv}, {o, o * vv}, {v, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // W -= 1/2 sum_kx t_{j x}^{y b} <n x||f y>
+        GemmSpec s; s.a = B_T2; s.b = B_OOVV; s.c = B_WRING; s.ar = -0.5;
+        s.M = (int)ov; s.N = (int)ov; s.K = (int)ov; s.nbatch = N3; s.nchunk = N;
+        for (int kj = 0; kj < N; ++kj) for (int kn = 0; kn < N; ++kn) for (int kb = 0; kb < N; ++kb) {
+            const int kf = kg.k4(kn, kb, kj);
+            for (int kx = 0; kx < N; ++kx) {
+                const int ky = kg.k4(kj, kx, kb);
+                s.offA.push_back(blk(S2, kj, kx, ky)); s.offB.push_back(blk(S2, kn, kx, kf));
+            }
+            s.offC.push_back(blk(S2, kj, kn, kb));
+        }
+        s.rowA = tab({{o, o * vv}, {v, 1}}); s.colA = tab({{o, vv}, {v, v}});
+        s.rowB = tab({{o, vv}, {v, 1}}); s.colB = tab({{o, o * vv}, {v, v}});
+        s.rowC = tab({{o, o * vv}, {v, v}}); s.colC = tab({{o, vv}, {v, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // ZR = sum_kn t_{in}^{af} W_{jn}^{bf}
+        GemmSpec s; s.a = B_T2; s.b = B_WRING; s.c = B_ZR; s.acc = false;
+        s.M = (int)ov; s.N = (int)ov; s.K = (int)ov; s.nbatch = N3; s.nchunk = N;
+        for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
+            const int kb = kg.k4(ki, kj, ka);
+            for (int kn = 0; kn < N; ++kn) { s.offA.push_back(blk(S2, ki, kn, ka)); s.offB.push_back(blk(S2, kj, kn, kb)); }
+            s.offC.push_back(blk(S2, ki, kj, ka));
+        }
+        s.rowA = tab({{o, o * vv}, {v, v}}); s.colA = tab({{o, vv}, {v, 1}});
+        s.rowB = tab({{o, vv}, {v, 1}}); s.colB = tab({{o, o * vv}, {v, v}});
+        s.rowC = tab({{o, o * vv}, {v, v}}); s.colC = tab({{o, vv}, {v, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // TT(r,b,i,j) = sum_c <r ka b kb||c ki j kj> t_i^c ;  ZR -= sum_r t_r^a TT(r,b,i,j)
+        GemmSpec s; s.a = B_OVVO; s.b = B_T1; s.c = B_TT; s.acc = false;
+        s.M = (int)(ov * o); s.N = o; s.K = v; s.nbatch = N3; s.nchunk = 1;
+        for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
+            const int kb = kg.k4(ki, kj, ka);
+            s.offA.push_back(blk(S2, ka, kb, ki)); s.offB.push_back(ki * ov); s.offC.push_back(blk(Sooov, ki, kj, ka));
+        }
+        s.rowA = tab({{(int)ov, v * o}, {o, 1}}); s.colA = tab({{v, o}});
+        s.rowB = tab({{v, 1}}); s.colB = tab({{o, v}});
+        s.rowC = tab({{(int)ov, oo}, {o, 1}}); s.colC = tab({{o, o}});
+        if ((rc = G(s))) return rc;
+        GemmSpec s2; s2.a = B_T1; s2.b = B_TT; s2.c = B_ZR; s2.ar = -1.0;
+        s2.M = v; s2.N = (int)(oo * v); s2.K = o; s2.nbatch = N3; s2.nchunk = 1;
+        for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
+            s2.offA.push_back(ka * ov); s2.offB.push_back(blk(Sooov, ki, kj, ka)); s2.offC.push_back(blk(S2, ki, kj, ka));
+        }
+        s2.rowA = tab({{v, 1}}); s2.colA = tab({{o, v}});
+        s2.rowB = tab({{o, v * oo}}); s2.colB = tab({{(int)oo, 1}, {v, oo}});
+        s2.rowC = tab({{v, v}}); s2.colC = tab({{(int)oo, vv}, {v, 1}});
+        if ((rc = G(s2))) return rc;
+    }
+    // remaining terms under P(ab) and P(ij)
+    {   // ZAB = sum_f t_ij^af F'^{bf}(kb)
+        GemmSpec s; s.a = B_T2; s.b = B_FVVP; s.c = B_ZAB; s.acc = false;
+        s.M = (int)(oo * v); s.N = v; s.K = v; s.nbatch = N3; s.nchunk = 1;
+        for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
+            const int kb = kg.k4(ki, kj, ka);
+            s.offA.push_back(blk(S2, ki, kj, ka)); s.offB.push_back(kb * vv); s.offC.push_back(blk(S2, ki, kj, ka));
+        }
+        s.rowA = tab({{(int)(oo * v), v}}); s.colA = tab({{v, 1}});
+        s.rowB = tab({{v, 1}}); s.colB = tab({{v, v}});
+        s.rowC = tab({{(int)(oo * v), v}}); s.colC = tab({{v, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // ZAB -= sum_r t_r^a <r b||i j> = sum_r t_r^a conj(ooov[ki,kj,ka](i,j,r,b))
+        GemmSpec s; s.a = B_T1; s.b = B_OOOV; s.c = B_ZAB; s.ar = -1.0; s.conjB = true;
+        s.M = v; s.N = (int)(oo * v); s.K = o; s.nbatch = N3; s.nchunk = 1;
+        for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
+            s.offA.push_back(ka * ov); s.offB.push_back(blk(Sooov, ki, kj, ka)); s.offC.push_back(blk(S2, ki, kj, ka));
+        }
+        s.rowA = tab({{v, 1}}); s.colA = tab({{o, v}});
+        s.rowB = tab({{o, v}}); s.colB = tab({{(int)oo, ov}, {v, 1}});
+        s.rowC = tab({{v, v}}); s.colC = tab({{(int)oo, vv}, {v, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // ZIJ = - sum_n t_{i n}^{ab} F'_{nj}(kj)
+        GemmSpec s; s.a = B_T2; s.b = B_FOOP; s.c = B_ZIJ; s.acc = false; s.ar = -1.0;
+        s.M = (int)(o * vv); s.N = o; s.K = o; s.nbatch = N3; s.nchunk = 1;
+        for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
+            s.offA.push_back(blk(S2, ki, kj, ka)); s.offB.push_back(kj * oo); s.offC.push_back(blk(S2, ki, kj, ka));
+        }
+        s.rowA = tab({{o, o * vv}, {(int)vv, 1}}); s.colA = tab({{o, vv}});
+        s.rowB = tab({{o, o}}); s.colB = tab({{o, 1}});
+        s.rowC = tab({{o, o * vv}, {(int)vv, 1}}); s.colC = tab({{o, vv}});
+        if ((rc = G(s))) return rc;
+    }
+    {   // ZIJ += sum_c <a b||c j> t_i^c = - sum_c t_i^c conj(ovvv[kj,ki,ka](j,c,a,b))
+        GemmSpec s; s.a = B_T1; s.b = B_OVVV; s.c = B_ZIJ; s.ar = -1.0; s.conjB = true;
+        s.M = o; s.N = (int)(o * vv); s.K = v; s.nbatch = N3; s.nchunk = 1;
+        for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
+            s.offA.push_back(ki * ov); s.offB.push_back(blk(Sovvv, kj, ki, ka)); s.offC.push_back(blk(S2, ki, kj, ka));
+        }
+        s.rowA = tab({{o, v}}); s.colA = tab({{v, 1}});
+        s.rowB = tab({{v, vv}}); s.colB = tab({{o, vv * v}, {(int)vv, 1}});
+        s.rowC = tab({{o, o * vv}}); s.colC = tab({{o, vv}, {(int)vv, 1}});
+        if ((rc = G(s))) return rc;
+    }
+    h->seq.push_back({4, 0});
+    return 0;
+}
+
+
+void set_sizes(ccsd_ctx* h) {
+    const long long N = h->N, o = h->o, v = h->v, N3 = N * N * N;
+    const long long sz[NBUF] = {N * o * o, N * v * v, N * o * v, N3 * o * o * o * o, N3 * o * o * o * v,
+                                N3 * o * o * v * v, N3 * o * o * v * v, N3 * o * v * v * v, N3 * v * v * v * v,
+                                h->n1, h->n2, h->n1, h->n2, h->n2, h->n2,
+                                N * o * v, N * o * o, N * v * v, N * o * o, N * v * v,
+                                N3 * o * o * o * o, N3 * v * v * v * v, h->n2, N3 * o * o * o * v, N3 * o * o * o * v,
+                                h->n2, h->n2, h->n2};
+    for (int i = 0; i < NBUF; ++i) h->bufsize[i] = sz[i];
+}
+
+dim3 ew_grid(long long n) {
+    long long b = (n + 255) / 256;
+    if (b > 152LL * 16) b = 152LL * 16;
+    if (b < 1) b = 1;
+    return dim3((unsigned)b);
+}
+
+int launch_gemm(ccsd_ctx* h, GemmPlan& p) {
+    GemmArgs g = p.args;
+    g.A = h->buf[p.a]; g.B = h->buf[p.b]; g.C = h->buf[p.c]; g.work = h->work;
+    dim3 grid((unsigned)p.blocks, (unsigned)g.nsplit);
+    switch (p.cfg) {
+        case CFG_64x64:  zgemm_kb_kernel<64, 64, 8, 4, 4><<<grid, 256, 0, h->st>>>(g); break;
+        case CFG_64x32:  zgemm_kb_kernel<64, 32, 8, 4, 2><<<grid, 256, 0, h->st>>>(g); break;
+        case CFG_128x16: zgemm_kb_kernel<128, 16, 8, 8, 1><<<grid, 256, 0, h->st>>>(g); break;
+        default:         zgemm_kb_kernel<16, 16, 8, 1, 1><<<grid, 256, 0, h->st>>>(g); break;
+    }
+    ++h->launches;
+    if (g.nsplit > 1) {
+        zgemm_split_reduce<<<ew_grid((long long)g.nbatch * g.M * g.N), 256, 0, h->st>>>(g);
+        ++h->launches;
+    }
+    return 0;
+}
+
+int run_residual(ccsd_ctx* h) {
+    const int N = h->N, o = h->o, v = h->v;
+    for (const Step& s : h->seq) {
+        switch (s.kind) {
+            case 0: launch_gemm(h, h->gemms[s.idx]); break;
+            case 1: {
+                const CopyPlan& c = h->copies[s.idx];
+                copy_kernel<<<ew_grid(c.n), 256, 0, h->st>>>(h->buf[c.dst], h->buf[c.src], c.n, c.conj);
+                ++h->launches;
+                break;
+            }
+            case 2: {
+                const PermPlan& pp = h->perms[s.idx];
+                permute4_kernel<<<ew_grid((long long)pp.p.nbatch * pp.p.n0 * pp.p.n1 * pp.p.n2 * pp.p.n3), 256, 0, h->st>>>(
+                    h->buf[pp.dst], h->buf[pp.src], pp.p);
+                ++h->launches;
+                break;
+            }
+            case 3:
+                tau_kernel<<<ew_grid(h->n2), 256, 0, h->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_TAU], h->buf[B_TAUT],
+                                                               h->kb_of, N, o, v);
+                ++h->launches;
+                break;
+            case 4:
+                antisym_kernel<<<ew_grid(h->n2), 256, 0, h->st>>>(h->buf[B_R2], h->buf[B_ZAB], h->buf[B_ZIJ], h->buf[B_ZR],
+                                                                   h->kb_of, N, o, v);
+                ++h->launches;
+                break;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { last_err(e); return CCSD_ERR_CUDA; }
+    return 0;
+}
+
+int reduce_max(ccsd_ctx* h, const double2* x, long long n, double* out_host) {
+    maxabs_partial<<<h->red_blocks, 256, 0, h->st>>>(x, n, h->red);
+    final_max<<<1, 32, 0, h->st>>>(h->red, h->red_blocks, h->red_out);
+    h->launches += 2;
+    CK(cudaMemcpyAsync(out_host, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return 0;
+}
+
+int reduce_redot(ccsd_ctx* h, const double2* x, const double2* y, long long n, double* out_host) {
+    redot_partial<<<h->red_blocks, 256, 0, h->st>>>(x, y, n, h->red);
+    final_sum<<<1, 32, 0, h->st>>>(h->red, h->red_blocks, h->red_out);
+    h->launches += 2;
+    CK(cudaMemcpyAsync(out_host, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return 0;
+}
+
+size_t footprint_bytes(const ccsd_config* c, int borrowed) {
+    const long long N = (long long)c->nk_dims[0] * c->nk_dims[1] * c->nk_dims[2];
+    const long long o = c->nocc, v = c->nvir;
+    const long long N3 = N * N * N;
+    const long long n1 = N * o * v, n2 = N3 * o * o * v * v;
+    long long el = 0;
+    if (!borrowed) el += N * (o * o + v * v + o * v) + N3 * (o * o * o * o + o * o * o * v + 2 * o * o * v * v + o * v * v * v + v * v * v * v);
+    el += 2 * (n1 + n2);                       // amplitudes, residual
+    el += 2 * n2;                              // tau, tau~
+    el += N3 * o * o * o * o;                  // Whh
+    el += N3 * v * v * v * v;                  // Wab
+    el += n2;                                  // Wring
+    el += 2 * N3 * o * o * o * v;              // Q, TT
+    el += 3 * n2;                              // ZAB, ZIJ, ZR
+    el += N * (2 * o * v + 2 * o * o + 2 * v * v);
+    el += 2LL * c->diis_depth * (n1 + n2);     // DIIS history
+    size_t bytes = (size_t)el * 16;
+    bytes += (size_t)64 << 20;                 // tables, split-K partials, reductions (bound)
+    return bytes;
+}
+
+bool valid_cfg(const ccsd_config* c) {
+    if (!c) return false;
+    for (int i = 0; i < 3; ++i) if (c->nk_dims[i] < 1 || c->nk_dims[i] > 64) return false;
+    if (c->nocc < 1 || c->nvir < 1 || c->nocc > 256 || c->nvir > 512) return false;
+    if (c->precision != CCSD_FP64) return false;
+    if (c->diis_depth < 0 || c->diis_depth == 1 || c->diis_depth > 8) return false;
+    const long long N = (long long)c->nk_dims[0] * c->nk_dims[1] * c->nk_dims[2];
+    const long long vvvv = (long long)c->nvir * c->nvir * c->nvir * c->nvir;
+    if (vvvv * 1 > (1LL << 30)) return false;          // block offsets are 32-bit inside a block
+    if (N * N * N * vvvv > (1LL << 40)) return false;
+    return true;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ccsd_footprint(const ccsd_config* cfg, int inputs_on_device, size_t* bytes) {
+    if (!valid_cfg(cfg) || !bytes) return CCSD_ERR_INVALID;
+    *bytes = footprint_bytes(cfg, inputs_on_device);
+    return CCSD_OK;
+}
+
+
+int ccsd_plan_check(const ccsd_config* cfg, long long* n_launches, size_t* table_bytes) {
+    if (!valid_cfg(cfg)) return CCSD_ERR_INVALID;
+    ccsd_ctx* h = new (std::nothrow) ccsd_ctx();
+    if (!h) return CCSD_ERR_OOM;
+    h->cfg = *cfg;
+    h->kg.init(cfg->nk_dims);
+    h->N = h->kg.N; h->o = cfg->nocc; h->v = cfg->nvir;
+    const long long N = h->N;
+    h->n1 = N * h->o * h->v;
+    h->n2 = N * N * N * h->o * h->o * h->v * h->v;
+    set_sizes(h);
+    Alloc al{h};
+    al.dry = true;
+    size_t work_need = 0;
+    const int rc = build_plan(h, al, work_need);
+    long long n = 0;
+    for (const Step& st : h->seq) n += (st.kind == 0 && h->gemms[st.idx].args.nsplit > 1) ? 2 : 1;
+    if (n_launches) *n_launches = n;
+    if (table_bytes) *table_bytes = h->owned_bytes;
+    delete h;
+    return rc;
+}
+
+int ccsd_create(const ccsd_config* cfg, const ccsd_inputs* in, void* stream, ccsd_t* out) {
+    if (!out) return CCSD_ERR_INVALID;
+    *out = nullptr;
+    if (!valid_cfg(cfg) || !in || in->int_dtype != CCSD_C128) return CCSD_ERR_INVALID;
+    const void* ins[9] = {in->f_oo, in->f_vv, in->f_ov, in->oooo, in->ooov, in->oovv, in->ovvo, in->ovvv, in->vvvv};
+    for (const void* p : ins) if (!p) return CCSD_ERR_INVALID;
+    ccsd_ctx* h = new (std::nothrow) ccsd_ctx();
+    if (!h) return CCSD_ERR_OOM;
+    h->cfg = *cfg;
+    h->kg.init(cfg->nk_dims);
+    h->N = h->kg.N; h->o = cfg->nocc; h->v = cfg->nvir;
+    h->st = (cudaStream_t)stream;
+    const long long N = h->N, o = h->o, v = h->v, N3 = N * N * N;
+    h->n1 = N * o * v;
+    h->n2 = N3 * o * o * v * v;
+    Alloc al{h};
+    auto fail = [&](int code) { ccsd_destroy(h); return code; };
+
+    // inputs: borrow device pointers, copy host ones
+    const long long sizes[9] = {N * o * o, N * v * v, N * o * v, N3 * o * o * o * o, N3 * o * o * o * v,
+                                N3 * o * o * v * v, N3 * o * o * v * v, N3 * o * v * v * v, N3 * v * v * v * v};
+    for (int i = 0; i < 9; ++i) {
+        if (is_device_ptr(ins[i])) {
+            h->buf[B_FOO_IN + i] = (double2*)ins[i];
+        } else {
+            double2* d = (double2*)al.get((size_t)sizes[i] * 16);
+            if (!d) return fail(al.err);
+            if (cudaMemcpyAsync(d, ins[i], (size_t)sizes[i] * 16, cudaMemcpyHostToDevice, h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
+            h->buf[B_FOO_IN + i] = d;
+        }
+    }
+    auto dalloc = [&](long long n) { return (double2*)al.get((size_t)n * 16); };
+    h->amp = dalloc(h->n1 + h->n2);
+    h->res = dalloc(h->n1 + h->n2);
+    if (!h->amp || !h->res) return fail(al.err);
+    h->buf[B_T1] = h->amp; h->buf[B_T2] = h->amp + h->n1;
+    h->buf[B_R1] = h->res; h->buf[B_R2] = h->res + h->n1;
+    h->buf[B_TAU] = dalloc(h->n2); h->buf[B_TAUT] = dalloc(h->n2);
+    h->buf[B_FOV] = dalloc(N * o * v); h->buf[B_FOO] = dalloc(N * o * o); h->buf[B_FVV] = dalloc(N * v * v);
+    h->buf[B_FOOP] = dalloc(N * o * o); h->buf[B_FVVP] = dalloc(N * v * v);
+    h->buf[B_WHH] = dalloc(N3 * o * o * o * o);
+    h->buf[B_WAB] = dalloc(N3 * v * v * v * v);
+    h->buf[B_WRING] = dalloc(h->n2);
+    h->buf[B_Q] = dalloc(N3 * o * o * o * v);
+    h->buf[B_TT] = dalloc(N3 * o * o * o * v);
+    h->buf[B_ZAB] = dalloc(h->n2); h->buf[B_ZIJ] = dalloc(h->n2); h->buf[B_ZR] = dalloc(h->n2);
+    if (al.err) return fail(al.err);
+    for (int d = 0; d < cfg->diis_depth; ++d) {
+        h->hx.push_back(dalloc(h->n1 + h->n2));
+        h->he.push_back(dalloc(h->n1 + h->n2));
+    }
+    if (al.err) return fail(al.err);
+    h->gram.assign(cfg->diis_depth, std::vector<double>(cfg->diis_depth, 0.0));
+    if (cudaMemsetAsync(h->amp, 0, (size_t)(h->n1 + h->n2) * 16, h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
+
+    // Fock diagonals and the fourth momentum of doubles blocks
+    {
+        std::vector<double2> foo((size_t)(N * o * o)), fvv((size_t)(N * v * v));
+        if (cudaMemcpyAsync(foo.data(), h->buf[B_FOO_IN], foo.size() * 16, cudaMemcpyDefault, h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
+        if (cudaMemcpyAsync(fvv.data(), h->buf[B_FVV_IN], fvv.size() * 16, cudaMemcpyDefault, h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
+        if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
+        std::vector<double> eo((size_t)(N * o)), ev((size_t)(N * v));
+        for (long long k = 0; k < N; ++k) {
+            for (long long i = 0; i < o; ++i) eo[(size_t)(k * o + i)] = foo[(size_t)((k * o + i) * o + i)].x;
+            for (long long a = 0; a < v; ++a) ev[(size_t)(k * v + a)] = fvv[(size_t)((k * v + a) * v + a)].x;
+        }
+        for (double x : eo) for (double y : ev) if (!(x - y < 0.0 || x - y > 0.0)) return fail(CCSD_ERR_INVALID);
+        h->eo = upload(al, eo, h->st);
+        h->ev = upload(al, ev, h->st);
+        std::vector<int> kb((size_t)N3);
+        for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka)
+            kb[(size_t)(((long long)ki * N + kj) * N + ka)] = h->kg.k4(ki, kj, ka);
+        h->kb_of = upload(al, kb, h->st);
+        if (al.err) return fail(al.err);
+    }
+    set_sizes(h);
+    size_t work_need = 0;
+    int rc = build_plan(h, al, work_need);
+    if (rc) return fail(rc);
+    if (work_need) { h->work = dalloc((long long)work_need); if (!h->work) return fail(al.err); }
+    h->red_blocks = 152 * 4;
+    h->red = (double*)al.get(sizeof(double) * h->red_blocks);
+    h->red_out = (double*)al.get(sizeof(double) * 4);
+    h->cred = (double2*)al.get(sizeof(double2) * h->red_blocks);
+    h->cred_out = (double2*)al.get(sizeof(double2) * 2);
+    if (al.err) return fail(al.err);
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
+    *out = h;
+    return CCSD_OK;
+}
+
+int ccsd_residual(ccsd_t h, const void* t1, const void* t2, void* r1, void* r2) {
+    if (!h || !t1 || !t2 || !r1 || !r2) return CCSD_ERR_INVALID;
+    h->launches = 0;
+    double2* save[4] = {h->buf[B_T1], h->buf[B_T2], h->buf[B_R1], h->buf[B_R2]};
+    h->buf[B_T1] = (double2*)t1; h->buf[B_T2] = (double2*)t2;
+    h->buf[B_R1] = (double2*)r1; h->buf[B_R2] = (double2*)r2;
+    int rc = run_residual(h);
+    h->buf[B_T1] = save[0]; h->buf[B_T2] = save[1]; h->buf[B_R1] = save[2]; h->buf[B_R2] = save[3];
+    return rc;
+}
+
+int ccsd_iterate(ccsd_t h, int n_iter, int* done, double* max_resid) {
+    if (!h || n_iter < 0) return CCSD_ERR_INVALID;
+    if (done) *done = 0;
+    h->launches = 0;
+    const long long n = h->n1 + h->n2;
+    double mr = 0.0;
+    for (int it = 0; it < n_iter; ++it) {
+        int rc = run_residual(h);
+        if (rc) return rc;
+        if ((rc = reduce_max(h, h->res, n, &mr))) return rc;
+        if (max_resid) *max_resid = mr;
+        if (!std::isfinite(mr)) return CCSD_ERR_DIVERGED;
+        if (mr < h->cfg.conv_tol) { if (done) *done = 1; return CCSD_OK; }
+        const int depth = h->cfg.diis_depth;
+        if (depth == 0) {
+            update_kernel<<<ew_grid(n), 256, 0, h->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_R1], h->buf[B_R2],
+                                                         h->eo, h->ev, h->kb_of, h->N, h->o, h->v, nullptr, nullptr);
+            ++h->launches;
+        } else {
+            const int slot = h->diis_next;
+            double2* x = h->hx[slot];
+            double2* e = h->he[slot];
+            CK(cudaMemcpyAsync(x, h->amp, (size_t)n * 16, cudaMemcpyDeviceToDevice, h->st));
+            update_kernel<<<ew_grid(n), 256, 0, h->st>>>(x, x + h->n1, h->buf[B_R1], h->buf[B_R2],
+                                                         h->eo, h->ev, h->kb_of, h->N, h->o, h->v, e, e + h->n1);
+            ++h->launches;
+            h->diis_next = (slot + 1) % depth;
+            if (h->diis_count < depth) ++h->diis_count;
+            const int m = h->diis_count;
+            for (int j = 0; j < m; ++j) {
+                double d = 0.0;
+                if ((rc = reduce_redot(h, e, h->he[j], n, &d))) return rc;
+                h->gram[slot][j] = h->gram[j][slot] = d;
+            }
+            if (m < 2) {
+                CK(cudaMemcpyAsync(h->amp, x, (size_t)n * 16, cudaMemcpyDeviceToDevice, h->st));
+            } else {
+                // Pulay: [B -1; -1 0][c; l] = [0; -1], solved by Gaussian elimination with pivoting
+                const int S = m + 1;
+                std::vector<double> A((size_t)S * S, 0.0), b((size_t)S, 0.0);
+                for (int i = 0; i < m; ++i) for (int j = 0; j < m; ++j) A[(size_t)i * S + j] = h->gram[i][j];
+                for (int i = 0; i < m; ++i) { A[(size_t)i * S + m] = -1.0; A[(size_t)m * S + i] = -1.0; }
+                b[(size_t)m] = -1.0;
+                for (int c = 0; c < S; ++c) {
+                    int p = c;
+                    for (int r = c + 1; r < S; ++r) if (std::fabs(A[(size_t)r * S + c]) > std::fabs(A[(size_t)p * S + c])) p = r;
+                    if (p != c) { for (int k = 0; k < S; ++k) std::swap(A[(size_t)c * S + k], A[(size_t)p * S + k]); std::swap(b[c], b[p]); }
+                    const double piv = A[(size_t)c * S + c];
+                    if (piv == 0.0) return CCSD_ERR_DIVERGED;
+                    for (int r = c + 1; r < S; ++r) {
+                        const double f = A[(size_t)r * S + c] / piv;
+                        for (int k = c; k < S; ++k) A[(size_t)r * S + k] -= f * A[(size_t)c * S + k];
+                        b[r] -= f * b[c];
+                    }
+                }
+                std::vector<double> xs((size_t)S, 0.0);
+                for (int r = S - 1; r >= 0; --r) {
+                    double s = b[r];
+                    for (int k = r + 1; k < S; ++k) s -= A[(size_t)r * S + k] * xs[k];
+                    xs[r] = s / A[(size_t)r * S + r];
+                }
+                Combo cb{};
+                cb.m = m;
+                for (int j = 0; j < m; ++j) { cb.x[j] = h->hx[j]; cb.c[j] = xs[j]; }
+                combo_kernel<<<ew_grid(n), 256, 0, h->st>>>(h->amp, cb, n);
+                ++h->launches;
+            }
+        }
+        cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) { last_err(ce); return CCSD_ERR_CUDA; }
+    }
+    CK(cudaStreamSynchronize(h->st));
+    return CCSD_OK;
+}
+
+int ccsd_solve(ccsd_t h, int* iterations, double* max_resid) {
+    if (!h) return CCSD_ERR_INVALID;
+    int done = 0, it = 0;
+    double mr = 0.0;
+    for (; it <= h->cfg.max_iter; ++it) {
+        int rc = ccsd_iterate(h, 1, &done, &mr);
+        if (rc) { if (iterations) *iterations = it; return rc; }
+        if (done) break;
+    }
+    if (iterations) *iterations = it;
+    if (max_resid) *max_resid = mr;
+    return done ? CCSD_OK : CCSD_ERR_NOT_CONVERGED;
+}
+
+int ccsd_energy(ccsd_t h, double* e_real, double* e_imag) {
+    if (!h) return CCSD_ERR_INVALID;
+    energy_partial<<<h->red_blocks, 256, 0, h->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_FOV_IN], h->buf[B_OOVV],
+                                                     h->N, h->o, h->v, h->cred);
+    final_csum<<<1, 32, 0, h->st>>>(h->cred, h->red_blocks, h->cred_out);
+    double2 e;
+    CK(cudaMemcpyAsync(&e, h->cred_out, sizeof(double2), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (e_real) *e_real = e.x / h->N;
+    if (e_imag) *e_imag = e.y / h->N;
+    return CCSD_OK;
+}
+
+int ccsd_get_amplitudes(ccsd_t h, void* t1, void* t2) {
+    if (!h || !t1 || !t2) return CCSD_ERR_INVALID;
+    CK(cudaMemcpyAsync(t1, h->buf[B_T1], (size_t)h->n1 * 16, cudaMemcpyDefault, h->st));
+    CK(cudaMemcpyAsync(t2, h->buf[B_T2], (size_t)h->n2 * 16, cudaMemcpyDefault, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return CCSD_OK;
+}
+
+int ccsd_set_amplitudes(ccsd_t h, const void* t1, const void* t2) {
+    if (!h || !t1 || !t2) return CCSD_ERR_INVALID;
+    CK(cudaMemcpyAsync(h->buf[B_T1], t1, (size_t)h->n1 * 16, cudaMemcpyDefault, h->st));
+    CK(cudaMemcpyAsync(h->buf[B_T2], t2, (size_t)h->n2 * 16, cudaMemcpyDefault, h->st));
+    h->diis_count = 0; h->diis_next = 0;
+    CK(cudaStreamSynchronize(h->st));
+    return CCSD_OK;
+}
+
+int ccsd_last_launch_count(ccsd_t h, long long* launches) {
+    if (!h || !launches) return CCSD_ERR_INVALID;
+    *launches = h->launches;
+    return CCSD_OK;
+}
+
+int ccsd_destroy(ccsd_t h) {
+    if (!h) return CCSD_ERR_INVALID;
+    if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
+    for (void* p : h->owned) cudaFree(p);
+    delete h;
+    return CCSD_OK;
+}
+
+const char* ccsd_strerror(int code) {
+    switch (code) {
+        case CCSD_OK: return "ok";
+        case CCSD_ERR_INVALID: return "invalid argument (shape, null pointer, dtype or config)";
+        case CCSD_ERR_OOM: return "device memory exhausted or admission refused";
+        case CCSD_ERR_CUDA: return "CUDA runtime error";
+        case CCSD_ERR_NOT_CONVERGED: return "iteration limit reached before convergence";
+        case CCSD_ERR_DIVERGED: return "non-finite or diverging residual";
+        case CCSD_ERR_TIMEOUT: return "bounded device wait gave up";
+        default: return "unknown error code";
+    }
+}
+
+}  // extern "C"

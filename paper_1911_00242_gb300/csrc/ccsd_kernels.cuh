@@ -1,0 +1,285 @@
+// Elementwise and reduction kernels of the CCSD iteration (FP64).
+//
+// Layout conventions (row-major, complex interleaved):
+//   t1/R1  [k][i][a]               t2/R2/tau  [ki][kj][ka][i][j][a][b], kb implied
+// `kb_of[(ki*N + kj)*N + ka]` is the fourth momentum of a doubles block,
+// `neg` tables are not needed: every map below is precomputed on the host.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ccsdk {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// tau~ = t2 + 1/2 x and tau = t2 + x with
+// x = delta(ki,ka) t_i^a t_j^b - delta(ki,kb) t_i^b t_j^a
+// (paper Sec. 2: 1/4 and 1/2 of P(ab)P(ij) t1 t1, whose four terms pair up).
+__global__ void tau_kernel(const double2* __restrict__ t1, const double2* __restrict__ t2,
+                           double2* __restrict__ tau, double2* __restrict__ taut,
+                           const int* __restrict__ kb_of, int N, int o, int v)
+{
+    const long long blk = (long long)o * o * v * v;
+    const long long total = (long long)N * N * N * blk;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long kk = e / blk;
+        int r = (int)(e % blk);
+        const int b = r % v; r /= v;
+        const int a = r % v; r /= v;
+        const int j = r % o; const int i = r / o;
+        const int ka = (int)(kk % N), kj = (int)((kk / N) % N), ki = (int)(kk / ((long long)N * N));
+        const int kb = kb_of[kk];
+        double2 x = make_double2(0.0, 0.0);
+        if (ki == ka) {
+            const double2 p = cmul(t1[((long long)ki * o + i) * v + a], t1[((long long)kj * o + j) * v + b]);
+            x.x += p.x; x.y += p.y;
+        }
+        if (ki == kb) {
+            const double2 p = cmul(t1[((long long)ki * o + i) * v + b], t1[((long long)kj * o + j) * v + a]);
+            x.x -= p.x; x.y -= p.y;
+        }
+        const double2 t = t2[e];
+        tau[e] = make_double2(t.x + x.x, t.y + x.y);
+        taut[e] = make_double2(t.x + 0.5 * x.x, t.y + 0.5 * x.y);
+    }
+}
+
+// dst = conj(src) or dst = src, n elements
+__global__ void copy_kernel(double2* __restrict__ dst, const double2* __restrict__ src, long long n, int conj)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        double2 s = src[e];
+        if (conj) s.y = -s.y;
+        dst[e] = s;
+    }
+}
+
+// Batched 4-index permuted copy:
+//   dst[offD[b] + i0*d0 + i1*d1 + i2*d2 + i3*d3] = src[offS[b] + i0*s0 + i1*s1 + i2*s2 + i3*s3]
+struct Perm4 {
+    const long long* offD; const long long* offS;
+    int n0, n1, n2, n3;
+    int d0, d1, d2, d3, s0, s1, s2, s3;
+    int nbatch;
+};
+__global__ void permute4_kernel(double2* __restrict__ dst, const double2* __restrict__ src, const Perm4 p)
+{
+    const long long blk = (long long)p.n0 * p.n1 * p.n2 * p.n3;
+    const long long total = blk * p.nbatch;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long b = e / blk;
+        int r = (int)(e % blk);
+        const int i3 = r % p.n3; r /= p.n3;
+        const int i2 = r % p.n2; r /= p.n2;
+        const int i1 = r % p.n1; const int i0 = r / p.n1;
+        dst[p.offD[b] + (long long)i0 * p.d0 + (long long)i1 * p.d1 + (long long)i2 * p.d2 + (long long)i3 * p.d3] =
+            src[p.offS[b] + (long long)i0 * p.s0 + (long long)i1 * p.s1 + (long long)i2 * p.s2 + (long long)i3 * p.s3];
+    }
+}
+
+// R2 += Zab - Zab(a<->b) + Zij - Zij(i<->j) + Zr - Zr(i<->j) - Zr(a<->b) + Zr(both):
+// the P_-(ab), P_-(ij) and P_-(ij)P_-(ab) of Eq. ori_EqDouble (operator of Sec. 2;
+// swapping an index swaps its momentum too).
+__global__ void antisym_kernel(double2* __restrict__ R2, const double2* __restrict__ Zab,
+                               const double2* __restrict__ Zij, const double2* __restrict__ Zr,
+                               const int* __restrict__ kb_of, int N, int o, int v)
+{
+    const long long blk = (long long)o * o * v * v;
+    const long long total = (long long)N * N * N * blk;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long kk = e / blk;
+        int r = (int)(e % blk);
+        const int b = r % v; r /= v;
+        const int a = r % v; r /= v;
+        const int j = r % o; const int i = r / o;
+        const int ka = (int)(kk % N), kj = (int)((kk / N) % N), ki = (int)(kk / ((long long)N * N));
+        const int kb = kb_of[kk];
+        // (ki,kj,ka)(i,j,a,b) ; (i<->j): (kj,ki,ka)(j,i,a,b) ; (a<->b): (ki,kj,kb)(i,j,b,a)
+        const long long e_ij = (((long long)kj * N + ki) * N + ka) * blk + (((long long)j * o + i) * v + a) * v + b;
+        const long long e_ab = (((long long)ki * N + kj) * N + kb) * blk + (((long long)i * o + j) * v + b) * v + a;
+        const long long e_2 = (((long long)kj * N + ki) * N + kb) * blk + (((long long)j * o + i) * v + b) * v + a;
+        const double2 x0 = Zab[e], x1 = Zab[e_ab], y0 = Zij[e], y1 = Zij[e_ij];
+        const double2 z0 = Zr[e], z1 = Zr[e_ij], z2 = Zr[e_ab], z3 = Zr[e_2];
+        double2 out = R2[e];
+        out.x += x0.x - x1.x + y0.x - y1.x + z0.x - z1.x - z2.x + z3.x;
+        out.y += x0.y - x1.y + y0.y - y1.y + z0.y - z1.y - z2.y + z3.y;
+        R2[e] = out;
+    }
+}
+
+// Block-wise max |R| partials over an array (grid-stride; fixed per-thread order).
+__global__ void maxabs_partial(const double2* __restrict__ x, long long n, double* __restrict__ part)
+{
+    __shared__ double sm[256];
+    double m = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const double2 z = x[e];
+        const double a = sqrt(z.x * z.x + z.y * z.y);
+        m = (a > m || a != a) ? a : m;     // NaN propagates
+    }
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            const double o2 = sm[threadIdx.x + s];
+            if (o2 > sm[threadIdx.x] || o2 != o2) sm[threadIdx.x] = o2;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// t1 += R1 / D1, t2 += R2 / D2 (paper Sec. 4.4.13), D from the Fock diagonal
+// eo[k][i], ev[k][a].  When err != nullptr also stores e = R / D (DIIS error).
+__global__ void update_kernel(double2* __restrict__ t1, double2* __restrict__ t2,
+                              const double2* __restrict__ R1, const double2* __restrict__ R2,
+                              const double* __restrict__ eo, const double* __restrict__ ev,
+                              const int* __restrict__ kb_of, int N, int o, int v,
+                              double2* __restrict__ err1, double2* __restrict__ err2)
+{
+    const long long n1 = (long long)N * o * v;
+    const long long blk = (long long)o * o * v * v;
+    const long long total = n1 + (long long)N * N * N * blk;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        if (e < n1) {
+            const int a = (int)(e % v);
+            const int i = (int)((e / v) % o);
+            const int k = (int)(e / ((long long)o * v));
+            const double d = eo[k * o + i] - ev[k * v + a];
+            const double2 r = R1[e];
+            const double2 q = make_double2(r.x / d, r.y / d);
+            double2 t = t1[e];
+            t.x += q.x; t.y += q.y;
+            t1[e] = t;
+            if (err1) err1[e] = q;
+        } else {
+            const long long f = e - n1;
+            const long long kk = f / blk;
+            int r = (int)(f % blk);
+            const int b = r % v; r /= v;
+            const int a = r % v; r /= v;
+            const int j = r % o; const int i = r / o;
+            const int ka = (int)(kk % N), kj = (int)((kk / N) % N), ki = (int)(kk / ((long long)N * N));
+            const int kb = kb_of[kk];
+            const double d = eo[ki * o + i] + eo[kj * o + j] - ev[ka * v + a] - ev[kb * v + b];
+            const double2 rr = R2[f];
+            const double2 q = make_double2(rr.x / d, rr.y / d);
+            double2 t = t2[f];
+            t.x += q.x; t.y += q.y;
+            t2[f] = t;
+            if (err2) err2[f] = q;
+        }
+    }
+}
+
+// Energy partial sums: sum f_ia t_i^a + 1/4 sum <ij||ab> t_ij^ab
+//                    + 1/2 sum_{ki,kj} <i ki j kj||a ki b kj> t_i^a t_j^b.
+__global__ void energy_partial(const double2* __restrict__ t1, const double2* __restrict__ t2,
+                               const double2* __restrict__ fov, const double2* __restrict__ oovv,
+                               int N, int o, int v, double2* __restrict__ part)
+{
+    __shared__ double sr[256], si[256];
+    const long long n1 = (long long)N * o * v;
+    const long long blk = (long long)o * o * v * v;
+    const long long n2 = (long long)N * N * N * blk;
+    double er = 0.0, ei = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n1 + n2;
+         e += (long long)gridDim.x * blockDim.x) {
+        if (e < n1) {
+            const double2 p = cmul(fov[e], t1[e]);
+            er += p.x; ei += p.y;
+        } else {
+            const long long f = e - n1;
+            const double2 g = oovv[f];
+            double2 amp = t2[f];
+            amp.x *= 0.25; amp.y *= 0.25;
+            const long long kk = f / blk;
+            const int ka = (int)(kk % N), kj = (int)((kk / N) % N), ki = (int)(kk / ((long long)N * N));
+            if (ka == ki) {
+                int r = (int)(f % blk);
+                const int b = r % v; r /= v;
+                const int a = r % v; r /= v;
+                const int j = r % o; const int i = r / o;
+                const double2 q = cmul(t1[((long long)ki * o + i) * v + a], t1[((long long)kj * o + j) * v + b]);
+                amp.x += 0.5 * q.x; amp.y += 0.5 * q.y;
+            }
+            const double2 p = cmul(g, amp);
+            er += p.x; ei += p.y;
+        }
+    }
+    sr[threadIdx.x] = er; si[threadIdx.x] = ei;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) { sr[threadIdx.x] += sr[threadIdx.x + s]; si[threadIdx.x] += si[threadIdx.x + s]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sr[0], si[0]);
+}
+
+// Re <x|y> partial sums over n complex elements (DIIS Gram matrix).
+__global__ void redot_partial(const double2* __restrict__ x, const double2* __restrict__ y, long long n,
+                              double* __restrict__ part)
+{
+    __shared__ double sm[256];
+    double s = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const double2 a = x[e], b = y[e];
+        s += a.x * b.x + a.y * b.y;
+    }
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// Fixed-order final reductions (one block).
+__global__ void final_max(const double* __restrict__ part, int n, double* __restrict__ out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < n; ++i) { const double x = part[i]; if (x > m || x != x) m = x; }
+        *out = m;
+    }
+}
+__global__ void final_sum(const double* __restrict__ part, int n, double* __restrict__ out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += part[i];
+        *out = s;
+    }
+}
+__global__ void final_csum(const double2* __restrict__ part, int n, double2* __restrict__ out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double r = 0.0, i2 = 0.0;
+        for (int i = 0; i < n; ++i) { r += part[i].x; i2 += part[i].y; }
+        *out = make_double2(r, i2);
+    }
+}
+
+// x = sum_h c_h x_h over up to 8 history vectors (DIIS extrapolation).
+struct Combo { const double2* x[8]; double c[8]; int m; };
+__global__ void combo_kernel(double2* __restrict__ out, const Combo cb, long long n)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        double r = 0.0, im = 0.0;
+        for (int h = 0; h < cb.m; ++h) { const double2 z = cb.x[h][e]; r += cb.c[h] * z.x; im += cb.c[h] * z.y; }
+        out[e] = make_double2(r, im);
+    }
+}
+
+}  // namespace ccsdk

@@ -1,0 +1,161 @@
+// k-blocked batched complex GEMM (SIMT, FP64 DFMA).
+//
+//   C_b (+)= alpha * sum_{c < nchunk} opA(A_{b,c}) opB(B_{b,c})      b < nbatch
+//
+// Every contraction of the periodic CCSD residual is a sum over one
+// "chunk" momentum (k_e, k_n, k_m, ...) of dense orbital contractions between
+// momentum blocks whose positions follow from momentum conservation (paper
+// Sec. 3.2.5).  The position of block (b, c) of each operand is an element
+// offset in a device table; inside a block the element (r, s) sits at
+// row_off[r] + col_off[s], which expresses any index permutation of a
+// row-major orbital block (all CCSD layouts are separable that way).  This
+// replaces the paper's ALLTOALL "index changes" (Sec. 4.3.3): operands are
+// read in place, whatever their storage order.
+//
+// GB300's FP64 pipe (about 1 TFLOP/s, a 75th of its FP32 rate) is the bound:
+// one 64x64x8 complex tile step is ~130k DFMA, so global loads without
+// staging overlap are a rounding error and tiles are chosen to waste as few
+// DFMAs on padding as possible.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ccsdk {
+
+struct GemmArgs {
+    const double2* A; const long long* offA; const int* rowA; const int* colA;
+    const double2* B; const long long* offB; const int* rowB; const int* colB;
+    double2* C;       const long long* offC; const int* rowC; const int* colC;
+    double2* work;    // split partials [nsplit][nbatch][M*N] when nsplit > 1
+    int M, N, K, nbatch, nchunk, nsplit, chunks_per_split;
+    int conjA, conjB, accumulate;
+    double alpha_re, alpha_im;
+    int tiles_m, tiles_n;
+};
+
+template <int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+zgemm_kb_kernel(const GemmArgs g)
+{
+    constexpr int NT = (BM / TM) * (BN / TN);
+    constexpr int TX = BN / TN;
+    __shared__ double2 As[BK][BM];
+    __shared__ double2 Bs[BK][BN];
+
+    const int ntile = g.tiles_m * g.tiles_n;
+    const int tile = blockIdx.x % ntile;
+    const long long b = blockIdx.x / ntile;
+    const int split = blockIdx.y;
+    const int m0 = (tile % g.tiles_m) * BM;
+    const int n0 = (tile / g.tiles_m) * BN;
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+
+    double cr[TM][TN], ci[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) { cr[i][j] = 0.0; ci[i][j] = 0.0; }
+
+    const double sa = g.conjA ? -1.0 : 1.0;
+    const double sb = g.conjB ? -1.0 : 1.0;
+    const int c_begin = split * g.chunks_per_split;
+    int c_end = c_begin + g.chunks_per_split;
+    if (c_end > g.nchunk) c_end = g.nchunk;
+
+    for (int c = c_begin; c < c_end; ++c) {
+        const double2* Ab = g.A + g.offA[b * g.nchunk + c];
+        const double2* Bb = g.B + g.offB[b * g.nchunk + c];
+        for (int k0 = 0; k0 < g.K; k0 += BK) {
+            for (int e = tid; e < BM * BK; e += NT) {
+                const int mm = e % BM, kk = e / BM;
+                const int m = m0 + mm, k = k0 + kk;
+                double2 v = make_double2(0.0, 0.0);
+                if (m < g.M && k < g.K) {
+                    v = __ldg(Ab + (long long)g.rowA[m] + g.colA[k]);
+                    v.y *= sa;
+                }
+                As[kk][mm] = v;
+            }
+            for (int e = tid; e < BN * BK; e += NT) {
+                const int nn = e % BN, kk = e / BN;
+                const int n = n0 + nn, k = k0 + kk;
+                double2 v = make_double2(0.0, 0.0);
+                if (n < g.N && k < g.K) {
+                    v = __ldg(Bb + (long long)g.rowB[k] + g.colB[n]);
+                    v.y *= sb;
+                }
+                Bs[kk][nn] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                double2 a[TM], bb[TN];
+#pragma unroll
+                for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+                for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) {
+                        cr[i][j] = fma(a[i].x, bb[j].x, cr[i][j]);
+                        cr[i][j] = fma(-a[i].y, bb[j].y, cr[i][j]);
+                        ci[i][j] = fma(a[i].x, bb[j].y, ci[i][j]);
+                        ci[i][j] = fma(a[i].y, bb[j].x, ci[i][j]);
+                    }
+            }
+            __syncthreads();
+        }
+    }
+
+    if (g.nsplit > 1) {
+        double2* W = g.work + ((long long)split * g.nbatch + b) * (long long)g.M * g.N;
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int m = m0 + ty * TM + i, n = n0 + tx * TN + j;
+                if (m < g.M && n < g.N) W[(long long)m * g.N + n] = make_double2(cr[i][j], ci[i][j]);
+            }
+        return;
+    }
+    double2* Cb = g.C + g.offC[b];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int m = m0 + ty * TM + i, n = n0 + tx * TN + j;
+            if (m < g.M && n < g.N) {
+                double2* p = Cb + (long long)g.rowC[m] + g.colC[n];
+                const double re = g.alpha_re * cr[i][j] - g.alpha_im * ci[i][j];
+                const double im = g.alpha_re * ci[i][j] + g.alpha_im * cr[i][j];
+                if (g.accumulate) { double2 o = *p; o.x += re; o.y += im; *p = o; }
+                else *p = make_double2(re, im);
+            }
+        }
+}
+
+// Deterministic split-K reduction: C_b (+)= alpha * sum_s work[s][b] in split order.
+__global__ void zgemm_split_reduce(const GemmArgs g)
+{
+    const long long total = (long long)g.nbatch * g.M * g.N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long b = e / ((long long)g.M * g.N);
+        const int mn = (int)(e % ((long long)g.M * g.N));
+        const int m = mn / g.N, n = mn % g.N;
+        double re = 0.0, im = 0.0;
+        for (int s = 0; s < g.nsplit; ++s) {
+            const double2 w = g.work[((long long)s * g.nbatch + b) * (long long)g.M * g.N + mn];
+            re += w.x; im += w.y;
+        }
+        double2* p = g.C + g.offC[b] + (long long)g.rowC[m] + g.colC[n];
+        const double r2 = g.alpha_re * re - g.alpha_im * im;
+        const double i2 = g.alpha_re * im + g.alpha_im * re;
+        if (g.accumulate) { double2 o = *p; o.x += r2; o.y += i2; *p = o; }
+        else *p = make_double2(r2, i2);
+    }
+}
+
+}  // namespace ccsdk
