@@ -74,6 +74,8 @@ CONFIGS = {
     "chain_k4_o4_v8": SynthSpec((4, 1, 1), 4, 8, 1001),
     "grid222_o8_v32": SynthSpec((2, 2, 2), 8, 32, 1002),
     "grid333_o8_v24_c64": SynthSpec((3, 3, 3), 8, 24, 1003, int_dtype="c64"),
+    # smaller grid with the FP64 workload's orbitals, for profiling captures
+    "grid221_o8_v32": SynthSpec((2, 2, 1), 8, 32, 1012),
 }
 
 

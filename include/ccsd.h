@@ -120,6 +120,18 @@ int ccsd_set_amplitudes(ccsd_t h, const void* t1, const void* t2);
 /* Number of kernel launches the last ccsd_iterate/ccsd_residual call made. */
 int ccsd_last_launch_count(ccsd_t h, long long* launches);
 
+/* Tracing: with tracing enabled, every step of the residual plan and the
+ * amplitude update are bracketed by CUDA events on the handle's stream and
+ * their durations accumulate per step (enabling resets the accumulators).
+ * Steps are numbered 0 .. n_steps-1 in launch order; the last is the update.
+ * For step i: its name, how often it ran, total milliseconds, algorithmic real
+ * flops per launch (a complex multiply-add counts 8) and algorithmic bytes per
+ * launch for the memory-bound steps (0 when not applicable). */
+int ccsd_trace_enable(ccsd_t h, int enable);
+int ccsd_trace_count(ccsd_t h, int* n_steps);
+int ccsd_trace_step(ccsd_t h, int i, const char** name, long long* calls, double* total_ms,
+                    double* flops, double* bytes);
+
 int ccsd_destroy(ccsd_t h);
 
 const char* ccsd_strerror(int code);

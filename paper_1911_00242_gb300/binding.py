@@ -51,6 +51,11 @@ SYMBOLS = {
     "ccsd_get_amplitudes": ([ctypes.c_void_p] * 3, ctypes.c_int),
     "ccsd_set_amplitudes": ([ctypes.c_void_p] * 3, ctypes.c_int),
     "ccsd_last_launch_count": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+    "ccsd_trace_enable": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "ccsd_trace_count": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "ccsd_trace_step": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                         ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
+                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "ccsd_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "ccsd_strerror": ([ctypes.c_int], ctypes.c_char_p),
 }
@@ -156,6 +161,23 @@ class Solver:
         n = ctypes.c_longlong(0)
         check(self.lib.ccsd_last_launch_count(self.h, ctypes.byref(n)), "ccsd_last_launch_count")
         return n.value
+
+    def trace(self, enable=True):
+        check(self.lib.ccsd_trace_enable(self.h, 1 if enable else 0), "ccsd_trace_enable")
+
+    def trace_steps(self):
+        """[(name, calls, total_ms, flops_per_call, bytes_per_call)] in launch order."""
+        n = ctypes.c_int(0)
+        check(self.lib.ccsd_trace_count(self.h, ctypes.byref(n)), "ccsd_trace_count")
+        out = []
+        for i in range(n.value):
+            nm = ctypes.c_char_p()
+            calls = ctypes.c_longlong(0)
+            ms, fl, by = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+            check(self.lib.ccsd_trace_step(self.h, i, ctypes.byref(nm), ctypes.byref(calls), ctypes.byref(ms),
+                                           ctypes.byref(fl), ctypes.byref(by)), "ccsd_trace_step")
+            out.append((nm.value.decode(), calls.value, ms.value, fl.value, by.value))
+        return out
 
     def close(self):
         if getattr(self, "h", None):

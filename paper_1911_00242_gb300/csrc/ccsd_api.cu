@@ -80,6 +80,9 @@ struct PermPlan {
 struct Step {           // one element of the launch sequence
     int kind;           // 0 gemm, 1 copy, 2 perm, 3 tau, 4 antisym
     int idx;
+    const char* name;
+    double flops;       // algorithmic real flops per launch (complex MAC = 8)
+    double bytes;       // algorithmic bytes per launch for the memory-bound steps
 };
 
 }  // namespace
@@ -113,6 +116,12 @@ struct ccsd_ctx {
     std::vector<Step> seq;
     long long launches = 0;
     int red_blocks = 0;
+    const char* cur_name = "";
+    // tracing: CUDA events around every step of the residual plan
+    int trace = 0;
+    std::vector<cudaEvent_t> ev0, ev1;
+    std::vector<double> step_ms;
+    std::vector<long long> step_calls;
 };
 
 namespace {
@@ -235,14 +244,15 @@ int finalize_gemm(ccsd_ctx* h, Alloc& al, GemmSpec s, size_t& work_need) {
     g.rowC = upload(al, s.rowC, h->st); g.colC = upload(al, s.colC, h->st);
     if (al.err) return al.err;
     h->gemms.push_back(p);
-    h->seq.push_back({0, (int)h->gemms.size() - 1});
+    h->seq.push_back({0, (int)h->gemms.size() - 1, h->cur_name,
+                      8.0 * s.M * (double)s.N * s.K * s.nchunk * s.nbatch, 0.0});
     return 0;
 }
 
 int add_copy(ccsd_ctx* h, int dst, int src, long long n, int conj) {
     if (n > h->bufsize[dst] || n > h->bufsize[src]) return CCSD_ERR_INVALID;
     h->copies.push_back({dst, src, n, conj});
-    h->seq.push_back({1, (int)h->copies.size() - 1});
+    h->seq.push_back({1, (int)h->copies.size() - 1, h->cur_name, 0.0, 32.0 * (double)n});
     return 0;
 }
 
@@ -265,7 +275,7 @@ int add_perm(ccsd_ctx* h, Alloc& al, int dst, int src, int n0, int n1, int n2, i
     pp.p.offS = upload(al, offS, h->st);
     if (al.err) return al.err;
     h->perms.push_back(pp);
-    h->seq.push_back({2, (int)h->perms.size() - 1});
+    h->seq.push_back({2, (int)h->perms.size() - 1, h->cur_name, 0.0, 32.0 * (double)offD.size() * n0 * n1 * n2 * n3});
     return 0;
 }
 
@@ -282,8 +292,9 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     auto G = [&](GemmSpec& s) { return finalize_gemm(h, al, s, work_need); };
 
     // ---------------- tau, tau~
-    h->seq.push_back({3, 0});
+    h->seq.push_back({3, 0, "tau", 0.0, 16.0 * (3.0 * h->n2 + h->n1)});
 
+    h->cur_name = "F_ov";
     // ---------------- F~_ov (Eq. ori_F_ov): f_ov + sum t_r^c <p k r k^||g k c k^>
     if ((rc = add_copy(h, B_FOV, B_FOV_IN, (long long)N * ov, 0))) return rc;
     {
@@ -298,6 +309,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{(int)ov, 1}}); s.colC = {0};
         if ((rc = G(s))) return rc;
     }
+    h->cur_name = "F_oo";
     // ---------------- F~_oo (Eq. ori_F_oo)
     if ((rc = add_copy(h, B_FOO, B_FOO_IN, (long long)N * oo, 0))) return rc;
     {   // + 1/2 sum_c f_p^c t_q^c
@@ -334,6 +346,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{o, o}}); s.colC = tab({{o, 1}});
         if ((rc = G(s))) return rc;
     }
+    h->cur_name = "F_vv";
     // ---------------- F~_vv (Eq. ori_F_vv)
     if ((rc = add_copy(h, B_FVV, B_FVV_IN, (long long)N * vv, 0))) return rc;
     {   // - 1/2 sum_r f_r^h t_r^g
@@ -370,6 +383,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{v, v}}); s.colC = tab({{v, 1}});
         if ((rc = G(s))) return rc;
     }
+    h->cur_name = "F_prime";
     // ---------------- F' combinations used by T2
     if ((rc = add_copy(h, B_FVVP, B_FVV, (long long)N * vv, 0))) return rc;
     {   // F~^bf - 1/2 sum_r t_r^b F~_r^f
@@ -391,6 +405,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{o, o}}); s.colC = tab({{o, 1}});
         if ((rc = G(s))) return rc;
     }
+    h->cur_name = "R1";
     // ---------------- R1 (Eq. ori_EqSingle); driver <a|f|i> = f_ov^*
     if ((rc = add_copy(h, B_R1, B_FOV_IN, (long long)N * ov, 1))) return rc;
     {   // + sum_c F~^{ac} t_i^c
@@ -462,9 +477,11 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         if ((rc = G(s))) return rc;
     }
 
+    h->cur_name = "R2_driver";
     // ---------------- R2 (Eq. ori_EqDouble); driver <ab||ij> = <ij||ab>^*
     if ((rc = add_copy(h, B_R2, B_OOVV, (long long)N * N * N * S2, 1))) return rc;
     const int N3 = N * N * N;
+    h->cur_name = "hole_hole_W";
     // hole-hole: Whh = <mn||ij> + P(ij) t_j^c <mn||ic> + 1/2 tau_ij^ef <mn||ef>
     if ((rc = add_copy(h, B_WHH, B_OOOO, (long long)N3 * Soooo, 0))) return rc;
     {
@@ -504,6 +521,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{(int)oo, oo}}); s.colC = tab({{(int)oo, 1}});
         if ((rc = G(s))) return rc;
     }
+    h->cur_name = "hole_hole";
     {   // R2 += 1/2 sum_km tau_{mn}^{ab} Whh_{mnij}
         GemmSpec s; s.a = B_WHH; s.b = B_TAU; s.c = B_R2; s.ar = 0.5;
         s.M = (int)oo; s.N = (int)vv; s.K = (int)oo; s.nbatch = N3; s.nchunk = N;
@@ -519,6 +537,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{(int)oo, vv}}); s.colC = tab({{(int)vv, 1}});
         if ((rc = G(s))) return rc;
     }
+    h->cur_name = "ladder_W";
     // ladder: Wab = <ab||ef> - P(ab) t_r^b <a r||e f>
     if ((rc = add_copy(h, B_WAB, B_VVVV, (long long)N3 * Svvvv, 0))) return rc;
     {   // + sum_r t_r^b(kb) ovvv[kb,ka,ke](r,a,e,f)
@@ -543,6 +562,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{v, vv}, {(int)vv, 1}}); s.colC = tab({{v, vv * v}});
         if ((rc = G(s))) return rc;
     }
+    h->cur_name = "ladder";
     {   // R2 += 1/2 sum_ke tau_ij^ef Wab^{abef}; batches grouped by (ka, kb) for L2 reuse
         GemmSpec s; s.a = B_TAU; s.b = B_WAB; s.c = B_R2; s.ar = 0.5;
         s.M = (int)oo; s.N = (int)vv; s.K = (int)vv; s.nbatch = N3; s.nchunk = N;
@@ -556,6 +576,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{(int)oo, vv}}); s.colC = tab({{(int)vv, 1}});
         if ((rc = G(s))) return rc;
     }
+    h->cur_name = "ring_W_t1";
     // ring: W~_jn^bf (Eq. Def_Woovv), stored [kj,kn,kb](j,n,b,f), kf = kn + kb - kj
     {
         std::vector<long long> offD, offS;
@@ -608,6 +629,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{v, v}}); s.colC = tab({{o, vv}, {o, o * vv}, {v, 1}});
         if ((rc = G(s))) return rc;
     }
+    h->cur_name = "ring_W_t2";
     {   // W -= 1/2 sum_kx t_{j x}^{y b} <n x||f y>
         GemmSpec s; s.a = B_T2; s.b = B_OOVV; s.c = B_WRING; s.ar = -0.5;
         s.M = (int)ov; s.N = (int)ov; s.K = (int)ov; s.nbatch = N3; s.nchunk = N;
@@ -624,6 +646,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{o, o * vv}, {v, v}}); s.colC = tab({{o, vv}, {v, 1}});
         if ((rc = G(s))) return rc;
     }
+    h->cur_name = "ring";
     {   // ZR = sum_kn t_{in}^{af} W_{jn}^{bf}
         GemmSpec s; s.a = B_T2; s.b = B_WRING; s.c = B_ZR; s.acc = false;
         s.M = (int)ov; s.N = (int)ov; s.K = (int)ov; s.nbatch = N3; s.nchunk = N;
@@ -637,6 +660,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{o, o * vv}, {v, v}}); s.colC = tab({{o, vv}, {v, 1}});
         if ((rc = G(s))) return rc;
     }
+    h->cur_name = "ring_t1t1";
     {   // TT(r,b,i,j) = sum_c <r ka b kb||c ki j kj> t_i^c ;  ZR -= sum_r t_r^a TT(r,b,i,j)
         GemmSpec s; s.a = B_OVVO; s.b = B_T1; s.c = B_TT; s.acc = false;
         s.M = (int)(ov * o); s.N = o; s.K = v; s.nbatch = N3; s.nchunk = 1;
@@ -658,6 +682,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s2.rowC = tab({{v, v}}); s2.colC = tab({{(int)oo, vv}, {v, 1}});
         if ((rc = G(s2))) return rc;
     }
+    h->cur_name = "fock_t1_terms";
     // remaining terms under P(ab) and P(ij)
     {   // ZAB = sum_f t_ij^af F'^{bf}(kb)
         GemmSpec s; s.a = B_T2; s.b = B_FVVP; s.c = B_ZAB; s.acc = false;
@@ -704,7 +729,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{o, o * vv}}); s.colC = tab({{o, vv}, {(int)vv, 1}});
         if ((rc = G(s))) return rc;
     }
-    h->seq.push_back({4, 0});
+    h->seq.push_back({4, 0, "antisym_R2", 0.0, 16.0 * 10.0 * h->n2});
     return 0;
 }
 
@@ -745,9 +770,23 @@ int launch_gemm(ccsd_ctx* h, GemmPlan& p) {
     return 0;
 }
 
+// Accumulate the elapsed time of traced steps [a, b) (synchronizes the stream).
+int trace_collect(ccsd_ctx* h, size_t a, size_t b) {
+    CK(cudaStreamSynchronize(h->st));
+    for (size_t i = a; i < b; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->ev0[i], h->ev1[i]));
+        h->step_ms[i] += ms;
+        h->step_calls[i] += 1;
+    }
+    return 0;
+}
+
 int run_residual(ccsd_ctx* h) {
     const int N = h->N, o = h->o, v = h->v;
-    for (const Step& s : h->seq) {
+    for (size_t si = 0; si < h->seq.size(); ++si) {
+        const Step& s = h->seq[si];
+        if (h->trace) cudaEventRecord(h->ev0[si], h->st);
         switch (s.kind) {
             case 0: launch_gemm(h, h->gemms[s.idx]); break;
             case 1: {
@@ -774,9 +813,11 @@ int run_residual(ccsd_ctx* h) {
                 ++h->launches;
                 break;
         }
+        if (h->trace) cudaEventRecord(h->ev1[si], h->st);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { last_err(e); return CCSD_ERR_CUDA; }
+    if (h->trace) return trace_collect(h, 0, h->seq.size());
     return 0;
 }
 
@@ -988,10 +1029,13 @@ int ccsd_iterate(ccsd_t h, int n_iter, int* done, double* max_resid) {
         if (!std::isfinite(mr)) return CCSD_ERR_DIVERGED;
         if (mr < h->cfg.conv_tol) { if (done) *done = 1; return CCSD_OK; }
         const int depth = h->cfg.diis_depth;
+        const size_t tu = h->seq.size();     // trace slot of the update
+        if (h->trace) cudaEventRecord(h->ev0[tu], h->st);
         if (depth == 0) {
             update_kernel<<<ew_grid(n), 256, 0, h->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_R1], h->buf[B_R2],
                                                          h->eo, h->ev, h->kb_of, h->N, h->o, h->v, nullptr, nullptr);
             ++h->launches;
+            if (h->trace) { cudaEventRecord(h->ev1[tu], h->st); if ((rc = trace_collect(h, tu, tu + 1))) return rc; }
         } else {
             const int slot = h->diis_next;
             double2* x = h->hx[slot];
@@ -1000,6 +1044,7 @@ int ccsd_iterate(ccsd_t h, int n_iter, int* done, double* max_resid) {
             update_kernel<<<ew_grid(n), 256, 0, h->st>>>(x, x + h->n1, h->buf[B_R1], h->buf[B_R2],
                                                          h->eo, h->ev, h->kb_of, h->N, h->o, h->v, e, e + h->n1);
             ++h->launches;
+            if (h->trace) { cudaEventRecord(h->ev1[tu], h->st); if ((rc = trace_collect(h, tu, tu + 1))) return rc; }
             h->diis_next = (slot + 1) % depth;
             if (h->diis_count < depth) ++h->diis_count;
             const int m = h->diis_count;
@@ -1099,10 +1144,47 @@ int ccsd_last_launch_count(ccsd_t h, long long* launches) {
     return CCSD_OK;
 }
 
+
+int ccsd_trace_enable(ccsd_t h, int enable) {
+    if (!h) return CCSD_ERR_INVALID;
+    const size_t n = h->seq.size() + 1;          // plan steps + the amplitude update
+    if (enable && h->ev0.empty()) {
+        h->ev0.resize(n); h->ev1.resize(n);
+        for (size_t i = 0; i < n; ++i) {
+            CK(cudaEventCreate(&h->ev0[i]));
+            CK(cudaEventCreate(&h->ev1[i]));
+        }
+    }
+    h->step_ms.assign(n, 0.0);
+    h->step_calls.assign(n, 0);
+    h->trace = enable ? 1 : 0;
+    return CCSD_OK;
+}
+
+int ccsd_trace_count(ccsd_t h, int* n_steps) {
+    if (!h || !n_steps) return CCSD_ERR_INVALID;
+    *n_steps = (int)h->seq.size() + 1;
+    return CCSD_OK;
+}
+
+int ccsd_trace_step(ccsd_t h, int i, const char** name, long long* calls, double* total_ms,
+                    double* flops, double* bytes) {
+    if (!h || i < 0 || i > (int)h->seq.size()) return CCSD_ERR_INVALID;
+    const bool upd = i == (int)h->seq.size();
+    if (name) *name = upd ? "update" : h->seq[i].name;
+    if (calls) *calls = i < (int)h->step_calls.size() ? h->step_calls[i] : 0;
+    if (total_ms) *total_ms = i < (int)h->step_ms.size() ? h->step_ms[i] : 0.0;
+    if (flops) *flops = upd ? 0.0 : h->seq[i].flops;
+    if (bytes) *bytes = upd ? (h->cfg.diis_depth ? 80.0 : 48.0) * (double)(h->n1 + h->n2) : h->seq[i].bytes;
+    return CCSD_OK;
+}
+
 int ccsd_destroy(ccsd_t h) {
     if (!h) return CCSD_ERR_INVALID;
     if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
     for (void* p : h->owned) cudaFree(p);
+    for (cudaEvent_t e : h->ev0) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->ev1) cudaEventDestroy(e);
     delete h;
     return CCSD_OK;
 }
