@@ -136,6 +136,26 @@ int ccsd_destroy(ccsd_t h);
 
 const char* ccsd_strerror(int code);
 
+/* Correlation energy per unit cell of the amplitudes t1, t2 (same expression
+ * as ccsd_energy), for callers that cannot allocate device memory: code
+ * running inside a CUDA stream capture, hosts whose allocator owns all device
+ * memory, loops that must not pay for an allocation.  The paper has no
+ * counterpart; this is a library convenience.
+ *   nk_dims, nocc, nvir  problem shape as in ccsd_config
+ *   f_ov, oovv, t1, t2   device pointers in the layout above (complex128)
+ *   e_out                device pointer to 2 doubles: real, imaginary part
+ *   stream               cudaStream_t the work is enqueued on (asynchronous)
+ * It allocates nothing: its scratch (one partial sum per momentum block) is a
+ * fixed 512 KiB device array inside the library, which every GPU that loads
+ * the library keeps until the process exits.  Requires N_k^3 + 1 <= 32768
+ * (N_k <= 31); larger grids return CCSD_ERR_INVALID before any launch.  The
+ * first call on a device looks the array's device address up once, so make
+ * that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (different streams, or different host
+ * threads on one device) race and must be serialized by the caller. */
+int ccsd_energy_noalloc(const int nk_dims[3], int nocc, int nvir, const void* f_ov, const void* oovv,
+                        const void* t1, const void* t2, void* e_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

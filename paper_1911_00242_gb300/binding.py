@@ -58,6 +58,8 @@ SYMBOLS = {
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "ccsd_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "ccsd_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "ccsd_energy_noalloc": ([ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 6,
+                            ctypes.c_int),
 }
 
 _lib = None

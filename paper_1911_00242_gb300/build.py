@@ -5,7 +5,7 @@ import subprocess
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libccsd_gb300.so")
-SOURCES = [os.path.join(PKG, "csrc", "ccsd_api.cu")]
+SOURCES = [os.path.join(PKG, "csrc", "ccsd_api.cu"), os.path.join(PKG, "csrc", "ccsd_noalloc.cu")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
