@@ -46,6 +46,10 @@ extern "C" {
 #define CCSD_ERR_TIMEOUT      (-6)  /* a bounded device wait gave up             */
 
 #define CCSD_FP64   0   /* every contraction in FP64 (DFMA)                    */
+#define CCSD_MIXED  1   /* contractions in FP32 arithmetic with FP32 accumulation
+                           (operands rounded from the FP64 data); update, norms,
+                           DIIS and energy stay FP64; ccsd_solve finishes with
+                           polish_iters FP64 iterations                       */
 
 #define CCSD_C128   0   /* integral blocks complex128                          */
 
@@ -54,12 +58,16 @@ typedef struct ccsd_ctx* ccsd_t;
 typedef struct {
     int    nk_dims[3];    /* k grid (n1, n2, n3), each >= 1                     */
     int    nocc, nvir;    /* occupied / virtual spin orbitals per k, >= 1       */
-    int    precision;     /* CCSD_FP64                                          */
+    int    precision;     /* CCSD_FP64 or CCSD_MIXED                            */
     int    diis_depth;    /* 0 = plain successive substitution (paper Sec. 4.4.12);
                              2..8 = Pulay DIIS over that many updates            */
     int    max_iter;      /* used by ccsd_solve                                 */
     double conv_tol;      /* max|R1| and max|R2| threshold, Eqs. (criterion_single,
                              criterion_double)                                   */
+    int    polish_iters;  /* CCSD_MIXED: FP64 iterations ccsd_solve runs after the
+                             mixed ones (0..100)                                 */
+    double mixed_tol;     /* CCSD_MIXED: ccsd_solve switches to FP64 once the mixed
+                             max|R| < max(mixed_tol, conv_tol)                  */
 } ccsd_config;
 
 typedef struct {
@@ -88,6 +96,12 @@ int ccsd_footprint(const ccsd_config* cfg, int inputs_on_device, size_t* bytes);
  * evaluation, *table_bytes the size of the plan's index tables. */
 int ccsd_plan_check(const ccsd_config* cfg, long long* n_launches, size_t* table_bytes);
 
+/* Self-test of the tensor-core GEMM of the mixed form: C = A B^T for random
+ * complex A (M x K) and B (Ncols x K) through the TF32 path (nterms 1: plain
+ * TF32, 3: split TF32) against the FP64 engine; *rel_err = max|dC| / max|C|.
+ * Sizes up to 4096.  CCSD_ERR_TIMEOUT if a bounded device wait gave up. */
+int ccsd_tc_selftest(int M, int Ncols, int K, int nterms, unsigned long long seed, double* rel_err);
+
 /* One residual evaluation R(t) (paper Eqs. ori_EqSingle, ori_EqDouble with the
  * full Fock matrix inside F~): t1, t2 are read and r1, r2 written, all device
  * pointers in the layout above (r1 like t1, r2 like t2).  Does not touch the
@@ -103,8 +117,16 @@ int ccsd_residual(ccsd_t h, const void* t1, const void* t2, void* r1, void* r2);
 int ccsd_iterate(ccsd_t h, int n_iter, int* done, double* max_resid);
 
 /* Iterates until convergence or cfg->max_iter updates; CCSD_ERR_NOT_CONVERGED
- * when the limit is reached (the amplitudes remain readable). */
+ * when the limit is reached (the amplitudes remain readable).  For CCSD_MIXED
+ * handles: mixed iterations until max|R| < max(mixed_tol, conv_tol), then up
+ * to polish_iters FP64 iterations (fewer if the FP64 max|R| < conv_tol);
+ * CCSD_OK when the mixed phase reached its tolerance. */
 int ccsd_solve(ccsd_t h, int* iterations, double* max_resid);
+
+/* Arithmetic of the following ccsd_iterate/ccsd_residual calls: CCSD_FP64 on
+ * any handle, CCSD_MIXED only on handles created with it.  Clears the DIIS
+ * history. */
+int ccsd_set_precision(ccsd_t h, int precision);
 
 /* Correlation energy of the current amplitudes per unit cell (supercell
  * total / N_k): sum f_ia t_i^a + 1/4 sum <ij||ab> t_ij^ab

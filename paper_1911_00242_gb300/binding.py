@@ -19,6 +19,7 @@ CCSD_ERR_NOT_CONVERGED = -4
 CCSD_ERR_DIVERGED = -5
 CCSD_ERR_TIMEOUT = -6
 CCSD_FP64 = 0
+CCSD_MIXED = 1
 CCSD_C128 = 0
 
 BLOCKS = ("oooo", "ooov", "oovv", "ovvo", "ovvv", "vvvv")
@@ -27,7 +28,7 @@ BLOCKS = ("oooo", "ooov", "oovv", "ovvo", "ovvv", "vvvv")
 class ccsd_config(ctypes.Structure):
     _fields_ = [("nk_dims", ctypes.c_int * 3), ("nocc", ctypes.c_int), ("nvir", ctypes.c_int),
                 ("precision", ctypes.c_int), ("diis_depth", ctypes.c_int), ("max_iter", ctypes.c_int),
-                ("conv_tol", ctypes.c_double)]
+                ("conv_tol", ctypes.c_double), ("polish_iters", ctypes.c_int), ("mixed_tol", ctypes.c_double)]
 
 
 class ccsd_inputs(ctypes.Structure):
@@ -43,10 +44,13 @@ SYMBOLS = {
     "ccsd_footprint": ([ctypes.POINTER(ccsd_config), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "ccsd_plan_check": ([ctypes.POINTER(ccsd_config), ctypes.POINTER(ctypes.c_longlong),
                          ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "ccsd_tc_selftest": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
+                          ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "ccsd_residual": ([ctypes.c_void_p] * 5, ctypes.c_int),
     "ccsd_iterate": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                       ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "ccsd_solve": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "ccsd_set_precision": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "ccsd_energy": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "ccsd_get_amplitudes": ([ctypes.c_void_p] * 3, ctypes.c_int),
     "ccsd_set_amplitudes": ([ctypes.c_void_p] * 3, ctypes.c_int),
@@ -103,11 +107,13 @@ def _ptr(x):
     return x.ctypes.data
 
 
-def make_config(grid, nocc, nvir, precision=CCSD_FP64, diis_depth=0, max_iter=100, conv_tol=1e-8):
+def make_config(grid, nocc, nvir, precision=CCSD_FP64, diis_depth=0, max_iter=100, conv_tol=1e-8,
+                polish_iters=2, mixed_tol=1e-7):
     c = ccsd_config()
     c.nk_dims[0], c.nk_dims[1], c.nk_dims[2] = grid
     c.nocc, c.nvir, c.precision = nocc, nvir, precision
     c.diis_depth, c.max_iter, c.conv_tol = diis_depth, max_iter, conv_tol
+    c.polish_iters, c.mixed_tol = polish_iters, mixed_tol
     return c
 
 
@@ -146,6 +152,9 @@ class Solver:
         if code not in (CCSD_OK, CCSD_ERR_NOT_CONVERGED):
             check(code, "ccsd_solve")
         return code == CCSD_OK, it.value, mr.value
+
+    def set_precision(self, precision):
+        check(self.lib.ccsd_set_precision(self.h, precision), "ccsd_set_precision")
 
     def energy(self):
         er = ctypes.c_double(0.0)

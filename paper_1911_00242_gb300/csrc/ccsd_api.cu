@@ -20,8 +20,11 @@
 // and the update t <- t + R/D with convergence test and energy (Sec. 4.4).
 #include "../../include/ccsd.h"
 #include "ccsd_kernels.cuh"
+#include "tcgemm.cuh"
 #include "zgemm_kb.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -78,11 +81,24 @@ struct PermPlan {
 };
 
 struct Step {           // one element of the launch sequence
-    int kind;           // 0 gemm, 1 copy, 2 perm, 3 tau, 4 antisym
+    int kind;           // 0 gemm, 1 copy, 2 perm, 3 tau, 4 antisym, 5 embed, 6 tensor-core gemm, 7 zero
     int idx;
     const char* name;
     double flops;       // algorithmic real flops per launch (complex MAC = 8)
     double bytes;       // algorithmic bytes per launch for the memory-bound steps
+    int mode = 0;       // 0 always; 1 only without tensor cores; 2 only with tensor cores (mixed form)
+};
+
+struct EmbedPlan {      // operand preparation for the tensor-core GEMM
+    int src;
+    EmbedArgs a;        // a.src resolved at launch
+};
+
+struct TcPlan {
+    CUtensorMap mA_big, mA_small, mB_big, mB_small;
+    TcArgs a;           // a.C resolved at launch
+    int c;
+    int blocks;
 };
 
 }  // namespace
@@ -117,6 +133,12 @@ struct ccsd_ctx {
     long long launches = 0;
     int red_blocks = 0;
     const char* cur_name = "";
+    int fp32 = 0;                    // contractions in FP32 arithmetic (mixed form)
+    // mixed form: tensor-core operands (TF32 big/small parts of the real embeddings)
+    std::vector<EmbedPlan> embeds;
+    std::vector<TcPlan> tcs;
+    std::vector<int> const_embeds;   // embeds of constant inputs, run once at creation
+    int* tc_err = nullptr;
     // tracing: CUDA events around every step of the residual plan
     int trace = 0;
     std::vector<cudaEvent_t> ev0, ev1;
@@ -279,6 +301,122 @@ int add_perm(ccsd_ctx* h, Alloc& al, int dst, int src, int n0, int n1, int n2, i
     return 0;
 }
 
+// Driver entry point for TMA descriptors (no link against libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2D fp32 tensor [rows][kpad] with a (32 x box_rows) box and 128-byte swizzle.
+int encode_map(CUtensorMap* m, const float* base, long long rows, int kpad, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return CCSD_ERR_CUDA;
+    cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kpad * 4};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : CCSD_ERR_CUDA;
+}
+
+struct TcBuf { float* big; float* small; long long rows; int kpad; };
+
+int tc_alloc(ccsd_ctx* h, Alloc& al, TcBuf& t, long long rows, int kpad) {
+    t.rows = rows; t.kpad = kpad;
+    t.big = (float*)al.get((size_t)rows * kpad * 4);
+    t.small = (float*)al.get((size_t)rows * kpad * 4);
+    if (al.err) return al.err;
+    if (!al.dry) {
+        // padding columns must read as zero; the embed kernels write only the others
+        if (cudaMemsetAsync(t.big, 0, (size_t)rows * kpad * 4, h->st) != cudaSuccess ||
+            cudaMemsetAsync(t.small, 0, (size_t)rows * kpad * 4, h->st) != cudaSuccess) return CCSD_ERR_CUDA;
+    }
+    return 0;
+}
+
+int add_embed(ccsd_ctx* h, Alloc& al, int src, const TcBuf& dst, int mode, int R, int Kc,
+              const std::vector<long long>& srcoff, const std::vector<int>& srow, const std::vector<int>& scol,
+              bool constant) {
+    const long long nblk = (long long)srcoff.size();
+    if ((int)srow.size() != R || (int)scol.size() != Kc || 2 * Kc > dst.kpad) return CCSD_ERR_INVALID;
+    const long long hi = *std::max_element(srcoff.begin(), srcoff.end()) + *std::max_element(srow.begin(), srow.end()) +
+                         *std::max_element(scol.begin(), scol.end());
+    const long long lo = *std::min_element(srcoff.begin(), srcoff.end()) + *std::min_element(srow.begin(), srow.end()) +
+                         *std::min_element(scol.begin(), scol.end());
+    if (lo < 0 || hi >= h->bufsize[src]) return CCSD_ERR_INVALID;
+    if (nblk * R * (mode == 0 ? 1 : 2) > dst.rows) return CCSD_ERR_INVALID;
+    EmbedPlan e{};
+    e.src = src;
+    e.a.srcoff = upload(al, srcoff, h->st);
+    e.a.srow = upload(al, srow, h->st);
+    e.a.scol = upload(al, scol, h->st);
+    if (al.err) return al.err;
+    e.a.big = dst.big; e.a.small = dst.small;
+    e.a.nblk = (int)nblk; e.a.R = R; e.a.Kc = Kc; e.a.Kpad = dst.kpad; e.a.mode = mode;
+    h->embeds.push_back(e);
+    if (constant) {
+        h->const_embeds.push_back((int)h->embeds.size() - 1);
+    } else {
+        Step st{5, (int)h->embeds.size() - 1, h->cur_name, 0.0, (16.0 + (mode == 0 ? 16.0 : 32.0)) * nblk * R * Kc};
+        st.mode = 2;
+        h->seq.push_back(st);
+    }
+    return 0;
+}
+
+int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M, int Nr, int nbatch, int nchunk,
+           const std::vector<int>& rowA, const std::vector<int>& rowB, const std::vector<long long>& offC,
+           const std::vector<int>& colC, double alpha, int nterms) {
+    if (A.kpad != B.kpad || A.kpad % TC_BK) return CCSD_ERR_INVALID;
+    if ((long long)rowA.size() != (long long)nbatch * nchunk || (long long)rowB.size() != (long long)nbatch * nchunk ||
+        (long long)offC.size() != (long long)nbatch * M || (int)colC.size() * 2 != Nr) return CCSD_ERR_INVALID;
+    for (int x : rowA) if (x < 0 || x >= A.rows) return CCSD_ERR_INVALID;
+    for (int x : rowB) if (x < 0 || x >= B.rows) return CCSD_ERR_INVALID;
+    const long long chi = *std::max_element(offC.begin(), offC.end()) + *std::max_element(colC.begin(), colC.end());
+    const long long clo = *std::min_element(offC.begin(), offC.end()) + *std::min_element(colC.begin(), colC.end());
+    if (clo < 0 || chi >= h->bufsize[c]) return CCSD_ERR_INVALID;
+    TcPlan t{};
+    t.c = c;
+    TcArgs& a = t.a;
+    a.rowA = upload(al, rowA, h->st); a.rowB = upload(al, rowB, h->st);
+    a.offC = upload(al, offC, h->st); a.colC = upload(al, colC, h->st);
+    if (al.err) return al.err;
+    a.err = h->tc_err;
+    a.M = M; a.Nr = Nr; a.nchunk = nchunk; a.kstages = A.kpad / TC_BK; a.nterms = nterms;
+    a.tiles_m = (M + TC_BM - 1) / TC_BM; a.tiles_n = (Nr + TC_BN - 1) / TC_BN;
+    a.alpha_re = alpha; a.alpha_im = 0.0;
+    t.blocks = a.tiles_m * a.tiles_n * nbatch;
+    if (!al.dry) {
+        int rc;
+        if ((rc = encode_map(&t.mA_big, A.big, A.rows, A.kpad, TC_BM)) || (rc = encode_map(&t.mA_small, A.small, A.rows, A.kpad, TC_BM)) ||
+            (rc = encode_map(&t.mB_big, B.big, B.rows, B.kpad, TC_BN)) || (rc = encode_map(&t.mB_small, B.small, B.rows, B.kpad, TC_BN)))
+            return rc;
+    }
+    h->tcs.push_back(t);
+    Step st{6, (int)h->tcs.size() - 1, h->cur_name,
+            8.0 * (double)M * (Nr / 2) * (A.kpad / 2) * nchunk * nbatch, 0.0};
+    st.mode = 2;
+    h->seq.push_back(st);
+    return 0;
+}
+
+void add_zero(ccsd_ctx* h, int buf) {
+    Step st{7, buf, h->cur_name, 0.0, 16.0 * (double)h->bufsize[buf]};
+    st.mode = 2;
+    h->seq.push_back(st);
+}
+
 // Build the full residual plan.
 int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     const KGrid& kg = h->kg;
@@ -290,6 +428,20 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     auto blk = [&](long long S, int a, int b, int c) { return kk3(a, b, c) * S; };
     int rc;
     auto G = [&](GemmSpec& s) { return finalize_gemm(h, al, s, work_need); };
+    const bool mixed = h->cfg.precision == CCSD_MIXED;
+    TcBuf tc_la{}, tc_lb{}, tc_ra{}, tc_rb{}, tc_b1{};
+    if (mixed) {
+        const int kpl = (int)((2 * vv + TC_BK - 1) / TC_BK * TC_BK);
+        const int kpr = (int)((2 * ov + TC_BK - 1) / TC_BK * TC_BK);
+        const long long N3l = (long long)N * N * N;
+        h->tc_err = (int*)al.get(sizeof(int));
+        if (al.err) return al.err;
+        if (!al.dry && cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st) != cudaSuccess) return CCSD_ERR_CUDA;
+        if ((rc = tc_alloc(h, al, tc_la, N3l * oo, kpl)) || (rc = tc_alloc(h, al, tc_lb, N3l * 2 * vv, kpl)) ||
+            (rc = tc_alloc(h, al, tc_ra, N3l * ov, kpr)) || (rc = tc_alloc(h, al, tc_rb, N3l * 2 * ov, kpr)) ||
+            (rc = tc_alloc(h, al, tc_b1, N3l * 2 * ov, kpr)))
+            return rc;
+    }
 
     // ---------------- tau, tau~
     h->seq.push_back({3, 0, "tau", 0.0, 16.0 * (3.0 * h->n2 + h->n1)});
@@ -575,6 +727,31 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowB = tab({{(int)vv, 1}}); s.colB = tab({{(int)vv, vv}});
         s.rowC = tab({{(int)oo, vv}}); s.colC = tab({{(int)vv, 1}});
         if ((rc = G(s))) return rc;
+        if (mixed) h->seq.back().mode = 1;
+    }
+    if (mixed) {
+        // tensor-core ladder: A' = tau in [S = ki + kj][ke][ki](ij)(ef), B' = embedded W' [ka][kb][ke]
+        std::vector<long long> so; std::vector<int> sr, sc;
+        for (int S = 0; S < N; ++S) for (int ke = 0; ke < N; ++ke) for (int ki = 0; ki < N; ++ki)
+            so.push_back(blk(S2, ki, kg.k4(S, 0, ki), ke));
+        if ((rc = add_embed(h, al, B_TAU, tc_la, 0, (int)oo, (int)vv, so, tab({{(int)oo, vv}}), tab({{(int)vv, 1}}), false))) return rc;
+        so.clear();
+        for (int ka = 0; ka < N; ++ka) for (int kb = 0; kb < N; ++kb) for (int ke = 0; ke < N; ++ke)
+            so.push_back(blk(Svvvv, ka, kb, ke));
+        if ((rc = add_embed(h, al, B_WAB, tc_lb, 1, (int)vv, (int)vv, so, tab({{(int)vv, vv}}), tab({{(int)vv, 1}}), false))) return rc;
+        std::vector<int> ra, rb, cc; std::vector<long long> oc;
+        const int M = (int)(N * oo);
+        for (int ka = 0; ka < N; ++ka) for (int kb = 0; kb < N; ++kb) {
+            const int S = kg.k4(ka, kb, 0);
+            for (int ke = 0; ke < N; ++ke) {
+                ra.push_back((int)((((long long)S * N + ke) * N) * oo));
+                rb.push_back((int)((((long long)ka * N + kb) * N + ke) * 2 * vv));
+            }
+            for (int ki = 0; ki < N; ++ki)
+                for (int ij = 0; ij < (int)oo; ++ij) oc.push_back(blk(S2, ki, kg.k4(S, 0, ki), ka) + ij * vv);
+        }
+        cc = tab({{(int)vv, 1}});
+        if ((rc = add_tc(h, al, tc_la, tc_lb, B_R2, M, (int)(2 * vv), N * N, N, ra, rb, oc, cc, 0.5, 3))) return rc;
     }
     h->cur_name = "ring_W_t1";
     // ring: W~_jn^bf (Eq. Def_Woovv), stored [kj,kn,kb](j,n,b,f), kf = kn + kb - kj
@@ -645,6 +822,34 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowB = tab({{o, vv}, {v, 1}}); s.colB = tab({{o, o * vv}, {v, v}});
         s.rowC = tab({{o, o * vv}, {v, v}}); s.colC = tab({{o, vv}, {v, 1}});
         if ((rc = G(s))) return rc;
+        if (mixed) h->seq.back().mode = 1;
+    }
+    if (mixed) {
+        // A_ring[ki][ka][kn](i,a)(n,f) = t2[ki,kn,ka](i,n,a,f); since t_jx^yb = -t_jx^by the same
+        // operand serves W -= 1/2 t_jx^yb <nx||fy> with the sign folded into alpha.
+        std::vector<long long> so;
+        for (int ki = 0; ki < N; ++ki) for (int ka = 0; ka < N; ++ka) for (int kn = 0; kn < N; ++kn)
+            so.push_back(blk(S2, ki, kn, ka));
+        if ((rc = add_embed(h, al, B_T2, tc_ra, 0, (int)ov, (int)ov, so, tab({{o, o * vv}, {v, v}}),
+                            tab({{o, vv}, {v, 1}}), false))) return rc;
+        // constant B: <n kn x kx||f kf y ky> as rows (n,f), columns (x,y), blocks [kn][kf][kx]
+        so.clear();
+        for (int kn = 0; kn < N; ++kn) for (int kf = 0; kf < N; ++kf) for (int kx = 0; kx < N; ++kx)
+            so.push_back(blk(S2, kn, kx, kf));
+        if ((rc = add_embed(h, al, B_OOVV, tc_b1, 1, (int)ov, (int)ov, so, tab({{o, o * vv}, {v, v}}),
+                            tab({{o, vv}, {v, 1}}), true))) return rc;
+        std::vector<int> ra, rb; std::vector<long long> oc;
+        for (int kj = 0; kj < N; ++kj) for (int kb = 0; kb < N; ++kb) for (int kn = 0; kn < N; ++kn) {
+            const int kf = kg.k4(kn, kb, kj);
+            for (int kx = 0; kx < N; ++kx) {
+                ra.push_back((int)((((long long)kj * N + kb) * N + kx) * ov));
+                rb.push_back((int)((((long long)kn * N + kf) * N + kx) * 2 * ov));
+            }
+            for (int j = 0; j < o; ++j) for (int b = 0; b < v; ++b)
+                oc.push_back(blk(S2, kj, kn, kb) + j * o * vv + b * v);
+        }
+        if ((rc = add_tc(h, al, tc_ra, tc_b1, B_WRING, (int)ov, (int)(2 * ov), N3, N, ra, rb, oc,
+                         tab({{o, vv}, {v, 1}}), 0.5, 3))) return rc;
     }
     h->cur_name = "ring";
     {   // ZR = sum_kn t_{in}^{af} W_{jn}^{bf}
@@ -659,6 +864,27 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowB = tab({{o, vv}, {v, 1}}); s.colB = tab({{o, o * vv}, {v, v}});
         s.rowC = tab({{o, o * vv}, {v, v}}); s.colC = tab({{o, vv}, {v, 1}});
         if ((rc = G(s))) return rc;
+        if (mixed) h->seq.back().mode = 1;
+    }
+    if (mixed) {
+        add_zero(h, B_ZR);
+        std::vector<long long> so;       // B_ring[kj][kb][kn]: rows (j,b), columns (n,f) of W~
+        for (int kj = 0; kj < N; ++kj) for (int kb = 0; kb < N; ++kb) for (int kn = 0; kn < N; ++kn)
+            so.push_back(blk(S2, kj, kn, kb));
+        if ((rc = add_embed(h, al, B_WRING, tc_rb, 1, (int)ov, (int)ov, so, tab({{o, o * vv}, {v, v}}),
+                            tab({{o, vv}, {v, 1}}), false))) return rc;
+        std::vector<int> ra, rb; std::vector<long long> oc;
+        for (int ki = 0; ki < N; ++ki) for (int ka = 0; ka < N; ++ka) for (int kj = 0; kj < N; ++kj) {
+            const int kb = kg.k4(ki, kj, ka);
+            for (int kn = 0; kn < N; ++kn) {
+                ra.push_back((int)((((long long)ki * N + ka) * N + kn) * ov));
+                rb.push_back((int)((((long long)kj * N + kb) * N + kn) * 2 * ov));
+            }
+            for (int i = 0; i < o; ++i) for (int a = 0; a < v; ++a)
+                oc.push_back(blk(S2, ki, kj, ka) + i * o * vv + a * v);
+        }
+        if ((rc = add_tc(h, al, tc_ra, tc_rb, B_ZR, (int)ov, (int)(2 * ov), N3, N, ra, rb, oc,
+                         tab({{o, vv}, {v, 1}}), 1.0, 3))) return rc;
     }
     h->cur_name = "ring_t1t1";
     {   // TT(r,b,i,j) = sum_c <r ka b kb||c ki j kj> t_i^c ;  ZR -= sum_r t_r^a TT(r,b,i,j)
@@ -756,11 +982,20 @@ int launch_gemm(ccsd_ctx* h, GemmPlan& p) {
     GemmArgs g = p.args;
     g.A = h->buf[p.a]; g.B = h->buf[p.b]; g.C = h->buf[p.c]; g.work = h->work;
     dim3 grid((unsigned)p.blocks, (unsigned)g.nsplit);
-    switch (p.cfg) {
-        case CFG_64x64:  zgemm_kb_kernel<64, 64, 8, 4, 4><<<grid, 256, 0, h->st>>>(g); break;
-        case CFG_64x32:  zgemm_kb_kernel<64, 32, 8, 4, 2><<<grid, 256, 0, h->st>>>(g); break;
-        case CFG_128x16: zgemm_kb_kernel<128, 16, 8, 8, 1><<<grid, 256, 0, h->st>>>(g); break;
-        default:         zgemm_kb_kernel<16, 16, 8, 1, 1><<<grid, 256, 0, h->st>>>(g); break;
+    if (h->fp32) {
+        switch (p.cfg) {
+            case CFG_64x64:  zgemm_kb_kernel<64, 64, 8, 4, 4, float><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_64x32:  zgemm_kb_kernel<64, 32, 8, 4, 2, float><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_128x16: zgemm_kb_kernel<128, 16, 8, 8, 1, float><<<grid, 256, 0, h->st>>>(g); break;
+            default:         zgemm_kb_kernel<16, 16, 8, 1, 1, float><<<grid, 256, 0, h->st>>>(g); break;
+        }
+    } else {
+        switch (p.cfg) {
+            case CFG_64x64:  zgemm_kb_kernel<64, 64, 8, 4, 4><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_64x32:  zgemm_kb_kernel<64, 32, 8, 4, 2><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_128x16: zgemm_kb_kernel<128, 16, 8, 8, 1><<<grid, 256, 0, h->st>>>(g); break;
+            default:         zgemm_kb_kernel<16, 16, 8, 1, 1><<<grid, 256, 0, h->st>>>(g); break;
+        }
     }
     ++h->launches;
     if (g.nsplit > 1) {
@@ -770,10 +1005,31 @@ int launch_gemm(ccsd_ctx* h, GemmPlan& p) {
     return 0;
 }
 
+void launch_embed(ccsd_ctx* h, EmbedPlan& e) {
+    EmbedArgs a = e.a;
+    a.src = h->buf[e.src];
+    embed_kernel<<<ew_grid((long long)a.nblk * a.R * a.Kc), 256, 0, h->st>>>(a);
+    ++h->launches;
+}
+
+void launch_tc(ccsd_ctx* h, TcPlan& t) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
+        attr_set = true;
+    }
+    TcArgs a = t.a;
+    a.C = h->buf[t.c];
+    tc_gemm_kernel<<<t.blocks, 128, TC_SMEM_BYTES, h->st>>>(t.mA_big, t.mA_small, t.mB_big, t.mB_small, a);
+    ++h->launches;
+}
+
 // Accumulate the elapsed time of traced steps [a, b) (synchronizes the stream).
 int trace_collect(ccsd_ctx* h, size_t a, size_t b) {
     CK(cudaStreamSynchronize(h->st));
+    const bool tc = h->fp32 && h->cfg.precision == CCSD_MIXED;
     for (size_t i = a; i < b; ++i) {
+        if (i < h->seq.size() && ((h->seq[i].mode == 1 && tc) || (h->seq[i].mode == 2 && !tc))) continue;
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, h->ev0[i], h->ev1[i]));
         h->step_ms[i] += ms;
@@ -784,8 +1040,10 @@ int trace_collect(ccsd_ctx* h, size_t a, size_t b) {
 
 int run_residual(ccsd_ctx* h) {
     const int N = h->N, o = h->o, v = h->v;
+    const bool tc = h->fp32 && h->cfg.precision == CCSD_MIXED;
     for (size_t si = 0; si < h->seq.size(); ++si) {
         const Step& s = h->seq[si];
+        if ((s.mode == 1 && tc) || (s.mode == 2 && !tc)) continue;
         if (h->trace) cudaEventRecord(h->ev0[si], h->st);
         switch (s.kind) {
             case 0: launch_gemm(h, h->gemms[s.idx]); break;
@@ -812,11 +1070,27 @@ int run_residual(ccsd_ctx* h) {
                                                                    h->kb_of, N, o, v);
                 ++h->launches;
                 break;
+            case 5: launch_embed(h, h->embeds[s.idx]); break;
+            case 6: launch_tc(h, h->tcs[s.idx]); break;
+            case 7:
+                cudaMemsetAsync(h->buf[s.idx], 0, (size_t)h->bufsize[s.idx] * 16, h->st);
+                break;
         }
         if (h->trace) cudaEventRecord(h->ev1[si], h->st);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { last_err(e); return CCSD_ERR_CUDA; }
+    if (tc) {
+        // a bounded wait inside a tensor-core GEMM gave up: report, clear, fail the call
+        int flag = 0;
+        CK(cudaMemcpyAsync(&flag, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        if (flag) {
+            snprintf(g_errbuf, sizeof g_errbuf, "tensor-core GEMM wait timed out (code %d)", flag);
+            CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st));
+            return CCSD_ERR_TIMEOUT;
+        }
+    }
     if (h->trace) return trace_collect(h, 0, h->seq.size());
     return 0;
 }
@@ -864,7 +1138,8 @@ bool valid_cfg(const ccsd_config* c) {
     if (!c) return false;
     for (int i = 0; i < 3; ++i) if (c->nk_dims[i] < 1 || c->nk_dims[i] > 64) return false;
     if (c->nocc < 1 || c->nvir < 1 || c->nocc > 256 || c->nvir > 512) return false;
-    if (c->precision != CCSD_FP64) return false;
+    if (c->precision != CCSD_FP64 && c->precision != CCSD_MIXED) return false;
+    if (c->precision == CCSD_MIXED && (c->polish_iters < 0 || c->polish_iters > 100)) return false;
     if (c->diis_depth < 0 || c->diis_depth == 1 || c->diis_depth > 8) return false;
     const long long N = (long long)c->nk_dims[0] * c->nk_dims[1] * c->nk_dims[2];
     const long long vvvv = (long long)c->nvir * c->nvir * c->nvir * c->nvir;
@@ -913,6 +1188,73 @@ int ccsd_plan_check(const ccsd_config* cfg, long long* n_launches, size_t* table
     return rc;
 }
 
+int ccsd_tc_selftest(int M, int Ncols, int K, int nterms, unsigned long long seed, double* rel_err) {
+    if (M < 1 || Ncols < 1 || K < 1 || M > 4096 || Ncols > 4096 || K > 4096 || (nterms != 1 && nterms != 3) || !rel_err)
+        return CCSD_ERR_INVALID;
+    ccsd_ctx* h = new (std::nothrow) ccsd_ctx();
+    if (!h) return CCSD_ERR_OOM;
+    h->cfg.precision = CCSD_MIXED;
+    Alloc al{h};
+    auto fail = [&](int code) { ccsd_destroy(h); return code; };
+    const long long nA = (long long)M * K, nB = (long long)Ncols * K, nC = (long long)M * Ncols;
+    // random complex operands on the host, uniform in [-1, 1)
+    std::vector<double2> hA((size_t)nA), hB((size_t)nB);
+    unsigned long long x = seed * 6364136223846793005ULL + 1442695040888963407ULL;
+    auto rnd = [&]() { x = x * 6364136223846793005ULL + 1442695040888963407ULL; return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0; };
+    for (auto& z : hA) { z.x = rnd(); z.y = rnd(); }
+    for (auto& z : hB) { z.x = rnd(); z.y = rnd(); }
+    h->buf[B_ZAB] = upload(al, hA, h->st); h->bufsize[B_ZAB] = nA;
+    h->buf[B_ZIJ] = upload(al, hB, h->st); h->bufsize[B_ZIJ] = nB;
+    h->buf[B_ZR] = (double2*)al.get((size_t)nC * 16); h->bufsize[B_ZR] = nC;
+    h->buf[B_TAU] = (double2*)al.get((size_t)nC * 16); h->bufsize[B_TAU] = nC;
+    h->tc_err = (int*)al.get(sizeof(int));
+    if (al.err) return fail(al.err);
+    if (cudaMemsetAsync(h->buf[B_ZR], 0, (size_t)nC * 16, h->st) != cudaSuccess ||
+        cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
+    // reference: FP64 SIMT engine, C_ref = A B^T
+    size_t work_need = 0;
+    GemmSpec g; g.a = B_ZAB; g.b = B_ZIJ; g.c = B_TAU; g.acc = false;
+    g.M = M; g.N = Ncols; g.K = K; g.nbatch = 1; g.nchunk = 1;
+    g.offA = {0}; g.offB = {0}; g.offC = {0};
+    g.rowA = tab({{M, K}}); g.colA = tab({{K, 1}});
+    g.rowB = tab({{K, 1}}); g.colB = tab({{Ncols, K}});
+    g.rowC = tab({{M, Ncols}}); g.colC = tab({{Ncols, 1}});
+    int rc = finalize_gemm(h, al, g, work_need);
+    if (rc) return fail(rc);
+    if (work_need) { h->work = (double2*)al.get(work_need * 16); if (!h->work) return fail(al.err); }
+    // tensor cores: embed, GEMM
+    const int kpad = (2 * K + TC_BK - 1) / TC_BK * TC_BK;
+    TcBuf ta{}, tb{};
+    if ((rc = tc_alloc(h, al, ta, M, kpad)) || (rc = tc_alloc(h, al, tb, 2LL * Ncols, kpad))) return fail(rc);
+    if ((rc = add_embed(h, al, B_ZAB, ta, 0, M, K, {0}, tab({{M, K}}), tab({{K, 1}}), false)) ||
+        (rc = add_embed(h, al, B_ZIJ, tb, 1, Ncols, K, {0}, tab({{Ncols, K}}), tab({{K, 1}}), false)))
+        return fail(rc);
+    std::vector<long long> oc;
+    for (int m = 0; m < M; ++m) oc.push_back((long long)m * Ncols);
+    if ((rc = add_tc(h, al, ta, tb, B_ZR, M, 2 * Ncols, 1, 1, {0}, {0}, oc, tab({{Ncols, 1}}), 1.0, nterms)))
+        return fail(rc);
+    launch_gemm(h, h->gemms[0]);
+    launch_embed(h, h->embeds[0]);
+    launch_embed(h, h->embeds[1]);
+    launch_tc(h, h->tcs[0]);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
+    int flag = 0;
+    std::vector<double2> c1((size_t)nC), c2((size_t)nC);
+    if (cudaMemcpy(&flag, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(c1.data(), h->buf[B_ZR], (size_t)nC * 16, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(c2.data(), h->buf[B_TAU], (size_t)nC * 16, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(CCSD_ERR_CUDA);
+    if (flag) return fail(CCSD_ERR_TIMEOUT);
+    double num = 0.0, den = 0.0;
+    for (long long i = 0; i < nC; ++i) {
+        num = std::max(num, std::hypot(c1[(size_t)i].x - c2[(size_t)i].x, c1[(size_t)i].y - c2[(size_t)i].y));
+        den = std::max(den, std::hypot(c2[(size_t)i].x, c2[(size_t)i].y));
+    }
+    *rel_err = den > 0 ? num / den : num;
+    ccsd_destroy(h);
+    return CCSD_OK;
+}
+
 int ccsd_create(const ccsd_config* cfg, const ccsd_inputs* in, void* stream, ccsd_t* out) {
     if (!out) return CCSD_ERR_INVALID;
     *out = nullptr;
@@ -925,6 +1267,7 @@ int ccsd_create(const ccsd_config* cfg, const ccsd_inputs* in, void* stream, ccs
     h->kg.init(cfg->nk_dims);
     h->N = h->kg.N; h->o = cfg->nocc; h->v = cfg->nvir;
     h->st = (cudaStream_t)stream;
+    h->fp32 = cfg->precision == CCSD_MIXED ? 1 : 0;
     const long long N = h->N, o = h->o, v = h->v, N3 = N * N * N;
     h->n1 = N * o * v;
     h->n2 = N3 * o * o * v * v;
@@ -993,6 +1336,7 @@ int ccsd_create(const ccsd_config* cfg, const ccsd_inputs* in, void* stream, ccs
     int rc = build_plan(h, al, work_need);
     if (rc) return fail(rc);
     if (work_need) { h->work = dalloc((long long)work_need); if (!h->work) return fail(al.err); }
+    for (int ei : h->const_embeds) launch_embed(h, h->embeds[ei]);
     h->red_blocks = 152 * 4;
     h->red = (double*)al.get(sizeof(double) * h->red_blocks);
     h->red_out = (double*)al.get(sizeof(double) * 4);
@@ -1098,14 +1442,43 @@ int ccsd_solve(ccsd_t h, int* iterations, double* max_resid) {
     if (!h) return CCSD_ERR_INVALID;
     int done = 0, it = 0;
     double mr = 0.0;
+    const bool mixed = h->cfg.precision == CCSD_MIXED;
+    const double tol0 = h->cfg.conv_tol;
+    if (mixed) {
+        ccsd_set_precision(h, CCSD_MIXED);
+        h->cfg.conv_tol = std::max(h->cfg.mixed_tol, tol0);
+    }
     for (; it <= h->cfg.max_iter; ++it) {
         int rc = ccsd_iterate(h, 1, &done, &mr);
-        if (rc) { if (iterations) *iterations = it; return rc; }
+        if (rc) { h->cfg.conv_tol = tol0; if (iterations) *iterations = it; return rc; }
         if (done) break;
+    }
+    h->cfg.conv_tol = tol0;
+    if (mixed && done) {
+        // FP64 polish: the fixed point of the exact equations
+        ccsd_set_precision(h, CCSD_FP64);
+        int d2 = 0;
+        for (int p = 0; p < h->cfg.polish_iters; ++p) {
+            int rc = ccsd_iterate(h, 1, &d2, &mr);
+            if (rc) { if (iterations) *iterations = it; return rc; }
+            if (d2) break;
+            ++it;
+        }
+        ccsd_set_precision(h, CCSD_MIXED);
     }
     if (iterations) *iterations = it;
     if (max_resid) *max_resid = mr;
     return done ? CCSD_OK : CCSD_ERR_NOT_CONVERGED;
+}
+
+int ccsd_set_precision(ccsd_t h, int precision) {
+    if (!h) return CCSD_ERR_INVALID;
+    if (precision == CCSD_FP64) h->fp32 = 0;
+    else if (precision == CCSD_MIXED && h->cfg.precision == CCSD_MIXED) h->fp32 = 1;
+    else return CCSD_ERR_INVALID;
+    h->diis_count = 0;
+    h->diis_next = 0;
+    return CCSD_OK;
 }
 
 int ccsd_energy(ccsd_t h, double* e_real, double* e_imag) {

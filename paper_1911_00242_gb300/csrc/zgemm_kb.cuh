@@ -16,6 +16,11 @@
 // one 64x64x8 complex tile step is ~130k DFMA, so global loads without
 // staging overlap are a rounding error and tiles are chosen to waste as few
 // DFMAs on padding as possible.
+//
+// The kernel is instantiated for two arithmetic types: double (the FP64 form)
+// and float (the mixed form's CUDA-core contractions: operands are read from
+// the complex128 buffers and rounded to FP32 on load, products accumulate in
+// FP32, and the epilogue adds alpha * acc into the FP64 result).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -33,14 +38,19 @@ struct GemmArgs {
     int tiles_m, tiles_n;
 };
 
-template <int BM, int BN, int BK, int TM, int TN>
+template <typename T> struct Cplx;
+template <> struct Cplx<double> { using V = double2; };
+template <> struct Cplx<float> { using V = float2; };
+
+template <int BM, int BN, int BK, int TM, int TN, typename T = double>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 zgemm_kb_kernel(const GemmArgs g)
 {
+    using V = typename Cplx<T>::V;
     constexpr int NT = (BM / TM) * (BN / TN);
     constexpr int TX = BN / TN;
-    __shared__ double2 As[BK][BM];
-    __shared__ double2 Bs[BK][BN];
+    __shared__ V As[BK][BM];
+    __shared__ V Bs[BK][BN];
 
     const int ntile = g.tiles_m * g.tiles_n;
     const int tile = blockIdx.x % ntile;
@@ -51,14 +61,14 @@ zgemm_kb_kernel(const GemmArgs g)
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
 
-    double cr[TM][TN], ci[TM][TN];
+    T cr[TM][TN], ci[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) { cr[i][j] = 0.0; ci[i][j] = 0.0; }
+        for (int j = 0; j < TN; ++j) { cr[i][j] = T(0); ci[i][j] = T(0); }
 
-    const double sa = g.conjA ? -1.0 : 1.0;
-    const double sb = g.conjB ? -1.0 : 1.0;
+    const T sa = g.conjA ? T(-1) : T(1);
+    const T sb = g.conjB ? T(-1) : T(1);
     const int c_begin = split * g.chunks_per_split;
     int c_end = c_begin + g.chunks_per_split;
     if (c_end > g.nchunk) c_end = g.nchunk;
@@ -70,27 +80,27 @@ zgemm_kb_kernel(const GemmArgs g)
             for (int e = tid; e < BM * BK; e += NT) {
                 const int mm = e % BM, kk = e / BM;
                 const int m = m0 + mm, k = k0 + kk;
-                double2 v = make_double2(0.0, 0.0);
+                V v; v.x = T(0); v.y = T(0);
                 if (m < g.M && k < g.K) {
-                    v = __ldg(Ab + (long long)g.rowA[m] + g.colA[k]);
-                    v.y *= sa;
+                    const double2 w = __ldg(Ab + (long long)g.rowA[m] + g.colA[k]);
+                    v.x = T(w.x); v.y = T(w.y) * sa;
                 }
                 As[kk][mm] = v;
             }
             for (int e = tid; e < BN * BK; e += NT) {
                 const int nn = e % BN, kk = e / BN;
                 const int n = n0 + nn, k = k0 + kk;
-                double2 v = make_double2(0.0, 0.0);
+                V v; v.x = T(0); v.y = T(0);
                 if (n < g.N && k < g.K) {
-                    v = __ldg(Bb + (long long)g.rowB[k] + g.colB[n]);
-                    v.y *= sb;
+                    const double2 w = __ldg(Bb + (long long)g.rowB[k] + g.colB[n]);
+                    v.x = T(w.x); v.y = T(w.y) * sb;
                 }
                 Bs[kk][nn] = v;
             }
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < BK; ++kk) {
-                double2 a[TM], bb[TN];
+                V a[TM], bb[TN];
 #pragma unroll
                 for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
 #pragma unroll
@@ -116,7 +126,7 @@ zgemm_kb_kernel(const GemmArgs g)
 #pragma unroll
             for (int j = 0; j < TN; ++j) {
                 const int m = m0 + ty * TM + i, n = n0 + tx * TN + j;
-                if (m < g.M && n < g.N) W[(long long)m * g.N + n] = make_double2(cr[i][j], ci[i][j]);
+                if (m < g.M && n < g.N) W[(long long)m * g.N + n] = make_double2((double)cr[i][j], (double)ci[i][j]);
             }
         return;
     }
@@ -128,8 +138,9 @@ zgemm_kb_kernel(const GemmArgs g)
             const int m = m0 + ty * TM + i, n = n0 + tx * TN + j;
             if (m < g.M && n < g.N) {
                 double2* p = Cb + (long long)g.rowC[m] + g.colC[n];
-                const double re = g.alpha_re * cr[i][j] - g.alpha_im * ci[i][j];
-                const double im = g.alpha_re * ci[i][j] + g.alpha_im * cr[i][j];
+                const double xr = (double)cr[i][j], xi = (double)ci[i][j];
+                const double re = g.alpha_re * xr - g.alpha_im * xi;
+                const double im = g.alpha_re * xi + g.alpha_im * xr;
                 if (g.accumulate) { double2 o = *p; o.x += re; o.y += im; *p = o; }
                 else *p = make_double2(re, im);
             }

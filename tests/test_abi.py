@@ -82,3 +82,17 @@ def test_plan_indices_in_bounds(libpath, grid, o, v):
     tb = ctypes.c_size_t(0)
     assert lib.ccsd_plan_check(ctypes.byref(cfg), ctypes.byref(n), ctypes.byref(tb)) == 0
     assert 40 <= n.value <= 80
+
+
+@pytest.mark.parametrize("grid,o,v", [((1, 1, 1), 3, 5), ((2, 1, 1), 2, 3), ((3, 2, 1), 5, 7),
+                                      ((4, 1, 1), 4, 8), ((2, 2, 2), 8, 32), ((3, 3, 3), 8, 24),
+                                      ((2, 2, 2), 1, 2), ((2, 2, 1), 8, 32)])
+def test_mixed_plan_indices_in_bounds(libpath, grid, o, v):
+    """The mixed form's plan, including the tensor-core GEMMs and operand embeddings."""
+    from paper_1911_00242_gb300 import binding
+    lib = binding.load(libpath)
+    cfg = binding.make_config(grid, o, v, precision=binding.CCSD_MIXED)
+    n = ctypes.c_longlong(0)
+    tb = ctypes.c_size_t(0)
+    assert lib.ccsd_plan_check(ctypes.byref(cfg), ctypes.byref(n), ctypes.byref(tb)) == 0
+    assert n.value >= 50
