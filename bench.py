@@ -33,6 +33,15 @@ WORKLOADS = {"grid222_o8_v32": dict(diis_depth=6),
              "grid221_o8_v32": dict(diis_depth=6)}
 METRIC = "CCSD iter/s"
 FP64_PEAK_TFLOPS = 1.25          # GB300 nominal FP64 (152 SMs x 2.07 GHz x ~4 flop/clk/SM)
+TF32_NOMINAL_RATIO = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rates
+SOLVE_TOL = 1e-9                 # max|R| for the time-to-solution comparison
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 
 
@@ -140,6 +149,68 @@ def run_reference(args, spec, inp):
     }
 
 
+def run_mixed(args, spec, dev, depth, local, fp64_solve, fp64_ms_per_iter):
+    """The mixed form on the same inputs: iterations per second (traced) and the
+    time to solution with FP64 polish, with |dE| against the FP64 solution."""
+    import torch
+    from paper_1911_00242_gb300.binding import CCSD_MIXED, Solver
+    S = Solver(spec.grid, spec.nocc, spec.nvir, dev, precision=CCSD_MIXED, diis_depth=depth, max_iter=1000,
+               conv_tol=1e-12, mixed_tol=1e-7, polish_iters=2)
+    for _ in range(args.warmup):
+        S.iterate(1)
+    torch.cuda.synchronize()
+    S.trace(True)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        S.iterate(1)
+        launches += S.launches()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    steps = S.trace_steps()
+    S.trace(False)
+    S.close()
+    tc = [s for s in steps if s[0] in ("ladder", "ring", "ring_W_t2") and s[3] > 0 and s[1] > 0]
+    dom = max(tc, key=lambda s: s[2]) if tc else max(steps, key=lambda s: s[2])
+    name, calls, tot_ms, fl, by = dom
+    avg_s = tot_ms / max(calls, 1) / 1e3
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops")
+    peak = bf16 * TF32_NOMINAL_RATIO if bf16 else 1900.0 * TF32_NOMINAL_RATIO
+    achieved = fl / avg_s / 1e12
+    out = {
+        "value": 1e3 / ms, "unit": "iter/s", "ms_per_step": ms, "steps": args.steps, "gpu_launches": launches,
+        "precision": "tcgen05 split-TF32 (3 passes) for ladder and ring, FP32 CUDA cores elsewhere, FP64 update",
+        "contraction_tflops": flops_per_iteration(spec) / (ms / 1e3) / 1e12,
+        "speedup_per_iter_vs_fp64": fp64_ms_per_iter / ms,
+        "roofline": {"kernel": f"tc_gemm_kernel ({name})", "bound": "tensor", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "executed_frac": 3.0 * achieved / peak,
+                     "peak_source": ("measured bf16 %.0f TFLOP/s x nominal TF32/BF16 ratio" % bf16) if bf16
+                     else "fallback 1.9 PFLOP/s bf16 x nominal TF32/BF16 ratio",
+                     "flops_per_launch": fl, "launch_ms": avg_s * 1e3},
+    }
+    if fp64_solve is not None:
+        S = Solver(spec.grid, spec.nocc, spec.nvir, dev, precision=CCSD_MIXED, diis_depth=depth, max_iter=1000,
+                   conv_tol=SOLVE_TOL, mixed_tol=1e-7, polish_iters=2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ok, iters, mr = S.solve()
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        e = S.energy().real
+        S.close()
+        out["solve"] = {"converged_mixed_phase": ok, "iterations_incl_polish": iters, "polish_iters": 2,
+                        "max_resid": mr, "seconds": secs, "e_per_cell": e,
+                        "abs_dE_vs_fp64": abs(e - fp64_solve["e_per_cell"]),
+                        "speedup_vs_fp64_solve": fp64_solve["seconds_est"] / secs}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -149,6 +220,8 @@ def main():
     ap.add_argument("--workload", default="grid222_o8_v32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-form comparison")
+    ap.add_argument("--no-solve", action="store_true", help="skip the time-to-solution comparison")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -174,7 +247,7 @@ def main():
     inp = cs.generate(spec)
     dev = {k: torch.from_numpy(v).to(f"cuda:{local}") for k, v in inp.items()}
     depth = WORKLOADS[args.workload]["diis_depth"]
-    S = Solver(spec.grid, spec.nocc, spec.nvir, dev, diis_depth=depth, max_iter=1000, conv_tol=1e-12)
+    S = Solver(spec.grid, spec.nocc, spec.nvir, dev, diis_depth=depth, max_iter=1000, conv_tol=SOLVE_TOL)
     zeros1 = torch.zeros((spec.nk, spec.nocc, spec.nvir), dtype=torch.complex128, device=f"cuda:{local}")
     zeros2 = torch.zeros((spec.nk,) * 3 + (spec.nocc,) * 2 + (spec.nvir,) * 2, dtype=torch.complex128,
                          device=f"cuda:{local}")
@@ -243,6 +316,21 @@ def main():
         "clocks": clk,
         "step_ms": trace_summary,
     }
+
+    if not args.no_solve:
+        # FP64 time to solution: continue the timed handle until max|R| < SOLVE_TOL
+        # (the timed steps are the first iterations of this solve)
+        t0 = time.perf_counter()
+        ok, its, mres = S.solve()
+        torch.cuda.synchronize()
+        t_more = time.perf_counter() - t0
+        fp64_iters = args.warmup + args.steps + its
+        result["fp64_solve"] = {"converged": ok, "iterations": fp64_iters, "max_resid": mres,
+                                "seconds_est": (args.warmup + args.steps) * ms / args.steps / 1e3 + t_more,
+                                "e_per_cell": S.energy().real}
+
+    if not args.no_mixed:
+        result["mixed"] = run_mixed(args, spec, dev, depth, local, result.get("fp64_solve"), ms / args.steps)
 
     if not args.no_e2e:
         # end to end through the C ABI from pinned host buffers: create (copies

@@ -94,6 +94,10 @@ struct EmbedPlan {      // operand preparation for the tensor-core GEMM
     EmbedArgs a;        // a.src resolved at launch
 };
 
+struct WPlan {          // fused W' formation + embedding for one k_a slab of the ladder
+    WprimeArgs a;       // vvvv / ovvv / t1 resolved at launch
+};
+
 struct TcPlan {
     CUtensorMap mA_big, mA_small, mB_big, mB_small;
     TcArgs a;           // a.C resolved at launch
@@ -111,6 +115,7 @@ struct ccsd_ctx {
     cudaStream_t st = nullptr;
     double2* buf[NBUF] = {};
     long long bufsize[NBUF] = {};   // elements, for plan bound checks
+    float2* shadow[NBUF] = {};       // mixed form: complex64 copies read by the FP32 kernels
     std::vector<void*> owned;        // device allocations to free
     size_t owned_bytes = 0;
     double2* amp = nullptr;          // [t1 | t2]
@@ -137,6 +142,7 @@ struct ccsd_ctx {
     // mixed form: tensor-core operands (TF32 big/small parts of the real embeddings)
     std::vector<EmbedPlan> embeds;
     std::vector<TcPlan> tcs;
+    std::vector<WPlan> wplans;
     std::vector<int> const_embeds;   // embeds of constant inputs, run once at creation
     int* tc_err = nullptr;
     // tracing: CUDA events around every step of the residual plan
@@ -203,9 +209,9 @@ struct GemmSpec {
 };
 
 // Tile configurations: (BM, BN, BK, TM, TN), 256 threads each.
-enum { CFG_64x64 = 0, CFG_64x32 = 1, CFG_128x16 = 2, CFG_16x16 = 3 };
-const int CFG_BM[4] = {64, 64, 128, 16};
-const int CFG_BN[4] = {64, 32, 16, 16};
+enum { CFG_64x64 = 0, CFG_64x32 = 1, CFG_128x16 = 2, CFG_16x16 = 3, CFG_32x16 = 4 };
+const int CFG_BM[5] = {64, 64, 128, 16, 32};
+const int CFG_BN[5] = {64, 32, 16, 16, 16};
 
 const int kSMs = 152;
 
@@ -243,7 +249,8 @@ int finalize_gemm(ccsd_ctx* h, Alloc& al, GemmSpec s, size_t& work_need) {
     p.a = s.a; p.b = s.b; p.c = s.c;
     if (s.N >= 48) p.cfg = CFG_64x64;
     else if (s.N > 16) p.cfg = CFG_64x32;
-    else if (s.M > 16) p.cfg = CFG_128x16;
+    else if (s.M > 64) p.cfg = CFG_128x16;
+    else if (s.M > 16) p.cfg = CFG_32x16;
     else p.cfg = CFG_16x16;
     GemmArgs& g = p.args;
     g.M = s.M; g.N = s.N; g.K = s.K; g.nbatch = s.nbatch; g.nchunk = s.nchunk;
@@ -254,7 +261,7 @@ int finalize_gemm(ccsd_ctx* h, Alloc& al, GemmSpec s, size_t& work_need) {
     const long long ctas = (long long)g.tiles_m * g.tiles_n * s.nbatch;
     int nsplit = 1;
     if (ctas < 2 * kSMs && s.nchunk > 1) {
-        nsplit = (int)std::min<long long>(s.nchunk, (2 * kSMs + ctas - 1) / ctas);
+        nsplit = (int)std::min<long long>(s.nchunk, (4 * kSMs + ctas - 1) / ctas);
     }
     g.chunks_per_split = (s.nchunk + nsplit - 1) / nsplit;
     g.nsplit = (s.nchunk + g.chunks_per_split - 1) / g.chunks_per_split;
@@ -417,6 +424,8 @@ void add_zero(ccsd_ctx* h, int buf) {
     h->seq.push_back(st);
 }
 
+dim3 ew_grid(long long n);
+
 // Build the full residual plan.
 int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     const KGrid& kg = h->kg;
@@ -429,21 +438,45 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     int rc;
     auto G = [&](GemmSpec& s) { return finalize_gemm(h, al, s, work_need); };
     const bool mixed = h->cfg.precision == CCSD_MIXED;
-    TcBuf tc_la{}, tc_lb{}, tc_ra{}, tc_rb{}, tc_b1{};
+    TcBuf tc_la{}, tc_lb{}, tc_ra{}, tc_rb{}, tc_b1{}, tc_ha{}, tc_hb{}, tc_h2a{}, tc_h2b{};
+    int ladder_nka = 1;
     if (mixed) {
         const int kpl = (int)((2 * vv + TC_BK - 1) / TC_BK * TC_BK);
         const int kpr = (int)((2 * ov + TC_BK - 1) / TC_BK * TC_BK);
         const long long N3l = (long long)N * N * N;
         h->tc_err = (int*)al.get(sizeof(int));
         if (al.err) return al.err;
+        // complex64 copies: the inputs once here, t1 at the start of every residual
+        for (int bi = B_FOO_IN; bi <= B_T1; ++bi) {
+            if (bi == B_T2) continue;
+            h->shadow[bi] = (float2*)al.get((size_t)h->bufsize[bi] * 8);
+            if (al.err) return al.err;
+            if (!al.dry && bi != B_T1)
+                to_c64_kernel<<<ew_grid(h->bufsize[bi]), 256, 0, h->st>>>(h->shadow[bi], h->buf[bi], h->bufsize[bi]);
+        }
         if (!al.dry && cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st) != cudaSuccess) return CCSD_ERR_CUDA;
-        if ((rc = tc_alloc(h, al, tc_la, N3l * oo, kpl)) || (rc = tc_alloc(h, al, tc_lb, N3l * 2 * vv, kpl)) ||
+        // ladder k_a slab: enough CTAs per launch for ~4 waves, B operand within ~8 GB
+        const long long per_ka_ctas = (long long)N * ((N * oo + TC_BM - 1) / TC_BM) * ((2 * vv + TC_BN - 1) / TC_BN);
+        const long long per_ka_bytes = (long long)N * N * 2 * vv * kpl * 4 * 2;
+        ladder_nka = (int)std::min<long long>(N, std::max<long long>(1, (4 * kSMs + per_ka_ctas - 1) / per_ka_ctas));
+        while (ladder_nka > 1 && ladder_nka * per_ka_bytes > (8LL << 30)) --ladder_nka;
+        if ((rc = tc_alloc(h, al, tc_la, N3l * oo, kpl)) ||
+            (rc = tc_alloc(h, al, tc_lb, (long long)ladder_nka * N * N * 2 * vv, kpl)) ||
             (rc = tc_alloc(h, al, tc_ra, N3l * ov, kpr)) || (rc = tc_alloc(h, al, tc_rb, N3l * 2 * ov, kpr)) ||
             (rc = tc_alloc(h, al, tc_b1, N3l * 2 * ov, kpr)))
+            return rc;
+        const int kpo = (int)((2 * oo + TC_BK - 1) / TC_BK * TC_BK);
+        if ((rc = tc_alloc(h, al, tc_ha, N3l * oo, kpl)) || (rc = tc_alloc(h, al, tc_hb, N3l * 2 * oo, kpl)) ||
+            (rc = tc_alloc(h, al, tc_h2a, N3l * oo, kpo)) || (rc = tc_alloc(h, al, tc_h2b, N3l * 2 * vv, kpo)))
             return rc;
     }
 
     // ---------------- tau, tau~
+    if (mixed) {
+        Step st{9, B_T1, "tau", 0.0, 24.0 * h->n1};
+        st.mode = 2;
+        h->seq.push_back(st);
+    }
     h->seq.push_back({3, 0, "tau", 0.0, 16.0 * (3.0 * h->n2 + h->n1)});
 
     h->cur_name = "F_ov";
@@ -672,6 +705,33 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowB = tab({{(int)vv, 1}}); s.colB = tab({{(int)oo, vv}});
         s.rowC = tab({{(int)oo, oo}}); s.colC = tab({{(int)oo, 1}});
         if ((rc = G(s))) return rc;
+        if (mixed) h->seq.back().mode = 1;
+    }
+    if (mixed) {
+        // X on tensor cores, one batch per momentum sum S = km + kn = ki + kj:
+        // rows (km, mn) of <mn||ef> (constant operand), columns (ki, ij) of tau, K = (ke, ef)
+        std::vector<long long> so;
+        for (int S = 0; S < N; ++S) for (int ke = 0; ke < N; ++ke) for (int km = 0; km < N; ++km)
+            so.push_back(blk(S2, km, kg.k4(S, 0, km), ke));
+        if ((rc = add_embed(h, al, B_OOVV, tc_ha, 0, (int)oo, (int)vv, so, tab({{(int)oo, vv}}), tab({{(int)vv, 1}}), true)))
+            return rc;
+        so.clear();
+        for (int S = 0; S < N; ++S) for (int ke = 0; ke < N; ++ke) for (int ki = 0; ki < N; ++ki)
+            so.push_back(blk(S2, ki, kg.k4(S, 0, ki), ke));
+        if ((rc = add_embed(h, al, B_TAU, tc_hb, 1, (int)oo, (int)vv, so, tab({{(int)oo, vv}}), tab({{(int)vv, 1}}), false)))
+            return rc;
+        std::vector<int> ra, rb; std::vector<long long> oc;
+        for (int S = 0; S < N; ++S) {
+            for (int ke = 0; ke < N; ++ke) {
+                ra.push_back((int)((((long long)S * N + ke) * N) * oo));
+                rb.push_back((int)((((long long)S * N + ke) * N) * 2 * oo));
+            }
+            for (int km = 0; km < N; ++km)
+                for (int mn = 0; mn < (int)oo; ++mn)
+                    oc.push_back(((long long)km * N + kg.k4(S, 0, km)) * N * Soooo + mn * oo);
+        }
+        if ((rc = add_tc(h, al, tc_ha, tc_hb, B_WHH, (int)(N * oo), (int)(2 * N * oo), N, N, ra, rb, oc,
+                         tab({{N, Soooo}, {(int)oo, 1}}), 0.5, 3))) return rc;
     }
     h->cur_name = "hole_hole";
     {   // R2 += 1/2 sum_km tau_{mn}^{ab} Whh_{mnij}
@@ -688,9 +748,37 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowB = tab({{(int)oo, vv}}); s.colB = tab({{(int)vv, 1}});
         s.rowC = tab({{(int)oo, vv}}); s.colC = tab({{(int)vv, 1}});
         if ((rc = G(s))) return rc;
+        if (mixed) h->seq.back().mode = 1;
+    }
+    if (mixed) {
+        // R2 += 1/2 tau_mn^ab Whh_mnij on tensor cores, one batch per S = ki + kj:
+        // rows (ki, ij) of Whh^T, columns (ka, ab) of tau, K = (km, mn)
+        std::vector<long long> so;
+        for (int S = 0; S < N; ++S) for (int km = 0; km < N; ++km) for (int ki = 0; ki < N; ++ki)
+            so.push_back(blk(Soooo, km, kg.k4(S, 0, km), ki));
+        if ((rc = add_embed(h, al, B_WHH, tc_h2a, 0, (int)oo, (int)oo, so, tab({{(int)oo, 1}}), tab({{(int)oo, oo}}), false)))
+            return rc;
+        so.clear();
+        for (int S = 0; S < N; ++S) for (int km = 0; km < N; ++km) for (int ka = 0; ka < N; ++ka)
+            so.push_back(blk(S2, km, kg.k4(S, 0, km), ka));
+        if ((rc = add_embed(h, al, B_TAU, tc_h2b, 1, (int)vv, (int)oo, so, tab({{(int)vv, 1}}), tab({{(int)oo, vv}}), false)))
+            return rc;
+        std::vector<int> ra, rb; std::vector<long long> oc;
+        for (int S = 0; S < N; ++S) {
+            for (int km = 0; km < N; ++km) {
+                ra.push_back((int)((((long long)S * N + km) * N) * oo));
+                rb.push_back((int)((((long long)S * N + km) * N) * 2 * vv));
+            }
+            for (int ki = 0; ki < N; ++ki)
+                for (int ij = 0; ij < (int)oo; ++ij)
+                    oc.push_back(((long long)ki * N + kg.k4(S, 0, ki)) * N * S2 + ij * vv);
+        }
+        if ((rc = add_tc(h, al, tc_h2a, tc_h2b, B_R2, (int)(N * oo), (int)(2 * N * vv), N, N, ra, rb, oc,
+                         tab({{N, S2}, {(int)vv, 1}}), 0.5, 3))) return rc;
     }
     h->cur_name = "ladder_W";
     // ladder: Wab = <ab||ef> - P(ab) t_r^b <a r||e f>
+    const size_t ladder_w_first = h->seq.size();
     if ((rc = add_copy(h, B_WAB, B_VVVV, (long long)N3 * Svvvv, 0))) return rc;
     {   // + sum_r t_r^b(kb) ovvv[kb,ka,ke](r,a,e,f)
         GemmSpec s; s.a = B_OVVV; s.b = B_T1; s.c = B_WAB;
@@ -714,6 +802,8 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{v, vv}, {(int)vv, 1}}); s.colC = tab({{v, vv * v}});
         if ((rc = G(s))) return rc;
     }
+    if (mixed)   // the tensor-core path forms W' inside its operand embedding
+        for (size_t i = ladder_w_first; i < h->seq.size(); ++i) h->seq[i].mode = 1;
     h->cur_name = "ladder";
     {   // R2 += 1/2 sum_ke tau_ij^ef Wab^{abef}; batches grouped by (ka, kb) for L2 reuse
         GemmSpec s; s.a = B_TAU; s.b = B_WAB; s.c = B_R2; s.ar = 0.5;
@@ -735,23 +825,32 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         for (int S = 0; S < N; ++S) for (int ke = 0; ke < N; ++ke) for (int ki = 0; ki < N; ++ki)
             so.push_back(blk(S2, ki, kg.k4(S, 0, ki), ke));
         if ((rc = add_embed(h, al, B_TAU, tc_la, 0, (int)oo, (int)vv, so, tab({{(int)oo, vv}}), tab({{(int)vv, 1}}), false))) return rc;
-        so.clear();
-        for (int ka = 0; ka < N; ++ka) for (int kb = 0; kb < N; ++kb) for (int ke = 0; ke < N; ++ke)
-            so.push_back(blk(Svvvv, ka, kb, ke));
-        if ((rc = add_embed(h, al, B_WAB, tc_lb, 1, (int)vv, (int)vv, so, tab({{(int)vv, vv}}), tab({{(int)vv, 1}}), false))) return rc;
-        std::vector<int> ra, rb, cc; std::vector<long long> oc;
+        // k_a slabs: W' for the slab is formed straight into the B operand, then its GEMM runs
         const int M = (int)(N * oo);
-        for (int ka = 0; ka < N; ++ka) for (int kb = 0; kb < N; ++kb) {
-            const int S = kg.k4(ka, kb, 0);
-            for (int ke = 0; ke < N; ++ke) {
-                ra.push_back((int)((((long long)S * N + ke) * N) * oo));
-                rb.push_back((int)((((long long)ka * N + kb) * N + ke) * 2 * vv));
+        for (int ka0 = 0; ka0 < N; ka0 += ladder_nka) {
+            const int nka = std::min(ladder_nka, N - ka0);
+            WPlan wp{};
+            wp.a.big = tc_lb.big; wp.a.small = tc_lb.small;
+            wp.a.N = N; wp.a.o = o; wp.a.v = v; wp.a.ka0 = ka0; wp.a.nka = nka; wp.a.Kpad = tc_lb.kpad;
+            if ((long long)nka * N * N * 2 * vv > tc_lb.rows) return CCSD_ERR_INVALID;
+            h->wplans.push_back(wp);
+            Step st{8, (int)h->wplans.size() - 1, h->cur_name, 16.0 * (double)nka * N * N * vv * vv * (o + o),
+                    (16.0 + 32.0) * (double)nka * N * N * vv * vv};
+            st.mode = 2;
+            h->seq.push_back(st);
+            std::vector<int> ra, rb, cc; std::vector<long long> oc;
+            for (int ka = ka0; ka < ka0 + nka; ++ka) for (int kb = 0; kb < N; ++kb) {
+                const int S = kg.k4(ka, kb, 0);
+                for (int ke = 0; ke < N; ++ke) {
+                    ra.push_back((int)((((long long)S * N + ke) * N) * oo));
+                    rb.push_back((int)((((long long)(ka - ka0) * N + kb) * N + ke) * 2 * vv));
+                }
+                for (int ki = 0; ki < N; ++ki)
+                    for (int ij = 0; ij < (int)oo; ++ij) oc.push_back(blk(S2, ki, kg.k4(S, 0, ki), ka) + ij * vv);
             }
-            for (int ki = 0; ki < N; ++ki)
-                for (int ij = 0; ij < (int)oo; ++ij) oc.push_back(blk(S2, ki, kg.k4(S, 0, ki), ka) + ij * vv);
+            cc = tab({{(int)vv, 1}});
+            if ((rc = add_tc(h, al, tc_la, tc_lb, B_R2, M, (int)(2 * vv), nka * N, N, ra, rb, oc, cc, 0.5, 3))) return rc;
         }
-        cc = tab({{(int)vv, 1}});
-        if ((rc = add_tc(h, al, tc_la, tc_lb, B_R2, M, (int)(2 * vv), N * N, N, ra, rb, oc, cc, 0.5, 3))) return rc;
     }
     h->cur_name = "ring_W_t1";
     // ring: W~_jn^bf (Eq. Def_Woovv), stored [kj,kn,kb](j,n,b,f), kf = kn + kb - kj
@@ -981,12 +1080,15 @@ dim3 ew_grid(long long n) {
 int launch_gemm(ccsd_ctx* h, GemmPlan& p) {
     GemmArgs g = p.args;
     g.A = h->buf[p.a]; g.B = h->buf[p.b]; g.C = h->buf[p.c]; g.work = h->work;
+    g.A32 = h->fp32 ? h->shadow[p.a] : nullptr;
+    g.B32 = h->fp32 ? h->shadow[p.b] : nullptr;
     dim3 grid((unsigned)p.blocks, (unsigned)g.nsplit);
     if (h->fp32) {
         switch (p.cfg) {
             case CFG_64x64:  zgemm_kb_kernel<64, 64, 8, 4, 4, float><<<grid, 256, 0, h->st>>>(g); break;
             case CFG_64x32:  zgemm_kb_kernel<64, 32, 8, 4, 2, float><<<grid, 256, 0, h->st>>>(g); break;
             case CFG_128x16: zgemm_kb_kernel<128, 16, 8, 8, 1, float><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_32x16:  zgemm_kb_kernel<32, 16, 8, 2, 1, float><<<grid, 256, 0, h->st>>>(g); break;
             default:         zgemm_kb_kernel<16, 16, 8, 1, 1, float><<<grid, 256, 0, h->st>>>(g); break;
         }
     } else {
@@ -994,6 +1096,7 @@ int launch_gemm(ccsd_ctx* h, GemmPlan& p) {
             case CFG_64x64:  zgemm_kb_kernel<64, 64, 8, 4, 4><<<grid, 256, 0, h->st>>>(g); break;
             case CFG_64x32:  zgemm_kb_kernel<64, 32, 8, 4, 2><<<grid, 256, 0, h->st>>>(g); break;
             case CFG_128x16: zgemm_kb_kernel<128, 16, 8, 8, 1><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_32x16:  zgemm_kb_kernel<32, 16, 8, 2, 1><<<grid, 256, 0, h->st>>>(g); break;
             default:         zgemm_kb_kernel<16, 16, 8, 1, 1><<<grid, 256, 0, h->st>>>(g); break;
         }
     }
@@ -1075,6 +1178,18 @@ int run_residual(ccsd_ctx* h) {
             case 7:
                 cudaMemsetAsync(h->buf[s.idx], 0, (size_t)h->bufsize[s.idx] * 16, h->st);
                 break;
+            case 9:   // refresh the complex64 copy of an amplitude buffer
+                to_c64_kernel<<<ew_grid(h->bufsize[s.idx]), 256, 0, h->st>>>(h->shadow[s.idx], h->buf[s.idx],
+                                                                             h->bufsize[s.idx]);
+                ++h->launches;
+                break;
+            case 8: {
+                WprimeArgs a = h->wplans[s.idx].a;
+                a.vvvv = h->shadow[B_VVVV]; a.ovvv = h->shadow[B_OVVV]; a.t1 = h->shadow[B_T1];
+                wprime_embed_kernel<<<ew_grid((long long)a.nka * N * N * v * v * v * v), 256, 0, h->st>>>(a);
+                ++h->launches;
+                break;
+            }
         }
         if (h->trace) cudaEventRecord(h->ev1[si], h->st);
     }

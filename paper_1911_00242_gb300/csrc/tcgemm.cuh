@@ -287,6 +287,12 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float(u);
 }
 
+// Split of a float into TF32-exact big + small parts (FP32 arithmetic only).
+__device__ __forceinline__ void split_tf32f(float x, float& big, float& small) {
+    big = tf32_round(x);
+    small = tf32_round(x - big);
+}
+
 // Split of a double into TF32-exact big + small parts.
 __device__ __forceinline__ void split_tf32(double x, float& big, float& small) {
     const float f = (float)x;
@@ -337,6 +343,80 @@ __global__ void embed_kernel(const EmbedArgs e)
                 e.small[o1] = is; e.small[o1 + 1] = rs;
             }
         }
+    }
+}
+
+}  // namespace ccsdk
+
+namespace ccsdk {
+
+// Fused ladder operand: W'^{abef} = <ab||ef> + sum_r t_r^b(kb) <r kb a ka||e ke f kf>
+//                                           - sum_r t_r^a(ka) <r ka b kb||e ke f kf>
+// (the ovvv form of -P(ab) t_r^b <a r||e f>), written straight into the B-side
+// embedding of the tensor-core GEMM for the k_a slab [ka0, ka0 + nka):
+//   rows (((ka - ka0) N + kb) N + ke) 2v^2 + 2(a v + b) + s, columns 2(e v + f) + r.
+// Everything runs in FP32 on complex64 copies of the integrals and of t1.
+struct WprimeArgs {
+    const float2* vvvv; const float2* ovvv; const float2* t1;   // complex64 copies
+    float* big; float* small;
+    int N, o, v, ka0, nka, Kpad;
+};
+
+__global__ void wprime_embed_kernel(const WprimeArgs w)
+{
+    const int N = w.N, o = w.o, v = w.v;
+    const long long vv = (long long)v * v, v4 = vv * vv;
+    const long long total = (long long)w.nka * N * N * v4;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+         x += (long long)gridDim.x * blockDim.x) {
+        const long long el = x % v4;
+        const long long bl = x / v4;                  // slab-local block ((ka - ka0) N + kb) N + ke
+        const int ke = (int)(bl % N);
+        const int kb = (int)((bl / N) % N);
+        const int ka = w.ka0 + (int)(bl / ((long long)N * N));
+        const int ef = (int)(el % vv);
+        const int ab = (int)(el / vv);
+        const int a = ab / v, b = ab % v;
+        const long long blk_ab = ((long long)ka * N + kb) * N + ke;   // vvvv / ovvv[ka,kb,ke]
+        const long long blk_ba = ((long long)kb * N + ka) * N + ke;   // ovvv[kb,ka,ke]
+        const float2 g = w.vvvv[blk_ab * v4 + el];
+        float sr = 0.f, si = 0.f;
+        const long long ov3 = (long long)o * v * vv;
+        for (int r = 0; r < o; ++r) {
+            // + t_r^b(kb) ovvv[kb,ka,ke](r,a,e,f)
+            const float2 tb = w.t1[((long long)kb * o + r) * v + b];
+            const float2 p = w.ovvv[blk_ba * ov3 + ((long long)r * v + a) * vv + ef];
+            sr = fmaf(tb.x, p.x, fmaf(-tb.y, p.y, sr));
+            si = fmaf(tb.x, p.y, fmaf(tb.y, p.x, si));
+            // - t_r^a(ka) ovvv[ka,kb,ke](r,b,e,f)
+            const float2 ta = w.t1[((long long)ka * o + r) * v + a];
+            const float2 q = w.ovvv[blk_ab * ov3 + ((long long)r * v + b) * vv + ef];
+            sr = fmaf(-ta.x, q.x, fmaf(ta.y, q.y, sr));
+            si = fmaf(-ta.x, q.y, fmaf(-ta.y, q.x, si));
+        }
+        float rb, rs, ib, is;
+        split_tf32f(g.x + sr, rb, rs);
+        split_tf32f(g.y + si, ib, is);
+        const long long o0 = (bl * 2 * vv + 2LL * ab) * (long long)w.Kpad + 2LL * ef;
+        const long long o1 = o0 + w.Kpad;
+        w.big[o0] = rb; w.big[o0 + 1] = -ib;
+        w.big[o1] = ib; w.big[o1 + 1] = rb;
+        w.small[o0] = rs; w.small[o0 + 1] = -is;
+        w.small[o1] = is; w.small[o1 + 1] = rs;
+    }
+}
+
+}  // namespace ccsdk
+
+namespace ccsdk {
+
+// dst = (complex64) src, n elements
+__global__ void to_c64_kernel(float2* __restrict__ dst, const double2* __restrict__ src, long long n)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const double2 z = src[e];
+        dst[e] = make_float2((float)z.x, (float)z.y);
     }
 }
 

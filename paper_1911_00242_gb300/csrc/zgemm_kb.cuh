@@ -19,8 +19,10 @@
 //
 // The kernel is instantiated for two arithmetic types: double (the FP64 form)
 // and float (the mixed form's CUDA-core contractions: operands are read from
-// the complex128 buffers and rounded to FP32 on load, products accumulate in
-// FP32, and the epilogue adds alpha * acc into the FP64 result).
+// complex64 copies where the plan has them, otherwise rounded from complex128
+// on load; products accumulate in FP32 and the epilogue adds alpha * acc into
+// the FP64 result).  On GB300 a double->float conversion issues on the slow
+// FP64 pipe, so the complex64 copies matter for throughput, not only bytes.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -30,6 +32,7 @@ namespace ccsdk {
 struct GemmArgs {
     const double2* A; const long long* offA; const int* rowA; const int* colA;
     const double2* B; const long long* offB; const int* rowB; const int* colB;
+    const float2* A32; const float2* B32;   // complex64 copies of A / B, used instead when set
     double2* C;       const long long* offC; const int* rowC; const int* colC;
     double2* work;    // split partials [nsplit][nbatch][M*N] when nsplit > 1
     int M, N, K, nbatch, nchunk, nsplit, chunks_per_split;
@@ -74,16 +77,21 @@ zgemm_kb_kernel(const GemmArgs g)
     if (c_end > g.nchunk) c_end = g.nchunk;
 
     for (int c = c_begin; c < c_end; ++c) {
-        const double2* Ab = g.A + g.offA[b * g.nchunk + c];
-        const double2* Bb = g.B + g.offB[b * g.nchunk + c];
+        const long long oa = g.offA[b * g.nchunk + c];
+        const long long ob = g.offB[b * g.nchunk + c];
+        const double2* Ab = g.A + oa;
+        const double2* Bb = g.B + ob;
+        const float2* Ab32 = g.A32 ? g.A32 + oa : nullptr;
+        const float2* Bb32 = g.B32 ? g.B32 + ob : nullptr;
         for (int k0 = 0; k0 < g.K; k0 += BK) {
             for (int e = tid; e < BM * BK; e += NT) {
                 const int mm = e % BM, kk = e / BM;
                 const int m = m0 + mm, k = k0 + kk;
                 V v; v.x = T(0); v.y = T(0);
                 if (m < g.M && k < g.K) {
-                    const double2 w = __ldg(Ab + (long long)g.rowA[m] + g.colA[k]);
-                    v.x = T(w.x); v.y = T(w.y) * sa;
+                    const long long q = (long long)g.rowA[m] + g.colA[k];
+                    if (Ab32) { const float2 w = __ldg(Ab32 + q); v.x = T(w.x); v.y = T(w.y) * sa; }
+                    else { const double2 w = __ldg(Ab + q); v.x = T(w.x); v.y = T(w.y) * sa; }
                 }
                 As[kk][mm] = v;
             }
@@ -92,8 +100,9 @@ zgemm_kb_kernel(const GemmArgs g)
                 const int n = n0 + nn, k = k0 + kk;
                 V v; v.x = T(0); v.y = T(0);
                 if (n < g.N && k < g.K) {
-                    const double2 w = __ldg(Bb + (long long)g.rowB[k] + g.colB[n]);
-                    v.x = T(w.x); v.y = T(w.y) * sb;
+                    const long long q = (long long)g.rowB[k] + g.colB[n];
+                    if (Bb32) { const float2 w = __ldg(Bb32 + q); v.x = T(w.x); v.y = T(w.y) * sb; }
+                    else { const double2 w = __ldg(Bb + q); v.x = T(w.x); v.y = T(w.y) * sb; }
                 }
                 Bs[kk][nn] = v;
             }
