@@ -174,7 +174,8 @@ def run_mixed(args, spec, dev, depth, local, fp64_solve, fp64_ms_per_iter):
     steps = S.trace_steps()
     S.trace(False)
     S.close()
-    tc = [s for s in steps if s[0] in ("ladder", "ring", "ring_W_t2") and s[3] > 0 and s[1] > 0]
+    tc = [s for s in steps if s[0] in ("ladder", "ring", "ring_W_t2", "hole_hole", "hole_hole_W")
+          and s[3] > 0 and s[1] > 0 and s[3] / (s[2] / max(s[1], 1) / 1e3) > 20e12]   # tensor-core steps
     dom = max(tc, key=lambda s: s[2]) if tc else max(steps, key=lambda s: s[2])
     name, calls, tot_ms, fl, by = dom
     avg_s = tot_ms / max(calls, 1) / 1e3

@@ -834,8 +834,8 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
             wp.a.N = N; wp.a.o = o; wp.a.v = v; wp.a.ka0 = ka0; wp.a.nka = nka; wp.a.Kpad = tc_lb.kpad;
             if ((long long)nka * N * N * 2 * vv > tc_lb.rows) return CCSD_ERR_INVALID;
             h->wplans.push_back(wp);
-            Step st{8, (int)h->wplans.size() - 1, h->cur_name, 16.0 * (double)nka * N * N * vv * vv * (o + o),
-                    (16.0 + 32.0) * (double)nka * N * N * vv * vv};
+            Step st{8, (int)h->wplans.size() - 1, "ladder_W", 0.0,
+                    (8.0 + 32.0) * (double)nka * N * N * vv * vv};
             st.mode = 2;
             h->seq.push_back(st);
             std::vector<int> ra, rb, cc; std::vector<long long> oc;
