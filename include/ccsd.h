@@ -156,6 +156,27 @@ int ccsd_trace_step(ccsd_t h, int i, const char** name, long long* calls, double
 
 int ccsd_destroy(ccsd_t h);
 
+/* ---------------------------------------------------------------- batched form
+ * n independent problems (any mix of grids and orbital counts, one precision,
+ * plain successive substitution: diis_depth must be 0) iterate together on a
+ * stream the batch owns.  Every contraction step of all members is one grouped
+ * persistent kernel launch whose tile shape an autotuner picks on the first
+ * iteration (one timing pass per candidate shape); an iteration -- residuals,
+ * per-member max|R|, update of the members not yet converged -- is replayed as
+ * one CUDA graph.  Members stop updating once their max|R| < conv_tol.
+ * The problem data follow the rules of ccsd_create (device inputs borrowed). */
+typedef struct ccsd_batch* ccsd_batch_t;
+int ccsd_batch_create(int n, const ccsd_config* cfgs, const ccsd_inputs* inputs, ccsd_batch_t* out);
+/* Up to n_iter iterations; done[i] / max_resid[i] per member (arrays of n, may be NULL). */
+int ccsd_batch_iterate(ccsd_batch_t b, int n_iter, int* done, double* max_resid);
+/* Per-member correlation energy per unit cell (arrays of n; e_imag may be NULL). */
+int ccsd_batch_energy(ccsd_batch_t b, double* e_real, double* e_imag);
+/* Handle of member i (owned by the batch; usable with ccsd_get_amplitudes etc.). */
+int ccsd_batch_member(ccsd_batch_t b, int i, ccsd_t* h);
+/* Kernel launches per iteration and the autotuned tile shape of each grouped step. */
+int ccsd_batch_stats(ccsd_batch_t b, long long* launches_per_iteration, int* tile_cfgs, int max_cfgs);
+int ccsd_batch_destroy(ccsd_batch_t b);
+
 const char* ccsd_strerror(int code);
 
 /* Correlation energy per unit cell of the amplitudes t1, t2 (same expression

@@ -61,6 +61,16 @@ SYMBOLS = {
                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "ccsd_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "ccsd_batch_create": ([ctypes.c_int, ctypes.POINTER(ccsd_config), ctypes.POINTER(ccsd_inputs),
+                           ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "ccsd_batch_iterate": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "ccsd_batch_energy": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+                          ctypes.c_int),
+    "ccsd_batch_member": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "ccsd_batch_stats": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
+                          ctypes.c_int], ctypes.c_int),
+    "ccsd_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "ccsd_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "ccsd_energy_noalloc": ([ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 6,
                             ctypes.c_int),
@@ -193,6 +203,63 @@ class Solver:
     def close(self):
         if getattr(self, "h", None):
             self.lib.ccsd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSolver:
+    """Many independent problems iterated together (grouped launches, CUDA graph).
+
+    `problems` is a list of (grid, nocc, nvir, arrays) with arrays as for Solver."""
+
+    def __init__(self, problems, **cfg):
+        self.lib = load()
+        n = len(problems)
+        cfgs = (ccsd_config * n)()
+        ins = (ccsd_inputs * n)()
+        self._keep = []
+        for i, (grid, nocc, nvir, arrays) in enumerate(problems):
+            cfgs[i] = make_config(grid, nocc, nvir, **cfg)
+            for name in ("f_oo", "f_vv", "f_ov") + BLOCKS:
+                setattr(ins[i], name, _ptr(arrays[name]))
+            ins[i].int_dtype = CCSD_C128
+            self._keep.append(arrays)
+        self.n = n
+        h = ctypes.c_void_p()
+        check(self.lib.ccsd_batch_create(n, cfgs, ins, ctypes.byref(h)), "ccsd_batch_create")
+        self.h = h
+
+    def iterate(self, n_iter=1):
+        done = (ctypes.c_int * self.n)()
+        mr = (ctypes.c_double * self.n)()
+        check(self.lib.ccsd_batch_iterate(self.h, n_iter, done, mr), "ccsd_batch_iterate")
+        return [bool(x) for x in done], list(mr)
+
+    def energies(self):
+        er = (ctypes.c_double * self.n)()
+        ei = (ctypes.c_double * self.n)()
+        check(self.lib.ccsd_batch_energy(self.h, er, ei), "ccsd_batch_energy")
+        return [complex(a, b) for a, b in zip(er, ei)]
+
+    def member_amplitudes(self, i, t1, t2):
+        h = ctypes.c_void_p()
+        check(self.lib.ccsd_batch_member(self.h, i, ctypes.byref(h)), "ccsd_batch_member")
+        check(self.lib.ccsd_get_amplitudes(h, _ptr(t1), _ptr(t2)), "ccsd_get_amplitudes")
+
+    def stats(self, max_cfgs=64):
+        n = ctypes.c_longlong(0)
+        cfgs = (ctypes.c_int * max_cfgs)()
+        check(self.lib.ccsd_batch_stats(self.h, ctypes.byref(n), cfgs, max_cfgs), "ccsd_batch_stats")
+        return n.value, list(cfgs)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ccsd_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -124,6 +124,7 @@ struct ccsd_ctx {
     double* ev = nullptr;            // ev[k][a]
     int* kb_of = nullptr;            // fourth momentum of doubles blocks
     double2* work = nullptr;         // split-K partials
+    size_t work_elems = 0;
     double* red = nullptr;           // reduction partials
     double* red_out = nullptr;       // scalars
     double2* cred = nullptr;
@@ -1141,13 +1142,15 @@ int trace_collect(ccsd_ctx* h, size_t a, size_t b) {
     return 0;
 }
 
-int run_residual(ccsd_ctx* h) {
-    const int N = h->N, o = h->o, v = h->v;
+bool step_active(const ccsd_ctx* h, const Step& s) {
     const bool tc = h->fp32 && h->cfg.precision == CCSD_MIXED;
-    for (size_t si = 0; si < h->seq.size(); ++si) {
-        const Step& s = h->seq[si];
-        if ((s.mode == 1 && tc) || (s.mode == 2 && !tc)) continue;
-        if (h->trace) cudaEventRecord(h->ev0[si], h->st);
+    return !((s.mode == 1 && tc) || (s.mode == 2 && !tc));
+}
+
+// Launches plan step si (no tracing, no mode check).
+void launch_step(ccsd_ctx* h, size_t si) {
+    const int N = h->N, o = h->o, v = h->v;
+    const Step& s = h->seq[si];
         switch (s.kind) {
             case 0: launch_gemm(h, h->gemms[s.idx]); break;
             case 1: {
@@ -1191,6 +1194,14 @@ int run_residual(ccsd_ctx* h) {
                 break;
             }
         }
+}
+
+int run_residual(ccsd_ctx* h) {
+    const bool tc = h->fp32 && h->cfg.precision == CCSD_MIXED;
+    for (size_t si = 0; si < h->seq.size(); ++si) {
+        if (!step_active(h, h->seq[si])) continue;
+        if (h->trace) cudaEventRecord(h->ev0[si], h->st);
+        launch_step(h, si);
         if (h->trace) cudaEventRecord(h->ev1[si], h->st);
     }
     cudaError_t e = cudaGetLastError();
@@ -1225,6 +1236,223 @@ int reduce_redot(ccsd_ctx* h, const double2* x, const double2* y, long long n, d
     h->launches += 2;
     CK(cudaMemcpyAsync(out_host, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
+    return 0;
+}
+
+// ================================================================ batched form
+// Many independent problems advance together.  Their plans have the same
+// step sequence (sizes differ), so the i-th active contraction of every member
+// runs in one grouped persistent launch (zgemm_grouped_kernel) whose tile
+// shape an autotuner picks; the other steps launch per member.  One iteration
+// (residual, max|R| per member, update) is captured in a CUDA graph and
+// replayed.
+struct BatchGroup {
+    int cfg = CFG_64x64;
+    std::vector<GemmArgs> args;       // per member, tiles for `cfg`, pointers resolved
+    GemmArgs* d_args = nullptr;
+    long long* d_prefix = nullptr;
+    long long total = 0;
+    std::vector<int> split_members;
+};
+
+}  // namespace
+
+struct ccsd_batch {
+    int n = 0;
+    std::vector<ccsd_ctx*> m;
+    cudaStream_t st = nullptr;
+    int fp32 = 0;
+    std::vector<std::vector<size_t>> gemm_steps;   // per member: seq index of each active GEMM
+    std::vector<BatchGroup> groups[2];             // [fp32]
+    int tuned[2] = {0, 0};
+    std::vector<void*> owned;
+    double* d_norms = nullptr;
+    int* d_done = nullptr;
+    double2* d_energy = nullptr;
+    std::vector<int> done;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long long launches = 0;
+};
+
+namespace {
+
+int batch_alloc(ccsd_batch* B, size_t bytes, void** p) {
+    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) { cudaGetLastError(); return CCSD_ERR_OOM; }
+    B->owned.push_back(*p);
+    return 0;
+}
+
+long long tiles_for(const GemmArgs& a, int cfg, int* tm, int* tn) {
+    *tm = (a.M + CFG_BM[cfg] - 1) / CFG_BM[cfg];
+    *tn = (a.N + CFG_BN[cfg] - 1) / CFG_BN[cfg];
+    return (long long)*tm * *tn * a.nbatch;
+}
+
+// (Re)builds the grouped launch descriptors of one precision with the tile
+// shapes in cfgs (one per group).
+int batch_build_groups(ccsd_batch* B, int fp32, const std::vector<int>& cfgs) {
+    const int ng = (int)B->gemm_steps[0].size();
+    std::vector<BatchGroup>& G = B->groups[fp32];
+    if ((int)G.size() != ng) G.assign(ng, BatchGroup());
+    for (int g = 0; g < ng; ++g) {
+        BatchGroup& bg = G[g];
+        bg.cfg = cfgs[g];
+        bg.args.clear();
+        bg.split_members.clear();
+        long long tot = 0;
+        std::vector<long long> prefix;
+        // group-wide split: only when the whole group cannot fill the GPU
+        long long plain = 0;
+        for (int i = 0; i < B->n; ++i) {
+            int tm, tn;
+            plain += tiles_for(B->m[i]->gemms[B->m[i]->seq[B->gemm_steps[i][g]].idx].args, bg.cfg, &tm, &tn);
+        }
+        const int want = plain < 2 * kSMs ? (int)((4 * kSMs + plain - 1) / std::max(1LL, plain)) : 1;
+        for (int i = 0; i < B->n; ++i) {
+            ccsd_ctx* h = B->m[i];
+            const GemmPlan& p = h->gemms[h->seq[B->gemm_steps[i][g]].idx];
+            GemmArgs a = p.args;
+            int tm, tn;
+            tiles_for(a, bg.cfg, &tm, &tn);
+            a.tiles_m = tm; a.tiles_n = tn;
+            const int ns = std::max(1, std::min(want, a.nchunk));
+            a.chunks_per_split = (a.nchunk + ns - 1) / ns;
+            a.nsplit = (a.nchunk + a.chunks_per_split - 1) / a.chunks_per_split;
+            if (a.nsplit > 1) {
+                const size_t need = (size_t)a.nsplit * a.nbatch * a.M * a.N;
+                if (need > h->work_elems) {
+                    void* w = nullptr;
+                    int rc = batch_alloc(B, need * 16, &w);
+                    if (rc) return rc;
+                    h->work = (double2*)w;
+                    h->work_elems = need;
+                }
+                bg.split_members.push_back(i);
+            }
+            a.A = h->buf[p.a]; a.B = h->buf[p.b]; a.C = h->buf[p.c]; a.work = h->work;
+            a.A32 = fp32 ? h->shadow[p.a] : nullptr;
+            a.B32 = fp32 ? h->shadow[p.b] : nullptr;
+            prefix.push_back(tot);
+            tot += (long long)tm * tn * a.nbatch * a.nsplit;
+            bg.args.push_back(a);
+        }
+        prefix.push_back(tot);
+        bg.total = tot;
+        if (!bg.d_args) {
+            void* x = nullptr;
+            int rc = batch_alloc(B, sizeof(GemmArgs) * B->n, &x);
+            if (rc) return rc;
+            bg.d_args = (GemmArgs*)x;
+            if ((rc = batch_alloc(B, sizeof(long long) * (B->n + 1), &x))) return rc;
+            bg.d_prefix = (long long*)x;
+        }
+        CK(cudaMemcpyAsync(bg.d_args, bg.args.data(), sizeof(GemmArgs) * B->n, cudaMemcpyHostToDevice, B->st));
+        CK(cudaMemcpyAsync(bg.d_prefix, prefix.data(), sizeof(long long) * (B->n + 1), cudaMemcpyHostToDevice, B->st));
+    }
+    CK(cudaStreamSynchronize(B->st));
+    return 0;
+}
+
+template <int BM, int BN, int TM, int TN>
+void grouped_launch(ccsd_batch* B, const BatchGroup& bg, int fp32) {
+    const long long ctas = std::min<long long>(bg.total, (long long)kSMs * 8);
+    if (fp32)
+        zgemm_grouped_kernel<BM, BN, 8, TM, TN, float><<<(unsigned)ctas, 256, 0, B->st>>>(bg.d_args, bg.d_prefix, B->n, bg.total);
+    else
+        zgemm_grouped_kernel<BM, BN, 8, TM, TN, double><<<(unsigned)ctas, 256, 0, B->st>>>(bg.d_args, bg.d_prefix, B->n, bg.total);
+}
+
+void launch_group(ccsd_batch* B, const BatchGroup& bg, int fp32) {
+    if (bg.total <= 0 || !bg.d_args) return;
+    switch (bg.cfg) {
+        case CFG_64x64: grouped_launch<64, 64, 4, 4>(B, bg, fp32); break;
+        case CFG_64x32: grouped_launch<64, 32, 4, 2>(B, bg, fp32); break;
+        case CFG_128x16: grouped_launch<128, 16, 8, 1>(B, bg, fp32); break;
+        case CFG_32x16: grouped_launch<32, 16, 2, 1>(B, bg, fp32); break;
+        default: grouped_launch<16, 16, 1, 1>(B, bg, fp32); break;
+    }
+    ++B->launches;
+    for (int i : bg.split_members) {
+        const GemmArgs& a = bg.args[i];
+        zgemm_split_reduce<<<ew_grid((long long)a.nbatch * a.M * a.N), 256, 0, B->st>>>(a);
+        ++B->launches;
+    }
+}
+
+// One residual of every member, contractions grouped.
+void batch_residual(ccsd_batch* B) {
+    const int fp32 = B->fp32;
+    const int ng = (int)B->gemm_steps[0].size();
+    std::vector<size_t> pos((size_t)B->n, 0);
+    for (int g = 0; g <= ng; ++g) {
+        for (int i = 0; i < B->n; ++i) {
+            ccsd_ctx* h = B->m[i];
+            const size_t end = g < ng ? B->gemm_steps[i][g] : h->seq.size();
+            for (size_t si = pos[i]; si < end; ++si)
+                if (step_active(h, h->seq[si]) && h->seq[si].kind != 0) { launch_step(h, si); ++B->launches; }
+            pos[i] = end + 1;
+        }
+        if (g < ng && g < (int)B->groups[fp32].size()) launch_group(B, B->groups[fp32][g], fp32);
+    }
+}
+
+// Residual, per-member max|R| into d_norms, update of unconverged members.
+void batch_iteration_body(ccsd_batch* B) {
+    batch_residual(B);
+    for (int i = 0; i < B->n; ++i) {
+        ccsd_ctx* h = B->m[i];
+        const long long nn = h->n1 + h->n2;
+        maxabs_partial<<<h->red_blocks, 256, 0, B->st>>>(h->res, nn, h->red);
+        final_max<<<1, 32, 0, B->st>>>(h->red, h->red_blocks, B->d_norms + i);
+        update_kernel<<<ew_grid(nn), 256, 0, B->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_R1], h->buf[B_R2],
+                                                      h->eo, h->ev, h->kb_of, h->N, h->o, h->v, nullptr, nullptr,
+                                                      B->d_done + i);
+        B->launches += 3;
+    }
+}
+
+// Autotuner: time every tile shape on every grouped contraction and keep the
+// fastest.  Safe at any time: each residual re-initializes what it accumulates.
+int batch_autotune(ccsd_batch* B, int fp32) {
+    const int ng = (int)B->gemm_steps[0].size();
+    const int cands[5] = {CFG_64x64, CFG_64x32, CFG_128x16, CFG_32x16, CFG_16x16};
+    std::vector<int> best(ng, CFG_64x64);
+    std::vector<float> best_ms(ng, 1e30f);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int c : cands) {
+        std::vector<int> cf(ng, c);
+        int rc = batch_build_groups(B, fp32, cf);
+        if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+        for (int g = 0; g < ng; ++g) {
+            launch_group(B, B->groups[fp32][g], fp32);     // warm
+            CK(cudaEventRecord(e0, B->st));
+            launch_group(B, B->groups[fp32][g], fp32);
+            CK(cudaEventRecord(e1, B->st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms[g]) { best_ms[g] = ms; best[g] = c; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc = batch_build_groups(B, fp32, best);
+    if (rc) return rc;
+    B->tuned[fp32] = 1;
+    return 0;
+}
+
+int batch_capture(ccsd_batch* B, int fp32) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(B->st, cudaStreamCaptureModeThreadLocal));
+    batch_iteration_body(B);
+    cudaError_t e = cudaStreamEndCapture(B->st, &g);
+    if (e != cudaSuccess) { last_err(e); return CCSD_ERR_CUDA; }
+    e = cudaGraphInstantiate(&B->graph[fp32], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { last_err(e); return CCSD_ERR_CUDA; }
     return 0;
 }
 
@@ -1451,6 +1679,7 @@ int ccsd_create(const ccsd_config* cfg, const ccsd_inputs* in, void* stream, ccs
     int rc = build_plan(h, al, work_need);
     if (rc) return fail(rc);
     if (work_need) { h->work = dalloc((long long)work_need); if (!h->work) return fail(al.err); }
+    h->work_elems = work_need;
     for (int ei : h->const_embeds) launch_embed(h, h->embeds[ei]);
     h->red_blocks = 152 * 4;
     h->red = (double*)al.get(sizeof(double) * h->red_blocks);
@@ -1664,6 +1893,129 @@ int ccsd_trace_step(ccsd_t h, int i, const char** name, long long* calls, double
     if (total_ms) *total_ms = i < (int)h->step_ms.size() ? h->step_ms[i] : 0.0;
     if (flops) *flops = upd ? 0.0 : h->seq[i].flops;
     if (bytes) *bytes = upd ? (h->cfg.diis_depth ? 80.0 : 48.0) * (double)(h->n1 + h->n2) : h->seq[i].bytes;
+    return CCSD_OK;
+}
+
+int ccsd_batch_create(int n, const ccsd_config* cfgs, const ccsd_inputs* inputs, ccsd_batch_t* out) {
+    if (!out || n < 1 || n > 4096 || !cfgs || !inputs) return CCSD_ERR_INVALID;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (cfgs[i].precision != cfgs[0].precision || cfgs[i].diis_depth != 0) return CCSD_ERR_INVALID;
+    ccsd_batch* B = new (std::nothrow) ccsd_batch();
+    if (!B) return CCSD_ERR_OOM;
+    B->n = n;
+    auto fail = [&](int code) { ccsd_batch_destroy(B); return code; };
+    if (cudaStreamCreateWithFlags(&B->st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); B->st = nullptr; return fail(CCSD_ERR_CUDA); }
+    for (int i = 0; i < n; ++i) {
+        ccsd_t h = nullptr;
+        int rc = ccsd_create(&cfgs[i], &inputs[i], B->st, &h);
+        if (rc) return fail(rc);
+        B->m.push_back(h);
+    }
+    B->fp32 = cfgs[0].precision == CCSD_MIXED ? 1 : 0;
+    for (int i = 0; i < n; ++i) {
+        std::vector<size_t> gs;
+        for (size_t si = 0; si < B->m[i]->seq.size(); ++si)
+            if (B->m[i]->seq[si].kind == 0 && step_active(B->m[i], B->m[i]->seq[si])) gs.push_back(si);
+        if (i > 0 && gs.size() != B->gemm_steps[0].size()) return fail(CCSD_ERR_INVALID);
+        B->gemm_steps.push_back(gs);
+    }
+    void* p = nullptr;
+    int rc;
+    if ((rc = batch_alloc(B, sizeof(double) * n, &p))) return fail(rc);
+    B->d_norms = (double*)p;
+    if ((rc = batch_alloc(B, sizeof(int) * n, &p))) return fail(rc);
+    B->d_done = (int*)p;
+    if ((rc = batch_alloc(B, sizeof(double2) * n, &p))) return fail(rc);
+    B->d_energy = (double2*)p;
+    B->done.assign(n, 0);
+    if (cudaMemsetAsync(B->d_done, 0, sizeof(int) * n, B->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
+    if (cudaStreamSynchronize(B->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
+    *out = B;
+    return CCSD_OK;
+}
+
+int ccsd_batch_iterate(ccsd_batch_t B, int n_iter, int* done, double* max_resid) {
+    if (!B || n_iter < 0) return CCSD_ERR_INVALID;
+    const int f = B->fp32;
+    int rc;
+    if (!B->tuned[f]) {
+        // start from each step's own tile shape (first member), warm every kernel, then tune
+        std::vector<int> cf;
+        for (size_t g = 0; g < B->gemm_steps[0].size(); ++g)
+            cf.push_back(B->m[0]->gemms[B->m[0]->seq[B->gemm_steps[0][g]].idx].cfg);
+        if ((rc = batch_build_groups(B, f, cf))) return rc;
+        batch_residual(B);
+        CK(cudaStreamSynchronize(B->st));
+        if ((rc = batch_autotune(B, f))) return rc;
+    }
+    if (!B->graph[f] && (rc = batch_capture(B, f))) return rc;
+    std::vector<double> norms((size_t)B->n, 0.0);
+    for (int it = 0; it < n_iter; ++it) {
+        CK(cudaGraphLaunch(B->graph[f], B->st));
+        CK(cudaMemcpyAsync(norms.data(), B->d_norms, sizeof(double) * B->n, cudaMemcpyDeviceToHost, B->st));
+        CK(cudaStreamSynchronize(B->st));
+        bool changed = false, all = true;
+        for (int i = 0; i < B->n; ++i) {
+            if (!std::isfinite(norms[i])) return CCSD_ERR_DIVERGED;
+            if (!B->done[i] && norms[i] < B->m[i]->cfg.conv_tol) { B->done[i] = 1; changed = true; }
+            all = all && B->done[i];
+        }
+        if (changed) {
+            CK(cudaMemcpyAsync(B->d_done, B->done.data(), sizeof(int) * B->n, cudaMemcpyHostToDevice, B->st));
+            CK(cudaStreamSynchronize(B->st));
+        }
+        if (all) break;
+    }
+    for (int i = 0; i < B->n; ++i) {
+        if (done) done[i] = B->done[i];
+        if (max_resid) max_resid[i] = norms[i];
+    }
+    return CCSD_OK;
+}
+
+int ccsd_batch_energy(ccsd_batch_t B, double* e_real, double* e_imag) {
+    if (!B || !e_real) return CCSD_ERR_INVALID;
+    for (int i = 0; i < B->n; ++i) {
+        double er = 0.0, ei = 0.0;
+        int rc = ccsd_energy(B->m[i], &er, &ei);
+        if (rc) return rc;
+        e_real[i] = er;
+        if (e_imag) e_imag[i] = ei;
+    }
+    return CCSD_OK;
+}
+
+int ccsd_batch_member(ccsd_batch_t B, int i, ccsd_t* h) {
+    if (!B || i < 0 || i >= B->n || !h) return CCSD_ERR_INVALID;
+    *h = B->m[i];
+    return CCSD_OK;
+}
+
+int ccsd_batch_stats(ccsd_batch_t B, long long* launches_per_iteration, int* tile_cfgs, int max_cfgs) {
+    if (!B) return CCSD_ERR_INVALID;
+    if (launches_per_iteration) {
+        long long n = 0;
+        for (int i = 0; i < B->n; ++i) {
+            for (const Step& st : B->m[i]->seq) if (step_active(B->m[i], st) && st.kind != 0) ++n;
+            n += 3;
+        }
+        for (const BatchGroup& g : B->groups[B->fp32]) n += 1 + (long long)g.split_members.size();
+        *launches_per_iteration = n;
+    }
+    if (tile_cfgs)
+        for (int g = 0; g < max_cfgs && g < (int)B->groups[B->fp32].size(); ++g) tile_cfgs[g] = B->groups[B->fp32][g].cfg;
+    return CCSD_OK;
+}
+
+int ccsd_batch_destroy(ccsd_batch_t B) {
+    if (!B) return CCSD_ERR_INVALID;
+    if (B->st) cudaStreamSynchronize(B->st);
+    for (int f = 0; f < 2; ++f) if (B->graph[f]) cudaGraphExecDestroy(B->graph[f]);
+    for (ccsd_ctx* h : B->m) ccsd_destroy(h);
+    for (void* p : B->owned) cudaFree(p);
+    if (B->st) cudaStreamDestroy(B->st);
+    delete B;
     return CCSD_OK;
 }
 

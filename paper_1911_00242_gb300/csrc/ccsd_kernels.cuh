@@ -142,8 +142,10 @@ __global__ void update_kernel(double2* __restrict__ t1, double2* __restrict__ t2
                               const double2* __restrict__ R1, const double2* __restrict__ R2,
                               const double* __restrict__ eo, const double* __restrict__ ev,
                               const int* __restrict__ kb_of, int N, int o, int v,
-                              double2* __restrict__ err1, double2* __restrict__ err2)
+                              double2* __restrict__ err1, double2* __restrict__ err2,
+                              const int* __restrict__ skip = nullptr)   // batched form: converged member
 {
+    if (skip && *skip) return;
     const long long n1 = (long long)N * o * v;
     const long long blk = (long long)o * o * v * v;
     const long long total = n1 + (long long)N * N * N * blk;

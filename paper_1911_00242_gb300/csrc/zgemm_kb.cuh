@@ -45,20 +45,15 @@ template <typename T> struct Cplx;
 template <> struct Cplx<double> { using V = double2; };
 template <> struct Cplx<float> { using V = float2; };
 
-template <int BM, int BN, int BK, int TM, int TN, typename T = double>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
-zgemm_kb_kernel(const GemmArgs g)
+// One output tile (tile, batch b, K split) of one GEMM; called by the plain
+// kernel below and by the grouped persistent kernel of the batched form.
+template <int BM, int BN, int BK, int TM, int TN, typename T>
+__device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long long b, int split,
+                                           typename Cplx<T>::V (&As)[BK][BM], typename Cplx<T>::V (&Bs)[BK][BN])
 {
     using V = typename Cplx<T>::V;
     constexpr int NT = (BM / TM) * (BN / TN);
     constexpr int TX = BN / TN;
-    __shared__ V As[BK][BM];
-    __shared__ V Bs[BK][BN];
-
-    const int ntile = g.tiles_m * g.tiles_n;
-    const int tile = blockIdx.x % ntile;
-    const long long b = blockIdx.x / ntile;
-    const int split = blockIdx.y;
     const int m0 = (tile % g.tiles_m) * BM;
     const int n0 = (tile / g.tiles_m) * BN;
     const int tid = threadIdx.x;
@@ -154,6 +149,44 @@ zgemm_kb_kernel(const GemmArgs g)
                 else *p = make_double2(re, im);
             }
         }
+}
+
+template <int BM, int BN, int BK, int TM, int TN, typename T = double>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+zgemm_kb_kernel(const GemmArgs g)
+{
+    using V = typename Cplx<T>::V;
+    __shared__ V As[BK][BM];
+    __shared__ V Bs[BK][BN];
+    const int ntile = g.tiles_m * g.tiles_n;
+    zgemm_tile<BM, BN, BK, TM, TN, T>(g, blockIdx.x % ntile, blockIdx.x / ntile, blockIdx.y, As, Bs);
+}
+
+// Grouped persistent form (batched solves): one launch covers the same plan
+// step of many independent problems.  Work item w of the flattened list
+// [member][split][batch][tile] maps to member i with prefix[i] <= w < prefix[i+1];
+// every CTA strides through the list.  All members use this launch's tile shape.
+template <int BM, int BN, int BK, int TM, int TN, typename T = double>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+zgemm_grouped_kernel(const GemmArgs* __restrict__ gs, const long long* __restrict__ prefix, int nmem, long long total)
+{
+    using V = typename Cplx<T>::V;
+    __shared__ V As[BK][BM];
+    __shared__ V Bs[BK][BN];
+    for (long long w = blockIdx.x; w < total; w += gridDim.x) {
+        int lo = 0, hi = nmem - 1;
+        while (lo < hi) {                       // last member whose prefix <= w
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= w) lo = mid; else hi = mid - 1;
+        }
+        const GemmArgs g = gs[lo];
+        const long long local = w - prefix[lo];
+        const long long ntile = (long long)g.tiles_m * g.tiles_n;
+        const long long per_split = ntile * g.nbatch;
+        const int split = (int)(local / per_split);
+        const long long r = local % per_split;
+        zgemm_tile<BM, BN, BK, TM, TN, T>(g, (int)(r % ntile), r / ntile, split, As, Bs);
+    }
 }
 
 // Deterministic split-K reduction: C_b (+)= alpha * sum_s work[s][b] in split order.
