@@ -30,7 +30,11 @@ import ccsd_synth as cs  # noqa: E402
 
 WORKLOADS = {"grid222_o8_v32": dict(diis_depth=6),
              # 2x2x1 grid, same orbitals: the profiling case (vvvv 1.1 GB, still larger than L2)
-             "grid221_o8_v32": dict(diis_depth=6)}
+             "grid221_o8_v32": dict(diis_depth=6),
+             # 64 independent problems of uneven size in grouped launches (batched form)
+             "batch64": dict(diis_depth=0),
+             # Poisson request stream into the serving loop (serving form)
+             "serve": dict(diis_depth=6)}
 METRIC = "CCSD iter/s"
 FP64_PEAK_TFLOPS = 1.25          # GB300 nominal FP64 (152 SMs x 2.07 GHz x ~4 flop/clk/SM)
 TF32_NOMINAL_RATIO = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rates
@@ -212,6 +216,91 @@ def run_mixed(args, spec, dev, depth, local, fp64_solve, fp64_ms_per_iter):
     return out
 
 
+def run_batch(args, local):
+    """Batched form: 64 problems (N_k in {1,2,4,8}, o 4..8, v 8..24) per iteration."""
+    import torch
+    from paper_1911_00242_gb300.binding import CCSD_MIXED, BatchSolver
+    specs = cs.batch_specs(64)
+    devs = [{k: torch.from_numpy(v).to(f"cuda:{local}") for k, v in cs.generate(s).items()} for s in specs]
+    prec = CCSD_MIXED if args.precision == "mixed" else 0
+    B = BatchSolver([(s.grid, s.nocc, s.nvir, d) for s, d in zip(specs, devs)], conv_tol=1e-30, precision=prec)
+    t0 = time.perf_counter()
+    B.iterate(1)                                 # autotune + graph capture + first iteration
+    t_setup = time.perf_counter() - t0
+    for _ in range(max(0, args.warmup - 1)):
+        B.iterate(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        B.iterate(1)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    launches, cfgs = B.stats()
+    fl = sum(flops_per_iteration(s) for s in specs)
+    B.close()
+    return {"metric": METRIC, "value": 64 * args.steps / dt, "unit": "member iter/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128", "data": "synthetic",
+            "config": {"workload": "batch64", "members": 64, "precision": args.precision,
+                       "nk": [s.nk for s in specs], "nocc": [s.nocc for s in specs], "nvir": [s.nvir for s in specs]},
+            "aggregate_tflops": fl * args.steps / dt / 1e12, "gpu_launches_per_step": launches,
+            "autotune_and_capture_s": t_setup, "tile_cfgs": cfgs[:40]}
+
+
+def run_serve(args, local):
+    """Serving form: Poisson arrivals into the request loop; p50/p99 time to converge."""
+    import torch
+    from paper_1911_00242_gb300.binding import CCSD_MIXED, Server
+    rng = np.random.default_rng([5000, 7])
+    small = cs.batch_specs(16, seed=4000)
+    large = cs.spec_for("grid222_o8_v32")
+    pool = [(s, {k: torch.from_numpy(v).pin_memory() for k, v in cs.generate(s).items()}) for s in small]
+    big = (large, {k: torch.from_numpy(v).pin_memory() for k, v in cs.generate(large).items()})
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=int(args.rate * args.duration * 2) + 10))
+    arrivals = arrivals[arrivals < args.duration]
+    picks = [(big if rng.random() < 0.1 else pool[int(rng.integers(0, len(pool)))]) for _ in arrivals]
+    cfg = dict(conv_tol=1e-7, diis_depth=6, max_iter=200, precision=CCSD_MIXED, mixed_tol=1e-7, polish_iters=0)
+    srv = Server(200 << 30, 32)
+    ids, t_start = [], time.perf_counter()
+    peak_bytes = peak_active = 0
+    for t_arr, (s, arr) in zip(arrivals, picks):
+        while time.perf_counter() - t_start < t_arr:
+            a, q, b = srv.stats()
+            peak_bytes, peak_active = max(peak_bytes, b), max(peak_active, a)
+            time.sleep(0.002)
+        ids.append((srv.submit(s.grid, s.nocc, s.nvir, arr, **cfg), s is large))
+    done = {}
+    while len(done) < len(ids):
+        for i, is_large in ids:
+            if i not in done:
+                st, e, t, it = srv.poll(i)
+                if st == 2 or st < 0:
+                    done[i] = (st, t, it, is_large)
+        a, q, b = srv.stats()
+        peak_bytes, peak_active = max(peak_bytes, b), max(peak_active, a)
+        time.sleep(0.005)
+    elapsed = time.perf_counter() - t_start
+    srv.close()
+    ok = [v for v in done.values() if v[0] == 2]
+    ts = np.array([v[1] for v in ok])
+    tl = np.array([v[1] for v in ok if v[3]])
+    tsm = np.array([v[1] for v in ok if not v[3]])
+    q = lambda x, p: float(np.percentile(x, p)) if len(x) else None   # noqa: E731
+    return {"metric": "CCSD solve time to converge", "value": q(ts, 99), "unit": "s (p99)", "n_gpus": 1,
+            "steps": len(ids), "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "mixed", "data": "synthetic",
+            "config": {"workload": "serve", "rate_per_s": args.rate, "duration_s": args.duration,
+                       "large_fraction": 0.1, "tolerance": 1e-7,
+                       "policy": "tcgen05 split-TF32 mixed iterations to max|R| < 1e-7, DIIS(6), no FP64 polish",
+                       "hbm_budget_gb": 200, "max_slots": 32},
+            "p50_s": q(ts, 50), "p99_s": q(ts, 99), "p50_small_s": q(tsm, 50), "p99_small_s": q(tsm, 99),
+            "p50_large_s": q(tl, 50), "p99_large_s": q(tl, 99),
+            "solves_per_s": len(ok) / elapsed, "submitted": len(ids), "completed": len(ok),
+            "failed": len(ids) - len(ok), "elapsed_s": elapsed, "peak_admitted_gb": peak_bytes / 2**30,
+            "peak_active": peak_active}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -223,12 +312,15 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-form comparison")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-solution comparison")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"], help="batch64: member precision")
+    ap.add_argument("--rate", type=float, default=5.0, help="serve: requests per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    spec = cs.spec_for(args.workload)
+    spec = cs.spec_for(args.workload) if args.workload in cs.CONFIGS else None
 
     if args.impl == "reference":
         if rank != 0:
@@ -239,6 +331,12 @@ def main():
 
     import torch
     torch.cuda.set_device(local)
+    if args.workload == "batch64":
+        print(json.dumps(run_batch(args, local)), flush=True)
+        return 0
+    if args.workload == "serve":
+        print(json.dumps(run_serve(args, local)), flush=True)
+        return 0
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -45,7 +45,7 @@ import numpy as np
 import scipy.fft as sfft
 
 __all__ = [
-    "SynthSpec", "CONFIGS", "spec_for", "generate", "generate_fock",
+    "SynthSpec", "CONFIGS", "spec_for", "batch_specs", "generate", "generate_fock",
     "realspace_supercell", "bloch_unitary", "STORED_BLOCKS", "random_amplitudes",
 ]
 
@@ -77,6 +77,23 @@ CONFIGS = {
     # smaller grid with the FP64 workload's orbitals, for profiling captures
     "grid221_o8_v32": SynthSpec((2, 2, 1), 8, 32, 1012),
 }
+
+
+BATCH_GRIDS = ((1, 1, 1), (2, 1, 1), (2, 2, 1), (2, 2, 2))      # N_k in {1, 2, 4, 8}
+
+
+def batch_specs(count: int = 64, seed: int = 2000) -> list:
+    """The batched workload: `count` independent problems, N_k drawn from
+    {1, 2, 4, 8}, n_occ uniform in 4..8, n_vir uniform in 8..24 (one size
+    stream seeded with `seed`), instance i seeded seed + i."""
+    rng = np.random.default_rng([seed, 41])
+    out = []
+    for i in range(count):
+        g = BATCH_GRIDS[int(rng.integers(0, len(BATCH_GRIDS)))]
+        o = int(rng.integers(4, 9))
+        v = int(rng.integers(8, 25))
+        out.append(SynthSpec(g, o, v, seed + i))
+    return out
 
 
 def spec_for(name: str, **over) -> SynthSpec:

@@ -177,6 +177,28 @@ int ccsd_batch_member(ccsd_batch_t b, int i, ccsd_t* h);
 int ccsd_batch_stats(ccsd_batch_t b, long long* launches_per_iteration, int* tile_cfgs, int max_cfgs);
 int ccsd_batch_destroy(ccsd_batch_t b);
 
+/* ---------------------------------------------------------------- serving form
+ * A request loop on its own host thread.  Submitted solves wait in FIFO order
+ * until their device-memory footprint fits in hbm_budget_bytes and one of
+ * max_slots slots is free; each admitted solve gets a stream and a handle whose
+ * integrals and amplitudes stay resident until it finishes.  All admitted
+ * solves advance together: each round enqueues one iteration of every solve
+ * (their kernels run concurrently) and then completes them.  Converged solves
+ * retire and free their memory for the queue.  A solve runs like ccsd_solve
+ * (mixed iterations, then polish_iters FP64 iterations, for CCSD_MIXED).
+ * The inputs a request points to must stay valid until it is done (host
+ * inputs are copied when the request is admitted). */
+typedef struct ccsd_server* ccsd_server_t;
+int ccsd_server_create(size_t hbm_budget_bytes, int max_slots, ccsd_server_t* out);
+int ccsd_submit(ccsd_server_t s, const ccsd_config* cfg, const ccsd_inputs* in, uint64_t* request_id);
+/* state: 0 queued, 1 running, 2 done, < 0 the CCSD_ERR_* code it ended with
+ * (CCSD_ERR_OOM: larger than the whole budget).  e_corr: energy per unit cell
+ * (done only); t_converge_s: submission to completion (finished only). */
+int ccsd_poll(ccsd_server_t s, uint64_t id, int* state, double* e_corr, double* t_converge_s, int* iterations);
+int ccsd_server_stats(ccsd_server_t s, int* active, int* queued, size_t* admitted_bytes);
+/* Finishes the admitted solves, cancels the queued ones, joins the thread. */
+int ccsd_server_destroy(ccsd_server_t s);
+
 const char* ccsd_strerror(int code);
 
 /* Correlation energy per unit cell of the amplitudes t1, t2 (same expression

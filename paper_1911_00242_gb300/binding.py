@@ -71,6 +71,14 @@ SYMBOLS = {
     "ccsd_batch_stats": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
                           ctypes.c_int], ctypes.c_int),
     "ccsd_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "ccsd_server_create": ([ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "ccsd_submit": ([ctypes.c_void_p, ctypes.POINTER(ccsd_config), ctypes.POINTER(ccsd_inputs),
+                     ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "ccsd_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "ccsd_server_stats": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "ccsd_server_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "ccsd_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "ccsd_energy_noalloc": ([ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 6,
                             ctypes.c_int),
@@ -260,6 +268,57 @@ class BatchSolver:
     def close(self):
         if getattr(self, "h", None):
             self.lib.ccsd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The serving loop: submit solves, poll for results (see ccsd_server_* in include/ccsd.h)."""
+
+    def __init__(self, hbm_budget_bytes, max_slots):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        check(self.lib.ccsd_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)), "ccsd_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, grid, nocc, nvir, arrays, **cfg):
+        c = make_config(grid, nocc, nvir, **cfg)
+        inp = ccsd_inputs()
+        for name in ("f_oo", "f_vv", "f_ov") + BLOCKS:
+            setattr(inp, name, _ptr(arrays[name]))
+        inp.int_dtype = CCSD_C128
+        rid = ctypes.c_uint64(0)
+        check(self.lib.ccsd_submit(self.h, ctypes.byref(c), ctypes.byref(inp), ctypes.byref(rid)), "ccsd_submit")
+        self._keep[rid.value] = arrays
+        return rid.value
+
+    def poll(self, rid):
+        st = ctypes.c_int(0)
+        e = ctypes.c_double(0.0)
+        t = ctypes.c_double(0.0)
+        it = ctypes.c_int(0)
+        check(self.lib.ccsd_poll(self.h, rid, ctypes.byref(st), ctypes.byref(e), ctypes.byref(t), ctypes.byref(it)),
+              "ccsd_poll")
+        if st.value == 2 or st.value < 0:
+            self._keep.pop(rid, None)
+        return st.value, e.value, t.value, it.value
+
+    def stats(self):
+        a = ctypes.c_int(0)
+        q = ctypes.c_int(0)
+        b = ctypes.c_size_t(0)
+        check(self.lib.ccsd_server_stats(self.h, ctypes.byref(a), ctypes.byref(q), ctypes.byref(b)), "ccsd_server_stats")
+        return a.value, q.value, b.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ccsd_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -28,10 +28,16 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 using namespace ccsdk;
@@ -129,6 +135,8 @@ struct ccsd_ctx {
     double* red_out = nullptr;       // scalars
     double2* cred = nullptr;
     double2* cred_out = nullptr;
+    double* norm_host = nullptr;     // pinned: max|R| of the last iteration
+    cudaEvent_t ev_norm = nullptr;
     std::vector<double2*> hx, he;    // DIIS history
     std::vector<std::vector<double>> gram;
     int diis_count = 0, diis_next = 0;
@@ -1196,8 +1204,8 @@ void launch_step(ccsd_ctx* h, size_t si) {
         }
 }
 
-int run_residual(ccsd_ctx* h) {
-    const bool tc = h->fp32 && h->cfg.precision == CCSD_MIXED;
+// Enqueues one residual evaluation; no host synchronization.
+int run_residual_async(ccsd_ctx* h) {
     for (size_t si = 0; si < h->seq.size(); ++si) {
         if (!step_active(h, h->seq[si])) continue;
         if (h->trace) cudaEventRecord(h->ev0[si], h->st);
@@ -1206,27 +1214,28 @@ int run_residual(ccsd_ctx* h) {
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { last_err(e); return CCSD_ERR_CUDA; }
-    if (tc) {
-        // a bounded wait inside a tensor-core GEMM gave up: report, clear, fail the call
-        int flag = 0;
-        CK(cudaMemcpyAsync(&flag, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-        CK(cudaStreamSynchronize(h->st));
-        if (flag) {
-            snprintf(g_errbuf, sizeof g_errbuf, "tensor-core GEMM wait timed out (code %d)", flag);
-            CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st));
-            return CCSD_ERR_TIMEOUT;
-        }
-    }
-    if (h->trace) return trace_collect(h, 0, h->seq.size());
     return 0;
 }
 
-int reduce_max(ccsd_ctx* h, const double2* x, long long n, double* out_host) {
-    maxabs_partial<<<h->red_blocks, 256, 0, h->st>>>(x, n, h->red);
-    final_max<<<1, 32, 0, h->st>>>(h->red, h->red_blocks, h->red_out);
-    h->launches += 2;
-    CK(cudaMemcpyAsync(out_host, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+// A bounded wait inside a tensor-core GEMM gave up: report, clear, fail (synchronizes).
+int check_tc_err(ccsd_ctx* h) {
+    if (!(h->fp32 && h->cfg.precision == CCSD_MIXED) || !h->tc_err) return 0;
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
+    if (flag) {
+        snprintf(g_errbuf, sizeof g_errbuf, "tensor-core GEMM wait timed out (code %d)", flag);
+        CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st));
+        return CCSD_ERR_TIMEOUT;
+    }
+    return 0;
+}
+
+int run_residual(ccsd_ctx* h) {
+    int rc = run_residual_async(h);
+    if (rc) return rc;
+    if ((rc = check_tc_err(h))) return rc;
+    if (h->trace) return trace_collect(h, 0, h->seq.size());
     return 0;
 }
 
@@ -1456,6 +1465,8 @@ int batch_capture(ccsd_batch* B, int fp32) {
     return 0;
 }
 
+size_t footprint_bytes(const ccsd_config* c, int borrowed);
+
 size_t footprint_bytes(const ccsd_config* c, int borrowed) {
     const long long N = (long long)c->nk_dims[0] * c->nk_dims[1] * c->nk_dims[2];
     const long long o = c->nocc, v = c->nvir;
@@ -1495,6 +1506,237 @@ bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// First half of an iteration: residual and max|R| on the device, the norm
+// copied into pinned host memory; returns without waiting.
+int iter_begin(ccsd_ctx* h) {
+    int rc = run_residual_async(h);
+    if (rc) return rc;
+    const long long n = h->n1 + h->n2;
+    maxabs_partial<<<h->red_blocks, 256, 0, h->st>>>(h->res, n, h->red);
+    final_max<<<1, 32, 0, h->st>>>(h->red, h->red_blocks, h->red_out);
+    h->launches += 2;
+    CK(cudaMemcpyAsync(h->norm_host, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaEventRecord(h->ev_norm, h->st));
+    return 0;
+}
+
+// Second half: waits for the norm, then the convergence test and the update
+// t <- t + R/D (plus DIIS) unless converged.
+int iter_end(ccsd_ctx* h, int* done, double* max_resid) {
+    *done = 0;
+    CK(cudaEventSynchronize(h->ev_norm));
+    int rc = check_tc_err(h);
+    if (rc) return rc;
+    if (h->trace && (rc = trace_collect(h, 0, h->seq.size()))) return rc;
+    const double mr = *h->norm_host;
+    const long long n = h->n1 + h->n2;
+    *max_resid = mr;
+    if (!std::isfinite(mr)) return CCSD_ERR_DIVERGED;
+    if (mr < h->cfg.conv_tol) { *done = 1; return CCSD_OK; }
+    const int depth = h->cfg.diis_depth;
+    const size_t tu = h->seq.size();     // trace slot of the update
+    if (h->trace) cudaEventRecord(h->ev0[tu], h->st);
+    if (depth == 0) {
+        update_kernel<<<ew_grid(n), 256, 0, h->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_R1], h->buf[B_R2],
+                                                     h->eo, h->ev, h->kb_of, h->N, h->o, h->v, nullptr, nullptr);
+        ++h->launches;
+        if (h->trace) { cudaEventRecord(h->ev1[tu], h->st); if ((rc = trace_collect(h, tu, tu + 1))) return rc; }
+    } else {
+        const int slot = h->diis_next;
+        double2* x = h->hx[slot];
+        double2* e = h->he[slot];
+        CK(cudaMemcpyAsync(x, h->amp, (size_t)n * 16, cudaMemcpyDeviceToDevice, h->st));
+        update_kernel<<<ew_grid(n), 256, 0, h->st>>>(x, x + h->n1, h->buf[B_R1], h->buf[B_R2],
+                                                     h->eo, h->ev, h->kb_of, h->N, h->o, h->v, e, e + h->n1);
+        ++h->launches;
+        if (h->trace) { cudaEventRecord(h->ev1[tu], h->st); if ((rc = trace_collect(h, tu, tu + 1))) return rc; }
+        h->diis_next = (slot + 1) % depth;
+        if (h->diis_count < depth) ++h->diis_count;
+        const int m = h->diis_count;
+        for (int j = 0; j < m; ++j) {
+            double d = 0.0;
+            if ((rc = reduce_redot(h, e, h->he[j], n, &d))) return rc;
+            h->gram[slot][j] = h->gram[j][slot] = d;
+        }
+        if (m < 2) {
+            CK(cudaMemcpyAsync(h->amp, x, (size_t)n * 16, cudaMemcpyDeviceToDevice, h->st));
+        } else {
+            // Pulay: [B -1; -1 0][c; l] = [0; -1], solved by Gaussian elimination with pivoting
+            const int S = m + 1;
+            std::vector<double> A((size_t)S * S, 0.0), b((size_t)S, 0.0);
+            for (int i = 0; i < m; ++i) for (int j = 0; j < m; ++j) A[(size_t)i * S + j] = h->gram[i][j];
+            for (int i = 0; i < m; ++i) { A[(size_t)i * S + m] = -1.0; A[(size_t)m * S + i] = -1.0; }
+            b[(size_t)m] = -1.0;
+            for (int c = 0; c < S; ++c) {
+                int p = c;
+                for (int r = c + 1; r < S; ++r) if (std::fabs(A[(size_t)r * S + c]) > std::fabs(A[(size_t)p * S + c])) p = r;
+                if (p != c) { for (int k = 0; k < S; ++k) std::swap(A[(size_t)c * S + k], A[(size_t)p * S + k]); std::swap(b[c], b[p]); }
+                const double piv = A[(size_t)c * S + c];
+                if (piv == 0.0) return CCSD_ERR_DIVERGED;
+                for (int r = c + 1; r < S; ++r) {
+                    const double f = A[(size_t)r * S + c] / piv;
+                    for (int k = c; k < S; ++k) A[(size_t)r * S + k] -= f * A[(size_t)c * S + k];
+                    b[r] -= f * b[c];
+                }
+            }
+            std::vector<double> xs((size_t)S, 0.0);
+            for (int r = S - 1; r >= 0; --r) {
+                double s = b[r];
+                for (int k = r + 1; k < S; ++k) s -= A[(size_t)r * S + k] * xs[k];
+                xs[r] = s / A[(size_t)r * S + r];
+            }
+            Combo cb{};
+            cb.m = m;
+            for (int j = 0; j < m; ++j) { cb.x[j] = h->hx[j]; cb.c[j] = xs[j]; }
+            combo_kernel<<<ew_grid(n), 256, 0, h->st>>>(h->amp, cb, n);
+            ++h->launches;
+        }
+    }
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) { last_err(ce); return CCSD_ERR_CUDA; }
+    return CCSD_OK;
+}
+
+
+// ================================================================ serving form
+// A host thread admits submitted solves by device-memory footprint, gives each
+// admitted solve its own stream and handle (integrals and amplitudes stay
+// resident until it finishes), and advances all admitted solves in rounds: it
+// first enqueues one iteration of every solve (so their kernels run
+// concurrently on the GPU), then completes them one by one.  Converged solves
+// retire, free their memory and make room for the queue.
+namespace {
+
+struct ServerReq {
+    uint64_t id = 0;
+    ccsd_config cfg{};
+    ccsd_inputs in{};
+    int state = 0;                 // 0 queued, 1 running, 2 done, < 0 error code
+    int phase = 0;                 // mixed form: 0 mixed iterations, 1 FP64 polish
+    int iters = 0, polish_left = 0;
+    double e_re = 0.0, e_im = 0.0, max_resid = 0.0;
+    double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+    size_t bytes = 0;
+    ccsd_t h = nullptr;
+    cudaStream_t st = nullptr;
+};
+
+}  // namespace
+
+struct ccsd_server {
+    size_t budget = 0, used = 0;
+    int max_slots = 1;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<ServerReq*> pending;
+    std::vector<ServerReq*> active;
+    std::map<uint64_t, ServerReq*> all;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::thread th;
+    std::chrono::steady_clock::time_point t0;
+};
+
+namespace {
+
+double server_now(const ccsd_server* S) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - S->t0).count();
+}
+
+size_t request_bytes(const ccsd_config& c) {
+    size_t b = footprint_bytes(&c, 0);
+    if (c.precision == CCSD_MIXED) b += b;     // tensor-core operands and complex64 copies (bound)
+    return b;
+}
+
+void server_finish(ccsd_server* S, ServerReq* r, int state) {
+    if (r->h) {
+        if (state == 2) ccsd_energy(r->h, &r->e_re, &r->e_im);
+        ccsd_destroy(r->h);
+        r->h = nullptr;
+    }
+    if (r->st) { cudaStreamDestroy(r->st); r->st = nullptr; }
+    std::lock_guard<std::mutex> lock(S->mu);
+    r->t_done = server_now(S);
+    r->state = state;
+    S->used -= r->bytes;
+}
+
+void server_loop(ccsd_server* S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::vector<ServerReq*> admit;
+        {
+            std::unique_lock<std::mutex> lock(S->mu);
+            if (S->active.empty())
+                S->cv.wait(lock, [&] { return S->stop || !S->pending.empty(); });
+            if (S->stop && S->active.empty() && S->pending.empty()) return;
+            if (S->stop) {                         // cancel what has not started
+                for (ServerReq* r : S->pending) { r->state = CCSD_ERR_INVALID; r->t_done = server_now(S); }
+                S->pending.clear();
+            }
+            while (!S->pending.empty() && (int)(S->active.size() + admit.size()) < S->max_slots) {
+                ServerReq* r = S->pending.front();
+                if (r->bytes > S->budget) {        // can never fit
+                    S->pending.pop_front();
+                    r->state = CCSD_ERR_OOM;
+                    r->t_done = server_now(S);
+                    continue;
+                }
+                if (S->used + r->bytes > S->budget) break;     // FIFO: wait for memory
+                S->pending.pop_front();
+                S->used += r->bytes;
+                admit.push_back(r);
+            }
+        }
+        for (ServerReq* r : admit) {
+            int rc = CCSD_OK;
+            if (cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); rc = CCSD_ERR_CUDA; }
+            if (!rc) rc = ccsd_create(&r->cfg, &r->in, r->st, &r->h);
+            if (rc) { server_finish(S, r, rc); continue; }
+            r->polish_left = r->cfg.precision == CCSD_MIXED ? r->cfg.polish_iters : 0;
+            if (r->cfg.precision == CCSD_MIXED) r->h->cfg.conv_tol = std::max(r->cfg.mixed_tol, r->cfg.conv_tol);
+            std::lock_guard<std::mutex> lock(S->mu);
+            r->t_admit = server_now(S);
+            r->state = 1;
+            S->active.push_back(r);
+        }
+        // one round: enqueue an iteration of every active solve, then complete each
+        std::vector<ServerReq*> act;
+        { std::lock_guard<std::mutex> lock(S->mu); act = S->active; }
+        std::vector<int> began(act.size(), 0);
+        for (size_t i = 0; i < act.size(); ++i) began[i] = iter_begin(act[i]->h);
+        std::vector<ServerReq*> keep;
+        for (size_t i = 0; i < act.size(); ++i) {
+            ServerReq* r = act[i];
+            int done = 0, rc = began[i];
+            double mr = 0.0;
+            if (!rc) rc = iter_end(r->h, &done, &mr);
+            r->max_resid = mr;
+            if (rc) { server_finish(S, r, rc); continue; }
+            if (!done) {
+                if (++r->iters >= r->cfg.max_iter) { server_finish(S, r, CCSD_ERR_NOT_CONVERGED); continue; }
+                if (r->phase == 1 && --r->polish_left <= 0) { server_finish(S, r, 2); continue; }
+                keep.push_back(r);
+                continue;
+            }
+            if (r->phase == 0 && r->polish_left > 0) {    // mixed phase done: FP64 polish
+                r->phase = 1;
+                ccsd_set_precision(r->h, CCSD_FP64);
+                r->h->cfg.conv_tol = r->cfg.conv_tol;
+                keep.push_back(r);
+                continue;
+            }
+            server_finish(S, r, 2);
+        }
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->active = keep;
+    }
 }
 
 }  // namespace
@@ -1687,6 +1929,8 @@ int ccsd_create(const ccsd_config* cfg, const ccsd_inputs* in, void* stream, ccs
     h->cred = (double2*)al.get(sizeof(double2) * h->red_blocks);
     h->cred_out = (double2*)al.get(sizeof(double2) * 2);
     if (al.err) return fail(al.err);
+    if (cudaMallocHost(&h->norm_host, sizeof(double)) != cudaSuccess) { cudaGetLastError(); h->norm_host = nullptr; return fail(CCSD_ERR_OOM); }
+    if (cudaEventCreateWithFlags(&h->ev_norm, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); h->ev_norm = nullptr; return fail(CCSD_ERR_CUDA); }
     if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
     *out = h;
     return CCSD_OK;
@@ -1707,76 +1951,15 @@ int ccsd_iterate(ccsd_t h, int n_iter, int* done, double* max_resid) {
     if (!h || n_iter < 0) return CCSD_ERR_INVALID;
     if (done) *done = 0;
     h->launches = 0;
-    const long long n = h->n1 + h->n2;
-    double mr = 0.0;
     for (int it = 0; it < n_iter; ++it) {
-        int rc = run_residual(h);
+        int d = 0;
+        double mr = 0.0;
+        int rc = iter_begin(h);
         if (rc) return rc;
-        if ((rc = reduce_max(h, h->res, n, &mr))) return rc;
+        rc = iter_end(h, &d, &mr);
         if (max_resid) *max_resid = mr;
-        if (!std::isfinite(mr)) return CCSD_ERR_DIVERGED;
-        if (mr < h->cfg.conv_tol) { if (done) *done = 1; return CCSD_OK; }
-        const int depth = h->cfg.diis_depth;
-        const size_t tu = h->seq.size();     // trace slot of the update
-        if (h->trace) cudaEventRecord(h->ev0[tu], h->st);
-        if (depth == 0) {
-            update_kernel<<<ew_grid(n), 256, 0, h->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_R1], h->buf[B_R2],
-                                                         h->eo, h->ev, h->kb_of, h->N, h->o, h->v, nullptr, nullptr);
-            ++h->launches;
-            if (h->trace) { cudaEventRecord(h->ev1[tu], h->st); if ((rc = trace_collect(h, tu, tu + 1))) return rc; }
-        } else {
-            const int slot = h->diis_next;
-            double2* x = h->hx[slot];
-            double2* e = h->he[slot];
-            CK(cudaMemcpyAsync(x, h->amp, (size_t)n * 16, cudaMemcpyDeviceToDevice, h->st));
-            update_kernel<<<ew_grid(n), 256, 0, h->st>>>(x, x + h->n1, h->buf[B_R1], h->buf[B_R2],
-                                                         h->eo, h->ev, h->kb_of, h->N, h->o, h->v, e, e + h->n1);
-            ++h->launches;
-            if (h->trace) { cudaEventRecord(h->ev1[tu], h->st); if ((rc = trace_collect(h, tu, tu + 1))) return rc; }
-            h->diis_next = (slot + 1) % depth;
-            if (h->diis_count < depth) ++h->diis_count;
-            const int m = h->diis_count;
-            for (int j = 0; j < m; ++j) {
-                double d = 0.0;
-                if ((rc = reduce_redot(h, e, h->he[j], n, &d))) return rc;
-                h->gram[slot][j] = h->gram[j][slot] = d;
-            }
-            if (m < 2) {
-                CK(cudaMemcpyAsync(h->amp, x, (size_t)n * 16, cudaMemcpyDeviceToDevice, h->st));
-            } else {
-                // Pulay: [B -1; -1 0][c; l] = [0; -1], solved by Gaussian elimination with pivoting
-                const int S = m + 1;
-                std::vector<double> A((size_t)S * S, 0.0), b((size_t)S, 0.0);
-                for (int i = 0; i < m; ++i) for (int j = 0; j < m; ++j) A[(size_t)i * S + j] = h->gram[i][j];
-                for (int i = 0; i < m; ++i) { A[(size_t)i * S + m] = -1.0; A[(size_t)m * S + i] = -1.0; }
-                b[(size_t)m] = -1.0;
-                for (int c = 0; c < S; ++c) {
-                    int p = c;
-                    for (int r = c + 1; r < S; ++r) if (std::fabs(A[(size_t)r * S + c]) > std::fabs(A[(size_t)p * S + c])) p = r;
-                    if (p != c) { for (int k = 0; k < S; ++k) std::swap(A[(size_t)c * S + k], A[(size_t)p * S + k]); std::swap(b[c], b[p]); }
-                    const double piv = A[(size_t)c * S + c];
-                    if (piv == 0.0) return CCSD_ERR_DIVERGED;
-                    for (int r = c + 1; r < S; ++r) {
-                        const double f = A[(size_t)r * S + c] / piv;
-                        for (int k = c; k < S; ++k) A[(size_t)r * S + k] -= f * A[(size_t)c * S + k];
-                        b[r] -= f * b[c];
-                    }
-                }
-                std::vector<double> xs((size_t)S, 0.0);
-                for (int r = S - 1; r >= 0; --r) {
-                    double s = b[r];
-                    for (int k = r + 1; k < S; ++k) s -= A[(size_t)r * S + k] * xs[k];
-                    xs[r] = s / A[(size_t)r * S + r];
-                }
-                Combo cb{};
-                cb.m = m;
-                for (int j = 0; j < m; ++j) { cb.x[j] = h->hx[j]; cb.c[j] = xs[j]; }
-                combo_kernel<<<ew_grid(n), 256, 0, h->st>>>(h->amp, cb, n);
-                ++h->launches;
-            }
-        }
-        cudaError_t ce = cudaGetLastError();
-        if (ce != cudaSuccess) { last_err(ce); return CCSD_ERR_CUDA; }
+        if (rc) return rc;
+        if (d) { if (done) *done = 1; return CCSD_OK; }
     }
     CK(cudaStreamSynchronize(h->st));
     return CCSD_OK;
@@ -2019,12 +2202,87 @@ int ccsd_batch_destroy(ccsd_batch_t B) {
     return CCSD_OK;
 }
 
+int ccsd_server_create(size_t hbm_budget_bytes, int max_slots, ccsd_server_t* out) {
+    if (!out || max_slots < 1 || max_slots > 1024 || hbm_budget_bytes == 0) return CCSD_ERR_INVALID;
+    ccsd_server* S = new (std::nothrow) ccsd_server();
+    if (!S) return CCSD_ERR_OOM;
+    S->budget = hbm_budget_bytes;
+    S->max_slots = max_slots;
+    S->t0 = std::chrono::steady_clock::now();
+    if (cudaGetDevice(&S->device) != cudaSuccess) { cudaGetLastError(); delete S; return CCSD_ERR_CUDA; }
+    try {
+        S->th = std::thread(server_loop, S);
+    } catch (...) {
+        delete S;
+        return CCSD_ERR_OOM;
+    }
+    *out = S;
+    return CCSD_OK;
+}
+
+int ccsd_submit(ccsd_server_t S, const ccsd_config* cfg, const ccsd_inputs* in, uint64_t* request_id) {
+    if (!S || !cfg || !in || !request_id || !valid_cfg(cfg) || in->int_dtype != CCSD_C128) return CCSD_ERR_INVALID;
+    ServerReq* r = new (std::nothrow) ServerReq();
+    if (!r) return CCSD_ERR_OOM;
+    r->cfg = *cfg;
+    r->in = *in;
+    r->bytes = request_bytes(*cfg);
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        if (S->stop) { delete r; return CCSD_ERR_INVALID; }
+        r->id = S->next_id++;
+        r->t_submit = server_now(S);
+        S->all[r->id] = r;
+        S->pending.push_back(r);
+    }
+    S->cv.notify_one();
+    *request_id = r->id;
+    return CCSD_OK;
+}
+
+int ccsd_poll(ccsd_server_t S, uint64_t id, int* state, double* e_corr, double* t_converge_s, int* iterations) {
+    if (!S) return CCSD_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end()) return CCSD_ERR_INVALID;
+    const ServerReq* r = it->second;
+    if (state) *state = r->state;
+    if (e_corr) *e_corr = r->e_re;
+    if (t_converge_s) *t_converge_s = (r->state == 2 || r->state < 0) ? r->t_done - r->t_submit : 0.0;
+    if (iterations) *iterations = r->iters;
+    return CCSD_OK;
+}
+
+int ccsd_server_stats(ccsd_server_t S, int* active, int* queued, size_t* admitted_bytes) {
+    if (!S) return CCSD_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (active) *active = (int)S->active.size();
+    if (queued) *queued = (int)S->pending.size();
+    if (admitted_bytes) *admitted_bytes = S->used;
+    return CCSD_OK;
+}
+
+int ccsd_server_destroy(ccsd_server_t S) {
+    if (!S) return CCSD_ERR_INVALID;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_one();
+    if (S->th.joinable()) S->th.join();
+    for (auto& kv : S->all) delete kv.second;
+    delete S;
+    return CCSD_OK;
+}
+
 int ccsd_destroy(ccsd_t h) {
     if (!h) return CCSD_ERR_INVALID;
     if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
     for (void* p : h->owned) cudaFree(p);
     for (cudaEvent_t e : h->ev0) cudaEventDestroy(e);
     for (cudaEvent_t e : h->ev1) cudaEventDestroy(e);
+    if (h->norm_host) cudaFreeHost(h->norm_host);
+    if (h->ev_norm) cudaEventDestroy(h->ev_norm);
     delete h;
     return CCSD_OK;
 }

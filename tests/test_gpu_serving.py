@@ -1,0 +1,103 @@
+"""Serving form: continuous batching of solves in a request loop.
+
+Each solve must give the same result alone and in the mix (it runs the same
+kernels on the same data; concurrency only interleaves independent streams),
+admission must respect the memory budget, and oversized requests fail cleanly."""
+import time
+
+import numpy as np
+import pytest
+
+import ccsd_synth as cs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SPECS = [
+    cs.SynthSpec((2, 1, 1), 3, 5, 3001),
+    cs.SynthSpec((1, 1, 1), 4, 8, 3002, time_reversal=False),
+    cs.SynthSpec((2, 2, 1), 2, 4, 3003),
+    cs.SynthSpec((4, 1, 1), 4, 6, 3004),
+    cs.SynthSpec((2, 1, 1), 5, 9, 3005),
+]
+
+
+def wait_all(srv, ids, timeout=300.0):
+    t0 = time.time()
+    out = {}
+    while len(out) < len(ids):
+        for i in ids:
+            if i in out:
+                continue
+            st, e, t, it = srv.poll(i)
+            if st == 2 or st < 0:
+                out[i] = (st, e, t, it)
+        assert time.time() - t0 < timeout, "serving loop did not finish"
+        time.sleep(0.01)
+    return out
+
+
+def standalone(spec, inp, **cfg):
+    from paper_1911_00242_gb300.binding import Solver
+    S = Solver(spec.grid, spec.nocc, spec.nvir, inp, **cfg)
+    ok, it, mr = S.solve()
+    e = S.energy().real
+    S.close()
+    return ok, e
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_results_alone_equal_results_in_mix(lib, precision):
+    from paper_1911_00242_gb300.binding import Server
+    cfg = dict(conv_tol=1e-8, diis_depth=6, max_iter=100, precision=precision, mixed_tol=1e-7, polish_iters=2)
+    inps = [cs.generate(s) for s in SPECS]
+    srv = Server(64 << 30, 8)
+    ids = [srv.submit(s.grid, s.nocc, s.nvir, inp, **cfg) for s, inp in zip(SPECS, inps)]
+    res = wait_all(srv, ids)
+    srv.close()
+    for s, inp, i in zip(SPECS, inps, ids):
+        st, e, t, it = res[i]
+        assert st == 2, (s, st)
+        ok, e_alone = standalone(s, inp, **cfg)
+        assert e == e_alone, (s, e, e_alone)
+        assert t > 0 and it > 0
+
+
+def test_admission_by_footprint(lib):
+    from paper_1911_00242_gb300 import binding
+    from paper_1911_00242_gb300.binding import Server
+    import ctypes
+    inps = [cs.generate(s) for s in SPECS]
+    fp = []
+    for s in SPECS:
+        c = binding.make_config(s.grid, s.nocc, s.nvir)
+        n = ctypes.c_size_t(0)
+        assert lib.ccsd_footprint(ctypes.byref(c), 0, ctypes.byref(n)) == 0
+        fp.append(n.value)
+    budget = max(fp) + min(fp)                 # at most two at a time
+    srv = Server(budget, 8)
+    ids = [srv.submit(s.grid, s.nocc, s.nvir, inp, conv_tol=1e-8, max_iter=100) for s, inp in zip(SPECS, inps)]
+    peak_queued, peak_bytes = 0, 0
+    done = {}
+    t0 = time.time()
+    while len(done) < len(ids):
+        a, q, b = srv.stats()
+        peak_queued = max(peak_queued, q)
+        peak_bytes = max(peak_bytes, b)
+        assert b <= budget
+        for i in ids:
+            if i not in done:
+                st, e, t, it = srv.poll(i)
+                if st == 2 or st < 0:
+                    done[i] = st
+        assert time.time() - t0 < 300
+        time.sleep(0.005)
+    srv.close()
+    assert all(st == 2 for st in done.values())
+    assert peak_queued > 0
+    # a request larger than the whole budget fails with CCSD_ERR_OOM instead of waiting forever
+    srv = Server(min(fp) // 2, 2)
+    i = srv.submit(SPECS[0].grid, SPECS[0].nocc, SPECS[0].nvir, inps[0])
+    st = wait_all(srv, [i])[i][0]
+    srv.close()
+    assert st == -2
