@@ -399,7 +399,10 @@ def main():
                 "peak_source": "recipe nominal FP64 1.25 TFLOP/s (measured DFMA/DMMA probe: 1.01/1.05)",
                 "traffic": load_traffic(name), "flops_per_launch": fl, "launch_ms": avg_s * 1e3}
     iter_flops = flops_per_iteration(spec)
-    trace_summary = {s[0]: round(s[2] / max(s[1], 1), 3) for s in steps}
+    trace_summary = {}
+    for st in steps:       # per step name: device ms per iteration, summed over its launches
+        if st[1]:
+            trace_summary[st[0]] = round(trace_summary.get(st[0], 0.0) + st[2] / st[1], 3)
 
     result = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,

@@ -213,6 +213,9 @@ struct GemmSpec {
     int M, N, K, nbatch, nchunk;
     std::vector<long long> offA, offB, offC;
     std::vector<int> rowA, colA, rowB, colB, rowC, colC;
+    std::vector<int> nchunk_b;               // optional per-batch chunk counts
+    std::vector<long long> offC2;            // optional antisymmetric mirror of C
+    std::vector<int> colC2;
     bool conjA = false, conjB = false, acc = true;
     double ar = 1.0, ai = 0.0;
 };
@@ -225,8 +228,19 @@ const int CFG_BN[5] = {64, 32, 16, 16, 16};
 const int kSMs = 152;
 
 int finalize_gemm(ccsd_ctx* h, Alloc& al, GemmSpec s, size_t& work_need) {
+    if (s.nbatch == 0) {
+        // an empty contraction (no momentum blocks for this shape): kept as a no-op step
+        // so that every problem has the same step sequence (batched form)
+        GemmPlan p{};
+        p.a = s.a; p.b = s.b; p.c = s.c; p.cfg = CFG_16x16; p.blocks = 0;
+        p.args.M = std::max(s.M, 1); p.args.N = std::max(s.N, 1); p.args.K = s.K;
+        p.args.nbatch = 0; p.args.nchunk = std::max(s.nchunk, 1); p.args.nsplit = 1; p.args.chunks_per_split = 1;
+        h->gemms.push_back(p);
+        h->seq.push_back({0, (int)h->gemms.size() - 1, h->cur_name, 0.0, 0.0});
+        return 0;
+    }
     // Put the larger output dimension on M (C^T = B^T A^T swaps the operands).
-    if (s.N > s.M) {
+    if (s.N > s.M && s.offC2.empty()) {
         std::swap(s.M, s.N);
         std::swap(s.a, s.b);
         std::swap(s.offA, s.offB);
@@ -254,6 +268,15 @@ int finalize_gemm(ccsd_ctx* h, Alloc& al, GemmSpec s, size_t& work_need) {
         snprintf(g_errbuf, sizeof g_errbuf, "plan %zu out of bounds", h->gemms.size());
         return CCSD_ERR_INVALID;
     }
+    if (!s.nchunk_b.empty()) {
+        if ((long long)s.nchunk_b.size() != s.nbatch) return CCSD_ERR_INVALID;
+        for (int x : s.nchunk_b) if (x < 0 || x > s.nchunk) return CCSD_ERR_INVALID;
+    }
+    if (!s.offC2.empty()) {
+        if ((long long)s.offC2.size() != s.nbatch || (int)s.colC2.size() != s.N) return CCSD_ERR_INVALID;
+        const std::pair<long long, long long> s2 = span(s.offC2, s.rowC, s.colC2);
+        if (s2.first < 0 || s2.second >= h->bufsize[s.c]) return CCSD_ERR_INVALID;
+    }
     GemmPlan p{};
     p.a = s.a; p.b = s.b; p.c = s.c;
     if (s.N >= 48) p.cfg = CFG_64x64;
@@ -280,10 +303,14 @@ int finalize_gemm(ccsd_ctx* h, Alloc& al, GemmSpec s, size_t& work_need) {
     g.rowA = upload(al, s.rowA, h->st); g.colA = upload(al, s.colA, h->st);
     g.rowB = upload(al, s.rowB, h->st); g.colB = upload(al, s.colB, h->st);
     g.rowC = upload(al, s.rowC, h->st); g.colC = upload(al, s.colC, h->st);
+    g.nchunk_b = s.nchunk_b.empty() ? nullptr : upload(al, s.nchunk_b, h->st);
+    g.offC2 = s.offC2.empty() ? nullptr : upload(al, s.offC2, h->st);
+    g.colC2 = s.colC2.empty() ? nullptr : upload(al, s.colC2, h->st);
     if (al.err) return al.err;
     h->gemms.push_back(p);
-    h->seq.push_back({0, (int)h->gemms.size() - 1, h->cur_name,
-                      8.0 * s.M * (double)s.N * s.K * s.nchunk * s.nbatch, 0.0});
+    double chunks = (double)s.nchunk * s.nbatch;
+    if (!s.nchunk_b.empty()) { chunks = 0.0; for (int x : s.nchunk_b) chunks += x; }
+    h->seq.push_back({0, (int)h->gemms.size() - 1, h->cur_name, 8.0 * s.M * (double)s.N * s.K * chunks, 0.0});
     return 0;
 }
 
@@ -702,19 +729,44 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{(int)oo, oo}, {o, 1}}); s.colC = tab({{o, o}});
         if ((rc = G(s))) return rc;
     }
-    {
-        GemmSpec s; s.a = B_OOVV; s.b = B_TAU; s.c = B_WHH; s.ar = 0.5;
-        s.M = (int)oo; s.N = (int)oo; s.K = (int)vv; s.nbatch = N3; s.nchunk = N;
-        for (int km = 0; km < N; ++km) for (int kn = 0; kn < N; ++kn) for (int ki = 0; ki < N; ++ki) {
-            const int kj = kg.k4(km, kn, ki);
-            for (int ke = 0; ke < N; ++ke) { s.offA.push_back(blk(S2, km, kn, ke)); s.offB.push_back(blk(S2, ki, kj, ke)); }
-            s.offC.push_back(blk(Soooo, km, kn, ki));
+    // packed index pairs for the hole-hole contractions
+    std::vector<int> vv_full = tab({{(int)vv, 1}}), vv_lt, oo_full = tab({{(int)oo, 1}}), oo_lt;
+    for (int x = 0; x < v; ++x) for (int y = x + 1; y < v; ++y) vv_lt.push_back(x * v + y);
+    for (int x = 0; x < o; ++x) for (int y = x + 1; y < o; ++y) oo_lt.push_back(x * o + y);
+    auto swap_pair = [](int x, int n) { return (x % n) * n + x / n; };
+    {   // Whh += 1/2 sum tau_ij^ef <mn||ef>, packed by antisymmetry in (e ke, f kf) and
+        // (m km, n kn): ke < kf with all e f plus ke = kf with e < f (factor 2), and only
+        // km < kn (all m n) or km = kn (m < n), mirrored as Whh(nm) = -Whh(mn).
+        for (int diag_mn = 0; diag_mn < 2; ++diag_mn) for (int diag_ef = 0; diag_ef < 2; ++diag_ef) {
+            GemmSpec s; s.a = B_TAU; s.b = B_OOVV; s.c = B_WHH; s.ar = 1.0;
+            const std::vector<int>& kc = diag_ef ? vv_lt : vv_full;
+            const std::vector<int>& nc = diag_mn ? oo_lt : oo_full;
+            s.M = (int)oo; s.N = (int)nc.size(); s.K = (int)kc.size(); s.nchunk = N; s.nbatch = 0;
+            for (int km = 0; km < N; ++km) for (int kn = km; kn < N; ++kn) {
+                if ((km == kn) != (diag_mn == 1)) continue;
+                const int S = kg.k4(km, kn, 0);
+                std::vector<int> kes;
+                for (int ke = 0; ke < N; ++ke) { const int kf = kg.k4(S, 0, ke); if (diag_ef ? ke == kf : ke < kf) kes.push_back(ke); }
+                if (kes.empty() || nc.empty() || kc.empty()) continue;
+                for (int ki = 0; ki < N; ++ki) {
+                    const int kj = kg.k4(km, kn, ki);
+                    for (int c = 0; c < N; ++c) {
+                        const int ke = kes[std::min<size_t>(c, kes.size() - 1)];
+                        s.offA.push_back(blk(S2, ki, kj, ke)); s.offB.push_back(blk(S2, km, kn, ke));
+                    }
+                    s.nchunk_b.push_back((int)kes.size());
+                    s.offC.push_back(blk(Soooo, km, kn, ki));
+                    s.offC2.push_back(blk(Soooo, kn, km, ki));
+                    ++s.nbatch;
+                }
+            }
+            s.rowA = tab({{(int)oo, vv}}); s.colA = kc;
+            s.rowB = kc; for (int x : nc) s.colB.push_back(x * (int)vv);
+            s.rowC = tab({{(int)oo, 1}});
+            for (int x : nc) { s.colC.push_back(x * (int)oo); s.colC2.push_back(swap_pair(x, o) * (int)oo); }
+            if ((rc = G(s))) return rc;
+            if (mixed) h->seq.back().mode = 1;
         }
-        s.rowA = tab({{(int)oo, vv}}); s.colA = tab({{(int)vv, 1}});
-        s.rowB = tab({{(int)vv, 1}}); s.colB = tab({{(int)oo, vv}});
-        s.rowC = tab({{(int)oo, oo}}); s.colC = tab({{(int)oo, 1}});
-        if ((rc = G(s))) return rc;
-        if (mixed) h->seq.back().mode = 1;
     }
     if (mixed) {
         // X on tensor cores, one batch per momentum sum S = km + kn = ki + kj:
@@ -743,21 +795,39 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                          tab({{N, Soooo}, {(int)oo, 1}}), 0.5, 3))) return rc;
     }
     h->cur_name = "hole_hole";
-    {   // R2 += 1/2 sum_km tau_{mn}^{ab} Whh_{mnij}
-        GemmSpec s; s.a = B_WHH; s.b = B_TAU; s.c = B_R2; s.ar = 0.5;
-        s.M = (int)oo; s.N = (int)vv; s.K = (int)oo; s.nbatch = N3; s.nchunk = N;
-        for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
-            for (int km = 0; km < N; ++km) {
-                const int kn = kg.k4(ki, kj, km);
-                s.offA.push_back(blk(Soooo, km, kn, ki)); s.offB.push_back(blk(S2, km, kn, ka));
+    {   // R2 += 1/2 sum tau_mn^ab Whh_mnij, packed: (m km) < (n kn) over the sum
+        // (factor 2) and (a ka) < (b kb) on the output with the mirror R2(ba) = -R2(ab).
+        for (int diag_ab = 0; diag_ab < 2; ++diag_ab) for (int diag_mn = 0; diag_mn < 2; ++diag_mn) {
+            GemmSpec s; s.a = B_WHH; s.b = B_TAU; s.c = B_R2; s.ar = 1.0;
+            const std::vector<int>& kc = diag_mn ? oo_lt : oo_full;
+            const std::vector<int>& nc = diag_ab ? vv_lt : vv_full;
+            s.M = (int)oo; s.N = (int)nc.size(); s.K = (int)kc.size(); s.nchunk = N; s.nbatch = 0;
+            for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) {
+                const int S = kg.k4(ki, kj, 0);
+                std::vector<int> kms;
+                for (int km = 0; km < N; ++km) { const int kn = kg.k4(S, 0, km); if (diag_mn ? km == kn : km < kn) kms.push_back(km); }
+                if (kms.empty() || nc.empty() || kc.empty()) continue;
+                for (int ka = 0; ka < N; ++ka) {
+                    const int kb = kg.k4(ki, kj, ka);
+                    if (!(diag_ab ? ka == kb : ka < kb)) continue;
+                    for (int c = 0; c < N; ++c) {
+                        const int km = kms[std::min<size_t>(c, kms.size() - 1)];
+                        const int kn = kg.k4(S, 0, km);
+                        s.offA.push_back(blk(Soooo, km, kn, ki)); s.offB.push_back(blk(S2, km, kn, ka));
+                    }
+                    s.nchunk_b.push_back((int)kms.size());
+                    s.offC.push_back(blk(S2, ki, kj, ka));
+                    s.offC2.push_back(blk(S2, ki, kj, kb));
+                    ++s.nbatch;
+                }
             }
-            s.offC.push_back(blk(S2, ki, kj, ka));
+            s.rowA = tab({{(int)oo, 1}}); for (int x : kc) s.colA.push_back(x * (int)oo);
+            for (int x : kc) s.rowB.push_back(x * (int)vv); s.colB = nc;
+            s.rowC = tab({{(int)oo, vv}}); s.colC = nc;
+            for (int x : nc) s.colC2.push_back(swap_pair(x, v));
+            if ((rc = G(s))) return rc;
+            if (mixed) h->seq.back().mode = 1;
         }
-        s.rowA = tab({{(int)oo, 1}}); s.colA = tab({{(int)oo, oo}});
-        s.rowB = tab({{(int)oo, vv}}); s.colB = tab({{(int)vv, 1}});
-        s.rowC = tab({{(int)oo, vv}}); s.colC = tab({{(int)vv, 1}});
-        if ((rc = G(s))) return rc;
-        if (mixed) h->seq.back().mode = 1;
     }
     if (mixed) {
         // R2 += 1/2 tau_mn^ab Whh_mnij on tensor cores, one batch per S = ki + kj:
@@ -789,10 +859,12 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     // ladder: Wab = <ab||ef> - P(ab) t_r^b <a r||e f>
     const size_t ladder_w_first = h->seq.size();
     if ((rc = add_copy(h, B_WAB, B_VVVV, (long long)N3 * Svvvv, 0))) return rc;
+    // (only the blocks ka <= kb: the packed ladder below reads no others)
+    const int NP = N * (N + 1) / 2;
     {   // + sum_r t_r^b(kb) ovvv[kb,ka,ke](r,a,e,f)
         GemmSpec s; s.a = B_OVVV; s.b = B_T1; s.c = B_WAB;
-        s.M = (int)(vv * v); s.N = v; s.K = o; s.nbatch = N3; s.nchunk = 1;
-        for (int ka = 0; ka < N; ++ka) for (int kb = 0; kb < N; ++kb) for (int ke = 0; ke < N; ++ke) {
+        s.M = (int)(vv * v); s.N = v; s.K = o; s.nbatch = NP * N; s.nchunk = 1;
+        for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) for (int ke = 0; ke < N; ++ke) {
             s.offA.push_back(blk(Sovvv, kb, ka, ke)); s.offB.push_back(kb * ov); s.offC.push_back(blk(Svvvv, ka, kb, ke));
         }
         s.rowA = tab({{(int)(vv * v), 1}}); s.colA = tab({{o, vv * v}});
@@ -802,8 +874,8 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     }
     {   // - sum_r t_r^a(ka) ovvv[ka,kb,ke](r,b,e,f)
         GemmSpec s; s.a = B_OVVV; s.b = B_T1; s.c = B_WAB; s.ar = -1.0;
-        s.M = (int)(vv * v); s.N = v; s.K = o; s.nbatch = N3; s.nchunk = 1;
-        for (int ka = 0; ka < N; ++ka) for (int kb = 0; kb < N; ++kb) for (int ke = 0; ke < N; ++ke) {
+        s.M = (int)(vv * v); s.N = v; s.K = o; s.nbatch = NP * N; s.nchunk = 1;
+        for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) for (int ke = 0; ke < N; ++ke) {
             s.offA.push_back(blk(Sovvv, ka, kb, ke)); s.offB.push_back(ka * ov); s.offC.push_back(blk(Svvvv, ka, kb, ke));
         }
         s.rowA = tab({{(int)(vv * v), 1}}); s.colA = tab({{o, vv * v}});
@@ -814,19 +886,60 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     if (mixed)   // the tensor-core path forms W' inside its operand embedding
         for (size_t i = ladder_w_first; i < h->seq.size(); ++i) h->seq[i].mode = 1;
     h->cur_name = "ladder";
-    {   // R2 += 1/2 sum_ke tau_ij^ef Wab^{abef}; batches grouped by (ka, kb) for L2 reuse
-        GemmSpec s; s.a = B_TAU; s.b = B_WAB; s.c = B_R2; s.ar = 0.5;
-        s.M = (int)oo; s.N = (int)vv; s.K = (int)vv; s.nbatch = N3; s.nchunk = N;
-        for (int ka = 0; ka < N; ++ka) for (int kb = 0; kb < N; ++kb) for (int ki = 0; ki < N; ++ki) {
-            const int kj = kg.k4(ka, kb, ki);
-            for (int ke = 0; ke < N; ++ke) { s.offA.push_back(blk(S2, ki, kj, ke)); s.offB.push_back(blk(Svvvv, ka, kb, ke)); }
-            s.offC.push_back(blk(S2, ki, kj, ka));
+    {   // R2 += 1/2 sum_{ke,e,f} tau_ij^ef W'^abef, packed by antisymmetry:
+        // tau and W' change sign under (e ke) <-> (f kf), so the half sum over ordered
+        // pairs is the full sum over (ke < kf, all e f) plus (ke = kf, e < f); W' also
+        // changes sign under (a ka) <-> (b kb), so only (ka < kb, all a b) and
+        // (ka = kb, a < b) are computed and the mirror R2(ba) = -R2(ab) is written by
+        // the same thread.  Four launches: {ka < kb, ka = kb} x {ke < kf, ke = kf}.
+        std::vector<int> pairs_full = tab({{(int)vv, 1}}), pairs_lt, pairs_lt_T;
+        for (int x = 0; x < v; ++x) for (int y = x + 1; y < v; ++y) { pairs_lt.push_back(x * v + y); pairs_lt_T.push_back(y * v + x); }
+        std::vector<int> swapped;                       // (a,b) -> (b,a) for every a, b
+        for (int x = 0; x < v; ++x) for (int y = 0; y < v; ++y) swapped.push_back(y * v + x);
+        for (int diag_ab = 0; diag_ab < 2; ++diag_ab) {
+            for (int diag_ef = 0; diag_ef < 2; ++diag_ef) {
+                GemmSpec s; s.a = B_TAU; s.b = B_WAB; s.c = B_R2; s.ar = 1.0;
+                const std::vector<int>& ncols = diag_ab ? pairs_lt : pairs_full;
+                const std::vector<int>& kcols = diag_ef ? pairs_lt : pairs_full;
+                s.M = (int)oo; s.N = (int)ncols.size(); s.K = (int)kcols.size(); s.nchunk = N;
+                s.nbatch = 0;
+                for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) {
+                    if ((ka == kb) != (diag_ab == 1)) continue;
+                    const int S = kg.k4(ka, kb, 0);
+                    std::vector<int> kes;
+                    for (int ke = 0; ke < N; ++ke) {
+                        const int kf = kg.k4(S, 0, ke);
+                        if (diag_ef ? (ke == kf) : (ke < kf)) kes.push_back(ke);
+                    }
+                    if (kes.empty() || (v < 2 && (diag_ab || diag_ef))) continue;
+                    for (int ki = 0; ki < N; ++ki) {
+                        const int kj = kg.k4(ka, kb, ki);
+                        for (int c = 0; c < N; ++c) {
+                            const int ke = kes[std::min<size_t>(c, kes.size() - 1)];
+                            s.offA.push_back(blk(S2, ki, kj, ke)); s.offB.push_back(blk(Svvvv, ka, kb, ke));
+                        }
+                        s.nchunk_b.push_back((int)kes.size());
+                        s.offC.push_back(blk(S2, ki, kj, ka));
+                        s.offC2.push_back(blk(S2, ki, kj, kb));
+                        ++s.nbatch;
+                    }
+                }
+                if (s.nbatch == 0) { if ((rc = G(s))) return rc; if (mixed) h->seq.back().mode = 1; continue; }
+                s.rowA = tab({{(int)oo, vv}}); s.colA = kcols;
+                s.rowB = kcols; s.colB.clear();
+                for (int x : ncols) s.colB.push_back(x * (int)vv);
+                s.rowC = tab({{(int)oo, vv}}); s.colC = ncols;
+                s.colC2.clear();
+                for (int x : ncols) s.colC2.push_back(swapped[x]);
+                if (diag_ab) {
+                    // the mirror of (ka = kb, a < b) is (b, a) in the same block
+                    s.colC2.clear();
+                    for (int x : ncols) s.colC2.push_back((x % v) * v + x / v);
+                }
+                if ((rc = G(s))) return rc;
+                if (mixed) h->seq.back().mode = 1;
+            }
         }
-        s.rowA = tab({{(int)oo, vv}}); s.colA = tab({{(int)vv, 1}});
-        s.rowB = tab({{(int)vv, 1}}); s.colB = tab({{(int)vv, vv}});
-        s.rowC = tab({{(int)oo, vv}}); s.colC = tab({{(int)vv, 1}});
-        if ((rc = G(s))) return rc;
-        if (mixed) h->seq.back().mode = 1;
     }
     if (mixed) {
         // tensor-core ladder: A' = tau in [S = ki + kj][ke][ki](ij)(ef), B' = embedded W' [ka][kb][ke]
@@ -1087,6 +1200,7 @@ dim3 ew_grid(long long n) {
 }
 
 int launch_gemm(ccsd_ctx* h, GemmPlan& p) {
+    if (p.blocks == 0) return 0;
     GemmArgs g = p.args;
     g.A = h->buf[p.a]; g.B = h->buf[p.b]; g.C = h->buf[p.c]; g.work = h->work;
     g.A32 = h->fp32 ? h->shadow[p.a] : nullptr;
@@ -1327,6 +1441,7 @@ int batch_build_groups(ccsd_batch* B, int fp32, const std::vector<int>& cfgs) {
             const int ns = std::max(1, std::min(want, a.nchunk));
             a.chunks_per_split = (a.nchunk + ns - 1) / ns;
             a.nsplit = (a.nchunk + a.chunks_per_split - 1) / a.chunks_per_split;
+            if (a.nbatch == 0) a.nsplit = 1;
             if (a.nsplit > 1) {
                 const size_t need = (size_t)a.nsplit * a.nbatch * a.M * a.N;
                 if (need > h->work_elems) {

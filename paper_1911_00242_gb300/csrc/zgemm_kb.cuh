@@ -35,6 +35,9 @@ struct GemmArgs {
     const float2* A32; const float2* B32;   // complex64 copies of A / B, used instead when set
     double2* C;       const long long* offC; const int* rowC; const int* colC;
     double2* work;    // split partials [nsplit][nbatch][M*N] when nsplit > 1
+    const int* nchunk_b;   // per-batch chunk count (<= nchunk), or null for nchunk everywhere
+    // antisymmetric mirror: each result is also subtracted at offC2[b] + rowC[m] + colC2[n]
+    const long long* offC2; const int* colC2;
     int M, N, K, nbatch, nchunk, nsplit, chunks_per_split;
     int conjA, conjB, accumulate;
     double alpha_re, alpha_im;
@@ -69,7 +72,8 @@ __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long lon
     const T sb = g.conjB ? T(-1) : T(1);
     const int c_begin = split * g.chunks_per_split;
     int c_end = c_begin + g.chunks_per_split;
-    if (c_end > g.nchunk) c_end = g.nchunk;
+    const int nch = g.nchunk_b ? g.nchunk_b[b] : g.nchunk;
+    if (c_end > nch) c_end = nch;
 
     for (int c = c_begin; c < c_end; ++c) {
         const long long oa = g.offA[b * g.nchunk + c];
@@ -147,6 +151,10 @@ __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long lon
                 const double im = g.alpha_re * xi + g.alpha_im * xr;
                 if (g.accumulate) { double2 o = *p; o.x += re; o.y += im; *p = o; }
                 else *p = make_double2(re, im);
+                if (g.offC2) {
+                    double2* q = g.C + g.offC2[b] + (long long)g.rowC[m] + g.colC2[n];
+                    double2 o = *q; o.x -= re; o.y -= im; *q = o;
+                }
             }
         }
 }
@@ -208,6 +216,10 @@ __global__ void zgemm_split_reduce(const GemmArgs g)
         const double i2 = g.alpha_re * im + g.alpha_im * re;
         if (g.accumulate) { double2 o = *p; o.x += r2; o.y += i2; *p = o; }
         else *p = make_double2(r2, i2);
+        if (g.offC2) {
+            double2* q = g.C + g.offC2[b] + (long long)g.rowC[m] + g.colC2[n];
+            double2 o = *q; o.x -= r2; o.y -= i2; *q = o;
+        }
     }
 }
 
