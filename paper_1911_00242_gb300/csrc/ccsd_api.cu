@@ -104,6 +104,10 @@ struct WPlan {          // fused W' formation + embedding for one k_a slab of th
     WprimeArgs a;       // vvvv / ovvv / t1 resolved at launch
 };
 
+struct WListPlan {      // fused W' formation + embedding for listed blocks and index pairs
+    WprimeListArgs a;
+};
+
 struct TcPlan {
     CUtensorMap mA_big, mA_small, mB_big, mB_small;
     TcArgs a;           // a.C resolved at launch
@@ -152,6 +156,7 @@ struct ccsd_ctx {
     std::vector<EmbedPlan> embeds;
     std::vector<TcPlan> tcs;
     std::vector<WPlan> wplans;
+    std::vector<WListPlan> wlists;
     std::vector<int> const_embeds;   // embeds of constant inputs, run once at creation
     int* tc_err = nullptr;
     // tracing: CUDA events around every step of the residual plan
@@ -420,7 +425,9 @@ int add_embed(ccsd_ctx* h, Alloc& al, int src, const TcBuf& dst, int mode, int R
 
 int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M, int Nr, int nbatch, int nchunk,
            const std::vector<int>& rowA, const std::vector<int>& rowB, const std::vector<long long>& offC,
-           const std::vector<int>& colC, double alpha, int nterms) {
+           const std::vector<int>& colC, double alpha, int nterms,
+           const std::vector<int>& nchunk_b = {}, const std::vector<long long>& offC2 = {},
+           const std::vector<int>& colC2 = {}) {
     if (A.kpad != B.kpad || A.kpad % TC_BK) return CCSD_ERR_INVALID;
     if ((long long)rowA.size() != (long long)nbatch * nchunk || (long long)rowB.size() != (long long)nbatch * nchunk ||
         (long long)offC.size() != (long long)nbatch * M || (int)colC.size() * 2 != Nr) return CCSD_ERR_INVALID;
@@ -429,11 +436,24 @@ int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M,
     const long long chi = *std::max_element(offC.begin(), offC.end()) + *std::max_element(colC.begin(), colC.end());
     const long long clo = *std::min_element(offC.begin(), offC.end()) + *std::min_element(colC.begin(), colC.end());
     if (clo < 0 || chi >= h->bufsize[c]) return CCSD_ERR_INVALID;
+    if (!nchunk_b.empty()) {
+        if ((long long)nchunk_b.size() != nbatch) return CCSD_ERR_INVALID;
+        for (int x : nchunk_b) if (x < 0 || x > nchunk) return CCSD_ERR_INVALID;
+    }
+    if (!offC2.empty()) {
+        if (offC2.size() != offC.size() || colC2.size() != colC.size()) return CCSD_ERR_INVALID;
+        const long long h2 = *std::max_element(offC2.begin(), offC2.end()) + *std::max_element(colC2.begin(), colC2.end());
+        const long long l2 = *std::min_element(offC2.begin(), offC2.end()) + *std::min_element(colC2.begin(), colC2.end());
+        if (l2 < 0 || h2 >= h->bufsize[c]) return CCSD_ERR_INVALID;
+    }
     TcPlan t{};
     t.c = c;
     TcArgs& a = t.a;
     a.rowA = upload(al, rowA, h->st); a.rowB = upload(al, rowB, h->st);
     a.offC = upload(al, offC, h->st); a.colC = upload(al, colC, h->st);
+    a.nchunk_b = nchunk_b.empty() ? nullptr : upload(al, nchunk_b, h->st);
+    a.offC2 = offC2.empty() ? nullptr : upload(al, offC2, h->st);
+    a.colC2 = colC2.empty() ? nullptr : upload(al, colC2, h->st);
     if (al.err) return al.err;
     a.err = h->tc_err;
     a.M = M; a.Nr = Nr; a.nchunk = nchunk; a.kstages = A.kpad / TC_BK; a.nterms = nterms;
@@ -447,8 +467,9 @@ int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M,
             return rc;
     }
     h->tcs.push_back(t);
-    Step st{6, (int)h->tcs.size() - 1, h->cur_name,
-            8.0 * (double)M * (Nr / 2) * (A.kpad / 2) * nchunk * nbatch, 0.0};
+    double chunks = (double)nchunk * nbatch;
+    if (!nchunk_b.empty()) { chunks = 0.0; for (int x : nchunk_b) chunks += x; }
+    Step st{6, (int)h->tcs.size() - 1, h->cur_name, 8.0 * (double)M * (Nr / 2) * (A.kpad / 2) * chunks, 0.0};
     st.mode = 2;
     h->seq.push_back(st);
     return 0;
@@ -474,8 +495,10 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     int rc;
     auto G = [&](GemmSpec& s) { return finalize_gemm(h, al, s, work_need); };
     const bool mixed = h->cfg.precision == CCSD_MIXED;
-    TcBuf tc_la{}, tc_lb{}, tc_ra{}, tc_rb{}, tc_b1{}, tc_ha{}, tc_hb{}, tc_h2a{}, tc_h2b{};
+    TcBuf tc_la{}, tc_lb{}, tc_ra{}, tc_rb{}, tc_b1{}, tc_ha{}, tc_hb{}, tc_h2a{}, tc_h2b{}, tc_lap{}, tc_lbp{};
     int ladder_nka = 1;
+    bool ladder_packed = false;
+    long long tc_lb_used = 0, tc_lbp_used = 0;   // rows handed out in the packed B buffers
     if (mixed) {
         const int kpl = (int)((2 * vv + TC_BK - 1) / TC_BK * TC_BK);
         const int kpr = (int)((2 * ov + TC_BK - 1) / TC_BK * TC_BK);
@@ -491,13 +514,37 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                 to_c64_kernel<<<ew_grid(h->bufsize[bi]), 256, 0, h->st>>>(h->shadow[bi], h->buf[bi], h->bufsize[bi]);
         }
         if (!al.dry && cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st) != cudaSuccess) return CCSD_ERR_CUDA;
-        // ladder k_a slab: enough CTAs per launch for ~4 waves, B operand within ~8 GB
+        // ladder: antisymmetry-packed operands when they fit in ~12 GB, else unpacked k_a
+        // slabs (enough CTAs per launch for ~4 waves, B operand within ~8 GB)
+        const long long nlt = (long long)v * (v - 1) / 2;
+        const int kplp = (int)((2 * nlt + TC_BK - 1) / TC_BK * TC_BK);
+        long long off_blocks = 0, diag_blocks_full = 0, diag_blocks_lt = 0;   // B blocks per kind
+        for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) {
+            const int S = kg.k4(ka, kb, 0);
+            for (int ke = 0; ke < N; ++ke) {
+                const int kf = kg.k4(S, 0, ke);
+                if (ke < kf) { if (ka < kb) off_blocks += 1; else diag_blocks_full += 1; }
+                else if (ke == kf) { if (ka < kb) diag_blocks_lt += 1; else diag_blocks_lt += 1; }
+            }
+        }
+        // rows: off-diagonal ef -> full (ab or a<b) x 2 rows; diagonal ef -> same
+        const long long rows_full = off_blocks * 2 * vv + diag_blocks_full * 2 * nlt;
+        long long rows_lt = 0;
+        for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) {
+            const int S = kg.k4(ka, kb, 0);
+            for (int ke = 0; ke < N; ++ke) if (ke == kg.k4(S, 0, ke)) rows_lt += 2 * (ka < kb ? vv : nlt);
+        }
+        const long long packed_bytes = (rows_full * kpl + rows_lt * kplp) * 4LL * 2;
+        ladder_packed = v >= 2 && packed_bytes <= (12LL << 30);
         const long long per_ka_ctas = (long long)N * ((N * oo + TC_BM - 1) / TC_BM) * ((2 * vv + TC_BN - 1) / TC_BN);
         const long long per_ka_bytes = (long long)N * N * 2 * vv * kpl * 4 * 2;
         ladder_nka = (int)std::min<long long>(N, std::max<long long>(1, (4 * kSMs + per_ka_ctas - 1) / per_ka_ctas));
         while (ladder_nka > 1 && ladder_nka * per_ka_bytes > (8LL << 30)) --ladder_nka;
+        if (ladder_packed &&
+            ((rc = tc_alloc(h, al, tc_lap, N3l * oo, kplp)) || (rc = tc_alloc(h, al, tc_lbp, std::max(rows_lt, 1LL), kplp))))
+            return rc;
         if ((rc = tc_alloc(h, al, tc_la, N3l * oo, kpl)) ||
-            (rc = tc_alloc(h, al, tc_lb, (long long)ladder_nka * N * N * 2 * vv, kpl)) ||
+            (rc = tc_alloc(h, al, tc_lb, ladder_packed ? std::max(rows_full, 1LL) : (long long)ladder_nka * N * N * 2 * vv, kpl)) ||
             (rc = tc_alloc(h, al, tc_ra, N3l * ov, kpr)) || (rc = tc_alloc(h, al, tc_rb, N3l * 2 * ov, kpr)) ||
             (rc = tc_alloc(h, al, tc_b1, N3l * 2 * ov, kpr)))
             return rc;
@@ -943,13 +990,88 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     }
     if (mixed) {
         // tensor-core ladder: A' = tau in [S = ki + kj][ke][ki](ij)(ef), B' = embedded W' [ka][kb][ke]
-        std::vector<long long> so; std::vector<int> sr, sc;
+        std::vector<long long> so_lad;
         for (int S = 0; S < N; ++S) for (int ke = 0; ke < N; ++ke) for (int ki = 0; ki < N; ++ki)
-            so.push_back(blk(S2, ki, kg.k4(S, 0, ki), ke));
-        if ((rc = add_embed(h, al, B_TAU, tc_la, 0, (int)oo, (int)vv, so, tab({{(int)oo, vv}}), tab({{(int)vv, 1}}), false))) return rc;
-        // k_a slabs: W' for the slab is formed straight into the B operand, then its GEMM runs
+            so_lad.push_back(blk(S2, ki, kg.k4(S, 0, ki), ke));
+        if ((rc = add_embed(h, al, B_TAU, tc_la, 0, (int)oo, (int)vv, so_lad, tab({{(int)oo, vv}}), tab({{(int)vv, 1}}), false))) return rc;
         const int M = (int)(N * oo);
-        for (int ka0 = 0; ka0 < N; ka0 += ladder_nka) {
+        if (ladder_packed) {
+            // antisymmetry-packed tensor-core ladder: (ka < kb | ka = kb, a < b) outputs with
+            // mirror, (ke < kf | ke = kf, e < f) contractions; four launches, W' formed
+            // straight into each launch's B operand for exactly the blocks it reads
+            std::vector<int> full_vv = tab({{(int)vv, 1}}), lt_vv;
+            for (int x = 0; x < v; ++x) for (int y = x + 1; y < v; ++y) lt_vv.push_back(x * v + y);
+            if ((rc = add_embed(h, al, B_TAU, tc_lap, 0, (int)oo, (int)lt_vv.size(), so_lad, tab({{(int)oo, vv}}), lt_vv, false)))
+                return rc;
+            for (int diag_ab = 0; diag_ab < 2; ++diag_ab) for (int diag_ef = 0; diag_ef < 2; ++diag_ef) {
+                const std::vector<int>& abl = diag_ab ? lt_vv : full_vv;
+                const std::vector<int>& efl = diag_ef ? lt_vv : full_vv;
+                if (abl.empty() || efl.empty()) continue;
+                const TcBuf& A = diag_ef ? tc_lap : tc_la;
+                TcBuf B = diag_ef ? tc_lbp : tc_lb;
+                std::vector<int> blk3, ra, rb, cc, cc2, cnt;
+                std::vector<long long> oc, oc2;
+                int nb = 0, nchmax = 0;
+                std::vector<std::pair<int, int>> batches;
+                std::vector<std::vector<int>> chunks;
+                for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) {
+                    if ((ka == kb) != (diag_ab == 1)) continue;
+                    const int S = kg.k4(ka, kb, 0);
+                    std::vector<int> kes;
+                    for (int ke = 0; ke < N; ++ke) { const int kf = kg.k4(S, 0, ke); if (diag_ef ? ke == kf : ke < kf) kes.push_back(ke); }
+                    if (kes.empty()) continue;
+                    batches.push_back({ka, kb});
+                    chunks.push_back(kes);
+                    nchmax = std::max<int>(nchmax, (int)kes.size());
+                }
+                if (batches.empty()) continue;
+                // rows of this launch's blocks start at first_row of its B buffer; block j of
+                // the launch occupies rows first_row + 2 nab j .. + 2 nab
+                const long long first_row = diag_ef ? tc_lbp_used : tc_lb_used;
+                const long long rows_per_block = 2LL * (long long)abl.size();
+                int used = 0;
+                for (size_t bb = 0; bb < batches.size(); ++bb) {
+                    const int ka = batches[bb].first, kb = batches[bb].second;
+                    const int S = kg.k4(ka, kb, 0);
+                    const std::vector<int>& kes = chunks[bb];
+                    for (int c = 0; c < nchmax; ++c) {
+                        const int cc_ = std::min<int>(c, (int)kes.size() - 1);
+                        ra.push_back((int)((((long long)S * N + kes[cc_]) * N) * oo));
+                        rb.push_back((int)(first_row + (long long)(used + cc_) * rows_per_block));
+                    }
+                    for (int ke : kes) { blk3.push_back(ka); blk3.push_back(kb); blk3.push_back(ke); }
+                    used += (int)kes.size();
+                    cnt.push_back((int)kes.size());
+                    for (int ki = 0; ki < N; ++ki)
+                        for (int ij = 0; ij < (int)oo; ++ij) {
+                            oc.push_back(blk(S2, ki, kg.k4(S, 0, ki), ka) + ij * vv);
+                            oc2.push_back(blk(S2, ki, kg.k4(S, 0, ki), kb) + ij * vv);
+                        }
+                    ++nb;
+                }
+                if (first_row + (long long)used * rows_per_block > B.rows) return CCSD_ERR_INVALID;
+                if (diag_ef) tc_lbp_used = first_row + (long long)used * rows_per_block;
+                else tc_lb_used = first_row + (long long)used * rows_per_block;
+                WListPlan wl{};
+                wl.a.big = B.big + (size_t)first_row * B.kpad;
+                wl.a.small = B.small + (size_t)first_row * B.kpad;
+                wl.a.blk = upload(al, blk3, h->st);
+                wl.a.abl = upload(al, abl, h->st);
+                wl.a.efl = upload(al, efl, h->st);
+                if (al.err) return al.err;
+                wl.a.nblk = (int)(blk3.size() / 3); wl.a.nab = (int)abl.size(); wl.a.nef = (int)efl.size();
+                wl.a.N = N; wl.a.o = o; wl.a.v = v; wl.a.Kpad = B.kpad;
+                h->wlists.push_back(wl);
+                Step st{10, (int)h->wlists.size() - 1, "ladder_W", 0.0, 40.0 * (double)wl.a.nblk * wl.a.nab * wl.a.nef};
+                st.mode = 2;
+                h->seq.push_back(st);
+                for (int x : abl) { cc.push_back(x); cc2.push_back((x % v) * v + x / v); }
+                if ((rc = add_tc(h, al, A, B, B_R2, M, (int)(2 * abl.size()), nb, nchmax, ra, rb, oc, cc, 1.0, 3,
+                                 cnt, oc2, cc2))) return rc;
+            }
+        }
+        // k_a slabs: W' for the slab is formed straight into the B operand, then its GEMM runs
+        for (int ka0 = 0; ka0 < N && !ladder_packed; ka0 += ladder_nka) {
             const int nka = std::min(ladder_nka, N - ka0);
             WPlan wp{};
             wp.a.big = tc_lb.big; wp.a.small = tc_lb.small;
@@ -1303,6 +1425,13 @@ void launch_step(ccsd_ctx* h, size_t si) {
             case 7:
                 cudaMemsetAsync(h->buf[s.idx], 0, (size_t)h->bufsize[s.idx] * 16, h->st);
                 break;
+            case 10: {
+                WprimeListArgs a = h->wlists[s.idx].a;
+                a.vvvv = h->shadow[B_VVVV]; a.ovvv = h->shadow[B_OVVV]; a.t1 = h->shadow[B_T1];
+                wprime_list_kernel<<<ew_grid((long long)a.nblk * a.nab * a.nef), 256, 0, h->st>>>(a);
+                ++h->launches;
+                break;
+            }
             case 9:   // refresh the complex64 copy of an amplitude buffer
                 to_c64_kernel<<<ew_grid(h->bufsize[s.idx]), 256, 0, h->st>>>(h->shadow[s.idx], h->buf[s.idx],
                                                                              h->bufsize[s.idx]);

@@ -58,6 +58,9 @@ struct TcArgs {
     int nterms;               // 1: A_big*B_big; 3: + A_big*B_small + A_small*B_big
     int tiles_m, tiles_n;
     double alpha_re, alpha_im;
+    const int* nchunk_b;      // per-batch chunk count (<= nchunk) or null
+    const long long* offC2;   // antisymmetric mirror: c is also subtracted at offC2[b*M+m] + colC2[n]
+    const int* colC2;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -164,7 +167,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
     const uint32_t tmem = *tmem_slot;
 
     const int per_chunk = g.nterms * g.kstages;
-    const int total = g.nchunk * per_chunk;
+    const int total = (g.nchunk_b ? g.nchunk_b[b] : g.nchunk) * per_chunk;
     int issued = 0;
 
     if (warp == 0 && lane == 0) {
@@ -231,6 +234,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
         const int row = m0 + warp * 32 + lane;
         const bool rvalid = row < g.M;
         const long long rbase = rvalid ? g.offC[b * g.M + row] : 0;
+        const long long rbase2 = (rvalid && g.offC2) ? g.offC2[b * g.M + row] : 0;
 #pragma unroll 1
         for (int c0 = 0; c0 < TC_BN; c0 += 32) {
             uint32_t v[32];
@@ -253,10 +257,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
                         const double xr = (double)__uint_as_float(v[2 * q]);
                         const double xi = (double)__uint_as_float(v[2 * q + 1]);
                         double2* p = g.C + rbase + g.colC[nr >> 1];
+                        const double yr = g.alpha_re * xr - g.alpha_im * xi;
+                        const double yi = g.alpha_re * xi + g.alpha_im * xr;
                         double2 o = *p;
-                        o.x += g.alpha_re * xr - g.alpha_im * xi;
-                        o.y += g.alpha_re * xi + g.alpha_im * xr;
+                        o.x += yr; o.y += yi;
                         *p = o;
+                        if (g.offC2) {
+                            double2* q = g.C + rbase2 + g.colC2[nr >> 1];
+                            double2 u = *q;
+                            u.x -= yr; u.y -= yi;
+                            *q = u;
+                        }
                     }
                 }
             }
@@ -417,6 +428,61 @@ __global__ void to_c64_kernel(float2* __restrict__ dst, const double2* __restric
          e += (long long)gridDim.x * blockDim.x) {
         const double2 z = src[e];
         dst[e] = make_float2((float)z.x, (float)z.y);
+    }
+}
+
+}  // namespace ccsdk
+
+namespace ccsdk {
+
+// W' embedding for the antisymmetry-packed tensor-core ladder: output block bi
+// is the momentum triple (ka, kb, ke) = blk[3 bi .. 3 bi + 2]; its rows are the
+// listed (a, b) pairs (2 per pair, B-side embedding) and its columns the listed
+// (e, f) pairs:  rows bi 2 nab + 2 ai + s, columns 2 ei + r.
+struct WprimeListArgs {
+    const float2* vvvv; const float2* ovvv; const float2* t1;
+    float* big; float* small;
+    const int* blk; const int* abl; const int* efl;
+    int nblk, nab, nef, N, o, v, Kpad;
+};
+
+__global__ void wprime_list_kernel(const WprimeListArgs w)
+{
+    const int N = w.N, o = w.o, v = w.v;
+    const long long vv = (long long)v * v, v4 = vv * vv, ov3 = (long long)o * v * vv;
+    const long long per = (long long)w.nab * w.nef;
+    const long long total = (long long)w.nblk * per;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+         x += (long long)gridDim.x * blockDim.x) {
+        const long long bi = x / per;
+        const int r0 = (int)(x % per);
+        const int ai = r0 / w.nef, ei = r0 % w.nef;
+        const int ka = w.blk[3 * bi], kb = w.blk[3 * bi + 1], ke = w.blk[3 * bi + 2];
+        const int ab = w.abl[ai], ef = w.efl[ei];
+        const int a = ab / v, b = ab % v;
+        const long long blk_ab = ((long long)ka * N + kb) * N + ke;
+        const long long blk_ba = ((long long)kb * N + ka) * N + ke;
+        const float2 g = w.vvvv[blk_ab * v4 + (long long)ab * vv + ef];
+        float sr = 0.f, si = 0.f;
+        for (int r = 0; r < o; ++r) {
+            const float2 tb = w.t1[((long long)kb * o + r) * v + b];
+            const float2 p = w.ovvv[blk_ba * ov3 + ((long long)r * v + a) * vv + ef];
+            sr = fmaf(tb.x, p.x, fmaf(-tb.y, p.y, sr));
+            si = fmaf(tb.x, p.y, fmaf(tb.y, p.x, si));
+            const float2 ta = w.t1[((long long)ka * o + r) * v + a];
+            const float2 q = w.ovvv[blk_ab * ov3 + ((long long)r * v + b) * vv + ef];
+            sr = fmaf(-ta.x, q.x, fmaf(ta.y, q.y, sr));
+            si = fmaf(-ta.x, q.y, fmaf(-ta.y, q.x, si));
+        }
+        float rb, rs, ib, is;
+        split_tf32f(g.x + sr, rb, rs);
+        split_tf32f(g.y + si, ib, is);
+        const long long o0 = (bi * 2 * w.nab + 2LL * ai) * (long long)w.Kpad + 2LL * ei;
+        const long long o1 = o0 + w.Kpad;
+        w.big[o0] = rb; w.big[o0 + 1] = -ib;
+        w.big[o1] = ib; w.big[o1 + 1] = rb;
+        w.small[o0] = rs; w.small[o0 + 1] = -is;
+        w.small[o1] = is; w.small[o1 + 1] = rs;
     }
 }
 
