@@ -47,6 +47,7 @@ import scipy.fft as sfft
 __all__ = [
     "SynthSpec", "CONFIGS", "spec_for", "batch_specs", "generate", "generate_fock",
     "realspace_supercell", "bloch_unitary", "STORED_BLOCKS", "random_amplitudes",
+    "generate_torch", "random_amplitudes_slabs", "random_amplitudes_torch",
 ]
 
 STORED_BLOCKS = ("oooo", "ooov", "oovv", "ovvo", "ovvv", "vvvv")
@@ -386,3 +387,153 @@ def random_amplitudes(spec: SynthSpec, seed: int, scale: float = 0.05):
           - x[KI, KJ, KB].transpose(0, 1, 2, 3, 4, 6, 5)
           + x[KJ, KI, KB].transpose(0, 1, 2, 4, 3, 6, 5)) * 0.5
     return np.ascontiguousarray(t1), np.ascontiguousarray(t2)
+
+
+# ------------------------------------------------ torch evaluation (large grids)
+# generate() holds every Bloch-transformed class tensor and its antisymmetrized
+# copy in host memory, about four times the stored blocks: too much for the
+# 3x3x3 grid with 24 virtuals (vvvv alone is 52 GB as complex64).  The same
+# recipe evaluated with torch (on a GPU, or on the CPU for the tests that pin it
+# to generate()) keeps only the Bloch-transformed classes of one block and its
+# result, and forms the antisymmetrized, Hermitized block row by row.  The raw
+# draws are the same numpy streams (_draw_slice), so the results agree with
+# generate() to the rounding of the FFTs.
+
+def _gk_torch(spec: SynthSpec, cls: str, torch, device):
+    n = {"o": spec.nocc, "v": spec.nvir}
+    N = spec.nk
+    g3 = tuple(spec.grid)
+    out = torch.empty((N, N, N, n[cls[0]], n[cls[1]], n[cls[2]], n[cls[3]]), dtype=torch.complex128,
+                      device=device)
+    fft_dims = (0, 1, 2, 4, 5, 6)
+    ifft_dims = (8, 9, 10)
+    workers = min(n[cls[0]], os.cpu_count() or 1, 16)
+    with ThreadPoolExecutor(max(workers, 1)) as ex:
+        futs = [ex.submit(_draw_slice, spec, cls, p) for p in range(n[cls[0]])]
+        for p, f in enumerate(futs):
+            g = f.result()                                     # (R1, q, R2, r, R3, s)
+            nq, nr, ns = g.shape[1], g.shape[3], g.shape[5]
+            x = torch.from_numpy(g).to(device).reshape(g3 + (nq,) + g3 + (nr,) + g3 + (ns,))
+            del g
+            x = torch.fft.fftn(x, dim=fft_dims)
+            x = torch.fft.ifftn(x, dim=ifft_dims, norm="forward")
+            x = x.reshape(N, nq, N, nr, N, ns)
+            out[:, :, :, p] = x.permute(0, 2, 4, 1, 3, 5)
+            del x
+    out *= 1.0 / N
+    return out
+
+
+def _block_torch(spec: SynthSpec, cls: str, ks, torch, device, out_dtype):
+    """One stored block: A = G - G(bra swap) - G(ket swap) + G(both) in k space,
+    H = (A + A^dagger) / 2 scaled, formed one (kp, kq) row of blocks at a time."""
+    N = spec.nk
+    names = {"g0": cls, "gb": _swap(cls, (1, 0, 2, 3)), "gk": _swap(cls, (0, 1, 3, 2)),
+             "gbk": _swap(cls, (1, 0, 3, 2))}
+    hc = _swap(cls, (2, 3, 0, 1))
+    hnames = {"g0": hc, "gb": _swap(hc, (1, 0, 2, 3)), "gk": _swap(hc, (0, 1, 3, 2)),
+              "gbk": _swap(hc, (1, 0, 3, 2))}
+    cache = {}
+    for c in list(names.values()) + list(hnames.values()):
+        if c not in cache:
+            cache[c] = _gk_torch(spec, c, torch, device)
+    ksd = torch.as_tensor(ks, dtype=torch.long, device=device)
+    ar = torch.arange(N, device=device)
+    sc = 0.5 * _scale(spec)
+
+    def antisym(nm, x, y, z):
+        # A_cls[x, y, z] for index tensors of one shape (ks implied), as in _antisym
+        kz = ksd[x, y, z]
+        a = cache[nm["g0"]][x, y, z] - cache[nm["gb"]][y, x, z].transpose(-4, -3)
+        a = a - cache[nm["gk"]][x, y, kz].transpose(-2, -1)
+        a = a + cache[nm["gbk"]][y, x, kz].transpose(-4, -3).transpose(-2, -1)
+        return a
+
+    shape = cache[cls].shape
+    out = torch.empty(shape, dtype=out_dtype, device=device)
+    for kp in range(N):
+        for kq in range(N):
+            xp = torch.full((N,), kp, device=device, dtype=torch.long)
+            xq = torch.full((N,), kq, device=device, dtype=torch.long)
+            A = antisym(names, xp, xq, ar)                     # [kp, kq, kr] over kr
+            kz = ksd[kp, kq]                                   # ks for each kr
+            Ah = antisym(hnames, ar, kz, xp)                   # A_h[kr, ks, kp]
+            h = A + torch.conj(Ah).permute(0, 3, 4, 1, 2)
+            h *= sc
+            out[kp, kq] = h.to(out_dtype)
+    cache.clear()
+    return out
+
+
+def generate_torch(spec: SynthSpec, device="cuda", blocks=STORED_BLOCKS) -> dict:
+    """generate() evaluated with torch on `device`: a dict of contiguous torch
+    tensors there (Fock blocks complex128, integral blocks complex128 or, for
+    int_dtype "c64", complex64)."""
+    import torch
+    ks = _ks_table(spec.grid)
+    f_oo, f_vv, f_ov = generate_fock(spec)
+    out = {"f_oo": torch.from_numpy(f_oo).to(device), "f_vv": torch.from_numpy(f_vv).to(device),
+           "f_ov": torch.from_numpy(f_ov).to(device)}
+    dt = torch.complex64 if spec.int_dtype == "c64" else torch.complex128
+    # largest last: the peak is the vvvv classes plus the smaller results
+    for b in sorted(blocks, key=lambda c: c.count("v")):
+        out[b] = _block_torch(spec, b, ks, torch, device, dt).contiguous()
+        if str(device).startswith("cuda"):
+            torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------- random amplitudes, one stream per k_i
+def _amp_draws(spec: SynthSpec, seed: int, ki: int, scale: float):
+    N, o, v = spec.nk, spec.nocc, spec.nvir
+    rng = np.random.default_rng([seed, 37, ki])
+    shape = (N, N, o, o, v, v)
+    return scale * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+
+
+def _t1_draws(spec: SynthSpec, seed: int, scale: float):
+    N, o, v = spec.nk, spec.nocc, spec.nvir
+    rng = np.random.default_rng([seed, 31])
+    return scale * (rng.standard_normal((N, o, v)) + 1j * rng.standard_normal((N, o, v)))
+
+
+def random_amplitudes_slabs(spec: SynthSpec, seed: int, scale: float = 0.05):
+    """Random antisymmetric, k-conserving t1 and t2 like random_amplitudes(), drawn
+    one k_i slab per stream so that the torch twin below can fill large grids
+    quickly; t2 = (x - x(i<->j) - x(a<->b) + x(both)) / 2."""
+    N = spec.nk
+    t1 = _t1_draws(spec, seed, scale)
+    x = np.stack([_amp_draws(spec, seed, ki, scale) for ki in range(N)])
+    ks = _ks_table(spec.grid)
+    kk = np.arange(N)
+    KI, KJ, KA = np.meshgrid(kk, kk, kk, indexing="ij")
+    KB = ks[KI, KJ, KA]
+    t2 = (x - x[KJ, KI, KA].transpose(0, 1, 2, 4, 3, 5, 6)
+          - x[KI, KJ, KB].transpose(0, 1, 2, 3, 4, 6, 5)
+          + x[KJ, KI, KB].transpose(0, 1, 2, 4, 3, 6, 5)) * 0.5
+    return np.ascontiguousarray(t1), np.ascontiguousarray(t2)
+
+
+def random_amplitudes_torch(spec: SynthSpec, seed: int, device="cuda", scale: float = 0.05):
+    """random_amplitudes_slabs() evaluated with torch on `device` (same draws)."""
+    import torch
+    N = spec.nk
+    t1 = torch.from_numpy(_t1_draws(spec, seed, scale)).to(device)
+    x = torch.empty((N, N, N, spec.nocc, spec.nocc, spec.nvir, spec.nvir), dtype=torch.complex128,
+                    device=device)
+    workers = min(N, os.cpu_count() or 1, 16)
+    with ThreadPoolExecutor(max(workers, 1)) as ex:
+        for ki, a in enumerate(ex.map(lambda k: _amp_draws(spec, seed, k, scale), range(N))):
+            x[ki] = torch.from_numpy(a).to(device)
+    ks = torch.as_tensor(_ks_table(spec.grid), dtype=torch.long, device=device)
+    t2 = torch.empty_like(x)
+    ar = torch.arange(N, device=device)
+    for ki in range(N):
+        # one k_i slab at a time: x[kj, ki, ka], x[ki, kj, kb], x[kj, ki, kb]
+        KJ, KA = torch.meshgrid(ar, ar, indexing="ij")
+        KI = torch.full_like(KJ, ki)
+        KB = ks[KI, KJ, KA]
+        y = x[ki] - x[KJ, KI, KA].transpose(-4, -3) - x[KI, KJ, KB].transpose(-2, -1) \
+            + x[KJ, KI, KB].transpose(-4, -3).transpose(-2, -1)
+        t2[ki] = y * 0.5
+    return t1.contiguous(), t2.contiguous()

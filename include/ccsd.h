@@ -52,6 +52,10 @@ extern "C" {
                            polish_iters FP64 iterations                       */
 
 #define CCSD_C128   0   /* integral blocks complex128                          */
+#define CCSD_C64    1   /* integral blocks complex64 (Fock blocks stay complex128):
+                           the FP64 form widens every element exactly to double on
+                           load, so it solves the equations of exactly these values;
+                           the mixed form reads them as stored                    */
 
 typedef struct ccsd_ctx* ccsd_t;
 
@@ -68,6 +72,13 @@ typedef struct {
                              mixed ones (0..100)                                 */
     double mixed_tol;     /* CCSD_MIXED: ccsd_solve switches to FP64 once the mixed
                              max|R| < max(mixed_tol, conv_tol)                  */
+    int    lean;          /* work-memory policy.  0: automatic -- problems whose
+                             tensor-core operands would exceed 24 GB share two
+                             operand buffers rewritten every residual, and the
+                             ladder's W' is formed in slabs of at most 12 GB;
+                             1: that lean layout at any size, with the W' slabs
+                             and the tensor-core ladder chunks cut to about a
+                             third (same results, more launches)                */
 } ccsd_config;
 
 typedef struct {
@@ -77,7 +88,7 @@ typedef struct {
      * memory during ccsd_create; pinned host memory copies fastest). */
     const void *f_oo, *f_vv, *f_ov;
     const void *oooo, *ooov, *oovv, *ovvo, *ovvv, *vvvv;
-    int int_dtype;        /* CCSD_C128                                          */
+    int int_dtype;        /* CCSD_C128 or CCSD_C64 (the six integral blocks)    */
 } ccsd_inputs;
 
 /* Creates a solver for one problem.  `stream` is a cudaStream_t (NULL = the
@@ -86,9 +97,12 @@ typedef struct {
  * work memory up front; returns CCSD_ERR_OOM if it does not fit. */
 int ccsd_create(const ccsd_config* cfg, const ccsd_inputs* in, void* stream, ccsd_t* out);
 
-/* Bytes of device memory ccsd_create would allocate for this config when
- * `inputs_on_device` is 1 (borrowed inputs) or 0 (copied inputs). */
-int ccsd_footprint(const ccsd_config* cfg, int inputs_on_device, size_t* bytes);
+/* Bytes of device memory ccsd_create allocates for this config when
+ * `inputs_on_device` is 1 (borrowed inputs) or 0 (copied inputs) and the
+ * integral blocks are int_dtype (CCSD_C128 / CCSD_C64): the total of a dry run
+ * of its allocations and plan, nothing allocated.  CCSD_ERR_INVALID for a bad
+ * config or dtype. */
+int ccsd_footprint(const ccsd_config* cfg, int inputs_on_device, int int_dtype, size_t* bytes);
 
 /* Builds the launch plan of this config on the host only (no GPU, no device
  * memory) and checks that every element each launch can touch lies inside

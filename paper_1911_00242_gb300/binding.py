@@ -21,6 +21,7 @@ CCSD_ERR_TIMEOUT = -6
 CCSD_FP64 = 0
 CCSD_MIXED = 1
 CCSD_C128 = 0
+CCSD_C64 = 1
 
 BLOCKS = ("oooo", "ooov", "oovv", "ovvo", "ovvv", "vvvv")
 
@@ -28,7 +29,8 @@ BLOCKS = ("oooo", "ooov", "oovv", "ovvo", "ovvv", "vvvv")
 class ccsd_config(ctypes.Structure):
     _fields_ = [("nk_dims", ctypes.c_int * 3), ("nocc", ctypes.c_int), ("nvir", ctypes.c_int),
                 ("precision", ctypes.c_int), ("diis_depth", ctypes.c_int), ("max_iter", ctypes.c_int),
-                ("conv_tol", ctypes.c_double), ("polish_iters", ctypes.c_int), ("mixed_tol", ctypes.c_double)]
+                ("conv_tol", ctypes.c_double), ("polish_iters", ctypes.c_int), ("mixed_tol", ctypes.c_double),
+                ("lean", ctypes.c_int)]
 
 
 class ccsd_inputs(ctypes.Structure):
@@ -41,7 +43,8 @@ class ccsd_inputs(ctypes.Structure):
 SYMBOLS = {
     "ccsd_create": ([ctypes.POINTER(ccsd_config), ctypes.POINTER(ccsd_inputs), ctypes.c_void_p,
                      ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
-    "ccsd_footprint": ([ctypes.POINTER(ccsd_config), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "ccsd_footprint": ([ctypes.POINTER(ccsd_config), ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
+                       ctypes.c_int),
     "ccsd_plan_check": ([ctypes.POINTER(ccsd_config), ctypes.POINTER(ctypes.c_longlong),
                          ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "ccsd_tc_selftest": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
@@ -125,31 +128,49 @@ def _ptr(x):
     return x.ctypes.data
 
 
+def int_dtype(arrays):
+    """CCSD_C128 or CCSD_C64 from the element type of the six integral blocks
+    (all must agree; the Fock blocks are always complex128)."""
+    kinds = {str(arrays[b].dtype).replace("torch.", "") for b in BLOCKS}
+    if kinds == {"complex128"}:
+        return CCSD_C128
+    if kinds == {"complex64"}:
+        return CCSD_C64
+    raise ValueError(f"integral blocks must all be complex128 or all complex64, got {sorted(kinds)}")
+
+
+def inputs_struct(arrays):
+    inp = ccsd_inputs()
+    for name in ("f_oo", "f_vv", "f_ov") + BLOCKS:
+        setattr(inp, name, _ptr(arrays[name]))
+    inp.int_dtype = int_dtype(arrays)
+    return inp
+
+
 def make_config(grid, nocc, nvir, precision=CCSD_FP64, diis_depth=0, max_iter=100, conv_tol=1e-8,
-                polish_iters=2, mixed_tol=1e-7):
+                polish_iters=2, mixed_tol=1e-7, lean=0):
     c = ccsd_config()
     c.nk_dims[0], c.nk_dims[1], c.nk_dims[2] = grid
     c.nocc, c.nvir, c.precision = nocc, nvir, precision
     c.diis_depth, c.max_iter, c.conv_tol = diis_depth, max_iter, conv_tol
     c.polish_iters, c.mixed_tol = polish_iters, mixed_tol
+    c.lean = lean
     return c
 
 
 class Solver:
     """One CCSD problem held by a library handle.
 
-    `arrays` maps f_oo, f_vv, f_ov and the six block names to contiguous
-    complex128 torch tensors (device: borrowed, kept referenced here) or numpy
-    arrays (host: copied by the library during creation)."""
+    `arrays` maps f_oo, f_vv, f_ov (complex128) and the six block names
+    (all complex128 or all complex64) to contiguous torch tensors (device:
+    borrowed, kept referenced here) or numpy arrays (host: copied by the
+    library during creation)."""
 
     def __init__(self, grid, nocc, nvir, arrays, stream=None, **cfg):
         self.lib = load()
         self.cfg = make_config(grid, nocc, nvir, **cfg)
         self._keep = dict(arrays)
-        inp = ccsd_inputs()
-        for name in ("f_oo", "f_vv", "f_ov") + BLOCKS:
-            setattr(inp, name, _ptr(arrays[name]))
-        inp.int_dtype = CCSD_C128
+        inp = inputs_struct(arrays)
         h = ctypes.c_void_p()
         check(self.lib.ccsd_create(ctypes.byref(self.cfg), ctypes.byref(inp), stream, ctypes.byref(h)), "ccsd_create")
         self.h = h
@@ -233,9 +254,7 @@ class BatchSolver:
         self._keep = []
         for i, (grid, nocc, nvir, arrays) in enumerate(problems):
             cfgs[i] = make_config(grid, nocc, nvir, **cfg)
-            for name in ("f_oo", "f_vv", "f_ov") + BLOCKS:
-                setattr(ins[i], name, _ptr(arrays[name]))
-            ins[i].int_dtype = CCSD_C128
+            ins[i] = inputs_struct(arrays)
             self._keep.append(arrays)
         self.n = n
         h = ctypes.c_void_p()
@@ -289,10 +308,7 @@ class Server:
 
     def submit(self, grid, nocc, nvir, arrays, **cfg):
         c = make_config(grid, nocc, nvir, **cfg)
-        inp = ccsd_inputs()
-        for name in ("f_oo", "f_vv", "f_ov") + BLOCKS:
-            setattr(inp, name, _ptr(arrays[name]))
-        inp.int_dtype = CCSD_C128
+        inp = inputs_struct(arrays)
         rid = ctypes.c_uint64(0)
         check(self.lib.ccsd_submit(self.h, ctypes.byref(c), ctypes.byref(inp), ctypes.byref(rid)), "ccsd_submit")
         self._keep[rid.value] = arrays

@@ -67,7 +67,7 @@ enum Buf {
     B_FOO_IN, B_FVV_IN, B_FOV_IN, B_OOOO, B_OOOV, B_OOVV, B_OVVO, B_OVVV, B_VVVV,
     B_T1, B_T2, B_R1, B_R2, B_TAU, B_TAUT,
     B_FOV, B_FOO, B_FVV, B_FOOP, B_FVVP,
-    B_WHH, B_WAB, B_WRING, B_Q, B_TT, B_ZAB, B_ZIJ, B_ZR,
+    B_WHH, B_WAB, B_WRING, B_Q, B_TT, B_STA, B_STB, B_ZR,   // B_STA, B_STB: tensor-core self-test operands
     NBUF
 };
 
@@ -87,7 +87,8 @@ struct PermPlan {
 };
 
 struct Step {           // one element of the launch sequence
-    int kind;           // 0 gemm, 1 copy, 2 perm, 3 tau, 4 antisym, 5 embed, 6 tensor-core gemm, 7 zero
+    int kind;           // 0 gemm, 1 copy, 2 perm, 3 tau, 4 antisym, 5 embed, 6 tensor-core gemm, 7 zero,
+                        // 9 complex64 refresh of t1, 10 W' formation into the ladder's B operand
     int idx;
     const char* name;
     double flops;       // algorithmic real flops per launch (complex MAC = 8)
@@ -98,10 +99,6 @@ struct Step {           // one element of the launch sequence
 struct EmbedPlan {      // operand preparation for the tensor-core GEMM
     int src;
     EmbedArgs a;        // a.src resolved at launch
-};
-
-struct WPlan {          // fused W' formation + embedding for one k_a slab of the ladder
-    WprimeArgs a;       // vvvv / ovvv / t1 resolved at launch
 };
 
 struct WListPlan {      // fused W' formation + embedding for listed blocks and index pairs
@@ -125,7 +122,8 @@ struct ccsd_ctx {
     cudaStream_t st = nullptr;
     double2* buf[NBUF] = {};
     long long bufsize[NBUF] = {};   // elements, for plan bound checks
-    float2* shadow[NBUF] = {};       // mixed form: complex64 copies read by the FP32 kernels
+    float2* shadow[NBUF] = {};       // complex64 data: mixed-form copies, or inputs stored complex64
+    bool in32[NBUF] = {};            // input stored complex64 only (shadow[] set, buf[] null)
     std::vector<void*> owned;        // device allocations to free
     size_t owned_bytes = 0;
     double2* amp = nullptr;          // [t1 | t2]
@@ -141,7 +139,11 @@ struct ccsd_ctx {
     double2* cred_out = nullptr;
     double* norm_host = nullptr;     // pinned: max|R| of the last iteration
     cudaEvent_t ev_norm = nullptr;
-    std::vector<double2*> hx, he;    // DIIS history
+    std::vector<double2*> hx, he;    // DIIS history on canonical blocks: [t1 | nc blocks of t2]
+    long long nc = 0;                // canonical t2 blocks (ki <= kj, ka <= kb)
+    int* d_cblk = nullptr;           // full block index of each canonical block
+    double* d_cw = nullptr;          // its weight: the number of blocks it stands for
+    int* d_cmap = nullptr;           // per full block: 4 * canonical index + 2 swap_ij + swap_ab
     std::vector<std::vector<double>> gram;
     int diis_count = 0, diis_next = 0;
     std::vector<GemmPlan> gemms;
@@ -152,10 +154,10 @@ struct ccsd_ctx {
     int red_blocks = 0;
     const char* cur_name = "";
     int fp32 = 0;                    // contractions in FP32 arithmetic (mixed form)
+    long long wab_cap_bytes = 12LL << 30;   // bound of the ladder's W' slab buffer
     // mixed form: tensor-core operands (TF32 big/small parts of the real embeddings)
     std::vector<EmbedPlan> embeds;
     std::vector<TcPlan> tcs;
-    std::vector<WPlan> wplans;
     std::vector<WListPlan> wlists;
     std::vector<int> const_embeds;   // embeds of constant inputs, run once at creation
     int* tc_err = nullptr;
@@ -231,6 +233,14 @@ const int CFG_BM[5] = {64, 64, 128, 16, 32};
 const int CFG_BN[5] = {64, 32, 16, 16, 16};
 
 const int kSMs = 152;
+
+// Momentum pairs (ka <= kb) whose ladder W' blocks one slab holds: as many as fit in
+// cap bytes, at least one.  The slab buffer holds that many pairs x N blocks of v^4.
+long long wab_pairs_per_slab(long long N, long long v, long long cap) {
+    const long long pairs = N * (N + 1) / 2;
+    const long long pair_bytes = 16 * N * v * v * v * v;
+    return std::max<long long>(1, std::min<long long>(pairs, cap / pair_bytes));
+}
 
 int finalize_gemm(ccsd_ctx* h, Alloc& al, GemmSpec s, size_t& work_need) {
     if (s.nbatch == 0) {
@@ -495,63 +505,90 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     int rc;
     auto G = [&](GemmSpec& s) { return finalize_gemm(h, al, s, work_need); };
     const bool mixed = h->cfg.precision == CCSD_MIXED;
-    TcBuf tc_la{}, tc_lb{}, tc_ra{}, tc_rb{}, tc_b1{}, tc_ha{}, tc_hb{}, tc_h2a{}, tc_h2b{}, tc_lap{}, tc_lbp{};
-    int ladder_nka = 1;
-    bool ladder_packed = false;
-    long long tc_lb_used = 0, tc_lbp_used = 0;   // rows handed out in the packed B buffers
+    TcBuf tc_la{}, tc_lap{}, tc_lb{}, tc_ra{}, tc_rb{}, tc_b1{}, tc_ha{}, tc_hb{}, tc_h2a{}, tc_h2b{};
+    bool pooled = false;          // tensor-core operands share two buffers, rewritten every residual
+    long long lb_floats = 0;      // capacity (floats per part) of the ladder's B-operand buffer
+    float* pool_b = nullptr;      // the B-side pool (big part; the small part follows it)
+    const long long nlt_vv = (long long)v * (v - 1) / 2;
+    const int kpl = (int)((2 * vv + TC_BK - 1) / TC_BK * TC_BK);
+    const int kplp = (int)((2 * nlt_vv + TC_BK - 1) / TC_BK * TC_BK);
     if (mixed) {
-        const int kpl = (int)((2 * vv + TC_BK - 1) / TC_BK * TC_BK);
         const int kpr = (int)((2 * ov + TC_BK - 1) / TC_BK * TC_BK);
+        const int kpo = (int)((2 * oo + TC_BK - 1) / TC_BK * TC_BK);
         const long long N3l = (long long)N * N * N;
         h->tc_err = (int*)al.get(sizeof(int));
         if (al.err) return al.err;
-        // complex64 copies: the inputs once here, t1 at the start of every residual
+        // complex64 copies: the inputs once here (unless stored so), t1 at the start of every residual
         for (int bi = B_FOO_IN; bi <= B_T1; ++bi) {
-            if (bi == B_T2) continue;
+            if (bi == B_T2 || h->in32[bi]) continue;
             h->shadow[bi] = (float2*)al.get((size_t)h->bufsize[bi] * 8);
             if (al.err) return al.err;
             if (!al.dry && bi != B_T1)
                 to_c64_kernel<<<ew_grid(h->bufsize[bi]), 256, 0, h->st>>>(h->shadow[bi], h->buf[bi], h->bufsize[bi]);
         }
         if (!al.dry && cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st) != cudaSuccess) return CCSD_ERR_CUDA;
-        // ladder: antisymmetry-packed operands when they fit in ~12 GB, else unpacked k_a
-        // slabs (enough CTAs per launch for ~4 waves, B operand within ~8 GB)
-        const long long nlt = (long long)v * (v - 1) / 2;
-        const int kplp = (int)((2 * nlt + TC_BK - 1) / TC_BK * TC_BK);
-        long long off_blocks = 0, diag_blocks_full = 0, diag_blocks_lt = 0;   // B blocks per kind
-        for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) {
-            const int S = kg.k4(ka, kb, 0);
-            for (int ke = 0; ke < N; ++ke) {
-                const int kf = kg.k4(S, 0, ke);
-                if (ke < kf) { if (ka < kb) off_blocks += 1; else diag_blocks_full += 1; }
-                else if (ke == kf) { if (ka < kb) diag_blocks_lt += 1; else diag_blocks_lt += 1; }
+        // ladder B rows of the largest packed class (floats per part)
+        long long lad_max = 0, lad_batch = 0;    // largest class, largest single (ka, kb) batch
+        for (int diag_ab = 0; diag_ab < 2; ++diag_ab) for (int diag_ef = 0; diag_ef < 2; ++diag_ef) {
+            const long long per_block = 2 * (diag_ab ? nlt_vv : vv) * (diag_ef ? kplp : kpl);
+            long long blocks = 0;
+            for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) {
+                if ((ka == kb) != (diag_ab == 1)) continue;
+                const int S = kg.k4(ka, kb, 0);
+                long long nb = 0;
+                for (int ke = 0; ke < N; ++ke) { const int kf = kg.k4(S, 0, ke); if (diag_ef ? ke == kf : ke < kf) ++nb; }
+                blocks += nb;
+                lad_batch = std::max(lad_batch, nb * per_block);
             }
+            lad_max = std::max(lad_max, blocks * per_block);
         }
-        // rows: off-diagonal ef -> full (ab or a<b) x 2 rows; diagonal ef -> same
-        const long long rows_full = off_blocks * 2 * vv + diag_blocks_full * 2 * nlt;
-        long long rows_lt = 0;
-        for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) {
-            const int S = kg.k4(ka, kb, 0);
-            for (int ke = 0; ke < N; ++ke) if (ke == kg.k4(S, 0, ke)) rows_lt += 2 * (ka < kb ? vv : nlt);
+        // 8 GB of big + small parts (a third of the largest class in the lean layout), and
+        // never less than one batch
+        const long long lad_cap = std::max(lad_batch, h->cfg.lean ? lad_max / 3 : 1LL << 30);
+        // operand sizes (floats per part): A side (mode 0) and B side (mode 1)
+        const long long fa[5] = {N3l * oo * kpl, N3l * oo * kplp, N3l * ov * kpr, N3l * oo * kpl, N3l * oo * kpo};
+        const long long fb[4] = {N3l * 2 * ov * kpr, N3l * 2 * ov * kpr, N3l * 2 * oo * kpl, N3l * 2 * vv * kpo};
+        long long total = std::min(lad_max, lad_cap);
+        for (long long x : fa) total += x;
+        for (long long x : fb) total += x;
+        pooled = h->cfg.lean || total * 8 > (24LL << 30);
+        if (!pooled) {
+            lb_floats = std::max(1LL, std::min(lad_max, lad_cap));
+            if ((rc = tc_alloc(h, al, tc_la, N3l * oo, kpl)) || (rc = tc_alloc(h, al, tc_lap, N3l * oo, std::max(kplp, TC_BK))) ||
+                (rc = tc_alloc(h, al, tc_lb, lb_floats / kpl + 1, kpl)) ||
+                (rc = tc_alloc(h, al, tc_ra, N3l * ov, kpr)) || (rc = tc_alloc(h, al, tc_rb, N3l * 2 * ov, kpr)) ||
+                (rc = tc_alloc(h, al, tc_b1, N3l * 2 * ov, kpr)) ||
+                (rc = tc_alloc(h, al, tc_ha, N3l * oo, kpl)) || (rc = tc_alloc(h, al, tc_hb, N3l * 2 * oo, kpl)) ||
+                (rc = tc_alloc(h, al, tc_h2a, N3l * oo, kpo)) || (rc = tc_alloc(h, al, tc_h2b, N3l * 2 * vv, kpo)))
+                return rc;
+            lb_floats = tc_lb.rows * kpl;
+        } else {
+            // Large problems: every tensor-core step embeds its operands into one of two pools
+            // just before its GEMM (stream order keeps them intact while it runs).  The B
+            // pool also serves the FP64 ladder's W' slab, which only FP64 iterations use.
+            long long pa = 0, pb = std::min(lad_max, lad_cap);
+            for (long long x : fa) pa = std::max(pa, x);
+            for (long long x : fb) pb = std::max(pb, x);
+            pb = std::max(pb, h->bufsize[B_WAB] * 2);
+            float* A = (float*)al.get((size_t)pa * 8);
+            pool_b = (float*)al.get((size_t)pb * 8);
+            if (al.err) return al.err;
+            lb_floats = pb;
+            auto view = [](float* base, long long floats, long long rows, int kpad) {
+                TcBuf t{base, base + floats, rows, kpad};
+                return t;
+            };
+            tc_la = view(A, pa, N3l * oo, kpl); tc_lap = view(A, pa, N3l * oo, std::max(kplp, TC_BK));
+            tc_ra = view(A, pa, N3l * ov, kpr); tc_ha = view(A, pa, N3l * oo, kpl); tc_h2a = view(A, pa, N3l * oo, kpo);
+            tc_rb = view(pool_b, pb, N3l * 2 * ov, kpr); tc_b1 = view(pool_b, pb, N3l * 2 * ov, kpr);
+            tc_hb = view(pool_b, pb, N3l * 2 * oo, kpl); tc_h2b = view(pool_b, pb, N3l * 2 * vv, kpo);
+            tc_lb = view(pool_b, pb, pb / kpl, kpl);
+            h->buf[B_WAB] = (double2*)pool_b;
         }
-        const long long packed_bytes = (rows_full * kpl + rows_lt * kplp) * 4LL * 2;
-        ladder_packed = v >= 2 && packed_bytes <= (12LL << 30);
-        const long long per_ka_ctas = (long long)N * ((N * oo + TC_BM - 1) / TC_BM) * ((2 * vv + TC_BN - 1) / TC_BN);
-        const long long per_ka_bytes = (long long)N * N * 2 * vv * kpl * 4 * 2;
-        ladder_nka = (int)std::min<long long>(N, std::max<long long>(1, (4 * kSMs + per_ka_ctas - 1) / per_ka_ctas));
-        while (ladder_nka > 1 && ladder_nka * per_ka_bytes > (8LL << 30)) --ladder_nka;
-        if (ladder_packed &&
-            ((rc = tc_alloc(h, al, tc_lap, N3l * oo, kplp)) || (rc = tc_alloc(h, al, tc_lbp, std::max(rows_lt, 1LL), kplp))))
-            return rc;
-        if ((rc = tc_alloc(h, al, tc_la, N3l * oo, kpl)) ||
-            (rc = tc_alloc(h, al, tc_lb, ladder_packed ? std::max(rows_full, 1LL) : (long long)ladder_nka * N * N * 2 * vv, kpl)) ||
-            (rc = tc_alloc(h, al, tc_ra, N3l * ov, kpr)) || (rc = tc_alloc(h, al, tc_rb, N3l * 2 * ov, kpr)) ||
-            (rc = tc_alloc(h, al, tc_b1, N3l * 2 * ov, kpr)))
-            return rc;
-        const int kpo = (int)((2 * oo + TC_BK - 1) / TC_BK * TC_BK);
-        if ((rc = tc_alloc(h, al, tc_ha, N3l * oo, kpl)) || (rc = tc_alloc(h, al, tc_hb, N3l * 2 * oo, kpl)) ||
-            (rc = tc_alloc(h, al, tc_h2a, N3l * oo, kpo)) || (rc = tc_alloc(h, al, tc_h2b, N3l * 2 * vv, kpo)))
-            return rc;
+    }
+    if (!pooled) {
+        h->buf[B_WAB] = (double2*)al.get((size_t)h->bufsize[B_WAB] * 16);
+        if (al.err) return al.err;
     }
 
     // ---------------- tau, tau~
@@ -821,7 +858,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         std::vector<long long> so;
         for (int S = 0; S < N; ++S) for (int ke = 0; ke < N; ++ke) for (int km = 0; km < N; ++km)
             so.push_back(blk(S2, km, kg.k4(S, 0, km), ke));
-        if ((rc = add_embed(h, al, B_OOVV, tc_ha, 0, (int)oo, (int)vv, so, tab({{(int)oo, vv}}), tab({{(int)vv, 1}}), true)))
+        if ((rc = add_embed(h, al, B_OOVV, tc_ha, 0, (int)oo, (int)vv, so, tab({{(int)oo, vv}}), tab({{(int)vv, 1}}), !pooled)))
             return rc;
         so.clear();
         for (int S = 0; S < N; ++S) for (int ke = 0; ke < N; ++ke) for (int ki = 0; ki < N; ++ki)
@@ -902,116 +939,132 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         if ((rc = add_tc(h, al, tc_h2a, tc_h2b, B_R2, (int)(N * oo), (int)(2 * N * vv), N, N, ra, rb, oc,
                          tab({{N, S2}, {(int)vv, 1}}), 0.5, 3))) return rc;
     }
-    h->cur_name = "ladder_W";
-    // ladder: Wab = <ab||ef> - P(ab) t_r^b <a r||e f>
-    const size_t ladder_w_first = h->seq.size();
-    if ((rc = add_copy(h, B_WAB, B_VVVV, (long long)N3 * Svvvv, 0))) return rc;
-    // (only the blocks ka <= kb: the packed ladder below reads no others)
-    const int NP = N * (N + 1) / 2;
-    {   // + sum_r t_r^b(kb) ovvv[kb,ka,ke](r,a,e,f)
-        GemmSpec s; s.a = B_OVVV; s.b = B_T1; s.c = B_WAB;
-        s.M = (int)(vv * v); s.N = v; s.K = o; s.nbatch = NP * N; s.nchunk = 1;
-        for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) for (int ke = 0; ke < N; ++ke) {
-            s.offA.push_back(blk(Sovvv, kb, ka, ke)); s.offB.push_back(kb * ov); s.offC.push_back(blk(Svvvv, ka, kb, ke));
-        }
-        s.rowA = tab({{(int)(vv * v), 1}}); s.colA = tab({{o, vv * v}});
-        s.rowB = tab({{o, v}}); s.colB = tab({{v, 1}});
-        s.rowC = tab({{v, vv * v}, {(int)vv, 1}}); s.colC = tab({{v, vv}});
-        if ((rc = G(s))) return rc;
-    }
-    {   // - sum_r t_r^a(ka) ovvv[ka,kb,ke](r,b,e,f)
-        GemmSpec s; s.a = B_OVVV; s.b = B_T1; s.c = B_WAB; s.ar = -1.0;
-        s.M = (int)(vv * v); s.N = v; s.K = o; s.nbatch = NP * N; s.nchunk = 1;
-        for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) for (int ke = 0; ke < N; ++ke) {
-            s.offA.push_back(blk(Sovvv, ka, kb, ke)); s.offB.push_back(ka * ov); s.offC.push_back(blk(Svvvv, ka, kb, ke));
-        }
-        s.rowA = tab({{(int)(vv * v), 1}}); s.colA = tab({{o, vv * v}});
-        s.rowB = tab({{o, v}}); s.colB = tab({{v, 1}});
-        s.rowC = tab({{v, vv}, {(int)vv, 1}}); s.colC = tab({{v, vv * v}});
-        if ((rc = G(s))) return rc;
-    }
-    if (mixed)   // the tensor-core path forms W' inside its operand embedding
-        for (size_t i = ladder_w_first; i < h->seq.size(); ++i) h->seq[i].mode = 1;
-    h->cur_name = "ladder";
-    {   // R2 += 1/2 sum_{ke,e,f} tau_ij^ef W'^abef, packed by antisymmetry:
-        // tau and W' change sign under (e ke) <-> (f kf), so the half sum over ordered
-        // pairs is the full sum over (ke < kf, all e f) plus (ke = kf, e < f); W' also
-        // changes sign under (a ka) <-> (b kb), so only (ka < kb, all a b) and
-        // (ka = kb, a < b) are computed and the mirror R2(ba) = -R2(ab) is written by
-        // the same thread.  Four launches: {ka < kb, ka = kb} x {ke < kf, ke = kf}.
-        std::vector<int> pairs_full = tab({{(int)vv, 1}}), pairs_lt, pairs_lt_T;
-        for (int x = 0; x < v; ++x) for (int y = x + 1; y < v; ++y) { pairs_lt.push_back(x * v + y); pairs_lt_T.push_back(y * v + x); }
+    // ladder: Wab = <ab||ef> - P(ab) t_r^b <a r||e f>, formed for slabs of momentum pairs
+    // (ka <= kb; the packed ladder reads no others) into a bounded buffer, each slab
+    // followed by its ladder contractions.  Slot p of a slab holds pair p's blocks
+    // [p][ke](a,b,e,f).
+    {
+        std::vector<std::pair<int, int>> pairs;
+        for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) pairs.push_back({ka, kb});
+        const long long pair_el = (long long)N * Svvvv;
+        const int per_slab = (int)wab_pairs_per_slab(N, v, h->wab_cap_bytes);
+        std::vector<int> pairs_full = tab({{(int)vv, 1}}), pairs_lt;
+        for (int x = 0; x < v; ++x) for (int y = x + 1; y < v; ++y) pairs_lt.push_back(x * v + y);
         std::vector<int> swapped;                       // (a,b) -> (b,a) for every a, b
         for (int x = 0; x < v; ++x) for (int y = 0; y < v; ++y) swapped.push_back(y * v + x);
-        for (int diag_ab = 0; diag_ab < 2; ++diag_ab) {
-            for (int diag_ef = 0; diag_ef < 2; ++diag_ef) {
-                GemmSpec s; s.a = B_TAU; s.b = B_WAB; s.c = B_R2; s.ar = 1.0;
-                const std::vector<int>& ncols = diag_ab ? pairs_lt : pairs_full;
-                const std::vector<int>& kcols = diag_ef ? pairs_lt : pairs_full;
-                s.M = (int)oo; s.N = (int)ncols.size(); s.K = (int)kcols.size(); s.nchunk = N;
-                s.nbatch = 0;
-                for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) {
-                    if ((ka == kb) != (diag_ab == 1)) continue;
-                    const int S = kg.k4(ka, kb, 0);
-                    std::vector<int> kes;
-                    for (int ke = 0; ke < N; ++ke) {
-                        const int kf = kg.k4(S, 0, ke);
-                        if (diag_ef ? (ke == kf) : (ke < kf)) kes.push_back(ke);
-                    }
-                    if (kes.empty() || (v < 2 && (diag_ab || diag_ef))) continue;
-                    for (int ki = 0; ki < N; ++ki) {
-                        const int kj = kg.k4(ka, kb, ki);
-                        for (int c = 0; c < N; ++c) {
-                            const int ke = kes[std::min<size_t>(c, kes.size() - 1)];
-                            s.offA.push_back(blk(S2, ki, kj, ke)); s.offB.push_back(blk(Svvvv, ka, kb, ke));
-                        }
-                        s.nchunk_b.push_back((int)kes.size());
-                        s.offC.push_back(blk(S2, ki, kj, ka));
-                        s.offC2.push_back(blk(S2, ki, kj, kb));
-                        ++s.nbatch;
-                    }
+        for (size_t p0 = 0; p0 < pairs.size(); p0 += per_slab) {
+            const size_t p1 = std::min(pairs.size(), p0 + per_slab);
+            h->cur_name = "ladder_W";
+            const size_t w_first = h->seq.size();
+            {   // W'[p] = vvvv[ka][kb]: one contiguous run of N blocks per pair
+                std::vector<long long> offD, offS;
+                for (size_t p = p0; p < p1; ++p) {
+                    offD.push_back((long long)(p - p0) * pair_el);
+                    offS.push_back(((long long)pairs[p].first * N + pairs[p].second) * pair_el);
                 }
-                if (s.nbatch == 0) { if ((rc = G(s))) return rc; if (mixed) h->seq.back().mode = 1; continue; }
-                s.rowA = tab({{(int)oo, vv}}); s.colA = kcols;
-                s.rowB = kcols; s.colB.clear();
-                for (int x : ncols) s.colB.push_back(x * (int)vv);
-                s.rowC = tab({{(int)oo, vv}}); s.colC = ncols;
-                s.colC2.clear();
-                for (int x : ncols) s.colC2.push_back(swapped[x]);
-                if (diag_ab) {
-                    // the mirror of (ka = kb, a < b) is (b, a) in the same block
-                    s.colC2.clear();
-                    for (int x : ncols) s.colC2.push_back((x % v) * v + x / v);
-                }
-                if ((rc = G(s))) return rc;
-                if (mixed) h->seq.back().mode = 1;
+                if ((rc = add_perm(h, al, B_WAB, B_VVVV, N * v, v, v, v, (int)(v * vv), (int)vv, v, 1,
+                                   (int)(v * vv), (int)vv, v, 1, offD, offS))) return rc;
             }
+            {   // + sum_r t_r^b(kb) ovvv[kb,ka,ke](r,a,e,f)
+                GemmSpec s; s.a = B_OVVV; s.b = B_T1; s.c = B_WAB;
+                s.M = (int)(vv * v); s.N = v; s.K = o; s.nbatch = (int)(p1 - p0) * N; s.nchunk = 1;
+                for (size_t p = p0; p < p1; ++p) for (int ke = 0; ke < N; ++ke) {
+                    const int ka = pairs[p].first, kb = pairs[p].second;
+                    s.offA.push_back(blk(Sovvv, kb, ka, ke)); s.offB.push_back(kb * ov);
+                    s.offC.push_back(((long long)(p - p0) * N + ke) * Svvvv);
+                }
+                s.rowA = tab({{(int)(vv * v), 1}}); s.colA = tab({{o, vv * v}});
+                s.rowB = tab({{o, v}}); s.colB = tab({{v, 1}});
+                s.rowC = tab({{v, vv * v}, {(int)vv, 1}}); s.colC = tab({{v, vv}});
+                if ((rc = G(s))) return rc;
+            }
+            {   // - sum_r t_r^a(ka) ovvv[ka,kb,ke](r,b,e,f)
+                GemmSpec s; s.a = B_OVVV; s.b = B_T1; s.c = B_WAB; s.ar = -1.0;
+                s.M = (int)(vv * v); s.N = v; s.K = o; s.nbatch = (int)(p1 - p0) * N; s.nchunk = 1;
+                for (size_t p = p0; p < p1; ++p) for (int ke = 0; ke < N; ++ke) {
+                    const int ka = pairs[p].first, kb = pairs[p].second;
+                    s.offA.push_back(blk(Sovvv, ka, kb, ke)); s.offB.push_back(ka * ov);
+                    s.offC.push_back(((long long)(p - p0) * N + ke) * Svvvv);
+                }
+                s.rowA = tab({{(int)(vv * v), 1}}); s.colA = tab({{o, vv * v}});
+                s.rowB = tab({{o, v}}); s.colB = tab({{v, 1}});
+                s.rowC = tab({{v, vv}, {(int)vv, 1}}); s.colC = tab({{v, vv * v}});
+                if ((rc = G(s))) return rc;
+            }
+            h->cur_name = "ladder";
+            // R2 += 1/2 sum_{ke,e,f} tau_ij^ef W'^abef, packed by antisymmetry: tau and W'
+            // change sign under (e ke) <-> (f kf), so the half sum over ordered pairs is the
+            // full sum over (ke < kf, all e f) plus (ke = kf, e < f); W' also changes sign
+            // under (a ka) <-> (b kb), so only (ka < kb, all a b) and (ka = kb, a < b) are
+            // computed and the mirror R2(ba) = -R2(ab) is written by the same thread.  Four
+            // launches per slab: {ka < kb, ka = kb} x {ke < kf, ke = kf}.
+            for (int diag_ab = 0; diag_ab < 2; ++diag_ab) {
+                for (int diag_ef = 0; diag_ef < 2; ++diag_ef) {
+                    GemmSpec s; s.a = B_TAU; s.b = B_WAB; s.c = B_R2; s.ar = 1.0;
+                    const std::vector<int>& ncols = diag_ab ? pairs_lt : pairs_full;
+                    const std::vector<int>& kcols = diag_ef ? pairs_lt : pairs_full;
+                    s.M = (int)oo; s.N = (int)ncols.size(); s.K = (int)kcols.size(); s.nchunk = N;
+                    s.nbatch = 0;
+                    for (size_t p = p0; p < p1; ++p) {
+                        const int ka = pairs[p].first, kb = pairs[p].second;
+                        if ((ka == kb) != (diag_ab == 1)) continue;
+                        const int S = kg.k4(ka, kb, 0);
+                        std::vector<int> kes;
+                        for (int ke = 0; ke < N; ++ke) {
+                            const int kf = kg.k4(S, 0, ke);
+                            if (diag_ef ? (ke == kf) : (ke < kf)) kes.push_back(ke);
+                        }
+                        if (kes.empty() || (v < 2 && (diag_ab || diag_ef))) continue;
+                        for (int ki = 0; ki < N; ++ki) {
+                            const int kj = kg.k4(ka, kb, ki);
+                            for (int c = 0; c < N; ++c) {
+                                const int ke = kes[std::min<size_t>(c, kes.size() - 1)];
+                                s.offA.push_back(blk(S2, ki, kj, ke));
+                                s.offB.push_back(((long long)(p - p0) * N + ke) * Svvvv);
+                            }
+                            s.nchunk_b.push_back((int)kes.size());
+                            s.offC.push_back(blk(S2, ki, kj, ka));
+                            s.offC2.push_back(blk(S2, ki, kj, kb));
+                            ++s.nbatch;
+                        }
+                    }
+                    if (s.nbatch == 0) { if ((rc = G(s))) return rc; continue; }
+                    s.rowA = tab({{(int)oo, vv}}); s.colA = kcols;
+                    s.rowB = kcols; s.colB.clear();
+                    for (int x : ncols) s.colB.push_back(x * (int)vv);
+                    s.rowC = tab({{(int)oo, vv}}); s.colC = ncols;
+                    s.colC2.clear();
+                    // the mirror of (a, b) is (b, a): in block kb for ka < kb, in the same
+                    // block for ka = kb
+                    for (int x : ncols) s.colC2.push_back(swapped[x]);
+                    if ((rc = G(s))) return rc;
+                }
+            }
+            // the tensor-core path forms W' inside its operand embedding
+            if (mixed) for (size_t i = w_first; i < h->seq.size(); ++i) h->seq[i].mode = 1;
         }
     }
     if (mixed) {
-        // tensor-core ladder: A' = tau in [S = ki + kj][ke][ki](ij)(ef), B' = embedded W' [ka][kb][ke]
+        // Tensor-core ladder, antisymmetry-packed like the FP64 one: outputs (ka < kb | ka = kb,
+        // a < b) with the mirror R2(ba) = -R2(ab), contractions over (ke < kf | ke = kf, e < f).
+        // A' = tau rows [S = ki + kj][ke][ki](ij), columns the (e f) list; B' = W' formed
+        // straight into its embedding for the blocks of one chunk at a time (the buffer
+        // holds lb_floats per part), each chunk followed by its GEMM.
         std::vector<long long> so_lad;
         for (int S = 0; S < N; ++S) for (int ke = 0; ke < N; ++ke) for (int ki = 0; ki < N; ++ki)
             so_lad.push_back(blk(S2, ki, kg.k4(S, 0, ki), ke));
-        if ((rc = add_embed(h, al, B_TAU, tc_la, 0, (int)oo, (int)vv, so_lad, tab({{(int)oo, vv}}), tab({{(int)vv, 1}}), false))) return rc;
+        std::vector<int> full_vv = tab({{(int)vv, 1}}), lt_vv;
+        for (int x = 0; x < v; ++x) for (int y = x + 1; y < v; ++y) lt_vv.push_back(x * v + y);
         const int M = (int)(N * oo);
-        if (ladder_packed) {
-            // antisymmetry-packed tensor-core ladder: (ka < kb | ka = kb, a < b) outputs with
-            // mirror, (ke < kf | ke = kf, e < f) contractions; four launches, W' formed
-            // straight into each launch's B operand for exactly the blocks it reads
-            std::vector<int> full_vv = tab({{(int)vv, 1}}), lt_vv;
-            for (int x = 0; x < v; ++x) for (int y = x + 1; y < v; ++y) lt_vv.push_back(x * v + y);
-            if ((rc = add_embed(h, al, B_TAU, tc_lap, 0, (int)oo, (int)lt_vv.size(), so_lad, tab({{(int)oo, vv}}), lt_vv, false)))
+        for (int diag_ef = 0; diag_ef < 2; ++diag_ef) {
+            const std::vector<int>& efl = diag_ef ? lt_vv : full_vv;
+            if (efl.empty()) continue;
+            const TcBuf& A = diag_ef ? tc_lap : tc_la;
+            if ((rc = add_embed(h, al, B_TAU, A, 0, (int)oo, (int)efl.size(), so_lad, tab({{(int)oo, vv}}), efl, false)))
                 return rc;
-            for (int diag_ab = 0; diag_ab < 2; ++diag_ab) for (int diag_ef = 0; diag_ef < 2; ++diag_ef) {
+            for (int diag_ab = 0; diag_ab < 2; ++diag_ab) {
                 const std::vector<int>& abl = diag_ab ? lt_vv : full_vv;
-                const std::vector<int>& efl = diag_ef ? lt_vv : full_vv;
-                if (abl.empty() || efl.empty()) continue;
-                const TcBuf& A = diag_ef ? tc_lap : tc_la;
-                TcBuf B = diag_ef ? tc_lbp : tc_lb;
-                std::vector<int> blk3, ra, rb, cc, cc2, cnt;
-                std::vector<long long> oc, oc2;
-                int nb = 0, nchmax = 0;
+                if (abl.empty()) continue;
                 std::vector<std::pair<int, int>> batches;
                 std::vector<std::vector<int>> chunks;
                 for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) {
@@ -1022,78 +1075,63 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                     if (kes.empty()) continue;
                     batches.push_back({ka, kb});
                     chunks.push_back(kes);
-                    nchmax = std::max<int>(nchmax, (int)kes.size());
                 }
-                if (batches.empty()) continue;
-                // rows of this launch's blocks start at first_row of its B buffer; block j of
-                // the launch occupies rows first_row + 2 nab j .. + 2 nab
-                const long long first_row = diag_ef ? tc_lbp_used : tc_lb_used;
                 const long long rows_per_block = 2LL * (long long)abl.size();
-                int used = 0;
-                for (size_t bb = 0; bb < batches.size(); ++bb) {
-                    const int ka = batches[bb].first, kb = batches[bb].second;
-                    const int S = kg.k4(ka, kb, 0);
-                    const std::vector<int>& kes = chunks[bb];
-                    for (int c = 0; c < nchmax; ++c) {
-                        const int cc_ = std::min<int>(c, (int)kes.size() - 1);
-                        ra.push_back((int)((((long long)S * N + kes[cc_]) * N) * oo));
-                        rb.push_back((int)(first_row + (long long)(used + cc_) * rows_per_block));
+                const long long cap_rows = lb_floats / A.kpad;
+                size_t b0 = 0;
+                while (b0 < batches.size()) {
+                    // as many (ka, kb) batches as their W' blocks fit in the buffer (at least one)
+                    size_t b1 = b0;
+                    long long rows = 0;
+                    while (b1 < batches.size() && (b1 == b0 || rows + (long long)chunks[b1].size() * rows_per_block <= cap_rows)) {
+                        rows += (long long)chunks[b1].size() * rows_per_block;
+                        ++b1;
                     }
-                    for (int ke : kes) { blk3.push_back(ka); blk3.push_back(kb); blk3.push_back(ke); }
-                    used += (int)kes.size();
-                    cnt.push_back((int)kes.size());
-                    for (int ki = 0; ki < N; ++ki)
-                        for (int ij = 0; ij < (int)oo; ++ij) {
-                            oc.push_back(blk(S2, ki, kg.k4(S, 0, ki), ka) + ij * vv);
-                            oc2.push_back(blk(S2, ki, kg.k4(S, 0, ki), kb) + ij * vv);
+                    if (rows > cap_rows) return CCSD_ERR_INVALID;
+                    TcBuf B{tc_lb.big, tc_lb.big + lb_floats, std::max(rows, 1LL), A.kpad};
+                    if (!pooled) B.small = tc_lb.small;
+                    int nchmax = 0;
+                    for (size_t bb = b0; bb < b1; ++bb) nchmax = std::max<int>(nchmax, (int)chunks[bb].size());
+                    std::vector<int> blk3, ra, rb, cc, cc2, cnt;
+                    std::vector<long long> oc, oc2;
+                    int used = 0;
+                    for (size_t bb = b0; bb < b1; ++bb) {
+                        const int ka = batches[bb].first, kb = batches[bb].second;
+                        const int S = kg.k4(ka, kb, 0);
+                        const std::vector<int>& kes = chunks[bb];
+                        for (int c = 0; c < nchmax; ++c) {
+                            const int cc_ = std::min<int>(c, (int)kes.size() - 1);
+                            ra.push_back((int)((((long long)S * N + kes[cc_]) * N) * oo));
+                            rb.push_back((int)((long long)(used + cc_) * rows_per_block));
                         }
-                    ++nb;
+                        for (int ke : kes) { blk3.push_back(ka); blk3.push_back(kb); blk3.push_back(ke); }
+                        used += (int)kes.size();
+                        cnt.push_back((int)kes.size());
+                        for (int ki = 0; ki < N; ++ki)
+                            for (int ij = 0; ij < (int)oo; ++ij) {
+                                oc.push_back(blk(S2, ki, kg.k4(S, 0, ki), ka) + ij * vv);
+                                oc2.push_back(blk(S2, ki, kg.k4(S, 0, ki), kb) + ij * vv);
+                            }
+                    }
+                    WListPlan wl{};
+                    wl.a.big = B.big; wl.a.small = B.small;
+                    wl.a.blk = upload(al, blk3, h->st);
+                    wl.a.abl = upload(al, abl, h->st);
+                    wl.a.efl = upload(al, efl, h->st);
+                    if (al.err) return al.err;
+                    wl.a.nblk = (int)(blk3.size() / 3); wl.a.nab = (int)abl.size(); wl.a.nef = (int)efl.size();
+                    wl.a.N = N; wl.a.o = o; wl.a.v = v; wl.a.Kpad = A.kpad;
+                    h->wlists.push_back(wl);
+                    Step st{10, (int)h->wlists.size() - 1, "ladder_W", 0.0, 40.0 * (double)wl.a.nblk * wl.a.nab * wl.a.nef};
+                    st.mode = 2;
+                    h->seq.push_back(st);
+                    cc.clear(); cc2.clear();
+                    for (int x : abl) { cc.push_back(x); cc2.push_back((x % v) * v + x / v); }
+                    if ((rc = add_tc(h, al, A, B, B_R2, M, (int)(2 * abl.size()), (int)(b1 - b0), nchmax, ra, rb, oc, cc,
+                                     1.0, 3, cnt, oc2, cc2))) return rc;
+                    b0 = b1;
                 }
-                if (first_row + (long long)used * rows_per_block > B.rows) return CCSD_ERR_INVALID;
-                if (diag_ef) tc_lbp_used = first_row + (long long)used * rows_per_block;
-                else tc_lb_used = first_row + (long long)used * rows_per_block;
-                WListPlan wl{};
-                wl.a.big = B.big + (size_t)first_row * B.kpad;
-                wl.a.small = B.small + (size_t)first_row * B.kpad;
-                wl.a.blk = upload(al, blk3, h->st);
-                wl.a.abl = upload(al, abl, h->st);
-                wl.a.efl = upload(al, efl, h->st);
-                if (al.err) return al.err;
-                wl.a.nblk = (int)(blk3.size() / 3); wl.a.nab = (int)abl.size(); wl.a.nef = (int)efl.size();
-                wl.a.N = N; wl.a.o = o; wl.a.v = v; wl.a.Kpad = B.kpad;
-                h->wlists.push_back(wl);
-                Step st{10, (int)h->wlists.size() - 1, "ladder_W", 0.0, 40.0 * (double)wl.a.nblk * wl.a.nab * wl.a.nef};
-                st.mode = 2;
-                h->seq.push_back(st);
-                for (int x : abl) { cc.push_back(x); cc2.push_back((x % v) * v + x / v); }
-                if ((rc = add_tc(h, al, A, B, B_R2, M, (int)(2 * abl.size()), nb, nchmax, ra, rb, oc, cc, 1.0, 3,
-                                 cnt, oc2, cc2))) return rc;
             }
-        }
-        // k_a slabs: W' for the slab is formed straight into the B operand, then its GEMM runs
-        for (int ka0 = 0; ka0 < N && !ladder_packed; ka0 += ladder_nka) {
-            const int nka = std::min(ladder_nka, N - ka0);
-            WPlan wp{};
-            wp.a.big = tc_lb.big; wp.a.small = tc_lb.small;
-            wp.a.N = N; wp.a.o = o; wp.a.v = v; wp.a.ka0 = ka0; wp.a.nka = nka; wp.a.Kpad = tc_lb.kpad;
-            if ((long long)nka * N * N * 2 * vv > tc_lb.rows) return CCSD_ERR_INVALID;
-            h->wplans.push_back(wp);
-            Step st{8, (int)h->wplans.size() - 1, "ladder_W", 0.0,
-                    (8.0 + 32.0) * (double)nka * N * N * vv * vv};
-            st.mode = 2;
-            h->seq.push_back(st);
-            std::vector<int> ra, rb, cc; std::vector<long long> oc;
-            for (int ka = ka0; ka < ka0 + nka; ++ka) for (int kb = 0; kb < N; ++kb) {
-                const int S = kg.k4(ka, kb, 0);
-                for (int ke = 0; ke < N; ++ke) {
-                    ra.push_back((int)((((long long)S * N + ke) * N) * oo));
-                    rb.push_back((int)((((long long)(ka - ka0) * N + kb) * N + ke) * 2 * vv));
-                }
-                for (int ki = 0; ki < N; ++ki)
-                    for (int ij = 0; ij < (int)oo; ++ij) oc.push_back(blk(S2, ki, kg.k4(S, 0, ki), ka) + ij * vv);
-            }
-            cc = tab({{(int)vv, 1}});
-            if ((rc = add_tc(h, al, tc_la, tc_lb, B_R2, M, (int)(2 * vv), nka * N, N, ra, rb, oc, cc, 0.5, 3))) return rc;
         }
     }
     h->cur_name = "ring_W_t1";
@@ -1180,7 +1218,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         for (int kn = 0; kn < N; ++kn) for (int kf = 0; kf < N; ++kf) for (int kx = 0; kx < N; ++kx)
             so.push_back(blk(S2, kn, kx, kf));
         if ((rc = add_embed(h, al, B_OOVV, tc_b1, 1, (int)ov, (int)ov, so, tab({{o, o * vv}, {v, v}}),
-                            tab({{o, vv}, {v, 1}}), true))) return rc;
+                            tab({{o, vv}, {v, 1}}), !pooled))) return rc;
         std::vector<int> ra, rb; std::vector<long long> oc;
         for (int kj = 0; kj < N; ++kj) for (int kb = 0; kb < N; ++kb) for (int kn = 0; kn < N; ++kn) {
             const int kf = kg.k4(kn, kb, kj);
@@ -1253,8 +1291,12 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     }
     h->cur_name = "fock_t1_terms";
     // remaining terms under P(ab) and P(ij)
-    {   // ZAB = sum_f t_ij^af F'^{bf}(kb)
-        GemmSpec s; s.a = B_T2; s.b = B_FVVP; s.c = B_ZAB; s.acc = false;
+    // The P(ab)-only terms (call them Zab) and the P(ij)-only terms (Zij) accumulate into
+    // ZR at half weight: Zab is antisymmetric in (i,j) and Zij in (a,b), so
+    // P(ij)P(ab) (Zab/2) = P(ab) Zab and P(ij)P(ab) (Zij/2) = P(ij) Zij, and one permuted
+    // sum finishes all of R2's terms.
+    {   // ZR += 1/2 sum_f t_ij^af F'^{bf}(kb)
+        GemmSpec s; s.a = B_T2; s.b = B_FVVP; s.c = B_ZR; s.ar = 0.5;
         s.M = (int)(oo * v); s.N = v; s.K = v; s.nbatch = N3; s.nchunk = 1;
         for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
             const int kb = kg.k4(ki, kj, ka);
@@ -1265,8 +1307,8 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{(int)(oo * v), v}}); s.colC = tab({{v, 1}});
         if ((rc = G(s))) return rc;
     }
-    {   // ZAB -= sum_r t_r^a <r b||i j> = sum_r t_r^a conj(ooov[ki,kj,ka](i,j,r,b))
-        GemmSpec s; s.a = B_T1; s.b = B_OOOV; s.c = B_ZAB; s.ar = -1.0; s.conjB = true;
+    {   // ZR -= 1/2 sum_r t_r^a <r b||i j> = 1/2 sum_r t_r^a conj(ooov[ki,kj,ka](i,j,r,b))
+        GemmSpec s; s.a = B_T1; s.b = B_OOOV; s.c = B_ZR; s.ar = -0.5; s.conjB = true;
         s.M = v; s.N = (int)(oo * v); s.K = o; s.nbatch = N3; s.nchunk = 1;
         for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
             s.offA.push_back(ka * ov); s.offB.push_back(blk(Sooov, ki, kj, ka)); s.offC.push_back(blk(S2, ki, kj, ka));
@@ -1276,8 +1318,8 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{v, v}}); s.colC = tab({{(int)oo, vv}, {v, 1}});
         if ((rc = G(s))) return rc;
     }
-    {   // ZIJ = - sum_n t_{i n}^{ab} F'_{nj}(kj)
-        GemmSpec s; s.a = B_T2; s.b = B_FOOP; s.c = B_ZIJ; s.acc = false; s.ar = -1.0;
+    {   // ZR -= 1/2 sum_n t_{i n}^{ab} F'_{nj}(kj)
+        GemmSpec s; s.a = B_T2; s.b = B_FOOP; s.c = B_ZR; s.ar = -0.5;
         s.M = (int)(o * vv); s.N = o; s.K = o; s.nbatch = N3; s.nchunk = 1;
         for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
             s.offA.push_back(blk(S2, ki, kj, ka)); s.offB.push_back(kj * oo); s.offC.push_back(blk(S2, ki, kj, ka));
@@ -1287,8 +1329,8 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{o, o * vv}, {(int)vv, 1}}); s.colC = tab({{o, vv}});
         if ((rc = G(s))) return rc;
     }
-    {   // ZIJ += sum_c <a b||c j> t_i^c = - sum_c t_i^c conj(ovvv[kj,ki,ka](j,c,a,b))
-        GemmSpec s; s.a = B_T1; s.b = B_OVVV; s.c = B_ZIJ; s.ar = -1.0; s.conjB = true;
+    {   // ZR += 1/2 sum_c <a b||c j> t_i^c = - 1/2 sum_c t_i^c conj(ovvv[kj,ki,ka](j,c,a,b))
+        GemmSpec s; s.a = B_T1; s.b = B_OVVV; s.c = B_ZR; s.ar = -0.5; s.conjB = true;
         s.M = o; s.N = (int)(o * vv); s.K = v; s.nbatch = N3; s.nchunk = 1;
         for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
             s.offA.push_back(ki * ov); s.offB.push_back(blk(Sovvv, kj, ki, ka)); s.offC.push_back(blk(S2, ki, kj, ka));
@@ -1298,7 +1340,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowC = tab({{o, o * vv}}); s.colC = tab({{o, vv}, {(int)vv, 1}});
         if ((rc = G(s))) return rc;
     }
-    h->seq.push_back({4, 0, "antisym_R2", 0.0, 16.0 * 10.0 * h->n2});
+    h->seq.push_back({4, 0, "antisym_R2", 0.0, 16.0 * 3.0 * h->n2});
     return 0;
 }
 
@@ -1309,7 +1351,8 @@ void set_sizes(ccsd_ctx* h) {
                                 N3 * o * o * v * v, N3 * o * o * v * v, N3 * o * v * v * v, N3 * v * v * v * v,
                                 h->n1, h->n2, h->n1, h->n2, h->n2, h->n2,
                                 N * o * v, N * o * o, N * v * v, N * o * o, N * v * v,
-                                N3 * o * o * o * o, N3 * v * v * v * v, h->n2, N3 * o * o * o * v, N3 * o * o * o * v,
+                                N3 * o * o * o * o, wab_pairs_per_slab(N, v, h->wab_cap_bytes) * N * v * v * v * v,
+                                h->n2, N3 * o * o * o * v, N3 * o * o * o * v,
                                 h->n2, h->n2, h->n2};
     for (int i = 0; i < NBUF; ++i) h->bufsize[i] = sz[i];
 }
@@ -1325,8 +1368,8 @@ int launch_gemm(ccsd_ctx* h, GemmPlan& p) {
     if (p.blocks == 0) return 0;
     GemmArgs g = p.args;
     g.A = h->buf[p.a]; g.B = h->buf[p.b]; g.C = h->buf[p.c]; g.work = h->work;
-    g.A32 = h->fp32 ? h->shadow[p.a] : nullptr;
-    g.B32 = h->fp32 ? h->shadow[p.b] : nullptr;
+    g.A32 = (h->fp32 || h->in32[p.a]) ? h->shadow[p.a] : nullptr;
+    g.B32 = (h->fp32 || h->in32[p.b]) ? h->shadow[p.b] : nullptr;
     dim3 grid((unsigned)p.blocks, (unsigned)g.nsplit);
     if (h->fp32) {
         switch (p.cfg) {
@@ -1356,7 +1399,8 @@ int launch_gemm(ccsd_ctx* h, GemmPlan& p) {
 void launch_embed(ccsd_ctx* h, EmbedPlan& e) {
     EmbedArgs a = e.a;
     a.src = h->buf[e.src];
-    embed_kernel<<<ew_grid((long long)a.nblk * a.R * a.Kc), 256, 0, h->st>>>(a);
+    a.src32 = h->in32[e.src] ? h->shadow[e.src] : nullptr;
+    embed_kernel<<<ew_grid((long long)a.nblk * a.R * (a.Kpad / 2)), 256, 0, h->st>>>(a);
     ++h->launches;
 }
 
@@ -1399,14 +1443,18 @@ void launch_step(ccsd_ctx* h, size_t si) {
             case 0: launch_gemm(h, h->gemms[s.idx]); break;
             case 1: {
                 const CopyPlan& c = h->copies[s.idx];
-                copy_kernel<<<ew_grid(c.n), 256, 0, h->st>>>(h->buf[c.dst], h->buf[c.src], c.n, c.conj);
+                if (h->in32[c.src])
+                    copy_kernel<<<ew_grid(c.n), 256, 0, h->st>>>(h->buf[c.dst], h->shadow[c.src], c.n, c.conj);
+                else
+                    copy_kernel<<<ew_grid(c.n), 256, 0, h->st>>>(h->buf[c.dst], h->buf[c.src], c.n, c.conj);
                 ++h->launches;
                 break;
             }
             case 2: {
                 const PermPlan& pp = h->perms[s.idx];
-                permute4_kernel<<<ew_grid((long long)pp.p.nbatch * pp.p.n0 * pp.p.n1 * pp.p.n2 * pp.p.n3), 256, 0, h->st>>>(
-                    h->buf[pp.dst], h->buf[pp.src], pp.p);
+                const dim3 g = ew_grid((long long)pp.p.nbatch * pp.p.n0 * pp.p.n1 * pp.p.n2 * pp.p.n3);
+                if (h->in32[pp.src]) permute4_kernel<<<g, 256, 0, h->st>>>(h->buf[pp.dst], h->shadow[pp.src], pp.p);
+                else permute4_kernel<<<g, 256, 0, h->st>>>(h->buf[pp.dst], h->buf[pp.src], pp.p);
                 ++h->launches;
                 break;
             }
@@ -1416,7 +1464,7 @@ void launch_step(ccsd_ctx* h, size_t si) {
                 ++h->launches;
                 break;
             case 4:
-                antisym_kernel<<<ew_grid(h->n2), 256, 0, h->st>>>(h->buf[B_R2], h->buf[B_ZAB], h->buf[B_ZIJ], h->buf[B_ZR],
+                antisym_kernel<<<ew_grid(h->n2), 256, 0, h->st>>>(h->buf[B_R2], h->buf[B_ZR],
                                                                    h->kb_of, N, o, v);
                 ++h->launches;
                 break;
@@ -1428,7 +1476,7 @@ void launch_step(ccsd_ctx* h, size_t si) {
             case 10: {
                 WprimeListArgs a = h->wlists[s.idx].a;
                 a.vvvv = h->shadow[B_VVVV]; a.ovvv = h->shadow[B_OVVV]; a.t1 = h->shadow[B_T1];
-                wprime_list_kernel<<<ew_grid((long long)a.nblk * a.nab * a.nef), 256, 0, h->st>>>(a);
+                wprime_list_kernel<<<ew_grid((long long)a.nblk * a.nab * (a.Kpad / 2)), 256, 0, h->st>>>(a);
                 ++h->launches;
                 break;
             }
@@ -1437,13 +1485,6 @@ void launch_step(ccsd_ctx* h, size_t si) {
                                                                              h->bufsize[s.idx]);
                 ++h->launches;
                 break;
-            case 8: {
-                WprimeArgs a = h->wplans[s.idx].a;
-                a.vvvv = h->shadow[B_VVVV]; a.ovvv = h->shadow[B_OVVV]; a.t1 = h->shadow[B_T1];
-                wprime_embed_kernel<<<ew_grid((long long)a.nka * N * N * v * v * v * v), 256, 0, h->st>>>(a);
-                ++h->launches;
-                break;
-            }
         }
 }
 
@@ -1482,14 +1523,6 @@ int run_residual(ccsd_ctx* h) {
     return 0;
 }
 
-int reduce_redot(ccsd_ctx* h, const double2* x, const double2* y, long long n, double* out_host) {
-    redot_partial<<<h->red_blocks, 256, 0, h->st>>>(x, y, n, h->red);
-    final_sum<<<1, 32, 0, h->st>>>(h->red, h->red_blocks, h->red_out);
-    h->launches += 2;
-    CK(cudaMemcpyAsync(out_host, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
-    return 0;
-}
 
 // ================================================================ batched form
 // Many independent problems advance together.  Their plans have the same
@@ -1583,8 +1616,8 @@ int batch_build_groups(ccsd_batch* B, int fp32, const std::vector<int>& cfgs) {
                 bg.split_members.push_back(i);
             }
             a.A = h->buf[p.a]; a.B = h->buf[p.b]; a.C = h->buf[p.c]; a.work = h->work;
-            a.A32 = fp32 ? h->shadow[p.a] : nullptr;
-            a.B32 = fp32 ? h->shadow[p.b] : nullptr;
+            a.A32 = (fp32 || h->in32[p.a]) ? h->shadow[p.a] : nullptr;
+            a.B32 = (fp32 || h->in32[p.b]) ? h->shadow[p.b] : nullptr;
             prefix.push_back(tot);
             tot += (long long)tm * tn * a.nbatch * a.nsplit;
             bg.args.push_back(a);
@@ -1709,29 +1742,6 @@ int batch_capture(ccsd_batch* B, int fp32) {
     return 0;
 }
 
-size_t footprint_bytes(const ccsd_config* c, int borrowed);
-
-size_t footprint_bytes(const ccsd_config* c, int borrowed) {
-    const long long N = (long long)c->nk_dims[0] * c->nk_dims[1] * c->nk_dims[2];
-    const long long o = c->nocc, v = c->nvir;
-    const long long N3 = N * N * N;
-    const long long n1 = N * o * v, n2 = N3 * o * o * v * v;
-    long long el = 0;
-    if (!borrowed) el += N * (o * o + v * v + o * v) + N3 * (o * o * o * o + o * o * o * v + 2 * o * o * v * v + o * v * v * v + v * v * v * v);
-    el += 2 * (n1 + n2);                       // amplitudes, residual
-    el += 2 * n2;                              // tau, tau~
-    el += N3 * o * o * o * o;                  // Whh
-    el += N3 * v * v * v * v;                  // Wab
-    el += n2;                                  // Wring
-    el += 2 * N3 * o * o * o * v;              // Q, TT
-    el += 3 * n2;                              // ZAB, ZIJ, ZR
-    el += N * (2 * o * v + 2 * o * o + 2 * v * v);
-    el += 2LL * c->diis_depth * (n1 + n2);     // DIIS history
-    size_t bytes = (size_t)el * 16;
-    bytes += (size_t)64 << 20;                 // tables, split-K partials, reductions (bound)
-    return bytes;
-}
-
 bool valid_cfg(const ccsd_config* c) {
     if (!c) return false;
     for (int i = 0; i < 3; ++i) if (c->nk_dims[i] < 1 || c->nk_dims[i] > 64) return false;
@@ -1739,6 +1749,7 @@ bool valid_cfg(const ccsd_config* c) {
     if (c->precision != CCSD_FP64 && c->precision != CCSD_MIXED) return false;
     if (c->precision == CCSD_MIXED && (c->polish_iters < 0 || c->polish_iters > 100)) return false;
     if (c->diis_depth < 0 || c->diis_depth == 1 || c->diis_depth > 8) return false;
+    if (c->lean != 0 && c->lean != 1) return false;
     const long long N = (long long)c->nk_dims[0] * c->nk_dims[1] * c->nk_dims[2];
     const long long vvvv = (long long)c->nvir * c->nvir * c->nvir * c->nvir;
     if (vvvv * 1 > (1LL << 30)) return false;          // block offsets are 32-bit inside a block
@@ -1750,6 +1761,140 @@ bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Fills a handle whose cfg, grid and sizes are set: inputs (device ones borrowed, host
+// ones copied), amplitudes, work buffers, DIIS history, Fock diagonals, the residual
+// plan and its tables.  With al.dry nothing is allocated, copied or launched and
+// h->owned_bytes ends as the device memory ccsd_create would take (ins may be null).
+int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_dev, int int_dtype) {
+    const long long N = h->N, o = h->o, v = h->v, N3 = N * N * N;
+    const long long sizes[9] = {N * o * o, N * v * v, N * o * v, N3 * o * o * o * o, N3 * o * o * o * v,
+                                N3 * o * o * v * v, N3 * o * o * v * v, N3 * o * v * v * v, N3 * v * v * v * v};
+    for (int i = 0; i < 9; ++i) {
+        const bool c64 = i >= 3 && int_dtype == CCSD_C64;
+        const size_t bytes = (size_t)sizes[i] * (c64 ? 8 : 16);
+        void* d = nullptr;
+        if (on_dev[i]) {
+            d = al.dry ? (void*)(uintptr_t)256 : const_cast<void*>(ins[i]);
+        } else {
+            d = al.get(bytes);
+            if (!d) return al.err;
+            if (!al.dry && cudaMemcpyAsync(d, ins[i], bytes, cudaMemcpyHostToDevice, h->st) != cudaSuccess) return CCSD_ERR_CUDA;
+        }
+        if (c64) { h->shadow[B_FOO_IN + i] = (float2*)d; h->in32[B_FOO_IN + i] = true; }
+        else h->buf[B_FOO_IN + i] = (double2*)d;
+    }
+    auto dalloc = [&](long long n) { return (double2*)al.get((size_t)n * 16); };
+    h->amp = dalloc(h->n1 + h->n2);
+    h->res = dalloc(h->n1 + h->n2);
+    if (!h->amp || !h->res) return al.err;
+    h->buf[B_T1] = h->amp; h->buf[B_T2] = h->amp + h->n1;
+    h->buf[B_R1] = h->res; h->buf[B_R2] = h->res + h->n1;
+    h->buf[B_TAU] = dalloc(h->n2); h->buf[B_TAUT] = dalloc(h->n2);
+    h->buf[B_FOV] = dalloc(N * o * v); h->buf[B_FOO] = dalloc(N * o * o); h->buf[B_FVV] = dalloc(N * v * v);
+    h->buf[B_FOOP] = dalloc(N * o * o); h->buf[B_FVVP] = dalloc(N * v * v);
+    h->buf[B_WHH] = dalloc(N3 * o * o * o * o);
+    h->buf[B_WRING] = dalloc(h->n2);
+    h->buf[B_Q] = dalloc(N3 * o * o * o * v);
+    h->buf[B_TT] = dalloc(N3 * o * o * o * v);
+    h->buf[B_ZR] = dalloc(h->n2);
+    if (al.err) return al.err;
+    if (h->cfg.diis_depth > 0) {
+        // canonical blocks of the DIIS history (t2 antisymmetry, paper Sec. 2)
+        std::vector<int> cblk, cmap((size_t)N3);
+        std::vector<double> cw;
+        std::vector<int> canon((size_t)N3, -1);
+        for (int ki = 0; ki < N; ++ki) for (int kj = ki; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
+            const int kb = h->kg.k4(ki, kj, ka);
+            if (ka > kb) continue;
+            const int f = (int)(((long long)ki * N + kj) * N + ka);
+            canon[(size_t)f] = (int)cblk.size();
+            cblk.push_back(f);
+            cw.push_back((ki < kj ? 2.0 : 1.0) * (ka < kb ? 2.0 : 1.0));
+        }
+        for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
+            const int kb = h->kg.k4(ki, kj, ka);
+            const int sij = ki > kj ? 1 : 0, sab = ka > kb ? 1 : 0;
+            const int c = (int)((((long long)(sij ? kj : ki)) * N + (sij ? ki : kj)) * N + (sab ? kb : ka));
+            if (canon[(size_t)c] < 0) return CCSD_ERR_INVALID;
+            cmap[(size_t)(((long long)ki * N + kj) * N + ka)] = canon[(size_t)c] * 4 + sij * 2 + sab;
+        }
+        h->nc = (long long)cblk.size();
+        h->d_cblk = upload(al, cblk, h->st);
+        h->d_cw = upload(al, cw, h->st);
+        h->d_cmap = upload(al, cmap, h->st);
+        const long long np = h->n1 + h->nc * o * o * v * v;
+        for (int d = 0; d < h->cfg.diis_depth; ++d) {
+            h->hx.push_back(dalloc(np));
+            h->he.push_back(dalloc(np));
+        }
+    }
+    if (al.err) return al.err;
+    h->gram.assign(h->cfg.diis_depth, std::vector<double>(h->cfg.diis_depth, 0.0));
+    if (!al.dry && cudaMemsetAsync(h->amp, 0, (size_t)(h->n1 + h->n2) * 16, h->st) != cudaSuccess) return CCSD_ERR_CUDA;
+
+    // Fock diagonals and the fourth momentum of doubles blocks
+    {
+        std::vector<double> eo((size_t)(N * o)), ev((size_t)(N * v));
+        if (!al.dry) {
+            std::vector<double2> foo((size_t)(N * o * o)), fvv((size_t)(N * v * v));
+            if (cudaMemcpyAsync(foo.data(), h->buf[B_FOO_IN], foo.size() * 16, cudaMemcpyDefault, h->st) != cudaSuccess ||
+                cudaMemcpyAsync(fvv.data(), h->buf[B_FVV_IN], fvv.size() * 16, cudaMemcpyDefault, h->st) != cudaSuccess ||
+                cudaStreamSynchronize(h->st) != cudaSuccess) return CCSD_ERR_CUDA;
+            for (long long k = 0; k < N; ++k) {
+                for (long long i = 0; i < o; ++i) eo[(size_t)(k * o + i)] = foo[(size_t)((k * o + i) * o + i)].x;
+                for (long long a = 0; a < v; ++a) ev[(size_t)(k * v + a)] = fvv[(size_t)((k * v + a) * v + a)].x;
+            }
+            for (double x : eo) for (double y : ev) if (!(x - y < 0.0 || x - y > 0.0)) return CCSD_ERR_INVALID;
+        }
+        h->eo = upload(al, eo, h->st);
+        h->ev = upload(al, ev, h->st);
+        std::vector<int> kb((size_t)N3);
+        for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka)
+            kb[(size_t)(((long long)ki * N + kj) * N + ka)] = h->kg.k4(ki, kj, ka);
+        h->kb_of = upload(al, kb, h->st);
+        if (al.err) return al.err;
+    }
+    set_sizes(h);
+    size_t work_need = 0;
+    int rc = build_plan(h, al, work_need);
+    if (rc) return rc;
+    if (work_need) { h->work = dalloc((long long)work_need); if (!h->work) return al.err; }
+    h->work_elems = work_need;
+    h->red_blocks = 152 * 4;
+    h->red = (double*)al.get(sizeof(double) * h->red_blocks);
+    h->red_out = (double*)al.get(sizeof(double) * 4);
+    h->cred = (double2*)al.get(sizeof(double2) * h->red_blocks);
+    h->cred_out = (double2*)al.get(sizeof(double2) * 2);
+    return al.err;
+}
+
+void init_ctx(ccsd_ctx* h, const ccsd_config* cfg) {
+    h->cfg = *cfg;
+    h->kg.init(cfg->nk_dims);
+    h->N = h->kg.N; h->o = cfg->nocc; h->v = cfg->nvir;
+    if (cfg->lean) {    // W' slabs of about a third of the momentum pairs
+        const long long N = h->N, v = h->v;
+        h->wab_cap_bytes = 16 * N * v * v * v * v * std::max<long long>(1, (N * (N + 1) / 2 + 2) / 3);
+    }
+    h->fp32 = cfg->precision == CCSD_MIXED ? 1 : 0;
+    const long long N = h->N;
+    h->n1 = N * h->o * h->v;
+    h->n2 = N * N * N * h->o * h->o * h->v * h->v;
+}
+
+// Device bytes ccsd_create takes for this config, from a dry run of its setup; 0 on error.
+size_t footprint_bytes(const ccsd_config* c, const bool* on_dev, int int_dtype) {
+    ccsd_ctx* h = new (std::nothrow) ccsd_ctx();
+    if (!h) return 0;
+    init_ctx(h, c);
+    Alloc al{h};
+    al.dry = true;
+    const int rc = setup_handle(h, al, nullptr, on_dev, int_dtype);
+    const size_t b = rc ? 0 : h->owned_bytes;
+    delete h;
+    return b;
 }
 
 }  // namespace
@@ -1793,21 +1938,27 @@ int iter_end(ccsd_ctx* h, int* done, double* max_resid) {
         const int slot = h->diis_next;
         double2* x = h->hx[slot];
         double2* e = h->he[slot];
-        CK(cudaMemcpyAsync(x, h->amp, (size_t)n * 16, cudaMemcpyDeviceToDevice, h->st));
-        update_kernel<<<ew_grid(n), 256, 0, h->st>>>(x, x + h->n1, h->buf[B_R1], h->buf[B_R2],
-                                                     h->eo, h->ev, h->kb_of, h->N, h->o, h->v, e, e + h->n1);
+        const long long blk = (long long)h->o * h->o * h->v * h->v;
+        const long long np = h->n1 + h->nc * blk;
+        diis_pack_update<<<ew_grid(np), 256, 0, h->st>>>(h->amp, h->res, x, e, h->d_cblk, h->nc, h->eo, h->ev,
+                                                         h->kb_of, h->N, h->o, h->v);
         ++h->launches;
         if (h->trace) { cudaEventRecord(h->ev1[tu], h->st); if ((rc = trace_collect(h, tu, tu + 1))) return rc; }
         h->diis_next = (slot + 1) % depth;
         if (h->diis_count < depth) ++h->diis_count;
         const int m = h->diis_count;
         for (int j = 0; j < m; ++j) {
+            redot_w_partial<<<h->red_blocks, 256, 0, h->st>>>(e, h->he[j], h->n1, blk, h->nc, h->d_cw, h->red);
+            final_sum<<<1, 32, 0, h->st>>>(h->red, h->red_blocks, h->red_out + 0);
+            h->launches += 2;
             double d = 0.0;
-            if ((rc = reduce_redot(h, e, h->he[j], n, &d))) return rc;
+            CK(cudaMemcpyAsync(&d, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+            CK(cudaStreamSynchronize(h->st));
             h->gram[slot][j] = h->gram[j][slot] = d;
         }
+        Combo cb{};
         if (m < 2) {
-            CK(cudaMemcpyAsync(h->amp, x, (size_t)n * 16, cudaMemcpyDeviceToDevice, h->st));
+            cb.m = 1; cb.x[0] = x; cb.c[0] = 1.0;
         } else {
             // Pulay: [B -1; -1 0][c; l] = [0; -1], solved by Gaussian elimination with pivoting
             const int S = m + 1;
@@ -1833,12 +1984,11 @@ int iter_end(ccsd_ctx* h, int* done, double* max_resid) {
                 for (int k = r + 1; k < S; ++k) s -= A[(size_t)r * S + k] * xs[k];
                 xs[r] = s / A[(size_t)r * S + r];
             }
-            Combo cb{};
             cb.m = m;
             for (int j = 0; j < m; ++j) { cb.x[j] = h->hx[j]; cb.c[j] = xs[j]; }
-            combo_kernel<<<ew_grid(n), 256, 0, h->st>>>(h->amp, cb, n);
-            ++h->launches;
         }
+        combo_unpack<<<ew_grid(n), 256, 0, h->st>>>(h->amp, cb, h->d_cmap, h->N, h->o, h->v);
+        ++h->launches;
     }
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) { last_err(ce); return CCSD_ERR_CUDA; }
@@ -1892,10 +2042,11 @@ double server_now(const ccsd_server* S) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - S->t0).count();
 }
 
-size_t request_bytes(const ccsd_config& c) {
-    size_t b = footprint_bytes(&c, 0);
-    if (c.precision == CCSD_MIXED) b += b;     // tensor-core operands and complex64 copies (bound)
-    return b;
+size_t request_bytes(const ccsd_config& c, const ccsd_inputs& in) {
+    const void* ins[9] = {in.f_oo, in.f_vv, in.f_ov, in.oooo, in.ooov, in.oovv, in.ovvo, in.ovvv, in.vvvv};
+    bool on_dev[9];
+    for (int i = 0; i < 9; ++i) on_dev[i] = is_device_ptr(ins[i]);
+    return footprint_bytes(&c, on_dev, in.int_dtype);
 }
 
 void server_finish(ccsd_server* S, ServerReq* r, int state) {
@@ -1987,10 +2138,12 @@ void server_loop(ccsd_server* S) {
 
 extern "C" {
 
-int ccsd_footprint(const ccsd_config* cfg, int inputs_on_device, size_t* bytes) {
-    if (!valid_cfg(cfg) || !bytes) return CCSD_ERR_INVALID;
-    *bytes = footprint_bytes(cfg, inputs_on_device);
-    return CCSD_OK;
+int ccsd_footprint(const ccsd_config* cfg, int inputs_on_device, int int_dtype, size_t* bytes) {
+    if (!valid_cfg(cfg) || !bytes || (int_dtype != CCSD_C128 && int_dtype != CCSD_C64)) return CCSD_ERR_INVALID;
+    bool on_dev[9];
+    for (bool& x : on_dev) x = inputs_on_device != 0;
+    *bytes = footprint_bytes(cfg, on_dev, int_dtype);
+    return *bytes ? CCSD_OK : CCSD_ERR_INVALID;
 }
 
 
@@ -1998,12 +2151,7 @@ int ccsd_plan_check(const ccsd_config* cfg, long long* n_launches, size_t* table
     if (!valid_cfg(cfg)) return CCSD_ERR_INVALID;
     ccsd_ctx* h = new (std::nothrow) ccsd_ctx();
     if (!h) return CCSD_ERR_OOM;
-    h->cfg = *cfg;
-    h->kg.init(cfg->nk_dims);
-    h->N = h->kg.N; h->o = cfg->nocc; h->v = cfg->nvir;
-    const long long N = h->N;
-    h->n1 = N * h->o * h->v;
-    h->n2 = N * N * N * h->o * h->o * h->v * h->v;
+    init_ctx(h, cfg);
     set_sizes(h);
     Alloc al{h};
     al.dry = true;
@@ -2032,8 +2180,8 @@ int ccsd_tc_selftest(int M, int Ncols, int K, int nterms, unsigned long long see
     auto rnd = [&]() { x = x * 6364136223846793005ULL + 1442695040888963407ULL; return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0; };
     for (auto& z : hA) { z.x = rnd(); z.y = rnd(); }
     for (auto& z : hB) { z.x = rnd(); z.y = rnd(); }
-    h->buf[B_ZAB] = upload(al, hA, h->st); h->bufsize[B_ZAB] = nA;
-    h->buf[B_ZIJ] = upload(al, hB, h->st); h->bufsize[B_ZIJ] = nB;
+    h->buf[B_STA] = upload(al, hA, h->st); h->bufsize[B_STA] = nA;
+    h->buf[B_STB] = upload(al, hB, h->st); h->bufsize[B_STB] = nB;
     h->buf[B_ZR] = (double2*)al.get((size_t)nC * 16); h->bufsize[B_ZR] = nC;
     h->buf[B_TAU] = (double2*)al.get((size_t)nC * 16); h->bufsize[B_TAU] = nC;
     h->tc_err = (int*)al.get(sizeof(int));
@@ -2042,7 +2190,7 @@ int ccsd_tc_selftest(int M, int Ncols, int K, int nterms, unsigned long long see
         cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
     // reference: FP64 SIMT engine, C_ref = A B^T
     size_t work_need = 0;
-    GemmSpec g; g.a = B_ZAB; g.b = B_ZIJ; g.c = B_TAU; g.acc = false;
+    GemmSpec g; g.a = B_STA; g.b = B_STB; g.c = B_TAU; g.acc = false;
     g.M = M; g.N = Ncols; g.K = K; g.nbatch = 1; g.nchunk = 1;
     g.offA = {0}; g.offB = {0}; g.offC = {0};
     g.rowA = tab({{M, K}}); g.colA = tab({{K, 1}});
@@ -2055,8 +2203,8 @@ int ccsd_tc_selftest(int M, int Ncols, int K, int nterms, unsigned long long see
     const int kpad = (2 * K + TC_BK - 1) / TC_BK * TC_BK;
     TcBuf ta{}, tb{};
     if ((rc = tc_alloc(h, al, ta, M, kpad)) || (rc = tc_alloc(h, al, tb, 2LL * Ncols, kpad))) return fail(rc);
-    if ((rc = add_embed(h, al, B_ZAB, ta, 0, M, K, {0}, tab({{M, K}}), tab({{K, 1}}), false)) ||
-        (rc = add_embed(h, al, B_ZIJ, tb, 1, Ncols, K, {0}, tab({{Ncols, K}}), tab({{K, 1}}), false)))
+    if ((rc = add_embed(h, al, B_STA, ta, 0, M, K, {0}, tab({{M, K}}), tab({{K, 1}}), false)) ||
+        (rc = add_embed(h, al, B_STB, tb, 1, Ncols, K, {0}, tab({{Ncols, K}}), tab({{K, 1}}), false)))
         return fail(rc);
     std::vector<long long> oc;
     for (int m = 0; m < M; ++m) oc.push_back((long long)m * Ncols);
@@ -2087,92 +2235,20 @@ int ccsd_tc_selftest(int M, int Ncols, int K, int nterms, unsigned long long see
 int ccsd_create(const ccsd_config* cfg, const ccsd_inputs* in, void* stream, ccsd_t* out) {
     if (!out) return CCSD_ERR_INVALID;
     *out = nullptr;
-    if (!valid_cfg(cfg) || !in || in->int_dtype != CCSD_C128) return CCSD_ERR_INVALID;
+    if (!valid_cfg(cfg) || !in || (in->int_dtype != CCSD_C128 && in->int_dtype != CCSD_C64)) return CCSD_ERR_INVALID;
     const void* ins[9] = {in->f_oo, in->f_vv, in->f_ov, in->oooo, in->ooov, in->oovv, in->ovvo, in->ovvv, in->vvvv};
     for (const void* p : ins) if (!p) return CCSD_ERR_INVALID;
+    bool on_dev[9];
+    for (int i = 0; i < 9; ++i) on_dev[i] = is_device_ptr(ins[i]);
     ccsd_ctx* h = new (std::nothrow) ccsd_ctx();
     if (!h) return CCSD_ERR_OOM;
-    h->cfg = *cfg;
-    h->kg.init(cfg->nk_dims);
-    h->N = h->kg.N; h->o = cfg->nocc; h->v = cfg->nvir;
+    init_ctx(h, cfg);
     h->st = (cudaStream_t)stream;
-    h->fp32 = cfg->precision == CCSD_MIXED ? 1 : 0;
-    const long long N = h->N, o = h->o, v = h->v, N3 = N * N * N;
-    h->n1 = N * o * v;
-    h->n2 = N3 * o * o * v * v;
     Alloc al{h};
     auto fail = [&](int code) { ccsd_destroy(h); return code; };
-
-    // inputs: borrow device pointers, copy host ones
-    const long long sizes[9] = {N * o * o, N * v * v, N * o * v, N3 * o * o * o * o, N3 * o * o * o * v,
-                                N3 * o * o * v * v, N3 * o * o * v * v, N3 * o * v * v * v, N3 * v * v * v * v};
-    for (int i = 0; i < 9; ++i) {
-        if (is_device_ptr(ins[i])) {
-            h->buf[B_FOO_IN + i] = (double2*)ins[i];
-        } else {
-            double2* d = (double2*)al.get((size_t)sizes[i] * 16);
-            if (!d) return fail(al.err);
-            if (cudaMemcpyAsync(d, ins[i], (size_t)sizes[i] * 16, cudaMemcpyHostToDevice, h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
-            h->buf[B_FOO_IN + i] = d;
-        }
-    }
-    auto dalloc = [&](long long n) { return (double2*)al.get((size_t)n * 16); };
-    h->amp = dalloc(h->n1 + h->n2);
-    h->res = dalloc(h->n1 + h->n2);
-    if (!h->amp || !h->res) return fail(al.err);
-    h->buf[B_T1] = h->amp; h->buf[B_T2] = h->amp + h->n1;
-    h->buf[B_R1] = h->res; h->buf[B_R2] = h->res + h->n1;
-    h->buf[B_TAU] = dalloc(h->n2); h->buf[B_TAUT] = dalloc(h->n2);
-    h->buf[B_FOV] = dalloc(N * o * v); h->buf[B_FOO] = dalloc(N * o * o); h->buf[B_FVV] = dalloc(N * v * v);
-    h->buf[B_FOOP] = dalloc(N * o * o); h->buf[B_FVVP] = dalloc(N * v * v);
-    h->buf[B_WHH] = dalloc(N3 * o * o * o * o);
-    h->buf[B_WAB] = dalloc(N3 * v * v * v * v);
-    h->buf[B_WRING] = dalloc(h->n2);
-    h->buf[B_Q] = dalloc(N3 * o * o * o * v);
-    h->buf[B_TT] = dalloc(N3 * o * o * o * v);
-    h->buf[B_ZAB] = dalloc(h->n2); h->buf[B_ZIJ] = dalloc(h->n2); h->buf[B_ZR] = dalloc(h->n2);
-    if (al.err) return fail(al.err);
-    for (int d = 0; d < cfg->diis_depth; ++d) {
-        h->hx.push_back(dalloc(h->n1 + h->n2));
-        h->he.push_back(dalloc(h->n1 + h->n2));
-    }
-    if (al.err) return fail(al.err);
-    h->gram.assign(cfg->diis_depth, std::vector<double>(cfg->diis_depth, 0.0));
-    if (cudaMemsetAsync(h->amp, 0, (size_t)(h->n1 + h->n2) * 16, h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
-
-    // Fock diagonals and the fourth momentum of doubles blocks
-    {
-        std::vector<double2> foo((size_t)(N * o * o)), fvv((size_t)(N * v * v));
-        if (cudaMemcpyAsync(foo.data(), h->buf[B_FOO_IN], foo.size() * 16, cudaMemcpyDefault, h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
-        if (cudaMemcpyAsync(fvv.data(), h->buf[B_FVV_IN], fvv.size() * 16, cudaMemcpyDefault, h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
-        if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
-        std::vector<double> eo((size_t)(N * o)), ev((size_t)(N * v));
-        for (long long k = 0; k < N; ++k) {
-            for (long long i = 0; i < o; ++i) eo[(size_t)(k * o + i)] = foo[(size_t)((k * o + i) * o + i)].x;
-            for (long long a = 0; a < v; ++a) ev[(size_t)(k * v + a)] = fvv[(size_t)((k * v + a) * v + a)].x;
-        }
-        for (double x : eo) for (double y : ev) if (!(x - y < 0.0 || x - y > 0.0)) return fail(CCSD_ERR_INVALID);
-        h->eo = upload(al, eo, h->st);
-        h->ev = upload(al, ev, h->st);
-        std::vector<int> kb((size_t)N3);
-        for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka)
-            kb[(size_t)(((long long)ki * N + kj) * N + ka)] = h->kg.k4(ki, kj, ka);
-        h->kb_of = upload(al, kb, h->st);
-        if (al.err) return fail(al.err);
-    }
-    set_sizes(h);
-    size_t work_need = 0;
-    int rc = build_plan(h, al, work_need);
+    int rc = setup_handle(h, al, ins, on_dev, in->int_dtype);
     if (rc) return fail(rc);
-    if (work_need) { h->work = dalloc((long long)work_need); if (!h->work) return fail(al.err); }
-    h->work_elems = work_need;
     for (int ei : h->const_embeds) launch_embed(h, h->embeds[ei]);
-    h->red_blocks = 152 * 4;
-    h->red = (double*)al.get(sizeof(double) * h->red_blocks);
-    h->red_out = (double*)al.get(sizeof(double) * 4);
-    h->cred = (double2*)al.get(sizeof(double2) * h->red_blocks);
-    h->cred_out = (double2*)al.get(sizeof(double2) * 2);
-    if (al.err) return fail(al.err);
     if (cudaMallocHost(&h->norm_host, sizeof(double)) != cudaSuccess) { cudaGetLastError(); h->norm_host = nullptr; return fail(CCSD_ERR_OOM); }
     if (cudaEventCreateWithFlags(&h->ev_norm, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); h->ev_norm = nullptr; return fail(CCSD_ERR_CUDA); }
     if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
@@ -2254,8 +2330,12 @@ int ccsd_set_precision(ccsd_t h, int precision) {
 
 int ccsd_energy(ccsd_t h, double* e_real, double* e_imag) {
     if (!h) return CCSD_ERR_INVALID;
-    energy_partial<<<h->red_blocks, 256, 0, h->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_FOV_IN], h->buf[B_OOVV],
-                                                     h->N, h->o, h->v, h->cred);
+    if (h->in32[B_OOVV])
+        energy_partial<<<h->red_blocks, 256, 0, h->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_FOV_IN], h->shadow[B_OOVV],
+                                                         h->N, h->o, h->v, h->cred);
+    else
+        energy_partial<<<h->red_blocks, 256, 0, h->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_FOV_IN], h->buf[B_OOVV],
+                                                         h->N, h->o, h->v, h->cred);
     final_csum<<<1, 32, 0, h->st>>>(h->cred, h->red_blocks, h->cred_out);
     double2 e;
     CK(cudaMemcpyAsync(&e, h->cred_out, sizeof(double2), cudaMemcpyDeviceToHost, h->st));
@@ -2465,12 +2545,15 @@ int ccsd_server_create(size_t hbm_budget_bytes, int max_slots, ccsd_server_t* ou
 }
 
 int ccsd_submit(ccsd_server_t S, const ccsd_config* cfg, const ccsd_inputs* in, uint64_t* request_id) {
-    if (!S || !cfg || !in || !request_id || !valid_cfg(cfg) || in->int_dtype != CCSD_C128) return CCSD_ERR_INVALID;
+    if (!S || !cfg || !in || !request_id || !valid_cfg(cfg) || (in->int_dtype != CCSD_C128 && in->int_dtype != CCSD_C64))
+        return CCSD_ERR_INVALID;
+    const size_t bytes = request_bytes(*cfg, *in);
+    if (!bytes) return CCSD_ERR_INVALID;
     ServerReq* r = new (std::nothrow) ServerReq();
     if (!r) return CCSD_ERR_OOM;
     r->cfg = *cfg;
     r->in = *in;
-    r->bytes = request_bytes(*cfg);
+    r->bytes = bytes;
     {
         std::lock_guard<std::mutex> lock(S->mu);
         if (S->stop) { delete r; return CCSD_ERR_INVALID; }

@@ -14,6 +14,10 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// Loads of an input element stored complex128 or complex64 (widened exactly).
+__device__ __forceinline__ double2 ldz(const double2* p) { return *p; }
+__device__ __forceinline__ double2 ldz(const float2* p) { const float2 f = *p; return make_double2(f.x, f.y); }
+
 // tau~ = t2 + 1/2 x and tau = t2 + x with
 // x = delta(ki,ka) t_i^a t_j^b - delta(ki,kb) t_i^b t_j^a
 // (paper Sec. 2: 1/4 and 1/2 of P(ab)P(ij) t1 t1, whose four terms pair up).
@@ -48,11 +52,12 @@ __global__ void tau_kernel(const double2* __restrict__ t1, const double2* __rest
 }
 
 // dst = conj(src) or dst = src, n elements
-__global__ void copy_kernel(double2* __restrict__ dst, const double2* __restrict__ src, long long n, int conj)
+template <typename TS>
+__global__ void copy_kernel(double2* __restrict__ dst, const TS* __restrict__ src, long long n, int conj)
 {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
-        double2 s = src[e];
+        double2 s = ldz(src + e);
         if (conj) s.y = -s.y;
         dst[e] = s;
     }
@@ -66,7 +71,8 @@ struct Perm4 {
     int d0, d1, d2, d3, s0, s1, s2, s3;
     int nbatch;
 };
-__global__ void permute4_kernel(double2* __restrict__ dst, const double2* __restrict__ src, const Perm4 p)
+template <typename TS>
+__global__ void permute4_kernel(double2* __restrict__ dst, const TS* __restrict__ src, const Perm4 p)
 {
     const long long blk = (long long)p.n0 * p.n1 * p.n2 * p.n3;
     const long long total = blk * p.nbatch;
@@ -78,15 +84,15 @@ __global__ void permute4_kernel(double2* __restrict__ dst, const double2* __rest
         const int i2 = r % p.n2; r /= p.n2;
         const int i1 = r % p.n1; const int i0 = r / p.n1;
         dst[p.offD[b] + (long long)i0 * p.d0 + (long long)i1 * p.d1 + (long long)i2 * p.d2 + (long long)i3 * p.d3] =
-            src[p.offS[b] + (long long)i0 * p.s0 + (long long)i1 * p.s1 + (long long)i2 * p.s2 + (long long)i3 * p.s3];
+            ldz(src + p.offS[b] + (long long)i0 * p.s0 + (long long)i1 * p.s1 + (long long)i2 * p.s2 + (long long)i3 * p.s3);
     }
 }
 
-// R2 += Zab - Zab(a<->b) + Zij - Zij(i<->j) + Zr - Zr(i<->j) - Zr(a<->b) + Zr(both):
-// the P_-(ab), P_-(ij) and P_-(ij)P_-(ab) of Eq. ori_EqDouble (operator of Sec. 2;
-// swapping an index swaps its momentum too).
-__global__ void antisym_kernel(double2* __restrict__ R2, const double2* __restrict__ Zab,
-                               const double2* __restrict__ Zij, const double2* __restrict__ Zr,
+// R2 += Zr - Zr(i<->j) - Zr(a<->b) + Zr(both): the P_-(ij)P_-(ab) of Eq. ori_EqDouble
+// (operator of Sec. 2; swapping an index swaps its momentum too).  The terms under
+// P_-(ab) or P_-(ij) alone enter Zr at half weight (they are antisymmetric in the
+// other index pair), so this one sum applies all three operators.
+__global__ void antisym_kernel(double2* __restrict__ R2, const double2* __restrict__ Zr,
                                const int* __restrict__ kb_of, int N, int o, int v)
 {
     const long long blk = (long long)o * o * v * v;
@@ -104,11 +110,10 @@ __global__ void antisym_kernel(double2* __restrict__ R2, const double2* __restri
         const long long e_ij = (((long long)kj * N + ki) * N + ka) * blk + (((long long)j * o + i) * v + a) * v + b;
         const long long e_ab = (((long long)ki * N + kj) * N + kb) * blk + (((long long)i * o + j) * v + b) * v + a;
         const long long e_2 = (((long long)kj * N + ki) * N + kb) * blk + (((long long)j * o + i) * v + b) * v + a;
-        const double2 x0 = Zab[e], x1 = Zab[e_ab], y0 = Zij[e], y1 = Zij[e_ij];
         const double2 z0 = Zr[e], z1 = Zr[e_ij], z2 = Zr[e_ab], z3 = Zr[e_2];
         double2 out = R2[e];
-        out.x += x0.x - x1.x + y0.x - y1.x + z0.x - z1.x - z2.x + z3.x;
-        out.y += x0.y - x1.y + y0.y - y1.y + z0.y - z1.y - z2.y + z3.y;
+        out.x += z0.x - z1.x - z2.x + z3.x;
+        out.y += z0.y - z1.y - z2.y + z3.y;
         R2[e] = out;
     }
 }
@@ -184,8 +189,9 @@ __global__ void update_kernel(double2* __restrict__ t1, double2* __restrict__ t2
 
 // Energy partial sums: sum f_ia t_i^a + 1/4 sum <ij||ab> t_ij^ab
 //                    + 1/2 sum_{ki,kj} <i ki j kj||a ki b kj> t_i^a t_j^b.
+template <typename TS>
 __global__ void energy_partial(const double2* __restrict__ t1, const double2* __restrict__ t2,
-                               const double2* __restrict__ fov, const double2* __restrict__ oovv,
+                               const double2* __restrict__ fov, const TS* __restrict__ oovv,
                                int N, int o, int v, double2* __restrict__ part)
 {
     __shared__ double sr[256], si[256];
@@ -200,7 +206,7 @@ __global__ void energy_partial(const double2* __restrict__ t1, const double2* __
             er += p.x; ei += p.y;
         } else {
             const long long f = e - n1;
-            const double2 g = oovv[f];
+            const double2 g = ldz(oovv + f);
             double2 amp = t2[f];
             amp.x *= 0.25; amp.y *= 0.25;
             const long long kk = f / blk;
@@ -281,6 +287,108 @@ __global__ void combo_kernel(double2* __restrict__ out, const Combo cb, long lon
         double r = 0.0, im = 0.0;
         for (int h = 0; h < cb.m; ++h) { const double2 z = cb.x[h][e]; r += cb.c[h] * z.x; im += cb.c[h] * z.y; }
         out[e] = make_double2(r, im);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// DIIS history on canonical momentum blocks.  t2 is antisymmetric under
+// (ki,i) <-> (kj,j) and under (ka,a) <-> (kb,b), so the blocks with ki <= kj and
+// ka <= kb determine all others; history vectors hold t1 followed by those
+// blocks only (about a quarter of t2).  cblk[p] is the full block index of
+// canonical block p, cw[p] the number of blocks it stands for (its weight in the
+// full inner product), cmap[f] = 4 p + 2 swap_ij + swap_ab for every full block f.
+// x = t + R/D and e = R/D on the canonical elements (t1 part first).
+__global__ void diis_pack_update(const double2* __restrict__ amp, const double2* __restrict__ res,
+                                 double2* __restrict__ x_out, double2* __restrict__ e_out,
+                                 const int* __restrict__ cblk, long long nc,
+                                 const double* __restrict__ eo, const double* __restrict__ ev,
+                                 const int* __restrict__ kb_of, int N, int o, int v)
+{
+    const long long n1 = (long long)N * o * v;
+    const long long blk = (long long)o * o * v * v;
+    const long long total = n1 + nc * blk;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long q;
+        double d;
+        if (e < n1) {
+            const int a = (int)(e % v);
+            const int i = (int)((e / v) % o);
+            const int k = (int)(e / ((long long)o * v));
+            d = eo[k * o + i] - ev[k * v + a];
+            q = e;
+        } else {
+            const long long pe = e - n1;
+            const long long f = cblk[pe / blk];
+            int r = (int)(pe % blk);
+            q = n1 + f * blk + r;
+            const int b = r % v; r /= v;
+            const int a = r % v; r /= v;
+            const int j = r % o; const int i = r / o;
+            const int ka = (int)(f % N), kj = (int)((f / N) % N), ki = (int)(f / ((long long)N * N));
+            const int kb = kb_of[f];
+            d = eo[ki * o + i] + eo[kj * o + j] - ev[ka * v + a] - ev[kb * v + b];
+        }
+        const double2 rq = res[q];
+        const double2 step = make_double2(rq.x / d, rq.y / d);
+        const double2 t = amp[q];
+        x_out[e] = make_double2(t.x + step.x, t.y + step.y);
+        e_out[e] = step;
+    }
+}
+
+// Weighted Re <x|y> partial sums over canonical vectors (the full inner product).
+__global__ void redot_w_partial(const double2* __restrict__ x, const double2* __restrict__ y, long long n1,
+                                long long blk, long long nc, const double* __restrict__ cw,
+                                double* __restrict__ part)
+{
+    __shared__ double sm[256];
+    double s = 0.0;
+    const long long n = n1 + nc * blk;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const double2 a = x[e], b = y[e];
+        const double w = e < n1 ? 1.0 : cw[(e - n1) / blk];
+        s += w * (a.x * b.x + a.y * b.y);
+    }
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// amp = sum_h c_h x_h over canonical history vectors, expanded to every block
+// with the antisymmetry signs.
+__global__ void combo_unpack(double2* __restrict__ out, const Combo cb, const int* __restrict__ cmap,
+                             int N, int o, int v)
+{
+    const long long n1 = (long long)N * o * v;
+    const long long blk = (long long)o * o * v * v;
+    const long long total = n1 + (long long)N * N * N * blk;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long src;
+        double sg = 1.0;
+        if (e < n1) {
+            src = e;
+        } else {
+            const long long f = (e - n1) / blk;
+            int r = (int)((e - n1) % blk);
+            const int b = r % v; r /= v;
+            const int a = r % v; r /= v;
+            const int j = r % o; const int i = r / o;
+            const int m = cmap[f];
+            const int sij = (m >> 1) & 1, sab = m & 1;
+            const int i2 = sij ? j : i, j2 = sij ? i : j, a2 = sab ? b : a, b2 = sab ? a : b;
+            src = n1 + (long long)(m >> 2) * blk + (((long long)i2 * o + j2) * v + a2) * v + b2;
+            if (sij != sab) sg = -1.0;
+        }
+        double re = 0.0, im = 0.0;
+        for (int h = 0; h < cb.m; ++h) { const double2 z = cb.x[h][src]; re += cb.c[h] * z.x; im += cb.c[h] * z.y; }
+        out[e] = make_double2(sg * re, sg * im);
     }
 }
 

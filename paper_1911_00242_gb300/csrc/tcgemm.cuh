@@ -320,26 +320,38 @@ namespace ccsdk {
 // embedding, split into TF32-exact big and small parts:
 //   mode 0 (A side): row b*R + r,           columns (2k, 2k+1) = (Re, Im)
 //   mode 1 (B side): rows b*2R + 2r, +1,    columns (2k, 2k+1) = (Re, -Im) / (Im, Re)
-// Row length Kpad >= 2 Kc; the padding columns are zero from allocation.
+// Row length Kpad >= 2 Kc; the padding columns are written as zero, so a buffer
+// can be reused by operands of other shapes.
 struct EmbedArgs {
-    const double2* src; const long long* srcoff; const int* srow; const int* scol;
+    const double2* src; const float2* src32;   // source complex128, or complex64 when src32 is set
+    const long long* srcoff; const int* srow; const int* scol;
     float* big; float* small;
     int nblk, R, Kc, Kpad, mode;
 };
 
 __global__ void embed_kernel(const EmbedArgs e)
 {
-    const long long total = (long long)e.nblk * e.R * e.Kc;
+    const int kh = e.Kpad / 2;                       // column pairs, padding included
+    const long long total = (long long)e.nblk * e.R * kh;
     for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
          x += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(x % e.Kc);
-        const long long br = x / e.Kc;
+        const int k = (int)(x % kh);
+        const long long br = x / kh;
         const int r = (int)(br % e.R);
         const long long b = br / e.R;
-        const double2 z = e.src[e.srcoff[b] + (long long)e.srow[r] + e.scol[k]];
-        float rb, rs, ib, is;
-        split_tf32(z.x, rb, rs);
-        split_tf32(z.y, ib, is);
+        float rb = 0.f, rs = 0.f, ib = 0.f, is = 0.f;   // padding columns are written as zero
+        if (k >= e.Kc) {
+        } else if (e.src32) {
+            const long long q = e.srcoff[b] + (long long)e.srow[r] + e.scol[k];
+            const float2 z = e.src32[q];
+            split_tf32f(z.x, rb, rs);
+            split_tf32f(z.y, ib, is);
+        } else {
+            const long long q = e.srcoff[b] + (long long)e.srow[r] + e.scol[k];
+            const double2 z = e.src[q];
+            split_tf32(z.x, rb, rs);
+            split_tf32(z.y, ib, is);
+        }
         if (e.mode == 0) {
             const long long o = (b * e.R + r) * (long long)e.Kpad + 2LL * k;
             e.big[o] = rb; e.big[o + 1] = ib;
@@ -361,66 +373,6 @@ __global__ void embed_kernel(const EmbedArgs e)
 
 namespace ccsdk {
 
-// Fused ladder operand: W'^{abef} = <ab||ef> + sum_r t_r^b(kb) <r kb a ka||e ke f kf>
-//                                           - sum_r t_r^a(ka) <r ka b kb||e ke f kf>
-// (the ovvv form of -P(ab) t_r^b <a r||e f>), written straight into the B-side
-// embedding of the tensor-core GEMM for the k_a slab [ka0, ka0 + nka):
-//   rows (((ka - ka0) N + kb) N + ke) 2v^2 + 2(a v + b) + s, columns 2(e v + f) + r.
-// Everything runs in FP32 on complex64 copies of the integrals and of t1.
-struct WprimeArgs {
-    const float2* vvvv; const float2* ovvv; const float2* t1;   // complex64 copies
-    float* big; float* small;
-    int N, o, v, ka0, nka, Kpad;
-};
-
-__global__ void wprime_embed_kernel(const WprimeArgs w)
-{
-    const int N = w.N, o = w.o, v = w.v;
-    const long long vv = (long long)v * v, v4 = vv * vv;
-    const long long total = (long long)w.nka * N * N * v4;
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
-         x += (long long)gridDim.x * blockDim.x) {
-        const long long el = x % v4;
-        const long long bl = x / v4;                  // slab-local block ((ka - ka0) N + kb) N + ke
-        const int ke = (int)(bl % N);
-        const int kb = (int)((bl / N) % N);
-        const int ka = w.ka0 + (int)(bl / ((long long)N * N));
-        const int ef = (int)(el % vv);
-        const int ab = (int)(el / vv);
-        const int a = ab / v, b = ab % v;
-        const long long blk_ab = ((long long)ka * N + kb) * N + ke;   // vvvv / ovvv[ka,kb,ke]
-        const long long blk_ba = ((long long)kb * N + ka) * N + ke;   // ovvv[kb,ka,ke]
-        const float2 g = w.vvvv[blk_ab * v4 + el];
-        float sr = 0.f, si = 0.f;
-        const long long ov3 = (long long)o * v * vv;
-        for (int r = 0; r < o; ++r) {
-            // + t_r^b(kb) ovvv[kb,ka,ke](r,a,e,f)
-            const float2 tb = w.t1[((long long)kb * o + r) * v + b];
-            const float2 p = w.ovvv[blk_ba * ov3 + ((long long)r * v + a) * vv + ef];
-            sr = fmaf(tb.x, p.x, fmaf(-tb.y, p.y, sr));
-            si = fmaf(tb.x, p.y, fmaf(tb.y, p.x, si));
-            // - t_r^a(ka) ovvv[ka,kb,ke](r,b,e,f)
-            const float2 ta = w.t1[((long long)ka * o + r) * v + a];
-            const float2 q = w.ovvv[blk_ab * ov3 + ((long long)r * v + b) * vv + ef];
-            sr = fmaf(-ta.x, q.x, fmaf(ta.y, q.y, sr));
-            si = fmaf(-ta.x, q.y, fmaf(-ta.y, q.x, si));
-        }
-        float rb, rs, ib, is;
-        split_tf32f(g.x + sr, rb, rs);
-        split_tf32f(g.y + si, ib, is);
-        const long long o0 = (bl * 2 * vv + 2LL * ab) * (long long)w.Kpad + 2LL * ef;
-        const long long o1 = o0 + w.Kpad;
-        w.big[o0] = rb; w.big[o0 + 1] = -ib;
-        w.big[o1] = ib; w.big[o1 + 1] = rb;
-        w.small[o0] = rs; w.small[o0 + 1] = -is;
-        w.small[o1] = is; w.small[o1 + 1] = rs;
-    }
-}
-
-}  // namespace ccsdk
-
-namespace ccsdk {
-
 // dst = (complex64) src, n elements
 __global__ void to_c64_kernel(float2* __restrict__ dst, const double2* __restrict__ src, long long n)
 {
@@ -435,10 +387,14 @@ __global__ void to_c64_kernel(float2* __restrict__ dst, const double2* __restric
 
 namespace ccsdk {
 
-// W' embedding for the antisymmetry-packed tensor-core ladder: output block bi
-// is the momentum triple (ka, kb, ke) = blk[3 bi .. 3 bi + 2]; its rows are the
-// listed (a, b) pairs (2 per pair, B-side embedding) and its columns the listed
-// (e, f) pairs:  rows bi 2 nab + 2 ai + s, columns 2 ei + r.
+// Ladder operand W'^{abef} = <ab||ef> + sum_r t_r^b(kb) <r kb a ka||e ke f kf>
+//                             - sum_r t_r^a(ka) <r ka b kb||e ke f kf>
+// (the ovvv form of -P(ab) t_r^b <a r||e f>), formed in FP32 from complex64
+// integrals and t1 and written straight into the B-side embedding of the
+// antisymmetry-packed tensor-core ladder: output block bi is the momentum triple
+// (ka, kb, ke) = blk[3 bi .. 3 bi + 2]; its rows are the listed (a, b) pairs
+// (2 per pair) and its columns the listed (e, f) pairs:
+// rows bi 2 nab + 2 ai + s, columns 2 ei + r; padding columns are written as zero.
 struct WprimeListArgs {
     const float2* vvvv; const float2* ovvv; const float2* t1;
     float* big; float* small;
@@ -450,13 +406,21 @@ __global__ void wprime_list_kernel(const WprimeListArgs w)
 {
     const int N = w.N, o = w.o, v = w.v;
     const long long vv = (long long)v * v, v4 = vv * vv, ov3 = (long long)o * v * vv;
-    const long long per = (long long)w.nab * w.nef;
+    const int kh = w.Kpad / 2;                       // column pairs, padding included
+    const long long per = (long long)w.nab * kh;
     const long long total = (long long)w.nblk * per;
     for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
          x += (long long)gridDim.x * blockDim.x) {
         const long long bi = x / per;
         const int r0 = (int)(x % per);
-        const int ai = r0 / w.nef, ei = r0 % w.nef;
+        const int ai = r0 / kh, ei = r0 % kh;
+        const long long o0 = (bi * 2 * w.nab + 2LL * ai) * (long long)w.Kpad + 2LL * ei;
+        const long long o1 = o0 + w.Kpad;
+        if (ei >= w.nef) {                           // padding columns
+            w.big[o0] = 0.f; w.big[o0 + 1] = 0.f; w.big[o1] = 0.f; w.big[o1 + 1] = 0.f;
+            w.small[o0] = 0.f; w.small[o0 + 1] = 0.f; w.small[o1] = 0.f; w.small[o1 + 1] = 0.f;
+            continue;
+        }
         const int ka = w.blk[3 * bi], kb = w.blk[3 * bi + 1], ke = w.blk[3 * bi + 2];
         const int ab = w.abl[ai], ef = w.efl[ei];
         const int a = ab / v, b = ab % v;
@@ -477,8 +441,6 @@ __global__ void wprime_list_kernel(const WprimeListArgs w)
         float rb, rs, ib, is;
         split_tf32f(g.x + sr, rb, rs);
         split_tf32f(g.y + si, ib, is);
-        const long long o0 = (bi * 2 * w.nab + 2LL * ai) * (long long)w.Kpad + 2LL * ei;
-        const long long o1 = o0 + w.Kpad;
         w.big[o0] = rb; w.big[o0 + 1] = -ib;
         w.big[o1] = ib; w.big[o1 + 1] = rb;
         w.small[o0] = rs; w.small[o0 + 1] = -is;

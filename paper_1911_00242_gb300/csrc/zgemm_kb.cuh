@@ -21,7 +21,8 @@
 // and float (the mixed form's CUDA-core contractions: operands are read from
 // complex64 copies where the plan has them, otherwise rounded from complex128
 // on load; products accumulate in FP32 and the epilogue adds alpha * acc into
-// the FP64 result).  On GB300 a double->float conversion issues on the slow
+// the FP64 result).  Integrals stored complex64 are read through A32/B32 by
+// both; the double instance widens them exactly.  On GB300 a double->float conversion issues on the slow
 // FP64 pipe, so the complex64 copies matter for throughput, not only bytes.
 #pragma once
 #include <cuda_runtime.h>
@@ -32,7 +33,7 @@ namespace ccsdk {
 struct GemmArgs {
     const double2* A; const long long* offA; const int* rowA; const int* colA;
     const double2* B; const long long* offB; const int* rowB; const int* colB;
-    const float2* A32; const float2* B32;   // complex64 copies of A / B, used instead when set
+    const float2* A32; const float2* B32;   // complex64 A / B (copies, or inputs stored so), used instead when set
     double2* C;       const long long* offC; const int* rowC; const int* colC;
     double2* work;    // split partials [nsplit][nbatch][M*N] when nsplit > 1
     const int* nchunk_b;   // per-batch chunk count (<= nchunk), or null for nchunk everywhere
@@ -78,10 +79,10 @@ __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long lon
     for (int c = c_begin; c < c_end; ++c) {
         const long long oa = g.offA[b * g.nchunk + c];
         const long long ob = g.offB[b * g.nchunk + c];
-        const double2* Ab = g.A + oa;
-        const double2* Bb = g.B + ob;
         const float2* Ab32 = g.A32 ? g.A32 + oa : nullptr;
         const float2* Bb32 = g.B32 ? g.B32 + ob : nullptr;
+        const double2* Ab = Ab32 ? nullptr : g.A + oa;
+        const double2* Bb = Bb32 ? nullptr : g.B + ob;
         for (int k0 = 0; k0 < g.K; k0 += BK) {
             for (int e = tid; e < BM * BK; e += NT) {
                 const int mm = e % BM, kk = e / BM;

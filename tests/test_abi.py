@@ -45,10 +45,29 @@ def test_strerror_and_invalid_config_without_gpu(libpath):
     assert lib.ccsd_strerror(-1).startswith(b"invalid")
     cfg = binding.make_config((0, 1, 1), 2, 3)
     n = ctypes.c_size_t(0)
-    assert lib.ccsd_footprint(ctypes.byref(cfg), 1, ctypes.byref(n)) == binding.CCSD_ERR_INVALID
+    assert lib.ccsd_footprint(ctypes.byref(cfg), 1, binding.CCSD_C128, ctypes.byref(n)) == binding.CCSD_ERR_INVALID
     cfg = binding.make_config((2, 2, 2), 8, 32, diis_depth=6)
-    assert lib.ccsd_footprint(ctypes.byref(cfg), 1, ctypes.byref(n)) == 0
-    assert 15e9 < n.value < 30e9
+    assert lib.ccsd_footprint(ctypes.byref(cfg), 1, 7, ctypes.byref(n)) == binding.CCSD_ERR_INVALID
+    assert lib.ccsd_footprint(ctypes.byref(cfg), 1, binding.CCSD_C128, ctypes.byref(n)) == 0
+    # the t2-sized arrays alone: amplitudes, residual, tau, tau~, W~_ring, the permuted
+    # sum, plus 2 x 6 DIIS vectors over t1 and the canonical blocks (ki <= kj, ka <= kb)
+    # of t2 (16 bytes per element)
+    N, o, v = 8, 8, 32
+    n1, n2 = N * o * v, N ** 3 * o * o * v * v
+    c = [(x, y, z) for x in range(2) for y in range(2) for z in range(2)]
+    ks = lambda a, b, d: tuple((a[i] + b[i] - d[i]) % 2 for i in range(3))
+    nc = sum(1 for ki in range(N) for kj in range(ki, N) for ka in range(N)
+             if ka <= c.index(ks(c[ki], c[kj], c[ka])))
+    floor = (6 * n2 + 12 * (n1 + nc * o * o * v * v)) * 16
+    assert floor < n.value < floor + 8e9
+    borrowed = n.value
+    # copied inputs add the integral bytes: complex128, or half of them as complex64
+    ints = N ** 3 * (o ** 4 + o ** 3 * v + 2 * o * o * v * v + o * v ** 3 + v ** 4)
+    m = ctypes.c_size_t(0)
+    assert lib.ccsd_footprint(ctypes.byref(cfg), 0, binding.CCSD_C128, ctypes.byref(m)) == 0
+    assert abs(m.value - borrowed - 16 * ints) < 1e6
+    assert lib.ccsd_footprint(ctypes.byref(cfg), 0, binding.CCSD_C64, ctypes.byref(m)) == 0
+    assert abs(m.value - borrowed - 8 * ints) < 1e6
     h = ctypes.c_void_p()
     assert lib.ccsd_create(ctypes.byref(cfg), None, None, ctypes.byref(h)) == binding.CCSD_ERR_INVALID
 
@@ -70,28 +89,31 @@ def _load_fresh(path):
         binding._lib = saved
 
 
+@pytest.mark.parametrize("lean", [0, 1])
 @pytest.mark.parametrize("grid,o,v", [((1, 1, 1), 3, 5), ((2, 1, 1), 2, 3), ((3, 2, 1), 5, 7),
                                       ((4, 1, 1), 4, 8), ((2, 2, 2), 8, 32), ((3, 3, 3), 8, 24),
                                       ((2, 2, 2), 1, 2)])
-def test_plan_indices_in_bounds(libpath, grid, o, v):
+def test_plan_indices_in_bounds(libpath, grid, o, v, lean):
     """Every launch of the residual plan stays inside its buffers (host-side check)."""
     from paper_1911_00242_gb300 import binding
     lib = binding.load(libpath)
-    cfg = binding.make_config(grid, o, v)
+    cfg = binding.make_config(grid, o, v, lean=lean)
     n = ctypes.c_longlong(0)
     tb = ctypes.c_size_t(0)
     assert lib.ccsd_plan_check(ctypes.byref(cfg), ctypes.byref(n), ctypes.byref(tb)) == 0
-    assert 40 <= n.value <= 80
+    assert 40 <= n.value <= 120      # the ladder runs in W' slabs on large grids
 
 
+@pytest.mark.parametrize("lean", [0, 1])
 @pytest.mark.parametrize("grid,o,v", [((1, 1, 1), 3, 5), ((2, 1, 1), 2, 3), ((3, 2, 1), 5, 7),
                                       ((4, 1, 1), 4, 8), ((2, 2, 2), 8, 32), ((3, 3, 3), 8, 24),
-                                      ((2, 2, 2), 1, 2), ((2, 2, 1), 8, 32)])
-def test_mixed_plan_indices_in_bounds(libpath, grid, o, v):
-    """The mixed form's plan, including the tensor-core GEMMs and operand embeddings."""
+                                      ((2, 2, 2), 1, 2), ((2, 2, 1), 8, 32), ((3, 1, 1), 2, 1)])
+def test_mixed_plan_indices_in_bounds(libpath, grid, o, v, lean):
+    """The mixed form's plan, including the tensor-core GEMMs and operand embeddings,
+    in the default and in the lean (pooled operands, chunked ladder) layout."""
     from paper_1911_00242_gb300 import binding
     lib = binding.load(libpath)
-    cfg = binding.make_config(grid, o, v, precision=binding.CCSD_MIXED)
+    cfg = binding.make_config(grid, o, v, precision=binding.CCSD_MIXED, lean=lean)
     n = ctypes.c_longlong(0)
     tb = ctypes.c_size_t(0)
     assert lib.ccsd_plan_check(ctypes.byref(cfg), ctypes.byref(n), ctypes.byref(tb)) == 0

@@ -72,7 +72,7 @@ def test_admission_by_footprint(lib):
     for s in SPECS:
         c = binding.make_config(s.grid, s.nocc, s.nvir)
         n = ctypes.c_size_t(0)
-        assert lib.ccsd_footprint(ctypes.byref(c), 0, ctypes.byref(n)) == 0
+        assert lib.ccsd_footprint(ctypes.byref(c), 0, binding.CCSD_C128, ctypes.byref(n)) == 0
         fp.append(n.value)
     budget = max(fp) + min(fp)                 # at most two at a time
     srv = Server(budget, 8)

@@ -196,3 +196,26 @@ def test_chain_converges_with_and_without_diis():
     assert a["converged"] and b["converged"]
     assert b["iters"] < a["iters"]
     assert abs(a["energies"][-1] - b["energies"][-1]) < 1e-8 * spec.nk
+
+
+@pytest.mark.parametrize("spec", [cs.SynthSpec((2, 2, 1), 2, 3, 61, time_reversal=False, fock_offdiag=0.1),
+                                  cs.SynthSpec((3, 1, 1), 2, 4, 62),
+                                  cs.SynthSpec((2, 1, 1), 3, 2, 63, int_dtype="c64")],
+                         ids=["complex", "real", "c64"])
+def test_block_oracle_equals_full_oracle(spec):
+    """ccsd_k_block (residual at chosen momentum blocks, for grids too large for the
+    full oracle) reproduces ccsd_k.residual block by block; with complex64 inputs it
+    widens each block exactly, as the full oracle does with widened arrays."""
+    from oracle import ccsd_k_block
+    inp = cs.generate(spec)
+    t1, t2 = cs.random_amplitudes(spec, 3)
+    P = ccsd_k.Problem(spec.grid, spec.nocc, spec.nvir, {k: np.asarray(v, np.complex128) for k, v in inp.items()})
+    R1, R2 = ccsd_k.residual(P, t1, t2)
+    B = ccsd_k_block.BlockResidual(ccsd_k_block.BlockProblem(spec.grid, spec.nocc, spec.nvir, inp), t1, t2)
+    N = spec.nk
+    for k in range(N):
+        np.testing.assert_allclose(B.r1(k), R1[k], rtol=0, atol=1e-14)
+    for ki in range(N):
+        for kj in range(N):
+            for ka in range(N):
+                np.testing.assert_allclose(B.r2(ki, kj, ka), R2[ki, kj, ka], rtol=0, atol=1e-14)

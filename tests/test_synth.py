@@ -65,3 +65,38 @@ def test_seeded_and_layout():
     ev = np.real(np.einsum("kaa->ka", a["f_vv"]))
     assert eo.min() >= -1.5 and eo.max() <= -0.5 and ev.min() >= 0.5 and ev.max() <= 2.5
     assert np.all(a["f_ov"] == 0)
+
+
+@pytest.mark.parametrize("spec", [cs.SynthSpec((2, 2, 1), 2, 3, 7, time_reversal=False, fock_offdiag=0.1),
+                                  cs.SynthSpec((3, 1, 1), 2, 4, 3),
+                                  cs.SynthSpec((2, 1, 1), 3, 2, 9, int_dtype="c64")],
+                         ids=["complex", "real", "c64"])
+def test_torch_evaluation_matches_generate(spec):
+    """generate_torch() (the route for grids whose blocks do not fit the host twice) is
+    the same recipe: the same draws, and values equal to generate() up to FFT rounding
+    (complex128), or to one rounding to complex64."""
+    torch = pytest.importorskip("torch")
+    a = cs.generate(spec)
+    b = cs.generate_torch(spec, "cpu")
+    for k in a:
+        y = b[k].numpy()
+        assert y.dtype == a[k].dtype and y.shape == a[k].shape
+        tol = 1e-15 if a[k].dtype == np.complex128 else 2e-9
+        assert np.abs(a[k] - y).max() <= tol, k
+    t1a, t2a = cs.random_amplitudes_slabs(spec, 5)
+    t1b, t2b = cs.random_amplitudes_torch(spec, 5, "cpu")
+    assert np.array_equal(t1a, t1b.numpy()) and np.array_equal(t2a, t2b.numpy())
+
+
+def test_slab_amplitudes_antisymmetric_and_conserving():
+    spec = cs.SynthSpec((3, 2, 1), 2, 3, 13)
+    t1, t2 = cs.random_amplitudes_slabs(spec, 8)
+    N = spec.nk
+    for ki in range(N):
+        for kj in range(N):
+            for ka in range(N):
+                kb = k4(spec.grid, ki, kj, ka)
+                b = t2[ki, kj, ka]
+                np.testing.assert_allclose(b, -t2[kj, ki, ka].transpose(1, 0, 2, 3), rtol=0, atol=1e-16)
+                np.testing.assert_allclose(b, -t2[ki, kj, kb].transpose(0, 1, 3, 2), rtol=0, atol=1e-16)
+    assert np.abs(t2).max() > 0 and np.abs(t1).max() > 0
