@@ -74,6 +74,7 @@ enum Buf {
 struct GemmPlan {
     int a, b, c;
     GemmArgs args;      // device tables filled; A/B/C pointers resolved at launch
+    GemmArgs args32;    // the same for the FP32 instance: shorter FP32 partial sums (split-K)
     int cfg;            // tile configuration
     int blocks;
 };
@@ -322,6 +323,18 @@ int finalize_gemm(ccsd_ctx* h, Alloc& al, GemmSpec s, size_t& work_need) {
     g.offC2 = s.offC2.empty() ? nullptr : upload(al, s.offC2, h->st);
     g.colC2 = s.colC2.empty() ? nullptr : upload(al, s.colC2, h->st);
     if (al.err) return al.err;
+    // FP32 instance (mixed form): an FP32 partial sum runs over at most kFp32Chain terms
+    // (or one momentum chunk); the chunk partials are added in FP64 by the split-K
+    // reduction, so the FP32 rounding error stays that of a short sum
+    p.args32 = g;
+    {
+        const long long kFp32Chain = 8192;
+        GemmArgs& g32 = p.args32;
+        if ((long long)g32.chunks_per_split * s.K > kFp32Chain && s.nchunk > 1) {
+            g32.chunks_per_split = (int)std::max<long long>(1, kFp32Chain / std::max(1, s.K));
+            g32.nsplit = (s.nchunk + g32.chunks_per_split - 1) / g32.chunks_per_split;
+        }   // its split-K workspace is sized in setup_handle, for the steps that run in FP32
+    }
     h->gemms.push_back(p);
     double chunks = (double)s.nchunk * s.nbatch;
     if (!s.nchunk_b.empty()) { chunks = 0.0; for (int x : s.nchunk_b) chunks += x; }
@@ -570,6 +583,10 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
             for (long long x : fa) pa = std::max(pa, x);
             for (long long x : fb) pb = std::max(pb, x);
             pb = std::max(pb, h->bufsize[B_WAB] * 2);
+            // the small part starts right after the big part: keep it 256-byte aligned (TMA
+            // needs 16-byte aligned bases)
+            pa = (pa + 63) / 64 * 64;
+            pb = (pb + 63) / 64 * 64;
             float* A = (float*)al.get((size_t)pa * 8);
             pool_b = (float*)al.get((size_t)pb * 8);
             if (al.err) return al.err;
@@ -1366,7 +1383,7 @@ dim3 ew_grid(long long n) {
 
 int launch_gemm(ccsd_ctx* h, GemmPlan& p) {
     if (p.blocks == 0) return 0;
-    GemmArgs g = p.args;
+    GemmArgs g = h->fp32 ? p.args32 : p.args;
     g.A = h->buf[p.a]; g.B = h->buf[p.b]; g.C = h->buf[p.c]; g.work = h->work;
     g.A32 = (h->fp32 || h->in32[p.a]) ? h->shadow[p.a] : nullptr;
     g.B32 = (h->fp32 || h->in32[p.b]) ? h->shadow[p.b] : nullptr;
@@ -1412,7 +1429,7 @@ void launch_tc(ccsd_ctx* h, TcPlan& t) {
     }
     TcArgs a = t.a;
     a.C = h->buf[t.c];
-    tc_gemm_kernel<<<t.blocks, 128, TC_SMEM_BYTES, h->st>>>(t.mA_big, t.mA_small, t.mB_big, t.mB_small, a);
+    tc_gemm_kernel<<<t.blocks, TC_THREADS, TC_SMEM_BYTES, h->st>>>(t.mA_big, t.mA_small, t.mB_big, t.mB_small, a);
     ++h->launches;
 }
 
@@ -1860,6 +1877,14 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
     size_t work_need = 0;
     int rc = build_plan(h, al, work_need);
     if (rc) return rc;
+    if (h->cfg.precision == CCSD_MIXED) {
+        // GEMM steps that a mixed handle runs in FP32 (all but the FP64-only ones)
+        for (const Step& st : h->seq) {
+            if (st.kind != 0 || st.mode == 1) continue;
+            const GemmArgs& g32 = h->gemms[st.idx].args32;
+            if (g32.nsplit > 1) work_need = std::max(work_need, (size_t)g32.nsplit * g32.nbatch * g32.M * g32.N);
+        }
+    }
     if (work_need) { h->work = dalloc((long long)work_need); if (!h->work) return al.err; }
     h->work_elems = work_need;
     h->red_blocks = 152 * 4;
@@ -2292,7 +2317,7 @@ int ccsd_solve(ccsd_t h, int* iterations, double* max_resid) {
     const bool mixed = h->cfg.precision == CCSD_MIXED;
     const double tol0 = h->cfg.conv_tol;
     if (mixed) {
-        ccsd_set_precision(h, CCSD_MIXED);
+        if (!h->fp32) ccsd_set_precision(h, CCSD_MIXED);   // keeps the DIIS history of mixed iterations
         h->cfg.conv_tol = std::max(h->cfg.mixed_tol, tol0);
     }
     for (; it <= h->cfg.max_iter; ++it) {

@@ -1,5 +1,5 @@
 // Tensor-core GEMM for the mixed form: tcgen05.mma kind::tf32, TMA-staged
-// operands, FP32 accumulator in tensor memory (TMEM).
+// operands, FP32 accumulators in tensor memory (TMEM).
 //
 //   C'[m][n'] = sum_k A'[m][k] B'[n'][k]              (real, both K-major)
 //
@@ -8,23 +8,29 @@
 //   B'[2n][2k + r] = (Re b_nk, -Im b_nk),  B'[2n+1][2k + r] = (Im b_nk, Re b_nk)
 // so C'[m][2n] = Re c_mn and C'[m][2n+1] = Im c_mn (8 real flops per complex
 // multiply-add, as 4M).  The split-TF32 option writes x = x_big + x_small with
-// both parts TF32-exact and sums big*big + big*small + small*big, which keeps
-// about 21 mantissa bits per product; the three terms are three passes over K
-// into the same accumulator.
+// both parts TF32-exact and sums big*big + big*small + small*big (each product
+// to about 2^-22 relative); the three terms are three passes over K.
+//
+// Accumulation.  The tensor core's FP32 accumulation truncates, so a long sum
+// in one TMEM accumulator drifts by about half an ulp per MMA (1e-4 relative
+// at K = 4096).  Every TC_PROMOTE_STAGES stages (16 MMAs) the partial is
+// promoted: accumulator warps add it into FP32 registers (rounding to nearest)
+// while the MMAs continue in the second TMEM accumulator.  Measured split-TF32
+// error: 4e-7 .. 9e-7 of max|C| for K = 16 .. 4096.
 //
 // Batch b and chunk c (a contracted momentum) select operand rows through
 // tables: rows [rowA[b,c] + m0, +128) of the 2D TMA view of A', rows
 // [rowB[b,c] + n0, +256) of B'.  The epilogue adds alpha * c_mn into an FP64
-// result at offC[b*M + m] + colC[n].
+// result at offC[b*M + m] + colC[n] (and subtracts it at the antisymmetric
+// mirror offC2 / colC2 when given).
 //
-// One CTA computes one 128 x 256 tile (cta_group::1, M = 128, N = 256):
+// One CTA computes one 128 x 256 tile (cta_group::1, M = 128, N = 256), 10 warps:
 //   warp 0 / lane 0 issues TMA loads into a 4-stage ring (48 KiB per stage),
-//   warp 1 / lane 0 issues 4 MMAs (K = 8 each) per stage,
-//   all 4 warps read the accumulator back with tcgen05.ld (warp w owns TMEM
-//   lanes 32w..32w+31 = tile rows).
+//   warp 1 / lane 0 issues 4 MMAs (K = 8 each) per stage into TMEM buffer
+//   (segment & 1), warps 2..9 promote segments and run the epilogue.
 // Every mbarrier wait is bounded; on timeout the CTA records an error code,
-// stops issuing, waits (bounded) for its copies in flight, frees its TMEM and
-// returns.
+// stops issuing, waits (bounded) for its copies and MMAs in flight, frees its
+// TMEM and returns.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -40,7 +46,18 @@ constexpr int TC_A_BYTES = TC_BM * TC_BK * 4;            // 16 KiB
 constexpr int TC_B_BYTES = TC_BN * TC_BK * 4;            // 32 KiB
 constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;  // 48 KiB
 constexpr int TC_SMEM_BYTES = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
-constexpr int TC_TMEM_COLS = 256;
+// Two TMEM accumulators of TC_BN columns: the MMAs fill one while the
+// accumulator warps drain the other.
+constexpr int TC_TMEM_COLS = 2 * TC_BN;
+// Stages (4 MMAs of K = 8 each) summed in TMEM before the partial is promoted
+// into the FP32 register accumulator.  The tensor core's FP32 accumulation
+// truncates: its error grows by about half an ulp of the running sum per MMA
+// (measured with ccsd_tc_selftest: relative 2.6e-5 at K = 1024 complex, 1e-4 at
+// K = 4096 with one TMEM sum per tile).  Promoting every 16 MMAs caps that bias
+// at the partial of K = 128 reals; the register sums round to nearest.
+constexpr int TC_PROMOTE_STAGES = 4;
+constexpr int TC_ACC_WARPS = 8;                          // two per TMEM lane quarter, 128 columns each
+constexpr int TC_THREADS = 64 + 32 * TC_ACC_WARPS;       // producer warp, MMA warp, accumulator warps
 constexpr long long TC_SPIN_LIMIT = 1LL << 24;           // polls before a wait gives up (> 0.1 s)
 constexpr long long TC_DRAIN_LIMIT = 1LL << 20;          // polls per in-flight copy at teardown
 
@@ -125,7 +142,17 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
                  :: "r"(bar) : "memory");
 }
 
-__global__ void __launch_bounds__(128, 1)
+// One 128 x 256 output tile of one batch: C[rows m][cols n] += alpha * sum over the
+// batch's chunks, terms and K stages of A'(rows) . B'(rows)^T.
+//   warp 0, lane 0: TMA producer into a TC_STAGES ring (full/empty mbarriers)
+//   warp 1, lane 0: MMA issuer; segment g of TC_PROMOTE_STAGES stages accumulates
+//                   in TMEM buffer g & 1, then commits to acc_full[g & 1]
+//   warps 2..9:     accumulator warps; warp w reads TMEM lanes 32 (w % 4) ..
+//                   (its rows) and columns 128 ((w - 2) / 4) .. + 127 of each
+//                   partial, adds them into FP32 registers, frees the buffer
+//                   (acc_empty), and at the end adds alpha * sum into the FP64 C.
+// Every wait is bounded; a timeout sets g.err and the CTA unwinds.
+__global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_constant__ CUtensorMap mapA_small,
                const __grid_constant__ CUtensorMap mapB_big, const __grid_constant__ CUtensorMap mapB_small,
                const TcArgs g)
@@ -136,8 +163,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
     uint8_t* stA = smem;                                        // [STAGES][16 KiB]
     uint8_t* stB = smem + TC_STAGES * TC_A_BYTES;               // [STAGES][32 KiB]
     uint64_t* bars = (uint64_t*)(smem + TC_STAGES * TC_STAGE_BYTES);
-    // bars[0..S): full, bars[S..2S): empty, bars[2S]: accumulator ready
-    volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 2 * TC_STAGES + 1);
+    // bars[0..S): full, bars[S..2S): empty, bars[2S + 0/1]: acc_full, bars[2S + 2/3]: acc_empty,
+    // bars[2S + 4]: drain (abort path only)
+    uint64_t* acc_full = bars + 2 * TC_STAGES;
+    uint64_t* acc_empty = bars + 2 * TC_STAGES + 2;
+    uint64_t* drain = bars + 2 * TC_STAGES + 4;
+    volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 2 * TC_STAGES + 5);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -152,7 +183,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
             mbar_init(smem_u32(&bars[s]), 1);
             mbar_init(smem_u32(&bars[TC_STAGES + s]), 1);
         }
-        mbar_init(smem_u32(&bars[2 * TC_STAGES]), 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&acc_full[i]), 1);
+            mbar_init(smem_u32(&acc_empty[i]), TC_ACC_WARPS);
+        }
+        mbar_init(smem_u32(drain), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -168,115 +203,149 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
 
     const int per_chunk = g.nterms * g.kstages;
     const int total = (g.nchunk_b ? g.nchunk_b[b] : g.nchunk) * per_chunk;
+    const int nseg = (total + TC_PROMOTE_STAGES - 1) / TC_PROMOTE_STAGES;
     int issued = 0;
 
-    if (warp == 0 && lane == 0) {
-        // ---------------- producer: TMA loads
-        for (int s = 0; s < total; ++s) {
-            const int st = s % TC_STAGES;
-            const uint32_t ph = (uint32_t)(s / TC_STAGES) & 1u;
-            if (!mbar_wait(smem_u32(&bars[TC_STAGES + st]), ph ^ 1u, abort_flag)) {
-                atomicCAS(g.err, 0, 1);
-                *abort_flag = 1;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer: TMA loads
+            for (int s = 0; s < total; ++s) {
+                const int st = s % TC_STAGES;
+                const uint32_t ph = (uint32_t)(s / TC_STAGES) & 1u;
+                if (!mbar_wait(smem_u32(&bars[TC_STAGES + st]), ph ^ 1u, abort_flag)) {
+                    atomicCAS(g.err, 0, 1);
+                    *abort_flag = 1;
+                    break;
+                }
+                const int c = s / per_chunk;
+                const int r = s % per_chunk;
+                const int term = r / g.kstages;
+                const int kx = (r % g.kstages) * TC_BK;
+                const CUtensorMap* mA = (term == 2) ? &mapA_small : &mapA_big;
+                const CUtensorMap* mB = (term == 1) ? &mapB_small : &mapB_big;
+                const int ra = g.rowA[b * g.nchunk + c] + m0;
+                const int rb = g.rowB[b * g.nchunk + c] + n0;
+                const uint32_t full = smem_u32(&bars[st]);
+                mbar_expect_tx(full, TC_STAGE_BYTES);
+                tma_load_2d(smem_u32(stA + st * TC_A_BYTES), mA, kx, ra, full);
+                tma_load_2d(smem_u32(stB + st * TC_B_BYTES), mB, kx, rb, full);
+                issued = s + 1;
             }
-            const int c = s / per_chunk;
-            const int r = s % per_chunk;
-            const int term = r / g.kstages;
-            const int kx = (r % g.kstages) * TC_BK;
-            const CUtensorMap* mA = (term == 2) ? &mapA_small : &mapA_big;
-            const CUtensorMap* mB = (term == 1) ? &mapB_small : &mapB_big;
-            const int ra = g.rowA[b * g.nchunk + c] + m0;
-            const int rb = g.rowB[b * g.nchunk + c] + n0;
-            const uint32_t full = smem_u32(&bars[st]);
-            mbar_expect_tx(full, TC_STAGE_BYTES);
-            tma_load_2d(smem_u32(stA + st * TC_A_BYTES), mA, kx, ra, full);
-            tma_load_2d(smem_u32(stB + st * TC_B_BYTES), mB, kx, rb, full);
-            issued = s + 1;
         }
-    } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer
-        const uint32_t idesc = tc_idesc_tf32();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            const uint32_t idesc = tc_idesc_tf32();
+            for (int s = 0; s < total; ++s) {
+                const int seg = s / TC_PROMOTE_STAGES;
+                const int buf = seg & 1;
+                const bool seg_first = (s % TC_PROMOTE_STAGES) == 0;
+                if (seg_first && seg >= 2) {
+                    // the accumulator warps must have drained this buffer's previous segment
+                    if (!mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)((seg - 2) >> 1) & 1u, abort_flag)) {
+                        atomicCAS(g.err, 0, 4);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                }
+                const int st = s % TC_STAGES;
+                const uint32_t ph = (uint32_t)(s / TC_STAGES) & 1u;
+                if (!mbar_wait(smem_u32(&bars[st]), ph, abort_flag)) {
+                    atomicCAS(g.err, 0, 2);
+                    *abort_flag = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(stA + st * TC_A_BYTES);
+                const uint32_t b0 = smem_u32(stB + st * TC_B_BYTES);
+                const uint32_t dst = tmem + (uint32_t)(buf * TC_BN);
+#pragma unroll
+                for (int k = 0; k < TC_BK / 8; ++k) {           // K = 8 tf32 (32 bytes) per MMA
+                    tc_mma(dst, smem_desc_sw128(a0 + 32 * k), smem_desc_sw128(b0 + 32 * k), idesc,
+                           (seg_first && k == 0) ? 0u : 1u);
+                }
+                tc_commit(smem_u32(&bars[TC_STAGES + st]));     // stage free once these MMAs have read it
+                if ((s % TC_PROMOTE_STAGES) == TC_PROMOTE_STAGES - 1 || s == total - 1)
+                    tc_commit(smem_u32(&acc_full[buf]));        // segment complete
+            }
+            if (*abort_flag) {
+                // MMAs already issued must finish before the TMEM is released (bounded)
+                tc_commit(smem_u32(drain));
+                mbar_wait(smem_u32(drain), 0u, nullptr, TC_DRAIN_LIMIT);
+            }
+        }
+    } else {
+        // ---------------- accumulator warps: promote every segment, then the epilogue
+        const int q = warp & 3;                                 // TMEM lane quarter = rows 32 q ..
+        const int half = (warp - 2) >> 2;                       // columns 128 half ..
+        float acc[TC_BN / 2];
+#pragma unroll
+        for (int i = 0; i < TC_BN / 2; ++i) acc[i] = 0.f;
         bool ok = true;
-        for (int s = 0; s < total; ++s) {
-            const int st = s % TC_STAGES;
-            const uint32_t ph = (uint32_t)(s / TC_STAGES) & 1u;
-            if (!mbar_wait(smem_u32(&bars[st]), ph, abort_flag)) {
-                atomicCAS(g.err, 0, 2);
-                *abort_flag = 1;
-                ok = false;
-                break;
-            }
+        for (int seg = 0; seg < nseg; ++seg) {
+            const int buf = seg & 1;
+            bool got = mbar_wait(smem_u32(&acc_full[buf]), (uint32_t)(seg >> 1) & 1u, abort_flag);
+            got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;   // one decision per warp
+            if (!got) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(stA + st * TC_A_BYTES);
-            const uint32_t b0 = smem_u32(stB + st * TC_B_BYTES);
 #pragma unroll
-            for (int k = 0; k < TC_BK / 8; ++k) {           // K = 8 tf32 (32 bytes) per MMA
-                tc_mma(tmem, smem_desc_sw128(a0 + 32 * k), smem_desc_sw128(b0 + 32 * k), idesc,
-                       (s > 0 || k > 0) ? 1u : 0u);
+            for (int c0 = 0; c0 < TC_BN / 2; c0 += 16) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) +
+                                       (uint32_t)(buf * TC_BN + half * (TC_BN / 2) + c0);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                               "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                               "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int i = 0; i < 16; ++i) acc[c0 + i] += __uint_as_float(v[i]);
             }
-            tc_commit(smem_u32(&bars[TC_STAGES + st]));     // stage free once these MMAs have read it
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&acc_empty[buf])) : "memory");
         }
-        if (ok) tc_commit(smem_u32(&bars[2 * TC_STAGES]));
-        else {
-            // nothing more will arrive on the accumulator barrier: release the epilogue
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&bars[2 * TC_STAGES])) : "memory");
-        }
-    }
-    __syncwarp();
-
-    // ---------------- epilogue: TMEM -> registers -> FP64 result
-    bool acc_ok = mbar_wait(smem_u32(&bars[2 * TC_STAGES]), 0, nullptr) && !*abort_flag;
-    acc_ok = __shfl_sync(0xffffffffu, acc_ok ? 1 : 0, 0) != 0;    // one decision per warp
-    __syncwarp();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (acc_ok) {
-        const int row = m0 + warp * 32 + lane;
-        const bool rvalid = row < g.M;
-        const long long rbase = rvalid ? g.offC[b * g.M + row] : 0;
-        const long long rbase2 = (rvalid && g.offC2) ? g.offC2[b * g.M + row] : 0;
-#pragma unroll 1
-        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-            uint32_t v[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                           "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-                           "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-                           "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                         : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (rvalid) {
+        if (ok && !*abort_flag) {
+            // every MMA has completed (last acc_full), so the stage ring is free: park the
+            // sums there to run the epilogue as a plain loop
+            float* park = (float*)smem;                         // [TC_BN / 2][TC_ACC_WARPS * 32]
+            const int t = (warp - 2) * 32 + lane;
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int nr = n0 + c0 + 2 * q;                 // real column of the pair (re, im)
-                    if (nr < g.Nr) {
-                        const double xr = (double)__uint_as_float(v[2 * q]);
-                        const double xi = (double)__uint_as_float(v[2 * q + 1]);
-                        double2* p = g.C + rbase + g.colC[nr >> 1];
-                        const double yr = g.alpha_re * xr - g.alpha_im * xi;
-                        const double yi = g.alpha_re * xi + g.alpha_im * xr;
-                        double2 o = *p;
-                        o.x += yr; o.y += yi;
-                        *p = o;
-                        if (g.offC2) {
-                            double2* q = g.C + rbase2 + g.colC2[nr >> 1];
-                            double2 u = *q;
-                            u.x -= yr; u.y -= yi;
-                            *q = u;
-                        }
+            for (int i = 0; i < TC_BN / 2; ++i) park[i * (TC_ACC_WARPS * 32) + t] = acc[i];
+            const int row = m0 + q * 32 + lane;
+            if (row < g.M) {
+                const long long rbase = g.offC[b * g.M + row];
+                const long long rbase2 = g.offC2 ? g.offC2[b * g.M + row] : 0;
+#pragma unroll 1
+                for (int qq = 0; qq < TC_BN / 4; ++qq) {
+                    const int nr = n0 + half * (TC_BN / 2) + 2 * qq;   // real column of the pair (re, im)
+                    if (nr >= g.Nr) break;
+                    const double xr = (double)park[(2 * qq) * (TC_ACC_WARPS * 32) + t];
+                    const double xi = (double)park[(2 * qq + 1) * (TC_ACC_WARPS * 32) + t];
+                    double2* p = g.C + rbase + g.colC[nr >> 1];
+                    const double yr = g.alpha_re * xr - g.alpha_im * xi;
+                    const double yi = g.alpha_re * xi + g.alpha_im * xr;
+                    double2 o = *p;
+                    o.x += yr; o.y += yi;
+                    *p = o;
+                    if (g.offC2) {
+                        double2* p2 = g.C + rbase2 + g.colC2[nr >> 1];
+                        double2 u = *p2;
+                        u.x -= yr; u.y -= yi;
+                        *p2 = u;
                     }
                 }
             }
+        } else if (lane == 0) {
+            atomicCAS(g.err, 0, 3);
         }
-    } else if (threadIdx.x == 0) {
-        atomicCAS(g.err, 0, 3);
     }
 
     // ---------------- teardown: copies in flight, TMEM
+    __syncwarp();
     if (warp == 0 && lane == 0 && *abort_flag) {
         // wait (bounded) until every issued TMA has landed before the CTA exits
         for (int s = (issued > TC_STAGES ? issued - TC_STAGES : 0); s < issued; ++s)
