@@ -538,8 +538,12 @@ def main():
     name, calls, tot_ms, fl, by = dom
     avg_s = tot_ms / max(calls, 1) / 1e3
     achieved = fl / avg_s / 1e12 if fl else by / avg_s / 1e9
+    # achieved counts 8 real flops per complex multiply-add (the algorithmic 4M count);
+    # the FP64 engine executes 3M products (3 FMAs = 6 flops), reported as executed_*
     roofline = {"kernel": f"zgemm_kb ({name})", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "executed_tflops": 0.75 * achieved, "executed_frac": 0.75 * achieved / FP64_PEAK_TFLOPS,
+                "complex_product": "3M: 3 FP64 FMAs per complex multiply-add",
                 "peak_source": "recipe nominal FP64 1.25 TFLOP/s (measured DFMA/DMMA probe: 1.01/1.05)",
                 "traffic": load_traffic(name), "flops_per_launch": fl, "launch_ms": avg_s * 1e3}
     iter_flops = flops_per_iteration(spec)

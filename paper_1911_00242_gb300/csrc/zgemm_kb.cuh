@@ -49,25 +49,50 @@ template <typename T> struct Cplx;
 template <> struct Cplx<double> { using V = double2; };
 template <> struct Cplx<float> { using V = float2; };
 
+// Shared-memory staging of one K step: the complex tiles, and for the FP64
+// instance also Re + Im of every element (the third factor of the 3M product).
+template <int BM, int BN, int BK, typename T>
+struct ZgemmSmem {
+    typename Cplx<T>::V A[BK][BM];
+    typename Cplx<T>::V B[BK][BN];
+    T As[BK][BM];
+    T Bs[BK][BN];
+};
+
 // One output tile (tile, batch b, K split) of one GEMM; called by the plain
 // kernel below and by the grouped persistent kernel of the batched form.
+//
+// FP64 instance: 3M complex products.  With a = ar + i ai, b = br + i bi,
+//   t1 = sum ar br,  t2 = sum ai bi,  t3 = sum (ar + ai)(br + bi),
+//   Re c = t1 - t2,  Im c = t3 - t1 - t2,
+// three FP64 FMAs per complex multiply-add instead of four (the sums ar + ai
+// and br + bi are formed once per element when the tile is staged).  The FP32
+// instance keeps the four-product form, whose imaginary part has no
+// cancellation (its operands are already rounded to FP32).
 template <int BM, int BN, int BK, int TM, int TN, typename T>
 __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long long b, int split,
-                                           typename Cplx<T>::V (&As)[BK][BM], typename Cplx<T>::V (&Bs)[BK][BN])
+                                           ZgemmSmem<BM, BN, BK, T>& sm)
 {
     using V = typename Cplx<T>::V;
+    constexpr bool k3M = sizeof(T) == 8;
     constexpr int NT = (BM / TM) * (BN / TN);
     constexpr int TX = BN / TN;
     const int m0 = (tile % g.tiles_m) * BM;
     const int n0 = (tile / g.tiles_m) * BN;
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
+    auto& As = sm.A;
+    auto& Bs = sm.B;
 
-    T cr[TM][TN], ci[TM][TN];
+    // 4M: (cr, ci); 3M: (cr, ci, cs) = (t1, t2, t3)
+    T cr[TM][TN], ci[TM][TN], cs[TM][k3M ? TN : 1];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) { cr[i][j] = T(0); ci[i][j] = T(0); }
+        for (int j = 0; j < TN; ++j) {
+            cr[i][j] = T(0); ci[i][j] = T(0);
+            if (k3M) cs[i][k3M ? j : 0] = T(0);
+        }
 
     const T sa = g.conjA ? T(-1) : T(1);
     const T sb = g.conjB ? T(-1) : T(1);
@@ -94,6 +119,7 @@ __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long lon
                     else { const double2 w = __ldg(Ab + q); v.x = T(w.x); v.y = T(w.y) * sa; }
                 }
                 As[kk][mm] = v;
+                if (k3M) sm.As[kk][mm] = v.x + v.y;
             }
             for (int e = tid; e < BN * BK; e += NT) {
                 const int nn = e % BN, kk = e / BN;
@@ -105,6 +131,7 @@ __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long lon
                     else { const double2 w = __ldg(Bb + q); v.x = T(w.x); v.y = T(w.y) * sb; }
                 }
                 Bs[kk][nn] = v;
+                if (k3M) sm.Bs[kk][nn] = v.x + v.y;
             }
             __syncthreads();
 #pragma unroll
@@ -114,20 +141,46 @@ __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long lon
                 for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
 #pragma unroll
                 for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx * TN + j];
+                if (k3M) {
+                    T sa[TM], sb[TN];
 #pragma unroll
-                for (int i = 0; i < TM; ++i)
+                    for (int i = 0; i < TM; ++i) sa[i] = sm.As[kk][ty * TM + i];
 #pragma unroll
-                    for (int j = 0; j < TN; ++j) {
-                        cr[i][j] = fma(a[i].x, bb[j].x, cr[i][j]);
-                        cr[i][j] = fma(-a[i].y, bb[j].y, cr[i][j]);
-                        ci[i][j] = fma(a[i].x, bb[j].y, ci[i][j]);
-                        ci[i][j] = fma(a[i].y, bb[j].x, ci[i][j]);
-                    }
+                    for (int j = 0; j < TN; ++j) sb[j] = sm.Bs[kk][tx * TN + j];
+#pragma unroll
+                    for (int i = 0; i < TM; ++i)
+#pragma unroll
+                        for (int j = 0; j < TN; ++j) {
+                            cr[i][j] = fma(a[i].x, bb[j].x, cr[i][j]);
+                            ci[i][j] = fma(a[i].y, bb[j].y, ci[i][j]);
+                            cs[i][k3M ? j : 0] = fma(sa[i], sb[j], cs[i][k3M ? j : 0]);
+                        }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < TM; ++i)
+#pragma unroll
+                        for (int j = 0; j < TN; ++j) {
+                            cr[i][j] = fma(a[i].x, bb[j].x, cr[i][j]);
+                            cr[i][j] = fma(-a[i].y, bb[j].y, cr[i][j]);
+                            ci[i][j] = fma(a[i].x, bb[j].y, ci[i][j]);
+                            ci[i][j] = fma(a[i].y, bb[j].x, ci[i][j]);
+                        }
+                }
             }
             __syncthreads();
         }
     }
 
+    if (k3M) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const T t1 = cr[i][j], t2 = ci[i][j];
+                cr[i][j] = t1 - t2;
+                ci[i][j] = cs[i][k3M ? j : 0] - t1 - t2;
+            }
+    }
     if (g.nsplit > 1) {
         double2* W = g.work + ((long long)split * g.nbatch + b) * (long long)g.M * g.N;
 #pragma unroll
@@ -164,11 +217,9 @@ template <int BM, int BN, int BK, int TM, int TN, typename T = double>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 zgemm_kb_kernel(const GemmArgs g)
 {
-    using V = typename Cplx<T>::V;
-    __shared__ V As[BK][BM];
-    __shared__ V Bs[BK][BN];
+    __shared__ ZgemmSmem<BM, BN, BK, T> sm;
     const int ntile = g.tiles_m * g.tiles_n;
-    zgemm_tile<BM, BN, BK, TM, TN, T>(g, blockIdx.x % ntile, blockIdx.x / ntile, blockIdx.y, As, Bs);
+    zgemm_tile<BM, BN, BK, TM, TN, T>(g, blockIdx.x % ntile, blockIdx.x / ntile, blockIdx.y, sm);
 }
 
 // Grouped persistent form (batched solves): one launch covers the same plan
@@ -179,9 +230,7 @@ template <int BM, int BN, int BK, int TM, int TN, typename T = double>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 zgemm_grouped_kernel(const GemmArgs* __restrict__ gs, const long long* __restrict__ prefix, int nmem, long long total)
 {
-    using V = typename Cplx<T>::V;
-    __shared__ V As[BK][BM];
-    __shared__ V Bs[BK][BN];
+    __shared__ ZgemmSmem<BM, BN, BK, T> sm;
     for (long long w = blockIdx.x; w < total; w += gridDim.x) {
         int lo = 0, hi = nmem - 1;
         while (lo < hi) {                       // last member whose prefix <= w
@@ -194,7 +243,7 @@ zgemm_grouped_kernel(const GemmArgs* __restrict__ gs, const long long* __restric
         const long long per_split = ntile * g.nbatch;
         const int split = (int)(local / per_split);
         const long long r = local % per_split;
-        zgemm_tile<BM, BN, BK, TM, TN, T>(g, (int)(r % ntile), r / ntile, split, As, Bs);
+        zgemm_tile<BM, BN, BK, TM, TN, T>(g, (int)(r % ntile), r / ntile, split, sm);
     }
 }
 
