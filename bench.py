@@ -189,8 +189,13 @@ def run_mixed(args, spec, dev, depth, local, fp64_solve, fp64_ms_per_iter):
     bf16 = peaks.get("bf16_tflops")
     peak = bf16 * TF32_NOMINAL_RATIO if bf16 else 1900.0 * TF32_NOMINAL_RATIO
     achieved = fl / avg_s / 1e12
+    summ = {}
+    for st in steps:
+        if st[1]:
+            summ[st[0]] = round(summ.get(st[0], 0.0) + st[2] / st[1], 3)
     out = {
         "value": 1e3 / ms, "unit": "iter/s", "ms_per_step": ms, "steps": args.steps, "gpu_launches": launches,
+        "step_ms": summ,
         "precision": "tcgen05 split-TF32 (3 passes) for ladder and ring, FP32 CUDA cores elsewhere, FP64 update",
         "contraction_tflops": flops_per_iteration(spec) / (ms / 1e3) / 1e12,
         "speedup_per_iter_vs_fp64": fp64_ms_per_iter / ms,

@@ -505,6 +505,7 @@ void add_zero(ccsd_ctx* h, int buf) {
 }
 
 dim3 ew_grid(long long n);
+dim3 row_grid(long long rows);
 
 // Build the full residual plan.
 int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
@@ -531,7 +532,8 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         const long long N3l = (long long)N * N * N;
         h->tc_err = (int*)al.get(sizeof(int));
         if (al.err) return al.err;
-        // complex64 copies: the inputs once here (unless stored so), t1 at the start of every residual
+        // complex64 copies: the inputs once here (unless stored so), t1 at the start of every
+        // residual, t2 and tau~ by the tau kernel
         for (int bi = B_FOO_IN; bi <= B_T1; ++bi) {
             if (bi == B_T2 || h->in32[bi]) continue;
             h->shadow[bi] = (float2*)al.get((size_t)h->bufsize[bi] * 8);
@@ -539,6 +541,9 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
             if (!al.dry && bi != B_T1)
                 to_c64_kernel<<<ew_grid(h->bufsize[bi]), 256, 0, h->st>>>(h->shadow[bi], h->buf[bi], h->bufsize[bi]);
         }
+        h->shadow[B_T2] = (float2*)al.get((size_t)h->n2 * 8);
+        h->shadow[B_TAUT] = (float2*)al.get((size_t)h->n2 * 8);
+        if (al.err) return al.err;
         if (!al.dry && cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st) != cudaSuccess) return CCSD_ERR_CUDA;
         // ladder B rows of the largest packed class (floats per part)
         long long lad_max = 0, lad_batch = 0;    // largest class, largest single (ka, kb) batch
@@ -1223,31 +1228,41 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         if (mixed) h->seq.back().mode = 1;
     }
     if (mixed) {
-        // A_ring[ki][ka][kn](i,a)(n,f) = t2[ki,kn,ka](i,n,a,f); since t_jx^yb = -t_jx^by the same
-        // operand serves W -= 1/2 t_jx^yb <nx||fy> with the sign folded into alpha.
+        // Both ring GEMMs on tensor cores, one batch per momentum transfer D:
+        //   ring W:  rows (kj, j, b) with kb = kj - D, columns (kn, n, f) with kf = kn - D
+        //   ring C:  rows (ki, i, a) with ka = ki - D, columns (kj, j, b) with kb = kj + D
+        // so every output row and column of a batch is a full momentum block and the
+        // output offset stays separable (row part + column part).  A' rows are
+        // [D][chunk][first](first index, second index) of t2[first, chunk, second] with
+        // second = first - D; since t_jx^yb = -t_jx^by it serves both GEMMs (the sign
+        // of the W term is folded into alpha).
         std::vector<long long> so;
-        for (int ki = 0; ki < N; ++ki) for (int ka = 0; ka < N; ++ka) for (int kn = 0; kn < N; ++kn)
-            so.push_back(blk(S2, ki, kn, ka));
+        for (int D = 0; D < N; ++D) for (int kc = 0; kc < N; ++kc) for (int kf_ = 0; kf_ < N; ++kf_)
+            so.push_back(blk(S2, kf_, kc, kg.k4(kf_, 0, D)));
         if ((rc = add_embed(h, al, B_T2, tc_ra, 0, (int)ov, (int)ov, so, tab({{o, o * vv}, {v, v}}),
                             tab({{o, vv}, {v, 1}}), false))) return rc;
-        // constant B: <n kn x kx||f kf y ky> as rows (n,f), columns (x,y), blocks [kn][kf][kx]
+        // B of ring W: <n kn x kx||f kf y ky> rows (n,f), columns (x,y): [D][kx][kn], kf = kn - D
         so.clear();
-        for (int kn = 0; kn < N; ++kn) for (int kf = 0; kf < N; ++kf) for (int kx = 0; kx < N; ++kx)
-            so.push_back(blk(S2, kn, kx, kf));
+        for (int D = 0; D < N; ++D) for (int kx = 0; kx < N; ++kx) for (int kn = 0; kn < N; ++kn)
+            so.push_back(blk(S2, kn, kx, kg.k4(kn, 0, D)));
         if ((rc = add_embed(h, al, B_OOVV, tc_b1, 1, (int)ov, (int)ov, so, tab({{o, o * vv}, {v, v}}),
                             tab({{o, vv}, {v, 1}}), !pooled))) return rc;
-        std::vector<int> ra, rb; std::vector<long long> oc;
-        for (int kj = 0; kj < N; ++kj) for (int kb = 0; kb < N; ++kb) for (int kn = 0; kn < N; ++kn) {
-            const int kf = kg.k4(kn, kb, kj);
+        std::vector<int> ra, rb, cc; std::vector<long long> oc;
+        for (int D = 0; D < N; ++D) {
             for (int kx = 0; kx < N; ++kx) {
-                ra.push_back((int)((((long long)kj * N + kb) * N + kx) * ov));
-                rb.push_back((int)((((long long)kn * N + kf) * N + kx) * 2 * ov));
+                ra.push_back((int)(((long long)D * N + kx) * N * ov));
+                rb.push_back((int)(((long long)D * N + kx) * N * 2 * ov));
             }
-            for (int j = 0; j < o; ++j) for (int b = 0; b < v; ++b)
-                oc.push_back(blk(S2, kj, kn, kb) + j * o * vv + b * v);
+            for (int kj = 0; kj < N; ++kj) {
+                const int kb = kg.k4(kj, 0, D);
+                for (int j = 0; j < o; ++j) for (int b = 0; b < v; ++b)
+                    oc.push_back(((long long)kj * N * N + kb) * S2 + j * o * vv + b * v);
+            }
         }
-        if ((rc = add_tc(h, al, tc_ra, tc_b1, B_WRING, (int)ov, (int)(2 * ov), N3, N, ra, rb, oc,
-                         tab({{o, vv}, {v, 1}}), 0.5, 3))) return rc;
+        for (int kn = 0; kn < N; ++kn) for (int n = 0; n < o; ++n) for (int f = 0; f < v; ++f)
+            cc.push_back((int)((long long)kn * N * S2 + n * vv + f));
+        if ((rc = add_tc(h, al, tc_ra, tc_b1, B_WRING, (int)(N * ov), (int)(2 * N * ov), N, N, ra, rb, oc, cc, 0.5, 3)))
+            return rc;
     }
     h->cur_name = "ring";
     {   // ZR = sum_kn t_{in}^{af} W_{jn}^{bf}
@@ -1266,23 +1281,28 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     }
     if (mixed) {
         add_zero(h, B_ZR);
-        std::vector<long long> so;       // B_ring[kj][kb][kn]: rows (j,b), columns (n,f) of W~
-        for (int kj = 0; kj < N; ++kj) for (int kb = 0; kb < N; ++kb) for (int kn = 0; kn < N; ++kn)
-            so.push_back(blk(S2, kj, kn, kb));
+        // B_ring[D][kn][kj]: rows (j,b), columns (n,f) of W~[kj, kn, kb], kb = kj + D
+        std::vector<long long> so;
+        for (int D = 0; D < N; ++D) for (int kn = 0; kn < N; ++kn) for (int kj = 0; kj < N; ++kj)
+            so.push_back(blk(S2, kj, kn, kg.k4(kj, D, 0)));
         if ((rc = add_embed(h, al, B_WRING, tc_rb, 1, (int)ov, (int)ov, so, tab({{o, o * vv}, {v, v}}),
                             tab({{o, vv}, {v, 1}}), false))) return rc;
-        std::vector<int> ra, rb; std::vector<long long> oc;
-        for (int ki = 0; ki < N; ++ki) for (int ka = 0; ka < N; ++ka) for (int kj = 0; kj < N; ++kj) {
-            const int kb = kg.k4(ki, kj, ka);
+        std::vector<int> ra, rb, cc; std::vector<long long> oc;
+        for (int D = 0; D < N; ++D) {
             for (int kn = 0; kn < N; ++kn) {
-                ra.push_back((int)((((long long)ki * N + ka) * N + kn) * ov));
-                rb.push_back((int)((((long long)kj * N + kb) * N + kn) * 2 * ov));
+                ra.push_back((int)(((long long)D * N + kn) * N * ov));
+                rb.push_back((int)(((long long)D * N + kn) * N * 2 * ov));
             }
-            for (int i = 0; i < o; ++i) for (int a = 0; a < v; ++a)
-                oc.push_back(blk(S2, ki, kj, ka) + i * o * vv + a * v);
+            for (int ki = 0; ki < N; ++ki) {
+                const int ka = kg.k4(ki, 0, D);
+                for (int i2 = 0; i2 < o; ++i2) for (int a = 0; a < v; ++a)
+                    oc.push_back(((long long)ki * N * N + ka) * S2 + i2 * o * vv + a * v);
+            }
         }
-        if ((rc = add_tc(h, al, tc_ra, tc_rb, B_ZR, (int)ov, (int)(2 * ov), N3, N, ra, rb, oc,
-                         tab({{o, vv}, {v, 1}}), 1.0, 3))) return rc;
+        for (int kj = 0; kj < N; ++kj) for (int j = 0; j < o; ++j) for (int b = 0; b < v; ++b)
+            cc.push_back((int)((long long)kj * N * S2 + j * vv + b));
+        if ((rc = add_tc(h, al, tc_ra, tc_rb, B_ZR, (int)(N * ov), (int)(2 * N * ov), N, N, ra, rb, oc, cc, 1.0, 3)))
+            return rc;
     }
     h->cur_name = "ring_t1t1";
     {   // TT(r,b,i,j) = sum_c <r ka b kb||c ki j kj> t_i^c ;  ZR -= sum_r t_r^a TT(r,b,i,j)
@@ -1374,6 +1394,11 @@ void set_sizes(ccsd_ctx* h) {
     for (int i = 0; i < NBUF; ++i) h->bufsize[i] = sz[i];
 }
 
+// One CTA per row for the row-wise operand kernels (grid-stride beyond 2^31 - 1 rows).
+dim3 row_grid(long long rows) {
+    return dim3((unsigned)std::max(1LL, std::min(rows, 2147483647LL)));
+}
+
 dim3 ew_grid(long long n) {
     long long b = (n + 255) / 256;
     if (b > 152LL * 16) b = 152LL * 16;
@@ -1417,7 +1442,7 @@ void launch_embed(ccsd_ctx* h, EmbedPlan& e) {
     EmbedArgs a = e.a;
     a.src = h->buf[e.src];
     a.src32 = h->in32[e.src] ? h->shadow[e.src] : nullptr;
-    embed_kernel<<<ew_grid((long long)a.nblk * a.R * (a.Kpad / 2)), 256, 0, h->st>>>(a);
+    embed_kernel<<<row_grid((long long)a.nblk * a.R), a.Kpad / 2 >= 256 ? 256 : 128, 0, h->st>>>(a);
     ++h->launches;
 }
 
@@ -1476,8 +1501,12 @@ void launch_step(ccsd_ctx* h, size_t si) {
                 break;
             }
             case 3:
+            {
+                const bool c64 = h->fp32 && h->cfg.precision == CCSD_MIXED;
                 tau_kernel<<<ew_grid(h->n2), 256, 0, h->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_TAU], h->buf[B_TAUT],
-                                                               h->kb_of, N, o, v);
+                                                               h->kb_of, N, o, v, c64 ? h->shadow[B_T2] : nullptr,
+                                                               c64 ? h->shadow[B_TAUT] : nullptr);
+            }
                 ++h->launches;
                 break;
             case 4:
@@ -1493,7 +1522,7 @@ void launch_step(ccsd_ctx* h, size_t si) {
             case 10: {
                 WprimeListArgs a = h->wlists[s.idx].a;
                 a.vvvv = h->shadow[B_VVVV]; a.ovvv = h->shadow[B_OVVV]; a.t1 = h->shadow[B_T1];
-                wprime_list_kernel<<<ew_grid((long long)a.nblk * a.nab * (a.Kpad / 2)), 256, 0, h->st>>>(a);
+                wprime_list_kernel<<<row_grid((long long)a.nblk * a.nab), 256, 0, h->st>>>(a);
                 ++h->launches;
                 break;
             }

@@ -21,9 +21,13 @@ __device__ __forceinline__ double2 ldz(const float2* p) { const float2 f = *p; r
 // tau~ = t2 + 1/2 x and tau = t2 + x with
 // x = delta(ki,ka) t_i^a t_j^b - delta(ki,kb) t_i^b t_j^a
 // (paper Sec. 2: 1/4 and 1/2 of P(ab)P(ij) t1 t1, whose four terms pair up).
+// Mixed form: t2_32 / taut_32 (when set) receive complex64 copies of t2 and tau~
+// for the FP32 contractions (a double->float conversion issues on GB300's FP64
+// pipe, so each element is converted once here instead of in every GEMM).
 __global__ void tau_kernel(const double2* __restrict__ t1, const double2* __restrict__ t2,
                            double2* __restrict__ tau, double2* __restrict__ taut,
-                           const int* __restrict__ kb_of, int N, int o, int v)
+                           const int* __restrict__ kb_of, int N, int o, int v,
+                           float2* __restrict__ t2_32 = nullptr, float2* __restrict__ taut_32 = nullptr)
 {
     const long long blk = (long long)o * o * v * v;
     const long long total = (long long)N * N * N * blk;
@@ -47,7 +51,12 @@ __global__ void tau_kernel(const double2* __restrict__ t1, const double2* __rest
         }
         const double2 t = t2[e];
         tau[e] = make_double2(t.x + x.x, t.y + x.y);
-        taut[e] = make_double2(t.x + 0.5 * x.x, t.y + 0.5 * x.y);
+        const double2 tt = make_double2(t.x + 0.5 * x.x, t.y + 0.5 * x.y);
+        taut[e] = tt;
+        if (t2_32) {
+            t2_32[e] = make_float2((float)t.x, (float)t.y);
+            taut_32[e] = make_float2((float)tt.x, (float)tt.y);
+        }
     }
 }
 

@@ -398,41 +398,43 @@ struct EmbedArgs {
     int nblk, R, Kc, Kpad, mode;
 };
 
+// One CTA per operand row (b, r): its threads sweep the row's column pairs, so
+// the per-element index arithmetic is one 32-bit add.
 __global__ void embed_kernel(const EmbedArgs e)
 {
     const int kh = e.Kpad / 2;                       // column pairs, padding included
-    const long long total = (long long)e.nblk * e.R * kh;
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
-         x += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(x % kh);
-        const long long br = x / kh;
+    const long long rows = (long long)e.nblk * e.R;
+    for (long long br = blockIdx.x; br < rows; br += gridDim.x) {
         const int r = (int)(br % e.R);
         const long long b = br / e.R;
-        float rb = 0.f, rs = 0.f, ib = 0.f, is = 0.f;   // padding columns are written as zero
-        if (k >= e.Kc) {
-        } else if (e.src32) {
-            const long long q = e.srcoff[b] + (long long)e.srow[r] + e.scol[k];
-            const float2 z = e.src32[q];
-            split_tf32f(z.x, rb, rs);
-            split_tf32f(z.y, ib, is);
-        } else {
-            const long long q = e.srcoff[b] + (long long)e.srow[r] + e.scol[k];
-            const double2 z = e.src[q];
-            split_tf32(z.x, rb, rs);
-            split_tf32(z.y, ib, is);
-        }
-        if (e.mode == 0) {
-            const long long o = (b * e.R + r) * (long long)e.Kpad + 2LL * k;
-            e.big[o] = rb; e.big[o + 1] = ib;
-            if (e.small) { e.small[o] = rs; e.small[o + 1] = is; }
-        } else {
-            const long long o0 = (b * 2 * e.R + 2 * r) * (long long)e.Kpad + 2LL * k;
-            const long long o1 = o0 + e.Kpad;
-            e.big[o0] = rb; e.big[o0 + 1] = -ib;
-            e.big[o1] = ib; e.big[o1 + 1] = rb;
-            if (e.small) {
-                e.small[o0] = rs; e.small[o0 + 1] = -is;
-                e.small[o1] = is; e.small[o1 + 1] = rs;
+        const long long base = e.srcoff[b] + (long long)e.srow[r];
+        const long long o = (e.mode == 0 ? (b * e.R + r) : (b * 2 * e.R + 2 * r)) * (long long)e.Kpad;
+        for (int k = threadIdx.x; k < kh; k += blockDim.x) {
+            float rb = 0.f, rs = 0.f, ib = 0.f, is = 0.f;   // padding columns are written as zero
+            if (k < e.Kc) {
+                const long long q = base + e.scol[k];
+                if (e.src32) {
+                    const float2 z = e.src32[q];
+                    split_tf32f(z.x, rb, rs);
+                    split_tf32f(z.y, ib, is);
+                } else {
+                    const double2 z = e.src[q];
+                    split_tf32(z.x, rb, rs);
+                    split_tf32(z.y, ib, is);
+                }
+            }
+            const long long o0 = o + 2LL * k;
+            if (e.mode == 0) {
+                *(float2*)(e.big + o0) = make_float2(rb, ib);
+                if (e.small) *(float2*)(e.small + o0) = make_float2(rs, is);
+            } else {
+                const long long o1 = o0 + e.Kpad;
+                *(float2*)(e.big + o0) = make_float2(rb, -ib);
+                *(float2*)(e.big + o1) = make_float2(ib, rb);
+                if (e.small) {
+                    *(float2*)(e.small + o0) = make_float2(rs, -is);
+                    *(float2*)(e.small + o1) = make_float2(is, rs);
+                }
             }
         }
     }
@@ -471,49 +473,60 @@ struct WprimeListArgs {
     int nblk, nab, nef, N, o, v, Kpad;
 };
 
+// One CTA per output row pair (block bi, pair ai): t1 and the ovvv rows it needs are
+// fixed for the CTA, its threads sweep the (e, f) list.
 __global__ void wprime_list_kernel(const WprimeListArgs w)
 {
     const int N = w.N, o = w.o, v = w.v;
     const long long vv = (long long)v * v, v4 = vv * vv, ov3 = (long long)o * v * vv;
     const int kh = w.Kpad / 2;                       // column pairs, padding included
-    const long long per = (long long)w.nab * kh;
-    const long long total = (long long)w.nblk * per;
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
-         x += (long long)gridDim.x * blockDim.x) {
-        const long long bi = x / per;
-        const int r0 = (int)(x % per);
-        const int ai = r0 / kh, ei = r0 % kh;
-        const long long o0 = (bi * 2 * w.nab + 2LL * ai) * (long long)w.Kpad + 2LL * ei;
-        const long long o1 = o0 + w.Kpad;
-        if (ei >= w.nef) {                           // padding columns
-            w.big[o0] = 0.f; w.big[o0 + 1] = 0.f; w.big[o1] = 0.f; w.big[o1 + 1] = 0.f;
-            w.small[o0] = 0.f; w.small[o0 + 1] = 0.f; w.small[o1] = 0.f; w.small[o1 + 1] = 0.f;
-            continue;
-        }
+    const long long rows = (long long)w.nblk * w.nab;
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const long long bi = row / w.nab;
+        const int ai = (int)(row - bi * w.nab);
         const int ka = w.blk[3 * bi], kb = w.blk[3 * bi + 1], ke = w.blk[3 * bi + 2];
-        const int ab = w.abl[ai], ef = w.efl[ei];
+        const int ab = w.abl[ai];
         const int a = ab / v, b = ab % v;
         const long long blk_ab = ((long long)ka * N + kb) * N + ke;
         const long long blk_ba = ((long long)kb * N + ka) * N + ke;
-        const float2 g = w.vvvv[blk_ab * v4 + (long long)ab * vv + ef];
-        float sr = 0.f, si = 0.f;
-        for (int r = 0; r < o; ++r) {
-            const float2 tb = w.t1[((long long)kb * o + r) * v + b];
-            const float2 p = w.ovvv[blk_ba * ov3 + ((long long)r * v + a) * vv + ef];
-            sr = fmaf(tb.x, p.x, fmaf(-tb.y, p.y, sr));
-            si = fmaf(tb.x, p.y, fmaf(tb.y, p.x, si));
-            const float2 ta = w.t1[((long long)ka * o + r) * v + a];
-            const float2 q = w.ovvv[blk_ab * ov3 + ((long long)r * v + b) * vv + ef];
-            sr = fmaf(-ta.x, q.x, fmaf(ta.y, q.y, sr));
-            si = fmaf(-ta.x, q.y, fmaf(-ta.y, q.x, si));
+        const float2* g0 = w.vvvv + blk_ab * v4 + (long long)ab * vv;
+        const float2* pa = w.ovvv + blk_ba * ov3 + (long long)a * vv;     // + r v vv: ovvv[kb,ka,ke](r,a,.)
+        const float2* pb = w.ovvv + blk_ab * ov3 + (long long)b * vv;     // ovvv[ka,kb,ke](r,b,.)
+        const float2* tb = w.t1 + (long long)kb * o * v + b;              // + r v: t_r^b(kb)
+        const float2* ta = w.t1 + (long long)ka * o * v + a;              // t_r^a(ka)
+        const long long o0row = (bi * 2 * w.nab + 2LL * ai) * (long long)w.Kpad;
+        for (int ei = threadIdx.x; ei < kh; ei += blockDim.x) {
+            const long long o0 = o0row + 2LL * ei;
+            const long long o1 = o0 + w.Kpad;
+            if (ei >= w.nef) {                       // padding columns
+                *(float2*)(w.big + o0) = make_float2(0.f, 0.f);
+                *(float2*)(w.big + o1) = make_float2(0.f, 0.f);
+                *(float2*)(w.small + o0) = make_float2(0.f, 0.f);
+                *(float2*)(w.small + o1) = make_float2(0.f, 0.f);
+                continue;
+            }
+            const int ef = w.efl[ei];
+            const float2 g = g0[ef];
+            float sr = 0.f, si = 0.f;
+            for (int r = 0; r < o; ++r) {
+                // + t_r^b(kb) ovvv[kb,ka,ke](r,a,e,f) - t_r^a(ka) ovvv[ka,kb,ke](r,b,e,f)
+                const float2 tbr = tb[r * v];
+                const float2 p = pa[(long long)r * v * vv + ef];
+                sr = fmaf(tbr.x, p.x, fmaf(-tbr.y, p.y, sr));
+                si = fmaf(tbr.x, p.y, fmaf(tbr.y, p.x, si));
+                const float2 tar = ta[r * v];
+                const float2 q = pb[(long long)r * v * vv + ef];
+                sr = fmaf(-tar.x, q.x, fmaf(tar.y, q.y, sr));
+                si = fmaf(-tar.x, q.y, fmaf(-tar.y, q.x, si));
+            }
+            float rb, rs, ib, is;
+            split_tf32f(g.x + sr, rb, rs);
+            split_tf32f(g.y + si, ib, is);
+            *(float2*)(w.big + o0) = make_float2(rb, -ib);
+            *(float2*)(w.big + o1) = make_float2(ib, rb);
+            *(float2*)(w.small + o0) = make_float2(rs, -is);
+            *(float2*)(w.small + o1) = make_float2(is, rs);
         }
-        float rb, rs, ib, is;
-        split_tf32f(g.x + sr, rb, rs);
-        split_tf32f(g.y + si, ib, is);
-        w.big[o0] = rb; w.big[o0 + 1] = -ib;
-        w.big[o1] = ib; w.big[o1 + 1] = rb;
-        w.small[o0] = rs; w.small[o0 + 1] = -is;
-        w.small[o1] = is; w.small[o1 + 1] = rs;
     }
 }
 
