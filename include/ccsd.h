@@ -116,6 +116,14 @@ int ccsd_plan_check(const ccsd_config* cfg, long long* n_launches, size_t* table
  * Sizes up to 4096.  CCSD_ERR_TIMEOUT if a bounded device wait gave up. */
 int ccsd_tc_selftest(int M, int Ncols, int K, int nterms, unsigned long long seed, double* rel_err);
 
+/* Failure-detection self-test of the tensor-core GEMM: a 128 x 128 x 64 product
+ * in which the loader never fills one pipeline stage, with a short wait limit,
+ * so the MMA issuer's bounded wait gives up.  The kernel records the timeout in
+ * its error word, stops issuing, drains its copies and MMAs in flight, frees its
+ * TMEM and returns; the call returns CCSD_ERR_TIMEOUT (the expected outcome) and
+ * the CUDA context stays usable.  Any other code means the failure path is broken. */
+int ccsd_tc_timeout_selftest(void);
+
 /* One residual evaluation R(t) (paper Eqs. ori_EqSingle, ori_EqDouble with the
  * full Fock matrix inside F~): t1, t2 are read and r1, r2 written, all device
  * pointers in the layout above (r1 like t1, r2 like t2).  Does not touch the

@@ -49,6 +49,7 @@ SYMBOLS = {
                          ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "ccsd_tc_selftest": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
                           ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "ccsd_tc_timeout_selftest": ([], ctypes.c_int),
     "ccsd_residual": ([ctypes.c_void_p] * 5, ctypes.c_int),
     "ccsd_iterate": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                       ctypes.POINTER(ctypes.c_double)], ctypes.c_int),

@@ -479,6 +479,8 @@ int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M,
     a.colC2 = colC2.empty() ? nullptr : upload(al, colC2, h->st);
     if (al.err) return al.err;
     a.err = h->tc_err;
+    a.spin_limit = TC_SPIN_LIMIT;
+    a.skip_stage = -1;
     a.M = M; a.Nr = Nr; a.nchunk = nchunk; a.kstages = A.kpad / TC_BK; a.nterms = nterms;
     a.tiles_m = (M + TC_BM - 1) / TC_BM; a.tiles_n = (Nr + TC_BN - 1) / TC_BN;
     a.alpha_re = alpha; a.alpha_im = 0.0;
@@ -2219,9 +2221,13 @@ int ccsd_plan_check(const ccsd_config* cfg, long long* n_launches, size_t* table
     return rc;
 }
 
-int ccsd_tc_selftest(int M, int Ncols, int K, int nterms, unsigned long long seed, double* rel_err) {
-    if (M < 1 || Ncols < 1 || K < 1 || M > 4096 || Ncols > 4096 || K > 4096 || (nterms != 1 && nterms != 3) || !rel_err)
-        return CCSD_ERR_INVALID;
+}  // extern "C"
+
+namespace {
+
+// The tensor-core self-test; skip_stage >= 0 leaves that pipeline stage unloaded
+// (with a short wait limit) to exercise the bounded-wait failure path.
+int tc_selftest_impl(int M, int Ncols, int K, int nterms, unsigned long long seed, int skip_stage, double* rel_err) {
     ccsd_ctx* h = new (std::nothrow) ccsd_ctx();
     if (!h) return CCSD_ERR_OOM;
     h->cfg.precision = CCSD_MIXED;
@@ -2264,6 +2270,10 @@ int ccsd_tc_selftest(int M, int Ncols, int K, int nterms, unsigned long long see
     for (int m = 0; m < M; ++m) oc.push_back((long long)m * Ncols);
     if ((rc = add_tc(h, al, ta, tb, B_ZR, M, 2 * Ncols, 1, 1, {0}, {0}, oc, tab({{Ncols, 1}}), 1.0, nterms)))
         return fail(rc);
+    if (skip_stage >= 0) {
+        h->tcs[0].a.skip_stage = skip_stage;
+        h->tcs[0].a.spin_limit = 1LL << 14;
+    }
     launch_gemm(h, h->gemms[0]);
     launch_embed(h, h->embeds[0]);
     launch_embed(h, h->embeds[1]);
@@ -2284,6 +2294,21 @@ int ccsd_tc_selftest(int M, int Ncols, int K, int nterms, unsigned long long see
     *rel_err = den > 0 ? num / den : num;
     ccsd_destroy(h);
     return CCSD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ccsd_tc_selftest(int M, int Ncols, int K, int nterms, unsigned long long seed, double* rel_err) {
+    if (M < 1 || Ncols < 1 || K < 1 || M > 4096 || Ncols > 4096 || K > 4096 || (nterms != 1 && nterms != 3) || !rel_err)
+        return CCSD_ERR_INVALID;
+    return tc_selftest_impl(M, Ncols, K, nterms, seed, -1, rel_err);
+}
+
+int ccsd_tc_timeout_selftest(void) {
+    double err = 0.0;
+    return tc_selftest_impl(128, 128, 64, 1, 1, 1, &err);
 }
 
 int ccsd_create(const ccsd_config* cfg, const ccsd_inputs* in, void* stream, ccsd_t* out) {

@@ -78,6 +78,8 @@ struct TcArgs {
     const int* nchunk_b;      // per-batch chunk count (<= nchunk) or null
     const long long* offC2;   // antisymmetric mirror: c is also subtracted at offC2[b*M+m] + colC2[n]
     const int* colC2;
+    long long spin_limit;     // polls before a wait gives up (TC_SPIN_LIMIT)
+    int skip_stage;           // failure-detection self-test: this stage is never loaded (-1: none)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -212,11 +214,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
             for (int s = 0; s < total; ++s) {
                 const int st = s % TC_STAGES;
                 const uint32_t ph = (uint32_t)(s / TC_STAGES) & 1u;
-                if (!mbar_wait(smem_u32(&bars[TC_STAGES + st]), ph ^ 1u, abort_flag)) {
+                if (!mbar_wait(smem_u32(&bars[TC_STAGES + st]), ph ^ 1u, abort_flag, g.spin_limit)) {
                     atomicCAS(g.err, 0, 1);
                     *abort_flag = 1;
                     break;
                 }
+                if (s == g.skip_stage) continue;           // nothing will complete this stage
                 const int c = s / per_chunk;
                 const int r = s % per_chunk;
                 const int term = r / g.kstages;
@@ -242,7 +245,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
                 const bool seg_first = (s % TC_PROMOTE_STAGES) == 0;
                 if (seg_first && seg >= 2) {
                     // the accumulator warps must have drained this buffer's previous segment
-                    if (!mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)((seg - 2) >> 1) & 1u, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)((seg - 2) >> 1) & 1u, abort_flag, g.spin_limit)) {
                         atomicCAS(g.err, 0, 4);
                         *abort_flag = 1;
                         break;
@@ -251,7 +254,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
                 }
                 const int st = s % TC_STAGES;
                 const uint32_t ph = (uint32_t)(s / TC_STAGES) & 1u;
-                if (!mbar_wait(smem_u32(&bars[st]), ph, abort_flag)) {
+                if (!mbar_wait(smem_u32(&bars[st]), ph, abort_flag, g.spin_limit)) {
                     atomicCAS(g.err, 0, 2);
                     *abort_flag = 1;
                     break;
@@ -285,7 +288,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
         bool ok = true;
         for (int seg = 0; seg < nseg; ++seg) {
             const int buf = seg & 1;
-            bool got = mbar_wait(smem_u32(&acc_full[buf]), (uint32_t)(seg >> 1) & 1u, abort_flag);
+            bool got = mbar_wait(smem_u32(&acc_full[buf]), (uint32_t)(seg >> 1) & 1u, abort_flag, g.spin_limit);
             got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;   // one decision per warp
             if (!got) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
