@@ -228,6 +228,8 @@ def run_batch(args, local):
     import torch
     from paper_1911_00242_gb300.binding import CCSD_MIXED, BatchSolver
     specs = cs.batch_specs(64)
+    if args.precision == "mixed":      # mixed members hold complex64 integrals
+        specs = [cs.SynthSpec(**{**s.__dict__, "int_dtype": "c64"}) for s in specs]
     devs = [{k: torch.from_numpy(v).to(f"cuda:{local}") for k, v in cs.generate(s).items()} for s in specs]
     prec = CCSD_MIXED if args.precision == "mixed" else 0
     B = BatchSolver([(s.grid, s.nocc, s.nvir, d) for s, d in zip(specs, devs)], conv_tol=1e-30, precision=prec)
@@ -248,7 +250,7 @@ def run_batch(args, local):
     return {"metric": METRIC, "value": 64 * args.steps / dt, "unit": "member iter/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "c128", "data": "synthetic",
+            "dtype": "c64 integrals, mixed" if args.precision == "mixed" else "c128", "data": "synthetic",
             "config": {"workload": "batch64", "members": 64, "precision": args.precision,
                        "nk": [s.nk for s in specs], "nocc": [s.nocc for s in specs], "nvir": [s.nvir for s in specs]},
             "aggregate_tflops": fl * args.steps / dt / 1e12, "gpu_launches_per_step": launches,

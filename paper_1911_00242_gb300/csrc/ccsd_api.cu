@@ -89,7 +89,8 @@ struct PermPlan {
 
 struct Step {           // one element of the launch sequence
     int kind;           // 0 gemm, 1 copy, 2 perm, 3 tau, 4 antisym, 5 embed, 6 tensor-core gemm, 7 zero,
-                        // 9 complex64 refresh of t1, 10 W' formation into the ladder's B operand
+                        // 9 complex64 refresh of a buffer, 10 W' formation into the ladder's B operand,
+                        // 11 fused Fock/t1 terms of R2 (mixed form), 12 transposed complex64 F'vv
     int idx;
     const char* name;
     double flops;       // algorithmic real flops per launch (complex MAC = 8)
@@ -1329,6 +1330,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         if ((rc = G(s2))) return rc;
     }
     h->cur_name = "fock_t1_terms";
+    const size_t fock_first = h->seq.size();
     // remaining terms under P(ab) and P(ij)
     // The P(ab)-only terms (call them Zab) and the P(ij)-only terms (Zij) accumulate into
     // ZR at half weight: Zab is antisymmetric in (i,j) and Zij in (a,b), so
@@ -1378,6 +1380,18 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowB = tab({{v, vv}}); s.colB = tab({{o, vv * v}, {(int)vv, 1}});
         s.rowC = tab({{o, o * vv}}); s.colC = tab({{o, vv}, {(int)vv, 1}});
         if ((rc = G(s))) return rc;
+    }
+    if (mixed) {
+        // the four GEMMs above run in FP64 iterations only; mixed iterations fuse them
+        for (size_t i = fock_first; i < h->seq.size(); ++i) h->seq[i].mode = 1;
+        h->shadow[B_FVVP] = (float2*)al.get((size_t)h->bufsize[B_FVVP] * 8);
+        h->shadow[B_FOOP] = (float2*)al.get((size_t)h->bufsize[B_FOOP] * 8);
+        if (al.err) return al.err;
+        Step s1{12, B_FVVP, h->cur_name, 0.0, 24.0 * h->bufsize[B_FVVP]};
+        Step s2{9, B_FOOP, h->cur_name, 0.0, 24.0 * h->bufsize[B_FOOP]};
+        Step s3{11, 0, h->cur_name, 8.0 * 2.0 * (o + v) * (double)h->n2, 8.0 * 4.0 * h->n2};
+        s1.mode = s2.mode = s3.mode = 2;
+        h->seq.push_back(s1); h->seq.push_back(s2); h->seq.push_back(s3);
     }
     h->seq.push_back({4, 0, "antisym_R2", 0.0, 16.0 * 3.0 * h->n2});
     return 0;
@@ -1528,7 +1542,18 @@ void launch_step(ccsd_ctx* h, size_t si) {
                 ++h->launches;
                 break;
             }
-            case 9:   // refresh the complex64 copy of an amplitude buffer
+            case 11: {   // mixed form: fused P(ab)-only / P(ij)-only terms into ZR
+                fock_terms_kernel<<<ew_grid(h->n2), 256, 0, h->st>>>(
+                    h->buf[B_ZR], h->shadow[B_T2], h->shadow[B_T1], h->shadow[B_FVVP], h->shadow[B_FOOP],
+                    h->shadow[B_OOOV], h->shadow[B_OVVV], h->kb_of, N, o, v);
+                ++h->launches;
+                break;
+            }
+            case 12:  // complex64 copy of F'vv, transposed per k (fused Fock terms)
+                to_c64_transpose_kernel<<<ew_grid(h->bufsize[s.idx]), 256, 0, h->st>>>(h->shadow[s.idx], h->buf[s.idx], N, v);
+                ++h->launches;
+                break;
+            case 9:   // refresh the complex64 copy of an amplitude or intermediate buffer
                 to_c64_kernel<<<ew_grid(h->bufsize[s.idx]), 256, 0, h->st>>>(h->shadow[s.idx], h->buf[s.idx],
                                                                              h->bufsize[s.idx]);
                 ++h->launches;

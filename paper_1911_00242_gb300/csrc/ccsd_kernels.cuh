@@ -300,6 +300,77 @@ __global__ void combo_kernel(double2* __restrict__ out, const Combo cb, long lon
 }
 
 // ---------------------------------------------------------------------------
+// Mixed form: the P(ab)-only and P(ij)-only terms of R2 at half weight, fused
+// into one pass over Zr (FP32 products and sums, FP64 accumulation into Zr):
+//   Zr += 1/2 sum_f t_ij^af F'^{bf}(kb) - 1/2 sum_r t_r^a(ka) <ij||rb>^*
+//       - 1/2 sum_n t_in^ab F'_nj(kj)   - 1/2 sum_c t_i^c(ki) <jc||ab>^*
+// (<ij||rb> = ooov[ki,kj,ka](i,j,r,b), <jc||ab> = ovvv[kj,ki,ka](j,c,a,b)); the
+// same terms the FP64 form forms as four GEMMs.  Every short sum (o or v terms)
+// is one thread's, so the pass reads t2 once and writes Zr once.
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float2 cfma_conjb(float2 a, float2 b, float2 c) {
+    return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(-a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+
+// dst[k][c][r] = (complex64) src[k][r][c] for nk blocks of n x n
+__global__ void to_c64_transpose_kernel(float2* __restrict__ dst, const double2* __restrict__ src, int nk, int n)
+{
+    const long long total = (long long)nk * n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long k = e / ((long long)n * n);
+        const int rc = (int)(e % ((long long)n * n));
+        const int c = rc / n, r = rc % n;
+        const double2 z = src[(k * n + r) * n + c];
+        dst[e] = make_float2((float)z.x, (float)z.y);
+    }
+}
+
+// fvvpT is F'^{bf} transposed per k: fvvpT[kb][f][b], so that the threads of a warp
+// (consecutive b) read consecutive elements.
+__global__ void fock_terms_kernel(double2* __restrict__ Zr, const float2* __restrict__ t2,
+                                  const float2* __restrict__ t1, const float2* __restrict__ fvvpT,
+                                  const float2* __restrict__ foop, const float2* __restrict__ ooov,
+                                  const float2* __restrict__ ovvv, const int* __restrict__ kb_of,
+                                  int N, int o, int v)
+{
+    const long long blk = (long long)o * o * v * v;
+    const long long total = (long long)N * N * N * blk;
+    const long long vv = (long long)v * v, ov3 = (long long)o * v * vv, o3v = (long long)o * o * o * v;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long kk = e / blk;
+        int r = (int)(e % blk);
+        const int b = r % v; r /= v;
+        const int a = r % v; r /= v;
+        const int j = r % o; const int i = r / o;
+        const int ka = (int)(kk % N), kj = (int)((kk / N) % N), ki = (int)(kk / ((long long)N * N));
+        const int kb = kb_of[kk];
+        const float2* tb = t2 + kk * blk;
+        float2 p = make_float2(0.f, 0.f), q = make_float2(0.f, 0.f);
+        const float2* trow = tb + (((long long)i * o + j) * v + a) * v;             // t_ij^{a f}
+        const float2* fcol = fvvpT + (long long)kb * v * v + b;                     // F'^{b f}(kb) at f v
+        for (int f = 0; f < v; ++f) p = cfma(trow[f], fcol[(long long)f * v], p);
+        const float2* oo = ooov + kk * o3v + ((long long)i * o + j) * o * v + b;    // <ij||r b>
+        const float2* ta = t1 + (long long)ka * o * v + a;                          // t_r^a(ka)
+        for (int rr = 0; rr < o; ++rr) q = cfma_conjb(ta[rr * v], oo[(long long)rr * v], q);
+        const float2* tn = tb + ((long long)i * o * v + a) * v + b;                 // t_in^{ab}, n stride v^2
+        const float2* fo = foop + (long long)kj * o * o + j;                        // F'_{n j}(kj)
+        for (int n = 0; n < o; ++n) q = cfma(tn[(long long)n * vv], fo[n * o], q);
+        const long long kjia = ((long long)kj * N + ki) * N + ka;
+        const float2* vb = ovvv + kjia * ov3 + (long long)j * v * vv + (long long)a * v + b;   // <j c||a b>
+        const float2* ti = t1 + ((long long)ki * o + i) * v;                        // t_i^c(ki)
+        for (int c = 0; c < v; ++c) q = cfma_conjb(ti[c], vb[(long long)c * vv], q);
+        double2 z = Zr[e];
+        z.x += 0.5 * ((double)p.x - (double)q.x);
+        z.y += 0.5 * ((double)p.y - (double)q.y);
+        Zr[e] = z;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // DIIS history on canonical momentum blocks.  t2 is antisymmetric under
 // (ki,i) <-> (kj,j) and under (ka,a) <-> (kb,b), so the blocks with ki <= kj and
 // ka <= kb determine all others; history vectors hold t1 followed by those

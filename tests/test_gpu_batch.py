@@ -72,3 +72,21 @@ def test_mixed_batch_energy(lib):
         ref = driver.solve(P, tol=1e-10, max_iter=200)
         assert abs(e.real - ref["energies"][-1].real / s.nk) < 1e-6
     B.close()
+
+
+def test_mixed_batch_complex64_members(lib):
+    """The batched workload's mixed members hold complex64 integrals: the same
+    energies to 1e-6 Ha against the oracle on the widened integrals."""
+    from paper_1911_00242_gb300.binding import CCSD_MIXED, BatchSolver
+    specs = [cs.SynthSpec(**{**s.__dict__, "int_dtype": "c64"}) for s in (SPECS[0], SPECS[2], SPECS[3])]
+    inps = [cs.generate(s) for s in specs]
+    B = BatchSolver([(s.grid, s.nocc, s.nvir, dev(i)) for s, i in zip(specs, inps)], conv_tol=1e-7,
+                    precision=CCSD_MIXED)
+    done, mr = B.iterate(200)
+    assert all(done)
+    eb = B.energies()
+    for s, inp, e in zip(specs, inps, eb):
+        P = ccsd_k.Problem(s.grid, s.nocc, s.nvir, {k: np.asarray(v, np.complex128) for k, v in inp.items()})
+        ref = driver.solve(P, tol=1e-10, max_iter=200)
+        assert abs(e.real - ref["energies"][-1].real / s.nk) < 1e-6
+    B.close()
