@@ -326,10 +326,13 @@ def run_grid333(args, local):
     dev = cs.generate_torch(spec, device)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
+    if args.vvvv_on_host:       # vvvv stays in host memory, read in place by the kernels
+        dev["vvvv"] = dev["vvvv"].cpu()
     torch.cuda.empty_cache()
     depth = WORKLOADS["grid333_o8_v24_c64"]["diis_depth"]
     S = Solver(spec.grid, spec.nocc, spec.nvir, dev, precision=CCSD_MIXED, diis_depth=depth, max_iter=300,
-               conv_tol=1e-8, mixed_tol=1e-7, polish_iters=2)
+               conv_tol=1e-8, mixed_tol=1e-7, polish_iters=2, vvvv_on_host=args.vvvv_on_host)
+    free_b, total_b = torch.cuda.mem_get_info()
     stream = torch.cuda.current_stream()
     t_solve0 = time.perf_counter()
     for _ in range(args.warmup):
@@ -402,7 +405,8 @@ def run_grid333(args, local):
         "config": {"workload": "grid333_o8_v24_c64", "nk_grid": list(spec.grid), "nocc": spec.nocc,
                    "nvir": spec.nvir, "int_dtype": "c64", "precision": "mixed", "diis": depth,
                    "parallelism": "single", "l2": "inputs larger than L2 (vvvv 52 GB)",
-                   "input_synthesis_s": t_gen},
+                   "input_synthesis_s": t_gen, "vvvv": "host memory, read in place" if args.vvvv_on_host
+                   else "device memory", "device_gb_in_use": (total_b - free_b) / 1e9},
         "contraction_tflops": flops_per_iteration(spec) / (ms / 1e3) / 1e12,
         "roofline": {"kernel": f"tc_gemm_kernel ({name})", "bound": "tensor", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "executed_frac": 3.0 * achieved / peak,
@@ -463,6 +467,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"], help="batch64: member precision")
     ap.add_argument("--rate", type=float, default=5.0, help="serve: requests per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--vvvv-on-host", action="store_true",
+                    help="grid333_o8_v24_c64: keep vvvv in host memory (read in place over the host link)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

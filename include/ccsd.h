@@ -89,6 +89,14 @@ typedef struct {
     const void *f_oo, *f_vv, *f_ov;
     const void *oooo, *ooov, *oovv, *ovvo, *ovvv, *vvvv;
     int int_dtype;        /* CCSD_C128 or CCSD_C64 (the six integral blocks)    */
+    int vvvv_on_host;     /* 1: a host vvvv stays in host memory and the kernels
+                             read it in place (the library registers it as
+                             mapped pinned memory unless it already is, and
+                             unregisters it at ccsd_destroy); it is read once per
+                             iteration (the ladder's W' formation), so this frees
+                             its N^3 v^4 elements of device memory for about one
+                             host-link transfer of it per iteration.  0: host
+                             inputs are copied.  Ignored for a device pointer.  */
 } ccsd_inputs;
 
 /* Creates a solver for one problem.  `stream` is a cudaStream_t (NULL = the

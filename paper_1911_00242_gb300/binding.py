@@ -37,7 +37,7 @@ class ccsd_inputs(ctypes.Structure):
     _fields_ = [("f_oo", ctypes.c_void_p), ("f_vv", ctypes.c_void_p), ("f_ov", ctypes.c_void_p),
                 ("oooo", ctypes.c_void_p), ("ooov", ctypes.c_void_p), ("oovv", ctypes.c_void_p),
                 ("ovvo", ctypes.c_void_p), ("ovvv", ctypes.c_void_p), ("vvvv", ctypes.c_void_p),
-                ("int_dtype", ctypes.c_int)]
+                ("int_dtype", ctypes.c_int), ("vvvv_on_host", ctypes.c_int)]
 
 
 SYMBOLS = {
@@ -140,11 +140,12 @@ def int_dtype(arrays):
     raise ValueError(f"integral blocks must all be complex128 or all complex64, got {sorted(kinds)}")
 
 
-def inputs_struct(arrays):
+def inputs_struct(arrays, vvvv_on_host=False):
     inp = ccsd_inputs()
     for name in ("f_oo", "f_vv", "f_ov") + BLOCKS:
         setattr(inp, name, _ptr(arrays[name]))
     inp.int_dtype = int_dtype(arrays)
+    inp.vvvv_on_host = 1 if vvvv_on_host else 0
     return inp
 
 
@@ -165,13 +166,14 @@ class Solver:
     `arrays` maps f_oo, f_vv, f_ov (complex128) and the six block names
     (all complex128 or all complex64) to contiguous torch tensors (device:
     borrowed, kept referenced here) or numpy arrays (host: copied by the
-    library during creation)."""
+    library during creation; with vvvv_on_host a host vvvv is read in place
+    instead, and must stay alive with the solver)."""
 
-    def __init__(self, grid, nocc, nvir, arrays, stream=None, **cfg):
+    def __init__(self, grid, nocc, nvir, arrays, stream=None, vvvv_on_host=False, **cfg):
         self.lib = load()
         self.cfg = make_config(grid, nocc, nvir, **cfg)
         self._keep = dict(arrays)
-        inp = inputs_struct(arrays)
+        inp = inputs_struct(arrays, vvvv_on_host)
         h = ctypes.c_void_p()
         check(self.lib.ccsd_create(ctypes.byref(self.cfg), ctypes.byref(inp), stream, ctypes.byref(h)), "ccsd_create")
         self.h = h

@@ -127,6 +127,7 @@ struct ccsd_ctx {
     float2* shadow[NBUF] = {};       // complex64 data: mixed-form copies, or inputs stored complex64
     bool in32[NBUF] = {};            // input stored complex64 only (shadow[] set, buf[] null)
     std::vector<void*> owned;        // device allocations to free
+    void* host_registered = nullptr; // host vvvv registered by the library (unregistered at destroy)
     size_t owned_bytes = 0;
     double2* amp = nullptr;          // [t1 | t2]
     double2* res = nullptr;          // [R1 | R2]
@@ -1840,7 +1841,8 @@ bool is_device_ptr(const void* p) {
 // ones copied), amplitudes, work buffers, DIIS history, Fock diagonals, the residual
 // plan and its tables.  With al.dry nothing is allocated, copied or launched and
 // h->owned_bytes ends as the device memory ccsd_create would take (ins may be null).
-int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_dev, int int_dtype) {
+int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_dev, int int_dtype,
+                 bool vvvv_on_host) {
     const long long N = h->N, o = h->o, v = h->v, N3 = N * N * N;
     const long long sizes[9] = {N * o * o, N * v * v, N * o * v, N3 * o * o * o * o, N3 * o * o * o * v,
                                 N3 * o * o * v * v, N3 * o * o * v * v, N3 * o * v * v * v, N3 * v * v * v * v};
@@ -1850,6 +1852,18 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
         void* d = nullptr;
         if (on_dev[i]) {
             d = al.dry ? (void*)(uintptr_t)256 : const_cast<void*>(ins[i]);
+        } else if (i == 8 && vvvv_on_host) {
+            // vvvv read in place from host memory (mapped, pinned): no device copy
+            if (al.dry) {
+                d = (void*)(uintptr_t)256;
+            } else {
+                void* hp = const_cast<void*>(ins[i]);
+                cudaError_t e = cudaHostRegister(hp, bytes, cudaHostRegisterMapped);
+                if (e == cudaSuccess) h->host_registered = hp;
+                else if (e == cudaErrorHostMemoryAlreadyRegistered) cudaGetLastError();
+                else { cudaGetLastError(); return CCSD_ERR_CUDA; }
+                if (cudaHostGetDevicePointer(&d, hp, 0) != cudaSuccess) { cudaGetLastError(); return CCSD_ERR_CUDA; }
+            }
         } else {
             d = al.get(bytes);
             if (!d) return al.err;
@@ -1966,13 +1980,13 @@ void init_ctx(ccsd_ctx* h, const ccsd_config* cfg) {
 }
 
 // Device bytes ccsd_create takes for this config, from a dry run of its setup; 0 on error.
-size_t footprint_bytes(const ccsd_config* c, const bool* on_dev, int int_dtype) {
+size_t footprint_bytes(const ccsd_config* c, const bool* on_dev, int int_dtype, bool vvvv_on_host = false) {
     ccsd_ctx* h = new (std::nothrow) ccsd_ctx();
     if (!h) return 0;
     init_ctx(h, c);
     Alloc al{h};
     al.dry = true;
-    const int rc = setup_handle(h, al, nullptr, on_dev, int_dtype);
+    const int rc = setup_handle(h, al, nullptr, on_dev, int_dtype, vvvv_on_host);
     const size_t b = rc ? 0 : h->owned_bytes;
     delete h;
     return b;
@@ -2127,7 +2141,7 @@ size_t request_bytes(const ccsd_config& c, const ccsd_inputs& in) {
     const void* ins[9] = {in.f_oo, in.f_vv, in.f_ov, in.oooo, in.ooov, in.oovv, in.ovvo, in.ovvv, in.vvvv};
     bool on_dev[9];
     for (int i = 0; i < 9; ++i) on_dev[i] = is_device_ptr(ins[i]);
-    return footprint_bytes(&c, on_dev, in.int_dtype);
+    return footprint_bytes(&c, on_dev, in.int_dtype, in.vvvv_on_host != 0);
 }
 
 void server_finish(ccsd_server* S, ServerReq* r, int state) {
@@ -2350,7 +2364,7 @@ int ccsd_create(const ccsd_config* cfg, const ccsd_inputs* in, void* stream, ccs
     h->st = (cudaStream_t)stream;
     Alloc al{h};
     auto fail = [&](int code) { ccsd_destroy(h); return code; };
-    int rc = setup_handle(h, al, ins, on_dev, in->int_dtype);
+    int rc = setup_handle(h, al, ins, on_dev, in->int_dtype, in->vvvv_on_host != 0);
     if (rc) return fail(rc);
     for (int ei : h->const_embeds) launch_embed(h, h->embeds[ei]);
     if (cudaMallocHost(&h->norm_host, sizeof(double)) != cudaSuccess) { cudaGetLastError(); h->norm_host = nullptr; return fail(CCSD_ERR_OOM); }
@@ -2714,6 +2728,7 @@ int ccsd_destroy(ccsd_t h) {
     for (cudaEvent_t e : h->ev1) cudaEventDestroy(e);
     if (h->norm_host) cudaFreeHost(h->norm_host);
     if (h->ev_norm) cudaEventDestroy(h->ev_norm);
+    if (h->host_registered) cudaHostUnregister(h->host_registered);
     delete h;
     return CCSD_OK;
 }

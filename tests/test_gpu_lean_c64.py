@@ -114,3 +114,44 @@ def test_c64_fp64_solve_chain(lib):
     t2 = torch.empty((spec.nk,) * 3 + (spec.nocc,) * 2 + (spec.nvir,) * 2, dtype=torch.complex128, device="cuda")
     S.get_amplitudes(t1, t2)
     assert abs(t2.cpu().numpy() - ref["t2"]).max() < 1e-7
+
+
+@pytest.mark.parametrize("spec", [cs.SynthSpec((3, 1, 1), 2, 1, 511), cs.SynthSpec((2, 2, 1), 1, 2, 512),
+                                  cs.SynthSpec((1, 1, 1), 1, 1, 513, time_reversal=False)],
+                         ids=["v1", "o1", "o1v1"])
+def test_degenerate_sizes_both_forms(lib, spec):
+    """One virtual or one occupied spin orbital per k: the packed (e < f, a < b, m < n)
+    index lists are empty, so only the momentum-pair halves of the contractions remain."""
+    from paper_1911_00242_gb300.binding import CCSD_FP64, CCSD_MIXED
+    inp = cs.generate(spec)
+    S, (d1, d2, r1, r2), R1, R2 = residual_pair(spec, inp, 53)
+    assert abs(r1.cpu().numpy() - R1).max() < 1e-12 and abs(r2.cpu().numpy() - R2).max() < 1e-12
+    for lean in (0, 1):
+        S, (d1, d2, r1, r2), R1, R2 = residual_pair(spec, inp, 53, precision=CCSD_MIXED, lean=lean)
+        scale = max(abs(R1).max(), abs(R2).max(), 1e-30)
+        assert abs(r1.cpu().numpy() - R1).max() / scale < 1e-5
+        assert abs(r2.cpu().numpy() - R2).max() / scale < 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_vvvv_read_in_place_from_host(lib, dtype):
+    """vvvv_on_host: the kernels read a host vvvv in place (mapped pinned memory):
+    the same residuals, bit for bit, as with vvvv in device memory, in both forms."""
+    from paper_1911_00242_gb300.binding import CCSD_MIXED, Solver
+    spec = cs.SynthSpec((3, 1, 1), 3, 5, 521, int_dtype=dtype)
+    inp = cs.generate(spec)
+    t1, t2 = cs.random_amplitudes(spec, 54)
+    d1, d2 = dev(t1), dev(t2)
+    for prec in (0, CCSD_MIXED):
+        out = []
+        for on_host in (False, True):
+            arrays = {k: dev(v) for k, v in inp.items()}
+            if on_host:
+                arrays["vvvv"] = np.ascontiguousarray(inp["vvvv"])        # pageable host memory
+            S = Solver(spec.grid, spec.nocc, spec.nvir, arrays, precision=prec, vvvv_on_host=on_host)
+            r1, r2 = torch.empty_like(d1), torch.empty_like(d2)
+            S.residual(d1, d2, r1, r2)
+            torch.cuda.synchronize()
+            out.append((r1.cpu().numpy(), r2.cpu().numpy()))
+            S.close()
+        assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
