@@ -352,16 +352,20 @@ __global__ void fock_terms_kernel(double2* __restrict__ Zr, const float2* __rest
         float2 p = make_float2(0.f, 0.f), q = make_float2(0.f, 0.f);
         const float2* trow = tb + (((long long)i * o + j) * v + a) * v;             // t_ij^{a f}
         const float2* fcol = fvvpT + (long long)kb * v * v + b;                     // F'^{b f}(kb) at f v
+#pragma unroll 4
         for (int f = 0; f < v; ++f) p = cfma(trow[f], fcol[(long long)f * v], p);
         const float2* oo = ooov + kk * o3v + ((long long)i * o + j) * o * v + b;    // <ij||r b>
         const float2* ta = t1 + (long long)ka * o * v + a;                          // t_r^a(ka)
+#pragma unroll 4
         for (int rr = 0; rr < o; ++rr) q = cfma_conjb(ta[rr * v], oo[(long long)rr * v], q);
         const float2* tn = tb + ((long long)i * o * v + a) * v + b;                 // t_in^{ab}, n stride v^2
         const float2* fo = foop + (long long)kj * o * o + j;                        // F'_{n j}(kj)
+#pragma unroll 4
         for (int n = 0; n < o; ++n) q = cfma(tn[(long long)n * vv], fo[n * o], q);
         const long long kjia = ((long long)kj * N + ki) * N + ka;
         const float2* vb = ovvv + kjia * ov3 + (long long)j * v * vv + (long long)a * v + b;   // <j c||a b>
         const float2* ti = t1 + ((long long)ki * o + i) * v;                        // t_i^c(ki)
+#pragma unroll 4
         for (int c = 0; c < v; ++c) q = cfma_conjb(ti[c], vb[(long long)c * vv], q);
         double2 z = Zr[e];
         z.x += 0.5 * ((double)p.x - (double)q.x);

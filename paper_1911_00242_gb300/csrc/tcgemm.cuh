@@ -511,6 +511,7 @@ __global__ void wprime_list_kernel(const WprimeListArgs w)
             const int ef = w.efl[ei];
             const float2 g = g0[ef];
             float sr = 0.f, si = 0.f;
+#pragma unroll 4
             for (int r = 0; r < o; ++r) {
                 // + t_r^b(kb) ovvv[kb,ka,ke](r,a,e,f) - t_r^a(ka) ovvv[ka,kb,ke](r,b,e,f)
                 const float2 tbr = tb[r * v];
