@@ -129,6 +129,16 @@ def load_traffic(kernel_name):
 SAMPLE_FOR = {"grid222_o8_v32": "grid221_o8_v32", "grid221_o8_v32": "grid221_o8_v32"}
 
 
+def max_over_ranks(x, dist, device):
+    """The slowest rank's value (the job's time); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def oracle_sample(name):
     from oracle import ccsd_k
     spec = cs.spec_for(name)
@@ -236,9 +246,16 @@ def run_mixed(args, spec, dev, depth, local, fp64_solve, fp64_ms_per_iter):
         secs = time.perf_counter() - t0
         e = S.energy().real
         S.close()
+        # the same solve without the polish: the accuracy of the mixed iterations alone
+        S = Solver(spec.grid, spec.nocc, spec.nvir, dev, precision=CCSD_MIXED, diis_depth=depth, max_iter=1000,
+                   conv_tol=SOLVE_TOL, mixed_tol=1e-7, polish_iters=0)
+        S.solve()
+        e0 = S.energy().real
+        S.close()
         out["solve"] = {"converged_mixed_phase": ok, "iterations_incl_polish": iters, "polish_iters": 2,
                         "max_resid": mr, "seconds": secs, "e_per_cell": e,
                         "abs_dE_vs_fp64": abs(e - fp64_solve["e_per_cell"]),
+                        "abs_dE_without_polish": abs(e0 - fp64_solve["e_per_cell"]),
                         "speedup_vs_fp64_solve": fp64_solve["seconds_est"] / secs}
     return out
 
@@ -401,6 +418,14 @@ def run_grid333(args, local):
         extra += 1
     e_fp64 = S.energy()
     S.close()
+    # the same solve without the polish: the accuracy of the mixed iterations alone
+    S = Solver(spec.grid, spec.nocc, spec.nvir, dev, precision=CCSD_MIXED, diis_depth=depth, max_iter=300,
+               conv_tol=1e-8, mixed_tol=1e-7, polish_iters=0, vvvv_on_host=args.vvvv_on_host)
+    t0 = time.perf_counter()
+    S.solve()
+    t_mixed_only = time.perf_counter() - t0
+    e_mixed_only = S.energy()
+    S.close()
 
     tc = [x for x in steps if x[3] > 0 and x[1] > 0 and x[3] / (x[2] / x[1] / 1e3) > 20e12]
     dom = max(tc, key=lambda x: x[2])
@@ -440,6 +465,8 @@ def run_grid333(args, local):
         "fp64": {"ms_per_iter": fp64_ms, "speedup_per_iter_mixed_vs_fp64": fp64_ms / ms,
                  "continued_iterations": fp64_timed + extra, "converged": bool(d), "max_resid": mr64,
                  "e_per_cell": e_fp64.real, "abs_dE_mixed_vs_fp64": abs(e_mixed.real - e_fp64.real),
+                 "abs_dE_mixed_without_polish": abs(e_mixed_only.real - e_fp64.real),
+                 "mixed_solve_without_polish_s": t_mixed_only,
                  "solve_seconds_est": fp64_solve_est,
                  "solve_est_basis": "FP64 from t = 0 taking the mixed solve's iteration count",
                  "speedup_solve_est": fp64_solve_est / t_solve, "step_ms": summ64},
@@ -563,10 +590,7 @@ def main():
     steps = S.trace_steps()
     S.trace(False)
     energy = S.energy()
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, f"cuda:{local}")
     value = world * args.steps / (ms / 1e3)
 
     # dominant kernel: the plan step with the most device time

@@ -241,26 +241,6 @@ __global__ void energy_partial(const double2* __restrict__ t1, const double2* __
     if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sr[0], si[0]);
 }
 
-// Re <x|y> partial sums over n complex elements (DIIS Gram matrix).
-__global__ void redot_partial(const double2* __restrict__ x, const double2* __restrict__ y, long long n,
-                              double* __restrict__ part)
-{
-    __shared__ double sm[256];
-    double s = 0.0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
-        const double2 a = x[e], b = y[e];
-        s += a.x * b.x + a.y * b.y;
-    }
-    sm[threadIdx.x] = s;
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
-}
-
 // Fixed-order final reductions (one block).
 __global__ void final_max(const double* __restrict__ part, int n, double* __restrict__ out)
 {
