@@ -260,6 +260,76 @@ def run_mixed(args, spec, dev, depth, local, fp64_solve, fp64_ms_per_iter):
     return out
 
 
+def run_ozaki(args, spec, dev, depth, fp64_solve, fp64_ms_per_iter, slices=7):
+    """The Ozaki form (FP64-accurate contractions on the BF16 tensor cores) on the same
+    inputs: iterations per second (traced), roofline of its dominant tensor-core GEMM,
+    and the time to solution with |dE| against the FP64 form's solution."""
+    import torch
+    from paper_1911_00242_gb300.binding import CCSD_OZAKI, Solver
+    S = Solver(spec.grid, spec.nocc, spec.nvir, dev, precision=CCSD_OZAKI, diis_depth=depth, max_iter=1000,
+               conv_tol=1e-12, oz_slices=slices)
+    for _ in range(args.warmup):
+        S.iterate(1)
+    torch.cuda.synchronize()
+    S.trace(True)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        S.iterate(1)
+        launches += S.launches()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    steps = S.trace_steps()
+    S.trace(False)
+    S.close()
+    pairs = slices * (slices + 1) // 2
+    tc = [s for s in steps if s[0] in ("ladder", "ring", "ring_W_t2", "hole_hole", "hole_hole_W")
+          and s[3] > 0 and s[1] > 0 and s[3] / (s[2] / max(s[1], 1) / 1e3) > 5e12]   # tensor-core steps
+    dom = max(tc, key=lambda s: s[2]) if tc else max(steps, key=lambda s: s[2])
+    name, calls, tot_ms, fl, by = dom
+    avg_s = tot_ms / max(calls, 1) / 1e3
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops") or 1900.0
+    achieved = fl / avg_s / 1e12
+    summ = {}
+    for st in steps:
+        if st[1]:
+            summ[st[0]] = round(summ.get(st[0], 0.0) + st[2] / st[1], 3)
+    out = {
+        "value": 1e3 / ms, "unit": "iter/s", "ms_per_step": ms, "steps": args.steps, "gpu_launches": launches,
+        "step_ms": summ, "slices": slices,
+        "precision": (f"Ozaki scheme: {slices} BF16 slices per operand row, {pairs} slice-pair products per "
+                      "contraction on tcgen05 (exact FP32 windows, double-float sum) for ladder, ring and "
+                      "hole-hole; FP64 elsewhere"),
+        "contraction_tflops": flops_per_iteration(spec) / (ms / 1e3) / 1e12,
+        "speedup_per_iter_vs_fp64": fp64_ms_per_iter / ms,
+        "roofline": {"kernel": f"oz_gemm_kernel ({name})", "bound": "tensor", "achieved": achieved,
+                     "peak": bf16, "unit": "TFLOP/s", "frac": achieved / bf16,
+                     "executed_tflops": pairs * achieved, "executed_frac": pairs * achieved / bf16,
+                     "peak_source": "measured bf16 %.0f TFLOP/s (of measured)" % bf16
+                     if peaks.get("bf16_tflops") else "fallback 1.9 PFLOP/s bf16",
+                     "flops_per_launch": fl, "launch_ms": avg_s * 1e3},
+    }
+    if fp64_solve is not None:
+        S = Solver(spec.grid, spec.nocc, spec.nvir, dev, precision=CCSD_OZAKI, diis_depth=depth, max_iter=1000,
+                   conv_tol=SOLVE_TOL, oz_slices=slices)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ok, iters, mr = S.solve()
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        e = S.energy().real
+        S.close()
+        out["solve"] = {"converged": ok, "iterations": iters, "max_resid": mr, "seconds": secs, "e_per_cell": e,
+                        "abs_dE_vs_fp64": abs(e - fp64_solve["e_per_cell"]),
+                        "speedup_vs_fp64_solve": fp64_solve["seconds_est"] / secs}
+    return out
+
+
 def run_batch(args, local):
     """Batched form: 64 problems (N_k in {1,2,4,8}, o 4..8, v 8..24) per iteration."""
     import torch
@@ -510,6 +580,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-form comparison")
+    ap.add_argument("--no-ozaki", action="store_true", help="skip the Ozaki-form comparison")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-solution comparison")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"], help="batch64: member precision")
     ap.add_argument("--rate", type=float, default=5.0, help="serve: requests per second")
@@ -641,6 +712,8 @@ def main():
 
     if not args.no_mixed:
         result["mixed"] = run_mixed(args, spec, dev, depth, local, result.get("fp64_solve"), ms / args.steps)
+    if not args.no_ozaki:
+        result["ozaki"] = run_ozaki(args, spec, dev, depth, result.get("fp64_solve"), ms / args.steps)
 
     if not args.no_e2e:
         # end to end through the C ABI from pinned host buffers: create (copies

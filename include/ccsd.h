@@ -51,6 +51,16 @@ extern "C" {
                            DIIS and energy stay FP64; ccsd_solve finishes with
                            polish_iters FP64 iterations                       */
 
+#define CCSD_OZAKI  2   /* FP64-accurate: the ladder, ring and hole-hole
+                           contractions on the BF16 tensor cores by the Ozaki
+                           scheme (error-free splitting of each operand row
+                           into oz_slices 7-bit slices under a power-of-two
+                           scale; slice products summed exactly in TMEM, then
+                           in double-float), everything else in FP64 (DFMA).
+                           Relative error of a contraction about
+                           2^-(7 oz_slices) of sum |a||b| (7 slices: FP64-like);
+                           operand rows must lie within about 1e-36 .. 1e36.  */
+
 #define CCSD_C128   0   /* integral blocks complex128                          */
 #define CCSD_C64    1   /* integral blocks complex64 (Fock blocks stay complex128):
                            the FP64 form widens every element exactly to double on
@@ -62,7 +72,7 @@ typedef struct ccsd_ctx* ccsd_t;
 typedef struct {
     int    nk_dims[3];    /* k grid (n1, n2, n3), each >= 1                     */
     int    nocc, nvir;    /* occupied / virtual spin orbitals per k, >= 1       */
-    int    precision;     /* CCSD_FP64 or CCSD_MIXED                            */
+    int    precision;     /* CCSD_FP64, CCSD_MIXED or CCSD_OZAKI                */
     int    diis_depth;    /* 0 = plain successive substitution (paper Sec. 4.4.12);
                              2..8 = Pulay DIIS over that many updates            */
     int    max_iter;      /* used by ccsd_solve                                 */
@@ -79,6 +89,7 @@ typedef struct {
                              1: that lean layout at any size, with the W' slabs
                              and the tensor-core ladder chunks cut to about a
                              third (same results, more launches)                */
+    int    oz_slices;     /* CCSD_OZAKI: slices per operand, 3..8 (0 = 7)       */
 } ccsd_config;
 
 typedef struct {
@@ -95,8 +106,14 @@ typedef struct {
                              unregisters it at ccsd_destroy); it is read once per
                              iteration (the ladder's W' formation), so this frees
                              its N^3 v^4 elements of device memory for about one
-                             host-link transfer of it per iteration.  0: host
-                             inputs are copied.  Ignored for a device pointer.  */
+                             host-link transfer of it per iteration.  The
+                             tensor-core forms with a CCSD_C64 vvvv gather each
+                             ladder chunk's blocks into a device staging area (a
+                             kernel reading the mapped memory with wide loads)
+                             and form W' from there; otherwise the kernels read
+                             the mapped memory directly.  0:
+                             host inputs are copied.  Ignored for a device
+                             pointer.  */
 } ccsd_inputs;
 
 /* Creates a solver for one problem.  `stream` is a cudaStream_t (NULL = the
@@ -132,6 +149,18 @@ int ccsd_tc_selftest(int M, int Ncols, int K, int nterms, unsigned long long see
  * the CUDA context stays usable.  Any other code means the failure path is broken. */
 int ccsd_tc_timeout_selftest(void);
 
+/* The Ozaki-scheme GEMM of CCSD_OZAKI on its own: C = A B^T for complex A
+ * (M x K) and B (Ncols x K), row-major, complex interleaved, all host arrays
+ * (C is overwritten), with `slices` BF16 slices per operand row (1..8).  The
+ * operands are split and multiplied by exactly the kernels the solver runs;
+ * tests compare C with an FP64 product on the host.  Sizes M, Ncols up to 4096,
+ * K up to 8192.  CCSD_ERR_TIMEOUT if a bounded device wait gave up. */
+int ccsd_oz_gemm(int M, int Ncols, int K, int slices, const double* A, const double* B, double* C);
+
+/* Failure-detection self-test of the Ozaki GEMM, as ccsd_tc_timeout_selftest:
+ * returns CCSD_ERR_TIMEOUT when the failure path works. */
+int ccsd_oz_timeout_selftest(void);
+
 /* One residual evaluation R(t) (paper Eqs. ori_EqSingle, ori_EqDouble with the
  * full Fock matrix inside F~): t1, t2 are read and r1, r2 written, all device
  * pointers in the layout above (r1 like t1, r2 like t2).  Does not touch the
@@ -154,8 +183,8 @@ int ccsd_iterate(ccsd_t h, int n_iter, int* done, double* max_resid);
 int ccsd_solve(ccsd_t h, int* iterations, double* max_resid);
 
 /* Arithmetic of the following ccsd_iterate/ccsd_residual calls: CCSD_FP64 on
- * any handle, CCSD_MIXED only on handles created with it.  Clears the DIIS
- * history. */
+ * any handle, CCSD_MIXED / CCSD_OZAKI only on handles created with that
+ * precision.  Clears the DIIS history. */
 int ccsd_set_precision(ccsd_t h, int precision);
 
 /* Correlation energy of the current amplitudes per unit cell (supercell
@@ -188,7 +217,8 @@ int ccsd_destroy(ccsd_t h);
 
 /* ---------------------------------------------------------------- batched form
  * n independent problems (any mix of grids and orbital counts, one precision,
- * plain successive substitution: diis_depth must be 0) iterate together on a
+ * CCSD_FP64 or CCSD_MIXED, plain successive substitution: diis_depth must be 0)
+ * iterate together on a
  * stream the batch owns.  Every contraction step of all members is one grouped
  * persistent kernel launch whose tile shape an autotuner picks on the first
  * iteration (one timing pass per candidate shape); an iteration -- residuals,

@@ -20,6 +20,7 @@ CCSD_ERR_DIVERGED = -5
 CCSD_ERR_TIMEOUT = -6
 CCSD_FP64 = 0
 CCSD_MIXED = 1
+CCSD_OZAKI = 2
 CCSD_C128 = 0
 CCSD_C64 = 1
 
@@ -30,7 +31,7 @@ class ccsd_config(ctypes.Structure):
     _fields_ = [("nk_dims", ctypes.c_int * 3), ("nocc", ctypes.c_int), ("nvir", ctypes.c_int),
                 ("precision", ctypes.c_int), ("diis_depth", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("conv_tol", ctypes.c_double), ("polish_iters", ctypes.c_int), ("mixed_tol", ctypes.c_double),
-                ("lean", ctypes.c_int)]
+                ("lean", ctypes.c_int), ("oz_slices", ctypes.c_int)]
 
 
 class ccsd_inputs(ctypes.Structure):
@@ -50,6 +51,9 @@ SYMBOLS = {
     "ccsd_tc_selftest": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
                           ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "ccsd_tc_timeout_selftest": ([], ctypes.c_int),
+    "ccsd_oz_gemm": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                      ctypes.c_void_p], ctypes.c_int),
+    "ccsd_oz_timeout_selftest": ([], ctypes.c_int),
     "ccsd_residual": ([ctypes.c_void_p] * 5, ctypes.c_int),
     "ccsd_iterate": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                       ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -150,13 +154,14 @@ def inputs_struct(arrays, vvvv_on_host=False):
 
 
 def make_config(grid, nocc, nvir, precision=CCSD_FP64, diis_depth=0, max_iter=100, conv_tol=1e-8,
-                polish_iters=2, mixed_tol=1e-7, lean=0):
+                polish_iters=2, mixed_tol=1e-7, lean=0, oz_slices=0):
     c = ccsd_config()
     c.nk_dims[0], c.nk_dims[1], c.nk_dims[2] = grid
     c.nocc, c.nvir, c.precision = nocc, nvir, precision
     c.diis_depth, c.max_iter, c.conv_tol = diis_depth, max_iter, conv_tol
     c.polish_iters, c.mixed_tol = polish_iters, mixed_tol
     c.lean = lean
+    c.oz_slices = oz_slices
     return c
 
 
@@ -345,3 +350,18 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def oz_gemm(A, B, slices=7):
+    """C = A B^T (complex128 numpy arrays, A: M x K, B: Ncols x K) through the
+    Ozaki-scheme tensor-core kernels of CCSD_OZAKI (ccsd_oz_gemm)."""
+    import numpy as np
+    lib = load()
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    B = np.ascontiguousarray(B, dtype=np.complex128)
+    M, K = A.shape
+    Nc, K2 = B.shape
+    assert K == K2
+    C = np.empty((M, Nc), dtype=np.complex128)
+    check(lib.ccsd_oz_gemm(M, Nc, K, slices, A.ctypes.data, B.ctypes.data, C.ctypes.data), "ccsd_oz_gemm")
+    return C

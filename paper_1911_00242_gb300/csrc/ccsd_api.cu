@@ -21,6 +21,7 @@
 #include "../../include/ccsd.h"
 #include "ccsd_kernels.cuh"
 #include "tcgemm.cuh"
+#include "ozaki.cuh"
 #include "zgemm_kb.cuh"
 
 #include <cuda.h>
@@ -29,6 +30,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <condition_variable>
 #include <cstdio>
@@ -90,26 +92,34 @@ struct PermPlan {
 struct Step {           // one element of the launch sequence
     int kind;           // 0 gemm, 1 copy, 2 perm, 3 tau, 4 antisym, 5 embed, 6 tensor-core gemm, 7 zero,
                         // 9 complex64 refresh of a buffer, 10 W' formation into the ladder's B operand,
-                        // 11 fused Fock/t1 terms of R2 (mixed form), 12 transposed complex64 F'vv
+                        // 11 fused Fock/t1 terms of R2 (mixed form), 12 transposed complex64 F'vv,
+                        // 13 staging of host vvvv blocks for one ladder chunk
     int idx;
     const char* name;
     double flops;       // algorithmic real flops per launch (complex MAC = 8)
     double bytes;       // algorithmic bytes per launch for the memory-bound steps
-    int mode = 0;       // 0 always; 1 only without tensor cores; 2 only with tensor cores (mixed form)
+    int mode = 0;       // 0 always; 1 only without tensor cores; 2 only with tensor cores (mixed
+                        // or Ozaki iterations); 3 only in mixed (FP32) iterations; 4 only outside them
 };
 
 struct EmbedPlan {      // operand preparation for the tensor-core GEMM
     int src;
+    bool oz = false;    // Ozaki slices (z) instead of split-TF32 parts (a)
     EmbedArgs a;        // a.src resolved at launch
+    OzEmbedArgs z;
 };
 
 struct WListPlan {      // fused W' formation + embedding for listed blocks and index pairs
+    bool oz = false;
     WprimeListArgs a;
+    OzWprimeArgs z;
 };
 
 struct TcPlan {
-    CUtensorMap mA_big, mA_small, mB_big, mB_small;
+    CUtensorMap mA_big, mA_small, mB_big, mB_small;   // Ozaki: mA_big / mB_big map the slice planes
+    bool oz = false;
     TcArgs a;           // a.C resolved at launch
+    OzArgs z;
     int c;
     int blocks;
 };
@@ -128,6 +138,11 @@ struct ccsd_ctx {
     bool in32[NBUF] = {};            // input stored complex64 only (shadow[] set, buf[] null)
     std::vector<void*> owned;        // device allocations to free
     void* host_registered = nullptr; // host vvvv registered by the library (unregistered at destroy)
+    const char* vvvv_host = nullptr; // host vvvv read in place (vvvv_on_host), or null
+    float2* vstage = nullptr;        // complex64 host vvvv: device staging of one ladder chunk's blocks
+    bool stage_w16 = false;          // the staging gather moves 16-byte words
+    std::vector<std::pair<const long long*, int>> stages;   // per staging step: source block offsets
+                                                            // (16-byte words, device table), block count
     size_t owned_bytes = 0;
     double2* amp = nullptr;          // [t1 | t2]
     double2* res = nullptr;          // [R1 | R2]
@@ -157,8 +172,11 @@ struct ccsd_ctx {
     int red_blocks = 0;
     const char* cur_name = "";
     int fp32 = 0;                    // contractions in FP32 arithmetic (mixed form)
+    int oz_on = 0;                   // Ozaki-scheme tensor-core contractions active (CCSD_OZAKI)
+    int oz_slices = 7;               // slices per operand row (CCSD_OZAKI)
     long long wab_cap_bytes = 12LL << 30;   // bound of the ladder's W' slab buffer
-    // mixed form: tensor-core operands (TF32 big/small parts of the real embeddings)
+    // mixed and Ozaki forms: tensor-core operands (TF32 big/small parts, or BF16 slice
+    // planes and row scales, of the real embeddings)
     std::vector<EmbedPlan> embeds;
     std::vector<TcPlan> tcs;
     std::vector<WListPlan> wlists;
@@ -403,10 +421,35 @@ int encode_map(CUtensorMap* m, const float* base, long long rows, int kpad, int 
     return r == CUDA_SUCCESS ? 0 : CCSD_ERR_CUDA;
 }
 
-struct TcBuf { float* big; float* small; long long rows; int kpad; };
+// The Ozaki operand: `planes` BF16 slice planes of rows x kpad, stacked as one 2D view.
+int encode_map_bf16(CUtensorMap* m, const uint16_t* base, long long rows, int kpad, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return CCSD_ERR_CUDA;
+    cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+    cuuint32_t box[2] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : CCSD_ERR_CUDA;
+}
+
+// A tensor-core operand: split-TF32 parts (big, small: rows x kpad floats each), or for
+// the Ozaki form BF16 slice planes (sl: planes x rows x kpad) and row scales (sc).
+struct TcBuf { float* big; float* small; long long rows; int kpad; uint16_t* sl = nullptr; float* sc = nullptr; };
 
 int tc_alloc(ccsd_ctx* h, Alloc& al, TcBuf& t, long long rows, int kpad) {
     t.rows = rows; t.kpad = kpad;
+    if (h->cfg.precision == CCSD_OZAKI) {
+        const size_t bytes = (size_t)rows * kpad * 2 * h->oz_slices;
+        t.big = t.small = nullptr;
+        t.sl = (uint16_t*)al.get(bytes);
+        t.sc = (float*)al.get((size_t)rows * 4);
+        if (al.err) return al.err;
+        if (!al.dry && cudaMemsetAsync(t.sl, 0, bytes, h->st) != cudaSuccess) return CCSD_ERR_CUDA;
+        return 0;
+    }
     t.big = (float*)al.get((size_t)rows * kpad * 4);
     t.small = (float*)al.get((size_t)rows * kpad * 4);
     if (al.err) return al.err;
@@ -437,6 +480,13 @@ int add_embed(ccsd_ctx* h, Alloc& al, int src, const TcBuf& dst, int mode, int R
     if (al.err) return al.err;
     e.a.big = dst.big; e.a.small = dst.small;
     e.a.nblk = (int)nblk; e.a.R = R; e.a.Kc = Kc; e.a.Kpad = dst.kpad; e.a.mode = mode;
+    if (h->cfg.precision == CCSD_OZAKI) {
+        e.oz = true;
+        e.z.srcoff = e.a.srcoff; e.z.srow = e.a.srow; e.z.scol = e.a.scol;
+        e.z.sl = dst.sl; e.z.sc = dst.sc; e.z.rows = dst.rows;
+        e.z.nblk = (int)nblk; e.z.R = R; e.z.Kc = Kc; e.z.Kpad = dst.kpad; e.z.mode = mode;
+        e.z.slices = h->oz_slices;
+    }
     h->embeds.push_back(e);
     if (constant) {
         h->const_embeds.push_back((int)h->embeds.size() - 1);
@@ -453,7 +503,10 @@ int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M,
            const std::vector<int>& colC, double alpha, int nterms,
            const std::vector<int>& nchunk_b = {}, const std::vector<long long>& offC2 = {},
            const std::vector<int>& colC2 = {}) {
-    if (A.kpad != B.kpad || A.kpad % TC_BK) return CCSD_ERR_INVALID;
+    const bool oz = h->cfg.precision == CCSD_OZAKI;
+    if (A.kpad != B.kpad || A.kpad % (oz ? OZ_BK : TC_BK)) return CCSD_ERR_INVALID;
+    if (oz && ((long long)h->oz_slices * A.rows > INT_MAX || (long long)h->oz_slices * B.rows > INT_MAX))
+        return CCSD_ERR_INVALID;
     if ((long long)rowA.size() != (long long)nbatch * nchunk || (long long)rowB.size() != (long long)nbatch * nchunk ||
         (long long)offC.size() != (long long)nbatch * M || (int)colC.size() * 2 != Nr) return CCSD_ERR_INVALID;
     for (int x : rowA) if (x < 0 || x >= A.rows) return CCSD_ERR_INVALID;
@@ -487,7 +540,24 @@ int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M,
     a.tiles_m = (M + TC_BM - 1) / TC_BM; a.tiles_n = (Nr + TC_BN - 1) / TC_BN;
     a.alpha_re = alpha; a.alpha_im = 0.0;
     t.blocks = a.tiles_m * a.tiles_n * nbatch;
-    if (!al.dry) {
+    if (oz) {
+        t.oz = true;
+        OzArgs& z = t.z;
+        z.rowA = a.rowA; z.rowB = a.rowB; z.offC = a.offC; z.colC = a.colC;
+        z.nchunk_b = a.nchunk_b; z.offC2 = a.offC2; z.colC2 = a.colC2;
+        z.err = a.err; z.spin_limit = a.spin_limit; z.skip_stage = -1;
+        z.scA = A.sc; z.scB = B.sc; z.rowsA = (int)A.rows; z.rowsB = (int)B.rows;
+        z.M = M; z.Nr = Nr; z.nchunk = nchunk; z.kstages = A.kpad / OZ_BK; z.slices = h->oz_slices;
+        z.tiles_m = (M + OZ_BM - 1) / OZ_BM; z.tiles_n = (Nr + OZ_BN - 1) / OZ_BN;
+        z.alpha_re = alpha; z.alpha_im = 0.0;
+        t.blocks = z.tiles_m * z.tiles_n * nbatch;
+        if (!al.dry) {
+            int rc;
+            if ((rc = encode_map_bf16(&t.mA_big, A.sl, A.rows * h->oz_slices, A.kpad, OZ_BM)) ||
+                (rc = encode_map_bf16(&t.mB_big, B.sl, B.rows * h->oz_slices, B.kpad, OZ_BN)))
+                return rc;
+        }
+    } else if (!al.dry) {
         int rc;
         if ((rc = encode_map(&t.mA_big, A.big, A.rows, A.kpad, TC_BM)) || (rc = encode_map(&t.mA_small, A.small, A.rows, A.kpad, TC_BM)) ||
             (rc = encode_map(&t.mB_big, B.big, B.rows, B.kpad, TC_BN)) || (rc = encode_map(&t.mB_small, B.small, B.rows, B.kpad, TC_BN)))
@@ -523,31 +593,36 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     int rc;
     auto G = [&](GemmSpec& s) { return finalize_gemm(h, al, s, work_need); };
     const bool mixed = h->cfg.precision == CCSD_MIXED;
+    const bool oz = h->cfg.precision == CCSD_OZAKI;
+    const bool tcp = mixed || oz;  // the plan has tensor-core variants of the large contractions
     TcBuf tc_la{}, tc_lap{}, tc_lb{}, tc_ra{}, tc_rb{}, tc_b1{}, tc_ha{}, tc_hb{}, tc_h2a{}, tc_h2b{};
     bool pooled = false;          // tensor-core operands share two buffers, rewritten every residual
-    long long lb_floats = 0;      // capacity (floats per part) of the ladder's B-operand buffer
+    long long lb_floats = 0;      // capacity (elements per part / slice plane) of the ladder's B-operand buffer
     float* pool_b = nullptr;      // the B-side pool (big part; the small part follows it)
     const long long nlt_vv = (long long)v * (v - 1) / 2;
-    const int kpl = (int)((2 * vv + TC_BK - 1) / TC_BK * TC_BK);
-    const int kplp = (int)((2 * nlt_vv + TC_BK - 1) / TC_BK * TC_BK);
-    if (mixed) {
-        const int kpr = (int)((2 * ov + TC_BK - 1) / TC_BK * TC_BK);
-        const int kpo = (int)((2 * oo + TC_BK - 1) / TC_BK * TC_BK);
+    const int KQ = oz ? OZ_BK : TC_BK;      // row padding: one pipeline stage of K
+    const int kpl = (int)((2 * vv + KQ - 1) / KQ * KQ);
+    const int kplp = (int)((2 * nlt_vv + KQ - 1) / KQ * KQ);
+    if (tcp) {
+        const int kpr = (int)((2 * ov + KQ - 1) / KQ * KQ);
+        const int kpo = (int)((2 * oo + KQ - 1) / KQ * KQ);
         const long long N3l = (long long)N * N * N;
         h->tc_err = (int*)al.get(sizeof(int));
         if (al.err) return al.err;
-        // complex64 copies: the inputs once here (unless stored so), t1 at the start of every
-        // residual, t2 and tau~ by the tau kernel
-        for (int bi = B_FOO_IN; bi <= B_T1; ++bi) {
-            if (bi == B_T2 || h->in32[bi]) continue;
-            h->shadow[bi] = (float2*)al.get((size_t)h->bufsize[bi] * 8);
+        if (mixed) {
+            // complex64 copies: the inputs once here (unless stored so), t1 at the start of every
+            // residual, t2 and tau~ by the tau kernel
+            for (int bi = B_FOO_IN; bi <= B_T1; ++bi) {
+                if (bi == B_T2 || h->in32[bi]) continue;
+                h->shadow[bi] = (float2*)al.get((size_t)h->bufsize[bi] * 8);
+                if (al.err) return al.err;
+                if (!al.dry && bi != B_T1)
+                    to_c64_kernel<<<ew_grid(h->bufsize[bi]), 256, 0, h->st>>>(h->shadow[bi], h->buf[bi], h->bufsize[bi]);
+            }
+            h->shadow[B_T2] = (float2*)al.get((size_t)h->n2 * 8);
+            h->shadow[B_TAUT] = (float2*)al.get((size_t)h->n2 * 8);
             if (al.err) return al.err;
-            if (!al.dry && bi != B_T1)
-                to_c64_kernel<<<ew_grid(h->bufsize[bi]), 256, 0, h->st>>>(h->shadow[bi], h->buf[bi], h->bufsize[bi]);
         }
-        h->shadow[B_T2] = (float2*)al.get((size_t)h->n2 * 8);
-        h->shadow[B_TAUT] = (float2*)al.get((size_t)h->n2 * 8);
-        if (al.err) return al.err;
         if (!al.dry && cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st) != cudaSuccess) return CCSD_ERR_CUDA;
         // ladder B rows of the largest packed class (floats per part)
         long long lad_max = 0, lad_batch = 0;    // largest class, largest single (ka, kb) batch
@@ -564,19 +639,21 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
             }
             lad_max = std::max(lad_max, blocks * per_block);
         }
-        // 8 GB of big + small parts (a third of the largest class in the lean layout), and
-        // never less than one batch
-        const long long lad_cap = std::max(lad_batch, h->cfg.lean ? lad_max / 3 : 1LL << 30);
+        // bytes per operand element: split-TF32 big + small parts, or the Ozaki slice planes
+        const long long epb = oz ? 2LL * h->oz_slices : 8LL;
+        // 8 GB of operand (a third of the largest class in the lean layout), and never less
+        // than one batch
+        const long long lad_cap = std::max(lad_batch, h->cfg.lean ? lad_max / 3 : (8LL << 30) / epb);
         // operand sizes (floats per part): A side (mode 0) and B side (mode 1)
         const long long fa[5] = {N3l * oo * kpl, N3l * oo * kplp, N3l * ov * kpr, N3l * oo * kpl, N3l * oo * kpo};
         const long long fb[4] = {N3l * 2 * ov * kpr, N3l * 2 * ov * kpr, N3l * 2 * oo * kpl, N3l * 2 * vv * kpo};
         long long total = std::min(lad_max, lad_cap);
         for (long long x : fa) total += x;
         for (long long x : fb) total += x;
-        pooled = h->cfg.lean || total * 8 > (24LL << 30);
+        pooled = h->cfg.lean || total * epb > (24LL << 30);
         if (!pooled) {
             lb_floats = std::max(1LL, std::min(lad_max, lad_cap));
-            if ((rc = tc_alloc(h, al, tc_la, N3l * oo, kpl)) || (rc = tc_alloc(h, al, tc_lap, N3l * oo, std::max(kplp, TC_BK))) ||
+            if ((rc = tc_alloc(h, al, tc_la, N3l * oo, kpl)) || (rc = tc_alloc(h, al, tc_lap, N3l * oo, std::max(kplp, KQ))) ||
                 (rc = tc_alloc(h, al, tc_lb, lb_floats / kpl + 1, kpl)) ||
                 (rc = tc_alloc(h, al, tc_ra, N3l * ov, kpr)) || (rc = tc_alloc(h, al, tc_rb, N3l * 2 * ov, kpr)) ||
                 (rc = tc_alloc(h, al, tc_b1, N3l * 2 * ov, kpr)) ||
@@ -591,24 +668,38 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
             long long pa = 0, pb = std::min(lad_max, lad_cap);
             for (long long x : fa) pa = std::max(pa, x);
             for (long long x : fb) pb = std::max(pb, x);
-            pb = std::max(pb, h->bufsize[B_WAB] * 2);
+            // the FP64 W' slab (16 bytes per element) shares the B pool
+            pb = std::max(pb, (h->bufsize[B_WAB] * 16 + epb - 1) / epb);
             // the small part starts right after the big part: keep it 256-byte aligned (TMA
             // needs 16-byte aligned bases)
             pa = (pa + 63) / 64 * 64;
             pb = (pb + 63) / 64 * 64;
-            float* A = (float*)al.get((size_t)pa * 8);
-            pool_b = (float*)al.get((size_t)pb * 8);
+            float* A = (float*)al.get((size_t)(pa * epb));
+            pool_b = (float*)al.get((size_t)(pb * epb));
+            float* scA = nullptr;
+            float* scB = nullptr;
+            if (oz) {   // row scales of the largest A-side and B-side operands
+                const long long ra = N3l * std::max(oo, ov);
+                const long long rb = std::max({N3l * 2 * ov, N3l * 2 * oo, N3l * 2 * vv, pb / kpl + 1});
+                scA = (float*)al.get((size_t)ra * 4);
+                scB = (float*)al.get((size_t)rb * 4);
+            }
             if (al.err) return al.err;
             lb_floats = pb;
-            auto view = [](float* base, long long floats, long long rows, int kpad) {
+            auto view = [oz](float* base, float* sc, long long floats, long long rows, int kpad) {
+                if (oz) {
+                    TcBuf t{nullptr, nullptr, rows, kpad, (uint16_t*)base, sc};
+                    return t;
+                }
                 TcBuf t{base, base + floats, rows, kpad};
                 return t;
             };
-            tc_la = view(A, pa, N3l * oo, kpl); tc_lap = view(A, pa, N3l * oo, std::max(kplp, TC_BK));
-            tc_ra = view(A, pa, N3l * ov, kpr); tc_ha = view(A, pa, N3l * oo, kpl); tc_h2a = view(A, pa, N3l * oo, kpo);
-            tc_rb = view(pool_b, pb, N3l * 2 * ov, kpr); tc_b1 = view(pool_b, pb, N3l * 2 * ov, kpr);
-            tc_hb = view(pool_b, pb, N3l * 2 * oo, kpl); tc_h2b = view(pool_b, pb, N3l * 2 * vv, kpo);
-            tc_lb = view(pool_b, pb, pb / kpl, kpl);
+            tc_la = view(A, scA, pa, N3l * oo, kpl); tc_lap = view(A, scA, pa, N3l * oo, std::max(kplp, KQ));
+            tc_ra = view(A, scA, pa, N3l * ov, kpr); tc_ha = view(A, scA, pa, N3l * oo, kpl);
+            tc_h2a = view(A, scA, pa, N3l * oo, kpo);
+            tc_rb = view(pool_b, scB, pb, N3l * 2 * ov, kpr); tc_b1 = view(pool_b, scB, pb, N3l * 2 * ov, kpr);
+            tc_hb = view(pool_b, scB, pb, N3l * 2 * oo, kpl); tc_h2b = view(pool_b, scB, pb, N3l * 2 * vv, kpo);
+            tc_lb = view(pool_b, scB, pb, pb / kpl, kpl);
             h->buf[B_WAB] = (double2*)pool_b;
         }
     }
@@ -620,7 +711,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     // ---------------- tau, tau~
     if (mixed) {
         Step st{9, B_T1, "tau", 0.0, 24.0 * h->n1};
-        st.mode = 2;
+        st.mode = 3;
         h->seq.push_back(st);
     }
     h->seq.push_back({3, 0, "tau", 0.0, 16.0 * (3.0 * h->n2 + h->n1)});
@@ -875,10 +966,10 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
             s.rowC = tab({{(int)oo, 1}});
             for (int x : nc) { s.colC.push_back(x * (int)oo); s.colC2.push_back(swap_pair(x, o) * (int)oo); }
             if ((rc = G(s))) return rc;
-            if (mixed) h->seq.back().mode = 1;
+            if (tcp) h->seq.back().mode = 1;
         }
     }
-    if (mixed) {
+    if (tcp) {
         // X on tensor cores, one batch per momentum sum S = km + kn = ki + kj:
         // rows (km, mn) of <mn||ef> (constant operand), columns (ki, ij) of tau, K = (ke, ef)
         std::vector<long long> so;
@@ -936,10 +1027,10 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
             s.rowC = tab({{(int)oo, vv}}); s.colC = nc;
             for (int x : nc) s.colC2.push_back(swap_pair(x, v));
             if ((rc = G(s))) return rc;
-            if (mixed) h->seq.back().mode = 1;
+            if (tcp) h->seq.back().mode = 1;
         }
     }
-    if (mixed) {
+    if (tcp) {
         // R2 += 1/2 tau_mn^ab Whh_mnij on tensor cores, one batch per S = ki + kj:
         // rows (ki, ij) of Whh^T, columns (ka, ab) of tau, K = (km, mn)
         std::vector<long long> so;
@@ -1067,10 +1158,11 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                 }
             }
             // the tensor-core path forms W' inside its operand embedding
-            if (mixed) for (size_t i = w_first; i < h->seq.size(); ++i) h->seq[i].mode = 1;
+            if (tcp) for (size_t i = w_first; i < h->seq.size(); ++i) h->seq[i].mode = 1;
         }
     }
-    if (mixed) {
+    long long stage_blocks = 0;       // largest number of staged vvvv blocks of one ladder chunk
+    if (tcp) {
         // Tensor-core ladder, antisymmetry-packed like the FP64 one: outputs (ka < kb | ka = kb,
         // a < b) with the mirror R2(ba) = -R2(ab), contractions over (ke < kf | ke = kf, e < f).
         // A' = tau rows [S = ki + kj][ke][ki](ij), columns the (e f) list; B' = W' formed
@@ -1116,6 +1208,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                     if (rows > cap_rows) return CCSD_ERR_INVALID;
                     TcBuf B{tc_lb.big, tc_lb.big + lb_floats, std::max(rows, 1LL), A.kpad};
                     if (!pooled) B.small = tc_lb.small;
+                    if (oz) { B.big = B.small = nullptr; B.sl = tc_lb.sl; B.sc = tc_lb.sc; }
                     int nchmax = 0;
                     for (size_t bb = b0; bb < b1; ++bb) nchmax = std::max<int>(nchmax, (int)chunks[bb].size());
                     std::vector<int> blk3, ra, rb, cc, cc2, cnt;
@@ -1140,6 +1233,25 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                             }
                     }
                     WListPlan wl{};
+                    if (h->vvvv_host && h->in32[B_VVVV]) {
+                        // complex64 vvvv in host memory: the chunk's blocks are copied into a
+                        // device staging area first (bulk DMA), and W' reads them there
+                        const long long v4 = vv * vv;
+                        std::vector<long long> src, vofs;
+                        for (size_t q = 0; q < blk3.size() / 3; ++q) {
+                            src.push_back(((long long)blk3[3 * q] * N + blk3[3 * q + 1]) * N * v4 + (long long)blk3[3 * q + 2] * v4);
+                            vofs.push_back((long long)q * v4);
+                        }
+                        stage_blocks = std::max<long long>(stage_blocks, (long long)src.size());
+                        h->stage_w16 = v % 2 == 0 && ((uintptr_t)h->vvvv_host % 16) == 0;
+                        if (h->stage_w16) for (long long& x : src) x /= 2;   // complex64 pairs (16-byte words)
+                        h->stages.push_back({upload(al, src, h->st), (int)src.size()});
+                        if (al.err) return al.err;
+                        Step st{13, (int)h->stages.size() - 1, "ladder_W", 0.0, 16.0 * (double)src.size() * v4};
+                        st.mode = 2;
+                        h->seq.push_back(st);
+                        wl.a.vofs = upload(al, vofs, h->st);
+                    }
                     wl.a.big = B.big; wl.a.small = B.small;
                     wl.a.blk = upload(al, blk3, h->st);
                     wl.a.abl = upload(al, abl, h->st);
@@ -1147,6 +1259,14 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                     if (al.err) return al.err;
                     wl.a.nblk = (int)(blk3.size() / 3); wl.a.nab = (int)abl.size(); wl.a.nef = (int)efl.size();
                     wl.a.N = N; wl.a.o = o; wl.a.v = v; wl.a.Kpad = A.kpad;
+                    if (oz) {
+                        wl.oz = true;
+                        OzWprimeArgs& z = wl.z;
+                        z.sl = B.sl; z.sc = B.sc; z.rows = B.rows;
+                        z.blk = wl.a.blk; z.abl = wl.a.abl; z.efl = wl.a.efl; z.vofs = wl.a.vofs;
+                        z.nblk = wl.a.nblk; z.nab = wl.a.nab; z.nef = wl.a.nef;
+                        z.N = N; z.o = o; z.v = v; z.Kpad = A.kpad; z.slices = h->oz_slices;
+                    }
                     h->wlists.push_back(wl);
                     Step st{10, (int)h->wlists.size() - 1, "ladder_W", 0.0, 40.0 * (double)wl.a.nblk * wl.a.nab * wl.a.nef};
                     st.mode = 2;
@@ -1159,6 +1279,10 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                 }
             }
         }
+    }
+    if (stage_blocks > 0) {
+        h->vstage = (float2*)al.get((size_t)stage_blocks * (size_t)(vv * vv) * 8);
+        if (al.err) return al.err;
     }
     h->cur_name = "ring_W_t1";
     // ring: W~_jn^bf (Eq. Def_Woovv), stored [kj,kn,kb](j,n,b,f), kf = kn + kb - kj
@@ -1229,9 +1353,9 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowB = tab({{o, vv}, {v, 1}}); s.colB = tab({{o, o * vv}, {v, v}});
         s.rowC = tab({{o, o * vv}, {v, v}}); s.colC = tab({{o, vv}, {v, 1}});
         if ((rc = G(s))) return rc;
-        if (mixed) h->seq.back().mode = 1;
+        if (tcp) h->seq.back().mode = 1;
     }
-    if (mixed) {
+    if (tcp) {
         // Both ring GEMMs on tensor cores, one batch per momentum transfer D:
         //   ring W:  rows (kj, j, b) with kb = kj - D, columns (kn, n, f) with kf = kn - D
         //   ring C:  rows (ki, i, a) with ka = ki - D, columns (kj, j, b) with kb = kj + D
@@ -1281,9 +1405,9 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s.rowB = tab({{o, vv}, {v, 1}}); s.colB = tab({{o, o * vv}, {v, v}});
         s.rowC = tab({{o, o * vv}, {v, v}}); s.colC = tab({{o, vv}, {v, 1}});
         if ((rc = G(s))) return rc;
-        if (mixed) h->seq.back().mode = 1;
+        if (tcp) h->seq.back().mode = 1;
     }
-    if (mixed) {
+    if (tcp) {
         add_zero(h, B_ZR);
         // B_ring[D][kn][kj]: rows (j,b), columns (n,f) of W~[kj, kn, kb], kb = kj + D
         std::vector<long long> so;
@@ -1383,15 +1507,15 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         if ((rc = G(s))) return rc;
     }
     if (mixed) {
-        // the four GEMMs above run in FP64 iterations only; mixed iterations fuse them
-        for (size_t i = fock_first; i < h->seq.size(); ++i) h->seq[i].mode = 1;
+        // the four GEMMs above run outside mixed iterations only; mixed iterations fuse them
+        for (size_t i = fock_first; i < h->seq.size(); ++i) h->seq[i].mode = 4;
         h->shadow[B_FVVP] = (float2*)al.get((size_t)h->bufsize[B_FVVP] * 8);
         h->shadow[B_FOOP] = (float2*)al.get((size_t)h->bufsize[B_FOOP] * 8);
         if (al.err) return al.err;
         Step s1{12, B_FVVP, h->cur_name, 0.0, 24.0 * h->bufsize[B_FVVP]};
         Step s2{9, B_FOOP, h->cur_name, 0.0, 24.0 * h->bufsize[B_FOOP]};
         Step s3{11, 0, h->cur_name, 8.0 * 2.0 * (o + v) * (double)h->n2, 8.0 * 4.0 * h->n2};
-        s1.mode = s2.mode = s3.mode = 2;
+        s1.mode = s2.mode = s3.mode = 3;
         h->seq.push_back(s1); h->seq.push_back(s2); h->seq.push_back(s3);
     }
     h->seq.push_back({4, 0, "antisym_R2", 0.0, 16.0 * 3.0 * h->n2});
@@ -1456,6 +1580,14 @@ int launch_gemm(ccsd_ctx* h, GemmPlan& p) {
 }
 
 void launch_embed(ccsd_ctx* h, EmbedPlan& e) {
+    if (e.oz) {
+        OzEmbedArgs z = e.z;
+        z.src = h->buf[e.src];
+        z.src32 = h->in32[e.src] ? h->shadow[e.src] : nullptr;
+        oz_embed_kernel<<<row_grid((long long)z.nblk * z.R), z.Kpad / 2 >= 256 ? 256 : 128, 0, h->st>>>(z);
+        ++h->launches;
+        return;
+    }
     EmbedArgs a = e.a;
     a.src = h->buf[e.src];
     a.src32 = h->in32[e.src] ? h->shadow[e.src] : nullptr;
@@ -1464,6 +1596,18 @@ void launch_embed(ccsd_ctx* h, EmbedPlan& e) {
 }
 
 void launch_tc(ccsd_ctx* h, TcPlan& t) {
+    if (t.oz) {
+        static bool oz_attr_set = false;
+        if (!oz_attr_set) {
+            cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
+            oz_attr_set = true;
+        }
+        OzArgs z = t.z;
+        z.C = h->buf[t.c];
+        oz_gemm_kernel<<<t.blocks, OZ_THREADS, OZ_SMEM_BYTES, h->st>>>(t.mA_big, t.mB_big, z);
+        ++h->launches;
+        return;
+    }
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
@@ -1476,11 +1620,12 @@ void launch_tc(ccsd_ctx* h, TcPlan& t) {
 }
 
 // Accumulate the elapsed time of traced steps [a, b) (synchronizes the stream).
+bool step_active(const ccsd_ctx* h, const Step& s);
+
 int trace_collect(ccsd_ctx* h, size_t a, size_t b) {
     CK(cudaStreamSynchronize(h->st));
-    const bool tc = h->fp32 && h->cfg.precision == CCSD_MIXED;
     for (size_t i = a; i < b; ++i) {
-        if (i < h->seq.size() && ((h->seq[i].mode == 1 && tc) || (h->seq[i].mode == 2 && !tc))) continue;
+        if (i < h->seq.size() && !step_active(h, h->seq[i])) continue;
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, h->ev0[i], h->ev1[i]));
         h->step_ms[i] += ms;
@@ -1490,8 +1635,15 @@ int trace_collect(ccsd_ctx* h, size_t a, size_t b) {
 }
 
 bool step_active(const ccsd_ctx* h, const Step& s) {
-    const bool tc = h->fp32 && h->cfg.precision == CCSD_MIXED;
-    return !((s.mode == 1 && tc) || (s.mode == 2 && !tc));
+    const bool mixed_it = h->fp32 && h->cfg.precision == CCSD_MIXED;   // a mixed (FP32) iteration
+    const bool tc = mixed_it || h->oz_on;                              // tensor-core contractions
+    switch (s.mode) {
+        case 1: return !tc;
+        case 2: return tc;
+        case 3: return mixed_it;
+        case 4: return !mixed_it;
+        default: return true;
+    }
 }
 
 // Launches plan step si (no tracing, no mode check).
@@ -1536,9 +1688,38 @@ void launch_step(ccsd_ctx* h, size_t si) {
             case 7:
                 cudaMemsetAsync(h->buf[s.idx], 0, (size_t)h->bufsize[s.idx] * 16, h->st);
                 break;
+            case 13: {   // stage host vvvv blocks into device memory (a gather through the mapping)
+                const long long v4 = (long long)v * v * v * v;
+                if (h->stage_w16)    // 16-byte words (v^4 even, host array 16-byte aligned)
+                    gather_blocks_kernel<<<152 * 8, 256, 0, h->st>>>((float4*)h->vstage, (const float4*)h->shadow[B_VVVV],
+                                                                     h->stages[s.idx].first, h->stages[s.idx].second, v4 / 2);
+                else
+                    gather_blocks_kernel<<<152 * 8, 256, 0, h->st>>>(h->vstage, (const float2*)h->shadow[B_VVVV],
+                                                                     h->stages[s.idx].first, h->stages[s.idx].second, v4);
+                ++h->launches;
+                break;
+            }
             case 10: {
+                if (h->wlists[s.idx].oz) {
+                    static bool oz_w_attr = false;
+                    if (!oz_w_attr) {
+                        cudaFuncSetAttribute(oz_wprime_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                        oz_w_attr = true;
+                    }
+                    OzWprimeArgs z = h->wlists[s.idx].z;
+                    if (z.vofs) { z.vvvv32 = h->vstage; z.vvvv = nullptr; }
+                    else if (h->in32[B_VVVV]) { z.vvvv32 = h->shadow[B_VVVV]; z.vvvv = nullptr; }
+                    else { z.vvvv = h->buf[B_VVVV]; z.vvvv32 = nullptr; }
+                    if (h->in32[B_OVVV]) { z.ovvv32 = h->shadow[B_OVVV]; z.ovvv = nullptr; }
+                    else { z.ovvv = h->buf[B_OVVV]; z.ovvv32 = nullptr; }
+                    z.t1 = h->buf[B_T1];
+                    oz_wprime_kernel<<<row_grid((long long)z.nblk * z.nab), 256, (size_t)z.nef * 16, h->st>>>(z);
+                    ++h->launches;
+                    break;
+                }
                 WprimeListArgs a = h->wlists[s.idx].a;
-                a.vvvv = h->shadow[B_VVVV]; a.ovvv = h->shadow[B_OVVV]; a.t1 = h->shadow[B_T1];
+                a.vvvv = a.vofs ? h->vstage : h->shadow[B_VVVV];
+                a.ovvv = h->shadow[B_OVVV]; a.t1 = h->shadow[B_T1];
                 wprime_list_kernel<<<row_grid((long long)a.nblk * a.nab), 256, 0, h->st>>>(a);
                 ++h->launches;
                 break;
@@ -1577,7 +1758,7 @@ int run_residual_async(ccsd_ctx* h) {
 
 // A bounded wait inside a tensor-core GEMM gave up: report, clear, fail (synchronizes).
 int check_tc_err(ccsd_ctx* h) {
-    if (!(h->fp32 && h->cfg.precision == CCSD_MIXED) || !h->tc_err) return 0;
+    if (!((h->fp32 && h->cfg.precision == CCSD_MIXED) || h->oz_on) || !h->tc_err) return 0;
     int flag = 0;
     CK(cudaMemcpyAsync(&flag, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
@@ -1820,8 +2001,12 @@ bool valid_cfg(const ccsd_config* c) {
     if (!c) return false;
     for (int i = 0; i < 3; ++i) if (c->nk_dims[i] < 1 || c->nk_dims[i] > 64) return false;
     if (c->nocc < 1 || c->nvir < 1 || c->nocc > 256 || c->nvir > 512) return false;
-    if (c->precision != CCSD_FP64 && c->precision != CCSD_MIXED) return false;
+    if (c->precision != CCSD_FP64 && c->precision != CCSD_MIXED && c->precision != CCSD_OZAKI) return false;
     if (c->precision == CCSD_MIXED && (c->polish_iters < 0 || c->polish_iters > 100)) return false;
+    if (c->precision == CCSD_OZAKI) {
+        if (c->oz_slices != 0 && (c->oz_slices < 3 || c->oz_slices > OZ_MAX_SLICES)) return false;
+        if (c->nvir > 96) return false;       // one W' row (v^2 complex) is staged in shared memory
+    }
     if (c->diis_depth < 0 || c->diis_depth == 1 || c->diis_depth > 8) return false;
     if (c->lean != 0 && c->lean != 1) return false;
     const long long N = (long long)c->nk_dims[0] * c->nk_dims[1] * c->nk_dims[2];
@@ -1856,6 +2041,7 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
             // vvvv read in place from host memory (mapped, pinned): no device copy
             if (al.dry) {
                 d = (void*)(uintptr_t)256;
+                h->vvvv_host = (const char*)d;
             } else {
                 void* hp = const_cast<void*>(ins[i]);
                 cudaError_t e = cudaHostRegister(hp, bytes, cudaHostRegisterMapped);
@@ -1863,6 +2049,7 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
                 else if (e == cudaErrorHostMemoryAlreadyRegistered) cudaGetLastError();
                 else { cudaGetLastError(); return CCSD_ERR_CUDA; }
                 if (cudaHostGetDevicePointer(&d, hp, 0) != cudaSuccess) { cudaGetLastError(); return CCSD_ERR_CUDA; }
+                h->vvvv_host = (const char*)hp;
             }
         } else {
             d = al.get(bytes);
@@ -1950,7 +2137,7 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
     if (h->cfg.precision == CCSD_MIXED) {
         // GEMM steps that a mixed handle runs in FP32 (all but the FP64-only ones)
         for (const Step& st : h->seq) {
-            if (st.kind != 0 || st.mode == 1) continue;
+            if (st.kind != 0 || st.mode == 1 || st.mode == 4) continue;
             const GemmArgs& g32 = h->gemms[st.idx].args32;
             if (g32.nsplit > 1) work_need = std::max(work_need, (size_t)g32.nsplit * g32.nbatch * g32.M * g32.N);
         }
@@ -1974,6 +2161,8 @@ void init_ctx(ccsd_ctx* h, const ccsd_config* cfg) {
         h->wab_cap_bytes = 16 * N * v * v * v * v * std::max<long long>(1, (N * (N + 1) / 2 + 2) / 3);
     }
     h->fp32 = cfg->precision == CCSD_MIXED ? 1 : 0;
+    h->oz_on = cfg->precision == CCSD_OZAKI ? 1 : 0;
+    h->oz_slices = cfg->oz_slices ? cfg->oz_slices : 7;
     const long long N = h->N;
     h->n1 = N * h->o * h->v;
     h->n2 = N * N * N * h->o * h->o * h->v * h->v;
@@ -2335,9 +2524,71 @@ int tc_selftest_impl(int M, int Ncols, int K, int nterms, unsigned long long see
     return CCSD_OK;
 }
 
+// C = A B^T (complex, M x K and Ncols x K, row-major) through the Ozaki kernels:
+// embed both operands, one oz_gemm launch.  skip_stage >= 0 leaves that stage
+// unloaded (short wait limit) to exercise the bounded-wait failure path.
+int oz_gemm_impl(int M, int Ncols, int K, int slices, const double* A, const double* B, double* C, int skip_stage) {
+    ccsd_ctx* h = new (std::nothrow) ccsd_ctx();
+    if (!h) return CCSD_ERR_OOM;
+    h->cfg.precision = CCSD_OZAKI;
+    h->oz_slices = slices;
+    h->oz_on = 1;
+    Alloc al{h};
+    auto fail = [&](int code) { ccsd_destroy(h); return code; };
+    const long long nA = (long long)M * K, nB = (long long)Ncols * K, nC = (long long)M * Ncols;
+    std::vector<double2> hA((size_t)nA), hB((size_t)nB);
+    std::memcpy(hA.data(), A, (size_t)nA * 16);
+    std::memcpy(hB.data(), B, (size_t)nB * 16);
+    h->buf[B_STA] = upload(al, hA, h->st); h->bufsize[B_STA] = nA;
+    h->buf[B_STB] = upload(al, hB, h->st); h->bufsize[B_STB] = nB;
+    h->buf[B_ZR] = (double2*)al.get((size_t)nC * 16); h->bufsize[B_ZR] = nC;
+    h->tc_err = (int*)al.get(sizeof(int));
+    if (al.err) return fail(al.err);
+    if (cudaMemsetAsync(h->buf[B_ZR], 0, (size_t)nC * 16, h->st) != cudaSuccess ||
+        cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
+    const int kpad = (2 * K + OZ_BK - 1) / OZ_BK * OZ_BK;
+    TcBuf ta{}, tb{};
+    int rc;
+    if ((rc = tc_alloc(h, al, ta, M, kpad)) || (rc = tc_alloc(h, al, tb, 2LL * Ncols, kpad))) return fail(rc);
+    if ((rc = add_embed(h, al, B_STA, ta, 0, M, K, {0}, tab({{M, K}}), tab({{K, 1}}), false)) ||
+        (rc = add_embed(h, al, B_STB, tb, 1, Ncols, K, {0}, tab({{Ncols, K}}), tab({{K, 1}}), false)))
+        return fail(rc);
+    std::vector<long long> oc;
+    for (int m = 0; m < M; ++m) oc.push_back((long long)m * Ncols);
+    if ((rc = add_tc(h, al, ta, tb, B_ZR, M, 2 * Ncols, 1, 1, {0}, {0}, oc, tab({{Ncols, 1}}), 1.0, 1)))
+        return fail(rc);
+    if (skip_stage >= 0) {
+        h->tcs[0].z.skip_stage = skip_stage;
+        h->tcs[0].z.spin_limit = 1LL << 14;
+    }
+    launch_embed(h, h->embeds[0]);
+    launch_embed(h, h->embeds[1]);
+    launch_tc(h, h->tcs[0]);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
+    int flag = 0;
+    if (cudaMemcpy(&flag, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(C, h->buf[B_ZR], (size_t)nC * 16, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(CCSD_ERR_CUDA);
+    if (flag) return fail(CCSD_ERR_TIMEOUT);
+    ccsd_destroy(h);
+    return CCSD_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int ccsd_oz_gemm(int M, int Ncols, int K, int slices, const double* A, const double* B, double* C) {
+    if (M < 1 || Ncols < 1 || K < 1 || M > 4096 || Ncols > 4096 || K > 8192 || slices < 1 ||
+        slices > OZ_MAX_SLICES || !A || !B || !C)
+        return CCSD_ERR_INVALID;
+    return oz_gemm_impl(M, Ncols, K, slices, A, B, C, -1);
+}
+
+int ccsd_oz_timeout_selftest(void) {
+    std::vector<double> a(128 * 64 * 2, 1.0), c(128 * 128 * 2, 0.0);
+    return oz_gemm_impl(128, 128, 64, 2, a.data(), a.data(), c.data(), 1);
+}
 
 int ccsd_tc_selftest(int M, int Ncols, int K, int nterms, unsigned long long seed, double* rel_err) {
     if (M < 1 || Ncols < 1 || K < 1 || M > 4096 || Ncols > 4096 || K > 4096 || (nterms != 1 && nterms != 3) || !rel_err)
@@ -2438,8 +2689,9 @@ int ccsd_solve(ccsd_t h, int* iterations, double* max_resid) {
 
 int ccsd_set_precision(ccsd_t h, int precision) {
     if (!h) return CCSD_ERR_INVALID;
-    if (precision == CCSD_FP64) h->fp32 = 0;
+    if (precision == CCSD_FP64) { h->fp32 = 0; h->oz_on = 0; }
     else if (precision == CCSD_MIXED && h->cfg.precision == CCSD_MIXED) h->fp32 = 1;
+    else if (precision == CCSD_OZAKI && h->cfg.precision == CCSD_OZAKI) h->oz_on = 1;
     else return CCSD_ERR_INVALID;
     h->diis_count = 0;
     h->diis_next = 0;
@@ -2525,7 +2777,8 @@ int ccsd_batch_create(int n, const ccsd_config* cfgs, const ccsd_inputs* inputs,
     if (!out || n < 1 || n > 4096 || !cfgs || !inputs) return CCSD_ERR_INVALID;
     *out = nullptr;
     for (int i = 0; i < n; ++i)
-        if (cfgs[i].precision != cfgs[0].precision || cfgs[i].diis_depth != 0) return CCSD_ERR_INVALID;
+        if (cfgs[i].precision != cfgs[0].precision || cfgs[i].diis_depth != 0 || cfgs[i].precision == CCSD_OZAKI)
+            return CCSD_ERR_INVALID;
     ccsd_batch* B = new (std::nothrow) ccsd_batch();
     if (!B) return CCSD_ERR_OOM;
     B->n = n;

@@ -1,0 +1,587 @@
+// FP64-accurate complex contractions on the BF16 tensor cores (Ozaki scheme:
+// Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59 (2012) 95-118).  The operands
+// are split error-free into BF16 slices of small integers; the tensor core sums
+// the slice products exactly, and the exact partial sums are added in a
+// double-float register accumulator.
+//
+// Real embedding.  As for the split-TF32 kernel, a complex C = A B^T is the real
+// GEMM C'[m][n'] = sum_k A'[m][k] B'[n'][k] with
+//   A'[m][2k + r] = (Re a_mk, Im a_mk)
+//   B'[2n][2k + r] = (Re b_nk, -Im b_nk),  B'[2n+1][2k + r] = (Im b_nk, Re b_nk).
+//
+// Splitting (per operand row).  Row i of an embedded operand gets a power-of-two
+// scale 2^E_i > max_k |x_ik| and s slices of 7 bits:
+//   y_0 = x 2^-E_i in (-1, 1),   v_p = rint(2^7 y_p),   y_{p+1} = 2^7 y_p - v_p
+//   x = 2^E_i sum_{p<s} v_p 2^{-7(p+1)} + e,   |e| <= 2^{E_i - 7s - 1}
+// |v_0| <= 128 and |v_p| <= 64 for p > 0: integers that BF16 holds exactly.
+//
+// Products.  With row scales 2^Ea (A') and 2^Eb (B'),
+//   (A' B'^T)_mn = 2^{Ea_m + Eb_n} sum_{p,q} 2^{-7(p+q+2)} (V_p W_q^T)_mn.
+// The pairs with p + q <= s - 1 are formed (s (s + 1) / 2 of them); the others
+// lie below 2^{-7(s+1)} of 2^{Ea+Eb} per product.  A TMEM accumulator sums one
+// chunk's products of pairs with the same p + q over at most OZ_WIN stages
+// (512 products of magnitude <= 2^14), so its value is an integer below 2^23 and
+// the FP32 tensor-core accumulation is exact.  Each such window is multiplied by
+// its power of two (exact) and added into (hi, lo) with TwoSum (Knuth), so the
+// only roundings after the split are those of the double-float sum.  The window
+// factors are taken relative to the largest row scales of the output's chunks
+// (RA for its A' rows, RB for its B' rows), so (hi, lo) stay near unit magnitude
+// whatever the data's range; the epilogue multiplies by RA RB in FP64.
+//
+// One CTA computes a 128 x 128 tile, 18 warps: warp 0 / lane 0 issues TMA loads
+// into a 6-stage ring (32 KiB per stage: 64 BF16 of K for 128 rows of A' and of
+// B'), warp 1 / lane 0 issues 4 MMAs (kind::f16, BF16 inputs, K = 16) per stage
+// into TMEM buffer (window & 1), warps 2..17 promote windows and run the epilogue
+// (32 columns of one TMEM lane quarter each; hi in registers, lo in TMEM).
+// Every mbarrier wait is bounded, as in the split-TF32 kernel.
+#pragma once
+#include "tcgemm.cuh"
+
+namespace ccsdk {
+
+constexpr int OZ_BM = 128;
+constexpr int OZ_BN = 128;
+constexpr int OZ_BK = 64;                                  // BF16 elements per stage row (128 B)
+constexpr int OZ_STAGES = 6;
+constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;              // 16 KiB
+constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;              // 16 KiB
+constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;    // 32 KiB
+constexpr int OZ_LO_COL = 2 * OZ_BN;                       // TMEM columns of the lo accumulator
+constexpr int OZ_TMEM_COLS = 4 * OZ_BN;                    // two windows, lo, unused (power of two)
+constexpr int OZ_WIN = 8;                                  // stages per exact TMEM window
+constexpr int OZ_ACC_WARPS = 16;                           // four per TMEM lane quarter, 32 columns each
+constexpr int OZ_COLS = OZ_BN / (OZ_ACC_WARPS / 4);        // columns per accumulator thread
+constexpr int OZ_THREADS = 64 + 32 * OZ_ACC_WARPS;
+constexpr int OZ_REF_BYTES = OZ_ACC_WARPS * 64 * 4;       // per accumulator warp: column scales and inverses
+constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256 + OZ_REF_BYTES;
+constexpr int OZ_SLICE_BITS = 7;
+constexpr int OZ_MAX_SLICES = 8;
+constexpr int OZ_EXP_MIN = -120;                           // row-scale exponent clamp (see oz_row_exponent)
+constexpr int OZ_EXP_MAX = 120;
+
+struct OzArgs {
+    const int* rowA;          // [nbatch * nchunk] row of A' (within a slice plane) where chunk c of batch b starts
+    const int* rowB;          // [nbatch * nchunk]
+    const long long* offC;    // [nbatch * M] complex-element offset of output row m
+    const int* colC;          // [Nr / 2] complex-element offset of output column n
+    double2* C;               // FP64 result, C += alpha * c
+    int* err;                 // error word (0 = ok)
+    const float* scA;         // [rowsA] row scales 2^E of A'
+    const float* scB;         // [rowsB] row scales of B'
+    int rowsA, rowsB;         // rows of one slice plane (plane p starts at row p * rows)
+    int M, Nr, nchunk;
+    int kstages;              // K' / 64 per chunk
+    int slices;               // s (1 .. OZ_MAX_SLICES)
+    int tiles_m, tiles_n;
+    double alpha_re, alpha_im;
+    const int* nchunk_b;      // per-batch chunk count (<= nchunk) or null
+    const long long* offC2;   // antisymmetric mirror (subtracted) or null
+    const int* colC2;
+    long long spin_limit;
+    int skip_stage;           // failure-detection self-test: this stage is never loaded (-1: none)
+};
+
+// Instruction descriptor: D = F32, A = B = BF16 (kind::f16), both K-major, N = 128, M = 128.
+__host__ __device__ constexpr uint32_t oz_idesc_bf16() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void oz_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "setp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc) : "memory");
+}
+
+// Slice pairs in diagonal order: pair index pi -> d = p + q, p (q = d - p).
+__device__ __forceinline__ int oz_diag(int pi) {
+    int d = 0;
+    while ((d + 1) * (d + 2) / 2 <= pi) ++d;
+    return d;
+}
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += e;
+}
+
+// Stage r of a chunk (pairs in diagonal order, kstages stages per pair): its pair,
+// K stage, and whether it opens / closes a TMEM window.
+struct OzStage { int p, q, kst, d; bool first, last; };
+
+__device__ __forceinline__ OzStage oz_stage(int r, int kstages) {
+    OzStage o;
+    const int pi = r / kstages;
+    o.kst = r - pi * kstages;
+    o.d = oz_diag(pi);
+    o.p = pi - o.d * (o.d + 1) / 2;
+    o.q = o.d - o.p;
+    const int in_group = r - o.d * (o.d + 1) / 2 * kstages;  // stage index within diagonal d
+    const int glen = (o.d + 1) * kstages;
+    o.first = (in_group % OZ_WIN) == 0;
+    o.last = ((in_group + 1) % OZ_WIN) == 0 || in_group + 1 == glen;
+    return o;
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const OzArgs g)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* stA = smem;                                        // [STAGES][16 KiB]
+    uint8_t* stB = smem + OZ_STAGES * OZ_A_BYTES;               // [STAGES][16 KiB]
+    uint64_t* bars = (uint64_t*)(smem + OZ_STAGES * OZ_STAGE_BYTES);
+    uint64_t* acc_full = bars + 2 * OZ_STAGES;
+    uint64_t* acc_empty = bars + 2 * OZ_STAGES + 2;
+    uint64_t* drain = bars + 2 * OZ_STAGES + 4;
+    volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 2 * OZ_STAGES + 5);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntile = g.tiles_m * g.tiles_n;
+    const int tile = blockIdx.x % ntile;
+    const long long b = blockIdx.x / ntile;
+    const int m0 = (tile % g.tiles_m) * OZ_BM;
+    const int n0 = (tile / g.tiles_m) * OZ_BN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < OZ_STAGES; ++s) {
+            mbar_init(smem_u32(&bars[s]), 1);
+            mbar_init(smem_u32(&bars[OZ_STAGES + s]), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&acc_full[i]), 1);
+            mbar_init(smem_u32(&acc_empty[i]), OZ_ACC_WARPS);
+        }
+        mbar_init(smem_u32(drain), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32((const void*)tmem_slot)), "r"(OZ_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    const int npairs = g.slices * (g.slices + 1) / 2;
+    const int per_chunk = npairs * g.kstages;
+    const int nch = g.nchunk_b ? g.nchunk_b[b] : g.nchunk;
+    const int total = nch * per_chunk;
+    int issued = 0;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer: TMA loads
+            for (int s = 0; s < total; ++s) {
+                const int st = s % OZ_STAGES;
+                const uint32_t ph = (uint32_t)(s / OZ_STAGES) & 1u;
+                if (!mbar_wait(smem_u32(&bars[OZ_STAGES + st]), ph ^ 1u, abort_flag, g.spin_limit)) {
+                    atomicCAS(g.err, 0, 1);
+                    *abort_flag = 1;
+                    break;
+                }
+                if (s == g.skip_stage) continue;           // nothing will complete this stage
+                const int c = s / per_chunk;
+                const OzStage o = oz_stage(s - c * per_chunk, g.kstages);
+                const int ya = o.p * g.rowsA + g.rowA[b * g.nchunk + c] + m0;
+                const int yb = o.q * g.rowsB + g.rowB[b * g.nchunk + c] + n0;
+                const uint32_t full = smem_u32(&bars[st]);
+                mbar_expect_tx(full, OZ_STAGE_BYTES);
+                tma_load_2d(smem_u32(stA + st * OZ_A_BYTES), &mapA, o.kst * OZ_BK, ya, full);
+                tma_load_2d(smem_u32(stB + st * OZ_B_BYTES), &mapB, o.kst * OZ_BK, yb, full);
+                issued = s + 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer: window w accumulates in TMEM buffer w & 1
+            const uint32_t idesc = oz_idesc_bf16();
+            int w = 0;
+            for (int s = 0; s < total; ++s) {
+                const int c = s / per_chunk;
+                const OzStage o = oz_stage(s - c * per_chunk, g.kstages);
+                const int buf = w & 1;
+                if (o.first && w >= 2) {
+                    if (!mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)((w - 2) >> 1) & 1u, abort_flag, g.spin_limit)) {
+                        atomicCAS(g.err, 0, 4);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                }
+                const int st = s % OZ_STAGES;
+                const uint32_t ph = (uint32_t)(s / OZ_STAGES) & 1u;
+                if (!mbar_wait(smem_u32(&bars[st]), ph, abort_flag, g.spin_limit)) {
+                    atomicCAS(g.err, 0, 2);
+                    *abort_flag = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(stA + st * OZ_A_BYTES);
+                const uint32_t b0 = smem_u32(stB + st * OZ_B_BYTES);
+                const uint32_t dst = tmem + (uint32_t)(buf * OZ_BN);
+#pragma unroll
+                for (int k = 0; k < OZ_BK / 16; ++k) {          // K = 16 BF16 (32 bytes) per MMA
+                    oz_mma(dst, smem_desc_sw128(a0 + 32 * k), smem_desc_sw128(b0 + 32 * k), idesc,
+                           (o.first && k == 0) ? 0u : 1u);
+                }
+                tc_commit(smem_u32(&bars[OZ_STAGES + st]));
+                if (o.last) {
+                    tc_commit(smem_u32(&acc_full[buf]));
+                    ++w;
+                }
+            }
+            if (*abort_flag) {
+                tc_commit(smem_u32(drain));
+                mbar_wait(smem_u32(drain), 0u, nullptr, TC_DRAIN_LIMIT);
+            }
+        }
+    } else {
+        // ---------------- accumulator warps: exact windows -> (hi, lo), then the epilogue
+        const int qr = warp & 3;                                // TMEM lane quarter = rows 32 qr ..
+        const int half = (warp - 2) >> 2;                       // columns OZ_COLS half ..
+        const int row = m0 + qr * 32 + lane;
+        const uint32_t tlane = (uint32_t)(qr * 32) << 16;
+        const uint32_t tlo = tmem + tlane + (uint32_t)(OZ_LO_COL + half * OZ_COLS);   // this thread's lo
+        float hi[OZ_COLS];
+#pragma unroll
+        for (int i = 0; i < OZ_COLS; ++i) hi[i] = 0.f;
+#pragma unroll
+        for (int c0 = 0; c0 < OZ_COLS; c0 += 8)
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};"
+                         :: "r"(tlo + c0), "r"(0u) : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        // reference scales: RA over this row's chunks, RB over each column's (lane i: column i)
+        float RA = 0.f, RBl = 0.f;
+        const int col_l = n0 + half * OZ_COLS + lane;
+        for (int c = 0; c < nch; ++c) {
+            const int ra = g.rowA[b * g.nchunk + c] + row;
+            if (row < g.M && ra < g.rowsA) RA = fmaxf(RA, g.scA[ra]);
+            const int rb = g.rowB[b * g.nchunk + c] + col_l;
+            if (col_l < g.Nr && rb < g.rowsB) RBl = fmaxf(RBl, g.scB[rb]);
+        }
+        const float inv_ra = RA > 0.f ? 1.0f / RA : 0.f;        // exact: powers of two
+        float* colref = (float*)(smem + OZ_STAGES * OZ_STAGE_BYTES + 256) + (warp - 2) * 64;
+        colref[lane] = RBl;
+        colref[32 + lane] = RBl > 0.f ? 1.0f / RBl : 0.f;
+        __syncwarp();
+        bool ok = true;
+        int w = 0;
+        for (int c = 0; c < nch && ok; ++c) {
+            const int ra = g.rowA[b * g.nchunk + c] + row;
+            const float sa = (row < g.M && ra < g.rowsA) ? g.scA[ra] * inv_ra : 0.f;
+            const int rbase = g.rowB[b * g.nchunk + c] + n0 + half * OZ_COLS;
+            const float* scb = g.scB + rbase;                   // this thread's column scales
+            const int nvalid = min(g.Nr - (n0 + half * OZ_COLS), g.rowsB - rbase);
+            for (int d = 0; d < g.slices && ok; ++d) {
+                const float fa = sa * __int_as_float((127 - OZ_SLICE_BITS * (d + 2)) << 23);  // * 2^{-7(d+2)}
+                const int nwin = ((d + 1) * g.kstages + OZ_WIN - 1) / OZ_WIN;
+                for (int wi = 0; wi < nwin; ++wi, ++w) {
+                    const int buf = w & 1;
+                    bool got = mbar_wait(smem_u32(&acc_full[buf]), (uint32_t)(w >> 1) & 1u, abort_flag, g.spin_limit);
+                    got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+                    if (!got) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                    for (int c0 = 0; c0 < OZ_COLS; c0 += 8) {
+                        uint32_t v[8], l[8];
+                        const uint32_t taddr = tmem + tlane + (uint32_t)(buf * OZ_BN + half * OZ_COLS + c0);
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 "
+                                     "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                                       "=r"(v[6]), "=r"(v[7])
+                                     : "r"(taddr));
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 "
+                                     "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                     : "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]),
+                                       "=r"(l[6]), "=r"(l[7])
+                                     : "r"(tlo + c0));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const float sb = (c0 + i < nvalid) ? __ldg(scb + c0 + i) * colref[32 + c0 + i] : 0.f;
+                            float lo = __uint_as_float(l[i]);
+                            two_sum_acc(hi[c0 + i], lo, (__uint_as_float(v[i]) * sb) * fa);
+                            l[i] = __float_as_uint(lo);
+                        }
+                        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                                     :: "r"(tlo + c0), "r"(l[0]), "r"(l[1]), "r"(l[2]), "r"(l[3]), "r"(l[4]),
+                                        "r"(l[5]), "r"(l[6]), "r"(l[7]) : "memory");
+                    }
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&acc_empty[buf])) : "memory");
+                }
+            }
+        }
+        if (ok && !*abort_flag) {
+            // every MMA has completed: park (hi, lo) in the stage ring for the FP64 epilogue
+            constexpr int T = OZ_ACC_WARPS * 32;
+            float* park_hi = (float*)smem;                      // [OZ_COLS][T]
+            float* park_lo = park_hi + OZ_COLS * T;
+            const int t = (warp - 2) * 32 + lane;
+#pragma unroll
+            for (int c0 = 0; c0 < OZ_COLS; c0 += 8) {
+                uint32_t l[8];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 "
+                             "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]),
+                               "=r"(l[6]), "=r"(l[7])
+                             : "r"(tlo + c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    park_hi[(c0 + i) * T + t] = hi[c0 + i];
+                    park_lo[(c0 + i) * T + t] = __uint_as_float(l[i]);
+                }
+            }
+            if (row < g.M) {
+                const long long rb0 = g.offC[b * g.M + row];
+                const long long rb2 = g.offC2 ? g.offC2[b * g.M + row] : 0;
+#pragma unroll 1
+                for (int qq = 0; qq < OZ_COLS / 2; ++qq) {
+                    const int nr = n0 + half * OZ_COLS + 2 * qq;
+                    if (nr >= g.Nr) break;
+                    const double xr = ((double)park_hi[(2 * qq) * T + t] + (double)park_lo[(2 * qq) * T + t]) *
+                                      ((double)RA * (double)colref[2 * qq]);
+                    const double xi = ((double)park_hi[(2 * qq + 1) * T + t] + (double)park_lo[(2 * qq + 1) * T + t]) *
+                                      ((double)RA * (double)colref[2 * qq + 1]);
+                    const double yr = g.alpha_re * xr - g.alpha_im * xi;
+                    const double yi = g.alpha_re * xi + g.alpha_im * xr;
+                    double2* p = g.C + rb0 + g.colC[nr >> 1];
+                    double2 u = *p;
+                    u.x += yr; u.y += yi;
+                    *p = u;
+                    if (g.offC2) {
+                        double2* p2 = g.C + rb2 + g.colC2[nr >> 1];
+                        double2 z = *p2;
+                        z.x -= yr; z.y -= yi;
+                        *p2 = z;
+                    }
+                }
+            }
+        } else if (lane == 0) {
+            atomicCAS(g.err, 0, 3);
+        }
+    }
+
+    // ---------------- teardown: copies in flight, TMEM
+    __syncwarp();
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        for (int s = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); s < issued; ++s)
+            mbar_wait(smem_u32(&bars[s % OZ_STAGES]), (uint32_t)(s / OZ_STAGES) & 1u, nullptr, TC_DRAIN_LIMIT);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------- operand prep
+
+// Power-of-two scale exponent E with 2^E > amax (frexp), clamped to
+// [OZ_EXP_MIN, OZ_EXP_MAX] so that 2^E and 1 / 2^E are FP32 values: rows whose
+// largest element lies outside about 1e-36 .. 1e36 lose relative precision.
+__device__ __forceinline__ int oz_row_exponent(double amax) {
+    if (!(amax > 0.0)) return 0;
+    int e;
+    frexp(amax, &e);
+    return max(OZ_EXP_MIN, min(OZ_EXP_MAX, e));
+}
+
+// The s slices of x 2^-E (as BF16 bit patterns; the values are integers of at
+// most 8 bits, so the upper half of their FP32 pattern is exact).
+__device__ __forceinline__ void oz_split(double x, double inv_scale, int s, uint16_t* out) {
+    double y = x * inv_scale;
+    for (int p = 0; p < s; ++p) {
+        const double t = y * 128.0;
+        const double vp = rint(t);
+        y = t - vp;
+        out[p] = (uint16_t)(__float_as_uint((float)vp) >> 16);
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(uint16_t lo, uint16_t hi) {
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+__device__ __forceinline__ double block_max(double x, double* red) {
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();                              // red[] of a previous row is no longer read
+    if (lane == 0) red[warp] = x;
+    __syncthreads();
+    double m = 0.0;
+    for (int i = 0; i < nw; ++i) m = fmax(m, red[i]);
+    return m;
+}
+
+// Operand preparation for oz_gemm_kernel (the Ozaki analogue of embed_kernel):
+// gathers the complex block matrix X_b[r][k] = src[srcoff[b] + srow[r] + scol[k]],
+// scales each embedded row by its power of two and writes the s slice planes:
+//   mode 0 (A side): row b*R + r,         columns (2k, 2k+1) = (Re, Im)
+//   mode 1 (B side): rows b*2R + 2r, +1,  columns (2k, 2k+1) = (Re, -Im) / (Im, Re)
+// Plane p holds rows [0, rows) at sl + p * rows * Kpad; sc[row] = 2^E.
+struct OzEmbedArgs {
+    const double2* src; const float2* src32;
+    const long long* srcoff; const int* srow; const int* scol;
+    uint16_t* sl; float* sc;
+    long long rows;           // rows of one plane
+    int nblk, R, Kc, Kpad, mode, slices;
+};
+
+template <typename T>
+__device__ __forceinline__ void oz_embed_row(const OzEmbedArgs& e, const T* src, long long br, double* red) {
+    const int r = (int)(br % e.R);
+    const long long b = br / e.R;
+    const long long base = e.srcoff[b] + (long long)e.srow[r];
+    double m = 0.0;
+    for (int k = threadIdx.x; k < e.Kc; k += blockDim.x) {
+        const double2 z = ldz(src + base + e.scol[k]);
+        m = fmax(m, fmax(fabs(z.x), fabs(z.y)));
+    }
+    const int E = oz_row_exponent(block_max(m, red));
+    const double inv = ldexp(1.0, -E);
+    const float scale = ldexpf(1.0f, E);
+    const long long row0 = e.mode == 0 ? b * e.R + r : b * 2 * e.R + 2 * r;
+    const long long plane = e.rows * (long long)e.Kpad;
+    if (threadIdx.x == 0) {
+        e.sc[row0] = scale;
+        if (e.mode == 1) e.sc[row0 + 1] = scale;
+    }
+    uint32_t* out0 = (uint32_t*)(e.sl + row0 * e.Kpad);
+    const int kh = e.Kpad / 2;
+    for (int k = threadIdx.x; k < kh; k += blockDim.x) {
+        uint16_t sr[OZ_MAX_SLICES], si[OZ_MAX_SLICES];
+        if (k < e.Kc) {
+            const double2 z = ldz(src + base + e.scol[k]);
+            oz_split(z.x, inv, e.slices, sr);
+            oz_split(z.y, inv, e.slices, si);
+        } else {
+            for (int p = 0; p < e.slices; ++p) { sr[p] = 0; si[p] = 0; }
+        }
+        for (int p = 0; p < e.slices; ++p) {
+            uint32_t* o = out0 + (p * plane) / 2;
+            if (e.mode == 0) {
+                o[k] = pack_bf16x2(sr[p], si[p]);
+            } else {
+                o[k] = pack_bf16x2(sr[p], si[p] ^ 0x8000u);      // (Re, -Im)
+                o[kh + k] = pack_bf16x2(si[p], sr[p]);           // (Im, Re)
+            }
+        }
+    }
+}
+
+__global__ void oz_embed_kernel(const OzEmbedArgs e)
+{
+    __shared__ double red[32];
+    const long long rows = (long long)e.nblk * e.R;
+    for (long long br = blockIdx.x; br < rows; br += gridDim.x) {
+        if (e.src32) oz_embed_row(e, e.src32, br, red);
+        else oz_embed_row(e, e.src, br, red);
+    }
+}
+
+// Ladder operand W'^{abef} (the same quantity as wprime_list_kernel forms in FP32),
+// formed in FP64 and written as Ozaki slices of the B-side embedding: output block
+// bi is the momentum triple blk[3 bi ..], its rows the listed (a, b) pairs (2 per
+// pair), its columns the listed (e, f) pairs; rows bi 2 nab + 2 ai + s.
+struct OzWprimeArgs {
+    const double2* vvvv; const float2* vvvv32;     // one of them
+    const double2* ovvv; const float2* ovvv32;     // one of them
+    const double2* t1;
+    uint16_t* sl; float* sc;
+    const int* blk; const int* abl; const int* efl;
+    const long long* vofs;    // element offset of block bi's vvvv (staged copy), or null
+    long long rows;           // rows of one plane
+    int nblk, nab, nef, N, o, v, Kpad, slices;
+};
+
+template <typename TV, typename TO>
+__device__ void oz_wprime_row(const OzWprimeArgs& w, const TV* vvvv, const TO* ovvv, long long row,
+                              double2* vals, double* red) {
+    const int N = w.N, o = w.o, v = w.v;
+    const long long vv = (long long)v * v, v4 = vv * vv, ov3 = (long long)o * v * vv;
+    const long long bi = row / w.nab;
+    const int ai = (int)(row - bi * w.nab);
+    const int ka = w.blk[3 * bi], kb = w.blk[3 * bi + 1], ke = w.blk[3 * bi + 2];
+    const int ab = w.abl[ai];
+    const int a = ab / v, b = ab % v;
+    const long long blk_ab = ((long long)ka * N + kb) * N + ke;
+    const long long blk_ba = ((long long)kb * N + ka) * N + ke;
+    const TV* g0 = vvvv + (w.vofs ? w.vofs[bi] : blk_ab * v4) + (long long)ab * vv;
+    const TO* pa = ovvv + blk_ba * ov3 + (long long)a * vv;         // + r v vv: ovvv[kb,ka,ke](r,a,.)
+    const TO* pb = ovvv + blk_ab * ov3 + (long long)b * vv;         // ovvv[ka,kb,ke](r,b,.)
+    const double2* tb = w.t1 + (long long)kb * o * v + b;          // + r v: t_r^b(kb)
+    const double2* ta = w.t1 + (long long)ka * o * v + a;          // t_r^a(ka)
+    double m = 0.0;
+    for (int ei = threadIdx.x; ei < w.nef; ei += blockDim.x) {
+        const int ef = w.efl[ei];
+        double2 g = ldz(g0 + ef);
+        for (int r = 0; r < o; ++r) {
+            // + t_r^b(kb) ovvv[kb,ka,ke](r,a,e,f) - t_r^a(ka) ovvv[ka,kb,ke](r,b,e,f)
+            const double2 tbr = tb[r * v];
+            const double2 p = ldz(pa + (long long)r * v * vv + ef);
+            g.x = fma(tbr.x, p.x, fma(-tbr.y, p.y, g.x));
+            g.y = fma(tbr.x, p.y, fma(tbr.y, p.x, g.y));
+            const double2 tar = ta[r * v];
+            const double2 q = ldz(pb + (long long)r * v * vv + ef);
+            g.x = fma(-tar.x, q.x, fma(tar.y, q.y, g.x));
+            g.y = fma(-tar.x, q.y, fma(-tar.y, q.x, g.y));
+        }
+        vals[ei] = g;
+        m = fmax(m, fmax(fabs(g.x), fabs(g.y)));
+    }
+    const int E = oz_row_exponent(block_max(m, red));   // its barriers also publish vals[]
+    const double inv = ldexp(1.0, -E);
+    const float scale = ldexpf(1.0f, E);
+    const long long row0 = bi * 2 * w.nab + 2LL * ai;
+    const long long plane = w.rows * (long long)w.Kpad;
+    if (threadIdx.x == 0) { w.sc[row0] = scale; w.sc[row0 + 1] = scale; }
+    uint32_t* out0 = (uint32_t*)(w.sl + row0 * w.Kpad);
+    const int kh = w.Kpad / 2;
+    for (int k = threadIdx.x; k < kh; k += blockDim.x) {
+        uint16_t sr[OZ_MAX_SLICES], si[OZ_MAX_SLICES];
+        if (k < w.nef) {
+            const double2 z = vals[k];
+            oz_split(z.x, inv, w.slices, sr);
+            oz_split(z.y, inv, w.slices, si);
+        } else {
+            for (int p = 0; p < w.slices; ++p) { sr[p] = 0; si[p] = 0; }
+        }
+        for (int p = 0; p < w.slices; ++p) {
+            uint32_t* out = out0 + (p * plane) / 2;
+            out[k] = pack_bf16x2(sr[p], si[p] ^ 0x8000u);
+            out[kh + k] = pack_bf16x2(si[p], sr[p]);
+        }
+    }
+    __syncthreads();                                  // vals[] is rewritten by the next row
+}
+
+// One CTA per output row pair; dynamic shared memory holds the row's nef values.
+__global__ void oz_wprime_kernel(const OzWprimeArgs w)
+{
+    extern __shared__ double2 vals[];
+    __shared__ double red[32];
+    const long long rows = (long long)w.nblk * w.nab;
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        if (w.vvvv32) {
+            if (w.ovvv32) oz_wprime_row(w, w.vvvv32, w.ovvv32, row, vals, red);
+            else oz_wprime_row(w, w.vvvv32, w.ovvv, row, vals, red);
+        } else {
+            if (w.ovvv32) oz_wprime_row(w, w.vvvv, w.ovvv32, row, vals, red);
+            else oz_wprime_row(w, w.vvvv, w.ovvv, row, vals, red);
+        }
+    }
+}
+
+}  // namespace ccsdk

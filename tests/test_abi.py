@@ -118,3 +118,47 @@ def test_mixed_plan_indices_in_bounds(libpath, grid, o, v, lean):
     tb = ctypes.c_size_t(0)
     assert lib.ccsd_plan_check(ctypes.byref(cfg), ctypes.byref(n), ctypes.byref(tb)) == 0
     assert n.value >= 50
+
+
+@pytest.mark.parametrize("lean", [0, 1])
+@pytest.mark.parametrize("slices", [0, 3, 8])
+@pytest.mark.parametrize("grid,o,v", [((1, 1, 1), 3, 5), ((2, 1, 1), 2, 3), ((3, 2, 1), 5, 7),
+                                      ((2, 2, 2), 8, 32), ((3, 3, 3), 8, 24), ((2, 2, 1), 8, 32),
+                                      ((3, 1, 1), 2, 1)])
+def test_ozaki_plan_indices_in_bounds(libpath, grid, o, v, lean, slices):
+    """The Ozaki form's plan: the BF16 slice operands (pooled or not), the FP64 W' slices
+    of the chunked ladder and the tensor-core GEMMs pass the host-side bounds checks."""
+    from paper_1911_00242_gb300 import binding
+    lib = binding.load(libpath)
+    cfg = binding.make_config(grid, o, v, precision=binding.CCSD_OZAKI, lean=lean, oz_slices=slices)
+    n = ctypes.c_longlong(0)
+    tb = ctypes.c_size_t(0)
+    assert lib.ccsd_plan_check(ctypes.byref(cfg), ctypes.byref(n), ctypes.byref(tb)) == 0
+    assert n.value >= 50
+
+
+def test_ozaki_config_validation(libpath):
+    """Slice counts outside 3..8 and virtual spaces above 96 are refused; the batched form
+    takes no Ozaki members."""
+    from paper_1911_00242_gb300 import binding
+    lib = binding.load(libpath)
+    n = ctypes.c_longlong(0)
+    tb = ctypes.c_size_t(0)
+    for slices, v, ok in ((2, 8, False), (9, 8, False), (3, 8, True), (8, 8, True), (7, 97, False), (7, 96, True)):
+        cfg = binding.make_config((1, 1, 1), 2, v, precision=binding.CCSD_OZAKI, oz_slices=slices)
+        rc = lib.ccsd_plan_check(ctypes.byref(cfg), ctypes.byref(n), ctypes.byref(tb))
+        assert (rc == 0) == ok, (slices, v, rc)
+
+
+def test_ozaki_footprint_grows_with_slices(libpath):
+    """Operand memory of the Ozaki form: 2 bytes per slice per embedded element."""
+    from paper_1911_00242_gb300 import binding
+    lib = binding.load(libpath)
+    out = []
+    for slices in (3, 5, 7):
+        cfg = binding.make_config((2, 2, 1), 4, 16, precision=binding.CCSD_OZAKI, oz_slices=slices)
+        b = ctypes.c_size_t(0)
+        assert lib.ccsd_footprint(ctypes.byref(cfg), 1, binding.CCSD_C128, ctypes.byref(b)) == 0
+        out.append(b.value)
+    assert out[0] < out[1] < out[2]
+    assert out[2] - out[1] == out[1] - out[0]      # linear in the slice count

@@ -135,20 +135,22 @@ def test_degenerate_sizes_both_forms(lib, spec):
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_vvvv_read_in_place_from_host(lib, dtype):
-    """vvvv_on_host: the kernels read a host vvvv in place (mapped pinned memory):
-    the same residuals, bit for bit, as with vvvv in device memory, in both forms."""
+    """vvvv_on_host: a host vvvv is read in place (mapped pinned memory), or, in the mixed
+    form with complex64 integrals, staged chunk by chunk into device memory: the same
+    residuals, bit for bit, as with vvvv in device memory, in both forms and (lean) with
+    the ladder split into several chunks sharing one staging area."""
     from paper_1911_00242_gb300.binding import CCSD_MIXED, Solver
     spec = cs.SynthSpec((3, 1, 1), 3, 5, 521, int_dtype=dtype)
     inp = cs.generate(spec)
     t1, t2 = cs.random_amplitudes(spec, 54)
     d1, d2 = dev(t1), dev(t2)
-    for prec in (0, CCSD_MIXED):
+    for prec, lean in ((0, 0), (CCSD_MIXED, 0), (CCSD_MIXED, 1)):
         out = []
         for on_host in (False, True):
             arrays = {k: dev(v) for k, v in inp.items()}
             if on_host:
                 arrays["vvvv"] = np.ascontiguousarray(inp["vvvv"])        # pageable host memory
-            S = Solver(spec.grid, spec.nocc, spec.nvir, arrays, precision=prec, vvvv_on_host=on_host)
+            S = Solver(spec.grid, spec.nocc, spec.nvir, arrays, precision=prec, vvvv_on_host=on_host, lean=lean)
             r1, r2 = torch.empty_like(d1), torch.empty_like(d2)
             S.residual(d1, d2, r1, r2)
             torch.cuda.synchronize()
