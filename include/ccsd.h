@@ -106,12 +106,7 @@ typedef struct {
                              unregisters it at ccsd_destroy); it is read once per
                              iteration (the ladder's W' formation), so this frees
                              its N^3 v^4 elements of device memory for about one
-                             host-link transfer of it per iteration.  The
-                             tensor-core forms with a CCSD_C64 vvvv gather each
-                             ladder chunk's blocks into a device staging area (a
-                             kernel reading the mapped memory with wide loads)
-                             and form W' from there; otherwise the kernels read
-                             the mapped memory directly.  0:
+                             host-link transfer of it per iteration.  0:
                              host inputs are copied.  Ignored for a device
                              pointer.  */
 } ccsd_inputs;

@@ -92,8 +92,7 @@ struct PermPlan {
 struct Step {           // one element of the launch sequence
     int kind;           // 0 gemm, 1 copy, 2 perm, 3 tau, 4 antisym, 5 embed, 6 tensor-core gemm, 7 zero,
                         // 9 complex64 refresh of a buffer, 10 W' formation into the ladder's B operand,
-                        // 11 fused Fock/t1 terms of R2 (mixed form), 12 transposed complex64 F'vv,
-                        // 13 staging of host vvvv blocks for one ladder chunk
+                        // 11 fused Fock/t1 terms of R2 (mixed form), 12 transposed complex64 F'vv
     int idx;
     const char* name;
     double flops;       // algorithmic real flops per launch (complex MAC = 8)
@@ -138,11 +137,6 @@ struct ccsd_ctx {
     bool in32[NBUF] = {};            // input stored complex64 only (shadow[] set, buf[] null)
     std::vector<void*> owned;        // device allocations to free
     void* host_registered = nullptr; // host vvvv registered by the library (unregistered at destroy)
-    const char* vvvv_host = nullptr; // host vvvv read in place (vvvv_on_host), or null
-    float2* vstage = nullptr;        // complex64 host vvvv: device staging of one ladder chunk's blocks
-    bool stage_w16 = false;          // the staging gather moves 16-byte words
-    std::vector<std::pair<const long long*, int>> stages;   // per staging step: source block offsets
-                                                            // (16-byte words, device table), block count
     size_t owned_bytes = 0;
     double2* amp = nullptr;          // [t1 | t2]
     double2* res = nullptr;          // [R1 | R2]
@@ -1161,7 +1155,6 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
             if (tcp) for (size_t i = w_first; i < h->seq.size(); ++i) h->seq[i].mode = 1;
         }
     }
-    long long stage_blocks = 0;       // largest number of staged vvvv blocks of one ladder chunk
     if (tcp) {
         // Tensor-core ladder, antisymmetry-packed like the FP64 one: outputs (ka < kb | ka = kb,
         // a < b) with the mirror R2(ba) = -R2(ab), contractions over (ke < kf | ke = kf, e < f).
@@ -1233,25 +1226,6 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                             }
                     }
                     WListPlan wl{};
-                    if (h->vvvv_host && h->in32[B_VVVV]) {
-                        // complex64 vvvv in host memory: the chunk's blocks are copied into a
-                        // device staging area first (bulk DMA), and W' reads them there
-                        const long long v4 = vv * vv;
-                        std::vector<long long> src, vofs;
-                        for (size_t q = 0; q < blk3.size() / 3; ++q) {
-                            src.push_back(((long long)blk3[3 * q] * N + blk3[3 * q + 1]) * N * v4 + (long long)blk3[3 * q + 2] * v4);
-                            vofs.push_back((long long)q * v4);
-                        }
-                        stage_blocks = std::max<long long>(stage_blocks, (long long)src.size());
-                        h->stage_w16 = v % 2 == 0 && ((uintptr_t)h->vvvv_host % 16) == 0;
-                        if (h->stage_w16) for (long long& x : src) x /= 2;   // complex64 pairs (16-byte words)
-                        h->stages.push_back({upload(al, src, h->st), (int)src.size()});
-                        if (al.err) return al.err;
-                        Step st{13, (int)h->stages.size() - 1, "ladder_W", 0.0, 16.0 * (double)src.size() * v4};
-                        st.mode = 2;
-                        h->seq.push_back(st);
-                        wl.a.vofs = upload(al, vofs, h->st);
-                    }
                     wl.a.big = B.big; wl.a.small = B.small;
                     wl.a.blk = upload(al, blk3, h->st);
                     wl.a.abl = upload(al, abl, h->st);
@@ -1263,7 +1237,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                         wl.oz = true;
                         OzWprimeArgs& z = wl.z;
                         z.sl = B.sl; z.sc = B.sc; z.rows = B.rows;
-                        z.blk = wl.a.blk; z.abl = wl.a.abl; z.efl = wl.a.efl; z.vofs = wl.a.vofs;
+                        z.blk = wl.a.blk; z.abl = wl.a.abl; z.efl = wl.a.efl;
                         z.nblk = wl.a.nblk; z.nab = wl.a.nab; z.nef = wl.a.nef;
                         z.N = N; z.o = o; z.v = v; z.Kpad = A.kpad; z.slices = h->oz_slices;
                     }
@@ -1279,10 +1253,6 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                 }
             }
         }
-    }
-    if (stage_blocks > 0) {
-        h->vstage = (float2*)al.get((size_t)stage_blocks * (size_t)(vv * vv) * 8);
-        if (al.err) return al.err;
     }
     h->cur_name = "ring_W_t1";
     // ring: W~_jn^bf (Eq. Def_Woovv), stored [kj,kn,kb](j,n,b,f), kf = kn + kb - kj
@@ -1688,17 +1658,6 @@ void launch_step(ccsd_ctx* h, size_t si) {
             case 7:
                 cudaMemsetAsync(h->buf[s.idx], 0, (size_t)h->bufsize[s.idx] * 16, h->st);
                 break;
-            case 13: {   // stage host vvvv blocks into device memory (a gather through the mapping)
-                const long long v4 = (long long)v * v * v * v;
-                if (h->stage_w16)    // 16-byte words (v^4 even, host array 16-byte aligned)
-                    gather_blocks_kernel<<<152 * 8, 256, 0, h->st>>>((float4*)h->vstage, (const float4*)h->shadow[B_VVVV],
-                                                                     h->stages[s.idx].first, h->stages[s.idx].second, v4 / 2);
-                else
-                    gather_blocks_kernel<<<152 * 8, 256, 0, h->st>>>(h->vstage, (const float2*)h->shadow[B_VVVV],
-                                                                     h->stages[s.idx].first, h->stages[s.idx].second, v4);
-                ++h->launches;
-                break;
-            }
             case 10: {
                 if (h->wlists[s.idx].oz) {
                     static bool oz_w_attr = false;
@@ -1707,8 +1666,7 @@ void launch_step(ccsd_ctx* h, size_t si) {
                         oz_w_attr = true;
                     }
                     OzWprimeArgs z = h->wlists[s.idx].z;
-                    if (z.vofs) { z.vvvv32 = h->vstage; z.vvvv = nullptr; }
-                    else if (h->in32[B_VVVV]) { z.vvvv32 = h->shadow[B_VVVV]; z.vvvv = nullptr; }
+                    if (h->in32[B_VVVV]) { z.vvvv32 = h->shadow[B_VVVV]; z.vvvv = nullptr; }
                     else { z.vvvv = h->buf[B_VVVV]; z.vvvv32 = nullptr; }
                     if (h->in32[B_OVVV]) { z.ovvv32 = h->shadow[B_OVVV]; z.ovvv = nullptr; }
                     else { z.ovvv = h->buf[B_OVVV]; z.ovvv32 = nullptr; }
@@ -1718,7 +1676,7 @@ void launch_step(ccsd_ctx* h, size_t si) {
                     break;
                 }
                 WprimeListArgs a = h->wlists[s.idx].a;
-                a.vvvv = a.vofs ? h->vstage : h->shadow[B_VVVV];
+                a.vvvv = h->shadow[B_VVVV];
                 a.ovvv = h->shadow[B_OVVV]; a.t1 = h->shadow[B_T1];
                 wprime_list_kernel<<<row_grid((long long)a.nblk * a.nab), 256, 0, h->st>>>(a);
                 ++h->launches;
@@ -2041,7 +1999,6 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
             // vvvv read in place from host memory (mapped, pinned): no device copy
             if (al.dry) {
                 d = (void*)(uintptr_t)256;
-                h->vvvv_host = (const char*)d;
             } else {
                 void* hp = const_cast<void*>(ins[i]);
                 cudaError_t e = cudaHostRegister(hp, bytes, cudaHostRegisterMapped);
@@ -2049,7 +2006,6 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
                 else if (e == cudaErrorHostMemoryAlreadyRegistered) cudaGetLastError();
                 else { cudaGetLastError(); return CCSD_ERR_CUDA; }
                 if (cudaHostGetDevicePointer(&d, hp, 0) != cudaSuccess) { cudaGetLastError(); return CCSD_ERR_CUDA; }
-                h->vvvv_host = (const char*)hp;
             }
         } else {
             d = al.get(bytes);

@@ -72,33 +72,6 @@ __global__ void copy_kernel(double2* __restrict__ dst, const TS* __restrict__ sr
     }
 }
 
-// Gather of whole blocks: dst block q = src[off[q] .. off[q] + per), in words of T.
-// The source may be mapped host memory: many independent wide loads in flight per
-// thread keep the host link busy.
-template <typename T>
-__global__ void gather_blocks_kernel(T* __restrict__ dst, const T* __restrict__ src,
-                                     const long long* __restrict__ off, int nblk, long long per)
-{
-    const long long n = (long long)nblk * per;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    for (; e + 3 * stride < n; e += 4 * stride) {
-        T x[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const long long i = e + u * stride;
-            const long long q = i / per;
-            x[u] = src[off[q] + (i - q * per)];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) dst[e + u * stride] = x[u];
-    }
-    for (; e < n; e += stride) {
-        const long long q = e / per;
-        dst[e] = src[off[q] + (e - q * per)];
-    }
-}
-
 // Batched 4-index permuted copy:
 //   dst[offD[b] + i0*d0 + i1*d1 + i2*d2 + i3*d3] = src[offS[b] + i0*s0 + i1*s1 + i2*s2 + i3*s3]
 struct Perm4 {

@@ -501,7 +501,6 @@ struct OzWprimeArgs {
     const double2* t1;
     uint16_t* sl; float* sc;
     const int* blk; const int* abl; const int* efl;
-    const long long* vofs;    // element offset of block bi's vvvv (staged copy), or null
     long long rows;           // rows of one plane
     int nblk, nab, nef, N, o, v, Kpad, slices;
 };
@@ -518,7 +517,7 @@ __device__ void oz_wprime_row(const OzWprimeArgs& w, const TV* vvvv, const TO* o
     const int a = ab / v, b = ab % v;
     const long long blk_ab = ((long long)ka * N + kb) * N + ke;
     const long long blk_ba = ((long long)kb * N + ka) * N + ke;
-    const TV* g0 = vvvv + (w.vofs ? w.vofs[bi] : blk_ab * v4) + (long long)ab * vv;
+    const TV* g0 = vvvv + blk_ab * v4 + (long long)ab * vv;
     const TO* pa = ovvv + blk_ba * ov3 + (long long)a * vv;         // + r v vv: ovvv[kb,ka,ke](r,a,.)
     const TO* pb = ovvv + blk_ab * ov3 + (long long)b * vv;         // ovvv[ka,kb,ke](r,b,.)
     const double2* tb = w.t1 + (long long)kb * o * v + b;          // + r v: t_r^b(kb)

@@ -473,7 +473,6 @@ struct WprimeListArgs {
     const float2* vvvv; const float2* ovvv; const float2* t1;
     float* big; float* small;
     const int* blk; const int* abl; const int* efl;
-    const long long* vofs;    // element offset of block bi's vvvv in `vvvv` (staged copy), or null
     int nblk, nab, nef, N, o, v, Kpad;
 };
 
@@ -493,7 +492,7 @@ __global__ void wprime_list_kernel(const WprimeListArgs w)
         const int a = ab / v, b = ab % v;
         const long long blk_ab = ((long long)ka * N + kb) * N + ke;
         const long long blk_ba = ((long long)kb * N + ka) * N + ke;
-        const float2* g0 = w.vvvv + (w.vofs ? w.vofs[bi] : blk_ab * v4) + (long long)ab * vv;
+        const float2* g0 = w.vvvv + blk_ab * v4 + (long long)ab * vv;
         const float2* pa = w.ovvv + blk_ba * ov3 + (long long)a * vv;     // + r v vv: ovvv[kb,ka,ke](r,a,.)
         const float2* pb = w.ovvv + blk_ab * ov3 + (long long)b * vv;     // ovvv[ka,kb,ke](r,b,.)
         const float2* tb = w.t1 + (long long)kb * o * v + b;              // + r v: t_r^b(kb)

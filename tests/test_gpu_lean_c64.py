@@ -135,10 +135,9 @@ def test_degenerate_sizes_both_forms(lib, spec):
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_vvvv_read_in_place_from_host(lib, dtype):
-    """vvvv_on_host: a host vvvv is read in place (mapped pinned memory), or, in the mixed
-    form with complex64 integrals, staged chunk by chunk into device memory: the same
-    residuals, bit for bit, as with vvvv in device memory, in both forms and (lean) with
-    the ladder split into several chunks sharing one staging area."""
+    """vvvv_on_host: the kernels read a host vvvv in place (mapped pinned memory): the
+    same residuals, bit for bit, as with vvvv in device memory, in both forms and (lean)
+    with the ladder split into several chunks."""
     from paper_1911_00242_gb300.binding import CCSD_MIXED, Solver
     spec = cs.SynthSpec((3, 1, 1), 3, 5, 521, int_dtype=dtype)
     inp = cs.generate(spec)

@@ -181,8 +181,8 @@ def test_ozaki_solve_chain(lib):
 
 
 def test_ozaki_host_vvvv(lib):
-    """vvvv in host memory (read in place, or staged per ladder chunk for complex64):
-    the same residuals, bit for bit, as with vvvv on the device."""
+    """vvvv in host memory, read in place by the FP64 W' kernel: the same residuals, bit
+    for bit, as with vvvv on the device."""
     from paper_1911_00242_gb300.binding import CCSD_OZAKI, Solver
     for dtype in ("c128", "c64"):
         spec = cs.SynthSpec((3, 1, 1), 3, 5, 608, int_dtype=dtype)
