@@ -130,6 +130,17 @@ int ccsd_footprint(const ccsd_config* cfg, int inputs_on_device, int int_dtype, 
  * evaluation, *table_bytes the size of the plan's index tables. */
 int ccsd_plan_check(const ccsd_config* cfg, long long* n_launches, size_t* table_bytes);
 
+/* The launch plan of this config, built on the host as ccsd_plan_check does: for
+ * each of its *n_steps steps (at most max_steps are written; arrays may be NULL)
+ * the step kind (0 FP64/FP32 GEMM, 1 copy, 2 permutation, 3 tau, 4 antisymmetrize,
+ * 5 tensor-core operand embedding, 6 tensor-core GEMM, 7 zero, 9 complex64 copy,
+ * 10 W' formation, 11 fused Fock terms, 12 transposed F'vv), the iterations it
+ * runs in (mode 0 all; 1 without tensor cores; 2 with tensor cores; 3 mixed
+ * iterations only; 4 all but mixed iterations), its algorithmic real flops and
+ * its name (static strings owned by the library). */
+int ccsd_plan_describe(const ccsd_config* cfg, int max_steps, int* kinds, int* modes, double* flops,
+                       const char** names, int* n_steps);
+
 /* Self-test of the tensor-core GEMM of the mixed form: C = A B^T for random
  * complex A (M x K) and B (Ncols x K) through the TF32 path (nterms 1: plain
  * TF32, 3: split TF32) against the FP64 engine; *rel_err = max|dC| / max|C|.

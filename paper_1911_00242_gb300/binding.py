@@ -48,6 +48,9 @@ SYMBOLS = {
                        ctypes.c_int),
     "ccsd_plan_check": ([ctypes.POINTER(ccsd_config), ctypes.POINTER(ctypes.c_longlong),
                          ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "ccsd_plan_describe": ([ctypes.POINTER(ccsd_config), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "ccsd_tc_selftest": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
                           ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "ccsd_tc_timeout_selftest": ([], ctypes.c_int),
@@ -365,3 +368,17 @@ def oz_gemm(A, B, slices=7):
     C = np.empty((M, Nc), dtype=np.complex128)
     check(lib.ccsd_oz_gemm(M, Nc, K, slices, A.ctypes.data, B.ctypes.data, C.ctypes.data), "ccsd_oz_gemm")
     return C
+
+
+def plan_describe(grid, nocc, nvir, **cfg):
+    """The launch plan of a config (host only): a list of (name, kind, mode, flops)."""
+    lib = load()
+    c = make_config(grid, nocc, nvir, **cfg)
+    n = ctypes.c_int(0)
+    check(lib.ccsd_plan_describe(ctypes.byref(c), 0, None, None, None, None, ctypes.byref(n)), "ccsd_plan_describe")
+    k = (ctypes.c_int * n.value)()
+    m = (ctypes.c_int * n.value)()
+    f = (ctypes.c_double * n.value)()
+    nm = (ctypes.c_char_p * n.value)()
+    check(lib.ccsd_plan_describe(ctypes.byref(c), n.value, k, m, f, nm, ctypes.byref(n)), "ccsd_plan_describe")
+    return [(nm[i].decode(), k[i], m[i], f[i]) for i in range(n.value)]

@@ -168,6 +168,8 @@ struct ccsd_ctx {
     int fp32 = 0;                    // contractions in FP32 arithmetic (mixed form)
     int oz_on = 0;                   // Ozaki-scheme tensor-core contractions active (CCSD_OZAKI)
     int oz_slices = 7;               // slices per operand row (CCSD_OZAKI)
+    long long oz_work_elems = 0;     // split partials of the Ozaki GEMMs (complex elements)
+    double2* oz_work = nullptr;
     long long wab_cap_bytes = 12LL << 30;   // bound of the ladder's W' slab buffer
     // mixed and Ozaki forms: tensor-core operands (TF32 big/small parts, or BF16 slice
     // planes and row scales, of the real embeddings)
@@ -457,7 +459,8 @@ int tc_alloc(ccsd_ctx* h, Alloc& al, TcBuf& t, long long rows, int kpad) {
 
 int add_embed(ccsd_ctx* h, Alloc& al, int src, const TcBuf& dst, int mode, int R, int Kc,
               const std::vector<long long>& srcoff, const std::vector<int>& srow, const std::vector<int>& scol,
-              bool constant) {
+              bool constant, bool conj = false) {
+    if (conj && h->cfg.precision != CCSD_OZAKI) return CCSD_ERR_INVALID;
     const long long nblk = (long long)srcoff.size();
     if ((int)srow.size() != R || (int)scol.size() != Kc || 2 * Kc > dst.kpad) return CCSD_ERR_INVALID;
     const long long hi = *std::max_element(srcoff.begin(), srcoff.end()) + *std::max_element(srow.begin(), srow.end()) +
@@ -480,6 +483,7 @@ int add_embed(ccsd_ctx* h, Alloc& al, int src, const TcBuf& dst, int mode, int R
         e.z.sl = dst.sl; e.z.sc = dst.sc; e.z.rows = dst.rows;
         e.z.nblk = (int)nblk; e.z.R = R; e.z.Kc = Kc; e.z.Kpad = dst.kpad; e.z.mode = mode;
         e.z.slices = h->oz_slices;
+        e.z.conj = conj ? 1 : 0;
     }
     h->embeds.push_back(e);
     if (constant) {
@@ -496,17 +500,24 @@ int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M,
            const std::vector<int>& rowA, const std::vector<int>& rowB, const std::vector<long long>& offC,
            const std::vector<int>& colC, double alpha, int nterms,
            const std::vector<int>& nchunk_b = {}, const std::vector<long long>& offC2 = {},
-           const std::vector<int>& colC2 = {}) {
+           const std::vector<int>& colC2 = {}, double alpha_im = 0.0, bool overwrite = false,
+           const std::vector<int>& rowC = {}) {
+    // output row m of batch b starts at offC[b * M + m], or (rowC given) at offC[b] + rowC[m]
     const bool oz = h->cfg.precision == CCSD_OZAKI;
     if (A.kpad != B.kpad || A.kpad % (oz ? OZ_BK : TC_BK)) return CCSD_ERR_INVALID;
+    if (!oz && (alpha_im != 0.0 || overwrite || !rowC.empty())) return CCSD_ERR_INVALID;
     if (oz && ((long long)h->oz_slices * A.rows > INT_MAX || (long long)h->oz_slices * B.rows > INT_MAX))
         return CCSD_ERR_INVALID;
+    const long long noff = rowC.empty() ? (long long)nbatch * M : nbatch;
     if ((long long)rowA.size() != (long long)nbatch * nchunk || (long long)rowB.size() != (long long)nbatch * nchunk ||
-        (long long)offC.size() != (long long)nbatch * M || (int)colC.size() * 2 != Nr) return CCSD_ERR_INVALID;
+        (long long)offC.size() != noff || (int)colC.size() * 2 != Nr || (!rowC.empty() && (int)rowC.size() != M))
+        return CCSD_ERR_INVALID;
     for (int x : rowA) if (x < 0 || x >= A.rows) return CCSD_ERR_INVALID;
     for (int x : rowB) if (x < 0 || x >= B.rows) return CCSD_ERR_INVALID;
-    const long long chi = *std::max_element(offC.begin(), offC.end()) + *std::max_element(colC.begin(), colC.end());
-    const long long clo = *std::min_element(offC.begin(), offC.end()) + *std::min_element(colC.begin(), colC.end());
+    const long long rhi = rowC.empty() ? 0 : *std::max_element(rowC.begin(), rowC.end());
+    const long long rlo = rowC.empty() ? 0 : *std::min_element(rowC.begin(), rowC.end());
+    const long long chi = *std::max_element(offC.begin(), offC.end()) + rhi + *std::max_element(colC.begin(), colC.end());
+    const long long clo = *std::min_element(offC.begin(), offC.end()) + rlo + *std::min_element(colC.begin(), colC.end());
     if (clo < 0 || chi >= h->bufsize[c]) return CCSD_ERR_INVALID;
     if (!nchunk_b.empty()) {
         if ((long long)nchunk_b.size() != nbatch) return CCSD_ERR_INVALID;
@@ -514,8 +525,8 @@ int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M,
     }
     if (!offC2.empty()) {
         if (offC2.size() != offC.size() || colC2.size() != colC.size()) return CCSD_ERR_INVALID;
-        const long long h2 = *std::max_element(offC2.begin(), offC2.end()) + *std::max_element(colC2.begin(), colC2.end());
-        const long long l2 = *std::min_element(offC2.begin(), offC2.end()) + *std::min_element(colC2.begin(), colC2.end());
+        const long long h2 = *std::max_element(offC2.begin(), offC2.end()) + rhi + *std::max_element(colC2.begin(), colC2.end());
+        const long long l2 = *std::min_element(offC2.begin(), offC2.end()) + rlo + *std::min_element(colC2.begin(), colC2.end());
         if (l2 < 0 || h2 >= h->bufsize[c]) return CCSD_ERR_INVALID;
     }
     TcPlan t{};
@@ -543,8 +554,18 @@ int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M,
         z.scA = A.sc; z.scB = B.sc; z.rowsA = (int)A.rows; z.rowsB = (int)B.rows;
         z.M = M; z.Nr = Nr; z.nchunk = nchunk; z.kstages = A.kpad / OZ_BK; z.slices = h->oz_slices;
         z.tiles_m = (M + OZ_BM - 1) / OZ_BM; z.tiles_n = (Nr + OZ_BN - 1) / OZ_BN;
-        z.alpha_re = alpha; z.alpha_im = 0.0;
-        t.blocks = z.tiles_m * z.tiles_n * nbatch;
+        z.alpha_re = alpha; z.alpha_im = alpha_im; z.overwrite = overwrite ? 1 : 0;
+        z.rowC = rowC.empty() ? nullptr : upload(al, rowC, h->st);
+        if (al.err) return al.err;
+        z.nbatch = nbatch;
+        // too few tiles for the 152 SMs: split each tile's (chunk, diagonal) units over CTAs
+        const long long tiles = (long long)z.tiles_m * z.tiles_n * nbatch;
+        const int units = nchunk * h->oz_slices;
+        z.nsplit = 1;
+        if (tiles < 2 * 152) z.nsplit = (int)std::min<long long>(std::min(units, 16), (2 * 152 + tiles - 1) / tiles);
+        t.blocks = (int)(tiles * z.nsplit);
+        if (z.nsplit > 1)
+            h->oz_work_elems = std::max(h->oz_work_elems, (long long)z.nsplit * nbatch * M * (Nr / 2));
         if (!al.dry) {
             int rc;
             if ((rc = encode_map_bf16(&t.mA_big, A.sl, A.rows * h->oz_slices, A.kpad, OZ_BM)) ||
@@ -575,6 +596,151 @@ void add_zero(ccsd_ctx* h, int buf) {
 dim3 ew_grid(long long n);
 dim3 row_grid(long long rows);
 
+// Ozaki form: every remaining FP64 GEMM step with at least OZ_CONVERT_FLOPS of work gets a
+// tensor-core alternative (the FP64 step stays for native FP64 iterations, mode 1).  The
+// batches are split into groups whose distinct operand blocks fit the shared operand
+// buffers; each group is embedded just before its GEMM (stream order keeps the buffers
+// intact while it runs).  In the pooled layout the buffers are the tensor-core pools; else
+// two buffers of at most OZ_GENERIC_CAP elements per slice plane are allocated here.
+constexpr double OZ_CONVERT_FLOPS = 5e8;
+// cost model of the conversion (measured on GB300: the per-CTA fixed cost of a launch of
+// oz_gemm_kernel, the time of one 128 x 128 x 64 stage, embedding bandwidth, FP64 GEMM rate)
+constexpr double OZ_CTA_SECONDS = 8e-6;
+constexpr double OZ_STAGE_SECONDS = 0.35e-6;
+constexpr double OZ_EMBED_BPS = 2e12;
+constexpr double OZ_FP64_FLOPS = 1.1e12;
+constexpr long long OZ_GENERIC_CAP = 1LL << 28;
+
+int oz_convert_gemms(ccsd_ctx* h, Alloc& al, std::map<int, GemmSpec>& specs, bool pooled, float* pool_a,
+                     float* pool_b, long long pool_ae, long long pool_be, float* pool_asc, float* pool_bsc,
+                     long long pool_ar, long long pool_br) {
+    struct Cand { int gi; int kpad; long long needA, needB, rowsA, rowsB; };
+    std::map<int, Cand> cand;                  // by plan index of the FP64 GEMM
+    long long maxA = 0, maxB = 0, maxRA = 0, maxRB = 0;
+    for (const Step& st : h->seq) {
+        if (st.kind != 0 || st.mode != 0 || st.flops < OZ_CONVERT_FLOPS) continue;
+        auto it = specs.find(st.idx);
+        if (it == specs.end() || it->second.nbatch == 0) continue;
+        GemmSpec& s = it->second;
+        // orientation: C^T = B^T A^T when that needs fewer 128 x 128 tiles (rows M, real columns 2N)
+        auto tiles = [](long long m, long long n) { return ((m + 127) / 128) * ((2 * n + 127) / 128); };
+        if (s.offC2.empty() && tiles(s.N, s.M) < tiles(s.M, s.N)) {
+            std::swap(s.M, s.N);
+            std::swap(s.a, s.b);
+            std::swap(s.offA, s.offB);
+            std::swap(s.conjA, s.conjB);
+            std::vector<int> ra = s.colB, ca = s.rowB, rb = s.colA, cb = s.rowA;
+            s.rowA = ra; s.colA = ca; s.rowB = rb; s.colB = cb;
+            std::swap(s.rowC, s.colC);
+        }
+        const int kpad = (2 * s.K + OZ_BK - 1) / OZ_BK * OZ_BK;
+        std::vector<long long> ua(s.offA), ub(s.offB);
+        std::sort(ua.begin(), ua.end()); ua.erase(std::unique(ua.begin(), ua.end()), ua.end());
+        std::sort(ub.begin(), ub.end()); ub.erase(std::unique(ub.begin(), ub.end()), ub.end());
+        // worth it?  Tensor-core estimate: per CTA a fixed cost plus its stages (all tiles,
+        // padding included), plus the operand embedding at HBM speed; FP64 estimate: the
+        // algorithmic flops at the FP64 rate.
+        const double ctas = (double)tiles(s.M, s.N) * s.nbatch;
+        const double stages = (double)s.nchunk * (h->oz_slices * (h->oz_slices + 1) / 2) * (kpad / OZ_BK);
+        const double emb = ((double)ua.size() * s.M + (double)ub.size() * 2 * s.N) * kpad * 2.0 * h->oz_slices;
+        const double t_tc = (ctas * OZ_CTA_SECONDS + ctas * stages * OZ_STAGE_SECONDS) / 152.0 + emb / OZ_EMBED_BPS;
+        const double t_fp64 = st.flops / OZ_FP64_FLOPS;
+        if (t_tc > 0.7 * t_fp64) continue;
+        // the largest single batch must fit: its chunks' A blocks and B blocks
+        const long long ra = (long long)s.nchunk * s.M, rb = (long long)s.nchunk * 2 * s.N;
+        cand[st.idx] = Cand{st.idx, kpad, ra * kpad, rb * kpad, ra, rb};
+        // whole-GEMM sizes (distinct blocks) bound what a generic buffer needs
+        maxA = std::max(maxA, (long long)ua.size() * s.M * kpad);
+        maxB = std::max(maxB, (long long)ub.size() * 2 * s.N * kpad);
+        maxRA = std::max(maxRA, (long long)ua.size() * s.M);
+        maxRB = std::max(maxRB, (long long)ub.size() * 2 * s.N);
+    }
+    if (cand.empty()) return 0;
+    uint16_t *ga = nullptr, *gb = nullptr;
+    float *gasc = nullptr, *gbsc = nullptr;
+    long long capA, capB, capRA, capRB;
+    if (pooled) {
+        ga = (uint16_t*)pool_a; gb = (uint16_t*)pool_b; gasc = pool_asc; gbsc = pool_bsc;
+        capA = pool_ae; capB = pool_be; capRA = pool_ar; capRB = pool_br;
+    } else {
+        capA = std::min(maxA, OZ_GENERIC_CAP); capB = std::min(maxB, OZ_GENERIC_CAP);
+        for (auto& kv : cand) { capA = std::max(capA, kv.second.needA); capB = std::max(capB, kv.second.needB); }
+        capRA = maxRA; capRB = maxRB;
+        TcBuf ta{}, tb{};
+        int rc;
+        if ((rc = tc_alloc(h, al, ta, capA / OZ_BK + 1, OZ_BK)) || (rc = tc_alloc(h, al, tb, capB / OZ_BK + 1, OZ_BK)))
+            return rc;
+        ga = ta.sl; gb = tb.sl;
+        gasc = (float*)al.get((size_t)capRA * 4);
+        gbsc = (float*)al.get((size_t)capRB * 4);
+        if (al.err) return al.err;
+    }
+    std::vector<Step> old;
+    old.swap(h->seq);
+    const char* saved_name = h->cur_name;
+    for (const Step& st : old) {
+        auto it = cand.find(st.kind == 0 ? st.idx : -1);
+        if (st.kind != 0 || st.mode != 0 || it == cand.end() || it->second.needA > capA || it->second.needB > capB ||
+            it->second.rowsA > capRA || it->second.rowsB > capRB) {
+            h->seq.push_back(st);
+            continue;
+        }
+        Step f = st;
+        f.mode = 1;                             // the FP64 GEMM: native FP64 iterations only
+        h->seq.push_back(f);
+        h->cur_name = st.name;
+        const GemmSpec& s = specs.at(st.idx);
+        const int kpad = it->second.kpad;
+        int b0 = 0;
+        while (b0 < s.nbatch) {
+            // a group of batches whose distinct blocks fit the buffers
+            std::map<long long, int> ia, ib;       // block offset -> block index in the group
+            int b1 = b0;
+            while (b1 < s.nbatch) {
+                // blocks this batch would add
+                std::vector<long long> newa, newb;
+                for (int c = 0; c < s.nchunk; ++c) {
+                    const long long xa = s.offA[(size_t)b1 * s.nchunk + c], xb = s.offB[(size_t)b1 * s.nchunk + c];
+                    if (!ia.count(xa) && std::find(newa.begin(), newa.end(), xa) == newa.end()) newa.push_back(xa);
+                    if (!ib.count(xb) && std::find(newb.begin(), newb.end(), xb) == newb.end()) newb.push_back(xb);
+                }
+                const long long ra = (long long)(ia.size() + newa.size()) * s.M;
+                const long long rb = (long long)(ib.size() + newb.size()) * 2 * s.N;
+                if (b1 > b0 && (ra * kpad > capA || rb * kpad > capB || ra > capRA || rb > capRB)) break;
+                for (long long x : newa) ia.emplace(x, (int)ia.size());
+                for (long long x : newb) ib.emplace(x, (int)ib.size());
+                ++b1;
+            }
+            std::vector<long long> offa((size_t)ia.size()), offb((size_t)ib.size());
+            for (auto& kv : ia) offa[(size_t)kv.second] = kv.first;
+            for (auto& kv : ib) offb[(size_t)kv.second] = kv.first;
+            TcBuf A{nullptr, nullptr, (long long)ia.size() * s.M, kpad, ga, gasc};
+            TcBuf B{nullptr, nullptr, (long long)ib.size() * 2 * s.N, kpad, gb, gbsc};
+            int rc;
+            if ((rc = add_embed(h, al, s.a, A, 0, s.M, s.K, offa, s.rowA, s.colA, false, s.conjA)) ||
+                (rc = add_embed(h, al, s.b, B, 1, s.N, s.K, offb, s.colB, s.rowB, false, s.conjB)))
+                return rc;
+            std::vector<int> rowa, rowb, nchb;
+            std::vector<long long> oc, oc2;
+            for (int b = b0; b < b1; ++b) {
+                for (int c = 0; c < s.nchunk; ++c) {
+                    rowa.push_back(ia.at(s.offA[(size_t)b * s.nchunk + c]) * s.M);
+                    rowb.push_back(ib.at(s.offB[(size_t)b * s.nchunk + c]) * 2 * s.N);
+                }
+                oc.push_back(s.offC[b]);
+                if (!s.offC2.empty()) oc2.push_back(s.offC2[b]);
+                if (!s.nchunk_b.empty()) nchb.push_back(s.nchunk_b[b]);
+            }
+            if ((rc = add_tc(h, al, A, B, s.c, s.M, 2 * s.N, b1 - b0, s.nchunk, rowa, rowb, oc, s.colC, s.ar, 1, nchb,
+                             oc2, s.offC2.empty() ? std::vector<int>{} : s.colC2, s.ai, !s.acc, s.rowC)))
+                return rc;
+            b0 = b1;
+        }
+    }
+    h->cur_name = saved_name;
+    return 0;
+}
+
 // Build the full residual plan.
 int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     const KGrid& kg = h->kg;
@@ -585,7 +751,11 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     auto kk3 = [&](int a, int b, int c) { return ((long long)a * N + b) * N + c; };
     auto blk = [&](long long S, int a, int b, int c) { return kk3(a, b, c) * S; };
     int rc;
-    auto G = [&](GemmSpec& s) { return finalize_gemm(h, al, s, work_need); };
+    std::map<int, GemmSpec> oz_specs;   // Ozaki form: the spec of every FP64 GEMM (by plan index)
+    auto G = [&](GemmSpec& s) {
+        if (h->cfg.precision == CCSD_OZAKI) oz_specs[(int)h->gemms.size()] = s;
+        return finalize_gemm(h, al, s, work_need);
+    };
     const bool mixed = h->cfg.precision == CCSD_MIXED;
     const bool oz = h->cfg.precision == CCSD_OZAKI;
     const bool tcp = mixed || oz;  // the plan has tensor-core variants of the large contractions
@@ -593,6 +763,10 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     bool pooled = false;          // tensor-core operands share two buffers, rewritten every residual
     long long lb_floats = 0;      // capacity (elements per part / slice plane) of the ladder's B-operand buffer
     float* pool_b = nullptr;      // the B-side pool (big part; the small part follows it)
+    float* pool_a = nullptr;      // the A-side pool
+    long long pool_ae = 0, pool_be = 0, pool_ar = 0, pool_br = 0;   // pool capacity: elements, scale rows
+    float* pool_asc = nullptr;
+    float* pool_bsc = nullptr;    // Ozaki pools: row scales
     const long long nlt_vv = (long long)v * (v - 1) / 2;
     const int KQ = oz ? OZ_BK : TC_BK;      // row padding: one pipeline stage of K
     const int kpl = (int)((2 * vv + KQ - 1) / KQ * KQ);
@@ -677,8 +851,10 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                 const long long rb = std::max({N3l * 2 * ov, N3l * 2 * oo, N3l * 2 * vv, pb / kpl + 1});
                 scA = (float*)al.get((size_t)ra * 4);
                 scB = (float*)al.get((size_t)rb * 4);
+                pool_ar = ra; pool_br = rb;
             }
             if (al.err) return al.err;
+            pool_a = A; pool_ae = pa; pool_be = pb; pool_asc = scA; pool_bsc = scB;
             lb_floats = pb;
             auto view = [oz](float* base, float* sc, long long floats, long long rows, int kpad) {
                 if (oz) {
@@ -1489,6 +1665,9 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         h->seq.push_back(s1); h->seq.push_back(s2); h->seq.push_back(s3);
     }
     h->seq.push_back({4, 0, "antisym_R2", 0.0, 16.0 * 3.0 * h->n2});
+    if (oz && (rc = oz_convert_gemms(h, al, oz_specs, pooled, pool_a, pool_b, pool_ae, pool_be, pool_asc, pool_bsc,
+                                     pool_ar, pool_br)))
+        return rc;
     return 0;
 }
 
@@ -1554,7 +1733,11 @@ void launch_embed(ccsd_ctx* h, EmbedPlan& e) {
         OzEmbedArgs z = e.z;
         z.src = h->buf[e.src];
         z.src32 = h->in32[e.src] ? h->shadow[e.src] : nullptr;
-        oz_embed_kernel<<<row_grid((long long)z.nblk * z.R), z.Kpad / 2 >= 256 ? 256 : 128, 0, h->st>>>(z);
+        const long long rows = (long long)z.nblk * z.R;
+        if (z.Kpad / 2 <= 64)       // one warp per row
+            oz_embed_kernel<<<row_grid((rows + 7) / 8), 256, 0, h->st>>>(z);
+        else
+            oz_embed_kernel<<<row_grid(rows), z.Kpad / 2 >= 256 ? 256 : 128, 0, h->st>>>(z);
         ++h->launches;
         return;
     }
@@ -1574,8 +1757,13 @@ void launch_tc(ccsd_ctx* h, TcPlan& t) {
         }
         OzArgs z = t.z;
         z.C = h->buf[t.c];
+        z.work = z.nsplit > 1 ? h->oz_work : nullptr;
         oz_gemm_kernel<<<t.blocks, OZ_THREADS, OZ_SMEM_BYTES, h->st>>>(t.mA_big, t.mB_big, z);
         ++h->launches;
+        if (z.work) {
+            oz_split_reduce<<<ew_grid((long long)z.nbatch * z.M * (z.Nr / 2)), 256, 0, h->st>>>(z);
+            ++h->launches;
+        }
         return;
     }
     static bool attr_set = false;
@@ -2099,6 +2287,7 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
         }
     }
     if (work_need) { h->work = dalloc((long long)work_need); if (!h->work) return al.err; }
+    if (h->oz_work_elems) { h->oz_work = dalloc(h->oz_work_elems); if (!h->oz_work) return al.err; }
     h->work_elems = work_need;
     h->red_blocks = 152 * 4;
     h->red = (double*)al.get(sizeof(double) * h->red_blocks);
@@ -2387,6 +2576,28 @@ int ccsd_footprint(const ccsd_config* cfg, int inputs_on_device, int int_dtype, 
 }
 
 
+int ccsd_plan_describe(const ccsd_config* cfg, int max_steps, int* kinds, int* modes, double* flops,
+                       const char** names, int* n_steps) {
+    if (!valid_cfg(cfg) || max_steps < 0 || !n_steps) return CCSD_ERR_INVALID;
+    ccsd_ctx* h = new (std::nothrow) ccsd_ctx();
+    if (!h) return CCSD_ERR_OOM;
+    init_ctx(h, cfg);
+    set_sizes(h);
+    Alloc al{h};
+    al.dry = true;
+    size_t work_need = 0;
+    const int rc = build_plan(h, al, work_need);
+    *n_steps = (int)h->seq.size();
+    for (int i = 0; i < (int)h->seq.size() && i < max_steps; ++i) {
+        if (kinds) kinds[i] = h->seq[i].kind;
+        if (modes) modes[i] = h->seq[i].mode;
+        if (flops) flops[i] = h->seq[i].flops;
+        if (names) names[i] = h->seq[i].name;    // static strings
+    }
+    delete h;
+    return rc;
+}
+
 int ccsd_plan_check(const ccsd_config* cfg, long long* n_launches, size_t* table_bytes) {
     if (!valid_cfg(cfg)) return CCSD_ERR_INVALID;
     ccsd_ctx* h = new (std::nothrow) ccsd_ctx();
@@ -2398,7 +2609,9 @@ int ccsd_plan_check(const ccsd_config* cfg, long long* n_launches, size_t* table
     size_t work_need = 0;
     const int rc = build_plan(h, al, work_need);
     long long n = 0;
-    for (const Step& st : h->seq) n += (st.kind == 0 && h->gemms[st.idx].args.nsplit > 1) ? 2 : 1;
+    for (const Step& st : h->seq)
+        n += ((st.kind == 0 && h->gemms[st.idx].args.nsplit > 1) || (st.kind == 6 && h->tcs[st.idx].oz &&
+              h->tcs[st.idx].z.nsplit > 1)) ? 2 : 1;
     if (n_launches) *n_launches = n;
     if (table_bytes) *table_bytes = h->owned_bytes;
     delete h;
@@ -2513,6 +2726,7 @@ int oz_gemm_impl(int M, int Ncols, int K, int slices, const double* A, const dou
     for (int m = 0; m < M; ++m) oc.push_back((long long)m * Ncols);
     if ((rc = add_tc(h, al, ta, tb, B_ZR, M, 2 * Ncols, 1, 1, {0}, {0}, oc, tab({{Ncols, 1}}), 1.0, 1)))
         return fail(rc);
+    if (h->oz_work_elems) { h->oz_work = (double2*)al.get((size_t)h->oz_work_elems * 16); if (al.err) return fail(al.err); }
     if (skip_stage >= 0) {
         h->tcs[0].z.skip_stage = skip_stage;
         h->tcs[0].z.spin_limit = 1LL << 14;

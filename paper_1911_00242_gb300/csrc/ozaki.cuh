@@ -32,7 +32,8 @@
 // into a 6-stage ring (32 KiB per stage: 64 BF16 of K for 128 rows of A' and of
 // B'), warp 1 / lane 0 issues 4 MMAs (kind::f16, BF16 inputs, K = 16) per stage
 // into TMEM buffer (window & 1), warps 2..17 promote windows and run the epilogue
-// (32 columns of one TMEM lane quarter each; hi in registers, lo in TMEM).
+// (32 columns of one TMEM lane quarter each; hi and lo live in TMEM as well, so a
+// thread holds only 8 columns at a time).
 // Every mbarrier wait is bounded, as in the split-TF32 kernel.
 #pragma once
 #include "tcgemm.cuh"
@@ -47,12 +48,13 @@ constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;              // 16 KiB
 constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;              // 16 KiB
 constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;    // 32 KiB
 constexpr int OZ_LO_COL = 2 * OZ_BN;                       // TMEM columns of the lo accumulator
-constexpr int OZ_TMEM_COLS = 4 * OZ_BN;                    // two windows, lo, unused (power of two)
+constexpr int OZ_HI_COL = 3 * OZ_BN;                       // TMEM columns of the hi accumulator
+constexpr int OZ_TMEM_COLS = 4 * OZ_BN;                    // two windows, lo, hi
 constexpr int OZ_WIN = 8;                                  // stages per exact TMEM window
 constexpr int OZ_ACC_WARPS = 16;                           // four per TMEM lane quarter, 32 columns each
 constexpr int OZ_COLS = OZ_BN / (OZ_ACC_WARPS / 4);        // columns per accumulator thread
 constexpr int OZ_THREADS = 64 + 32 * OZ_ACC_WARPS;
-constexpr int OZ_REF_BYTES = OZ_ACC_WARPS * 64 * 4;       // per accumulator warp: column scales and inverses
+constexpr int OZ_REF_BYTES = OZ_ACC_WARPS * 96 * 4;       // per accumulator warp: RB, 1 / RB, chunk column factors
 constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256 + OZ_REF_BYTES;
 constexpr int OZ_SLICE_BITS = 7;
 constexpr int OZ_MAX_SLICES = 8;
@@ -62,7 +64,8 @@ constexpr int OZ_EXP_MAX = 120;
 struct OzArgs {
     const int* rowA;          // [nbatch * nchunk] row of A' (within a slice plane) where chunk c of batch b starts
     const int* rowB;          // [nbatch * nchunk]
-    const long long* offC;    // [nbatch * M] complex-element offset of output row m
+    const long long* offC;    // [nbatch * M] complex-element offset of output row m (or [nbatch], rowC set)
+    const int* rowC;          // null, or [M]: row m of batch b starts at offC[b] + rowC[m] (offC2 alike)
     const int* colC;          // [Nr / 2] complex-element offset of output column n
     double2* C;               // FP64 result, C += alpha * c
     int* err;                 // error word (0 = ok)
@@ -79,6 +82,10 @@ struct OzArgs {
     const int* colC2;
     long long spin_limit;
     int skip_stage;           // failure-detection self-test: this stage is never loaded (-1: none)
+    int overwrite;            // 1: C = alpha c (and -alpha c at the mirror) instead of C += ...
+    int nbatch;
+    int nsplit;               // > 1: the (chunk, diagonal) units of a tile are split over nsplit CTAs
+    double2* work;            // nsplit > 1: partials [nsplit][nbatch][M][Nr / 2], summed by oz_split_reduce
 };
 
 // Instruction descriptor: D = F32, A = B = BF16 (kind::f16), both K-major, N = 128, M = 128.
@@ -108,22 +115,23 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
     lo += e;
 }
 
-// Stage r of a chunk (pairs in diagonal order, kstages stages per pair): its pair,
-// K stage, and whether it opens / closes a TMEM window.
-struct OzStage { int p, q, kst, d; bool first, last; };
-
-__device__ __forceinline__ OzStage oz_stage(int r, int kstages) {
-    OzStage o;
-    const int pi = r / kstages;
-    o.kst = r - pi * kstages;
-    o.d = oz_diag(pi);
-    o.p = pi - o.d * (o.d + 1) / 2;
-    o.q = o.d - o.p;
-    const int in_group = r - o.d * (o.d + 1) / 2 * kstages;  // stage index within diagonal d
-    const int glen = (o.d + 1) * kstages;
-    o.first = (in_group % OZ_WIN) == 0;
-    o.last = ((in_group + 1) % OZ_WIN) == 0 || in_group + 1 == glen;
-    return o;
+// Work of one tile, in units u = c * s + d (chunk c, diagonal d = p + q of the slice
+// pairs), each (d + 1) * kstages stages.  With nsplit > 1, CTA `split` takes the units
+// whose first stage lies in its share [split, split + 1) * total / nsplit of the stages.
+__device__ __forceinline__ void oz_unit_range(int nch, int S, int kstages, int nsplit, int split, int& u0, int& u1) {
+    const int nunits = nch * S;
+    if (nsplit <= 1) { u0 = 0; u1 = nunits; return; }
+    const long long per_chunk = (long long)(S * (S + 1) / 2) * kstages;
+    const long long total = per_chunk * nch;
+    const long long lo = total * split / nsplit, hi = total * (split + 1) / nsplit;
+    u0 = nunits; u1 = nunits;
+    for (int u = 0; u < nunits; ++u) {
+        const int c = u / S, d = u - (u / S) * S;
+        const long long start = c * per_chunk + (long long)(d * (d + 1) / 2) * kstages;
+        if (start >= lo && u0 == nunits) u0 = u;
+        if (start >= hi) { u1 = u; break; }
+    }
+    if (u1 < u0) u1 = u0;
 }
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
@@ -143,7 +151,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntile = g.tiles_m * g.tiles_n;
     const int tile = blockIdx.x % ntile;
-    const long long b = blockIdx.x / ntile;
+    const long long b = (blockIdx.x / ntile) % g.nbatch;
+    const int split = (int)(blockIdx.x / ntile / g.nbatch);
     const int m0 = (tile % g.tiles_m) * OZ_BM;
     const int n0 = (tile / g.tiles_m) * OZ_BN;
 
@@ -170,72 +179,85 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    const int npairs = g.slices * (g.slices + 1) / 2;
-    const int per_chunk = npairs * g.kstages;
+    const int S = g.slices;
     const int nch = g.nchunk_b ? g.nchunk_b[b] : g.nchunk;
-    const int total = nch * per_chunk;
+    int u0, u1;
+    oz_unit_range(nch, S, g.kstages, g.nsplit, split, u0, u1);
     int issued = 0;
 
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- producer: TMA loads
-            for (int s = 0; s < total; ++s) {
-                const int st = s % OZ_STAGES;
-                const uint32_t ph = (uint32_t)(s / OZ_STAGES) & 1u;
-                if (!mbar_wait(smem_u32(&bars[OZ_STAGES + st]), ph ^ 1u, abort_flag, g.spin_limit)) {
-                    atomicCAS(g.err, 0, 1);
-                    *abort_flag = 1;
-                    break;
+            int s = 0;
+            bool run = true;
+            for (int u = u0; u < u1 && run; ++u) {
+                const int c = u / S, d = u - c * S;
+                const int ra = g.rowA[b * g.nchunk + c] + m0, rb = g.rowB[b * g.nchunk + c] + n0;
+                for (int p = 0; p <= d && run; ++p) {
+                    const int ya = p * g.rowsA + ra, yb = (d - p) * g.rowsB + rb;
+                    for (int kst = 0; kst < g.kstages; ++kst, ++s) {
+                        const int st = s % OZ_STAGES;
+                        const uint32_t ph = (uint32_t)(s / OZ_STAGES) & 1u;
+                        if (!mbar_wait(smem_u32(&bars[OZ_STAGES + st]), ph ^ 1u, abort_flag, g.spin_limit)) {
+                            atomicCAS(g.err, 0, 1);
+                            *abort_flag = 1;
+                            run = false;
+                            break;
+                        }
+                        if (s == g.skip_stage) continue;   // nothing will complete this stage
+                        const uint32_t full = smem_u32(&bars[st]);
+                        mbar_expect_tx(full, OZ_STAGE_BYTES);
+                        tma_load_2d(smem_u32(stA + st * OZ_A_BYTES), &mapA, kst * OZ_BK, ya, full);
+                        tma_load_2d(smem_u32(stB + st * OZ_B_BYTES), &mapB, kst * OZ_BK, yb, full);
+                        issued = s + 1;
+                    }
                 }
-                if (s == g.skip_stage) continue;           // nothing will complete this stage
-                const int c = s / per_chunk;
-                const OzStage o = oz_stage(s - c * per_chunk, g.kstages);
-                const int ya = o.p * g.rowsA + g.rowA[b * g.nchunk + c] + m0;
-                const int yb = o.q * g.rowsB + g.rowB[b * g.nchunk + c] + n0;
-                const uint32_t full = smem_u32(&bars[st]);
-                mbar_expect_tx(full, OZ_STAGE_BYTES);
-                tma_load_2d(smem_u32(stA + st * OZ_A_BYTES), &mapA, o.kst * OZ_BK, ya, full);
-                tma_load_2d(smem_u32(stB + st * OZ_B_BYTES), &mapB, o.kst * OZ_BK, yb, full);
-                issued = s + 1;
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer: window w accumulates in TMEM buffer w & 1
             const uint32_t idesc = oz_idesc_bf16();
-            int w = 0;
-            for (int s = 0; s < total; ++s) {
-                const int c = s / per_chunk;
-                const OzStage o = oz_stage(s - c * per_chunk, g.kstages);
-                const int buf = w & 1;
-                if (o.first && w >= 2) {
-                    if (!mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)((w - 2) >> 1) & 1u, abort_flag, g.spin_limit)) {
-                        atomicCAS(g.err, 0, 4);
+            int w = 0, s = 0;
+            bool run = true;
+            for (int u = u0; u < u1 && run; ++u) {
+                const int d = u % S;
+                const int glen = (d + 1) * g.kstages;          // stages of this unit
+                for (int j = 0; j < glen; ++j, ++s) {
+                    const bool first = (j % OZ_WIN) == 0;
+                    const bool last = ((j + 1) % OZ_WIN) == 0 || j + 1 == glen;
+                    const int buf = w & 1;
+                    if (first && w >= 2) {
+                        if (!mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)((w - 2) >> 1) & 1u, abort_flag, g.spin_limit)) {
+                            atomicCAS(g.err, 0, 4);
+                            *abort_flag = 1;
+                            run = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    }
+                    const int st = s % OZ_STAGES;
+                    const uint32_t ph = (uint32_t)(s / OZ_STAGES) & 1u;
+                    if (!mbar_wait(smem_u32(&bars[st]), ph, abort_flag, g.spin_limit)) {
+                        atomicCAS(g.err, 0, 2);
                         *abort_flag = 1;
+                        run = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                }
-                const int st = s % OZ_STAGES;
-                const uint32_t ph = (uint32_t)(s / OZ_STAGES) & 1u;
-                if (!mbar_wait(smem_u32(&bars[st]), ph, abort_flag, g.spin_limit)) {
-                    atomicCAS(g.err, 0, 2);
-                    *abort_flag = 1;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a0 = smem_u32(stA + st * OZ_A_BYTES);
-                const uint32_t b0 = smem_u32(stB + st * OZ_B_BYTES);
-                const uint32_t dst = tmem + (uint32_t)(buf * OZ_BN);
+                    const uint32_t a0 = smem_u32(stA + st * OZ_A_BYTES);
+                    const uint32_t b0 = smem_u32(stB + st * OZ_B_BYTES);
+                    const uint32_t dst = tmem + (uint32_t)(buf * OZ_BN);
 #pragma unroll
-                for (int k = 0; k < OZ_BK / 16; ++k) {          // K = 16 BF16 (32 bytes) per MMA
-                    oz_mma(dst, smem_desc_sw128(a0 + 32 * k), smem_desc_sw128(b0 + 32 * k), idesc,
-                           (o.first && k == 0) ? 0u : 1u);
-                }
-                tc_commit(smem_u32(&bars[OZ_STAGES + st]));
-                if (o.last) {
-                    tc_commit(smem_u32(&acc_full[buf]));
-                    ++w;
+                    for (int k = 0; k < OZ_BK / 16; ++k) {      // K = 16 BF16 (32 bytes) per MMA
+                        oz_mma(dst, smem_desc_sw128(a0 + 32 * k), smem_desc_sw128(b0 + 32 * k), idesc,
+                               (first && k == 0) ? 0u : 1u);
+                    }
+                    tc_commit(smem_u32(&bars[OZ_STAGES + st]));
+                    if (last) {
+                        tc_commit(smem_u32(&acc_full[buf]));
+                        ++w;
+                    }
                 }
             }
             if (*abort_flag) {
@@ -250,37 +272,48 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         const int row = m0 + qr * 32 + lane;
         const uint32_t tlane = (uint32_t)(qr * 32) << 16;
         const uint32_t tlo = tmem + tlane + (uint32_t)(OZ_LO_COL + half * OZ_COLS);   // this thread's lo
-        float hi[OZ_COLS];
+        const uint32_t thi = tmem + tlane + (uint32_t)(OZ_HI_COL + half * OZ_COLS);   // and hi
 #pragma unroll
-        for (int i = 0; i < OZ_COLS; ++i) hi[i] = 0.f;
-#pragma unroll
-        for (int c0 = 0; c0 < OZ_COLS; c0 += 8)
+        for (int c0 = 0; c0 < OZ_COLS; c0 += 8) {
             asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};"
                          :: "r"(tlo + c0), "r"(0u) : "memory");
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};"
+                         :: "r"(thi + c0), "r"(0u) : "memory");
+        }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         // reference scales: RA over this row's chunks, RB over each column's (lane i: column i)
         float RA = 0.f, RBl = 0.f;
         const int col_l = n0 + half * OZ_COLS + lane;
-        for (int c = 0; c < nch; ++c) {
+        const int c_lo = u0 / S, c_hi = u1 > u0 ? (u1 - 1) / S + 1 : c_lo;
+        for (int c = c_lo; c < c_hi; ++c) {
             const int ra = g.rowA[b * g.nchunk + c] + row;
             if (row < g.M && ra < g.rowsA) RA = fmaxf(RA, g.scA[ra]);
             const int rb = g.rowB[b * g.nchunk + c] + col_l;
             if (col_l < g.Nr && rb < g.rowsB) RBl = fmaxf(RBl, g.scB[rb]);
         }
         const float inv_ra = RA > 0.f ? 1.0f / RA : 0.f;        // exact: powers of two
-        float* colref = (float*)(smem + OZ_STAGES * OZ_STAGE_BYTES + 256) + (warp - 2) * 64;
+        float* colref = (float*)(smem + OZ_STAGES * OZ_STAGE_BYTES + 256) + (warp - 2) * 96;
+        float* colfac = colref + 64;                            // this chunk's sb / RB per column
         colref[lane] = RBl;
         colref[32 + lane] = RBl > 0.f ? 1.0f / RBl : 0.f;
         __syncwarp();
+        int cur_c = -1;
         bool ok = true;
         int w = 0;
-        for (int c = 0; c < nch && ok; ++c) {
-            const int ra = g.rowA[b * g.nchunk + c] + row;
-            const float sa = (row < g.M && ra < g.rowsA) ? g.scA[ra] * inv_ra : 0.f;
-            const int rbase = g.rowB[b * g.nchunk + c] + n0 + half * OZ_COLS;
-            const float* scb = g.scB + rbase;                   // this thread's column scales
-            const int nvalid = min(g.Nr - (n0 + half * OZ_COLS), g.rowsB - rbase);
-            for (int d = 0; d < g.slices && ok; ++d) {
+        float sa = 0.f;
+        for (int u = u0; u < u1 && ok; ++u) {
+            const int c = u / S, d = u - c * S;
+            if (c != cur_c) {       // this row's factor; lane i: the factor of column i (one load each)
+                const int ra = g.rowA[b * g.nchunk + c] + row;
+                sa = (row < g.M && ra < g.rowsA) ? g.scA[ra] * inv_ra : 0.f;
+                const int rbase = g.rowB[b * g.nchunk + c] + n0 + half * OZ_COLS;
+                const int nvalid = min(g.Nr - (n0 + half * OZ_COLS), g.rowsB - rbase);
+                __syncwarp();
+                colfac[lane] = lane < nvalid ? g.scB[rbase + lane] * colref[32 + lane] : 0.f;
+                __syncwarp();
+                cur_c = c;
+            }
+            {
                 const float fa = sa * __int_as_float((127 - OZ_SLICE_BITS * (d + 2)) << 23);  // * 2^{-7(d+2)}
                 const int nwin = ((d + 1) * g.kstages + OZ_WIN - 1) / OZ_WIN;
                 for (int wi = 0; wi < nwin; ++wi, ++w) {
@@ -291,7 +324,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
                     for (int c0 = 0; c0 < OZ_COLS; c0 += 8) {
-                        uint32_t v[8], l[8];
+                        uint32_t v[8], l[8], hh[8];
                         const uint32_t taddr = tmem + tlane + (uint32_t)(buf * OZ_BN + half * OZ_COLS + c0);
                         asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 "
                                      "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -303,17 +336,26 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                                      : "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]),
                                        "=r"(l[6]), "=r"(l[7])
                                      : "r"(tlo + c0));
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 "
+                                     "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                     : "=r"(hh[0]), "=r"(hh[1]), "=r"(hh[2]), "=r"(hh[3]), "=r"(hh[4]), "=r"(hh[5]),
+                                       "=r"(hh[6]), "=r"(hh[7])
+                                     : "r"(thi + c0));
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            const float sb = (c0 + i < nvalid) ? __ldg(scb + c0 + i) * colref[32 + c0 + i] : 0.f;
-                            float lo = __uint_as_float(l[i]);
-                            two_sum_acc(hi[c0 + i], lo, (__uint_as_float(v[i]) * sb) * fa);
+                            const float sb = colfac[c0 + i];
+                            float lo = __uint_as_float(l[i]), hi = __uint_as_float(hh[i]);
+                            two_sum_acc(hi, lo, (__uint_as_float(v[i]) * sb) * fa);
                             l[i] = __float_as_uint(lo);
+                            hh[i] = __float_as_uint(hi);
                         }
                         asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
                                      :: "r"(tlo + c0), "r"(l[0]), "r"(l[1]), "r"(l[2]), "r"(l[3]), "r"(l[4]),
                                         "r"(l[5]), "r"(l[6]), "r"(l[7]) : "memory");
+                        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                                     :: "r"(thi + c0), "r"(hh[0]), "r"(hh[1]), "r"(hh[2]), "r"(hh[3]), "r"(hh[4]),
+                                        "r"(hh[5]), "r"(hh[6]), "r"(hh[7]) : "memory");
                     }
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -330,22 +372,27 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             const int t = (warp - 2) * 32 + lane;
 #pragma unroll
             for (int c0 = 0; c0 < OZ_COLS; c0 += 8) {
-                uint32_t l[8];
+                uint32_t l[8], hh[8];
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 "
                              "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                              : "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]),
                                "=r"(l[6]), "=r"(l[7])
                              : "r"(tlo + c0));
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 "
+                             "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(hh[0]), "=r"(hh[1]), "=r"(hh[2]), "=r"(hh[3]), "=r"(hh[4]), "=r"(hh[5]),
+                               "=r"(hh[6]), "=r"(hh[7])
+                             : "r"(thi + c0));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    park_hi[(c0 + i) * T + t] = hi[c0 + i];
+                    park_hi[(c0 + i) * T + t] = __uint_as_float(hh[i]);
                     park_lo[(c0 + i) * T + t] = __uint_as_float(l[i]);
                 }
             }
             if (row < g.M) {
-                const long long rb0 = g.offC[b * g.M + row];
-                const long long rb2 = g.offC2 ? g.offC2[b * g.M + row] : 0;
+                const long long rb0 = g.rowC ? g.offC[b] + g.rowC[row] : g.offC[b * g.M + row];
+                const long long rb2 = !g.offC2 ? 0 : g.rowC ? g.offC2[b] + g.rowC[row] : g.offC2[b * g.M + row];
 #pragma unroll 1
                 for (int qq = 0; qq < OZ_COLS / 2; ++qq) {
                     const int nr = n0 + half * OZ_COLS + 2 * qq;
@@ -354,15 +401,20 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                                       ((double)RA * (double)colref[2 * qq]);
                     const double xi = ((double)park_hi[(2 * qq + 1) * T + t] + (double)park_lo[(2 * qq + 1) * T + t]) *
                                       ((double)RA * (double)colref[2 * qq + 1]);
+                    if (g.work) {       // partial of this split; oz_split_reduce applies alpha
+                        g.work[(((long long)split * g.nbatch + b) * g.M + row) * (g.Nr / 2) + (nr >> 1)] =
+                            make_double2(xr, xi);
+                        continue;
+                    }
                     const double yr = g.alpha_re * xr - g.alpha_im * xi;
                     const double yi = g.alpha_re * xi + g.alpha_im * xr;
                     double2* p = g.C + rb0 + g.colC[nr >> 1];
-                    double2 u = *p;
+                    double2 u = g.overwrite ? make_double2(0.0, 0.0) : *p;
                     u.x += yr; u.y += yi;
                     *p = u;
                     if (g.offC2) {
                         double2* p2 = g.C + rb2 + g.colC2[nr >> 1];
-                        double2 z = *p2;
+                        double2 z = g.overwrite ? make_double2(0.0, 0.0) : *p2;
                         z.x -= yr; z.y -= yi;
                         *p2 = z;
                     }
@@ -386,43 +438,104 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     }
 }
 
-// ---------------------------------------------------------------- operand prep
-
-// Power-of-two scale exponent E with 2^E > amax (frexp), clamped to
-// [OZ_EXP_MIN, OZ_EXP_MAX] so that 2^E and 1 / 2^E are FP32 values: rows whose
-// largest element lies outside about 1e-36 .. 1e36 lose relative precision.
-__device__ __forceinline__ int oz_row_exponent(double amax) {
-    if (!(amax > 0.0)) return 0;
-    int e;
-    frexp(amax, &e);
-    return max(OZ_EXP_MIN, min(OZ_EXP_MAX, e));
+// Sum of the split partials in split order (deterministic), then the epilogue of
+// oz_gemm_kernel: C (+)= alpha * sum at offC[b M + m] + colC[n] (and the mirror).
+__global__ void oz_split_reduce(const OzArgs g)
+{
+    const int nc = g.Nr / 2;
+    const long long n = (long long)g.nbatch * g.M * nc;
+    const long long plane = n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        double xr = 0.0, xi = 0.0;
+        for (int sp = 0; sp < g.nsplit; ++sp) {
+            const double2 w = g.work[sp * plane + e];
+            xr += w.x; xi += w.y;
+        }
+        const long long bm = e / nc;              // b * M + m
+        const int col = (int)(e - bm * nc);
+        const long long bb = bm / g.M;
+        const int m = (int)(bm - bb * g.M);
+        const double yr = g.alpha_re * xr - g.alpha_im * xi;
+        const double yi = g.alpha_re * xi + g.alpha_im * xr;
+        const long long r0 = g.rowC ? g.offC[bb] + g.rowC[m] : g.offC[bm];
+        double2* p = g.C + r0 + g.colC[col];
+        double2 u = g.overwrite ? make_double2(0.0, 0.0) : *p;
+        u.x += yr; u.y += yi;
+        *p = u;
+        if (g.offC2) {
+            double2* p2 = g.C + (g.rowC ? g.offC2[bb] + g.rowC[m] : g.offC2[bm]) + g.colC2[col];
+            double2 z = g.overwrite ? make_double2(0.0, 0.0) : *p2;
+            z.x -= yr; z.y -= yi;
+            *p2 = z;
+        }
+    }
 }
 
-// The s slices of x 2^-E (as BF16 bit patterns; the values are integers of at
-// most 8 bits, so the upper half of their FP32 pattern is exact).
-__device__ __forceinline__ void oz_split(double x, double inv_scale, int s, uint16_t* out) {
-    double y = x * inv_scale;
-    for (int p = 0; p < s; ++p) {
-        const double t = y * 128.0;
-        const double vp = rint(t);
-        y = t - vp;
-        out[p] = (uint16_t)(__float_as_uint((float)vp) >> 16);
+// ---------------------------------------------------------------- operand prep
+
+// Row maxima are taken on the bit patterns: for non-negative doubles the unsigned
+// order of the patterns is the numeric order, and the integer pipes are far faster
+// than GB300's FP64 pipe.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+}
+
+// Power-of-two scale exponent E with 2^E > amax (the frexp exponent of amax, from
+// its bit pattern), clamped to [OZ_EXP_MIN, OZ_EXP_MAX] so that 2^E and 1 / 2^E are
+// FP32 values: rows whose largest element lies outside about 1e-36 .. 1e36 lose
+// relative precision.  0 for an all-zero row.
+__device__ __forceinline__ int oz_row_exponent(unsigned long long amax_bits) {
+    if (amax_bits == 0) return 0;
+    const int ef = (int)(amax_bits >> 52);              // biased exponent (0: subnormal)
+    return max(OZ_EXP_MIN, min(OZ_EXP_MAX, ef - 1022));
+}
+
+// The s slices of x 2^-E, from the 7s-bit fixed point Y = rint(x 2^{7s-E}) (|Y| <= 2^{7s};
+// `scale` = 2^{7s-E}, so x * scale is exact): balanced base-128 digits from the least
+// significant (in [-64, 63]), the remaining top digit (|v_0| <= 128) last.  Then
+// x = 2^E sum_p v_p 2^{-7(p+1)} up to 2^{E-7s-1}.  Integer arithmetic only after the
+// one conversion.  Output: BF16 bit patterns (the values are integers of at most 8
+// bits, so the upper half of their FP32 pattern is exact).
+__device__ __forceinline__ void oz_split(double x, double scale, int s, uint16_t* out) {
+    long long Y = __double2ll_rn(x * scale);
+    for (int p = s - 1; p > 0; --p) {
+        const int dg = (int)((Y + 64) & 127) - 64;
+        Y = (Y - dg) >> 7;
+        out[p] = (uint16_t)(__float_as_uint((float)dg) >> 16);
     }
+    out[0] = (uint16_t)(__float_as_uint((float)(int)Y) >> 16);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(uint16_t lo, uint16_t hi) {
     return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
-__device__ __forceinline__ double block_max(double x, double* red) {
-    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+        x = y > x ? y : x;
+    }
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long x, unsigned long long* red) {
+    x = warp_max_u64(x);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
     __syncthreads();                              // red[] of a previous row is no longer read
     if (lane == 0) red[warp] = x;
     __syncthreads();
-    double m = 0.0;
-    for (int i = 0; i < nw; ++i) m = fmax(m, red[i]);
+    unsigned long long m = 0;
+    for (int i = 0; i < nw; ++i) m = red[i] > m ? red[i] : m;
     return m;
+}
+
+// 2^{7s-E} as a double and 2^E as a float.
+__device__ __forceinline__ double oz_fixed_scale(int s, int E) {
+    return __longlong_as_double((long long)(1023 + OZ_SLICE_BITS * s - E) << 52);
+}
+__device__ __forceinline__ float oz_row_scale(int E) {
+    return __int_as_float((127 + E) << 23);
 }
 
 // Operand preparation for oz_gemm_kernel (the Ozaki analogue of embed_kernel):
@@ -437,35 +550,41 @@ struct OzEmbedArgs {
     uint16_t* sl; float* sc;
     long long rows;           // rows of one plane
     int nblk, R, Kc, Kpad, mode, slices;
+    int conj;                 // embed conj(X)
 };
 
-template <typename T>
-__device__ __forceinline__ void oz_embed_row(const OzEmbedArgs& e, const T* src, long long br, double* red) {
+// One row (b, r), by a group of nthr threads (a warp or the CTA); tid is the thread's
+// index in the group.  WARP: the group is one warp (no block barrier).
+template <bool WARP, typename T>
+__device__ __forceinline__ void oz_embed_row(const OzEmbedArgs& e, const T* src, long long br, int tid, int nthr,
+                                             unsigned long long* red) {
     const int r = (int)(br % e.R);
     const long long b = br / e.R;
     const long long base = e.srcoff[b] + (long long)e.srow[r];
-    double m = 0.0;
-    for (int k = threadIdx.x; k < e.Kc; k += blockDim.x) {
+    unsigned long long m = 0;
+    for (int k = tid; k < e.Kc; k += nthr) {
         const double2 z = ldz(src + base + e.scol[k]);
-        m = fmax(m, fmax(fabs(z.x), fabs(z.y)));
+        const unsigned long long a = abs_bits(z.x), c = abs_bits(z.y);
+        m = a > m ? a : m;
+        m = c > m ? c : m;
     }
-    const int E = oz_row_exponent(block_max(m, red));
-    const double inv = ldexp(1.0, -E);
-    const float scale = ldexpf(1.0f, E);
+    m = WARP ? warp_max_u64(m) : block_max_u64(m, red);
+    const int E = oz_row_exponent(m);
+    const double fx = oz_fixed_scale(e.slices, E);
     const long long row0 = e.mode == 0 ? b * e.R + r : b * 2 * e.R + 2 * r;
     const long long plane = e.rows * (long long)e.Kpad;
-    if (threadIdx.x == 0) {
-        e.sc[row0] = scale;
-        if (e.mode == 1) e.sc[row0 + 1] = scale;
+    if (tid == 0) {
+        e.sc[row0] = oz_row_scale(E);
+        if (e.mode == 1) e.sc[row0 + 1] = oz_row_scale(E);
     }
     uint32_t* out0 = (uint32_t*)(e.sl + row0 * e.Kpad);
     const int kh = e.Kpad / 2;
-    for (int k = threadIdx.x; k < kh; k += blockDim.x) {
+    for (int k = tid; k < kh; k += nthr) {
         uint16_t sr[OZ_MAX_SLICES], si[OZ_MAX_SLICES];
         if (k < e.Kc) {
             const double2 z = ldz(src + base + e.scol[k]);
-            oz_split(z.x, inv, e.slices, sr);
-            oz_split(z.y, inv, e.slices, si);
+            oz_split(z.x, fx, e.slices, sr);
+            oz_split(e.conj ? -z.y : z.y, fx, e.slices, si);
         } else {
             for (int p = 0; p < e.slices; ++p) { sr[p] = 0; si[p] = 0; }
         }
@@ -481,13 +600,23 @@ __device__ __forceinline__ void oz_embed_row(const OzEmbedArgs& e, const T* src,
     }
 }
 
+// Rows of at most 64 column pairs: one warp per row, 8 rows per CTA; longer rows: one
+// CTA per row.
 __global__ void oz_embed_kernel(const OzEmbedArgs e)
 {
-    __shared__ double red[32];
+    __shared__ unsigned long long red[32];
     const long long rows = (long long)e.nblk * e.R;
+    if (e.Kpad / 2 <= 64) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+        for (long long br = (long long)blockIdx.x * wpb + warp; br < rows; br += (long long)gridDim.x * wpb) {
+            if (e.src32) oz_embed_row<true>(e, e.src32, br, lane, 32, red);
+            else oz_embed_row<true>(e, e.src, br, lane, 32, red);
+        }
+        return;
+    }
     for (long long br = blockIdx.x; br < rows; br += gridDim.x) {
-        if (e.src32) oz_embed_row(e, e.src32, br, red);
-        else oz_embed_row(e, e.src, br, red);
+        if (e.src32) oz_embed_row<false>(e, e.src32, br, threadIdx.x, blockDim.x, red);
+        else oz_embed_row<false>(e, e.src, br, threadIdx.x, blockDim.x, red);
     }
 }
 
@@ -507,7 +636,7 @@ struct OzWprimeArgs {
 
 template <typename TV, typename TO>
 __device__ void oz_wprime_row(const OzWprimeArgs& w, const TV* vvvv, const TO* ovvv, long long row,
-                              double2* vals, double* red) {
+                              double2* vals, unsigned long long* red) {
     const int N = w.N, o = w.o, v = w.v;
     const long long vv = (long long)v * v, v4 = vv * vv, ov3 = (long long)o * v * vv;
     const long long bi = row / w.nab;
@@ -522,7 +651,7 @@ __device__ void oz_wprime_row(const OzWprimeArgs& w, const TV* vvvv, const TO* o
     const TO* pb = ovvv + blk_ab * ov3 + (long long)b * vv;         // ovvv[ka,kb,ke](r,b,.)
     const double2* tb = w.t1 + (long long)kb * o * v + b;          // + r v: t_r^b(kb)
     const double2* ta = w.t1 + (long long)ka * o * v + a;          // t_r^a(ka)
-    double m = 0.0;
+    unsigned long long m = 0;
     for (int ei = threadIdx.x; ei < w.nef; ei += blockDim.x) {
         const int ef = w.efl[ei];
         double2 g = ldz(g0 + ef);
@@ -538,11 +667,13 @@ __device__ void oz_wprime_row(const OzWprimeArgs& w, const TV* vvvv, const TO* o
             g.y = fma(-tar.x, q.y, fma(-tar.y, q.x, g.y));
         }
         vals[ei] = g;
-        m = fmax(m, fmax(fabs(g.x), fabs(g.y)));
+        const unsigned long long a = abs_bits(g.x), c = abs_bits(g.y);
+        m = a > m ? a : m;
+        m = c > m ? c : m;
     }
-    const int E = oz_row_exponent(block_max(m, red));   // its barriers also publish vals[]
-    const double inv = ldexp(1.0, -E);
-    const float scale = ldexpf(1.0f, E);
+    const int E = oz_row_exponent(block_max_u64(m, red));   // its barriers also publish vals[]
+    const double fx = oz_fixed_scale(w.slices, E);
+    const float scale = oz_row_scale(E);
     const long long row0 = bi * 2 * w.nab + 2LL * ai;
     const long long plane = w.rows * (long long)w.Kpad;
     if (threadIdx.x == 0) { w.sc[row0] = scale; w.sc[row0 + 1] = scale; }
@@ -552,8 +683,8 @@ __device__ void oz_wprime_row(const OzWprimeArgs& w, const TV* vvvv, const TO* o
         uint16_t sr[OZ_MAX_SLICES], si[OZ_MAX_SLICES];
         if (k < w.nef) {
             const double2 z = vals[k];
-            oz_split(z.x, inv, w.slices, sr);
-            oz_split(z.y, inv, w.slices, si);
+            oz_split(z.x, fx, w.slices, sr);
+            oz_split(z.y, fx, w.slices, si);
         } else {
             for (int p = 0; p < w.slices; ++p) { sr[p] = 0; si[p] = 0; }
         }
@@ -570,7 +701,7 @@ __device__ void oz_wprime_row(const OzWprimeArgs& w, const TV* vvvv, const TO* o
 __global__ void oz_wprime_kernel(const OzWprimeArgs w)
 {
     extern __shared__ double2 vals[];
-    __shared__ double red[32];
+    __shared__ unsigned long long red[32];
     const long long rows = (long long)w.nblk * w.nab;
     for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
         if (w.vvvv32) {

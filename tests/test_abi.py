@@ -162,3 +162,23 @@ def test_ozaki_footprint_grows_with_slices(libpath):
         out.append(b.value)
     assert out[0] < out[1] < out[2]
     assert out[2] - out[1] == out[1] - out[0]      # linear in the slice count
+
+
+def test_plan_describe_marks_tensor_core_alternatives(libpath):
+    """The plan listing: the FP64 form has only always-on steps; the Ozaki form keeps each
+    large FP64 GEMM as a native-FP64 alternative (mode 1) beside its tensor-core steps
+    (mode 2); the mixed form's FP32-only fused steps run in mixed iterations only (mode 3)."""
+    from paper_1911_00242_gb300 import binding
+    binding.load(libpath)
+    fp64 = binding.plan_describe((2, 2, 1), 4, 12)
+    assert {m for (_, _, m, _) in fp64} == {0}
+    oz = binding.plan_describe((2, 2, 1), 4, 12, precision=binding.CCSD_OZAKI)
+    names_tc = {n for (n, k, m, _) in oz if k == 6}
+    assert {"ladder", "ring", "ring_W_t2", "hole_hole", "hole_hole_W"} <= names_tc
+    assert all(m == 2 for (_, k, m, _) in oz if k in (5, 6, 10))
+    assert not any(k in (9, 11, 12) for (_, k, _, _) in oz)            # no FP32-only steps
+    mixed = binding.plan_describe((2, 2, 1), 4, 12, precision=binding.CCSD_MIXED)
+    assert all(m == 3 for (_, k, m, _) in mixed if k in (9, 11, 12))
+    # the ladder's FP64 W' slabs and FP64 contractions are alternatives in both tensor-core forms
+    for plan in (oz, mixed):
+        assert any(n == "ladder" and k == 0 and m == 1 for (n, k, m, _) in plan)
