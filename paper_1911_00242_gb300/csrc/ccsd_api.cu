@@ -596,8 +596,9 @@ void add_zero(ccsd_ctx* h, int buf) {
 dim3 ew_grid(long long n);
 dim3 row_grid(long long rows);
 
-// Ozaki form: every remaining FP64 GEMM step with at least OZ_CONVERT_FLOPS of work gets a
-// tensor-core alternative (the FP64 step stays for native FP64 iterations, mode 1).  The
+// Ozaki form: every remaining FP64 GEMM step with at least OZ_CONVERT_FLOPS of work that
+// the cost model below finds faster on the tensor cores than in the double-float engine
+// gets a tensor-core alternative (the GEMM step stays for native FP64 iterations, mode 1).  The
 // batches are split into groups whose distinct operand blocks fit the shared operand
 // buffers; each group is embedded just before its GEMM (stream order keeps the buffers
 // intact while it runs).  In the pooled layout the buffers are the tensor-core pools; else
@@ -608,7 +609,7 @@ constexpr double OZ_CONVERT_FLOPS = 5e8;
 constexpr double OZ_CTA_SECONDS = 8e-6;
 constexpr double OZ_STAGE_SECONDS = 0.35e-6;
 constexpr double OZ_EMBED_BPS = 2e12;
-constexpr double OZ_FP64_FLOPS = 1.1e12;
+constexpr double OZ_DF_FLOPS = 5e12;      // the double-float instance of the GEMM engine
 constexpr long long OZ_GENERIC_CAP = 1LL << 28;
 
 int oz_convert_gemms(ccsd_ctx* h, Alloc& al, std::map<int, GemmSpec>& specs, bool pooled, float* pool_a,
@@ -638,14 +639,14 @@ int oz_convert_gemms(ccsd_ctx* h, Alloc& al, std::map<int, GemmSpec>& specs, boo
         std::sort(ua.begin(), ua.end()); ua.erase(std::unique(ua.begin(), ua.end()), ua.end());
         std::sort(ub.begin(), ub.end()); ub.erase(std::unique(ub.begin(), ub.end()), ub.end());
         // worth it?  Tensor-core estimate: per CTA a fixed cost plus its stages (all tiles,
-        // padding included), plus the operand embedding at HBM speed; FP64 estimate: the
-        // algorithmic flops at the FP64 rate.
+        // padding included), plus the operand embedding at HBM speed; the alternative is the
+        // double-float GEMM engine (algorithmic flops at its rate).
         const double ctas = (double)tiles(s.M, s.N) * s.nbatch;
         const double stages = (double)s.nchunk * (h->oz_slices * (h->oz_slices + 1) / 2) * (kpad / OZ_BK);
         const double emb = ((double)ua.size() * s.M + (double)ub.size() * 2 * s.N) * kpad * 2.0 * h->oz_slices;
         const double t_tc = (ctas * OZ_CTA_SECONDS + ctas * stages * OZ_STAGE_SECONDS) / 152.0 + emb / OZ_EMBED_BPS;
-        const double t_fp64 = st.flops / OZ_FP64_FLOPS;
-        if (t_tc > 0.7 * t_fp64) continue;
+        const double t_df = st.flops / OZ_DF_FLOPS;
+        if (t_tc > 0.7 * t_df) continue;
         // the largest single batch must fit: its chunks' A blocks and B blocks
         const long long ra = (long long)s.nchunk * s.M, rb = (long long)s.nchunk * 2 * s.N;
         cand[st.idx] = Cand{st.idx, kpad, ra * kpad, rb * kpad, ra, rb};
@@ -1703,7 +1704,15 @@ int launch_gemm(ccsd_ctx* h, GemmPlan& p) {
     g.A32 = (h->fp32 || h->in32[p.a]) ? h->shadow[p.a] : nullptr;
     g.B32 = (h->fp32 || h->in32[p.b]) ? h->shadow[p.b] : nullptr;
     dim3 grid((unsigned)p.blocks, (unsigned)g.nsplit);
-    if (h->fp32) {
+    if (h->oz_on) {         // Ozaki form: the GEMMs left off the tensor cores run in double-float
+        switch (p.cfg) {
+            case CFG_64x64:  zgemm_kb_kernel<64, 64, 8, 4, 4, df><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_64x32:  zgemm_kb_kernel<64, 32, 8, 4, 2, df><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_128x16: zgemm_kb_kernel<128, 16, 8, 8, 1, df><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_32x16:  zgemm_kb_kernel<32, 16, 8, 2, 1, df><<<grid, 256, 0, h->st>>>(g); break;
+            default:         zgemm_kb_kernel<16, 16, 8, 1, 1, df><<<grid, 256, 0, h->st>>>(g); break;
+        }
+    } else if (h->fp32) {
         switch (p.cfg) {
             case CFG_64x64:  zgemm_kb_kernel<64, 64, 8, 4, 4, float><<<grid, 256, 0, h->st>>>(g); break;
             case CFG_64x32:  zgemm_kb_kernel<64, 32, 8, 4, 2, float><<<grid, 256, 0, h->st>>>(g); break;

@@ -20,8 +20,8 @@
 // The pairs with p + q <= s - 1 are formed (s (s + 1) / 2 of them); the others
 // lie below 2^{-7(s+1)} of 2^{Ea+Eb} per product.  A TMEM accumulator sums one
 // chunk's products of pairs with the same p + q over at most OZ_WIN stages
-// (512 products of magnitude <= 2^14), so its value is an integer below 2^23 and
-// the FP32 tensor-core accumulation is exact.  Each such window is multiplied by
+// (1024 products of magnitude <= 2^14), so every partial sum is an integer of
+// magnitude <= 2^24, which FP32 holds exactly: the tensor-core accumulation is exact.  Each such window is multiplied by
 // its power of two (exact) and added into (hi, lo) with TwoSum (Knuth), so the
 // only roundings after the split are those of the double-float sum.  The window
 // factors are taken relative to the largest row scales of the output's chunks
@@ -50,7 +50,7 @@ constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;    // 32 KiB
 constexpr int OZ_LO_COL = 2 * OZ_BN;                       // TMEM columns of the lo accumulator
 constexpr int OZ_HI_COL = 3 * OZ_BN;                       // TMEM columns of the hi accumulator
 constexpr int OZ_TMEM_COLS = 4 * OZ_BN;                    // two windows, lo, hi
-constexpr int OZ_WIN = 8;                                  // stages per exact TMEM window
+constexpr int OZ_WIN = 16;                                 // stages per exact TMEM window (64 K each)
 constexpr int OZ_ACC_WARPS = 16;                           // four per TMEM lane quarter, 32 columns each
 constexpr int OZ_COLS = OZ_BN / (OZ_ACC_WARPS / 4);        // columns per accumulator thread
 constexpr int OZ_THREADS = 64 + 32 * OZ_ACC_WARPS;

@@ -50,6 +50,19 @@ def test_oz_gemm_exact_on_integer_operands(lib, M, Nc, K):
     assert np.array_equal(C, ref)
 
 
+def test_oz_gemm_exact_at_the_window_bound(lib):
+    """The largest exact window: every entry (1 - 2^-20)(1 +- i) has top slice 128, so each
+    TMEM window of 16 stages sums 1024 products of exactly 2^14 to 2^24, the largest
+    integer range FP32 holds; the product must still be exact."""
+    from paper_1911_00242_gb300.binding import oz_gemm
+    x = 1.0 - 2.0 ** -20
+    A = np.full((128, 512), x + 1j * x)
+    B = np.full((128, 512), x - 1j * x)
+    C = oz_gemm(A, B, slices=5)
+    assert np.array_equal(C, A @ B.T)
+    assert C[0, 0] == 512 * 2 * x * x
+
+
 @pytest.mark.parametrize("slices", [3, 5, 7, 8])
 @pytest.mark.parametrize("M,Nc,K", [(256, 256, 2048), (130, 70, 333)])
 def test_oz_gemm_error_bound(lib, slices, M, Nc, K):
