@@ -19,9 +19,11 @@
 //   (A' B'^T)_mn = 2^{Ea_m + Eb_n} sum_{p,q} 2^{-7(p+q+2)} (V_p W_q^T)_mn.
 // The pairs with p + q <= s - 1 are formed (s (s + 1) / 2 of them); the others
 // lie below 2^{-7(s+1)} of 2^{Ea+Eb} per product.  A TMEM accumulator sums one
-// chunk's products of pairs with the same p + q over at most OZ_WIN stages
-// (1024 products of magnitude <= 2^14), so every partial sum is an integer of
-// magnitude <= 2^24, which FP32 holds exactly: the tensor-core accumulation is exact.  Each such window is multiplied by
+// chunk's products of pairs with the same d = p + q over at most oz_win(d) stages
+// (d = 0: 1024 products of magnitude <= 2^14; d > 0: every pair has a slice with
+// |v| <= 64, so 2048 products of magnitude <= 2^13), so every partial sum is an
+// integer of magnitude <= 2^24, which FP32 holds exactly: the tensor-core
+// accumulation is exact.  Each such window is multiplied by
 // its power of two (exact) and added into (hi, lo) with TwoSum (Knuth), so the
 // only roundings after the split are those of the double-float sum.  The window
 // factors are taken relative to the largest row scales of the output's chunks
@@ -50,7 +52,8 @@ constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;    // 32 KiB
 constexpr int OZ_LO_COL = 2 * OZ_BN;                       // TMEM columns of the lo accumulator
 constexpr int OZ_HI_COL = 3 * OZ_BN;                       // TMEM columns of the hi accumulator
 constexpr int OZ_TMEM_COLS = 4 * OZ_BN;                    // two windows, lo, hi
-constexpr int OZ_WIN = 16;                                 // stages per exact TMEM window (64 K each)
+// stages (64 K each) per exact TMEM window of diagonal d
+__host__ __device__ constexpr int oz_win(int d) { return d == 0 ? 16 : 32; }
 constexpr int OZ_ACC_WARPS = 16;                           // four per TMEM lane quarter, 32 columns each
 constexpr int OZ_COLS = OZ_BN / (OZ_ACC_WARPS / 4);        // columns per accumulator thread
 constexpr int OZ_THREADS = 64 + 32 * OZ_ACC_WARPS;
@@ -100,11 +103,16 @@ __device__ __forceinline__ void oz_mma(uint32_t tmem_d, uint64_t adesc, uint64_t
                  :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc) : "memory");
 }
 
-// Slice pairs in diagonal order: pair index pi -> d = p + q, p (q = d - p).
-__device__ __forceinline__ int oz_diag(int pi) {
-    int d = 0;
-    while ((d + 1) * (d + 2) / 2 <= pi) ++d;
-    return d;
+// 8 consecutive TMEM columns of this warp's lane quarter <-> registers (32x32b.x8).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+                    "r"(r[7]) : "memory");
 }
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
@@ -224,8 +232,9 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 const int d = u % S;
                 const int glen = (d + 1) * g.kstages;          // stages of this unit
                 for (int j = 0; j < glen; ++j, ++s) {
-                    const bool first = (j % OZ_WIN) == 0;
-                    const bool last = ((j + 1) % OZ_WIN) == 0 || j + 1 == glen;
+                    const int win = oz_win(d);
+                    const bool first = (j % win) == 0;
+                    const bool last = ((j + 1) % win) == 0 || j + 1 == glen;
                     const int buf = w & 1;
                     if (first && w >= 2) {
                         if (!mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)((w - 2) >> 1) & 1u, abort_flag, g.spin_limit)) {
@@ -315,7 +324,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             }
             {
                 const float fa = sa * __int_as_float((127 - OZ_SLICE_BITS * (d + 2)) << 23);  // * 2^{-7(d+2)}
-                const int nwin = ((d + 1) * g.kstages + OZ_WIN - 1) / OZ_WIN;
+                const int nwin = ((d + 1) * g.kstages + oz_win(d) - 1) / oz_win(d);
                 for (int wi = 0; wi < nwin; ++wi, ++w) {
                     const int buf = w & 1;
                     bool got = mbar_wait(smem_u32(&acc_full[buf]), (uint32_t)(w >> 1) & 1u, abort_flag, g.spin_limit);
@@ -325,22 +334,9 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 #pragma unroll
                     for (int c0 = 0; c0 < OZ_COLS; c0 += 8) {
                         uint32_t v[8], l[8], hh[8];
-                        const uint32_t taddr = tmem + tlane + (uint32_t)(buf * OZ_BN + half * OZ_COLS + c0);
-                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 "
-                                     "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                                       "=r"(v[6]), "=r"(v[7])
-                                     : "r"(taddr));
-                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 "
-                                     "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                     : "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]),
-                                       "=r"(l[6]), "=r"(l[7])
-                                     : "r"(tlo + c0));
-                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 "
-                                     "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                     : "=r"(hh[0]), "=r"(hh[1]), "=r"(hh[2]), "=r"(hh[3]), "=r"(hh[4]), "=r"(hh[5]),
-                                       "=r"(hh[6]), "=r"(hh[7])
-                                     : "r"(thi + c0));
+                        tmem_ld8(tmem + tlane + (uint32_t)(buf * OZ_BN + half * OZ_COLS + c0), v);
+                        tmem_ld8(tlo + c0, l);
+                        tmem_ld8(thi + c0, hh);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
@@ -350,12 +346,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                             l[i] = __float_as_uint(lo);
                             hh[i] = __float_as_uint(hi);
                         }
-                        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
-                                     :: "r"(tlo + c0), "r"(l[0]), "r"(l[1]), "r"(l[2]), "r"(l[3]), "r"(l[4]),
-                                        "r"(l[5]), "r"(l[6]), "r"(l[7]) : "memory");
-                        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
-                                     :: "r"(thi + c0), "r"(hh[0]), "r"(hh[1]), "r"(hh[2]), "r"(hh[3]), "r"(hh[4]),
-                                        "r"(hh[5]), "r"(hh[6]), "r"(hh[7]) : "memory");
+                        tmem_st8(tlo + c0, l);
+                        tmem_st8(thi + c0, hh);
                     }
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
