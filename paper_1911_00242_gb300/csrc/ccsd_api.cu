@@ -18,6 +18,12 @@
 //   (X_mnij = sum tau_ij^ef <mn||ef>; both W~ factorizations are the
 //    paper's Eq. ori_EqDouble regrouped, so R2 is unchanged)
 // and the update t <- t + R/D with convergence test and energy (Sec. 4.4).
+//
+// The mixed and Ozaki forms add tensor-core variants of the ladder, ring and
+// hole-hole contractions (steps of mode 2, tcgemm.cuh / ozaki.cuh) beside their FP64
+// steps (mode 1); a handle runs one or the other per iteration.  The mixed form runs
+// the remaining GEMMs in FP32 (and fuses the Fock terms), the Ozaki form runs them in
+// double-float.
 #include "../../include/ccsd.h"
 #include "ccsd_kernels.cuh"
 #include "tcgemm.cuh"
@@ -169,6 +175,7 @@ struct ccsd_ctx {
     int oz_on = 0;                   // Ozaki-scheme tensor-core contractions active (CCSD_OZAKI)
     int oz_slices = 7;               // slices per operand row (CCSD_OZAKI)
     long long oz_work_elems = 0;     // split partials of the Ozaki GEMMs (complex elements)
+    df2* ovvv_df = nullptr;          // Ozaki form, complex128 ovvv: its double-float copy
     double2* oz_work = nullptr;
     long long wab_cap_bytes = 12LL << 30;   // bound of the ladder's W' slab buffer
     // mixed and Ozaki forms: tensor-core operands (TF32 big/small parts, or BF16 slice
@@ -793,6 +800,14 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
             if (al.err) return al.err;
         }
         if (!al.dry && cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st) != cudaSuccess) return CCSD_ERR_CUDA;
+        if (oz && !h->in32[B_OVVV]) {
+            // the W' kernel's t1 terms run in double-float: convert the constant ovvv once
+            h->ovvv_df = (df2*)al.get((size_t)h->bufsize[B_OVVV] * sizeof(df2));
+            if (al.err) return al.err;
+            if (!al.dry)
+                to_df2_kernel<<<ew_grid(h->bufsize[B_OVVV]), 256, 0, h->st>>>(h->ovvv_df, h->buf[B_OVVV],
+                                                                             h->bufsize[B_OVVV]);
+        }
         // ladder B rows of the largest packed class (floats per part)
         long long lad_max = 0, lad_batch = 0;    // largest class, largest single (ka, kb) batch
         for (int diag_ab = 0; diag_ab < 2; ++diag_ab) for (int diag_ef = 0; diag_ef < 2; ++diag_ef) {
@@ -1865,10 +1880,11 @@ void launch_step(ccsd_ctx* h, size_t si) {
                     OzWprimeArgs z = h->wlists[s.idx].z;
                     if (h->in32[B_VVVV]) { z.vvvv32 = h->shadow[B_VVVV]; z.vvvv = nullptr; }
                     else { z.vvvv = h->buf[B_VVVV]; z.vvvv32 = nullptr; }
-                    if (h->in32[B_OVVV]) { z.ovvv32 = h->shadow[B_OVVV]; z.ovvv = nullptr; }
-                    else { z.ovvv = h->buf[B_OVVV]; z.ovvv32 = nullptr; }
+                    if (h->in32[B_OVVV]) { z.ovvv32 = h->shadow[B_OVVV]; z.ovvv_df = nullptr; }
+                    else { z.ovvv_df = h->ovvv_df; z.ovvv32 = nullptr; }
                     z.t1 = h->buf[B_T1];
-                    oz_wprime_kernel<<<row_grid((long long)z.nblk * z.nab), 256, (size_t)z.nef * 16, h->st>>>(z);
+                    oz_wprime_kernel<<<row_grid((long long)z.nblk * z.nab), 256, (size_t)(z.nef + 2 * z.o) * 16,
+                                       h->st>>>(z);
                     ++h->launches;
                     break;
                 }

@@ -39,6 +39,7 @@
 // Every mbarrier wait is bounded, as in the split-TF32 kernel.
 #pragma once
 #include "tcgemm.cuh"
+#include "dfloat.cuh"
 
 namespace ccsdk {
 
@@ -613,12 +614,13 @@ __global__ void oz_embed_kernel(const OzEmbedArgs e)
 }
 
 // Ladder operand W'^{abef} (the same quantity as wprime_list_kernel forms in FP32),
-// formed in FP64 and written as Ozaki slices of the B-side embedding: output block
+// formed in FP64-class arithmetic (t1 terms in double-float, vvvv added in FP64) and
+// written as Ozaki slices of the B-side embedding: output block
 // bi is the momentum triple blk[3 bi ..], its rows the listed (a, b) pairs (2 per
 // pair), its columns the listed (e, f) pairs; rows bi 2 nab + 2 ai + s.
 struct OzWprimeArgs {
     const double2* vvvv; const float2* vvvv32;     // one of them
-    const double2* ovvv; const float2* ovvv32;     // one of them
+    const df2* ovvv_df; const float2* ovvv32;      // one of them (complex128 input: its double-float copy)
     const double2* t1;
     uint16_t* sl; float* sc;
     const int* blk; const int* abl; const int* efl;
@@ -626,9 +628,11 @@ struct OzWprimeArgs {
     int nblk, nab, nef, N, o, v, Kpad, slices;
 };
 
+// The t1 terms are summed in double-float (FP32 pipe) from a double-float copy of
+// ovvv (or its complex64 values) and t1 values staged in shared memory.
 template <typename TV, typename TO>
 __device__ void oz_wprime_row(const OzWprimeArgs& w, const TV* vvvv, const TO* ovvv, long long row,
-                              double2* vals, unsigned long long* red) {
+                              double2* vals, unsigned long long* red, df2* t1s) {
     const int N = w.N, o = w.o, v = w.v;
     const long long vv = (long long)v * v, v4 = vv * vv, ov3 = (long long)o * v * vv;
     const long long bi = row / w.nab;
@@ -641,23 +645,35 @@ __device__ void oz_wprime_row(const OzWprimeArgs& w, const TV* vvvv, const TO* o
     const TV* g0 = vvvv + blk_ab * v4 + (long long)ab * vv;
     const TO* pa = ovvv + blk_ba * ov3 + (long long)a * vv;         // + r v vv: ovvv[kb,ka,ke](r,a,.)
     const TO* pb = ovvv + blk_ab * ov3 + (long long)b * vv;         // ovvv[ka,kb,ke](r,b,.)
-    const double2* tb = w.t1 + (long long)kb * o * v + b;          // + r v: t_r^b(kb)
-    const double2* ta = w.t1 + (long long)ka * o * v + a;          // t_r^a(ka)
+    // t1s[r] = t_r^b(kb), t1s[o + r] = -t_r^a(ka)
+    __syncthreads();                              // t1s of the previous row is no longer read
+    for (int r = threadIdx.x; r < 2 * o; r += blockDim.x) {
+        if (r < o) {
+            t1s[r] = ld_df2(w.t1 + (long long)kb * o * v + (long long)r * v + b);
+        } else {
+            const df2 z = ld_df2(w.t1 + (long long)ka * o * v + (long long)(r - o) * v + a);
+            t1s[r] = df2{-z.x, -z.y};
+        }
+    }
+    __syncthreads();
     unsigned long long m = 0;
     for (int ei = threadIdx.x; ei < w.nef; ei += blockDim.x) {
         const int ef = w.efl[ei];
-        double2 g = ldz(g0 + ef);
+        df2 s{df(0), df(0)};
         for (int r = 0; r < o; ++r) {
             // + t_r^b(kb) ovvv[kb,ka,ke](r,a,e,f) - t_r^a(ka) ovvv[ka,kb,ke](r,b,e,f)
-            const double2 tbr = tb[r * v];
-            const double2 p = ldz(pa + (long long)r * v * vv + ef);
-            g.x = fma(tbr.x, p.x, fma(-tbr.y, p.y, g.x));
-            g.y = fma(tbr.x, p.y, fma(tbr.y, p.x, g.y));
-            const double2 tar = ta[r * v];
-            const double2 q = ldz(pb + (long long)r * v * vv + ef);
-            g.x = fma(-tar.x, q.x, fma(tar.y, q.y, g.x));
-            g.y = fma(-tar.x, q.y, fma(-tar.y, q.x, g.y));
+            const df2 p = ld_df2(pa + (long long)r * v * vv + ef);
+            const df2 tb = t1s[r];
+            s.x = fma(tb.x, p.x, s.x); s.x = fma(-tb.y, p.y, s.x);
+            s.y = fma(tb.x, p.y, s.y); s.y = fma(tb.y, p.x, s.y);
+            const df2 q = ld_df2(pb + (long long)r * v * vv + ef);
+            const df2 ta = t1s[o + r];
+            s.x = fma(ta.x, q.x, s.x); s.x = fma(-ta.y, q.y, s.x);
+            s.y = fma(ta.x, q.y, s.y); s.y = fma(ta.y, q.x, s.y);
         }
+        double2 g = ldz(g0 + ef);
+        g.x += (double)s.x;
+        g.y += (double)s.y;
         vals[ei] = g;
         const unsigned long long a = abs_bits(g.x), c = abs_bits(g.y);
         m = a > m ? a : m;
@@ -692,16 +708,17 @@ __device__ void oz_wprime_row(const OzWprimeArgs& w, const TV* vvvv, const TO* o
 // One CTA per output row pair; dynamic shared memory holds the row's nef values.
 __global__ void oz_wprime_kernel(const OzWprimeArgs w)
 {
-    extern __shared__ double2 vals[];
+    extern __shared__ double2 vals[];             // [nef] values, then [2 o] t1 values (df2)
     __shared__ unsigned long long red[32];
+    df2* t1s = (df2*)(vals + w.nef);
     const long long rows = (long long)w.nblk * w.nab;
     for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
         if (w.vvvv32) {
-            if (w.ovvv32) oz_wprime_row(w, w.vvvv32, w.ovvv32, row, vals, red);
-            else oz_wprime_row(w, w.vvvv32, w.ovvv, row, vals, red);
+            if (w.ovvv32) oz_wprime_row(w, w.vvvv32, w.ovvv32, row, vals, red, t1s);
+            else oz_wprime_row(w, w.vvvv32, w.ovvv_df, row, vals, red, t1s);
         } else {
-            if (w.ovvv32) oz_wprime_row(w, w.vvvv, w.ovvv32, row, vals, red);
-            else oz_wprime_row(w, w.vvvv, w.ovvv, row, vals, red);
+            if (w.ovvv32) oz_wprime_row(w, w.vvvv, w.ovvv32, row, vals, red, t1s);
+            else oz_wprime_row(w, w.vvvv, w.ovvv_df, row, vals, red, t1s);
         }
     }
 }

@@ -25,6 +25,7 @@
 // both; the double instance widens them exactly.  On GB300 a double->float conversion issues on the slow
 // FP64 pipe, so the complex64 copies matter for throughput, not only bytes.
 #pragma once
+#include "dfloat.cuh"
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -44,62 +45,6 @@ struct GemmArgs {
     double alpha_re, alpha_im;
     int tiles_m, tiles_n;
 };
-
-// Double-float ("df") numbers for the Ozaki form's remaining GEMMs: x = h + l with
-// |l| <= ulp(h) / 2, about 48 significant bits, in FP32 arithmetic (GB300's FP32 pipe
-// issues about 64 times as many operations per clock as its FP64 pipe).  The
-// error-free transformations are TwoSum (Knuth) and the FMA product error; the
-// intrinsics keep the compiler from contracting or reassociating them.
-struct df {
-    float h, l;
-    __device__ __forceinline__ df() {}
-    __device__ __forceinline__ df(float a, float b) : h(a), l(b) {}
-    __device__ __forceinline__ explicit df(int x) : h((float)x), l(0.f) {}
-    __device__ __forceinline__ explicit df(float x) : h(x), l(0.f) {}
-    __device__ __forceinline__ explicit df(double x) : h((float)x), l((float)(x - (double)h)) {}
-    __device__ __forceinline__ explicit operator double() const { return (double)h + (double)l; }
-};
-
-__device__ __forceinline__ df df_renorm(float s, float t) {      // (s, t) -> h + l, |l| <= ulp(h) / 2
-    const float h = __fadd_rn(s, t);
-    return df(h, __fsub_rn(t, __fsub_rn(h, s)));
-}
-
-__device__ __forceinline__ df operator+(df a, df b) {
-    const float s = __fadd_rn(a.h, b.h);
-    const float bb = __fsub_rn(s, a.h);
-    float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
-    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
-    return df_renorm(s, e);
-}
-
-__device__ __forceinline__ df operator-(df a) { return df(-a.h, -a.l); }
-__device__ __forceinline__ df operator-(df a, df b) { return a + df(-b.h, -b.l); }
-
-__device__ __forceinline__ df operator*(df a, df b) {
-    const float p = __fmul_rn(a.h, b.h);
-    float e = __fmaf_rn(a.h, b.h, -p);
-    e = __fmaf_rn(a.h, b.l, e);
-    e = __fmaf_rn(a.l, b.h, e);
-    return df_renorm(p, e);
-}
-
-// a * b + c
-__device__ __forceinline__ df fma(df a, df b, df c) {
-    const float p = __fmul_rn(a.h, b.h);
-    float e = __fmaf_rn(a.h, b.h, -p);
-    e = __fmaf_rn(a.h, b.l, e);
-    e = __fmaf_rn(a.l, b.h, e);
-    const float s = __fadd_rn(p, c.h);
-    const float bb = __fsub_rn(s, p);
-    float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(c.h, bb));
-    t = __fadd_rn(t, __fadd_rn(e, c.l));
-    return df_renorm(s, t);
-}
-
-using ::fma;             // the float and double overloads stay visible beside the df one
-
-struct df2 { df x, y; };
 
 template <typename T> struct Cplx;
 template <> struct Cplx<double> { using V = double2; };
