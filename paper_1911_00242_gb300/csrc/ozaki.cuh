@@ -46,6 +46,7 @@ namespace ccsdk {
 constexpr int OZ_BM = 128;
 constexpr int OZ_BN = 128;
 constexpr int OZ_BK = 64;                                  // BF16 elements per stage row (128 B)
+static_assert(OZ_BK == 4 * 16, "the MMA issuer issues four K = 16 MMAs per stage");
 constexpr int OZ_STAGES = 6;
 constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;              // 16 KiB
 constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;              // 16 KiB
@@ -196,46 +197,57 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- producer: TMA loads
-            int s = 0;
+            // ---------------- producer: TMA loads.  The ring position (st, ph) advances
+            // incrementally: this single thread's issue rate bounds the pipeline.
+            const uint32_t sA0 = smem_u32(stA), sB0 = smem_u32(stB);
+            const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[OZ_STAGES]);
+            int s = 0, st = 0;
+            uint32_t ph = 0;
             bool run = true;
             for (int u = u0; u < u1 && run; ++u) {
                 const int c = u / S, d = u - c * S;
                 const int ra = g.rowA[b * g.nchunk + c] + m0, rb = g.rowB[b * g.nchunk + c] + n0;
                 for (int p = 0; p <= d && run; ++p) {
                     const int ya = p * g.rowsA + ra, yb = (d - p) * g.rowsB + rb;
-                    for (int kst = 0; kst < g.kstages; ++kst, ++s) {
-                        const int st = s % OZ_STAGES;
-                        const uint32_t ph = (uint32_t)(s / OZ_STAGES) & 1u;
-                        if (!mbar_wait(smem_u32(&bars[OZ_STAGES + st]), ph ^ 1u, abort_flag, g.spin_limit)) {
+                    for (int kst = 0; kst < g.kstages; ++kst) {
+                        if (!mbar_wait(empty0 + 8 * st, ph ^ 1u, abort_flag, g.spin_limit)) {
                             atomicCAS(g.err, 0, 1);
                             *abort_flag = 1;
                             run = false;
                             break;
                         }
-                        if (s == g.skip_stage) continue;   // nothing will complete this stage
-                        const uint32_t full = smem_u32(&bars[st]);
-                        mbar_expect_tx(full, OZ_STAGE_BYTES);
-                        tma_load_2d(smem_u32(stA + st * OZ_A_BYTES), &mapA, kst * OZ_BK, ya, full);
-                        tma_load_2d(smem_u32(stB + st * OZ_B_BYTES), &mapB, kst * OZ_BK, yb, full);
-                        issued = s + 1;
+                        if (s != g.skip_stage) {           // a skipped stage is never completed
+                            const uint32_t full = full0 + 8 * st;
+                            mbar_expect_tx(full, OZ_STAGE_BYTES);
+                            tma_load_2d(sA0 + st * OZ_A_BYTES, &mapA, kst * OZ_BK, ya, full);
+                            tma_load_2d(sB0 + st * OZ_B_BYTES, &mapB, kst * OZ_BK, yb, full);
+                            issued = s + 1;
+                        }
+                        ++s;
+                        if (++st == OZ_STAGES) { st = 0; ph ^= 1u; }
                     }
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---------------- MMA issuer: window w accumulates in TMEM buffer w & 1
+            // ---------------- MMA issuer: window w accumulates in TMEM buffer w & 1.  The
+            // descriptors of stage st are the stage-0 ones plus the stage offset (their
+            // start-address field is the shared address / 16, below 2^14).
             const uint32_t idesc = oz_idesc_bf16();
-            int w = 0, s = 0;
+            const uint64_t da0 = smem_desc_sw128(smem_u32(stA)), db0 = smem_desc_sw128(smem_u32(stB));
+            const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[OZ_STAGES]);
+            int w = 0, st = 0;
+            uint32_t ph = 0;
             bool run = true;
             for (int u = u0; u < u1 && run; ++u) {
                 const int d = u % S;
                 const int glen = (d + 1) * g.kstages;          // stages of this unit
-                for (int j = 0; j < glen; ++j, ++s) {
-                    const int win = oz_win(d);
-                    const bool first = (j % win) == 0;
-                    const bool last = ((j + 1) % win) == 0 || j + 1 == glen;
+                const int win = oz_win(d);
+                int jw = 0;                                     // stage within the window
+                for (int j = 0; j < glen; ++j) {
+                    const bool first = jw == 0;
+                    const bool last = jw + 1 == win || j + 1 == glen;
                     const int buf = w & 1;
                     if (first && w >= 2) {
                         if (!mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)((w - 2) >> 1) & 1u, abort_flag, g.spin_limit)) {
@@ -246,28 +258,29 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     }
-                    const int st = s % OZ_STAGES;
-                    const uint32_t ph = (uint32_t)(s / OZ_STAGES) & 1u;
-                    if (!mbar_wait(smem_u32(&bars[st]), ph, abort_flag, g.spin_limit)) {
+                    if (!mbar_wait(full0 + 8 * st, ph, abort_flag, g.spin_limit)) {
                         atomicCAS(g.err, 0, 2);
                         *abort_flag = 1;
                         run = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t a0 = smem_u32(stA + st * OZ_A_BYTES);
-                    const uint32_t b0 = smem_u32(stB + st * OZ_B_BYTES);
+                    const uint64_t da = da0 + (uint64_t)(st * (OZ_A_BYTES >> 4));
+                    const uint64_t db = db0 + (uint64_t)(st * (OZ_B_BYTES >> 4));
                     const uint32_t dst = tmem + (uint32_t)(buf * OZ_BN);
-#pragma unroll
-                    for (int k = 0; k < OZ_BK / 16; ++k) {      // K = 16 BF16 (32 bytes) per MMA
-                        oz_mma(dst, smem_desc_sw128(a0 + 32 * k), smem_desc_sw128(b0 + 32 * k), idesc,
-                               (first && k == 0) ? 0u : 1u);
-                    }
-                    tc_commit(smem_u32(&bars[OZ_STAGES + st]));
+                    oz_mma(dst, da, db, idesc, first ? 0u : 1u);          // K = 16 BF16 (32 bytes) each
+                    oz_mma(dst, da + 2, db + 2, idesc, 1u);
+                    oz_mma(dst, da + 4, db + 4, idesc, 1u);
+                    oz_mma(dst, da + 6, db + 6, idesc, 1u);
+                    tc_commit(empty0 + 8 * st);
                     if (last) {
                         tc_commit(smem_u32(&acc_full[buf]));
                         ++w;
+                        jw = 0;
+                    } else {
+                        ++jw;
                     }
+                    if (++st == OZ_STAGES) { st = 0; ph ^= 1u; }
                 }
             }
             if (*abort_flag) {

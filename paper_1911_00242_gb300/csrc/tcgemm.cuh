@@ -42,6 +42,8 @@ constexpr int TC_BM = 128;
 constexpr int TC_BN = 256;
 constexpr int TC_BK = 32;                                // fp32 elements per stage row (128 B)
 constexpr int TC_STAGES = 4;
+static_assert((TC_STAGES & (TC_STAGES - 1)) == 0, "the ring index is s & (TC_STAGES - 1)");
+static_assert(TC_BK == 4 * 8, "the MMA issuer issues four K = 8 MMAs per stage");
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 4;            // 16 KiB
 constexpr int TC_B_BYTES = TC_BN * TC_BK * 4;            // 32 KiB
 constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;  // 48 KiB
@@ -210,35 +212,49 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- producer: TMA loads
+            // ---------------- producer: TMA loads.  Chunk, term and K offset advance
+            // incrementally (no divisions): this single thread's issue rate bounds the pipeline.
+            const uint32_t sA0 = smem_u32(stA), sB0 = smem_u32(stB);
+            const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[TC_STAGES]);
+            int c = 0, term = 0, kx = 0;
+            int ra = g.rowA[b * g.nchunk] + m0, rb = g.rowB[b * g.nchunk] + n0;
             for (int s = 0; s < total; ++s) {
-                const int st = s % TC_STAGES;
+                const int st = s & (TC_STAGES - 1);
                 const uint32_t ph = (uint32_t)(s / TC_STAGES) & 1u;
-                if (!mbar_wait(smem_u32(&bars[TC_STAGES + st]), ph ^ 1u, abort_flag, g.spin_limit)) {
+                if (!mbar_wait(empty0 + 8 * st, ph ^ 1u, abort_flag, g.spin_limit)) {
                     atomicCAS(g.err, 0, 1);
                     *abort_flag = 1;
                     break;
                 }
-                if (s == g.skip_stage) continue;           // nothing will complete this stage
-                const int c = s / per_chunk;
-                const int r = s % per_chunk;
-                const int term = r / g.kstages;
-                const int kx = (r % g.kstages) * TC_BK;
-                const CUtensorMap* mA = (term == 2) ? &mapA_small : &mapA_big;
-                const CUtensorMap* mB = (term == 1) ? &mapB_small : &mapB_big;
-                const int ra = g.rowA[b * g.nchunk + c] + m0;
-                const int rb = g.rowB[b * g.nchunk + c] + n0;
-                const uint32_t full = smem_u32(&bars[st]);
-                mbar_expect_tx(full, TC_STAGE_BYTES);
-                tma_load_2d(smem_u32(stA + st * TC_A_BYTES), mA, kx, ra, full);
-                tma_load_2d(smem_u32(stB + st * TC_B_BYTES), mB, kx, rb, full);
-                issued = s + 1;
+                if (s != g.skip_stage) {                   // a skipped stage is never completed
+                    const CUtensorMap* mA = (term == 2) ? &mapA_small : &mapA_big;
+                    const CUtensorMap* mB = (term == 1) ? &mapB_small : &mapB_big;
+                    const uint32_t full = full0 + 8 * st;
+                    mbar_expect_tx(full, TC_STAGE_BYTES);
+                    tma_load_2d(sA0 + st * TC_A_BYTES, mA, kx, ra, full);
+                    tma_load_2d(sB0 + st * TC_B_BYTES, mB, kx, rb, full);
+                    issued = s + 1;
+                }
+                kx += TC_BK;
+                if (kx == g.kstages * TC_BK) {
+                    kx = 0;
+                    if (++term == g.nterms) {
+                        term = 0;
+                        if (++c < g.nchunk) {
+                            ra = g.rowA[b * g.nchunk + c] + m0;
+                            rb = g.rowB[b * g.nchunk + c] + n0;
+                        }
+                    }
+                }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---------------- MMA issuer
+            // ---------------- MMA issuer.  Stage descriptors: the stage-0 ones plus the
+            // stage offset (their start-address field is the shared address / 16, below 2^14).
             const uint32_t idesc = tc_idesc_tf32();
+            const uint64_t da0 = smem_desc_sw128(smem_u32(stA)), db0 = smem_desc_sw128(smem_u32(stB));
+            const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[TC_STAGES]);
             for (int s = 0; s < total; ++s) {
                 const int seg = s / TC_PROMOTE_STAGES;
                 const int buf = seg & 1;
@@ -252,23 +268,22 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 }
-                const int st = s % TC_STAGES;
+                const int st = s & (TC_STAGES - 1);
                 const uint32_t ph = (uint32_t)(s / TC_STAGES) & 1u;
-                if (!mbar_wait(smem_u32(&bars[st]), ph, abort_flag, g.spin_limit)) {
+                if (!mbar_wait(full0 + 8 * st, ph, abort_flag, g.spin_limit)) {
                     atomicCAS(g.err, 0, 2);
                     *abort_flag = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a0 = smem_u32(stA + st * TC_A_BYTES);
-                const uint32_t b0 = smem_u32(stB + st * TC_B_BYTES);
+                const uint64_t da = da0 + (uint64_t)(st * (TC_A_BYTES >> 4));
+                const uint64_t db = db0 + (uint64_t)(st * (TC_B_BYTES >> 4));
                 const uint32_t dst = tmem + (uint32_t)(buf * TC_BN);
-#pragma unroll
-                for (int k = 0; k < TC_BK / 8; ++k) {           // K = 8 tf32 (32 bytes) per MMA
-                    tc_mma(dst, smem_desc_sw128(a0 + 32 * k), smem_desc_sw128(b0 + 32 * k), idesc,
-                           (seg_first && k == 0) ? 0u : 1u);
-                }
-                tc_commit(smem_u32(&bars[TC_STAGES + st]));     // stage free once these MMAs have read it
+                tc_mma(dst, da, db, idesc, seg_first ? 0u : 1u);    // K = 8 tf32 (32 bytes) each
+                tc_mma(dst, da + 2, db + 2, idesc, 1u);
+                tc_mma(dst, da + 4, db + 4, idesc, 1u);
+                tc_mma(dst, da + 6, db + 6, idesc, 1u);
+                tc_commit(empty0 + 8 * st);                      // stage free once these MMAs have read it
                 if ((s % TC_PROMOTE_STAGES) == TC_PROMOTE_STAGES - 1 || s == total - 1)
                     tc_commit(smem_u32(&acc_full[buf]));        // segment complete
             }
