@@ -257,6 +257,22 @@ def run_mixed(args, spec, dev, depth, local, fp64_solve, fp64_ms_per_iter):
                         "abs_dE_vs_fp64": abs(e - fp64_solve["e_per_cell"]),
                         "abs_dE_without_polish": abs(e0 - fp64_solve["e_per_cell"]),
                         "speedup_vs_fp64_solve": fp64_solve["seconds_est"] / secs}
+        # the same solve with the polish iterations in the Ozaki form (FP64-accurate on the
+        # BF16 tensor cores) instead of native FP64
+        from paper_1911_00242_gb300.binding import CCSD_OZAKI
+        S = Solver(spec.grid, spec.nocc, spec.nvir, dev, precision=CCSD_MIXED, diis_depth=depth, max_iter=1000,
+                   conv_tol=SOLVE_TOL, mixed_tol=1e-7, polish_iters=2, polish_precision=CCSD_OZAKI)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ok2, iters2, mr2 = S.solve()
+        torch.cuda.synchronize()
+        secs2 = time.perf_counter() - t0
+        e2 = S.energy().real
+        S.close()
+        out["solve_ozaki_polish"] = {"converged_mixed_phase": ok2, "iterations_incl_polish": iters2,
+                                     "polish_iters": 2, "max_resid": mr2, "seconds": secs2, "e_per_cell": e2,
+                                     "abs_dE_vs_fp64": abs(e2 - fp64_solve["e_per_cell"]),
+                                     "speedup_vs_fp64_solve": fp64_solve["seconds_est"] / secs2}
     return out
 
 

@@ -78,7 +78,7 @@ typedef struct {
     int    max_iter;      /* used by ccsd_solve                                 */
     double conv_tol;      /* max|R1| and max|R2| threshold, Eqs. (criterion_single,
                              criterion_double)                                   */
-    int    polish_iters;  /* CCSD_MIXED: FP64 iterations ccsd_solve runs after the
+    int    polish_iters;  /* CCSD_MIXED: polish iterations ccsd_solve runs after the
                              mixed ones (0..100)                                 */
     double mixed_tol;     /* CCSD_MIXED: ccsd_solve switches to FP64 once the mixed
                              max|R| < max(mixed_tol, conv_tol)                  */
@@ -90,6 +90,10 @@ typedef struct {
                              and the tensor-core ladder chunks cut to about a
                              third (same results, more launches)                */
     int    oz_slices;     /* CCSD_OZAKI: slices per operand, 3..8 (0 = 7)       */
+    int    polish_precision; /* CCSD_MIXED: arithmetic of the polish iterations,
+                             CCSD_FP64 (default, 0) or CCSD_OZAKI (the handle then
+                             also carries the Ozaki steps; their operands share
+                             the pooled buffers in the lean layout)             */
 } ccsd_config;
 
 typedef struct {
@@ -184,13 +188,15 @@ int ccsd_iterate(ccsd_t h, int n_iter, int* done, double* max_resid);
 /* Iterates until convergence or cfg->max_iter updates; CCSD_ERR_NOT_CONVERGED
  * when the limit is reached (the amplitudes remain readable).  For CCSD_MIXED
  * handles: mixed iterations until max|R| < max(mixed_tol, conv_tol), then up
- * to polish_iters FP64 iterations (fewer if the FP64 max|R| < conv_tol);
+ * to polish_iters polish iterations in polish_precision (fewer if their
+ * max|R| < conv_tol);
  * CCSD_OK when the mixed phase reached its tolerance. */
 int ccsd_solve(ccsd_t h, int* iterations, double* max_resid);
 
 /* Arithmetic of the following ccsd_iterate/ccsd_residual calls: CCSD_FP64 on
- * any handle, CCSD_MIXED / CCSD_OZAKI only on handles created with that
- * precision.  Clears the DIIS history. */
+ * any handle, CCSD_MIXED only on handles created with it, CCSD_OZAKI on
+ * handles created with it or with CCSD_MIXED and polish_precision =
+ * CCSD_OZAKI.  Clears the DIIS history. */
 int ccsd_set_precision(ccsd_t h, int precision);
 
 /* Correlation energy of the current amplitudes per unit cell (supercell

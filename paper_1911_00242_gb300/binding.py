@@ -31,7 +31,7 @@ class ccsd_config(ctypes.Structure):
     _fields_ = [("nk_dims", ctypes.c_int * 3), ("nocc", ctypes.c_int), ("nvir", ctypes.c_int),
                 ("precision", ctypes.c_int), ("diis_depth", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("conv_tol", ctypes.c_double), ("polish_iters", ctypes.c_int), ("mixed_tol", ctypes.c_double),
-                ("lean", ctypes.c_int), ("oz_slices", ctypes.c_int)]
+                ("lean", ctypes.c_int), ("oz_slices", ctypes.c_int), ("polish_precision", ctypes.c_int)]
 
 
 class ccsd_inputs(ctypes.Structure):
@@ -157,7 +157,7 @@ def inputs_struct(arrays, vvvv_on_host=False):
 
 
 def make_config(grid, nocc, nvir, precision=CCSD_FP64, diis_depth=0, max_iter=100, conv_tol=1e-8,
-                polish_iters=2, mixed_tol=1e-7, lean=0, oz_slices=0):
+                polish_iters=2, mixed_tol=1e-7, lean=0, oz_slices=0, polish_precision=CCSD_FP64):
     c = ccsd_config()
     c.nk_dims[0], c.nk_dims[1], c.nk_dims[2] = grid
     c.nocc, c.nvir, c.precision = nocc, nvir, precision
@@ -165,6 +165,7 @@ def make_config(grid, nocc, nvir, precision=CCSD_FP64, diis_depth=0, max_iter=10
     c.polish_iters, c.mixed_tol = polish_iters, mixed_tol
     c.lean = lean
     c.oz_slices = oz_slices
+    c.polish_precision = polish_precision
     return c
 
 

@@ -103,8 +103,9 @@ struct Step {           // one element of the launch sequence
     const char* name;
     double flops;       // algorithmic real flops per launch (complex MAC = 8)
     double bytes;       // algorithmic bytes per launch for the memory-bound steps
-    int mode = 0;       // 0 always; 1 only without tensor cores; 2 only with tensor cores (mixed
-                        // or Ozaki iterations); 3 only in mixed (FP32) iterations; 4 only outside them
+    int mode = 0;       // 0 always; 1 only without tensor cores; 2 split-TF32 tensor-core steps
+                        // (mixed iterations); 3 only in mixed iterations; 4 only outside them;
+                        // 5 Ozaki tensor-core steps (Ozaki iterations)
 };
 
 struct EmbedPlan {      // operand preparation for the tensor-core GEMM
@@ -172,7 +173,9 @@ struct ccsd_ctx {
     int red_blocks = 0;
     const char* cur_name = "";
     int fp32 = 0;                    // contractions in FP32 arithmetic (mixed form)
-    int oz_on = 0;                   // Ozaki-scheme tensor-core contractions active (CCSD_OZAKI)
+    int oz_on = 0;                   // Ozaki-scheme tensor-core contractions active this iteration
+    bool has_oz = false;             // the plan has the Ozaki steps (CCSD_OZAKI, or the mixed form's Ozaki polish)
+    bool cur_oz = false;             // plan building: the operand set being added is the Ozaki one
     int oz_slices = 7;               // slices per operand row (CCSD_OZAKI)
     long long oz_work_elems = 0;     // split partials of the Ozaki GEMMs (complex elements)
     df2* ovvv_df = nullptr;          // Ozaki form, complex128 ovvv: its double-float copy
@@ -438,13 +441,16 @@ int encode_map_bf16(CUtensorMap* m, const uint16_t* base, long long rows, int kp
     return r == CUDA_SUCCESS ? 0 : CCSD_ERR_CUDA;
 }
 
+// Step mode of a tensor-core step of the operand set being added.
+int tc_mode(const ccsd_ctx* h) { return h->cur_oz ? 5 : 2; }
+
 // A tensor-core operand: split-TF32 parts (big, small: rows x kpad floats each), or for
 // the Ozaki form BF16 slice planes (sl: planes x rows x kpad) and row scales (sc).
 struct TcBuf { float* big; float* small; long long rows; int kpad; uint16_t* sl = nullptr; float* sc = nullptr; };
 
 int tc_alloc(ccsd_ctx* h, Alloc& al, TcBuf& t, long long rows, int kpad) {
     t.rows = rows; t.kpad = kpad;
-    if (h->cfg.precision == CCSD_OZAKI) {
+    if (h->cur_oz) {
         const size_t bytes = (size_t)rows * kpad * 2 * h->oz_slices;
         t.big = t.small = nullptr;
         t.sl = (uint16_t*)al.get(bytes);
@@ -467,7 +473,7 @@ int tc_alloc(ccsd_ctx* h, Alloc& al, TcBuf& t, long long rows, int kpad) {
 int add_embed(ccsd_ctx* h, Alloc& al, int src, const TcBuf& dst, int mode, int R, int Kc,
               const std::vector<long long>& srcoff, const std::vector<int>& srow, const std::vector<int>& scol,
               bool constant, bool conj = false) {
-    if (conj && h->cfg.precision != CCSD_OZAKI) return CCSD_ERR_INVALID;
+    if (conj && !h->cur_oz) return CCSD_ERR_INVALID;
     const long long nblk = (long long)srcoff.size();
     if ((int)srow.size() != R || (int)scol.size() != Kc || 2 * Kc > dst.kpad) return CCSD_ERR_INVALID;
     const long long hi = *std::max_element(srcoff.begin(), srcoff.end()) + *std::max_element(srow.begin(), srow.end()) +
@@ -484,7 +490,7 @@ int add_embed(ccsd_ctx* h, Alloc& al, int src, const TcBuf& dst, int mode, int R
     if (al.err) return al.err;
     e.a.big = dst.big; e.a.small = dst.small;
     e.a.nblk = (int)nblk; e.a.R = R; e.a.Kc = Kc; e.a.Kpad = dst.kpad; e.a.mode = mode;
-    if (h->cfg.precision == CCSD_OZAKI) {
+    if (h->cur_oz) {
         e.oz = true;
         e.z.srcoff = e.a.srcoff; e.z.srow = e.a.srow; e.z.scol = e.a.scol;
         e.z.sl = dst.sl; e.z.sc = dst.sc; e.z.rows = dst.rows;
@@ -497,7 +503,7 @@ int add_embed(ccsd_ctx* h, Alloc& al, int src, const TcBuf& dst, int mode, int R
         h->const_embeds.push_back((int)h->embeds.size() - 1);
     } else {
         Step st{5, (int)h->embeds.size() - 1, h->cur_name, 0.0, (16.0 + (mode == 0 ? 16.0 : 32.0)) * nblk * R * Kc};
-        st.mode = 2;
+        st.mode = tc_mode(h);
         h->seq.push_back(st);
     }
     return 0;
@@ -510,7 +516,7 @@ int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M,
            const std::vector<int>& colC2 = {}, double alpha_im = 0.0, bool overwrite = false,
            const std::vector<int>& rowC = {}) {
     // output row m of batch b starts at offC[b * M + m], or (rowC given) at offC[b] + rowC[m]
-    const bool oz = h->cfg.precision == CCSD_OZAKI;
+    const bool oz = h->cur_oz;
     if (A.kpad != B.kpad || A.kpad % (oz ? OZ_BK : TC_BK)) return CCSD_ERR_INVALID;
     if (!oz && (alpha_im != 0.0 || overwrite || !rowC.empty())) return CCSD_ERR_INVALID;
     if (oz && ((long long)h->oz_slices * A.rows > INT_MAX || (long long)h->oz_slices * B.rows > INT_MAX))
@@ -589,14 +595,14 @@ int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M,
     double chunks = (double)nchunk * nbatch;
     if (!nchunk_b.empty()) { chunks = 0.0; for (int x : nchunk_b) chunks += x; }
     Step st{6, (int)h->tcs.size() - 1, h->cur_name, 8.0 * (double)M * (Nr / 2) * (A.kpad / 2) * chunks, 0.0};
-    st.mode = 2;
+    st.mode = tc_mode(h);
     h->seq.push_back(st);
     return 0;
 }
 
 void add_zero(ccsd_ctx* h, int buf) {
     Step st{7, buf, h->cur_name, 0.0, 16.0 * (double)h->bufsize[buf]};
-    st.mode = 2;
+    st.mode = tc_mode(h);
     h->seq.push_back(st);
 }
 
@@ -767,21 +773,28 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     const bool mixed = h->cfg.precision == CCSD_MIXED;
     const bool oz = h->cfg.precision == CCSD_OZAKI;
     const bool tcp = mixed || oz;  // the plan has tensor-core variants of the large contractions
-    TcBuf tc_la{}, tc_lap{}, tc_lb{}, tc_ra{}, tc_rb{}, tc_b1{}, tc_ha{}, tc_hb{}, tc_h2a{}, tc_h2b{};
+    // Tensor-core operand sets: split TF32 (mixed iterations) and/or Ozaki slices (Ozaki
+    // iterations: the Ozaki form, or the mixed form's polish).  Both sets view the same
+    // pools in the pooled layout; the two never run in the same iteration.
+    struct TcSet {
+        bool oz;
+        int KQ, kpl, kplp, kpr, kpo;
+        long long epb;                       // bytes per operand element
+        TcBuf la, lap, lb, ra, rb, b1, ha, hb, h2a, h2b;
+        long long lb_floats;                 // ladder B capacity (elements per part / slice plane)
+        long long lad_max, lad_cap, pa, pb;  // sizes in elements per part / plane
+    };
+    std::vector<TcSet> sets;
+    if (mixed) sets.push_back(TcSet{false});
+    if (h->has_oz) sets.push_back(TcSet{true});
     bool pooled = false;          // tensor-core operands share two buffers, rewritten every residual
-    long long lb_floats = 0;      // capacity (elements per part / slice plane) of the ladder's B-operand buffer
     float* pool_b = nullptr;      // the B-side pool (big part; the small part follows it)
     float* pool_a = nullptr;      // the A-side pool
-    long long pool_ae = 0, pool_be = 0, pool_ar = 0, pool_br = 0;   // pool capacity: elements, scale rows
+    long long pool_ae = 0, pool_be = 0, pool_ar = 0, pool_br = 0;   // Ozaki capacity: elements, scale rows
     float* pool_asc = nullptr;
     float* pool_bsc = nullptr;    // Ozaki pools: row scales
     const long long nlt_vv = (long long)v * (v - 1) / 2;
-    const int KQ = oz ? OZ_BK : TC_BK;      // row padding: one pipeline stage of K
-    const int kpl = (int)((2 * vv + KQ - 1) / KQ * KQ);
-    const int kplp = (int)((2 * nlt_vv + KQ - 1) / KQ * KQ);
     if (tcp) {
-        const int kpr = (int)((2 * ov + KQ - 1) / KQ * KQ);
-        const int kpo = (int)((2 * oo + KQ - 1) / KQ * KQ);
         const long long N3l = (long long)N * N * N;
         h->tc_err = (int*)al.get(sizeof(int));
         if (al.err) return al.err;
@@ -800,92 +813,112 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
             if (al.err) return al.err;
         }
         if (!al.dry && cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st) != cudaSuccess) return CCSD_ERR_CUDA;
-        if (oz && !h->in32[B_OVVV]) {
-            // the W' kernel's t1 terms run in double-float: convert the constant ovvv once
+        if (h->has_oz && !h->in32[B_OVVV]) {
+            // the Ozaki W' kernel's t1 terms run in double-float: convert the constant ovvv once
             h->ovvv_df = (df2*)al.get((size_t)h->bufsize[B_OVVV] * sizeof(df2));
             if (al.err) return al.err;
             if (!al.dry)
                 to_df2_kernel<<<ew_grid(h->bufsize[B_OVVV]), 256, 0, h->st>>>(h->ovvv_df, h->buf[B_OVVV],
                                                                              h->bufsize[B_OVVV]);
         }
-        // ladder B rows of the largest packed class (floats per part)
-        long long lad_max = 0, lad_batch = 0;    // largest class, largest single (ka, kb) batch
-        for (int diag_ab = 0; diag_ab < 2; ++diag_ab) for (int diag_ef = 0; diag_ef < 2; ++diag_ef) {
-            const long long per_block = 2 * (diag_ab ? nlt_vv : vv) * (diag_ef ? kplp : kpl);
-            long long blocks = 0;
-            for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) {
-                if ((ka == kb) != (diag_ab == 1)) continue;
-                const int S = kg.k4(ka, kb, 0);
-                long long nb = 0;
-                for (int ke = 0; ke < N; ++ke) { const int kf = kg.k4(S, 0, ke); if (diag_ef ? ke == kf : ke < kf) ++nb; }
-                blocks += nb;
-                lad_batch = std::max(lad_batch, nb * per_block);
+        long long total_bytes = 0;
+        for (TcSet& T : sets) {
+            T.KQ = T.oz ? OZ_BK : TC_BK;      // row padding: one pipeline stage of K
+            auto rnd = [&](long long x) { return (int)((x + T.KQ - 1) / T.KQ * T.KQ); };
+            T.kpl = rnd(2 * vv); T.kplp = rnd(2 * nlt_vv); T.kpr = rnd(2 * ov); T.kpo = rnd(2 * oo);
+            // bytes per operand element: split-TF32 big + small parts, or the Ozaki slice planes
+            T.epb = T.oz ? 2LL * h->oz_slices : 8LL;
+            // ladder B rows of the largest packed class
+            long long lad_max = 0, lad_batch = 0;    // largest class, largest single (ka, kb) batch
+            for (int diag_ab = 0; diag_ab < 2; ++diag_ab) for (int diag_ef = 0; diag_ef < 2; ++diag_ef) {
+                const long long per_block = 2 * (diag_ab ? nlt_vv : vv) * (diag_ef ? T.kplp : T.kpl);
+                long long blocks = 0;
+                for (int ka = 0; ka < N; ++ka) for (int kb = ka; kb < N; ++kb) {
+                    if ((ka == kb) != (diag_ab == 1)) continue;
+                    const int S = kg.k4(ka, kb, 0);
+                    long long nb = 0;
+                    for (int ke = 0; ke < N; ++ke) { const int kf = kg.k4(S, 0, ke); if (diag_ef ? ke == kf : ke < kf) ++nb; }
+                    blocks += nb;
+                    lad_batch = std::max(lad_batch, nb * per_block);
+                }
+                lad_max = std::max(lad_max, blocks * per_block);
             }
-            lad_max = std::max(lad_max, blocks * per_block);
+            T.lad_max = lad_max;
+            // 8 GB of operand (a third of the largest class in the lean layout), and never less
+            // than one batch
+            T.lad_cap = std::max(lad_batch, h->cfg.lean ? lad_max / 3 : (8LL << 30) / T.epb);
+            // operand sizes (elements per part): A side (mode 0) and B side (mode 1)
+            const long long fa[5] = {N3l * oo * T.kpl, N3l * oo * T.kplp, N3l * ov * T.kpr, N3l * oo * T.kpl,
+                                     N3l * oo * T.kpo};
+            const long long fb[4] = {N3l * 2 * ov * T.kpr, N3l * 2 * ov * T.kpr, N3l * 2 * oo * T.kpl,
+                                     N3l * 2 * vv * T.kpo};
+            long long total = std::min(lad_max, T.lad_cap);
+            T.pa = 0; T.pb = std::min(lad_max, T.lad_cap);
+            for (long long x : fa) { total += x; T.pa = std::max(T.pa, x); }
+            for (long long x : fb) { total += x; T.pb = std::max(T.pb, x); }
+            total_bytes += total * T.epb;
         }
-        // bytes per operand element: split-TF32 big + small parts, or the Ozaki slice planes
-        const long long epb = oz ? 2LL * h->oz_slices : 8LL;
-        // 8 GB of operand (a third of the largest class in the lean layout), and never less
-        // than one batch
-        const long long lad_cap = std::max(lad_batch, h->cfg.lean ? lad_max / 3 : (8LL << 30) / epb);
-        // operand sizes (floats per part): A side (mode 0) and B side (mode 1)
-        const long long fa[5] = {N3l * oo * kpl, N3l * oo * kplp, N3l * ov * kpr, N3l * oo * kpl, N3l * oo * kpo};
-        const long long fb[4] = {N3l * 2 * ov * kpr, N3l * 2 * ov * kpr, N3l * 2 * oo * kpl, N3l * 2 * vv * kpo};
-        long long total = std::min(lad_max, lad_cap);
-        for (long long x : fa) total += x;
-        for (long long x : fb) total += x;
-        pooled = h->cfg.lean || total * epb > (24LL << 30);
+        pooled = h->cfg.lean || total_bytes > (24LL << 30) * (long long)sets.size();
         if (!pooled) {
-            lb_floats = std::max(1LL, std::min(lad_max, lad_cap));
-            if ((rc = tc_alloc(h, al, tc_la, N3l * oo, kpl)) || (rc = tc_alloc(h, al, tc_lap, N3l * oo, std::max(kplp, KQ))) ||
-                (rc = tc_alloc(h, al, tc_lb, lb_floats / kpl + 1, kpl)) ||
-                (rc = tc_alloc(h, al, tc_ra, N3l * ov, kpr)) || (rc = tc_alloc(h, al, tc_rb, N3l * 2 * ov, kpr)) ||
-                (rc = tc_alloc(h, al, tc_b1, N3l * 2 * ov, kpr)) ||
-                (rc = tc_alloc(h, al, tc_ha, N3l * oo, kpl)) || (rc = tc_alloc(h, al, tc_hb, N3l * 2 * oo, kpl)) ||
-                (rc = tc_alloc(h, al, tc_h2a, N3l * oo, kpo)) || (rc = tc_alloc(h, al, tc_h2b, N3l * 2 * vv, kpo)))
-                return rc;
-            lb_floats = tc_lb.rows * kpl;
+            for (TcSet& T : sets) {
+                h->cur_oz = T.oz;
+                T.lb_floats = std::max(1LL, std::min(T.lad_max, T.lad_cap));
+                if ((rc = tc_alloc(h, al, T.la, N3l * oo, T.kpl)) ||
+                    (rc = tc_alloc(h, al, T.lap, N3l * oo, std::max(T.kplp, T.KQ))) ||
+                    (rc = tc_alloc(h, al, T.lb, T.lb_floats / T.kpl + 1, T.kpl)) ||
+                    (rc = tc_alloc(h, al, T.ra, N3l * ov, T.kpr)) || (rc = tc_alloc(h, al, T.rb, N3l * 2 * ov, T.kpr)) ||
+                    (rc = tc_alloc(h, al, T.b1, N3l * 2 * ov, T.kpr)) ||
+                    (rc = tc_alloc(h, al, T.ha, N3l * oo, T.kpl)) || (rc = tc_alloc(h, al, T.hb, N3l * 2 * oo, T.kpl)) ||
+                    (rc = tc_alloc(h, al, T.h2a, N3l * oo, T.kpo)) || (rc = tc_alloc(h, al, T.h2b, N3l * 2 * vv, T.kpo)))
+                    return rc;
+                T.lb_floats = T.lb.rows * T.kpl;
+            }
         } else {
             // Large problems: every tensor-core step embeds its operands into one of two pools
             // just before its GEMM (stream order keeps them intact while it runs).  The B
             // pool also serves the FP64 ladder's W' slab, which only FP64 iterations use.
-            long long pa = 0, pb = std::min(lad_max, lad_cap);
-            for (long long x : fa) pa = std::max(pa, x);
-            for (long long x : fb) pb = std::max(pb, x);
-            // the FP64 W' slab (16 bytes per element) shares the B pool
-            pb = std::max(pb, (h->bufsize[B_WAB] * 16 + epb - 1) / epb);
-            // the small part starts right after the big part: keep it 256-byte aligned (TMA
-            // needs 16-byte aligned bases)
-            pa = (pa + 63) / 64 * 64;
-            pb = (pb + 63) / 64 * 64;
-            float* A = (float*)al.get((size_t)(pa * epb));
-            pool_b = (float*)al.get((size_t)(pb * epb));
-            float* scA = nullptr;
-            float* scB = nullptr;
-            if (oz) {   // row scales of the largest A-side and B-side operands
-                const long long ra = N3l * std::max(oo, ov);
-                const long long rb = std::max({N3l * 2 * ov, N3l * 2 * oo, N3l * 2 * vv, pb / kpl + 1});
-                scA = (float*)al.get((size_t)ra * 4);
-                scB = (float*)al.get((size_t)rb * 4);
-                pool_ar = ra; pool_br = rb;
+            long long bytes_a = 0, bytes_b = h->bufsize[B_WAB] * 16;
+            for (TcSet& T : sets) {
+                // the small part starts right after the big part: keep it 256-byte aligned (TMA
+                // needs 16-byte aligned bases)
+                T.pa = (T.pa + 63) / 64 * 64;
+                T.pb = (T.pb + 63) / 64 * 64;
+                bytes_a = std::max(bytes_a, T.pa * T.epb);
+                bytes_b = std::max(bytes_b, T.pb * T.epb);
             }
+            pool_a = (float*)al.get((size_t)bytes_a);
+            pool_b = (float*)al.get((size_t)bytes_b);
             if (al.err) return al.err;
-            pool_a = A; pool_ae = pa; pool_be = pb; pool_asc = scA; pool_bsc = scB;
-            lb_floats = pb;
-            auto view = [oz](float* base, float* sc, long long floats, long long rows, int kpad) {
-                if (oz) {
-                    TcBuf t{nullptr, nullptr, rows, kpad, (uint16_t*)base, sc};
-                    return t;
+            for (TcSet& T : sets) {
+                // elements per part / plane the pools hold for this set
+                const long long pa = bytes_a / T.epb / 64 * 64, pb = bytes_b / T.epb / 64 * 64;
+                float* scA = nullptr;
+                float* scB = nullptr;
+                if (T.oz) {   // row scales of the largest A-side and B-side operands
+                    const long long ra = N3l * std::max(oo, ov);
+                    const long long rb = std::max({N3l * 2 * ov, N3l * 2 * oo, N3l * 2 * vv, pb / T.kpl + 1});
+                    scA = (float*)al.get((size_t)ra * 4);
+                    scB = (float*)al.get((size_t)rb * 4);
+                    if (al.err) return al.err;
+                    pool_ar = ra; pool_br = rb; pool_ae = pa; pool_be = pb; pool_asc = scA; pool_bsc = scB;
                 }
-                TcBuf t{base, base + floats, rows, kpad};
-                return t;
-            };
-            tc_la = view(A, scA, pa, N3l * oo, kpl); tc_lap = view(A, scA, pa, N3l * oo, std::max(kplp, KQ));
-            tc_ra = view(A, scA, pa, N3l * ov, kpr); tc_ha = view(A, scA, pa, N3l * oo, kpl);
-            tc_h2a = view(A, scA, pa, N3l * oo, kpo);
-            tc_rb = view(pool_b, scB, pb, N3l * 2 * ov, kpr); tc_b1 = view(pool_b, scB, pb, N3l * 2 * ov, kpr);
-            tc_hb = view(pool_b, scB, pb, N3l * 2 * oo, kpl); tc_h2b = view(pool_b, scB, pb, N3l * 2 * vv, kpo);
-            tc_lb = view(pool_b, scB, pb, pb / kpl, kpl);
+                T.lb_floats = pb;
+                const bool zo = T.oz;
+                auto view = [zo](float* base, float* sc, long long floats, long long rows, int kpad) {
+                    if (zo) {
+                        TcBuf t{nullptr, nullptr, rows, kpad, (uint16_t*)base, sc};
+                        return t;
+                    }
+                    TcBuf t{base, base + floats, rows, kpad};
+                    return t;
+                };
+                T.la = view(pool_a, scA, pa, N3l * oo, T.kpl); T.lap = view(pool_a, scA, pa, N3l * oo, std::max(T.kplp, T.KQ));
+                T.ra = view(pool_a, scA, pa, N3l * ov, T.kpr); T.ha = view(pool_a, scA, pa, N3l * oo, T.kpl);
+                T.h2a = view(pool_a, scA, pa, N3l * oo, T.kpo);
+                T.rb = view(pool_b, scB, pb, N3l * 2 * ov, T.kpr); T.b1 = view(pool_b, scB, pb, N3l * 2 * ov, T.kpr);
+                T.hb = view(pool_b, scB, pb, N3l * 2 * oo, T.kpl); T.h2b = view(pool_b, scB, pb, N3l * 2 * vv, T.kpo);
+                T.lb = view(pool_b, scB, pb, pb / T.kpl, T.kpl);
+            }
             h->buf[B_WAB] = (double2*)pool_b;
         }
     }
@@ -1155,18 +1188,19 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
             if (tcp) h->seq.back().mode = 1;
         }
     }
-    if (tcp) {
+    for (TcSet& T : sets) {
+        h->cur_oz = T.oz;
         // X on tensor cores, one batch per momentum sum S = km + kn = ki + kj:
         // rows (km, mn) of <mn||ef> (constant operand), columns (ki, ij) of tau, K = (ke, ef)
         std::vector<long long> so;
         for (int S = 0; S < N; ++S) for (int ke = 0; ke < N; ++ke) for (int km = 0; km < N; ++km)
             so.push_back(blk(S2, km, kg.k4(S, 0, km), ke));
-        if ((rc = add_embed(h, al, B_OOVV, tc_ha, 0, (int)oo, (int)vv, so, tab({{(int)oo, vv}}), tab({{(int)vv, 1}}), !pooled)))
+        if ((rc = add_embed(h, al, B_OOVV, T.ha, 0, (int)oo, (int)vv, so, tab({{(int)oo, vv}}), tab({{(int)vv, 1}}), !pooled)))
             return rc;
         so.clear();
         for (int S = 0; S < N; ++S) for (int ke = 0; ke < N; ++ke) for (int ki = 0; ki < N; ++ki)
             so.push_back(blk(S2, ki, kg.k4(S, 0, ki), ke));
-        if ((rc = add_embed(h, al, B_TAU, tc_hb, 1, (int)oo, (int)vv, so, tab({{(int)oo, vv}}), tab({{(int)vv, 1}}), false)))
+        if ((rc = add_embed(h, al, B_TAU, T.hb, 1, (int)oo, (int)vv, so, tab({{(int)oo, vv}}), tab({{(int)vv, 1}}), false)))
             return rc;
         std::vector<int> ra, rb; std::vector<long long> oc;
         for (int S = 0; S < N; ++S) {
@@ -1178,7 +1212,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                 for (int mn = 0; mn < (int)oo; ++mn)
                     oc.push_back(((long long)km * N + kg.k4(S, 0, km)) * N * Soooo + mn * oo);
         }
-        if ((rc = add_tc(h, al, tc_ha, tc_hb, B_WHH, (int)(N * oo), (int)(2 * N * oo), N, N, ra, rb, oc,
+        if ((rc = add_tc(h, al, T.ha, T.hb, B_WHH, (int)(N * oo), (int)(2 * N * oo), N, N, ra, rb, oc,
                          tab({{N, Soooo}, {(int)oo, 1}}), 0.5, 3))) return rc;
     }
     h->cur_name = "hole_hole";
@@ -1216,18 +1250,19 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
             if (tcp) h->seq.back().mode = 1;
         }
     }
-    if (tcp) {
+    for (TcSet& T : sets) {
+        h->cur_oz = T.oz;
         // R2 += 1/2 tau_mn^ab Whh_mnij on tensor cores, one batch per S = ki + kj:
         // rows (ki, ij) of Whh^T, columns (ka, ab) of tau, K = (km, mn)
         std::vector<long long> so;
         for (int S = 0; S < N; ++S) for (int km = 0; km < N; ++km) for (int ki = 0; ki < N; ++ki)
             so.push_back(blk(Soooo, km, kg.k4(S, 0, km), ki));
-        if ((rc = add_embed(h, al, B_WHH, tc_h2a, 0, (int)oo, (int)oo, so, tab({{(int)oo, 1}}), tab({{(int)oo, oo}}), false)))
+        if ((rc = add_embed(h, al, B_WHH, T.h2a, 0, (int)oo, (int)oo, so, tab({{(int)oo, 1}}), tab({{(int)oo, oo}}), false)))
             return rc;
         so.clear();
         for (int S = 0; S < N; ++S) for (int km = 0; km < N; ++km) for (int ka = 0; ka < N; ++ka)
             so.push_back(blk(S2, km, kg.k4(S, 0, km), ka));
-        if ((rc = add_embed(h, al, B_TAU, tc_h2b, 1, (int)vv, (int)oo, so, tab({{(int)vv, 1}}), tab({{(int)oo, vv}}), false)))
+        if ((rc = add_embed(h, al, B_TAU, T.h2b, 1, (int)vv, (int)oo, so, tab({{(int)vv, 1}}), tab({{(int)oo, vv}}), false)))
             return rc;
         std::vector<int> ra, rb; std::vector<long long> oc;
         for (int S = 0; S < N; ++S) {
@@ -1239,7 +1274,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                 for (int ij = 0; ij < (int)oo; ++ij)
                     oc.push_back(((long long)ki * N + kg.k4(S, 0, ki)) * N * S2 + ij * vv);
         }
-        if ((rc = add_tc(h, al, tc_h2a, tc_h2b, B_R2, (int)(N * oo), (int)(2 * N * vv), N, N, ra, rb, oc,
+        if ((rc = add_tc(h, al, T.h2a, T.h2b, B_R2, (int)(N * oo), (int)(2 * N * vv), N, N, ra, rb, oc,
                          tab({{N, S2}, {(int)vv, 1}}), 0.5, 3))) return rc;
     }
     // ladder: Wab = <ab||ef> - P(ab) t_r^b <a r||e f>, formed for slabs of momentum pairs
@@ -1347,12 +1382,13 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
             if (tcp) for (size_t i = w_first; i < h->seq.size(); ++i) h->seq[i].mode = 1;
         }
     }
-    if (tcp) {
+    for (TcSet& T : sets) {
+        h->cur_oz = T.oz;
         // Tensor-core ladder, antisymmetry-packed like the FP64 one: outputs (ka < kb | ka = kb,
         // a < b) with the mirror R2(ba) = -R2(ab), contractions over (ke < kf | ke = kf, e < f).
         // A' = tau rows [S = ki + kj][ke][ki](ij), columns the (e f) list; B' = W' formed
         // straight into its embedding for the blocks of one chunk at a time (the buffer
-        // holds lb_floats per part), each chunk followed by its GEMM.
+        // holds T.lb_floats per part), each chunk followed by its GEMM.
         std::vector<long long> so_lad;
         for (int S = 0; S < N; ++S) for (int ke = 0; ke < N; ++ke) for (int ki = 0; ki < N; ++ki)
             so_lad.push_back(blk(S2, ki, kg.k4(S, 0, ki), ke));
@@ -1362,7 +1398,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         for (int diag_ef = 0; diag_ef < 2; ++diag_ef) {
             const std::vector<int>& efl = diag_ef ? lt_vv : full_vv;
             if (efl.empty()) continue;
-            const TcBuf& A = diag_ef ? tc_lap : tc_la;
+            const TcBuf& A = diag_ef ? T.lap : T.la;
             if ((rc = add_embed(h, al, B_TAU, A, 0, (int)oo, (int)efl.size(), so_lad, tab({{(int)oo, vv}}), efl, false)))
                 return rc;
             for (int diag_ab = 0; diag_ab < 2; ++diag_ab) {
@@ -1380,7 +1416,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                     chunks.push_back(kes);
                 }
                 const long long rows_per_block = 2LL * (long long)abl.size();
-                const long long cap_rows = lb_floats / A.kpad;
+                const long long cap_rows = T.lb_floats / A.kpad;
                 size_t b0 = 0;
                 while (b0 < batches.size()) {
                     // as many (ka, kb) batches as their W' blocks fit in the buffer (at least one)
@@ -1391,9 +1427,9 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                         ++b1;
                     }
                     if (rows > cap_rows) return CCSD_ERR_INVALID;
-                    TcBuf B{tc_lb.big, tc_lb.big + lb_floats, std::max(rows, 1LL), A.kpad};
-                    if (!pooled) B.small = tc_lb.small;
-                    if (oz) { B.big = B.small = nullptr; B.sl = tc_lb.sl; B.sc = tc_lb.sc; }
+                    TcBuf B{T.lb.big, T.lb.big + T.lb_floats, std::max(rows, 1LL), A.kpad};
+                    if (!pooled) B.small = T.lb.small;
+                    if (T.oz) { B.big = B.small = nullptr; B.sl = T.lb.sl; B.sc = T.lb.sc; }
                     int nchmax = 0;
                     for (size_t bb = b0; bb < b1; ++bb) nchmax = std::max<int>(nchmax, (int)chunks[bb].size());
                     std::vector<int> blk3, ra, rb, cc, cc2, cnt;
@@ -1425,7 +1461,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                     if (al.err) return al.err;
                     wl.a.nblk = (int)(blk3.size() / 3); wl.a.nab = (int)abl.size(); wl.a.nef = (int)efl.size();
                     wl.a.N = N; wl.a.o = o; wl.a.v = v; wl.a.Kpad = A.kpad;
-                    if (oz) {
+                    if (T.oz) {
                         wl.oz = true;
                         OzWprimeArgs& z = wl.z;
                         z.sl = B.sl; z.sc = B.sc; z.rows = B.rows;
@@ -1435,7 +1471,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                     }
                     h->wlists.push_back(wl);
                     Step st{10, (int)h->wlists.size() - 1, "ladder_W", 0.0, 40.0 * (double)wl.a.nblk * wl.a.nab * wl.a.nef};
-                    st.mode = 2;
+                    st.mode = tc_mode(h);
                     h->seq.push_back(st);
                     cc.clear(); cc2.clear();
                     for (int x : abl) { cc.push_back(x); cc2.push_back((x % v) * v + x / v); }
@@ -1517,7 +1553,8 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         if ((rc = G(s))) return rc;
         if (tcp) h->seq.back().mode = 1;
     }
-    if (tcp) {
+    for (TcSet& T : sets) {
+        h->cur_oz = T.oz;
         // Both ring GEMMs on tensor cores, one batch per momentum transfer D:
         //   ring W:  rows (kj, j, b) with kb = kj - D, columns (kn, n, f) with kf = kn - D
         //   ring C:  rows (ki, i, a) with ka = ki - D, columns (kj, j, b) with kb = kj + D
@@ -1529,13 +1566,13 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         std::vector<long long> so;
         for (int D = 0; D < N; ++D) for (int kc = 0; kc < N; ++kc) for (int kf_ = 0; kf_ < N; ++kf_)
             so.push_back(blk(S2, kf_, kc, kg.k4(kf_, 0, D)));
-        if ((rc = add_embed(h, al, B_T2, tc_ra, 0, (int)ov, (int)ov, so, tab({{o, o * vv}, {v, v}}),
+        if ((rc = add_embed(h, al, B_T2, T.ra, 0, (int)ov, (int)ov, so, tab({{o, o * vv}, {v, v}}),
                             tab({{o, vv}, {v, 1}}), false))) return rc;
         // B of ring W: <n kn x kx||f kf y ky> rows (n,f), columns (x,y): [D][kx][kn], kf = kn - D
         so.clear();
         for (int D = 0; D < N; ++D) for (int kx = 0; kx < N; ++kx) for (int kn = 0; kn < N; ++kn)
             so.push_back(blk(S2, kn, kx, kg.k4(kn, 0, D)));
-        if ((rc = add_embed(h, al, B_OOVV, tc_b1, 1, (int)ov, (int)ov, so, tab({{o, o * vv}, {v, v}}),
+        if ((rc = add_embed(h, al, B_OOVV, T.b1, 1, (int)ov, (int)ov, so, tab({{o, o * vv}, {v, v}}),
                             tab({{o, vv}, {v, 1}}), !pooled))) return rc;
         std::vector<int> ra, rb, cc; std::vector<long long> oc;
         for (int D = 0; D < N; ++D) {
@@ -1551,7 +1588,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         }
         for (int kn = 0; kn < N; ++kn) for (int n = 0; n < o; ++n) for (int f = 0; f < v; ++f)
             cc.push_back((int)((long long)kn * N * S2 + n * vv + f));
-        if ((rc = add_tc(h, al, tc_ra, tc_b1, B_WRING, (int)(N * ov), (int)(2 * N * ov), N, N, ra, rb, oc, cc, 0.5, 3)))
+        if ((rc = add_tc(h, al, T.ra, T.b1, B_WRING, (int)(N * ov), (int)(2 * N * ov), N, N, ra, rb, oc, cc, 0.5, 3)))
             return rc;
     }
     h->cur_name = "ring";
@@ -1569,13 +1606,14 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         if ((rc = G(s))) return rc;
         if (tcp) h->seq.back().mode = 1;
     }
-    if (tcp) {
+    for (TcSet& T : sets) {
+        h->cur_oz = T.oz;
         add_zero(h, B_ZR);
         // B_ring[D][kn][kj]: rows (j,b), columns (n,f) of W~[kj, kn, kb], kb = kj + D
         std::vector<long long> so;
         for (int D = 0; D < N; ++D) for (int kn = 0; kn < N; ++kn) for (int kj = 0; kj < N; ++kj)
             so.push_back(blk(S2, kj, kn, kg.k4(kj, D, 0)));
-        if ((rc = add_embed(h, al, B_WRING, tc_rb, 1, (int)ov, (int)ov, so, tab({{o, o * vv}, {v, v}}),
+        if ((rc = add_embed(h, al, B_WRING, T.rb, 1, (int)ov, (int)ov, so, tab({{o, o * vv}, {v, v}}),
                             tab({{o, vv}, {v, 1}}), false))) return rc;
         std::vector<int> ra, rb, cc; std::vector<long long> oc;
         for (int D = 0; D < N; ++D) {
@@ -1591,7 +1629,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         }
         for (int kj = 0; kj < N; ++kj) for (int j = 0; j < o; ++j) for (int b = 0; b < v; ++b)
             cc.push_back((int)((long long)kj * N * S2 + j * vv + b));
-        if ((rc = add_tc(h, al, tc_ra, tc_rb, B_ZR, (int)(N * ov), (int)(2 * N * ov), N, N, ra, rb, oc, cc, 1.0, 3)))
+        if ((rc = add_tc(h, al, T.ra, T.rb, B_ZR, (int)(N * ov), (int)(2 * N * ov), N, N, ra, rb, oc, cc, 1.0, 3)))
             return rc;
     }
     h->cur_name = "ring_t1t1";
@@ -1681,6 +1719,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         h->seq.push_back(s1); h->seq.push_back(s2); h->seq.push_back(s3);
     }
     h->seq.push_back({4, 0, "antisym_R2", 0.0, 16.0 * 3.0 * h->n2});
+    h->cur_oz = true;
     if (oz && (rc = oz_convert_gemms(h, al, oz_specs, pooled, pool_a, pool_b, pool_ae, pool_be, pool_asc, pool_bsc,
                                      pool_ar, pool_br)))
         return rc;
@@ -1821,9 +1860,10 @@ bool step_active(const ccsd_ctx* h, const Step& s) {
     const bool tc = mixed_it || h->oz_on;                              // tensor-core contractions
     switch (s.mode) {
         case 1: return !tc;
-        case 2: return tc;
+        case 2: return mixed_it;
         case 3: return mixed_it;
         case 4: return !mixed_it;
+        case 5: return h->oz_on != 0;
         default: return true;
     }
 }
@@ -2174,7 +2214,9 @@ bool valid_cfg(const ccsd_config* c) {
     if (c->nocc < 1 || c->nvir < 1 || c->nocc > 256 || c->nvir > 512) return false;
     if (c->precision != CCSD_FP64 && c->precision != CCSD_MIXED && c->precision != CCSD_OZAKI) return false;
     if (c->precision == CCSD_MIXED && (c->polish_iters < 0 || c->polish_iters > 100)) return false;
-    if (c->precision == CCSD_OZAKI) {
+    if (c->polish_precision != CCSD_FP64 && !(c->precision == CCSD_MIXED && c->polish_precision == CCSD_OZAKI))
+        return false;
+    if (c->precision == CCSD_OZAKI || c->polish_precision == CCSD_OZAKI) {
         if (c->oz_slices != 0 && (c->oz_slices < 3 || c->oz_slices > OZ_MAX_SLICES)) return false;
         if (c->nvir > 96) return false;       // one W' row (v^2 complex) is staged in shared memory
     }
@@ -2332,6 +2374,7 @@ void init_ctx(ccsd_ctx* h, const ccsd_config* cfg) {
     }
     h->fp32 = cfg->precision == CCSD_MIXED ? 1 : 0;
     h->oz_on = cfg->precision == CCSD_OZAKI ? 1 : 0;
+    h->has_oz = cfg->precision == CCSD_OZAKI || (cfg->precision == CCSD_MIXED && cfg->polish_precision == CCSD_OZAKI);
     h->oz_slices = cfg->oz_slices ? cfg->oz_slices : 7;
     const long long N = h->N;
     h->n1 = N * h->o * h->v;
@@ -2576,7 +2619,7 @@ void server_loop(ccsd_server* S) {
             }
             if (r->phase == 0 && r->polish_left > 0) {    // mixed phase done: FP64 polish
                 r->phase = 1;
-                ccsd_set_precision(r->h, CCSD_FP64);
+                ccsd_set_precision(r->h, r->cfg.polish_precision == CCSD_OZAKI ? CCSD_OZAKI : CCSD_FP64);
                 r->h->cfg.conv_tol = r->cfg.conv_tol;
                 keep.push_back(r);
                 continue;
@@ -2727,6 +2770,8 @@ int oz_gemm_impl(int M, int Ncols, int K, int slices, const double* A, const dou
     h->cfg.precision = CCSD_OZAKI;
     h->oz_slices = slices;
     h->oz_on = 1;
+    h->has_oz = true;
+    h->cur_oz = true;
     Alloc al{h};
     auto fail = [&](int code) { ccsd_destroy(h); return code; };
     const long long nA = (long long)M * K, nB = (long long)Ncols * K, nC = (long long)M * Ncols;
@@ -2866,8 +2911,8 @@ int ccsd_solve(ccsd_t h, int* iterations, double* max_resid) {
     }
     h->cfg.conv_tol = tol0;
     if (mixed && done) {
-        // FP64 polish: the fixed point of the exact equations
-        ccsd_set_precision(h, CCSD_FP64);
+        // polish (FP64, or the FP64-accurate Ozaki form): the fixed point of the exact equations
+        ccsd_set_precision(h, h->cfg.polish_precision == CCSD_OZAKI ? CCSD_OZAKI : CCSD_FP64);
         int d2 = 0;
         for (int p = 0; p < h->cfg.polish_iters; ++p) {
             int rc = ccsd_iterate(h, 1, &d2, &mr);
@@ -2885,8 +2930,8 @@ int ccsd_solve(ccsd_t h, int* iterations, double* max_resid) {
 int ccsd_set_precision(ccsd_t h, int precision) {
     if (!h) return CCSD_ERR_INVALID;
     if (precision == CCSD_FP64) { h->fp32 = 0; h->oz_on = 0; }
-    else if (precision == CCSD_MIXED && h->cfg.precision == CCSD_MIXED) h->fp32 = 1;
-    else if (precision == CCSD_OZAKI && h->cfg.precision == CCSD_OZAKI) h->oz_on = 1;
+    else if (precision == CCSD_MIXED && h->cfg.precision == CCSD_MIXED) { h->fp32 = 1; h->oz_on = 0; }
+    else if (precision == CCSD_OZAKI && h->has_oz) { h->fp32 = 0; h->oz_on = 1; }
     else return CCSD_ERR_INVALID;
     h->diis_count = 0;
     h->diis_next = 0;
@@ -2972,7 +3017,8 @@ int ccsd_batch_create(int n, const ccsd_config* cfgs, const ccsd_inputs* inputs,
     if (!out || n < 1 || n > 4096 || !cfgs || !inputs) return CCSD_ERR_INVALID;
     *out = nullptr;
     for (int i = 0; i < n; ++i)
-        if (cfgs[i].precision != cfgs[0].precision || cfgs[i].diis_depth != 0 || cfgs[i].precision == CCSD_OZAKI)
+        if (cfgs[i].precision != cfgs[0].precision || cfgs[i].diis_depth != 0 || cfgs[i].precision == CCSD_OZAKI ||
+            cfgs[i].polish_precision != CCSD_FP64)
             return CCSD_ERR_INVALID;
     ccsd_batch* B = new (std::nothrow) ccsd_batch();
     if (!B) return CCSD_ERR_OOM;

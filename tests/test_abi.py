@@ -167,7 +167,8 @@ def test_ozaki_footprint_grows_with_slices(libpath):
 def test_plan_describe_marks_tensor_core_alternatives(libpath):
     """The plan listing: the FP64 form has only always-on steps; the Ozaki form keeps each
     large FP64 GEMM as a native-FP64 alternative (mode 1) beside its tensor-core steps
-    (mode 2); the mixed form's FP32-only fused steps run in mixed iterations only (mode 3)."""
+    (mode 5); the mixed form's FP32-only fused steps run in mixed iterations only (mode 3),
+    its tensor-core steps in mode 2, and with an Ozaki polish it carries both sets."""
     from paper_1911_00242_gb300 import binding
     binding.load(libpath)
     fp64 = binding.plan_describe((2, 2, 1), 4, 12)
@@ -175,10 +176,36 @@ def test_plan_describe_marks_tensor_core_alternatives(libpath):
     oz = binding.plan_describe((2, 2, 1), 4, 12, precision=binding.CCSD_OZAKI)
     names_tc = {n for (n, k, m, _) in oz if k == 6}
     assert {"ladder", "ring", "ring_W_t2", "hole_hole", "hole_hole_W"} <= names_tc
-    assert all(m == 2 for (_, k, m, _) in oz if k in (5, 6, 10))
+    assert all(m == 5 for (_, k, m, _) in oz if k in (5, 6, 10))
     assert not any(k in (9, 11, 12) for (_, k, _, _) in oz)            # no FP32-only steps
     mixed = binding.plan_describe((2, 2, 1), 4, 12, precision=binding.CCSD_MIXED)
     assert all(m == 3 for (_, k, m, _) in mixed if k in (9, 11, 12))
     # the ladder's FP64 W' slabs and FP64 contractions are alternatives in both tensor-core forms
     for plan in (oz, mixed):
         assert any(n == "ladder" and k == 0 and m == 1 for (n, k, m, _) in plan)
+
+    both = binding.plan_describe((2, 2, 1), 4, 12, precision=binding.CCSD_MIXED,
+                                 polish_precision=binding.CCSD_OZAKI)
+    tc2 = [n for (n, k, m, _) in both if k == 6 and m == 2]
+    tc5 = [n for (n, k, m, _) in both if k == 6 and m == 5]
+    assert sorted(tc2) == sorted(n for (n, k, m, _) in mixed if k == 6)
+    assert sorted(tc5) == sorted(n for (n, k, m, _) in oz if k == 6)
+
+
+@pytest.mark.parametrize("lean", [0, 1])
+@pytest.mark.parametrize("grid,o,v", [((1, 1, 1), 3, 5), ((2, 1, 1), 2, 3), ((3, 2, 1), 5, 7),
+                                      ((2, 2, 2), 8, 32), ((3, 3, 3), 8, 24), ((3, 1, 1), 2, 1)])
+def test_mixed_with_ozaki_polish_plan_in_bounds(libpath, grid, o, v, lean):
+    """A mixed handle with an Ozaki polish: both operand sets (split TF32 and BF16 slices),
+    dedicated or viewing the same pools, pass the host-side bounds checks."""
+    from paper_1911_00242_gb300 import binding
+    lib = binding.load(libpath)
+    cfg = binding.make_config(grid, o, v, precision=binding.CCSD_MIXED, lean=lean,
+                              polish_precision=binding.CCSD_OZAKI)
+    n = ctypes.c_longlong(0)
+    tb = ctypes.c_size_t(0)
+    assert lib.ccsd_plan_check(ctypes.byref(cfg), ctypes.byref(n), ctypes.byref(tb)) == 0
+    # polish precision other than FP64 / Ozaki, or Ozaki polish on the FP64 form: refused
+    for prec, pol in ((binding.CCSD_FP64, binding.CCSD_OZAKI), (binding.CCSD_MIXED, binding.CCSD_MIXED)):
+        bad = binding.make_config(grid, o, v, precision=prec, polish_precision=pol)
+        assert lib.ccsd_plan_check(ctypes.byref(bad), ctypes.byref(n), ctypes.byref(tb)) != 0

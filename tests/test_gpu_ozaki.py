@@ -216,3 +216,43 @@ def test_ozaki_host_vvvv(lib):
                 out.append((r1.cpu().numpy(), r2.cpu().numpy()))
                 S.close()
             assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("lean", [0, 1])
+def test_mixed_with_ozaki_polish(lib, lean):
+    """A mixed handle that carries the Ozaki steps: residuals of its three arithmetics on one
+    handle (mixed, Ozaki, native FP64) against the oracle, then a DIIS(6) chain solve whose
+    polish iterations run in the Ozaki form: |dE| < 1e-8 Ha and max|dt| < 1e-7 against the
+    oracle's fixed point, the FP64 form's tolerances."""
+    from paper_1911_00242_gb300.binding import CCSD_FP64, CCSD_MIXED, CCSD_OZAKI, Solver
+    spec = cs.SynthSpec((2, 2, 1), 3, 6, 609, time_reversal=False)
+    inp = cs.generate(spec)
+    P = ccsd_k.Problem(spec.grid, spec.nocc, spec.nvir, inp)
+    t1, t2 = cs.random_amplitudes(spec, 64)
+    R1, R2 = ccsd_k.residual(P, t1, t2)
+    scale = max(abs(R1).max(), abs(R2).max())
+    S = Solver(spec.grid, spec.nocc, spec.nvir, {k: dev(v) for k, v in inp.items()}, precision=CCSD_MIXED,
+               polish_precision=CCSD_OZAKI, lean=lean)
+    d1, d2 = dev(t1), dev(t2)
+    r1, r2 = torch.empty_like(d1), torch.empty_like(d2)
+    for prec, tol in ((CCSD_MIXED, 1e-5), (CCSD_OZAKI, 1e-11), (CCSD_FP64, 1e-13), (CCSD_MIXED, 1e-5)):
+        S.set_precision(prec)
+        S.residual(d1, d2, r1, r2)
+        torch.cuda.synchronize()
+        e = max(abs(r1.cpu().numpy() - R1).max(), abs(r2.cpu().numpy() - R2).max()) / scale
+        assert e < tol, (prec, e)
+    S.close()
+    spec = cs.spec_for("chain_k4_o4_v8")
+    inp = cs.generate(spec)
+    P = ccsd_k.Problem(spec.grid, spec.nocc, spec.nvir, inp)
+    ref = driver.solve(P, tol=1e-10, max_iter=100, diis_depth=6)
+    S = Solver(spec.grid, spec.nocc, spec.nvir, {k: dev(v) for k, v in inp.items()}, precision=CCSD_MIXED,
+               polish_precision=CCSD_OZAKI, diis_depth=6, conv_tol=1e-9, mixed_tol=1e-7, polish_iters=6,
+               max_iter=100, lean=lean)
+    ok, iters, mr = S.solve()
+    assert ok and mr < 1e-9
+    assert abs(S.energy().real - ref["energies"][-1].real / spec.nk) < 1e-8
+    t1g = torch.empty((spec.nk, spec.nocc, spec.nvir), dtype=torch.complex128, device="cuda")
+    t2g = torch.empty((spec.nk,) * 3 + (spec.nocc,) * 2 + (spec.nvir,) * 2, dtype=torch.complex128, device="cuda")
+    S.get_amplitudes(t1g, t2g)
+    assert abs(t2g.cpu().numpy() - ref["t2"]).max() < 1e-7
