@@ -10,10 +10,12 @@
 //   B'[2n][2k + r] = (Re b_nk, -Im b_nk),  B'[2n+1][2k + r] = (Im b_nk, Re b_nk).
 //
 // Splitting (per operand row).  Row i of an embedded operand gets a power-of-two
-// scale 2^E_i > max_k |x_ik| and s slices of 7 bits:
-//   y_0 = x 2^-E_i in (-1, 1),   v_p = rint(2^7 y_p),   y_{p+1} = 2^7 y_p - v_p
-//   x = 2^E_i sum_{p<s} v_p 2^{-7(p+1)} + e,   |e| <= 2^{E_i - 7s - 1}
-// |v_0| <= 128 and |v_p| <= 64 for p > 0: integers that BF16 holds exactly.
+// scale 2^E_i > max_k |x_ik| and s slices of 7 bits: the fixed point
+// Y = rint(x 2^{7s - E_i}) (|Y| <= 2^{7s}) is written in balanced base-128 digits,
+// v_{s-1} .. v_1 in [-64, 63] from the least significant and the remaining top
+// digit v_0 (|v_0| <= 128), so that
+//   x = 2^E_i sum_{p<s} v_p 2^{-7(p+1)} + e,   |e| <= 2^{E_i - 7s - 1},
+// with integers that BF16 holds exactly.
 //
 // Products.  With row scales 2^Ea (A') and 2^Eb (B'),
 //   (A' B'^T)_mn = 2^{Ea_m + Eb_n} sum_{p,q} 2^{-7(p+q+2)} (V_p W_q^T)_mn.
@@ -35,7 +37,9 @@
 // B'), warp 1 / lane 0 issues 4 MMAs (kind::f16, BF16 inputs, K = 16) per stage
 // into TMEM buffer (window & 1), warps 2..17 promote windows and run the epilogue
 // (32 columns of one TMEM lane quarter each; hi and lo live in TMEM as well, so a
-// thread holds only 8 columns at a time).
+// thread holds only 8 columns at a time).  A launch with too few tiles for the SMs
+// splits each tile's (chunk, diagonal) units over several CTAs, whose partials
+// oz_split_reduce adds in a fixed order.
 // Every mbarrier wait is bounded, as in the split-TF32 kernel.
 #pragma once
 #include "tcgemm.cuh"
