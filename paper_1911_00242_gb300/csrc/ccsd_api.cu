@@ -1459,6 +1459,18 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                     wl.a.abl = upload(al, abl, h->st);
                     wl.a.efl = upload(al, efl, h->st);
                     if (al.err) return al.err;
+                    {   // groups of consecutive pairs with the same a (the list is ordered by a)
+                        std::vector<int> grp;
+                        for (int x = 0; x < (int)abl.size();) {
+                            int y = x + 1;
+                            while (y < (int)abl.size() && y - x < WP_GROUP && abl[y] / v == abl[x] / v) ++y;
+                            grp.push_back(x); grp.push_back(y - x);
+                            x = y;
+                        }
+                        wl.a.grp = upload(al, grp, h->st);
+                        if (al.err) return al.err;
+                        wl.a.ngrp = (int)(grp.size() / 2);
+                    }
                     wl.a.nblk = (int)(blk3.size() / 3); wl.a.nab = (int)abl.size(); wl.a.nef = (int)efl.size();
                     wl.a.N = N; wl.a.o = o; wl.a.v = v; wl.a.Kpad = A.kpad;
                     if (T.oz) {
@@ -1931,7 +1943,7 @@ void launch_step(ccsd_ctx* h, size_t si) {
                 WprimeListArgs a = h->wlists[s.idx].a;
                 a.vvvv = h->shadow[B_VVVV];
                 a.ovvv = h->shadow[B_OVVV]; a.t1 = h->shadow[B_T1];
-                wprime_list_kernel<<<row_grid((long long)a.nblk * a.nab), 256, 0, h->st>>>(a);
+                wprime_list_kernel<<<row_grid((long long)a.nblk * a.ngrp), 256, 0, h->st>>>(a);
                 ++h->launches;
                 break;
             }

@@ -488,63 +488,81 @@ struct WprimeListArgs {
     const float2* vvvv; const float2* ovvv; const float2* t1;
     float* big; float* small;
     const int* blk; const int* abl; const int* efl;
-    int nblk, nab, nef, N, o, v, Kpad;
+    const int* grp;           // [ngrp][2]: first index into abl and count (<= WP_GROUP) of rows sharing a
+    int nblk, nab, nef, N, o, v, Kpad, ngrp;
 };
 
-// One CTA per output row pair (block bi, pair ai): t1 and the ovvv rows it needs are
-// fixed for the CTA, its threads sweep the (e, f) list.
+constexpr int WP_GROUP = 4;   // rows (pairs a b with one a) that share the ovvv row of a
+
+// One CTA per group of up to WP_GROUP output row pairs of one block bi whose pairs (a, b)
+// share a: the ovvv row of a and t_r^a are loaded once for the group, and its threads
+// sweep the (e, f) list.
 __global__ void wprime_list_kernel(const WprimeListArgs w)
 {
     const int N = w.N, o = w.o, v = w.v;
     const long long vv = (long long)v * v, v4 = vv * vv, ov3 = (long long)o * v * vv;
     const int kh = w.Kpad / 2;                       // column pairs, padding included
-    const long long rows = (long long)w.nblk * w.nab;
-    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-        const long long bi = row / w.nab;
-        const int ai = (int)(row - bi * w.nab);
+    const long long units = (long long)w.nblk * w.ngrp;
+    for (long long unit = blockIdx.x; unit < units; unit += gridDim.x) {
+        const long long bi = unit / w.ngrp;
+        const int gi = (int)(unit - bi * w.ngrp);
+        const int a0i = w.grp[2 * gi], cnt = w.grp[2 * gi + 1];
         const int ka = w.blk[3 * bi], kb = w.blk[3 * bi + 1], ke = w.blk[3 * bi + 2];
-        const int ab = w.abl[ai];
-        const int a = ab / v, b = ab % v;
+        const int a = w.abl[a0i] / v;
         const long long blk_ab = ((long long)ka * N + kb) * N + ke;
         const long long blk_ba = ((long long)kb * N + ka) * N + ke;
-        const float2* g0 = w.vvvv + blk_ab * v4 + (long long)ab * vv;
         const float2* pa = w.ovvv + blk_ba * ov3 + (long long)a * vv;     // + r v vv: ovvv[kb,ka,ke](r,a,.)
-        const float2* pb = w.ovvv + blk_ab * ov3 + (long long)b * vv;     // ovvv[ka,kb,ke](r,b,.)
-        const float2* tb = w.t1 + (long long)kb * o * v + b;              // + r v: t_r^b(kb)
         const float2* ta = w.t1 + (long long)ka * o * v + a;              // t_r^a(ka)
-        const long long o0row = (bi * 2 * w.nab + 2LL * ai) * (long long)w.Kpad;
+        int bs[WP_GROUP];
+#pragma unroll
+        for (int g = 0; g < WP_GROUP; ++g) bs[g] = g < cnt ? w.abl[a0i + g] - a * v : 0;
         for (int ei = threadIdx.x; ei < kh; ei += blockDim.x) {
-            const long long o0 = o0row + 2LL * ei;
-            const long long o1 = o0 + w.Kpad;
             if (ei >= w.nef) {                       // padding columns
-                *(float2*)(w.big + o0) = make_float2(0.f, 0.f);
-                *(float2*)(w.big + o1) = make_float2(0.f, 0.f);
-                *(float2*)(w.small + o0) = make_float2(0.f, 0.f);
-                *(float2*)(w.small + o1) = make_float2(0.f, 0.f);
+                for (int g = 0; g < cnt; ++g) {
+                    const long long o0 = (bi * 2 * w.nab + 2LL * (a0i + g)) * (long long)w.Kpad + 2LL * ei;
+                    const long long o1 = o0 + w.Kpad;
+                    *(float2*)(w.big + o0) = make_float2(0.f, 0.f);
+                    *(float2*)(w.big + o1) = make_float2(0.f, 0.f);
+                    *(float2*)(w.small + o0) = make_float2(0.f, 0.f);
+                    *(float2*)(w.small + o1) = make_float2(0.f, 0.f);
+                }
                 continue;
             }
             const int ef = w.efl[ei];
-            const float2 g = g0[ef];
-            float sr = 0.f, si = 0.f;
-#pragma unroll 4
+            float sr[WP_GROUP], si[WP_GROUP];
+#pragma unroll
+            for (int g = 0; g < WP_GROUP; ++g) { sr[g] = 0.f; si[g] = 0.f; }
+#pragma unroll 2
             for (int r = 0; r < o; ++r) {
                 // + t_r^b(kb) ovvv[kb,ka,ke](r,a,e,f) - t_r^a(ka) ovvv[ka,kb,ke](r,b,e,f)
-                const float2 tbr = tb[r * v];
                 const float2 p = pa[(long long)r * v * vv + ef];
-                sr = fmaf(tbr.x, p.x, fmaf(-tbr.y, p.y, sr));
-                si = fmaf(tbr.x, p.y, fmaf(tbr.y, p.x, si));
                 const float2 tar = ta[r * v];
-                const float2 q = pb[(long long)r * v * vv + ef];
-                sr = fmaf(-tar.x, q.x, fmaf(tar.y, q.y, sr));
-                si = fmaf(-tar.x, q.y, fmaf(-tar.y, q.x, si));
+#pragma unroll
+                for (int g = 0; g < WP_GROUP; ++g) {
+                    if (g >= cnt) break;
+                    const float2 tbr = w.t1[(long long)kb * o * v + (long long)r * v + bs[g]];
+                    const float2 q = w.ovvv[blk_ab * ov3 + (long long)bs[g] * vv + (long long)r * v * vv + ef];
+                    sr[g] = fmaf(tbr.x, p.x, fmaf(-tbr.y, p.y, sr[g]));
+                    si[g] = fmaf(tbr.x, p.y, fmaf(tbr.y, p.x, si[g]));
+                    sr[g] = fmaf(-tar.x, q.x, fmaf(tar.y, q.y, sr[g]));
+                    si[g] = fmaf(-tar.x, q.y, fmaf(-tar.y, q.x, si[g]));
+                }
             }
-            float rb, rs, ib, is;
-            split_tf32f(g.x + sr, rb, rs);
-            split_tf32f(g.y + si, ib, is);
-            *(float2*)(w.big + o0) = make_float2(rb, -ib);
-            *(float2*)(w.big + o1) = make_float2(ib, rb);
-            *(float2*)(w.small + o0) = make_float2(rs, -is);
-            *(float2*)(w.small + o1) = make_float2(is, rs);
+#pragma unroll
+            for (int g = 0; g < WP_GROUP; ++g) {
+                if (g >= cnt) break;
+                const int ab = a * v + bs[g];
+                const float2 gv = w.vvvv[blk_ab * v4 + (long long)ab * vv + ef];
+                float rb, rs, ib, is;
+                split_tf32f(gv.x + sr[g], rb, rs);
+                split_tf32f(gv.y + si[g], ib, is);
+                const long long o0 = (bi * 2 * w.nab + 2LL * (a0i + g)) * (long long)w.Kpad + 2LL * ei;
+                const long long o1 = o0 + w.Kpad;
+                *(float2*)(w.big + o0) = make_float2(rb, -ib);
+                *(float2*)(w.big + o1) = make_float2(ib, rb);
+                *(float2*)(w.small + o0) = make_float2(rs, -is);
+                *(float2*)(w.small + o1) = make_float2(is, rs);
+            }
         }
     }
 }
