@@ -59,7 +59,9 @@ extern "C" {
                            in double-float), everything else in FP64 (DFMA).
                            Relative error of a contraction about
                            2^-(7 oz_slices) of sum |a||b| (7 slices: FP64-like);
-                           operand rows must lie within about 1e-36 .. 1e36.  */
+                           operand rows must lie within about 1e-36 .. 1e36;
+                           nvir <= 96 (one W' row is staged in shared memory);
+                           the other GEMMs run in double-float (about 48 bits)  */
 
 #define CCSD_C128   0   /* integral blocks complex128                          */
 #define CCSD_C64    1   /* integral blocks complex64 (Fock blocks stay complex128):
