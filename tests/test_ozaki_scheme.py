@@ -1,0 +1,359 @@
+"""The Ozaki form's arithmetic, modelled exactly on the CPU (no GPU, no library).
+
+The Ozaki form (`csrc/ozaki.cuh`) forms FP64-accurate products on the BF16 tensor
+cores (Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59 (2012) 95-118):
+
+* every operand row gets a power-of-two scale 2^E > max|x| and is cut into s balanced
+  base-128 digits (BF16 integers);
+* the slice pairs (p, q) with p + q <= s - 1 are multiplied, and the products of one
+  diagonal d = p + q of one momentum chunk are summed in an FP32 TMEM window of at
+  most oz_win(d) stages of 64;
+* each window is scaled by its power of two and added into a float pair (hi, lo) with
+  TwoSum (Knuth); the FP64 epilogue multiplies hi + lo by the reference scales RA RB.
+
+This module restates those steps in integer and rational arithmetic, with the
+kernel's constants read from the header, and checks what the form's accuracy rests
+on:
+
+1. the digits are in range, are exact in BF16, and reconstruct x within 2^{E-7s-1};
+2. every partial sum of a window is an integer of magnitude <= 2^24 (so the tensor
+   core's FP32 accumulation is exact), and one more stage would break that;
+3. the truncated pair sum is within the bound derived below of the exact product;
+4. the schedule of units, stages and windows forms every kept pair exactly once, and
+   the split of a tile's units over CTAs is a partition;
+5. the float-pair accumulation loses no more than its lo roundings.
+
+Error bound (per product a b, row scales 2^Ea, 2^Eb).  With a^ the split value,
+|a - a^| <= 2^{Ea-7s-1} and |a| < 2^Ea, so |ab - a^b^| <= 2^{Ea+Eb-7s}(1 + 2^{-7s-2}).
+The dropped pairs have p + q = d >= s, hence p, q >= 1 and |v_p w_q| <= 2^12; there are
+2s - 1 - d of them on diagonal d, each weighted 2^{-7(d+2)}.  Their sum is at most
+2^{Ea+Eb-7s} c_s / 4 with c_s = sum_{j=0}^{s-2} (s-1-j) 2^{-7j}.  The bound per product
+is therefore 2^{Ea+Eb-7s} (1 + 2^{-7s-2} + c_s / 4).
+"""
+import os
+import re
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "paper_1911_00242_gb300", "csrc", "ozaki.cuh")
+
+
+def _kernel_constants():
+    src = open(HEADER).read()
+
+    def const(name):
+        m = re.search(r"constexpr int %s = (-?\d+);" % name, src)
+        assert m, name
+        return int(m.group(1))
+
+    m = re.search(r"oz_win\(int d\)\s*\{\s*return d == 0 \? (\d+) : (\d+);\s*\}", src)
+    assert m, "oz_win"
+    return {
+        "BK": const("OZ_BK"),
+        "BITS": const("OZ_SLICE_BITS"),
+        "MAX_SLICES": const("OZ_MAX_SLICES"),
+        "EXP_MIN": const("OZ_EXP_MIN"),
+        "EXP_MAX": const("OZ_EXP_MAX"),
+        "WIN0": int(m.group(1)),
+        "WIN": int(m.group(2)),
+    }
+
+
+K = _kernel_constants()
+BITS = K["BITS"]
+BASE = 1 << BITS
+HALF = BASE >> 1
+
+
+def oz_win(d):
+    return K["WIN0"] if d == 0 else K["WIN"]
+
+
+# ---------------------------------------------------------------- the split
+def row_exponent(values):
+    """E with 2^E > max|x| (the exponent of the largest magnitude plus one), clamped."""
+    m = float(np.max(np.abs(values))) if len(values) else 0.0
+    if m == 0.0:
+        return 0
+    return max(K["EXP_MIN"], min(K["EXP_MAX"], int(np.frexp(m)[1])))
+
+
+def split(x, s, E):
+    """Balanced base-128 digits v_0 .. v_{s-1} of Y = rint(x 2^{7s-E}), least significant first."""
+    Y = int(np.rint(np.ldexp(x, BITS * s - E)))
+    v = [0] * s
+    for p in range(s - 1, 0, -1):
+        dg = ((Y + HALF) & (BASE - 1)) - HALF
+        Y = (Y - dg) >> BITS
+        v[p] = dg
+    v[0] = Y
+    return v
+
+
+def split_value(v, E):
+    return sum(Fraction(vp) * Fraction(2) ** (E - BITS * (p + 1)) for p, vp in enumerate(v))
+
+
+def c_s(s):
+    return sum(Fraction(s - 1 - j) / Fraction(BASE) ** j for j in range(s - 1))
+
+
+def product_bound(Ea, Eb, s):
+    return Fraction(2) ** (Ea + Eb - BITS * s) * (1 + Fraction(1, 2 ** (BITS * s + 2)) + c_s(s) / 4)
+
+
+def rows(rng, n, k, lo_exp, hi_exp):
+    """Rows whose magnitudes span 10^lo_exp .. 10^hi_exp, with a few exact powers of two."""
+    x = rng.standard_normal((n, k)) * 10.0 ** rng.uniform(lo_exp, hi_exp, (n, 1))
+    x[0, : k // 2] = np.ldexp(1.0, int(rng.integers(-40, 40)))
+    return x
+
+
+@pytest.mark.parametrize("s", [3, 5, 7, 8])
+def test_split_digits_range_bf16_and_reconstruction(s):
+    rng = np.random.default_rng(100 + s)
+    X = rows(rng, 12, 40, -30, 30)
+    for r in X:
+        E = row_exponent(r)
+        for x in r:
+            v = split(x, s, E)
+            assert all(-HALF <= d < HALF for d in v[1:])
+            assert abs(v[0]) <= BASE
+            # an integer of at most 8 significant bits: its FP32 pattern has a zero low half (BF16-exact)
+            assert all(int(np.float32(d).view(np.uint32)) & 0xFFFF == 0 for d in v)
+            assert abs(Fraction(x) - split_value(v, E)) <= Fraction(2) ** (E - BITS * s - 1)
+
+
+def test_split_top_digit_reaches_its_bound():
+    """|v_0| = 128 occurs (x just below 2^E), so the window bound must allow it."""
+    for s in (3, 5, 7):
+        E = 3
+        x = np.nextafter(np.ldexp(1.0, E), 0.0)
+        v = split(x, s, E)
+        assert v[0] == BASE and all(d == 0 for d in v[1:])
+        v = split(-x, s, E)
+        assert v[0] == -BASE and all(d == 0 for d in v[1:])
+
+
+def test_split_zero_and_clamped_rows():
+    assert row_exponent(np.zeros(4)) == 0
+    assert split(0.0, 7, 0) == [0] * 7
+    assert row_exponent(np.array([1e-300])) == K["EXP_MIN"]
+    assert row_exponent(np.array([1e300])) == K["EXP_MAX"]
+
+
+# ---------------------------------------------------------------- exact windows
+def test_window_sizes_keep_fp32_exact_and_are_maximal():
+    lim = 1 << 24
+    top, low = BASE, HALF
+    # d = 0: both digits are top digits
+    assert oz_win(0) * K["BK"] * top * top <= lim
+    assert (oz_win(0) + 1) * K["BK"] * top * top > lim
+    # d > 0: every pair holds at least one low digit
+    assert oz_win(1) * K["BK"] * top * low <= lim
+    assert (oz_win(1) + 1) * K["BK"] * top * low > lim
+
+
+@pytest.mark.parametrize("d", [0, 1])
+def test_worst_case_window_sums_exactly_in_fp32(d):
+    """A full window of the largest digits sums to exactly 2^24; every FP32 prefix is exact."""
+    n = oz_win(d) * K["BK"]
+    prod = BASE * BASE if d == 0 else BASE * HALF
+    terms = np.full(n, prod, dtype=np.int64)
+    acc = np.float32(0.0)
+    for t in terms:
+        acc = np.float32(acc + np.float32(t))
+    assert int(acc) == int(terms.sum()) == 1 << 24
+
+
+def test_random_window_prefixes_exact_in_fp32():
+    rng = np.random.default_rng(6)
+    for d in (0, 1, 3):
+        n = oz_win(d) * K["BK"]
+        a = rng.integers(-BASE, BASE + 1, n) if d == 0 else rng.integers(-HALF, HALF, n)
+        b = rng.integers(-BASE, BASE + 1, n)
+        t = a * b
+        exact = np.cumsum(t)
+        assert np.max(np.abs(exact)) <= 1 << 24
+        acc = np.float32(0.0)
+        for i in range(n):
+            acc = np.float32(acc + np.float32(t[i]))
+            assert int(acc) == exact[i]
+
+
+# ---------------------------------------------------------------- truncated products
+def pair_sum(va, vb, Ea, Eb, s, dmax):
+    """2^{Ea+Eb} sum_{p+q<=dmax} v_p w_q 2^{-7(p+q+2)}, exactly."""
+    tot = Fraction(0)
+    for p in range(s):
+        for q in range(s):
+            if p + q <= dmax:
+                tot += Fraction(va[p] * vb[q]) * Fraction(2) ** (Ea + Eb - BITS * (p + q + 2))
+    return tot
+
+
+@pytest.mark.parametrize("s", [3, 5, 7, 8])
+def test_truncated_dot_within_bound(s):
+    rng = np.random.default_rng(200 + s)
+    A = rows(rng, 4, 48, -8, 8)
+    B = rows(rng, 4, 48, -8, 8)
+    for a in A:
+        Ea = row_exponent(a)
+        sa = [split(x, s, Ea) for x in a]
+        for b in B:
+            Eb = row_exponent(b)
+            sb = [split(x, s, Eb) for x in b]
+            exact = sum(Fraction(x) * Fraction(y) for x, y in zip(a, b))
+            got = sum(pair_sum(u, w, Ea, Eb, s, s - 1) for u, w in zip(sa, sb))
+            assert abs(got - exact) <= len(a) * product_bound(Ea, Eb, s)
+
+
+def test_dropping_the_last_kept_diagonal_breaks_the_bound():
+    """The bound discriminates: forming only p + q <= s - 2 exceeds it.  Equal entries
+    with large digits (v_0 = 100, v_p = 60) make every product's error the same sign."""
+    s, E = 5, 2
+    x = float(split_value([100] + [60] * (s - 1), E))
+    a = np.full(48, x)
+    Ea = row_exponent(a)
+    assert Ea == E and split(x, s, E) == [100] + [60] * (s - 1)
+    v = split(x, s, E)
+    exact = len(a) * Fraction(x) ** 2
+    bound = len(a) * product_bound(E, E, s)
+    assert abs(len(a) * pair_sum(v, v, E, E, s, s - 1) - exact) <= bound
+    assert abs(len(a) * pair_sum(v, v, E, E, s, s - 2) - exact) > bound
+
+
+# ---------------------------------------------------------------- the kernel's schedule
+def unit_range(nch, S, kstages, nsplit, split_idx):
+    """The units [u0, u1) of one CTA when a tile's units are split over nsplit CTAs by stage count."""
+    nunits = nch * S
+    if nsplit <= 1:
+        return 0, nunits
+    per_chunk = S * (S + 1) // 2 * kstages
+    total = per_chunk * nch
+    lo, hi = total * split_idx // nsplit, total * (split_idx + 1) // nsplit
+    u0 = u1 = nunits
+    for u in range(nunits):
+        c, d = divmod(u, S)
+        start = c * per_chunk + d * (d + 1) // 2 * kstages
+        if start >= lo and u0 == nunits:
+            u0 = u
+        if start >= hi:
+            u1 = u
+            break
+    return u0, max(u0, u1)
+
+
+@pytest.mark.parametrize("nch,S,kstages", [(1, 7, 1), (1, 7, 4), (3, 7, 8), (2, 3, 2), (5, 8, 3), (1, 1, 1)])
+def test_unit_split_is_a_partition(nch, S, kstages):
+    nunits = nch * S
+    for nsplit in range(1, 17):
+        covered = []
+        prev = 0
+        for sp in range(nsplit):
+            u0, u1 = unit_range(nch, S, kstages, nsplit, sp)
+            assert u0 == prev and u0 <= u1 <= nunits
+            covered.extend(range(u0, u1))
+            prev = u1
+        assert covered == list(range(nunits))
+
+
+def schedule(nch, S, kstages):
+    """The MMA issuer's windows: lists of (chunk, p, q, kst) stages, per unit in order."""
+    wins = []
+    for u in range(nch * S):
+        c, d = divmod(u, S)
+        stages = [(c, p, d - p, kst) for p in range(d + 1) for kst in range(kstages)]
+        w = oz_win(d)
+        wins.extend(stages[i:i + w] for i in range(0, len(stages), w))
+    return wins
+
+
+@pytest.mark.parametrize("nch,S,kstages", [(1, 7, 40), (2, 7, 9), (3, 3, 17), (1, 8, 33)])
+def test_schedule_forms_each_kept_pair_once(nch, S, kstages):
+    wins = schedule(nch, S, kstages)
+    seen = [st for w in wins for st in w]
+    want = [(c, p, q, k) for c in range(nch) for p in range(S) for q in range(S) if p + q <= S - 1
+            for k in range(kstages)]
+    assert sorted(seen) == sorted(want) and len(seen) == len(set(seen))
+    for w in wins:
+        c, p, q, _ = w[0]
+        assert 0 < len(w) <= oz_win(p + q)
+        assert all(st[0] == c and st[1] + st[2] == p + q for st in w)
+
+
+def model_gemm(Ach, Bch, s):
+    """The kernel's arithmetic for one output element per (m, n): chunks of A' and B' rows
+    (lists of 1-D arrays of length kstages * 64), exact windows, FP32 window factors
+    relative to RA, RB, and the (hi, lo) TwoSum accumulation.  Returns, per (m, n),
+    (hi, lo, RA, RB, exact sum of the scaled windows, sum of |lo| after each add)."""
+    nch = len(Ach)
+    kst = len(Ach[0][0]) // K["BK"]
+    M, N = len(Ach[0]), len(Bch[0])
+    Ea = [[row_exponent(Ach[c][m]) for m in range(M)] for c in range(nch)]
+    Eb = [[row_exponent(Bch[c][n]) for n in range(N)] for c in range(nch)]
+    V = [[np.array([[split(x, s, Ea[c][m])[p] for x in Ach[c][m]] for m in range(M)], dtype=np.int64)
+          for p in range(s)] for c in range(nch)]
+    W = [[np.array([[split(x, s, Eb[c][n])[q] for x in Bch[c][n]] for n in range(N)], dtype=np.int64)
+          for q in range(s)] for c in range(nch)]
+    out = {}
+    for m in range(M):
+        RA = max(2.0 ** Ea[c][m] for c in range(nch))
+        for n in range(N):
+            RB = max(2.0 ** Eb[c][n] for c in range(nch))
+            hi, lo = np.float32(0.0), np.float32(0.0)
+            xsum, lo_abs = Fraction(0), 0.0
+            for win in schedule(nch, s, kst):
+                c, p0, q0, _ = win[0]
+                d = p0 + q0
+                acc = 0
+                for (_, p, q, k) in win:
+                    sl = slice(k * K["BK"], (k + 1) * K["BK"])
+                    part = V[c][p][m, sl] * W[c][q][n, sl]
+                    acc_prefix = acc + np.cumsum(part)
+                    assert np.max(np.abs(acc_prefix)) <= 1 << 24
+                    acc = int(acc_prefix[-1])
+                v = np.float32(acc)
+                assert int(v) == acc
+                sa = np.float32(2.0 ** Ea[c][m] / RA)
+                sb = np.float32(2.0 ** Eb[c][n] / RB)
+                fa = np.float32(sa * np.float32(2.0 ** (-BITS * (d + 2))))
+                x = np.float32(np.float32(v * sb) * fa)
+                assert Fraction(float(x)) == Fraction(acc) * Fraction(float(sb)) * Fraction(float(fa))
+                xsum += Fraction(float(x))
+                t = np.float32(hi + x)
+                bp = np.float32(t - hi)
+                e = np.float32(np.float32(hi - np.float32(t - bp)) + np.float32(x - bp))
+                assert Fraction(float(t)) + Fraction(float(e)) == Fraction(float(hi)) + Fraction(float(x))
+                hi = t
+                lo = np.float32(lo + e)
+                lo_abs += abs(float(lo))
+            out[m, n] = (hi, lo, RA, RB, xsum, lo_abs, Ea, Eb)
+    return out
+
+
+@pytest.mark.parametrize("s,nch,kst", [(7, 2, 2), (8, 1, 3), (5, 3, 1)])
+def test_kernel_model_matches_exact_product(s, nch, kst):
+    rng = np.random.default_rng(400 + s)
+    Kc = kst * K["BK"]
+    M = N = 3
+    # chunks with different magnitudes, so RA / RB and the relative window factors matter
+    Ach = [rng.standard_normal((M, Kc)) * 10.0 ** rng.uniform(-3, 3, (M, 1)) for _ in range(nch)]
+    Bch = [rng.standard_normal((N, Kc)) * 10.0 ** rng.uniform(-3, 3, (N, 1)) for _ in range(nch)]
+    out = model_gemm(Ach, Bch, s)
+    for (m, n), (hi, lo, RA, RB, xsum, lo_abs, Ea, Eb) in out.items():
+        exact = sum(Fraction(x) * Fraction(y) for c in range(nch) for x, y in zip(Ach[c][m], Bch[c][n]))
+        scheme = xsum * Fraction(RA) * Fraction(RB)
+        bound = sum(Kc * product_bound(Ea[c][m], Eb[c][n], s) for c in range(nch))
+        assert abs(scheme - exact) <= bound
+        # the float pair loses at most one FP32 rounding of lo per add
+        got = (Fraction(float(hi)) + Fraction(float(lo))) * Fraction(RA) * Fraction(RB)
+        assert abs(got - scheme) <= Fraction(lo_abs) * Fraction(2) ** -24 * (1 + Fraction(2) ** -23) \
+            * Fraction(RA) * Fraction(RB)
+        if s >= 7:
+            # FP64-level: the GPU tests' tolerance, 1e-13 of sum |a||b|
+            mag = sum(abs(Fraction(x) * Fraction(y)) for c in range(nch) for x, y in zip(Ach[c][m], Bch[c][n]))
+            assert abs(got - exact) <= Fraction(1, 10 ** 13) * mag
