@@ -2928,7 +2928,12 @@ int ccsd_solve(ccsd_t h, int* iterations, double* max_resid) {
         int d2 = 0;
         for (int p = 0; p < h->cfg.polish_iters; ++p) {
             int rc = ccsd_iterate(h, 1, &d2, &mr);
-            if (rc) { if (iterations) *iterations = it; return rc; }
+            if (rc) {
+                ccsd_set_precision(h, CCSD_MIXED);   // the handle stays a mixed-form handle
+                if (iterations) *iterations = it;
+                if (max_resid) *max_resid = mr;
+                return rc;
+            }
             if (d2) break;
             ++it;
         }
