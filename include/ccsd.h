@@ -77,13 +77,13 @@ typedef struct {
     int    precision;     /* CCSD_FP64, CCSD_MIXED or CCSD_OZAKI                */
     int    diis_depth;    /* 0 = plain successive substitution (paper Sec. 4.4.12);
                              2..8 = Pulay DIIS over that many updates            */
-    int    max_iter;      /* used by ccsd_solve                                 */
+    int    max_iter;      /* used by ccsd_solve, >= 0                           */
     double conv_tol;      /* max|R1| and max|R2| threshold, Eqs. (criterion_single,
-                             criterion_double)                                   */
+                             criterion_double); finite, >= 0 (0: never met)      */
     int    polish_iters;  /* CCSD_MIXED: polish iterations ccsd_solve runs after the
                              mixed ones (0..100)                                 */
     double mixed_tol;     /* CCSD_MIXED: ccsd_solve switches to FP64 once the mixed
-                             max|R| < max(mixed_tol, conv_tol)                  */
+                             max|R| < max(mixed_tol, conv_tol); finite, >= 0    */
     int    lean;          /* work-memory policy.  0: automatic -- problems whose
                              tensor-core operands would exceed 24 GB share two
                              operand buffers rewritten every residual, and the

@@ -2233,6 +2233,8 @@ bool valid_cfg(const ccsd_config* c) {
         if (c->nvir > 96) return false;       // one W' row (v^2 complex) is staged in shared memory
     }
     if (c->diis_depth < 0 || c->diis_depth == 1 || c->diis_depth > 8) return false;
+    if (c->max_iter < 0 || !(c->conv_tol >= 0.0) || !std::isfinite(c->conv_tol)) return false;
+    if (c->precision == CCSD_MIXED && (!(c->mixed_tol >= 0.0) || !std::isfinite(c->mixed_tol))) return false;
     if (c->lean != 0 && c->lean != 1) return false;
     const long long N = (long long)c->nk_dims[0] * c->nk_dims[1] * c->nk_dims[2];
     const long long vvvv = (long long)c->nvir * c->nvir * c->nvir * c->nvir;

@@ -70,6 +70,16 @@ def test_strerror_and_invalid_config_without_gpu(libpath):
     assert abs(m.value - borrowed - 8 * ints) < 1e6
     h = ctypes.c_void_p()
     assert lib.ccsd_create(ctypes.byref(cfg), None, None, ctypes.byref(h)) == binding.CCSD_ERR_INVALID
+    # iteration limits and tolerances
+    bad = [dict(max_iter=-1), dict(conv_tol=-1e-8), dict(conv_tol=float("nan")), dict(conv_tol=float("inf")),
+           dict(precision=binding.CCSD_MIXED, mixed_tol=float("nan")),
+           dict(precision=binding.CCSD_MIXED, mixed_tol=-1.0)]
+    for kw in bad:
+        cfg = binding.make_config((2, 2, 2), 8, 32, diis_depth=6, **kw)
+        assert lib.ccsd_footprint(ctypes.byref(cfg), 1, binding.CCSD_C128, ctypes.byref(n)) == binding.CCSD_ERR_INVALID, kw
+    for kw in (dict(max_iter=0), dict(conv_tol=0.0), dict(precision=binding.CCSD_MIXED, mixed_tol=0.0)):
+        cfg = binding.make_config((2, 2, 2), 8, 32, diis_depth=6, **kw)
+        assert lib.ccsd_footprint(ctypes.byref(cfg), 1, binding.CCSD_C128, ctypes.byref(n)) == 0, kw
 
 
 def test_no_cpu_fallback_when_library_missing(tmp_path):
