@@ -108,8 +108,9 @@ typedef struct {
     int int_dtype;        /* CCSD_C128 or CCSD_C64 (the six integral blocks)    */
     int vvvv_on_host;     /* 1: a host vvvv stays in host memory and the kernels
                              read it in place (the library registers it as
-                             mapped pinned memory unless it already is, and
-                             unregisters it at ccsd_destroy); it is read once per
+                             mapped pinned memory unless the caller already
+                             did, and unregisters it when the last handle
+                             reading it is destroyed); it is read once per
                              iteration (the ladder's W' formation), so this frees
                              its N^3 v^4 elements of device memory for about one
                              host-link transfer of it per iteration.  0:

@@ -143,7 +143,7 @@ struct ccsd_ctx {
     float2* shadow[NBUF] = {};       // complex64 data: mixed-form copies, or inputs stored complex64
     bool in32[NBUF] = {};            // input stored complex64 only (shadow[] set, buf[] null)
     std::vector<void*> owned;        // device allocations to free
-    void* host_registered = nullptr; // host vvvv registered by the library (unregistered at destroy)
+    void* host_registered = nullptr; // host vvvv registered (or counted) by the library; released at destroy
     size_t owned_bytes = 0;
     double2* amp = nullptr;          // [t1 | t2]
     double2* res = nullptr;          // [R1 | R2]
@@ -2243,6 +2243,40 @@ bool valid_cfg(const ccsd_config* c) {
     return true;
 }
 
+// Host ranges this library registered as mapped pinned memory (host vvvv read in
+// place), counted per handle: several live handles may share one host array, and
+// the range is unregistered when the last of them is destroyed.  A range the caller
+// registered is never unregistered here.
+struct HostReg { size_t bytes; int handles; };
+std::mutex g_host_reg_mu;
+std::map<void*, HostReg> g_host_reg;
+
+// 1: registered (or counted) by the library; 0: already registered by the caller;
+// < 0: error code.
+int host_register(void* p, size_t bytes) {
+    std::lock_guard<std::mutex> lock(g_host_reg_mu);
+    auto it = g_host_reg.find(p);
+    if (it != g_host_reg.end()) {
+        if (bytes > it->second.bytes) return CCSD_ERR_INVALID;   // a longer range from the same start
+        ++it->second.handles;
+        return 1;
+    }
+    const cudaError_t e = cudaHostRegister(p, bytes, cudaHostRegisterMapped);
+    if (e == cudaSuccess) { g_host_reg[p] = HostReg{bytes, 1}; return 1; }
+    cudaGetLastError();
+    return e == cudaErrorHostMemoryAlreadyRegistered ? 0 : CCSD_ERR_CUDA;
+}
+
+void host_unregister(void* p) {
+    std::lock_guard<std::mutex> lock(g_host_reg_mu);
+    auto it = g_host_reg.find(p);
+    if (it == g_host_reg.end()) return;
+    if (--it->second.handles == 0) {
+        cudaHostUnregister(p);
+        g_host_reg.erase(it);
+    }
+}
+
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
@@ -2270,10 +2304,9 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
                 d = (void*)(uintptr_t)256;
             } else {
                 void* hp = const_cast<void*>(ins[i]);
-                cudaError_t e = cudaHostRegister(hp, bytes, cudaHostRegisterMapped);
-                if (e == cudaSuccess) h->host_registered = hp;
-                else if (e == cudaErrorHostMemoryAlreadyRegistered) cudaGetLastError();
-                else { cudaGetLastError(); return CCSD_ERR_CUDA; }
+                const int r = host_register(hp, bytes);
+                if (r < 0) return r;
+                if (r == 1) h->host_registered = hp;
                 if (cudaHostGetDevicePointer(&d, hp, 0) != cudaSuccess) { cudaGetLastError(); return CCSD_ERR_CUDA; }
             }
         } else {
@@ -3241,7 +3274,7 @@ int ccsd_destroy(ccsd_t h) {
     for (cudaEvent_t e : h->ev1) cudaEventDestroy(e);
     if (h->norm_host) cudaFreeHost(h->norm_host);
     if (h->ev_norm) cudaEventDestroy(h->ev_norm);
-    if (h->host_registered) cudaHostUnregister(h->host_registered);
+    if (h->host_registered) host_unregister(h->host_registered);
     delete h;
     return CCSD_OK;
 }
