@@ -2593,14 +2593,18 @@ size_t request_bytes(const ccsd_config& c, const ccsd_inputs& in) {
     return footprint_bytes(&c, on_dev, in.int_dtype, in.vvvv_on_host != 0);
 }
 
+// Fields that ccsd_poll reads (state, energy, iterations, max|R|) change only under S->mu.
 void server_finish(ccsd_server* S, ServerReq* r, int state) {
+    double e_re = 0.0, e_im = 0.0;
     if (r->h) {
-        if (state == 2) ccsd_energy(r->h, &r->e_re, &r->e_im);
+        if (state == 2) ccsd_energy(r->h, &e_re, &e_im);
         ccsd_destroy(r->h);
         r->h = nullptr;
     }
     if (r->st) { cudaStreamDestroy(r->st); r->st = nullptr; }
     std::lock_guard<std::mutex> lock(S->mu);
+    r->e_re = e_re;
+    r->e_im = e_im;
     r->t_done = server_now(S);
     r->state = state;
     S->used -= r->bytes;
@@ -2656,10 +2660,15 @@ void server_loop(ccsd_server* S) {
             int done = 0, rc = began[i];
             double mr = 0.0;
             if (!rc) rc = iter_end(r->h, &done, &mr);
-            r->max_resid = mr;
+            int iters = 0;
+            {
+                std::lock_guard<std::mutex> lock(S->mu);
+                r->max_resid = mr;
+                if (!rc && !done) iters = ++r->iters;
+            }
             if (rc) { server_finish(S, r, rc); continue; }
             if (!done) {
-                if (++r->iters >= r->cfg.max_iter) { server_finish(S, r, CCSD_ERR_NOT_CONVERGED); continue; }
+                if (iters >= r->cfg.max_iter) { server_finish(S, r, CCSD_ERR_NOT_CONVERGED); continue; }
                 if (r->phase == 1 && --r->polish_left <= 0) { server_finish(S, r, 2); continue; }
                 keep.push_back(r);
                 continue;
