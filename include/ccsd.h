@@ -177,7 +177,8 @@ int ccsd_oz_timeout_selftest(void);
 /* One residual evaluation R(t) (paper Eqs. ori_EqSingle, ori_EqDouble with the
  * full Fock matrix inside F~): t1, t2 are read and r1, r2 written, all device
  * pointers in the layout above (r1 like t1, r2 like t2).  Does not touch the
- * handle's amplitudes. */
+ * handle's amplitudes.  CCSD_ERR_INVALID if a pointer is not device (or
+ * managed) memory. */
 int ccsd_residual(ccsd_t h, const void* t1, const void* t2, void* r1, void* r2);
 
 /* Up to n_iter iterations on the handle's amplitudes.  Each computes R(t);

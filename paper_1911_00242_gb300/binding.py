@@ -127,13 +127,67 @@ def check(code, where):
     return code
 
 
-def _ptr(x):
+def _invalid(where):
+    return CCSDError(CCSD_ERR_INVALID, where)
+
+
+def _ptr(x, where="argument"):
     """Device or host address of a torch tensor or numpy array (must be contiguous)."""
     if hasattr(x, "data_ptr"):
-        assert x.is_contiguous()
+        if not x.is_contiguous():
+            raise _invalid(f"{where}: tensor is not contiguous")
         return x.data_ptr()
-    assert x.flags.c_contiguous
+    if not x.flags.c_contiguous:
+        raise _invalid(f"{where}: array is not C-contiguous")
     return x.ctypes.data
+
+
+def _numel(x):
+    return x.numel() if hasattr(x, "numel") else int(x.size)
+
+
+def _dtype(x):
+    return str(x.dtype).replace("torch.", "")
+
+
+def _on_device(x):
+    return bool(getattr(x, "is_cuda", False))
+
+
+def expected_sizes(grid, nocc, nvir):
+    """Complex elements of every input and amplitude array (layouts of include/ccsd.h)."""
+    N = grid[0] * grid[1] * grid[2]
+    N3, o, v = N ** 3, nocc, nvir
+    return {"f_oo": N * o * o, "f_vv": N * v * v, "f_ov": N * o * v,
+            "oooo": N3 * o ** 4, "ooov": N3 * o ** 3 * v, "oovv": N3 * o * o * v * v,
+            "ovvo": N3 * o * o * v * v, "ovvv": N3 * o * v ** 3, "vvvv": N3 * v ** 4,
+            "t1": N * o * v, "t2": N3 * o * o * v * v}
+
+
+def check_arrays(grid, nocc, nvir, arrays, where):
+    """The library sees only pointers: check the element counts of the inputs and the
+    dtype of the Fock blocks here, before any kernel reads them."""
+    n = expected_sizes(grid, nocc, nvir)
+    for name in ("f_oo", "f_vv", "f_ov") + BLOCKS:
+        if name not in arrays:
+            raise _invalid(f"{where}: missing input {name}")
+        if _numel(arrays[name]) != n[name]:
+            raise _invalid(f"{where}: {name} has {_numel(arrays[name])} elements, expected {n[name]}")
+    for name in ("f_oo", "f_vv", "f_ov"):
+        if _dtype(arrays[name]) != "complex128":
+            raise _invalid(f"{where}: {name} must be complex128, got {_dtype(arrays[name])}")
+
+
+def check_amplitudes(n, pairs, where, device):
+    """(array, name) pairs of complex128 amplitude-shaped arrays with n[name] elements,
+    device tensors when `device`."""
+    for x, name in pairs:
+        if _dtype(x) != "complex128":
+            raise _invalid(f"{where}: {name} must be complex128, got {_dtype(x)}")
+        if _numel(x) != n[name]:
+            raise _invalid(f"{where}: {name} has {_numel(x)} elements, expected {n[name]}")
+        if device and not _on_device(x):
+            raise _invalid(f"{where}: {name} must be a CUDA tensor")
 
 
 def int_dtype(arrays):
@@ -150,7 +204,7 @@ def int_dtype(arrays):
 def inputs_struct(arrays, vvvv_on_host=False):
     inp = ccsd_inputs()
     for name in ("f_oo", "f_vv", "f_ov") + BLOCKS:
-        setattr(inp, name, _ptr(arrays[name]))
+        setattr(inp, name, _ptr(arrays[name], name))
     inp.int_dtype = int_dtype(arrays)
     inp.vvvv_on_host = 1 if vvvv_on_host else 0
     return inp
@@ -181,6 +235,8 @@ class Solver:
     def __init__(self, grid, nocc, nvir, arrays, stream=None, vvvv_on_host=False, **cfg):
         self.lib = load()
         self.cfg = make_config(grid, nocc, nvir, **cfg)
+        check_arrays(grid, nocc, nvir, arrays, "Solver")
+        self.sizes = expected_sizes(grid, nocc, nvir)
         self._keep = dict(arrays)
         inp = inputs_struct(arrays, vvvv_on_host)
         h = ctypes.c_void_p()
@@ -188,6 +244,7 @@ class Solver:
         self.h = h
 
     def residual(self, t1, t2, r1, r2):
+        check_amplitudes(self.sizes, ((t1, "t1"), (t2, "t2"), (r1, "t1"), (r2, "t2")), "residual", True)
         check(self.lib.ccsd_residual(self.h, _ptr(t1), _ptr(t2), _ptr(r1), _ptr(r2)), "ccsd_residual")
 
     def iterate(self, n=1):
@@ -214,9 +271,11 @@ class Solver:
         return complex(er.value, ei.value)
 
     def get_amplitudes(self, t1, t2):
+        check_amplitudes(self.sizes, ((t1, "t1"), (t2, "t2")), "get_amplitudes", False)
         check(self.lib.ccsd_get_amplitudes(self.h, _ptr(t1), _ptr(t2)), "ccsd_get_amplitudes")
 
     def set_amplitudes(self, t1, t2):
+        check_amplitudes(self.sizes, ((t1, "t1"), (t2, "t2")), "set_amplitudes", False)
         check(self.lib.ccsd_set_amplitudes(self.h, _ptr(t1), _ptr(t2)), "ccsd_set_amplitudes")
 
     def launches(self):
@@ -264,10 +323,13 @@ class BatchSolver:
         cfgs = (ccsd_config * n)()
         ins = (ccsd_inputs * n)()
         self._keep = []
+        self.sizes = []
         for i, (grid, nocc, nvir, arrays) in enumerate(problems):
             cfgs[i] = make_config(grid, nocc, nvir, **cfg)
+            check_arrays(grid, nocc, nvir, arrays, f"BatchSolver member {i}")
             ins[i] = inputs_struct(arrays)
             self._keep.append(arrays)
+            self.sizes.append(expected_sizes(grid, nocc, nvir))
         self.n = n
         h = ctypes.c_void_p()
         check(self.lib.ccsd_batch_create(n, cfgs, ins, ctypes.byref(h)), "ccsd_batch_create")
@@ -286,6 +348,9 @@ class BatchSolver:
         return [complex(a, b) for a, b in zip(er, ei)]
 
     def member_amplitudes(self, i, t1, t2):
+        if not 0 <= i < self.n:
+            raise _invalid(f"member_amplitudes: member {i} of {self.n}")
+        check_amplitudes(self.sizes[i], ((t1, "t1"), (t2, "t2")), "member_amplitudes", False)
         h = ctypes.c_void_p()
         check(self.lib.ccsd_batch_member(self.h, i, ctypes.byref(h)), "ccsd_batch_member")
         check(self.lib.ccsd_get_amplitudes(h, _ptr(t1), _ptr(t2)), "ccsd_get_amplitudes")
@@ -320,6 +385,7 @@ class Server:
 
     def submit(self, grid, nocc, nvir, arrays, **cfg):
         c = make_config(grid, nocc, nvir, **cfg)
+        check_arrays(grid, nocc, nvir, arrays, "submit")
         inp = inputs_struct(arrays)
         rid = ctypes.c_uint64(0)
         check(self.lib.ccsd_submit(self.h, ctypes.byref(c), ctypes.byref(inp), ctypes.byref(rid)), "ccsd_submit")

@@ -2923,6 +2923,8 @@ int ccsd_create(const ccsd_config* cfg, const ccsd_inputs* in, void* stream, ccs
 
 int ccsd_residual(ccsd_t h, const void* t1, const void* t2, void* r1, void* r2) {
     if (!h || !t1 || !t2 || !r1 || !r2) return CCSD_ERR_INVALID;
+    // the kernels read and write these directly: host memory is refused, not faulted on
+    if (!is_device_ptr(t1) || !is_device_ptr(t2) || !is_device_ptr(r1) || !is_device_ptr(r2)) return CCSD_ERR_INVALID;
     h->launches = 0;
     double2* save[4] = {h->buf[B_T1], h->buf[B_T2], h->buf[B_R1], h->buf[B_R2]};
     h->buf[B_T1] = (double2*)t1; h->buf[B_T2] = (double2*)t2;

@@ -219,3 +219,36 @@ def test_mixed_with_ozaki_polish_plan_in_bounds(libpath, grid, o, v, lean):
     for prec, pol in ((binding.CCSD_FP64, binding.CCSD_OZAKI), (binding.CCSD_MIXED, binding.CCSD_MIXED)):
         bad = binding.make_config(grid, o, v, precision=prec, polish_precision=pol)
         assert lib.ccsd_plan_check(ctypes.byref(bad), ctypes.byref(n), ctypes.byref(tb)) != 0
+
+
+def test_binding_checks_sizes_dtypes_and_devices():
+    """The library sees only pointers: the binding refuses arrays of the wrong size or
+    dtype before any kernel reads them (host arrays; no GPU needed)."""
+    import numpy as np
+    from paper_1911_00242_gb300 import binding
+    grid, o, v = (2, 1, 1), 2, 3
+    n = binding.expected_sizes(grid, o, v)
+    good = {k: np.zeros(n[k], np.complex128) for k in ("f_oo", "f_vv", "f_ov") + binding.BLOCKS}
+    binding.check_arrays(grid, o, v, good, "t")
+    c64 = dict(good, **{b: np.zeros(n[b], np.complex64) for b in binding.BLOCKS})
+    binding.check_arrays(grid, o, v, c64, "t")               # complex64 integrals are allowed
+    for name in ("f_oo", "ovvv", "vvvv"):
+        bad = dict(good, **{name: np.zeros(n[name] - 1, np.complex128)})
+        with pytest.raises(binding.CCSDError):
+            binding.check_arrays(grid, o, v, bad, "t")
+    with pytest.raises(binding.CCSDError):
+        binding.check_arrays(grid, o, v, dict(good, f_ov=np.zeros(n["f_ov"], np.complex64)), "t")
+    with pytest.raises(binding.CCSDError):
+        binding.check_arrays(grid, o, v, {k: x for k, x in good.items() if k != "oovv"}, "t")
+    with pytest.raises(binding.CCSDError):
+        binding.check_arrays((0, 1, 1), o, v, good, "t")
+    t1, t2 = np.zeros(n["t1"], np.complex128), np.zeros(n["t2"], np.complex128)
+    binding.check_amplitudes(n, ((t1, "t1"), (t2, "t2")), "t", False)
+    with pytest.raises(binding.CCSDError):                    # host arrays where device ones are needed
+        binding.check_amplitudes(n, ((t1, "t1"), (t2, "t2")), "t", True)
+    with pytest.raises(binding.CCSDError):
+        binding.check_amplitudes(n, ((t1.astype(np.complex64), "t1"),), "t", False)
+    with pytest.raises(binding.CCSDError):
+        binding.check_amplitudes(n, ((t2, "t1"),), "t", False)
+    with pytest.raises(binding.CCSDError):
+        binding._ptr(np.zeros((4, 4), np.complex128)[:, ::2], "t")
