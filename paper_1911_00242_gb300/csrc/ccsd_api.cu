@@ -45,6 +45,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <set>
 #include <thread>
 #include <vector>
 
@@ -400,16 +401,15 @@ int add_perm(ccsd_ctx* h, Alloc& al, int dst, int src, int n0, int n1, int n2, i
 
 // Driver entry point for TMA descriptors (no link against libcuda).
 PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {     // resolved once, thread-safe
         void* f = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
-        else
-            cudaGetLastError();
-    }
+            return (PFN_cuTensorMapEncodeTiled_v12000)f;
+        cudaGetLastError();
+        return (PFN_cuTensorMapEncodeTiled_v12000)nullptr;
+    }();
     return fn;
 }
 
@@ -1823,13 +1823,34 @@ void launch_embed(ccsd_ctx* h, EmbedPlan& e) {
     ++h->launches;
 }
 
+// A kernel's dynamic shared-memory limit is an attribute of the current device: it
+// is raised once per device and kernel, under a lock (the serving loop launches from
+// its own thread).
+enum { SMEM_TC = 0, SMEM_OZ = 1, SMEM_OZ_WPRIME = 2 };
+std::mutex g_smem_attr_mu;
+std::set<std::pair<int, int>> g_smem_attr_done;
+
+void ensure_smem_attr(int which) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); dev = 0; }
+    std::lock_guard<std::mutex> lock(g_smem_attr_mu);
+    if (!g_smem_attr_done.insert(std::make_pair(dev, which)).second) return;
+    switch (which) {
+        case SMEM_TC:
+            cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
+            break;
+        case SMEM_OZ:
+            cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
+            break;
+        default:
+            cudaFuncSetAttribute(oz_wprime_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            break;
+    }
+}
+
 void launch_tc(ccsd_ctx* h, TcPlan& t) {
     if (t.oz) {
-        static bool oz_attr_set = false;
-        if (!oz_attr_set) {
-            cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
-            oz_attr_set = true;
-        }
+        ensure_smem_attr(SMEM_OZ);
         OzArgs z = t.z;
         z.C = h->buf[t.c];
         z.work = z.nsplit > 1 ? h->oz_work : nullptr;
@@ -1841,11 +1862,7 @@ void launch_tc(ccsd_ctx* h, TcPlan& t) {
         }
         return;
     }
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
-        attr_set = true;
-    }
+    ensure_smem_attr(SMEM_TC);
     TcArgs a = t.a;
     a.C = h->buf[t.c];
     tc_gemm_kernel<<<t.blocks, TC_THREADS, TC_SMEM_BYTES, h->st>>>(t.mA_big, t.mA_small, t.mB_big, t.mB_small, a);
@@ -1924,11 +1941,7 @@ void launch_step(ccsd_ctx* h, size_t si) {
                 break;
             case 10: {
                 if (h->wlists[s.idx].oz) {
-                    static bool oz_w_attr = false;
-                    if (!oz_w_attr) {
-                        cudaFuncSetAttribute(oz_wprime_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-                        oz_w_attr = true;
-                    }
+                    ensure_smem_attr(SMEM_OZ_WPRIME);
                     OzWprimeArgs z = h->wlists[s.idx].z;
                     if (h->in32[B_VVVV]) { z.vvvv32 = h->shadow[B_VVVV]; z.vvvv = nullptr; }
                     else { z.vvvv = h->buf[B_VVVV]; z.vvvv32 = nullptr; }
