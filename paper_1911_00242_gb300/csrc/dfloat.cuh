@@ -5,6 +5,22 @@
 
 namespace ccsdk {
 
+// The rounded FP32 operations the error-free transformations are written with.  On
+// the device they are intrinsics, which the compiler neither contracts nor
+// reassociates; a host build (the CPU tests of this arithmetic) must be compiled
+// with -ffp-contract=off for the same guarantee.
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ float df_add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float df_sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float df_mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float df_fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+#else
+inline float df_add_rn(float a, float b) { return a + b; }
+inline float df_sub_rn(float a, float b) { return a - b; }
+inline float df_mul_rn(float a, float b) { return a * b; }
+inline float df_fma_rn(float a, float b, float c) { return fmaf(a, b, c); }
+#endif
+
 // Double-float ("df") numbers for the Ozaki form's FP64-class arithmetic off the
 // tensor cores (its remaining GEMMs and the t1 terms of the ladder's W'): x = h + l with
 // |l| <= ulp(h) / 2, about 48 significant bits, in FP32 arithmetic (GB300's FP32 pipe
@@ -13,48 +29,48 @@ namespace ccsdk {
 // intrinsics keep the compiler from contracting or reassociating them.
 struct df {
     float h, l;
-    __device__ __forceinline__ df() {}
-    __device__ __forceinline__ df(float a, float b) : h(a), l(b) {}
-    __device__ __forceinline__ explicit df(int x) : h((float)x), l(0.f) {}
-    __device__ __forceinline__ explicit df(float x) : h(x), l(0.f) {}
-    __device__ __forceinline__ explicit df(double x) : h((float)x), l((float)(x - (double)h)) {}
-    __device__ __forceinline__ explicit operator double() const { return (double)h + (double)l; }
+    __host__ __device__ __forceinline__ df() {}
+    __host__ __device__ __forceinline__ df(float a, float b) : h(a), l(b) {}
+    __host__ __device__ __forceinline__ explicit df(int x) : h((float)x), l(0.f) {}
+    __host__ __device__ __forceinline__ explicit df(float x) : h(x), l(0.f) {}
+    __host__ __device__ __forceinline__ explicit df(double x) : h((float)x), l((float)(x - (double)h)) {}
+    __host__ __device__ __forceinline__ explicit operator double() const { return (double)h + (double)l; }
 };
 
-__device__ __forceinline__ df df_renorm(float s, float t) {      // (s, t) -> h + l, |l| <= ulp(h) / 2
-    const float h = __fadd_rn(s, t);
-    return df(h, __fsub_rn(t, __fsub_rn(h, s)));
+__host__ __device__ __forceinline__ df df_renorm(float s, float t) {      // (s, t) -> h + l, |l| <= ulp(h) / 2
+    const float h = df_add_rn(s, t);
+    return df(h, df_sub_rn(t, df_sub_rn(h, s)));
 }
 
-__device__ __forceinline__ df operator+(df a, df b) {
-    const float s = __fadd_rn(a.h, b.h);
-    const float bb = __fsub_rn(s, a.h);
-    float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
-    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+__host__ __device__ __forceinline__ df operator+(df a, df b) {
+    const float s = df_add_rn(a.h, b.h);
+    const float bb = df_sub_rn(s, a.h);
+    float e = df_add_rn(df_sub_rn(a.h, df_sub_rn(s, bb)), df_sub_rn(b.h, bb));
+    e = df_add_rn(e, df_add_rn(a.l, b.l));
     return df_renorm(s, e);
 }
 
-__device__ __forceinline__ df operator-(df a) { return df(-a.h, -a.l); }
-__device__ __forceinline__ df operator-(df a, df b) { return a + df(-b.h, -b.l); }
+__host__ __device__ __forceinline__ df operator-(df a) { return df(-a.h, -a.l); }
+__host__ __device__ __forceinline__ df operator-(df a, df b) { return a + df(-b.h, -b.l); }
 
-__device__ __forceinline__ df operator*(df a, df b) {
-    const float p = __fmul_rn(a.h, b.h);
-    float e = __fmaf_rn(a.h, b.h, -p);
-    e = __fmaf_rn(a.h, b.l, e);
-    e = __fmaf_rn(a.l, b.h, e);
+__host__ __device__ __forceinline__ df operator*(df a, df b) {
+    const float p = df_mul_rn(a.h, b.h);
+    float e = df_fma_rn(a.h, b.h, -p);
+    e = df_fma_rn(a.h, b.l, e);
+    e = df_fma_rn(a.l, b.h, e);
     return df_renorm(p, e);
 }
 
 // a * b + c
-__device__ __forceinline__ df fma(df a, df b, df c) {
-    const float p = __fmul_rn(a.h, b.h);
-    float e = __fmaf_rn(a.h, b.h, -p);
-    e = __fmaf_rn(a.h, b.l, e);
-    e = __fmaf_rn(a.l, b.h, e);
-    const float s = __fadd_rn(p, c.h);
-    const float bb = __fsub_rn(s, p);
-    float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(c.h, bb));
-    t = __fadd_rn(t, __fadd_rn(e, c.l));
+__host__ __device__ __forceinline__ df fma(df a, df b, df c) {
+    const float p = df_mul_rn(a.h, b.h);
+    float e = df_fma_rn(a.h, b.h, -p);
+    e = df_fma_rn(a.h, b.l, e);
+    e = df_fma_rn(a.l, b.h, e);
+    const float s = df_add_rn(p, c.h);
+    const float bb = df_sub_rn(s, p);
+    float t = df_add_rn(df_sub_rn(p, df_sub_rn(s, bb)), df_sub_rn(c.h, bb));
+    t = df_add_rn(t, df_add_rn(e, c.l));
     return df_renorm(s, t);
 }
 
