@@ -44,6 +44,7 @@
 #pragma once
 #include "tcgemm.cuh"
 #include "dfloat.cuh"
+#include "ozaki_split.cuh"
 
 namespace ccsdk {
 
@@ -65,10 +66,6 @@ constexpr int OZ_COLS = OZ_BN / (OZ_ACC_WARPS / 4);        // columns per accumu
 constexpr int OZ_THREADS = 64 + 32 * OZ_ACC_WARPS;
 constexpr int OZ_REF_BYTES = OZ_ACC_WARPS * 96 * 4;       // per accumulator warp: RB, 1 / RB, chunk column factors
 constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256 + OZ_REF_BYTES;
-constexpr int OZ_SLICE_BITS = 7;
-constexpr int OZ_MAX_SLICES = 8;
-constexpr int OZ_EXP_MIN = -120;                           // row-scale exponent clamp (see oz_row_exponent)
-constexpr int OZ_EXP_MAX = 120;
 
 struct OzArgs {
     const int* rowA;          // [nbatch * nchunk] row of A' (within a slice plane) where chunk c of batch b starts
@@ -484,39 +481,6 @@ __global__ void oz_split_reduce(const OzArgs g)
 
 // ---------------------------------------------------------------- operand prep
 
-// Row maxima are taken on the bit patterns: for non-negative doubles the unsigned
-// order of the patterns is the numeric order, and the integer pipes are far faster
-// than GB300's FP64 pipe.
-__device__ __forceinline__ unsigned long long abs_bits(double x) {
-    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
-}
-
-// Power-of-two scale exponent E with 2^E > amax (the frexp exponent of amax, from
-// its bit pattern), clamped to [OZ_EXP_MIN, OZ_EXP_MAX] so that 2^E and 1 / 2^E are
-// FP32 values: rows whose largest element lies outside about 1e-36 .. 1e36 lose
-// relative precision.  0 for an all-zero row.
-__device__ __forceinline__ int oz_row_exponent(unsigned long long amax_bits) {
-    if (amax_bits == 0) return 0;
-    const int ef = (int)(amax_bits >> 52);              // biased exponent (0: subnormal)
-    return max(OZ_EXP_MIN, min(OZ_EXP_MAX, ef - 1022));
-}
-
-// The s slices of x 2^-E, from the 7s-bit fixed point Y = rint(x 2^{7s-E}) (|Y| <= 2^{7s};
-// `scale` = 2^{7s-E}, so x * scale is exact): balanced base-128 digits from the least
-// significant (in [-64, 63]), the remaining top digit (|v_0| <= 128) last.  Then
-// x = 2^E sum_p v_p 2^{-7(p+1)} up to 2^{E-7s-1}.  Integer arithmetic only after the
-// one conversion.  Output: BF16 bit patterns (the values are integers of at most 8
-// bits, so the upper half of their FP32 pattern is exact).
-__device__ __forceinline__ void oz_split(double x, double scale, int s, uint16_t* out) {
-    long long Y = __double2ll_rn(x * scale);
-    for (int p = s - 1; p > 0; --p) {
-        const int dg = (int)((Y + 64) & 127) - 64;
-        Y = (Y - dg) >> 7;
-        out[p] = (uint16_t)(__float_as_uint((float)dg) >> 16);
-    }
-    out[0] = (uint16_t)(__float_as_uint((float)(int)Y) >> 16);
-}
-
 __device__ __forceinline__ uint32_t pack_bf16x2(uint16_t lo, uint16_t hi) {
     return (uint32_t)lo | ((uint32_t)hi << 16);
 }
@@ -540,13 +504,6 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long x
     return m;
 }
 
-// 2^{7s-E} as a double and 2^E as a float.
-__device__ __forceinline__ double oz_fixed_scale(int s, int E) {
-    return __longlong_as_double((long long)(1023 + OZ_SLICE_BITS * s - E) << 52);
-}
-__device__ __forceinline__ float oz_row_scale(int E) {
-    return __int_as_float((127 + E) << 23);
-}
 
 // Operand preparation for oz_gemm_kernel (the Ozaki analogue of embed_kernel):
 // gathers the complex block matrix X_b[r][k] = src[srcoff[b] + srow[r] + scol[k]],

@@ -12,8 +12,9 @@ cores (Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59 (2012) 95-118):
   TwoSum (Knuth); the FP64 epilogue multiplies hi + lo by the reference scales RA RB.
 
 This module restates those steps in integer and rational arithmetic, with the
-kernel's constants read from the header, and checks what the form's accuracy rests
-on:
+kernel's constants read from the headers, checks that the restated split equals the
+kernels' own split code (csrc/ozaki_split.cuh, built for the host), and checks what
+the form's accuracy rests on:
 
 1. the digits are in range, are exact in BF16, and reconstruct x within 2^{E-7s-1};
 2. every partial sum of a window is an integer of magnitude <= 2^24 (so the tensor
@@ -30,19 +31,24 @@ The dropped pairs have p + q = d >= s, hence p, q >= 1 and |v_p w_q| <= 2^12; th
 2^{Ea+Eb-7s} c_s / 4 with c_s = sum_{j=0}^{s-2} (s-1-j) 2^{-7j}.  The bound per product
 is therefore 2^{Ea+Eb-7s} (1 + 2^{-7s-2} + c_s / 4).
 """
+import ctypes
 import os
 import re
+import shutil
+import subprocess
 from fractions import Fraction
 
 import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "paper_1911_00242_gb300", "csrc", "ozaki.cuh")
+CSRC = os.path.join(ROOT, "paper_1911_00242_gb300", "csrc")
+HEADERS = [os.path.join(CSRC, "ozaki.cuh"), os.path.join(CSRC, "ozaki_split.cuh")]
+PROBE = os.path.join(ROOT, "tests", "oz_split_probe.cu")
 
 
 def _kernel_constants():
-    src = open(HEADER).read()
+    src = "".join(open(h).read() for h in HEADERS)
 
     def const(name):
         m = re.search(r"constexpr int %s = (-?\d+);" % name, src)
@@ -143,6 +149,74 @@ def test_split_zero_and_clamped_rows():
     assert split(0.0, 7, 0) == [0] * 7
     assert row_exponent(np.array([1e-300])) == K["EXP_MIN"]
     assert row_exponent(np.array([1e300])) == K["EXP_MAX"]
+
+
+# ---------------------------------------------------------------- the kernel's own split code
+@pytest.fixture(scope="module")
+def probe(tmp_path_factory):
+    """csrc/ozaki_split.cuh built for the host (the same source the embedding kernels use)."""
+    home = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    nvcc = os.path.join(home, "bin", "nvcc")
+    nvcc = nvcc if os.path.exists(nvcc) else shutil.which("nvcc")
+    if not nvcc:
+        pytest.skip("nvcc not available")
+    out = str(tmp_path_factory.mktemp("ozprobe") / "libozprobe.so")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17", "-shared",
+                    "-Xcompiler", "-fPIC,-ffp-contract=off", "-o", out, PROBE], check=True, capture_output=True)
+    lib = ctypes.CDLL(out)
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.probe_row_exponent.argtypes = [dp, ctypes.c_int]
+    lib.probe_row_exponent.restype = ctypes.c_int
+    lib.probe_split.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint16)]
+    lib.probe_scales.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_float)]
+    return lib
+
+
+def kernel_split(probe, xs, s, E):
+    xs = np.ascontiguousarray(xs, dtype=np.float64)
+    out = np.zeros(len(xs) * s, np.uint16)
+    probe.probe_split(xs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(xs), s, E,
+                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)))
+    digits = (out.astype(np.uint32) << 16).view(np.float32)
+    assert np.all(digits == np.rint(digits))
+    return digits.astype(np.int64).reshape(len(xs), s)
+
+
+def kernel_row_exponent(probe, row):
+    row = np.ascontiguousarray(row, dtype=np.float64)
+    return probe.probe_row_exponent(row.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(row))
+
+
+@pytest.mark.parametrize("s", [3, 5, 7, 8])
+def test_kernel_split_code_equals_the_model(probe, s):
+    """The embedding kernels' split (row exponent, fixed point, digits, BF16 patterns)
+    gives the model's digits bit for bit, also at the top-digit bound, at exact ties of
+    the rounding (to even), for zeros and for rows outside the exponent clamp."""
+    rng = np.random.default_rng(500 + s)
+    X = rows(rng, 10, 40, -30, 30)
+    for r in X:
+        E = row_exponent(r)
+        assert kernel_row_exponent(probe, r) == E
+        got = kernel_split(probe, r, s, E)
+        assert [list(g) for g in got] == [split(x, s, E) for x in r]
+    E = 3
+    top = np.nextafter(np.ldexp(1.0, E), 0.0)
+    k = np.arange(-40, 40, dtype=np.float64)
+    ties = (k + 0.5) * np.ldexp(1.0, E - BITS * s)                # x 2^{7s-E} = k + 1/2 exactly
+    special = np.concatenate([[0.0, -0.0, top, -top, np.ldexp(1.0, E - 1)], ties])
+    got = kernel_split(probe, special, s, E)
+    assert [list(g) for g in got] == [split(x, s, E) for x in special]
+    for row in (np.array([0.0, 0.0]), np.array([1e-300, -2e-300]), np.array([3e300, 1.0]), np.array([5e-324])):
+        assert kernel_row_exponent(probe, row) == row_exponent(row)
+
+
+def test_kernel_scales_are_the_powers_of_two(probe):
+    f, r = ctypes.c_double(0.0), ctypes.c_float(0.0)
+    for s in (3, 7, 8):
+        for E in (K["EXP_MIN"], -7, 0, 5, K["EXP_MAX"]):
+            probe.probe_scales(s, E, ctypes.byref(f), ctypes.byref(r))
+            assert f.value == 2.0 ** (BITS * s - E)
+            assert r.value == 2.0 ** E
 
 
 # ---------------------------------------------------------------- exact windows
