@@ -36,6 +36,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tf32_split.cuh"
+
 namespace ccsdk {
 
 constexpr int TC_BM = 128;
@@ -376,32 +378,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
     }
 }
 
-// ---------------------------------------------------------------- operand prep
-__device__ __forceinline__ float tf32_round(float x) {
-    // round to nearest (ties away) at the 10-bit TF32 mantissa; TF32 MMAs then
-    // use these values exactly
-    uint32_t u = __float_as_uint(x);
-    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
-    return __uint_as_float(u);
-}
-
-// Split of a float into TF32-exact big + small parts (FP32 arithmetic only).
-__device__ __forceinline__ void split_tf32f(float x, float& big, float& small) {
-    big = tf32_round(x);
-    small = tf32_round(x - big);
-}
-
-// Split of a double into TF32-exact big + small parts.
-__device__ __forceinline__ void split_tf32(double x, float& big, float& small) {
-    const float f = (float)x;
-    big = tf32_round(f);
-    small = tf32_round((float)(x - (double)big));
-}
-
 }  // namespace ccsdk
 
 namespace ccsdk {
 
+// ---------------------------------------------------------------- operand prep
 // Operand preparation for tc_gemm_kernel: gathers a complex block matrix
 // X_b[r][k] = src[srcoff[b] + srow[r] + scol[k]] and writes its real
 // embedding, split into TF32-exact big and small parts:
