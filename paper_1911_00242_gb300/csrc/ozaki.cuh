@@ -45,6 +45,7 @@
 #include "tcgemm.cuh"
 #include "dfloat.cuh"
 #include "ozaki_split.cuh"
+#include "ozaki_schedule.cuh"
 
 namespace ccsdk {
 
@@ -59,8 +60,6 @@ constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;    // 32 KiB
 constexpr int OZ_LO_COL = 2 * OZ_BN;                       // TMEM columns of the lo accumulator
 constexpr int OZ_HI_COL = 3 * OZ_BN;                       // TMEM columns of the hi accumulator
 constexpr int OZ_TMEM_COLS = 4 * OZ_BN;                    // two windows, lo, hi
-// stages (64 K each) per exact TMEM window of diagonal d
-__host__ __device__ constexpr int oz_win(int d) { return d == 0 ? 16 : 32; }
 constexpr int OZ_ACC_WARPS = 16;                           // four per TMEM lane quarter, 32 columns each
 constexpr int OZ_COLS = OZ_BN / (OZ_ACC_WARPS / 4);        // columns per accumulator thread
 constexpr int OZ_THREADS = 64 + 32 * OZ_ACC_WARPS;
@@ -124,25 +123,6 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
     const float e = (hi - (s - bp)) + (x - bp);
     hi = s;
     lo += e;
-}
-
-// Work of one tile, in units u = c * s + d (chunk c, diagonal d = p + q of the slice
-// pairs), each (d + 1) * kstages stages.  With nsplit > 1, CTA `split` takes the units
-// whose first stage lies in its share [split, split + 1) * total / nsplit of the stages.
-__device__ __forceinline__ void oz_unit_range(int nch, int S, int kstages, int nsplit, int split, int& u0, int& u1) {
-    const int nunits = nch * S;
-    if (nsplit <= 1) { u0 = 0; u1 = nunits; return; }
-    const long long per_chunk = (long long)(S * (S + 1) / 2) * kstages;
-    const long long total = per_chunk * nch;
-    const long long lo = total * split / nsplit, hi = total * (split + 1) / nsplit;
-    u0 = nunits; u1 = nunits;
-    for (int u = 0; u < nunits; ++u) {
-        const int c = u / S, d = u - (u / S) * S;
-        const long long start = c * per_chunk + (long long)(d * (d + 1) / 2) * kstages;
-        if (start >= lo && u0 == nunits) u0 = u;
-        if (start >= hi) { u1 = u; break; }
-    }
-    if (u1 < u0) u1 = u0;
 }
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)

@@ -1,7 +1,9 @@
-// Host build of the Ozaki form's operand splitting (csrc/ozaki_split.cuh), for the CPU
-// tests in test_ozaki_scheme.py: the row exponent, the fixed-point scales and the
-// BF16 digit patterns, exactly as the embedding kernels compute them.
+// Host build of the Ozaki form's operand splitting (csrc/ozaki_split.cuh) and tile
+// schedule (csrc/ozaki_schedule.cuh), for the CPU tests in test_ozaki_scheme.py: the
+// row exponent, the fixed-point scales and the BF16 digit patterns, exactly as the
+// embedding kernels compute them, and the windows and unit split of the GEMM kernel.
 #include "../paper_1911_00242_gb300/csrc/ozaki_split.cuh"
+#include "../paper_1911_00242_gb300/csrc/ozaki_schedule.cuh"
 
 using namespace ccsdk;
 
@@ -25,6 +27,12 @@ void probe_split(const double* x, int n, int s, int E, uint16_t* out) {
 void probe_scales(int s, int E, double* fixed, float* row) {
     *fixed = oz_fixed_scale(s, E);
     *row = oz_row_scale(E);
+}
+
+int probe_win(int d) { return oz_win(d); }
+
+void probe_unit_range(int nch, int S, int kstages, int nsplit, int split, int* u0, int* u1) {
+    oz_unit_range(nch, S, kstages, nsplit, split, *u0, *u1);
 }
 
 }  // extern "C"

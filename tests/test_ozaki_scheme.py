@@ -43,7 +43,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1911_00242_gb300", "csrc")
-HEADERS = [os.path.join(CSRC, "ozaki.cuh"), os.path.join(CSRC, "ozaki_split.cuh")]
+HEADERS = [os.path.join(CSRC, "ozaki.cuh"), os.path.join(CSRC, "ozaki_split.cuh"),
+           os.path.join(CSRC, "ozaki_schedule.cuh")]
 PROBE = os.path.join(ROOT, "tests", "oz_split_probe.cu")
 
 
@@ -169,6 +170,10 @@ def probe(tmp_path_factory):
     lib.probe_row_exponent.restype = ctypes.c_int
     lib.probe_split.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint16)]
     lib.probe_scales.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_float)]
+    lib.probe_win.argtypes = [ctypes.c_int]
+    lib.probe_win.restype = ctypes.c_int
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.probe_unit_range.argtypes = [ctypes.c_int] * 5 + [ip, ip]
     return lib
 
 
@@ -333,6 +338,22 @@ def test_unit_split_is_a_partition(nch, S, kstages):
             covered.extend(range(u0, u1))
             prev = u1
         assert covered == list(range(nunits))
+
+
+def test_kernel_schedule_code_equals_the_model(probe):
+    """The GEMM kernel's window sizes and unit split (csrc/ozaki_schedule.cuh, built for
+    the host) equal the model's, and the kernel's split is a partition by itself."""
+    assert all(probe.probe_win(d) == oz_win(d) for d in range(K["MAX_SLICES"]))
+    u0, u1 = ctypes.c_int(0), ctypes.c_int(0)
+    for nch, S, kst in [(1, 7, 1), (1, 7, 4), (3, 7, 8), (2, 3, 2), (5, 8, 3), (1, 1, 1), (27, 7, 6)]:
+        for nsplit in range(1, 17):
+            prev = 0
+            for sp in range(nsplit):
+                probe.probe_unit_range(nch, S, kst, nsplit, sp, ctypes.byref(u0), ctypes.byref(u1))
+                assert (u0.value, u1.value) == unit_range(nch, S, kst, nsplit, sp)
+                assert u0.value == prev and u0.value <= u1.value <= nch * S
+                prev = u1.value
+            assert prev == nch * S
 
 
 def schedule(nch, S, kstages):
