@@ -277,6 +277,13 @@ int ccsd_server_destroy(ccsd_server_t s);
 
 const char* ccsd_strerror(int code);
 
+/* Why the most recent failing call on this host thread failed, where the library
+ * knows more than the code says (an invalid config field, a 32-bit table limit, the
+ * CUDA error text, a timed-out device wait); "" if nothing was recorded.  Every
+ * entry point but ccsd_energy_noalloc clears it when called from outside the
+ * library.  The pointer stays valid for the thread's lifetime. */
+const char* ccsd_last_error(void);
+
 /* Correlation energy per unit cell of the amplitudes t1, t2 (same expression
  * as ccsd_energy), for callers that cannot allocate device memory: code
  * running inside a CUDA stream capture, hosts whose allocator owns all device

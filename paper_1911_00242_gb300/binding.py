@@ -91,6 +91,7 @@ SYMBOLS = {
                            ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "ccsd_server_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "ccsd_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "ccsd_last_error": ([], ctypes.c_char_p),
     "ccsd_energy_noalloc": ([ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 6,
                             ctypes.c_int),
 }
@@ -99,10 +100,11 @@ _lib = None
 
 
 class CCSDError(RuntimeError):
-    def __init__(self, code, where):
+    def __init__(self, code, where, detail=None):
         self.code = code
         msg = _lib.ccsd_strerror(code).decode() if _lib is not None else str(code)
-        super().__init__(f"{where}: {msg} ({code})")
+        self.detail = detail or ""
+        super().__init__(f"{where}: {msg} ({code})" + (f": {self.detail}" if self.detail else ""))
 
 
 def load(path=LIB_PATH):
@@ -123,7 +125,7 @@ def load(path=LIB_PATH):
 
 def check(code, where):
     if code != CCSD_OK:
-        raise CCSDError(code, where)
+        raise CCSDError(code, where, _lib.ccsd_last_error().decode() if _lib is not None else None)
     return code
 
 

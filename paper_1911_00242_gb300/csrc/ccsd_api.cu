@@ -202,6 +202,23 @@ namespace {
 thread_local char g_errbuf[256];
 void last_err(cudaError_t e) { snprintf(g_errbuf, sizeof g_errbuf, "%s", cudaGetErrorString(e)); }
 
+// Records why a configuration or a call is refused (ccsd_last_error).
+bool refuse(const char* why) {
+    snprintf(g_errbuf, sizeof g_errbuf, "%s", why);
+    return false;
+}
+
+// Every exported entry point opens one: the outermost call on a thread clears the
+// message of ccsd_last_error, calls nested inside it (a failed create destroying its
+// handle, a solve resetting the precision) keep what the failure recorded.
+thread_local int g_api_depth = 0;
+struct ApiScope {
+    ApiScope() { if (g_api_depth++ == 0) g_errbuf[0] = 0; }
+    ~ApiScope() { --g_api_depth; }
+    ApiScope(const ApiScope&) = delete;
+    ApiScope& operator=(const ApiScope&) = delete;
+};
+
 struct Alloc {
     ccsd_ctx* h;
     int err = 0;
@@ -480,8 +497,8 @@ int add_embed(ccsd_ctx* h, Alloc& al, int src, const TcBuf& dst, int mode, int R
                          *std::max_element(scol.begin(), scol.end());
     const long long lo = *std::min_element(srcoff.begin(), srcoff.end()) + *std::min_element(srow.begin(), srow.end()) +
                          *std::min_element(scol.begin(), scol.end());
-    if (lo < 0 || hi >= h->bufsize[src]) return CCSD_ERR_INVALID;
-    if (nblk * R * (mode == 0 ? 1 : 2) > dst.rows) return CCSD_ERR_INVALID;
+    if (lo < 0 || hi >= h->bufsize[src]) { refuse("an operand gather offset is out of range (32-bit tables)"); return CCSD_ERR_INVALID; }
+    if (nblk * R * (mode == 0 ? 1 : 2) > dst.rows) { refuse("an embedded operand exceeds its buffer"); return CCSD_ERR_INVALID; }
     EmbedPlan e{};
     e.src = src;
     e.a.srcoff = upload(al, srcoff, h->st);
@@ -519,19 +536,21 @@ int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M,
     const bool oz = h->cur_oz;
     if (A.kpad != B.kpad || A.kpad % (oz ? OZ_BK : TC_BK)) return CCSD_ERR_INVALID;
     if (!oz && (alpha_im != 0.0 || overwrite || !rowC.empty())) return CCSD_ERR_INVALID;
-    if (oz && ((long long)h->oz_slices * A.rows > INT_MAX || (long long)h->oz_slices * B.rows > INT_MAX))
+    if (oz && ((long long)h->oz_slices * A.rows > INT_MAX || (long long)h->oz_slices * B.rows > INT_MAX)) {
+        refuse("a tensor-core operand exceeds 2^31 rows (32-bit row indices)");
         return CCSD_ERR_INVALID;
+    }
     const long long noff = rowC.empty() ? (long long)nbatch * M : nbatch;
     if ((long long)rowA.size() != (long long)nbatch * nchunk || (long long)rowB.size() != (long long)nbatch * nchunk ||
         (long long)offC.size() != noff || (int)colC.size() * 2 != Nr || (!rowC.empty() && (int)rowC.size() != M))
         return CCSD_ERR_INVALID;
-    for (int x : rowA) if (x < 0 || x >= A.rows) return CCSD_ERR_INVALID;
-    for (int x : rowB) if (x < 0 || x >= B.rows) return CCSD_ERR_INVALID;
+    for (int x : rowA) if (x < 0 || x >= A.rows) { refuse("a tensor-core operand row index is out of range (32-bit row indices)"); return CCSD_ERR_INVALID; }
+    for (int x : rowB) if (x < 0 || x >= B.rows) { refuse("a tensor-core operand row index is out of range (32-bit row indices)"); return CCSD_ERR_INVALID; }
     const long long rhi = rowC.empty() ? 0 : *std::max_element(rowC.begin(), rowC.end());
     const long long rlo = rowC.empty() ? 0 : *std::min_element(rowC.begin(), rowC.end());
     const long long chi = *std::max_element(offC.begin(), offC.end()) + rhi + *std::max_element(colC.begin(), colC.end());
     const long long clo = *std::min_element(offC.begin(), offC.end()) + rlo + *std::min_element(colC.begin(), colC.end());
-    if (clo < 0 || chi >= h->bufsize[c]) return CCSD_ERR_INVALID;
+    if (clo < 0 || chi >= h->bufsize[c]) { refuse("a tensor-core output offset is out of range (32-bit tables)"); return CCSD_ERR_INVALID; }
     if (!nchunk_b.empty()) {
         if ((long long)nchunk_b.size() != nbatch) return CCSD_ERR_INVALID;
         for (int x : nchunk_b) if (x < 0 || x > nchunk) return CCSD_ERR_INVALID;
@@ -540,7 +559,7 @@ int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M,
         if (offC2.size() != offC.size() || colC2.size() != colC.size()) return CCSD_ERR_INVALID;
         const long long h2 = *std::max_element(offC2.begin(), offC2.end()) + rhi + *std::max_element(colC2.begin(), colC2.end());
         const long long l2 = *std::min_element(offC2.begin(), offC2.end()) + rlo + *std::min_element(colC2.begin(), colC2.end());
-        if (l2 < 0 || h2 >= h->bufsize[c]) return CCSD_ERR_INVALID;
+        if (l2 < 0 || h2 >= h->bufsize[c]) { refuse("a tensor-core output offset is out of range (32-bit tables)"); return CCSD_ERR_INVALID; }
     }
     TcPlan t{};
     t.c = c;
@@ -2234,25 +2253,30 @@ int batch_capture(ccsd_batch* B, int fp32) {
 }
 
 bool valid_cfg(const ccsd_config* c) {
-    if (!c) return false;
-    for (int i = 0; i < 3; ++i) if (c->nk_dims[i] < 1 || c->nk_dims[i] > 64) return false;
-    if (c->nocc < 1 || c->nvir < 1 || c->nocc > 256 || c->nvir > 512) return false;
-    if (c->precision != CCSD_FP64 && c->precision != CCSD_MIXED && c->precision != CCSD_OZAKI) return false;
-    if (c->precision == CCSD_MIXED && (c->polish_iters < 0 || c->polish_iters > 100)) return false;
+    if (!c) return refuse("config is null");
+    for (int i = 0; i < 3; ++i) if (c->nk_dims[i] < 1 || c->nk_dims[i] > 64) return refuse("nk_dims must be 1..64");
+    if (c->nocc < 1 || c->nvir < 1 || c->nocc > 256 || c->nvir > 512) return refuse("nocc must be 1..256, nvir 1..512");
+    if (c->precision != CCSD_FP64 && c->precision != CCSD_MIXED && c->precision != CCSD_OZAKI)
+        return refuse("unknown precision");
+    if (c->precision == CCSD_MIXED && (c->polish_iters < 0 || c->polish_iters > 100))
+        return refuse("polish_iters must be 0..100");
     if (c->polish_precision != CCSD_FP64 && !(c->precision == CCSD_MIXED && c->polish_precision == CCSD_OZAKI))
-        return false;
+        return refuse("polish_precision must be CCSD_FP64, or CCSD_OZAKI for a CCSD_MIXED config");
     if (c->precision == CCSD_OZAKI || c->polish_precision == CCSD_OZAKI) {
-        if (c->oz_slices != 0 && (c->oz_slices < 3 || c->oz_slices > OZ_MAX_SLICES)) return false;
-        if (c->nvir > 96) return false;       // one W' row (v^2 complex) is staged in shared memory
+        if (c->oz_slices != 0 && (c->oz_slices < 3 || c->oz_slices > OZ_MAX_SLICES))
+            return refuse("oz_slices must be 0 or 3..8");
+        if (c->nvir > 96) return refuse("the Ozaki form needs nvir <= 96");   // one W' row (v^2 complex) in shared memory
     }
-    if (c->diis_depth < 0 || c->diis_depth == 1 || c->diis_depth > 8) return false;
-    if (c->max_iter < 0 || !(c->conv_tol >= 0.0) || !std::isfinite(c->conv_tol)) return false;
-    if (c->precision == CCSD_MIXED && (!(c->mixed_tol >= 0.0) || !std::isfinite(c->mixed_tol))) return false;
-    if (c->lean != 0 && c->lean != 1) return false;
+    if (c->diis_depth < 0 || c->diis_depth == 1 || c->diis_depth > 8) return refuse("diis_depth must be 0 or 2..8");
+    if (c->max_iter < 0) return refuse("max_iter must be >= 0");
+    if (!(c->conv_tol >= 0.0) || !std::isfinite(c->conv_tol)) return refuse("conv_tol must be finite and >= 0");
+    if (c->precision == CCSD_MIXED && (!(c->mixed_tol >= 0.0) || !std::isfinite(c->mixed_tol)))
+        return refuse("mixed_tol must be finite and >= 0");
+    if (c->lean != 0 && c->lean != 1) return refuse("lean must be 0 or 1");
     const long long N = (long long)c->nk_dims[0] * c->nk_dims[1] * c->nk_dims[2];
     const long long vvvv = (long long)c->nvir * c->nvir * c->nvir * c->nvir;
-    if (vvvv * 1 > (1LL << 30)) return false;          // block offsets are 32-bit inside a block
-    if (N * N * N * vvvv > (1LL << 40)) return false;
+    if (vvvv * 1 > (1LL << 30)) return refuse("nvir^4 must be <= 2^30 (32-bit offsets inside a block)");
+    if (N * N * N * vvvv > (1LL << 40)) return refuse("N_k^3 nvir^4 must be <= 2^40");
     return true;
 }
 
@@ -2705,6 +2729,7 @@ void server_loop(ccsd_server* S) {
 extern "C" {
 
 int ccsd_footprint(const ccsd_config* cfg, int inputs_on_device, int int_dtype, size_t* bytes) {
+    ApiScope api_scope_;
     if (!valid_cfg(cfg) || !bytes || (int_dtype != CCSD_C128 && int_dtype != CCSD_C64)) return CCSD_ERR_INVALID;
     bool on_dev[9];
     for (bool& x : on_dev) x = inputs_on_device != 0;
@@ -2715,6 +2740,7 @@ int ccsd_footprint(const ccsd_config* cfg, int inputs_on_device, int int_dtype, 
 
 int ccsd_plan_describe(const ccsd_config* cfg, int max_steps, int* kinds, int* modes, double* flops,
                        const char** names, int* n_steps) {
+    ApiScope api_scope_;
     if (!valid_cfg(cfg) || max_steps < 0 || !n_steps) return CCSD_ERR_INVALID;
     ccsd_ctx* h = new (std::nothrow) ccsd_ctx();
     if (!h) return CCSD_ERR_OOM;
@@ -2736,6 +2762,7 @@ int ccsd_plan_describe(const ccsd_config* cfg, int max_steps, int* kinds, int* m
 }
 
 int ccsd_plan_check(const ccsd_config* cfg, long long* n_launches, size_t* table_bytes) {
+    ApiScope api_scope_;
     if (!valid_cfg(cfg)) return CCSD_ERR_INVALID;
     ccsd_ctx* h = new (std::nothrow) ccsd_ctx();
     if (!h) return CCSD_ERR_OOM;
@@ -2888,6 +2915,7 @@ int oz_gemm_impl(int M, int Ncols, int K, int slices, const double* A, const dou
 extern "C" {
 
 int ccsd_oz_gemm(int M, int Ncols, int K, int slices, const double* A, const double* B, double* C) {
+    ApiScope api_scope_;
     if (M < 1 || Ncols < 1 || K < 1 || M > 4096 || Ncols > 4096 || K > 8192 || slices < 1 ||
         slices > OZ_MAX_SLICES || !A || !B || !C)
         return CCSD_ERR_INVALID;
@@ -2895,22 +2923,26 @@ int ccsd_oz_gemm(int M, int Ncols, int K, int slices, const double* A, const dou
 }
 
 int ccsd_oz_timeout_selftest(void) {
+    ApiScope api_scope_;
     std::vector<double> a(128 * 64 * 2, 1.0), c(128 * 128 * 2, 0.0);
     return oz_gemm_impl(128, 128, 64, 2, a.data(), a.data(), c.data(), 1);
 }
 
 int ccsd_tc_selftest(int M, int Ncols, int K, int nterms, unsigned long long seed, double* rel_err) {
+    ApiScope api_scope_;
     if (M < 1 || Ncols < 1 || K < 1 || M > 4096 || Ncols > 4096 || K > 4096 || (nterms != 1 && nterms != 3) || !rel_err)
         return CCSD_ERR_INVALID;
     return tc_selftest_impl(M, Ncols, K, nterms, seed, -1, rel_err);
 }
 
 int ccsd_tc_timeout_selftest(void) {
+    ApiScope api_scope_;
     double err = 0.0;
     return tc_selftest_impl(128, 128, 64, 1, 1, 1, &err);
 }
 
 int ccsd_create(const ccsd_config* cfg, const ccsd_inputs* in, void* stream, ccsd_t* out) {
+    ApiScope api_scope_;
     if (!out) return CCSD_ERR_INVALID;
     *out = nullptr;
     if (!valid_cfg(cfg) || !in || (in->int_dtype != CCSD_C128 && in->int_dtype != CCSD_C64)) return CCSD_ERR_INVALID;
@@ -2935,6 +2967,7 @@ int ccsd_create(const ccsd_config* cfg, const ccsd_inputs* in, void* stream, ccs
 }
 
 int ccsd_residual(ccsd_t h, const void* t1, const void* t2, void* r1, void* r2) {
+    ApiScope api_scope_;
     if (!h || !t1 || !t2 || !r1 || !r2) return CCSD_ERR_INVALID;
     // the kernels read and write these directly: host memory is refused, not faulted on
     if (!is_device_ptr(t1) || !is_device_ptr(t2) || !is_device_ptr(r1) || !is_device_ptr(r2)) return CCSD_ERR_INVALID;
@@ -2948,6 +2981,7 @@ int ccsd_residual(ccsd_t h, const void* t1, const void* t2, void* r1, void* r2) 
 }
 
 int ccsd_iterate(ccsd_t h, int n_iter, int* done, double* max_resid) {
+    ApiScope api_scope_;
     if (!h || n_iter < 0) return CCSD_ERR_INVALID;
     if (done) *done = 0;
     h->launches = 0;
@@ -2966,6 +3000,7 @@ int ccsd_iterate(ccsd_t h, int n_iter, int* done, double* max_resid) {
 }
 
 int ccsd_solve(ccsd_t h, int* iterations, double* max_resid) {
+    ApiScope api_scope_;
     if (!h) return CCSD_ERR_INVALID;
     int done = 0, it = 0;
     double mr = 0.0;
@@ -3004,6 +3039,7 @@ int ccsd_solve(ccsd_t h, int* iterations, double* max_resid) {
 }
 
 int ccsd_set_precision(ccsd_t h, int precision) {
+    ApiScope api_scope_;
     if (!h) return CCSD_ERR_INVALID;
     if (precision == CCSD_FP64) { h->fp32 = 0; h->oz_on = 0; }
     else if (precision == CCSD_MIXED && h->cfg.precision == CCSD_MIXED) { h->fp32 = 1; h->oz_on = 0; }
@@ -3015,6 +3051,7 @@ int ccsd_set_precision(ccsd_t h, int precision) {
 }
 
 int ccsd_energy(ccsd_t h, double* e_real, double* e_imag) {
+    ApiScope api_scope_;
     if (!h) return CCSD_ERR_INVALID;
     if (h->in32[B_OOVV])
         energy_partial<<<h->red_blocks, 256, 0, h->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_FOV_IN], h->shadow[B_OOVV],
@@ -3032,6 +3069,7 @@ int ccsd_energy(ccsd_t h, double* e_real, double* e_imag) {
 }
 
 int ccsd_get_amplitudes(ccsd_t h, void* t1, void* t2) {
+    ApiScope api_scope_;
     if (!h || !t1 || !t2) return CCSD_ERR_INVALID;
     CK(cudaMemcpyAsync(t1, h->buf[B_T1], (size_t)h->n1 * 16, cudaMemcpyDefault, h->st));
     CK(cudaMemcpyAsync(t2, h->buf[B_T2], (size_t)h->n2 * 16, cudaMemcpyDefault, h->st));
@@ -3040,6 +3078,7 @@ int ccsd_get_amplitudes(ccsd_t h, void* t1, void* t2) {
 }
 
 int ccsd_set_amplitudes(ccsd_t h, const void* t1, const void* t2) {
+    ApiScope api_scope_;
     if (!h || !t1 || !t2) return CCSD_ERR_INVALID;
     CK(cudaMemcpyAsync(h->buf[B_T1], t1, (size_t)h->n1 * 16, cudaMemcpyDefault, h->st));
     CK(cudaMemcpyAsync(h->buf[B_T2], t2, (size_t)h->n2 * 16, cudaMemcpyDefault, h->st));
@@ -3049,6 +3088,7 @@ int ccsd_set_amplitudes(ccsd_t h, const void* t1, const void* t2) {
 }
 
 int ccsd_last_launch_count(ccsd_t h, long long* launches) {
+    ApiScope api_scope_;
     if (!h || !launches) return CCSD_ERR_INVALID;
     *launches = h->launches;
     return CCSD_OK;
@@ -3056,6 +3096,7 @@ int ccsd_last_launch_count(ccsd_t h, long long* launches) {
 
 
 int ccsd_trace_enable(ccsd_t h, int enable) {
+    ApiScope api_scope_;
     if (!h) return CCSD_ERR_INVALID;
     const size_t n = h->seq.size() + 1;          // plan steps + the amplitude update
     if (enable && h->ev0.empty()) {
@@ -3072,6 +3113,7 @@ int ccsd_trace_enable(ccsd_t h, int enable) {
 }
 
 int ccsd_trace_count(ccsd_t h, int* n_steps) {
+    ApiScope api_scope_;
     if (!h || !n_steps) return CCSD_ERR_INVALID;
     *n_steps = (int)h->seq.size() + 1;
     return CCSD_OK;
@@ -3079,6 +3121,7 @@ int ccsd_trace_count(ccsd_t h, int* n_steps) {
 
 int ccsd_trace_step(ccsd_t h, int i, const char** name, long long* calls, double* total_ms,
                     double* flops, double* bytes) {
+    ApiScope api_scope_;
     if (!h || i < 0 || i > (int)h->seq.size()) return CCSD_ERR_INVALID;
     const bool upd = i == (int)h->seq.size();
     if (name) *name = upd ? "update" : h->seq[i].name;
@@ -3090,6 +3133,7 @@ int ccsd_trace_step(ccsd_t h, int i, const char** name, long long* calls, double
 }
 
 int ccsd_batch_create(int n, const ccsd_config* cfgs, const ccsd_inputs* inputs, ccsd_batch_t* out) {
+    ApiScope api_scope_;
     if (!out || n < 1 || n > 4096 || !cfgs || !inputs) return CCSD_ERR_INVALID;
     *out = nullptr;
     for (int i = 0; i < n; ++i)
@@ -3131,6 +3175,7 @@ int ccsd_batch_create(int n, const ccsd_config* cfgs, const ccsd_inputs* inputs,
 }
 
 int ccsd_batch_iterate(ccsd_batch_t B, int n_iter, int* done, double* max_resid) {
+    ApiScope api_scope_;
     if (!B || n_iter < 0) return CCSD_ERR_INVALID;
     const int f = B->fp32;
     int rc;
@@ -3170,6 +3215,7 @@ int ccsd_batch_iterate(ccsd_batch_t B, int n_iter, int* done, double* max_resid)
 }
 
 int ccsd_batch_energy(ccsd_batch_t B, double* e_real, double* e_imag) {
+    ApiScope api_scope_;
     if (!B || !e_real) return CCSD_ERR_INVALID;
     for (int i = 0; i < B->n; ++i) {
         double er = 0.0, ei = 0.0;
@@ -3182,12 +3228,14 @@ int ccsd_batch_energy(ccsd_batch_t B, double* e_real, double* e_imag) {
 }
 
 int ccsd_batch_member(ccsd_batch_t B, int i, ccsd_t* h) {
+    ApiScope api_scope_;
     if (!B || i < 0 || i >= B->n || !h) return CCSD_ERR_INVALID;
     *h = B->m[i];
     return CCSD_OK;
 }
 
 int ccsd_batch_stats(ccsd_batch_t B, long long* launches_per_iteration, int* tile_cfgs, int max_cfgs) {
+    ApiScope api_scope_;
     if (!B) return CCSD_ERR_INVALID;
     if (launches_per_iteration) {
         long long n = 0;
@@ -3204,6 +3252,7 @@ int ccsd_batch_stats(ccsd_batch_t B, long long* launches_per_iteration, int* til
 }
 
 int ccsd_batch_destroy(ccsd_batch_t B) {
+    ApiScope api_scope_;
     if (!B) return CCSD_ERR_INVALID;
     if (B->st) cudaStreamSynchronize(B->st);
     for (int f = 0; f < 2; ++f) if (B->graph[f]) cudaGraphExecDestroy(B->graph[f]);
@@ -3215,6 +3264,7 @@ int ccsd_batch_destroy(ccsd_batch_t B) {
 }
 
 int ccsd_server_create(size_t hbm_budget_bytes, int max_slots, ccsd_server_t* out) {
+    ApiScope api_scope_;
     if (!out || max_slots < 1 || max_slots > 1024 || hbm_budget_bytes == 0) return CCSD_ERR_INVALID;
     ccsd_server* S = new (std::nothrow) ccsd_server();
     if (!S) return CCSD_ERR_OOM;
@@ -3233,6 +3283,7 @@ int ccsd_server_create(size_t hbm_budget_bytes, int max_slots, ccsd_server_t* ou
 }
 
 int ccsd_submit(ccsd_server_t S, const ccsd_config* cfg, const ccsd_inputs* in, uint64_t* request_id) {
+    ApiScope api_scope_;
     if (!S || !cfg || !in || !request_id || !valid_cfg(cfg) || (in->int_dtype != CCSD_C128 && in->int_dtype != CCSD_C64))
         return CCSD_ERR_INVALID;
     const size_t bytes = request_bytes(*cfg, *in);
@@ -3256,6 +3307,7 @@ int ccsd_submit(ccsd_server_t S, const ccsd_config* cfg, const ccsd_inputs* in, 
 }
 
 int ccsd_poll(ccsd_server_t S, uint64_t id, int* state, double* e_corr, double* t_converge_s, int* iterations) {
+    ApiScope api_scope_;
     if (!S) return CCSD_ERR_INVALID;
     std::lock_guard<std::mutex> lock(S->mu);
     auto it = S->all.find(id);
@@ -3269,6 +3321,7 @@ int ccsd_poll(ccsd_server_t S, uint64_t id, int* state, double* e_corr, double* 
 }
 
 int ccsd_server_stats(ccsd_server_t S, int* active, int* queued, size_t* admitted_bytes) {
+    ApiScope api_scope_;
     if (!S) return CCSD_ERR_INVALID;
     std::lock_guard<std::mutex> lock(S->mu);
     if (active) *active = (int)S->active.size();
@@ -3278,6 +3331,7 @@ int ccsd_server_stats(ccsd_server_t S, int* active, int* queued, size_t* admitte
 }
 
 int ccsd_server_destroy(ccsd_server_t S) {
+    ApiScope api_scope_;
     if (!S) return CCSD_ERR_INVALID;
     {
         std::lock_guard<std::mutex> lock(S->mu);
@@ -3291,6 +3345,7 @@ int ccsd_server_destroy(ccsd_server_t S) {
 }
 
 int ccsd_destroy(ccsd_t h) {
+    ApiScope api_scope_;
     if (!h) return CCSD_ERR_INVALID;
     if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
     for (void* p : h->owned) cudaFree(p);
@@ -3302,6 +3357,8 @@ int ccsd_destroy(ccsd_t h) {
     delete h;
     return CCSD_OK;
 }
+
+const char* ccsd_last_error(void) { return g_errbuf; }
 
 const char* ccsd_strerror(int code) {
     switch (code) {

@@ -252,3 +252,40 @@ def test_binding_checks_sizes_dtypes_and_devices():
         binding.check_amplitudes(n, ((t2, "t1"),), "t", False)
     with pytest.raises(binding.CCSDError):
         binding._ptr(np.zeros((4, 4), np.complex128)[:, ::2], "t")
+
+
+def test_last_error_names_the_refused_field(libpath):
+    """ccsd_last_error says why a config is refused; the binding's CCSDError carries it,
+    and the next successful call on the thread clears it."""
+    from paper_1911_00242_gb300 import binding
+    lib = binding.load(libpath)
+    n = ctypes.c_size_t(0)
+    cases = [(dict(grid=(2, 1, 1), o=2, v=3, diis_depth=1), b"diis_depth"),
+             (dict(grid=(2, 1, 1), o=2, v=3, conv_tol=float("nan")), b"conv_tol"),
+             (dict(grid=(2, 1, 1), o=2, v=100, precision=binding.CCSD_OZAKI), b"nvir <= 96"),
+             (dict(grid=(2, 1, 1), o=2, v=3, precision=binding.CCSD_OZAKI, oz_slices=2), b"oz_slices"),
+             (dict(grid=(2, 1, 1), o=2, v=3, polish_precision=binding.CCSD_OZAKI), b"polish_precision"),
+             (dict(grid=(65, 1, 1), o=2, v=3), b"nk_dims")]
+    for kw, word in cases:
+        kw = dict(kw)
+        cfg = binding.make_config(kw.pop("grid"), kw.pop("o"), kw.pop("v"), **kw)
+        assert lib.ccsd_footprint(ctypes.byref(cfg), 1, binding.CCSD_C128, ctypes.byref(n)) == binding.CCSD_ERR_INVALID
+        assert word in lib.ccsd_last_error(), (word, lib.ccsd_last_error())
+        with pytest.raises(binding.CCSDError) as e:
+            binding.check(lib.ccsd_footprint(ctypes.byref(cfg), 1, binding.CCSD_C128, ctypes.byref(n)), "footprint")
+        assert word.decode() in str(e.value)
+    good = binding.make_config((2, 1, 1), 2, 3)
+    assert lib.ccsd_footprint(ctypes.byref(good), 1, binding.CCSD_C128, ctypes.byref(n)) == 0
+    assert lib.ccsd_last_error() == b""
+
+
+def test_plans_beyond_32_bit_tables_are_refused_with_a_reason(libpath):
+    """Tensor-core operand tables hold 32-bit row indices: a plan that would need more is
+    refused on the host, with the reason (the problem is far beyond device memory)."""
+    from paper_1911_00242_gb300 import binding
+    lib = binding.load(libpath)
+    for prec, grid, o, v in ((binding.CCSD_MIXED, (2, 2, 4), 33, 104), (binding.CCSD_OZAKI, (4, 2, 5), 2, 53)):
+        cfg = binding.make_config(grid, o, v, precision=prec, lean=1)
+        n, tb = ctypes.c_longlong(0), ctypes.c_size_t(0)
+        assert lib.ccsd_plan_check(ctypes.byref(cfg), ctypes.byref(n), ctypes.byref(tb)) == binding.CCSD_ERR_INVALID
+        assert b"32-bit" in lib.ccsd_last_error(), lib.ccsd_last_error()
