@@ -3138,8 +3138,10 @@ int ccsd_batch_create(int n, const ccsd_config* cfgs, const ccsd_inputs* inputs,
     *out = nullptr;
     for (int i = 0; i < n; ++i)
         if (cfgs[i].precision != cfgs[0].precision || cfgs[i].diis_depth != 0 || cfgs[i].precision == CCSD_OZAKI ||
-            cfgs[i].polish_precision != CCSD_FP64)
+            cfgs[i].polish_precision != CCSD_FP64) {
+            refuse("batch members share one precision (FP64 or mixed, FP64 polish) and use diis_depth 0");
             return CCSD_ERR_INVALID;
+        }
     ccsd_batch* B = new (std::nothrow) ccsd_batch();
     if (!B) return CCSD_ERR_OOM;
     B->n = n;
@@ -3156,7 +3158,10 @@ int ccsd_batch_create(int n, const ccsd_config* cfgs, const ccsd_inputs* inputs,
         std::vector<size_t> gs;
         for (size_t si = 0; si < B->m[i]->seq.size(); ++si)
             if (B->m[i]->seq[si].kind == 0 && step_active(B->m[i], B->m[i]->seq[si])) gs.push_back(si);
-        if (i > 0 && gs.size() != B->gemm_steps[0].size()) return fail(CCSD_ERR_INVALID);
+        if (i > 0 && gs.size() != B->gemm_steps[0].size()) {
+            refuse("batch members have different contraction sequences");
+            return fail(CCSD_ERR_INVALID);
+        }
         B->gemm_steps.push_back(gs);
     }
     void* p = nullptr;
