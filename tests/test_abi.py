@@ -289,3 +289,31 @@ def test_plans_beyond_32_bit_tables_are_refused_with_a_reason(libpath):
         n, tb = ctypes.c_longlong(0), ctypes.c_size_t(0)
         assert lib.ccsd_plan_check(ctypes.byref(cfg), ctypes.byref(n), ctypes.byref(tb)) == binding.CCSD_ERR_INVALID
         assert b"32-bit" in lib.ccsd_last_error(), lib.ccsd_last_error()
+
+
+def test_random_plans_in_bounds(libpath):
+    """A seeded sweep over configurations of every form, layout and DIIS depth: each plan
+    builds, every launch stays inside its buffers (ccsd_plan_check), and the footprint of
+    the same config is defined."""
+    import random
+    from paper_1911_00242_gb300 import binding
+    lib = binding.load(libpath)
+    rng = random.Random(2024)
+    checked = 0
+    while checked < 300:
+        grid = tuple(rng.choice([1, 1, 2, 2, 3]) for _ in range(3))
+        N = grid[0] * grid[1] * grid[2]
+        o, v = rng.randint(1, 10), rng.randint(1, 34)
+        if N ** 3 * v ** 4 * 16 > 20e9:
+            continue
+        prec = rng.choice([binding.CCSD_FP64, binding.CCSD_MIXED, binding.CCSD_OZAKI])
+        pol = binding.CCSD_OZAKI if prec == binding.CCSD_MIXED and rng.random() < 0.4 else binding.CCSD_FP64
+        sl = rng.choice([0, 3, 8]) if binding.CCSD_OZAKI in (prec, pol) else 0
+        cfg = binding.make_config(grid, o, v, precision=prec, lean=rng.choice([0, 1]), oz_slices=sl,
+                                  polish_precision=pol, diis_depth=rng.choice([0, 2, 6, 8]))
+        n, tb, fp = ctypes.c_longlong(0), ctypes.c_size_t(0), ctypes.c_size_t(0)
+        assert lib.ccsd_plan_check(ctypes.byref(cfg), ctypes.byref(n), ctypes.byref(tb)) == 0, \
+            (grid, o, v, prec, pol, lib.ccsd_last_error())
+        assert lib.ccsd_footprint(ctypes.byref(cfg), 1, binding.CCSD_C128, ctypes.byref(fp)) == 0
+        assert n.value > 0 and fp.value > 0
+        checked += 1
