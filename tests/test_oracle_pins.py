@@ -9,7 +9,8 @@
    localized basis (orbital-rotation invariance).
 5. Form A (Sec. 2) = form B (Sec. 3.3) on random unconverged amplitudes.
 6. Invariants: antisymmetry of R2, time reversal, coupling-constant scaling.
-7. Convergence with and without DIIS to the same fixed point (Sec. 4.4).
+7. Convergence with and without DIIS to the same fixed point (Sec. 4.4), and the
+   finite termination of DIIS on linear problems (its equivalence with GMRES).
 """
 import numpy as np
 import pytest
@@ -219,3 +220,47 @@ def test_block_oracle_equals_full_oracle(spec):
         for kj in range(N):
             for ka in range(N):
                 np.testing.assert_allclose(B.r2(ki, kj, ka), R2[ki, kj, ka], rtol=0, atol=1e-14)
+
+
+def _linear_problem(rng, n, complex_=False):
+    M = rng.standard_normal((n, n)) + (1j * rng.standard_normal((n, n)) if complex_ else 0)
+    A = np.diag(rng.uniform(3, 5, n)) + 0.3 * (M + M.conj().T)
+    b = rng.standard_normal(n) + (1j * rng.standard_normal(n) if complex_ else 0)
+    return A, b, np.real(np.diag(A)).copy(), np.linalg.solve(A, b)
+
+
+def _run_diis(diis, A, b, d, updates):
+    """The driver's update (x + r/D, error r/D) on the linear problem A x = b."""
+    x = np.zeros(len(b), np.result_type(A, b))
+    for _ in range(updates):
+        r = b - A @ x
+        g = x + r / d
+        x = diis.update(g, r / d) if diis is not None else g
+    return x
+
+
+def test_diis_terminates_on_linear_problems():
+    """DIIS (Pulay extrapolation on the update errors, coefficients summing to one) is
+    Anderson acceleration with full history, which on a linear fixed-point problem is
+    equivalent to GMRES (Walker and Ni, SIAM J. Numer. Anal. 49 (2011) 1715): in exact
+    arithmetic it reaches the solution of an n-dimensional real problem after n + 1
+    updates, while the plain Jacobi step still converges linearly.  A Gram matrix of the
+    amplitudes instead of the errors (a planted mistake) does not terminate."""
+    rng = np.random.default_rng(31)
+    for n in (3, 4, 6):
+        A, b, d, xs = _linear_problem(rng, n)
+        x = _run_diis(driver.DIIS(n + 2), A, b, d, n + 1)
+        assert np.linalg.norm(x - xs) < 1e-12 * np.linalg.norm(xs)
+        assert np.linalg.norm(_run_diis(None, A, b, d, n + 1) - xs) > 1e-6 * np.linalg.norm(xs)
+
+        class GramOfAmplitudes(driver.DIIS):
+            def update(self, x, e):
+                return driver.DIIS.update(self, x, x)
+
+        x = _run_diis(GramOfAmplitudes(n + 2), A, b, d, n + 1)
+        assert np.linalg.norm(x - xs) > 1e-3 * np.linalg.norm(xs)
+    # complex amplitudes: the real Gram matrix B_ij = Re <e_i|e_j> treats C^n as R^2n
+    n = 4
+    A, b, d, xs = _linear_problem(rng, n, complex_=True)
+    x = _run_diis(driver.DIIS(2 * n + 2), A, b, d, 2 * n + 1)
+    assert np.linalg.norm(x - xs) < 1e-12 * np.linalg.norm(xs)
