@@ -75,7 +75,7 @@ typedef struct {
     int    nk_dims[3];    /* k grid (n1, n2, n3), each >= 1                     */
     int    nocc, nvir;    /* occupied / virtual spin orbitals per k, >= 1       */
     int    precision;     /* CCSD_FP64, CCSD_MIXED or CCSD_OZAKI                */
-    int    diis_depth;    /* 0 = plain successive substitution (paper Sec. 4.4.12);
+    int    diis_depth;    /* 0 = plain successive substitution (paper Sec. 4.4.18);
                              2..8 = Pulay DIIS over that many updates            */
     int    max_iter;      /* used by ccsd_solve, >= 0                           */
     double conv_tol;      /* max|R1| and max|R2| threshold, Eqs. (criterion_single,
@@ -183,7 +183,7 @@ int ccsd_residual(ccsd_t h, const void* t1, const void* t2, void* r1, void* r2);
 
 /* Up to n_iter iterations on the handle's amplitudes.  Each computes R(t);
  * if max(max|R1|, max|R2|) < conv_tol it sets *done = 1 and stops without
- * updating; otherwise t <- t + R/D (paper Sec. 4.4.13, D from the Fock
+ * updating; otherwise t <- t + R/D (paper Sec. 4.4.19, D from the Fock
  * diagonal), followed by DIIS extrapolation when diis_depth > 0.
  * *max_resid receives the last max|R| (may be NULL).  Returns
  * CCSD_ERR_DIVERGED if R is not finite. */

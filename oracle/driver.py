@@ -2,7 +2,7 @@
 
 * start: t0 = f(0), i.e. one update from t = 0 (Sec. 3.2.2);
 * update: t <- t + R / D with D_i^a = f_ii - f^aa and
-  D_ij^ab = f_ii + f_jj - f^aa - f^bb (Eqs. in Sec. 4.4.13);
+  D_ij^ab = f_ii + f_jj - f^aa - f^bb (Eqs. in Sec. 4.4.19);
 * stop when max|R1| < eps and max|R2| < eps (Eqs. criterion_single/double);
 * optional DIIS (not in the paper, which uses plain successive substitution):
   Pulay extrapolation over the last m updates with error vectors e = R / D,

@@ -452,7 +452,7 @@ def residual_program(rk: Rank, t1, T):
         ka_ = (ki + d) % N
         for ke in R:
             Sc[(ki, kj, ka_)] += ein("ijef,abef->ijab", T_ij[(ki, kj, ke)], got[ke])
-    # S2-check to (ki, ka) (Sec. 4.4.9), horizontal index change
+    # S2-check to (ki, ka) (Sec. 4.4.10), horizontal index change
     out = {}
     for ka_ in R:
         out.setdefault(ka_, {})[(ki, kj, ka_)] = Sc[(ki, kj, ka_)]
@@ -460,7 +460,7 @@ def residual_program(rk: Rank, t1, T):
         for key, blk in blocks.items():
             S2[key] += blk
 
-    # ---- Sec. 4.4.10-4.4.11: t2 to (kb, ka); X~ on rank (ki, kj)
+    # ---- Sec. 4.4.11-4.4.12: t2 to (kb, ka); X~ on rank (ki, kj)
     out = {}
     for kj_ in R:
         kb_ = k4(a_, kj_, b_)
@@ -483,7 +483,7 @@ def residual_program(rk: Rank, t1, T):
         for ke in R:
             X[kmm] += ein("ijef,mnef->mnij", T_ij[(ki, kj, ke)], got[ke])
 
-    # ---- Sec. 4.4.13: Y~_mnij on rank (ki, kj): V~, diagonal swap, Y~
+    # ---- Sec. 4.4.14: Y~_mnij on rank (ki, kj): V~, diagonal swap, Y~
     Vo = {}
     for kmm in R:
         kn = k4(ki, kj, kmm)
@@ -497,7 +497,7 @@ def residual_program(rk: Rank, t1, T):
         y += ein("ic,jd,mncd->mnij", t1[ki], t1[kj], rk.I("oovv", kmm, kn, ki))
         Yo[kmm] = 0.5 * y
 
-    # ---- Sec. 4.4.12-4.4.13: A-tilde + A-hat on rank (kb, ka)
+    # ---- Sec. 4.4.13-4.4.16: A-tilde + A-hat on rank (kb, ka)
     kb, ka = a_, b_
     Sh = {}
     for ki_ in R:
@@ -533,7 +533,7 @@ def residual_program(rk: Rank, t1, T):
     for ki_ in R:
         kj_ = k4(ka, kb, ki_)
         Sh[(ki_, kj_, ka)] -= Ghsw[(ki_, kj_, kb)].transpose(0, 1, 3, 2)
-    # S2-hat to (ki, ka) (Sec. 4.4.14), vertical index change
+    # S2-hat to (ki, ka) (Sec. 4.4.17), vertical index change
     out = {}
     for ki_ in R:
         kj_ = k4(ka, kb, ki_)
@@ -545,7 +545,7 @@ def residual_program(rk: Rank, t1, T):
 
 
 def iterate_program(rk: Rank, t1, T, n_iter):
-    """n_iter Jacobi updates t <- t + R/D (Sec. 4.4.15-16) from the given amplitudes,
+    """n_iter Jacobi updates t <- t + R/D (Sec. 4.4.18-4.4.19) from the given amplitudes,
     each with the global max|R| (the convergence test).  Returns (t1, T, norms)."""
     N, km = rk.N, rk.km
     norms = []

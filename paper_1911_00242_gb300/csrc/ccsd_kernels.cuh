@@ -150,7 +150,7 @@ __global__ void maxabs_partial(const double2* __restrict__ x, long long n, doubl
     if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
 }
 
-// t1 += R1 / D1, t2 += R2 / D2 (paper Sec. 4.4.13), D from the Fock diagonal
+// t1 += R1 / D1, t2 += R2 / D2 (paper Sec. 4.4.19), D from the Fock diagonal
 // eo[k][i], ev[k][a].  When err != nullptr also stores e = R / D (DIIS error).
 __global__ void update_kernel(double2* __restrict__ t1, double2* __restrict__ t2,
                               const double2* __restrict__ R1, const double2* __restrict__ R2,
