@@ -1,7 +1,36 @@
-"""Shared test helpers: dense (unfolded) views of a synthetic problem."""
+"""Shared test helpers: dense (unfolded) views of a synthetic problem, and host builds
+of the kernels' host-callable headers."""
+import ctypes
+import os
+import shutil
+import subprocess
+
 import numpy as np
+import pytest
 
 import ccsd_synth as cs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def build_host_probe(source, name):
+    """Compiles tests/<source> (a host probe of a kernel header) into the repository's
+    git-ignored _build/ folder and loads it; skips without nvcc.  -ffp-contract=off keeps
+    every host floating-point operation a single rounding, as the device intrinsics are."""
+    home = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    nvcc = os.path.join(home, "bin", "nvcc")
+    nvcc = nvcc if os.path.exists(nvcc) else shutil.which("nvcc")
+    if not nvcc:
+        pytest.skip("nvcc not available")
+    outdir = os.path.join(ROOT, "_build", "probes")
+    os.makedirs(outdir, exist_ok=True)
+    out = os.path.join(outdir, f"lib{name}_{os.getpid()}.so")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17", "-shared",
+                    "-Xcompiler", "-fPIC,-ffp-contract=off", "-o", out, os.path.join(ROOT, "tests", source)],
+                   check=True, capture_output=True)
+    lib = ctypes.CDLL(out)
+    os.unlink(out)          # the loaded image stays mapped
+    return lib
 
 
 def dense_bloch(spec):

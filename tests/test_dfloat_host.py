@@ -14,34 +14,17 @@ The host build of the same source uses plain FP32 operations and fmaf, compiled 
 * a planted mistake (the product without its low-part terms) fails the product bound.
 """
 import ctypes
-import os
-import shutil
-import subprocess
 from fractions import Fraction
 
 import numpy as np
 import pytest
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-PROBE = os.path.join(ROOT, "tests", "df_host_probe.cu")
-
-
-def _nvcc():
-    home = os.environ.get("CUDA_HOME", "/usr/local/cuda")
-    p = os.path.join(home, "bin", "nvcc")
-    return p if os.path.exists(p) else shutil.which("nvcc")
+from helpers import build_host_probe
 
 
 @pytest.fixture(scope="module")
-def probe(tmp_path_factory):
-    nvcc = _nvcc()
-    if not nvcc:
-        pytest.skip("nvcc not available")
-    out = str(tmp_path_factory.mktemp("dfprobe") / "libdfprobe.so")
-    cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17", "-shared",
-           "-Xcompiler", "-fPIC,-ffp-contract=off", "-o", out, PROBE]
-    subprocess.run(cmd, check=True, capture_output=True)
-    lib = ctypes.CDLL(out)
+def probe():
+    lib = build_host_probe("df_host_probe.cu", "dfprobe")
     f = ctypes.POINTER(ctypes.c_float)
     d = ctypes.POINTER(ctypes.c_double)
     for name in ("probe_df_add", "probe_df_sub", "probe_df_mul"):

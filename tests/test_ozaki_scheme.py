@@ -34,18 +34,17 @@ is therefore 2^{Ea+Eb-7s} (1 + 2^{-7s-2} + c_s / 4).
 import ctypes
 import os
 import re
-import shutil
-import subprocess
 from fractions import Fraction
 
 import numpy as np
 import pytest
 
+from helpers import build_host_probe
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1911_00242_gb300", "csrc")
 HEADERS = [os.path.join(CSRC, "ozaki.cuh"), os.path.join(CSRC, "ozaki_split.cuh"),
            os.path.join(CSRC, "ozaki_schedule.cuh")]
-PROBE = os.path.join(ROOT, "tests", "oz_split_probe.cu")
 
 
 def _kernel_constants():
@@ -154,17 +153,10 @@ def test_split_zero_and_clamped_rows():
 
 # ---------------------------------------------------------------- the kernel's own split code
 @pytest.fixture(scope="module")
-def probe(tmp_path_factory):
-    """csrc/ozaki_split.cuh built for the host (the same source the embedding kernels use)."""
-    home = os.environ.get("CUDA_HOME", "/usr/local/cuda")
-    nvcc = os.path.join(home, "bin", "nvcc")
-    nvcc = nvcc if os.path.exists(nvcc) else shutil.which("nvcc")
-    if not nvcc:
-        pytest.skip("nvcc not available")
-    out = str(tmp_path_factory.mktemp("ozprobe") / "libozprobe.so")
-    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17", "-shared",
-                    "-Xcompiler", "-fPIC,-ffp-contract=off", "-o", out, PROBE], check=True, capture_output=True)
-    lib = ctypes.CDLL(out)
+def probe():
+    """csrc/ozaki_split.cuh and csrc/ozaki_schedule.cuh built for the host (the same
+    source the kernels use)."""
+    lib = build_host_probe("oz_split_probe.cu", "ozprobe")
     dp = ctypes.POINTER(ctypes.c_double)
     lib.probe_row_exponent.argtypes = [dp, ctypes.c_int]
     lib.probe_row_exponent.restype = ctypes.c_int

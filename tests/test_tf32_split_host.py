@@ -15,31 +15,20 @@ TF32 rounding unit; FP32 rounds at 2^-24):
   planted mistake) is off by about 2^-11 and fails it.
 """
 import ctypes
-import os
-import shutil
-import subprocess
 from fractions import Fraction
 
 import numpy as np
 import pytest
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-PROBE = os.path.join(ROOT, "tests", "tf32_split_probe.cu")
+from helpers import build_host_probe
+
 F = ctypes.POINTER(ctypes.c_float)
 D = ctypes.POINTER(ctypes.c_double)
 
 
 @pytest.fixture(scope="module")
-def probe(tmp_path_factory):
-    home = os.environ.get("CUDA_HOME", "/usr/local/cuda")
-    nvcc = os.path.join(home, "bin", "nvcc")
-    nvcc = nvcc if os.path.exists(nvcc) else shutil.which("nvcc")
-    if not nvcc:
-        pytest.skip("nvcc not available")
-    out = str(tmp_path_factory.mktemp("tf32probe") / "libtf32probe.so")
-    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17", "-shared",
-                    "-Xcompiler", "-fPIC,-ffp-contract=off", "-o", out, PROBE], check=True, capture_output=True)
-    lib = ctypes.CDLL(out)
+def probe():
+    lib = build_host_probe("tf32_split_probe.cu", "tf32probe")
     lib.probe_tf32_round.argtypes = [F, F, ctypes.c_int]
     lib.probe_split_tf32f.argtypes = [F, F, F, ctypes.c_int]
     lib.probe_split_tf32.argtypes = [D, F, F, ctypes.c_int]
