@@ -142,9 +142,10 @@ int ccsd_plan_check(const ccsd_config* cfg, long long* n_launches, size_t* table
  * the step kind (0 FP64/FP32 GEMM, 1 copy, 2 permutation, 3 tau, 4 antisymmetrize,
  * 5 tensor-core operand embedding, 6 tensor-core GEMM, 7 zero, 9 complex64 copy,
  * 10 W' formation, 11 fused Fock terms, 12 transposed F'vv), the iterations it
- * runs in (mode 0 all; 1 without tensor cores; 2 with tensor cores; 3 mixed
- * iterations only; 4 all but mixed iterations), its algorithmic real flops and
- * its name (static strings owned by the library). */
+ * runs in (mode 0 all; 1 without tensor cores; 2 split-TF32 tensor-core steps of
+ * mixed iterations; 3 mixed iterations only; 4 all but mixed iterations; 5 Ozaki
+ * tensor-core steps of Ozaki iterations), its algorithmic real flops and its
+ * name (static strings owned by the library). */
 int ccsd_plan_describe(const ccsd_config* cfg, int max_steps, int* kinds, int* modes, double* flops,
                        const char** names, int* n_steps);
 
@@ -229,6 +230,10 @@ int ccsd_trace_count(ccsd_t h, int* n_steps);
 int ccsd_trace_step(ccsd_t h, int i, const char** name, long long* calls, double* total_ms,
                     double* flops, double* bytes);
 
+/* Waits for the handle's stream, then frees everything the handle owns: its
+ * device memory (amplitudes, residuals, work buffers, copied inputs, plan
+ * tables), events and pinned buffers, and its count on a host vvvv registration.
+ * Borrowed inputs are left untouched.  CCSD_ERR_INVALID for NULL. */
 int ccsd_destroy(ccsd_t h);
 
 /* ---------------------------------------------------------------- batched form
