@@ -256,6 +256,7 @@ int ccsd_batch_energy(ccsd_batch_t b, double* e_real, double* e_imag);
 int ccsd_batch_member(ccsd_batch_t b, int i, ccsd_t* h);
 /* Kernel launches per iteration and the autotuned tile shape of each grouped step. */
 int ccsd_batch_stats(ccsd_batch_t b, long long* launches_per_iteration, int* tile_cfgs, int max_cfgs);
+/* Destroys every member handle and the batch's graphs, buffers and stream. */
 int ccsd_batch_destroy(ccsd_batch_t b);
 
 /* ---------------------------------------------------------------- serving form
@@ -266,20 +267,27 @@ int ccsd_batch_destroy(ccsd_batch_t b);
  * solves advance together: each round enqueues one iteration of every solve
  * (their kernels run concurrently) and then completes them.  Converged solves
  * retire and free their memory for the queue.  A solve runs like ccsd_solve
- * (mixed iterations, then polish_iters FP64 iterations, for CCSD_MIXED).
+ * (mixed iterations, then polish_iters iterations in polish_precision, for
+ * CCSD_MIXED).
  * The inputs a request points to must stay valid until it is done (host
  * inputs are copied when the request is admitted). */
 typedef struct ccsd_server* ccsd_server_t;
+/* Starts the loop on the current device: hbm_budget_bytes > 0, 1 <= max_slots <= 1024. */
 int ccsd_server_create(size_t hbm_budget_bytes, int max_slots, ccsd_server_t* out);
+/* Queues one solve (config and input pointers are copied into the request; the
+ * data they point to is not) and returns its id.  CCSD_ERR_INVALID for a bad
+ * config or after ccsd_server_destroy began. */
 int ccsd_submit(ccsd_server_t s, const ccsd_config* cfg, const ccsd_inputs* in, uint64_t* request_id);
 /* state: 0 queued, 1 running, 2 done, < 0 the CCSD_ERR_* code it ended with
  * (CCSD_ERR_OOM: larger than the whole budget).  e_corr: energy per unit cell
  * (done only); t_converge_s: submission to completion (finished only). */
 int ccsd_poll(ccsd_server_t s, uint64_t id, int* state, double* e_corr, double* t_converge_s, int* iterations);
+/* Running solves, queued solves and the device bytes admitted solves hold. */
 int ccsd_server_stats(ccsd_server_t s, int* active, int* queued, size_t* admitted_bytes);
 /* Finishes the admitted solves, cancels the queued ones, joins the thread. */
 int ccsd_server_destroy(ccsd_server_t s);
 
+/* A static description of a CCSD_* code. */
 const char* ccsd_strerror(int code);
 
 /* Why the most recent failing call on this host thread failed, where the library
