@@ -18,8 +18,6 @@ Modules
   fci         two-electron full CI (exactness pin)
   driver      t0 = f(0), Jacobi update t + R/D, convergence test (Sec. 4.4),
               DIIS, correlation energy
-The oracle is test infrastructure: the tests, the smoke check and the benchmark's
-CPU baseline use it; the product path never does.
 
 Every hot-path function is pinned by a test that does not reuse it (MP2
 closed form, two-electron FCI, molecular limit, supercell unfolding in two
