@@ -2,7 +2,9 @@
 
 Each case monkeypatches one plausible slip into the form-A oracle -- a dropped
 term, a wrong factor, a missing conjugate, a wrong momentum label -- and checks
-that the two-electron FCI pin or the unfolded-supercell pin sees it."""
+that the two-electron FCI pin or the unfolded-supercell pin sees it.  Slips in
+form B -- the literal sign of Eq. def_F_oo, a dropped part of Eq. EqDouble -- are
+caught by form A = form B."""
 import numpy as np
 import pytest
 
@@ -95,3 +97,48 @@ def test_wrong_momentum_label_is_caught(monkeypatch):
     monkeypatch.setattr(ccsd_k.Integrals, "get", get)
     spec = cs.SynthSpec((3, 1, 1), 2, 3, 44, time_reversal=False)
     assert _unfold_gap(spec) > 1e-8
+
+
+# ---------------------------------------------------------------- form B readings
+def _form_gap(spec):
+    """max |R(form A) - R(form B)| on random amplitudes."""
+    from oracle import ccsd_k_rearranged as form_b
+    P = ccsd_k.Problem(spec.grid, spec.nocc, spec.nvir, cs.generate(spec))
+    t1, t2 = cs.random_amplitudes(spec, 6)
+    a1, a2 = ccsd_k.residual(P, t1, t2)
+    b1, b2 = form_b.residual(P, t1, t2)
+    return max(abs(a1 - b1).max(), abs(a2 - b2).max())
+
+
+SPEC_B = cs.SynthSpec((2, 2, 1), 2, 3, 47, time_reversal=False, fock_offdiag=0.05)
+
+
+def test_form_b_baseline():
+    assert _form_gap(SPEC_B) < 1e-12
+
+
+def test_f_oo_sign_reading_is_pinned(monkeypatch):
+    """Reading G1: Eq. def_F_oo taken literally, with (f - K~) in its t1 term instead of
+    (f + K~), breaks form A = form B."""
+    from oracle import ccsd_k_rearranged as form_b
+    orig = form_b.fock_tilde
+
+    def literal(P, t1, t2):
+        Foo, Fvv, Fov = orig(P, t1, t2)
+        K = form_b._k_tilde(P, t1)
+        Foo = Foo.copy()
+        for k in P.km:
+            Foo[k] -= np.einsum("qc,pc->pq", t1[k], K[k])     # 1/2 t1 (f + K~) -> 1/2 t1 (f - K~)
+        return Foo, Fvv, Fov
+
+    monkeypatch.setattr(form_b, "fock_tilde", literal)
+    assert _form_gap(SPEC_B) > 1e-8
+
+
+@pytest.mark.parametrize("part", ["a_bar", "a_check", "a_tilde", "a_hat"])
+def test_each_part_of_eq_double_is_pinned(monkeypatch, part):
+    """Dropping any of the four parts of Eq. EqDouble breaks form A = form B."""
+    from oracle import ccsd_k_rearranged as form_b
+    orig = getattr(form_b, part)
+    monkeypatch.setattr(form_b, part, lambda *a: 0.0 * orig(*a))
+    assert _form_gap(SPEC_B) > 1e-8
