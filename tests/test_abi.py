@@ -317,3 +317,29 @@ def test_random_plans_in_bounds(libpath):
         assert lib.ccsd_footprint(ctypes.byref(cfg), 1, binding.CCSD_C128, ctypes.byref(fp)) == 0
         assert n.value > 0 and fp.value > 0
         checked += 1
+
+
+def test_contraction_flops_scale_as_nk4():
+    """The paper's cost claim: at fixed bands the contractions grow as N_k^4.  From the
+    host-built plan (ccsd_plan_describe, FP64 steps): the ring is exactly 8 N_k^4 o^3 v^3
+    real flops; the antisymmetry-packed ladder and hole-hole contractions pack pairs of
+    combined (k, orbital) indices, so their N_k^4 ratio approaches a constant near
+    (v / (v - 1))^2 from 1."""
+    from collections import defaultdict
+    from paper_1911_00242_gb300 import binding
+    o, v = 4, 12
+    flops = {}
+    for grid in [(1, 1, 1), (2, 1, 1), (2, 2, 1), (3, 1, 1), (2, 2, 2), (3, 3, 1)]:
+        agg = defaultdict(float)
+        for name, kind, mode, fl in binding.plan_describe(grid, o, v):
+            if mode in (0, 1):
+                agg[name] += fl
+        N = grid[0] * grid[1] * grid[2]
+        flops[N] = agg
+        assert agg["ring"] == 8.0 * N ** 4 * o ** 3 * v ** 3
+    prev = {"ladder": 1.0, "hole_hole": 1.0}
+    for N in sorted(flops):
+        for name in prev:
+            r = flops[N][name] / flops[1][name] / N ** 4
+            assert prev[name] - 1e-12 <= r <= 1.5, (name, N, r)      # non-decreasing, bounded
+            prev[name] = r
