@@ -29,6 +29,7 @@
 #include "tcgemm.cuh"
 #include "ozaki.cuh"
 #include "zgemm_kb.cuh"
+#include "diis.h"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -2541,32 +2542,11 @@ int iter_end(ccsd_ctx* h, int* done, double* max_resid) {
         if (m < 2) {
             cb.m = 1; cb.x[0] = x; cb.c[0] = 1.0;
         } else {
-            // Pulay: [B -1; -1 0][c; l] = [0; -1], solved by Gaussian elimination with pivoting
-            const int S = m + 1;
-            std::vector<double> A((size_t)S * S, 0.0), b((size_t)S, 0.0);
-            for (int i = 0; i < m; ++i) for (int j = 0; j < m; ++j) A[(size_t)i * S + j] = h->gram[i][j];
-            for (int i = 0; i < m; ++i) { A[(size_t)i * S + m] = -1.0; A[(size_t)m * S + i] = -1.0; }
-            b[(size_t)m] = -1.0;
-            for (int c = 0; c < S; ++c) {
-                int p = c;
-                for (int r = c + 1; r < S; ++r) if (std::fabs(A[(size_t)r * S + c]) > std::fabs(A[(size_t)p * S + c])) p = r;
-                if (p != c) { for (int k = 0; k < S; ++k) std::swap(A[(size_t)c * S + k], A[(size_t)p * S + k]); std::swap(b[c], b[p]); }
-                const double piv = A[(size_t)c * S + c];
-                if (piv == 0.0) return CCSD_ERR_DIVERGED;
-                for (int r = c + 1; r < S; ++r) {
-                    const double f = A[(size_t)r * S + c] / piv;
-                    for (int k = c; k < S; ++k) A[(size_t)r * S + k] -= f * A[(size_t)c * S + k];
-                    b[r] -= f * b[c];
-                }
-            }
-            std::vector<double> xs((size_t)S, 0.0);
-            for (int r = S - 1; r >= 0; --r) {
-                double s = b[r];
-                for (int k = r + 1; k < S; ++k) s -= A[(size_t)r * S + k] * xs[k];
-                xs[r] = s / A[(size_t)r * S + r];
-            }
+            // Pulay: [B -1; -1 0][c; l] = [0; -1]
+            double cs[8];
+            if (!diis_coefficients(h->gram, m, cs)) { refuse("the DIIS system is singular"); return CCSD_ERR_DIVERGED; }
             cb.m = m;
-            for (int j = 0; j < m; ++j) { cb.x[j] = h->hx[j]; cb.c[j] = xs[j]; }
+            for (int j = 0; j < m; ++j) { cb.x[j] = h->hx[j]; cb.c[j] = cs[j]; }
         }
         combo_unpack<<<ew_grid(n), 256, 0, h->st>>>(h->amp, cb, h->d_cmap, h->N, h->o, h->v);
         ++h->launches;
