@@ -30,6 +30,7 @@
 #include "ozaki.cuh"
 #include "zgemm_kb.cuh"
 #include "diis.h"
+#include "kgrid.h"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -53,25 +54,6 @@
 using namespace ccsdk;
 
 namespace {
-
-// ------------------------------------------------------------ k grid (host)
-struct KGrid {
-    int n[3] = {1, 1, 1};
-    int N = 1;
-    std::vector<int> c0, c1, c2;
-    void init(const int* d) {
-        n[0] = d[0]; n[1] = d[1]; n[2] = d[2];
-        N = n[0] * n[1] * n[2];
-        c0.resize(N); c1.resize(N); c2.resize(N);
-        for (int k = 0; k < N; ++k) { c0[k] = k / (n[1] * n[2]); c1[k] = (k / n[2]) % n[1]; c2[k] = k % n[2]; }
-    }
-    static int md(int x, int m) { x %= m; return x < 0 ? x + m : x; }
-    int flat(int a, int b, int c) const { return (md(a, n[0]) * n[1] + md(b, n[1])) * n[2] + md(c, n[2]); }
-    // k1 + k2 - k3 (momentum conservation k1 + k2 = k3 + k4, paper Sec. 3.2.5)
-    int k4(int k1, int k2, int k3) const {
-        return flat(c0[k1] + c0[k2] - c0[k3], c1[k1] + c1[k2] - c1[k3], c2[k1] + c2[k2] - c2[k3]);
-    }
-};
 
 enum Buf {
     B_FOO_IN, B_FVV_IN, B_FOV_IN, B_OOOO, B_OOOV, B_OOVV, B_OVVO, B_OVVV, B_VVVV,
@@ -2372,24 +2354,9 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
     if (al.err) return al.err;
     if (h->cfg.diis_depth > 0) {
         // canonical blocks of the DIIS history (t2 antisymmetry, paper Sec. 2)
-        std::vector<int> cblk, cmap((size_t)N3);
+        std::vector<int> cblk, cmap;
         std::vector<double> cw;
-        std::vector<int> canon((size_t)N3, -1);
-        for (int ki = 0; ki < N; ++ki) for (int kj = ki; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
-            const int kb = h->kg.k4(ki, kj, ka);
-            if (ka > kb) continue;
-            const int f = (int)(((long long)ki * N + kj) * N + ka);
-            canon[(size_t)f] = (int)cblk.size();
-            cblk.push_back(f);
-            cw.push_back((ki < kj ? 2.0 : 1.0) * (ka < kb ? 2.0 : 1.0));
-        }
-        for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
-            const int kb = h->kg.k4(ki, kj, ka);
-            const int sij = ki > kj ? 1 : 0, sab = ka > kb ? 1 : 0;
-            const int c = (int)((((long long)(sij ? kj : ki)) * N + (sij ? ki : kj)) * N + (sab ? kb : ka));
-            if (canon[(size_t)c] < 0) return CCSD_ERR_INVALID;
-            cmap[(size_t)(((long long)ki * N + kj) * N + ka)] = canon[(size_t)c] * 4 + sij * 2 + sab;
-        }
+        if (!diis_canonical_blocks(h->kg, cblk, cw, cmap)) return CCSD_ERR_INVALID;
         h->nc = (long long)cblk.size();
         h->d_cblk = upload(al, cblk, h->st);
         h->d_cw = upload(al, cw, h->st);

@@ -1,4 +1,7 @@
-// Pulay (DIIS) extrapolation coefficients, host code.  Given the Gram matrix
+// DIIS host code: the canonical blocks of the history and the Pulay
+// extrapolation coefficients.
+//
+// Pulay (DIIS) extrapolation coefficients.  Given the Gram matrix
 // B_ij = Re <e_i|e_j> of the last m update errors, the coefficients c minimise
 // |sum_i c_i e_i| subject to sum_i c_i = 1; with a Lagrange multiplier l they solve
 //   [ B  -1 ] [c]   [ 0]
@@ -10,7 +13,45 @@
 #include <utility>
 #include <vector>
 
+#include "kgrid.h"
+
 namespace ccsdk {
+
+// The DIIS history holds t1 and the canonical blocks of t2 only: t2 is
+// antisymmetric, t2[kj][ki][ka](j, i, a, b) = t2[ki][kj][kb](i, j, b, a)
+// = -t2[ki][kj][ka](i, j, a, b) with kb = ki + kj - ka (paper Sec. 2), so the blocks
+// with ki <= kj and ka <= kb determine all others.
+//   cblk[p]: full block index (ki N + kj) N + ka of canonical block p;
+//   cw[p]:   the number of full blocks it stands for (its weight in the full inner
+//            product: 2 for ki < kj times 2 for ka < kb);
+//   cmap[f]: 4 p + 2 swap_ij + swap_ab for every full block f, where p is the
+//            canonical block f is read from with those index swaps (sign -1 when
+//            exactly one swap applies).
+// Returns false if some block has no canonical partner (not possible on a grid).
+inline bool diis_canonical_blocks(const KGrid& kg, std::vector<int>& cblk, std::vector<double>& cw,
+                                  std::vector<int>& cmap) {
+    const int N = kg.N;
+    const long long N3 = (long long)N * N * N;
+    cblk.clear(); cw.clear();
+    cmap.assign((size_t)N3, 0);
+    std::vector<int> canon((size_t)N3, -1);
+    for (int ki = 0; ki < N; ++ki) for (int kj = ki; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
+        const int kb = kg.k4(ki, kj, ka);
+        if (ka > kb) continue;
+        const int f = (int)(((long long)ki * N + kj) * N + ka);
+        canon[(size_t)f] = (int)cblk.size();
+        cblk.push_back(f);
+        cw.push_back((ki < kj ? 2.0 : 1.0) * (ka < kb ? 2.0 : 1.0));
+    }
+    for (int ki = 0; ki < N; ++ki) for (int kj = 0; kj < N; ++kj) for (int ka = 0; ka < N; ++ka) {
+        const int kb = kg.k4(ki, kj, ka);
+        const int sij = ki > kj ? 1 : 0, sab = ka > kb ? 1 : 0;
+        const int c = (int)((((long long)(sij ? kj : ki)) * N + (sij ? ki : kj)) * N + (sab ? kb : ka));
+        if (canon[(size_t)c] < 0) return false;
+        cmap[(size_t)(((long long)ki * N + kj) * N + ka)] = canon[(size_t)c] * 4 + sij * 2 + sab;
+    }
+    return true;
+}
 
 // gram[i][j] for i, j < m (any row-indexable type); c receives m coefficients.
 // Returns false if the system is exactly singular (a zero pivot).

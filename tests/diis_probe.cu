@@ -9,3 +9,16 @@ extern "C" int probe_diis(const double* gram, int m, double* c) {
         for (int j = 0; j < m; ++j) g[(size_t)i][(size_t)j] = gram[(size_t)i * m + j];
     return ccsdk::diis_coefficients(g, m, c) ? 1 : 0;
 }
+
+// The canonical blocks of a grid; arrays have room for N^3 entries.
+extern "C" int probe_canonical(const int* dims, int* nc, int* cblk, double* cw, int* cmap) {
+    ccsdk::KGrid kg;
+    kg.init(dims);
+    std::vector<int> b, m;
+    std::vector<double> w;
+    if (!ccsdk::diis_canonical_blocks(kg, b, w, m)) return 0;
+    *nc = (int)b.size();
+    for (size_t p = 0; p < b.size(); ++p) { cblk[p] = b[p]; cw[p] = w[p]; }
+    for (size_t f = 0; f < m.size(); ++f) cmap[f] = m[f];
+    return 1;
+}

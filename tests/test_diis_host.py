@@ -10,6 +10,11 @@ The checks do not restate the library's elimination:
   random affine combinations (the constrained minimum);
 * a zero first error vector needs a row exchange and gives c = (1, 0);
 * two identical error vectors make the system singular, which the solve reports.
+
+The canonical blocks of the history (ki <= kj, ka <= kb) are checked on antisymmetric
+amplitudes built here with this module's own momentum arithmetic: the weights count
+every block once, the weighted inner product over canonical blocks equals the full
+one, and unpacking through cmap (with its swaps and signs) gives back every block.
 """
 import ctypes
 
@@ -27,6 +32,9 @@ def probe():
         d = ctypes.POINTER(ctypes.c_double)
         _lib.probe_diis.argtypes = [d, ctypes.c_int, d]
         _lib.probe_diis.restype = ctypes.c_int
+        ip = ctypes.POINTER(ctypes.c_int)
+        _lib.probe_canonical.argtypes = [ip, ip, ip, d, ip]
+        _lib.probe_canonical.restype = ctypes.c_int
     return _lib
 
 
@@ -79,3 +87,75 @@ def test_identical_errors_are_reported_singular():
     e = np.array([0.5, -1.0, 2.0, 0.25])
     ok, _ = solve(gram(np.stack([e, e, 2 * e])))
     assert not ok
+
+
+def canonical(grid):
+    N = grid[0] * grid[1] * grid[2]
+    dims = (ctypes.c_int * 3)(*grid)
+    nc = ctypes.c_int(0)
+    cblk = (ctypes.c_int * N ** 3)()
+    cw = (ctypes.c_double * N ** 3)()
+    cmap = (ctypes.c_int * N ** 3)()
+    assert probe().probe_canonical(dims, ctypes.byref(nc), cblk, cw, cmap) == 1
+    n = nc.value
+    return np.array(cblk[:n]), np.array(cw[:n]), np.array(cmap[:])
+
+
+def kb_table(grid):
+    """kb = ki + kj - ka per block, from the grid coordinates (independent of the library)."""
+    pts = [(a, b, c) for a in range(grid[0]) for b in range(grid[1]) for c in range(grid[2])]
+    index = {p: k for k, p in enumerate(pts)}
+    N = len(pts)
+    kb = np.zeros((N, N, N), int)
+    for ki, pi in enumerate(pts):
+        for kj, pj in enumerate(pts):
+            for ka, pa in enumerate(pts):
+                kb[ki, kj, ka] = index[tuple((pi[d] + pj[d] - pa[d]) % grid[d] for d in range(3))]
+    return kb
+
+
+def antisymmetric_t2(rng, grid, o, v):
+    """X - P(ij) X - P(ab) X + P(ij)P(ab) X for a random X: t2[ki,kj,ka](i,j,a,b)."""
+    N = grid[0] * grid[1] * grid[2]
+    kb = kb_table(grid)
+    X = rng.standard_normal((N, N, N, o, o, v, v)) + 1j * rng.standard_normal((N, N, N, o, o, v, v))
+    T = np.zeros_like(X)
+    for ki in range(N):
+        for kj in range(N):
+            for ka in range(N):
+                b = kb[ki, kj, ka]
+                T[ki, kj, ka] = (X[ki, kj, ka] - X[kj, ki, ka].transpose(1, 0, 2, 3)
+                                 - X[ki, kj, b].transpose(0, 1, 3, 2) + X[kj, ki, b].transpose(1, 0, 3, 2))
+    return T
+
+
+def test_canonical_blocks_weights_dot_and_unpack():
+    rng = np.random.default_rng(9)
+    for grid in [(1, 1, 1), (2, 1, 1), (3, 1, 1), (4, 1, 1), (2, 2, 1), (3, 2, 1), (2, 2, 2), (3, 3, 1)]:
+        N = grid[0] * grid[1] * grid[2]
+        o, v = 2, 3
+        cblk, cw, cmap = canonical(grid)
+        kb = kb_table(grid)
+        assert cw.sum() == N ** 3
+        for f in cblk:                                   # canonical: ki <= kj and ka <= kb
+            ki, kj, ka = f // (N * N), (f // N) % N, f % N
+            assert ki <= kj and ka <= kb[ki, kj, ka]
+        T, U = antisymmetric_t2(rng, grid, o, v), antisymmetric_t2(rng, grid, o, v)
+        Tf, Uf = T.reshape(N ** 3, o, o, v, v), U.reshape(N ** 3, o, o, v, v)
+        full = np.real(np.vdot(T, U))
+        canon = sum(w * np.real(np.vdot(Tf[f], Uf[f])) for f, w in zip(cblk, cw))
+        assert abs(full - canon) <= 1e-12 * abs(full) + 1e-12
+        if N > 1:                                        # unit weights (a plausible slip) miss it
+            unweighted = sum(np.real(np.vdot(Tf[f], Uf[f])) for f in cblk)
+            assert abs(full - unweighted) > 1e-6 * abs(full)
+        for f in range(N ** 3):                          # unpack every block from its canonical one
+            m = cmap[f]
+            p, sij, sab = m >> 2, (m >> 1) & 1, m & 1
+            blk = Tf[cblk[p]]
+            if sij:
+                blk = blk.transpose(1, 0, 2, 3)
+            if sab:
+                blk = blk.transpose(0, 1, 3, 2)
+            sign = -1.0 if sij != sab else 1.0
+            # the 4-term antisymmetrizer above rounds differently per block: 1e-13, not bits
+            np.testing.assert_allclose(sign * blk, Tf[f], rtol=0, atol=1e-13)
