@@ -2473,7 +2473,7 @@ int iter_end(ccsd_ctx* h, int* done, double* max_resid) {
     const double mr = *h->norm_host;
     const long long n = h->n1 + h->n2;
     *max_resid = mr;
-    if (!std::isfinite(mr)) return CCSD_ERR_DIVERGED;
+    if (!std::isfinite(mr)) { refuse("max|R| is not finite: the iteration diverged"); return CCSD_ERR_DIVERGED; }
     if (mr < h->cfg.conv_tol) { *done = 1; return CCSD_OK; }
     const int depth = h->cfg.diis_depth;
     const size_t tu = h->seq.size();     // trace slot of the update
@@ -3149,7 +3149,7 @@ int ccsd_batch_iterate(ccsd_batch_t B, int n_iter, int* done, double* max_resid)
         CK(cudaStreamSynchronize(B->st));
         bool changed = false, all = true;
         for (int i = 0; i < B->n; ++i) {
-            if (!std::isfinite(norms[i])) return CCSD_ERR_DIVERGED;
+            if (!std::isfinite(norms[i])) { refuse("a batch member's max|R| is not finite: it diverged"); return CCSD_ERR_DIVERGED; }
             if (!B->done[i] && norms[i] < B->m[i]->cfg.conv_tol) { B->done[i] = 1; changed = true; }
             all = all && B->done[i];
         }
