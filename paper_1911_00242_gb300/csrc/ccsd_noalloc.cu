@@ -51,10 +51,10 @@ __global__ void energy_blocks(const double2* __restrict__ t1, const double2* __r
             double2 amp = t[e];
             amp.x *= 0.25; amp.y *= 0.25;
             if (ka == ki) {
-                int r = (int)e;
-                const int bb = r % v; r /= v;
-                const int a = r % v; r /= v;
-                const int j = r % o; const int i = r / o;
+                long long r = e;                       // o^2 v^2 may exceed 2^31
+                const int bb = (int)(r % v); r /= v;
+                const int a = (int)(r % v); r /= v;
+                const int j = (int)(r % o); const int i = (int)(r / o);
                 const double2 q = cmul(t1[((long long)ki * o + i) * v + a], t1[((long long)kj * o + j) * v + bb]);
                 amp.x += 0.5 * q.x; amp.y += 0.5 * q.y;
             }
@@ -111,7 +111,8 @@ extern "C" int ccsd_energy_noalloc(const int nk_dims[3], int nocc, int nvir, con
     if (!nk_dims || !f_ov || !oovv || !t1 || !t2 || !e_out) return CCSD_ERR_INVALID;
     long long N = 1;
     for (int d = 0; d < 3; ++d) {
-        if (nk_dims[d] < 1) return CCSD_ERR_INVALID;
+        // the bound ccsd_create applies; it also keeps N^3 below 2^63
+        if (nk_dims[d] < 1 || nk_dims[d] > 64) return CCSD_ERR_INVALID;
         N *= nk_dims[d];
     }
     if (nocc < 1 || nvir < 1 || nocc > 256 || nvir > 512) return CCSD_ERR_INVALID;

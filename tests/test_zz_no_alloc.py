@@ -43,12 +43,14 @@ def test_noalloc_energy_matches_handle_energy(lib):
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch(lib):
-    spec = cs.SynthSpec((2, 1, 1), 2, 3, 902)
     buf = torch.zeros(16, dtype=torch.complex128, device="cuda")
     out = torch.zeros(2, dtype=torch.float64, device="cuda")
     p = buf.data_ptr()
-    # 32 x 32 x 32 k points need 32769 partial sums: more than the 32768 the library holds
-    rc = lib.ccsd_energy_noalloc(_dims((32, 32, 32)), 2, 3, p, p, p, p, out.data_ptr(), None)
+    # 32 k points need 32^3 + 1 = 32769 partial sums: one more than the 32768 the library holds
+    rc = lib.ccsd_energy_noalloc(_dims((32, 1, 1)), 2, 3, p, p, p, p, out.data_ptr(), None)
     assert rc == -1
+    # grid sides beyond 64 are refused before N_k^3 is formed (it would overflow 64 bits)
+    for grid in ((65, 1, 1), (1 << 21, 1, 1), (1 << 21, 1 << 21, 1 << 21)):
+        assert lib.ccsd_energy_noalloc(_dims(grid), 2, 3, p, p, p, p, out.data_ptr(), None) == -1
     torch.cuda.synchronize()
     assert np.all(out.cpu().numpy() == 0)
