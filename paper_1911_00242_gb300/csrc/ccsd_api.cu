@@ -2581,7 +2581,11 @@ size_t request_bytes(const ccsd_config& c, const ccsd_inputs& in) {
 void server_finish(ccsd_server* S, ServerReq* r, int state) {
     double e_re = 0.0, e_im = 0.0;
     if (r->h) {
-        if (state == 2) ccsd_energy(r->h, &e_re, &e_im);
+        if (state == 2) {
+            // a failed energy reduction ends the request with its code, not as converged
+            const int rc = ccsd_energy(r->h, &e_re, &e_im);
+            if (rc) { state = rc; e_re = e_im = 0.0; }
+        }
         ccsd_destroy(r->h);
         r->h = nullptr;
     }
@@ -2659,7 +2663,8 @@ void server_loop(ccsd_server* S) {
             }
             if (r->phase == 0 && r->polish_left > 0) {    // mixed phase done: FP64 polish
                 r->phase = 1;
-                ccsd_set_precision(r->h, r->cfg.polish_precision == CCSD_OZAKI ? CCSD_OZAKI : CCSD_FP64);
+                const int prc = ccsd_set_precision(r->h, r->cfg.polish_precision == CCSD_OZAKI ? CCSD_OZAKI : CCSD_FP64);
+                if (prc) { server_finish(S, r, prc); continue; }
                 r->h->cfg.conv_tol = r->cfg.conv_tol;
                 keep.push_back(r);
                 continue;
@@ -2965,12 +2970,23 @@ int ccsd_solve(ccsd_t h, int* iterations, double* max_resid) {
     h->cfg.conv_tol = tol0;
     if (mixed && done) {
         // polish (FP64, or the FP64-accurate Ozaki form): the fixed point of the exact equations
-        ccsd_set_precision(h, h->cfg.polish_precision == CCSD_OZAKI ? CCSD_OZAKI : CCSD_FP64);
+        int rc = ccsd_set_precision(h, h->cfg.polish_precision == CCSD_OZAKI ? CCSD_OZAKI : CCSD_FP64);
+        if (rc) { if (iterations) *iterations = it; if (max_resid) *max_resid = mr; return rc; }
         int d2 = 0;
         for (int p = 0; p < h->cfg.polish_iters; ++p) {
-            int rc = ccsd_iterate(h, 1, &d2, &mr);
+            rc = ccsd_iterate(h, 1, &d2, &mr);
             if (rc) {
-                ccsd_set_precision(h, CCSD_MIXED);   // the handle stays a mixed-form handle
+                // the handle goes back to the mixed form; the failure's code and its
+                // ccsd_last_error text are what the caller sees
+                char why[sizeof g_errbuf];
+                memcpy(why, g_errbuf, sizeof why);
+                const int back = ccsd_set_precision(h, CCSD_MIXED);
+                memcpy(g_errbuf, why, sizeof why);
+                if (back) {
+                    const size_t n = strlen(g_errbuf);
+                    snprintf(g_errbuf + n, sizeof g_errbuf - n, "%s(the handle stayed in the polish precision)",
+                             n ? " " : "");
+                }
                 if (iterations) *iterations = it;
                 if (max_resid) *max_resid = mr;
                 return rc;
@@ -2978,7 +2994,7 @@ int ccsd_solve(ccsd_t h, int* iterations, double* max_resid) {
             if (d2) break;
             ++it;
         }
-        ccsd_set_precision(h, CCSD_MIXED);
+        if ((rc = ccsd_set_precision(h, CCSD_MIXED))) return rc;
     }
     if (iterations) *iterations = it;
     if (max_resid) *max_resid = mr;
