@@ -287,14 +287,25 @@ int ccsd_server_stats(ccsd_server_t s, int* active, int* queued, size_t* admitte
 /* Finishes the admitted solves, cancels the queued ones, joins the thread. */
 int ccsd_server_destroy(ccsd_server_t s);
 
+/* The FP64 rate of the current device, measured: the roofline denominator of the
+ * FP64 form.  The paper has no counterpart; it states no hardware.  Runs two probe
+ * kernels with no memory traffic in their loops -- fused multiply-add chains
+ * (DFMA) and FP64 mma.sync (m8n8k4) -- at 2, 4 and 8 blocks of 256 threads per SM,
+ * times each with CUDA events on a stream of its own (about 1 s in total, after a
+ * warm-up launch per shape) and returns the best rate of each in TFLOP/s (2 flops
+ * per multiply-add).  Either pointer may be NULL (that probe is skipped), not both.
+ * Synchronizes the device's work it enqueued; allocates 8 bytes of device memory
+ * while it runs. */
+int ccsd_fp64_peak_probe(double* dfma_tflops, double* dmma_tflops);
+
 /* A static description of a CCSD_* code. */
 const char* ccsd_strerror(int code);
 
 /* Why the most recent failing call on this host thread failed, where the library
  * knows more than the code says (an invalid config field, a 32-bit table limit, the
  * CUDA error text, a timed-out device wait); "" if nothing was recorded.  Every
- * entry point but ccsd_energy_noalloc clears it when called from outside the
- * library.  The pointer stays valid for the thread's lifetime. */
+ * entry point but ccsd_energy_noalloc and ccsd_fp64_peak_probe clears it when
+ * called from outside the library.  The pointer stays valid for the thread's lifetime. */
 const char* ccsd_last_error(void);
 
 /* Correlation energy per unit cell of the amplitudes t1, t2 (same expression

@@ -92,6 +92,7 @@ SYMBOLS = {
     "ccsd_server_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "ccsd_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "ccsd_last_error": ([], ctypes.c_char_p),
+    "ccsd_fp64_peak_probe": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "ccsd_energy_noalloc": ([ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 6,
                             ctypes.c_int),
 }

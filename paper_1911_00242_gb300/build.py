@@ -5,7 +5,7 @@ import subprocess
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libccsd_gb300.so")
-SOURCES = [os.path.join(PKG, "csrc", "ccsd_api.cu"), os.path.join(PKG, "csrc", "ccsd_noalloc.cu")]
+SOURCES = [os.path.join(PKG, "csrc", f) for f in ("ccsd_api.cu", "ccsd_noalloc.cu", "peak_probe.cu")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -16,8 +16,24 @@ def nvcc():
 
 
 def build(verbose=False, extra=()):
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include"), *extra, "-o", LIB, *SOURCES]
+    """Compiles every translation unit in parallel, then links the shared library."""
+    from concurrent.futures import ThreadPoolExecutor
+    objdir = os.path.join(ROOT, "_build", "lib")
+    os.makedirs(objdir, exist_ok=True)
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
+             *extra]
+    objs = [os.path.join(objdir, os.path.splitext(os.path.basename(src))[0] + ".o") for src in SOURCES]
+
+    def compile_one(pair):
+        src, obj = pair
+        cmd = [nvcc(), *flags, "-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.run(cmd, check=True)
+
+    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        list(ex.map(compile_one, zip(SOURCES, objs)))
+    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs]
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True)
