@@ -30,6 +30,7 @@
 #include "ozaki.cuh"
 #include "zgemm_kb.cuh"
 #include "diis.h"
+#include "grouped.cuh"
 #include "kgrid.h"
 
 #include <cuda.h>
@@ -44,7 +45,9 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <set>
@@ -808,7 +811,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
                 h->shadow[bi] = (float2*)al.get((size_t)h->bufsize[bi] * 8);
                 if (al.err) return al.err;
                 if (!al.dry && bi != B_T1)
-                    to_c64_kernel<<<ew_grid(h->bufsize[bi]), 256, 0, h->st>>>(h->shadow[bi], h->buf[bi], h->bufsize[bi]);
+                    to_c64_kernel<<<ew_grid(h->bufsize[bi]), 256, 0, h->st>>>(ToC64Op{h->shadow[bi], h->buf[bi], h->bufsize[bi]});
             }
             h->shadow[B_T2] = (float2*)al.get((size_t)h->n2 * 8);
             h->shadow[B_TAUT] = (float2*)al.get((size_t)h->n2 * 8);
@@ -1805,6 +1808,47 @@ int launch_gemm(ccsd_ctx* h, GemmPlan& p) {
     return 0;
 }
 
+// Kernel arguments of plan steps, with the handle's buffers resolved.
+CopyOp copy_op(const ccsd_ctx* h, const CopyPlan& c) {
+    return CopyOp{h->buf[c.dst], h->in32[c.src] ? nullptr : h->buf[c.src], h->in32[c.src] ? h->shadow[c.src] : nullptr,
+                  c.n, c.conj};
+}
+
+PermOp perm_op(const ccsd_ctx* h, const PermPlan& pp) {
+    return PermOp{h->buf[pp.dst], h->in32[pp.src] ? nullptr : h->buf[pp.src],
+                  h->in32[pp.src] ? h->shadow[pp.src] : nullptr, pp.p};
+}
+
+TauOp tau_op(const ccsd_ctx* h) {
+    const bool c64 = h->fp32 && h->cfg.precision == CCSD_MIXED;
+    return TauOp{h->buf[B_T1], h->buf[B_T2], h->buf[B_TAU], h->buf[B_TAUT], h->kb_of, h->N, h->o, h->v,
+                 c64 ? h->shadow[B_T2] : nullptr, c64 ? h->shadow[B_TAUT] : nullptr};
+}
+
+FockTermsOp fock_terms_op(const ccsd_ctx* h) {
+    return FockTermsOp{h->buf[B_ZR], h->shadow[B_T2], h->shadow[B_T1], h->shadow[B_FVVP], h->shadow[B_FOOP],
+                       h->shadow[B_OOOV], h->shadow[B_OVVV], h->kb_of, h->N, h->o, h->v};
+}
+
+WprimeListArgs wprime_op(const ccsd_ctx* h, const WListPlan& w) {
+    WprimeListArgs a = w.a;
+    a.vvvv = h->shadow[B_VVVV];
+    a.ovvv = h->shadow[B_OVVV]; a.t1 = h->shadow[B_T1];
+    return a;
+}
+
+EmbedArgs embed_op(const ccsd_ctx* h, const EmbedPlan& e) {
+    EmbedArgs a = e.a;
+    a.src = h->buf[e.src];
+    a.src32 = h->in32[e.src] ? h->shadow[e.src] : nullptr;
+    return a;
+}
+
+UpdateOp update_op(const ccsd_ctx* h, const int* skip) {
+    return UpdateOp{h->buf[B_T1], h->buf[B_T2], h->buf[B_R1], h->buf[B_R2], h->eo, h->ev, h->kb_of,
+                    h->N, h->o, h->v, nullptr, nullptr, skip};
+}
+
 void launch_embed(ccsd_ctx* h, EmbedPlan& e) {
     if (e.oz) {
         OzEmbedArgs z = e.z;
@@ -1818,9 +1862,7 @@ void launch_embed(ccsd_ctx* h, EmbedPlan& e) {
         ++h->launches;
         return;
     }
-    EmbedArgs a = e.a;
-    a.src = h->buf[e.src];
-    a.src32 = h->in32[e.src] ? h->shadow[e.src] : nullptr;
+    const EmbedArgs a = embed_op(h, e);
     embed_kernel<<<row_grid((long long)a.nblk * a.R), a.Kpad / 2 >= 256 ? 256 : 128, 0, h->st>>>(a);
     ++h->launches;
 }
@@ -1828,7 +1870,7 @@ void launch_embed(ccsd_ctx* h, EmbedPlan& e) {
 // A kernel's dynamic shared-memory limit is an attribute of the current device: it
 // is raised once per device and kernel, under a lock (the serving loop launches from
 // its own thread).
-enum { SMEM_TC = 0, SMEM_OZ = 1, SMEM_OZ_WPRIME = 2 };
+enum { SMEM_TC = 0, SMEM_OZ = 1, SMEM_OZ_WPRIME = 2, SMEM_TC_GROUPED = 3 };
 std::mutex g_smem_attr_mu;
 std::set<std::pair<int, int>> g_smem_attr_done;
 
@@ -1843,6 +1885,9 @@ void ensure_smem_attr(int which) {
             break;
         case SMEM_OZ:
             cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
+            break;
+        case SMEM_TC_GROUPED:
+            cudaFuncSetAttribute(tc_gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
             break;
         default:
             cudaFuncSetAttribute(oz_wprime_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1907,33 +1952,23 @@ void launch_step(ccsd_ctx* h, size_t si) {
             case 0: launch_gemm(h, h->gemms[s.idx]); break;
             case 1: {
                 const CopyPlan& c = h->copies[s.idx];
-                if (h->in32[c.src])
-                    copy_kernel<<<ew_grid(c.n), 256, 0, h->st>>>(h->buf[c.dst], h->shadow[c.src], c.n, c.conj);
-                else
-                    copy_kernel<<<ew_grid(c.n), 256, 0, h->st>>>(h->buf[c.dst], h->buf[c.src], c.n, c.conj);
+                copy_kernel<<<ew_grid(c.n), 256, 0, h->st>>>(copy_op(h, c));
                 ++h->launches;
                 break;
             }
             case 2: {
                 const PermPlan& pp = h->perms[s.idx];
                 const dim3 g = ew_grid((long long)pp.p.nbatch * pp.p.n0 * pp.p.n1 * pp.p.n2 * pp.p.n3);
-                if (h->in32[pp.src]) permute4_kernel<<<g, 256, 0, h->st>>>(h->buf[pp.dst], h->shadow[pp.src], pp.p);
-                else permute4_kernel<<<g, 256, 0, h->st>>>(h->buf[pp.dst], h->buf[pp.src], pp.p);
+                permute4_kernel<<<g, 256, 0, h->st>>>(perm_op(h, pp));
                 ++h->launches;
                 break;
             }
             case 3:
-            {
-                const bool c64 = h->fp32 && h->cfg.precision == CCSD_MIXED;
-                tau_kernel<<<ew_grid(h->n2), 256, 0, h->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_TAU], h->buf[B_TAUT],
-                                                               h->kb_of, N, o, v, c64 ? h->shadow[B_T2] : nullptr,
-                                                               c64 ? h->shadow[B_TAUT] : nullptr);
-            }
+                tau_kernel<<<ew_grid(h->n2), 256, 0, h->st>>>(tau_op(h));
                 ++h->launches;
                 break;
             case 4:
-                antisym_kernel<<<ew_grid(h->n2), 256, 0, h->st>>>(h->buf[B_R2], h->buf[B_ZR],
-                                                                   h->kb_of, N, o, v);
+                antisym_kernel<<<ew_grid(h->n2), 256, 0, h->st>>>(AntisymOp{h->buf[B_R2], h->buf[B_ZR], h->kb_of, N, o, v});
                 ++h->launches;
                 break;
             case 5: launch_embed(h, h->embeds[s.idx]); break;
@@ -1955,27 +1990,22 @@ void launch_step(ccsd_ctx* h, size_t si) {
                     ++h->launches;
                     break;
                 }
-                WprimeListArgs a = h->wlists[s.idx].a;
-                a.vvvv = h->shadow[B_VVVV];
-                a.ovvv = h->shadow[B_OVVV]; a.t1 = h->shadow[B_T1];
+                const WprimeListArgs a = wprime_op(h, h->wlists[s.idx]);
                 wprime_list_kernel<<<row_grid((long long)a.nblk * a.ngrp), 256, 0, h->st>>>(a);
                 ++h->launches;
                 break;
             }
             case 11: {   // mixed form: fused P(ab)-only / P(ij)-only terms into ZR
-                fock_terms_kernel<<<ew_grid(h->n2), 256, 0, h->st>>>(
-                    h->buf[B_ZR], h->shadow[B_T2], h->shadow[B_T1], h->shadow[B_FVVP], h->shadow[B_FOOP],
-                    h->shadow[B_OOOV], h->shadow[B_OVVV], h->kb_of, N, o, v);
+                fock_terms_kernel<<<ew_grid(h->n2), 256, 0, h->st>>>(fock_terms_op(h));
                 ++h->launches;
                 break;
             }
             case 12:  // complex64 copy of F'vv, transposed per k (fused Fock terms)
-                to_c64_transpose_kernel<<<ew_grid(h->bufsize[s.idx]), 256, 0, h->st>>>(h->shadow[s.idx], h->buf[s.idx], N, v);
+                to_c64_transpose_kernel<<<ew_grid(h->bufsize[s.idx]), 256, 0, h->st>>>(ToC64TOp{h->shadow[s.idx], h->buf[s.idx], N, v});
                 ++h->launches;
                 break;
             case 9:   // refresh the complex64 copy of an amplitude or intermediate buffer
-                to_c64_kernel<<<ew_grid(h->bufsize[s.idx]), 256, 0, h->st>>>(h->shadow[s.idx], h->buf[s.idx],
-                                                                             h->bufsize[s.idx]);
+                to_c64_kernel<<<ew_grid(h->bufsize[s.idx]), 256, 0, h->st>>>(ToC64Op{h->shadow[s.idx], h->buf[s.idx], h->bufsize[s.idx]});
                 ++h->launches;
                 break;
         }
@@ -2017,13 +2047,20 @@ int run_residual(ccsd_ctx* h) {
 }
 
 
-// ================================================================ batched form
-// Many independent problems advance together.  Their plans have the same
-// step sequence (sizes differ), so the i-th active contraction of every member
-// runs in one grouped persistent launch (zgemm_grouped_kernel) whose tile
-// shape an autotuner picks; the other steps launch per member.  One iteration
-// (residual, max|R| per member, update) is captured in a CUDA graph and
-// replayed.
+// ================================================================ grouped iterations
+// Many independent problems advance together (the batched form, the serving loop).
+// Problems whose plans have the same step sequence (kinds and modes; sizes differ)
+// form a group, and every step of one iteration is ONE launch over all members of
+// the group:
+//   * contractions: zgemm_grouped_kernel, a persistent CTA set striding a
+//     [member][split][batch][tile] work list, with one tile shape per step (picked by
+//     an autotuner in the batched form); split-K reductions grouped the same way;
+//   * tensor-core contractions: tc_gemm_grouped_kernel, one CTA per tile of every
+//     member, each member's tensor maps and arguments read from global memory;
+//   * elementwise and row-wise steps (tau, copies, permutations, operand embedding,
+//     W' formation, Fock terms, antisymmetrization, zeroing): grouped_op_kernel;
+//   * max|R| per member, and the update of the members not yet converged.
+// The group's launch descriptors are built once per membership on the host.
 struct BatchGroup {
     int cfg = CFG_64x64;
     std::vector<GemmArgs> args;       // per member, tiles for `cfg`, pointers resolved
@@ -2031,25 +2068,424 @@ struct BatchGroup {
     long long* d_prefix = nullptr;
     long long total = 0;
     std::vector<int> split_members;
+    std::function<void(cudaStream_t)> reduce;   // grouped split-K reduction (members that split)
 };
+
+// One grouped launch: enqueues itself on a stream (no host synchronization).
+struct GLaunch {
+    std::function<void(cudaStream_t)> fn;
+    int launches = 0;
+    int gemm = -1;                    // index into Group::gemms for contraction steps
+};
+
+struct Group {
+    std::vector<ccsd_ctx*> m;
+    std::vector<int> ids;             // caller's member indices
+    int fp32 = 0;
+    std::vector<size_t> steps;        // active plan steps, the same in every member
+    std::vector<GLaunch> res;         // the residual, in plan order
+    std::vector<BatchGroup> gemms;
+    GLaunch norms, update;
+    double* d_norms = nullptr;        // max|R| of each member (a caller's slice, or owned)
+    int* d_err = nullptr;             // shared error word of the grouped tensor-core launches
+    std::vector<void*> owned;
+};
+
+// Step signature of a plan: members with equal signatures share every grouped launch.
+std::vector<std::pair<int, int>> plan_signature(const ccsd_ctx* h) {
+    std::vector<std::pair<int, int>> sig;
+    for (const Step& st : h->seq) sig.emplace_back(st.kind, st.mode);
+    return sig;
+}
+
+int group_alloc(Group& G, size_t bytes, void** p) {
+    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) { cudaGetLastError(); return CCSD_ERR_OOM; }
+    G.owned.push_back(*p);
+    return 0;
+}
+
+template <class T>
+T* group_upload(Group& G, const std::vector<T>& v, cudaStream_t st, int* rc) {
+    void* p = nullptr;
+    if ((*rc = group_alloc(G, v.size() * sizeof(T), &p))) return nullptr;
+    if (cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        *rc = CCSD_ERR_CUDA;
+        return nullptr;
+    }
+    return (T*)p;
+}
+
+void group_free(Group& G) {
+    for (void* p : G.owned) cudaFree(p);
+    G = Group();
+}
+
+long long grid_blocks(const dim3& g) { return (long long)g.x; }
+// row-wise ops stride their rows: a member's share of a grouped launch is bounded
+long long row_blocks(long long rows) { return std::max(1LL, std::min(rows, 8192LL)); }
+
+// A grouped launch of one operation type over the members; blocks[i] = member i's grid.
+template <class Op>
+int make_grouped(Group& G, const std::vector<Op>& ops, const std::vector<long long>& blocks, cudaStream_t st,
+                 GLaunch& out) {
+    std::vector<long long> prefix(1, 0);
+    for (long long b : blocks) prefix.push_back(prefix.back() + b);
+    const long long total = prefix.back();
+    if (total > 2147483647LL) { refuse("a grouped launch exceeds 2^31 - 1 blocks"); return CCSD_ERR_INVALID; }
+    int rc = 0;
+    const Op* d_ops = group_upload(G, ops, st, &rc);
+    if (rc) return rc;
+    const long long* d_prefix = group_upload(G, prefix, st, &rc);
+    if (rc) return rc;
+    const int n = (int)ops.size();
+    out.launches = total > 0 ? 1 : 0;
+    out.fn = [d_ops, d_prefix, n, total](cudaStream_t s) {
+        if (total > 0) grouped_op_kernel<Op><<<(unsigned)total, 256, 0, s>>>(d_ops, d_prefix, n);
+    };
+    return 0;
+}
+
+long long tiles_for(const GemmArgs& a, int cfg, int* tm, int* tn) {
+    *tm = (a.M + CFG_BM[cfg] - 1) / CFG_BM[cfg];
+    *tn = (a.N + CFG_BN[cfg] - 1) / CFG_BN[cfg];
+    return (long long)*tm * *tn * a.nbatch;
+}
+
+int group_gemm_descriptors(Group& G, BatchGroup& bg, size_t si, int cfg, cudaStream_t st, bool own_split = false) {
+    const int n = (int)G.m.size();
+    bg.cfg = cfg;
+    bg.args.clear();
+    bg.split_members.clear();
+    // Split-K by load balance: the persistent CTAs stride one work list, so no work item
+    // (a tile and its share of the chunks) should hold more than half the mean load of a
+    // CTA.  Skinny contractions (a few tiles over a long K, like the F~ and R1 sums) are
+    // then spread over many CTAs even when the whole group has plenty of tiles.
+    double total_work = 0.0;             // sum over members of tiles x K x chunks
+    for (int i = 0; i < n; ++i) {
+        int tm, tn;
+        const GemmArgs& a0 = G.m[i]->gemms[G.m[i]->seq[si].idx].args;
+        total_work += (double)tiles_for(a0, cfg, &tm, &tn) * a0.K * a0.nchunk;
+    }
+    const double item_cap = std::max(1.0, 0.5 * total_work / (double)(kSMs * 8));
+    long long tot = 0;
+    std::vector<long long> prefix;
+    std::vector<SplitReduceOp> red;
+    std::vector<long long> red_blocks;
+    for (int i = 0; i < n; ++i) {
+        ccsd_ctx* h = G.m[i];
+        const GemmPlan& p = h->gemms[h->seq[si].idx];
+        GemmArgs a = G.fp32 ? p.args32 : p.args;
+        int tm, tn;
+        tiles_for(a, cfg, &tm, &tn);
+        if (own_split) {
+            if (cfg != p.cfg) { refuse("members of a split-keeping group must share each step's tile shape"); return CCSD_ERR_INVALID; }
+            a.A = h->buf[p.a]; a.B = h->buf[p.b]; a.C = h->buf[p.c]; a.work = h->work;
+            a.A32 = (G.fp32 || h->in32[p.a]) ? h->shadow[p.a] : nullptr;
+            a.B32 = (G.fp32 || h->in32[p.b]) ? h->shadow[p.b] : nullptr;
+            if (a.nsplit > 1) {
+                bg.split_members.push_back(i);
+                red.push_back(SplitReduceOp{a});
+                red_blocks.push_back(grid_blocks(ew_grid((long long)a.nbatch * a.M * a.N)));
+            }
+            prefix.push_back(tot);
+            tot += (long long)tm * tn * a.nbatch * a.nsplit;
+            bg.args.push_back(a);
+            continue;
+        }
+        a.tiles_m = tm; a.tiles_n = tn;
+        const int ns = std::max(1, std::min(a.nchunk, (int)std::ceil((double)a.K * a.nchunk / item_cap)));
+        a.chunks_per_split = (a.nchunk + ns - 1) / ns;
+        a.nsplit = (a.nchunk + a.chunks_per_split - 1) / a.chunks_per_split;
+        if (G.fp32) {        // the FP32 instance keeps its partial sums short (see finalize_gemm)
+            const GemmArgs& g32 = p.args32;
+            if (g32.chunks_per_split < a.chunks_per_split) {
+                a.chunks_per_split = g32.chunks_per_split;
+                a.nsplit = (a.nchunk + a.chunks_per_split - 1) / a.chunks_per_split;
+            }
+        }
+        if (a.nbatch == 0) a.nsplit = 1;
+        if (a.nsplit > 1) {
+            const size_t need = (size_t)a.nsplit * a.nbatch * a.M * a.N;
+            if (need > h->work_elems) {          // the handle owns its split-K workspace
+                void* w = nullptr;
+                if (cudaMalloc(&w, need * 16) != cudaSuccess) { cudaGetLastError(); return CCSD_ERR_OOM; }
+                h->owned.push_back(w);
+                h->owned_bytes += need * 16;
+                h->work = (double2*)w;
+                h->work_elems = need;
+            }
+            bg.split_members.push_back(i);
+        }
+        a.A = h->buf[p.a]; a.B = h->buf[p.b]; a.C = h->buf[p.c]; a.work = h->work;
+        a.A32 = (G.fp32 || h->in32[p.a]) ? h->shadow[p.a] : nullptr;
+        a.B32 = (G.fp32 || h->in32[p.b]) ? h->shadow[p.b] : nullptr;
+        prefix.push_back(tot);
+        tot += (long long)tm * tn * a.nbatch * a.nsplit;
+        bg.args.push_back(a);
+        if (a.nsplit > 1) {
+            red.push_back(SplitReduceOp{a});
+            red_blocks.push_back(grid_blocks(ew_grid((long long)a.nbatch * a.M * a.N)));
+        }
+    }
+    prefix.push_back(tot);
+    bg.total = tot;
+    if (!bg.d_args) {
+        void* x = nullptr;
+        int rc = group_alloc(G, sizeof(GemmArgs) * n, &x);
+        if (rc) return rc;
+        bg.d_args = (GemmArgs*)x;
+        if ((rc = group_alloc(G, sizeof(long long) * (n + 1), &x))) return rc;
+        bg.d_prefix = (long long*)x;
+    }
+    CK(cudaMemcpyAsync(bg.d_args, bg.args.data(), sizeof(GemmArgs) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(bg.d_prefix, prefix.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, st));
+    bg.reduce = nullptr;
+    if (!red.empty()) {
+        GLaunch gl;
+        int rc = make_grouped(G, red, red_blocks, st, gl);
+        if (rc) return rc;
+        bg.reduce = gl.fn;
+    }
+    return 0;
+}
+
+template <int BM, int BN, int TM, int TN>
+void grouped_gemm_launch(const BatchGroup& bg, int fp32, cudaStream_t st, int n) {
+    const long long ctas = std::min<long long>(bg.total, (long long)kSMs * 8);
+    if (fp32)
+        zgemm_grouped_kernel<BM, BN, 8, TM, TN, float><<<(unsigned)ctas, 256, 0, st>>>(bg.d_args, bg.d_prefix, n, bg.total);
+    else
+        zgemm_grouped_kernel<BM, BN, 8, TM, TN, double><<<(unsigned)ctas, 256, 0, st>>>(bg.d_args, bg.d_prefix, n, bg.total);
+}
+
+void launch_gemm_group(const BatchGroup& bg, int fp32, cudaStream_t st, int n) {
+    if (bg.total <= 0 || !bg.d_args) return;
+    switch (bg.cfg) {
+        case CFG_64x64: grouped_gemm_launch<64, 64, 4, 4>(bg, fp32, st, n); break;
+        case CFG_64x32: grouped_gemm_launch<64, 32, 4, 2>(bg, fp32, st, n); break;
+        case CFG_128x16: grouped_gemm_launch<128, 16, 8, 1>(bg, fp32, st, n); break;
+        case CFG_32x16: grouped_gemm_launch<32, 16, 2, 1>(bg, fp32, st, n); break;
+        default: grouped_gemm_launch<16, 16, 1, 1>(bg, fp32, st, n); break;
+    }
+    if (bg.reduce) bg.reduce(st);
+}
+
+// Builds every grouped launch of one iteration of the group's members.  d_norms[i]
+// receives member i's max|R| (null: the group allocates its own array); d_skip[i] != 0
+// skips its update (may be null: all update).  cfgs: tile shape of each contraction
+// step (empty: each step's own shape in member 0).  own_split: every member keeps the
+// split-K choice of its own plan (its results are then bitwise those of a plain
+// iteration; the members must share each step's tile shape).
+int group_build(Group& G, int fp32, const std::vector<int>& cfgs, double* d_norms, const int* d_skip,
+                cudaStream_t st, bool own_split = false) {
+    const int n = (int)G.m.size();
+    if (n == 0) return 0;
+    G.fp32 = fp32;
+    ccsd_ctx* h0 = G.m[0];
+    int rc = group_alloc(G, sizeof(int), (void**)&G.d_err);
+    if (rc) return rc;
+    if (!d_norms && (rc = group_alloc(G, sizeof(double) * n, (void**)&d_norms))) return rc;
+    G.d_norms = d_norms;
+    CK(cudaMemsetAsync(G.d_err, 0, sizeof(int), st));
+    G.steps.clear();
+    for (size_t si = 0; si < h0->seq.size(); ++si)
+        if (step_active(h0, h0->seq[si])) G.steps.push_back(si);
+    int ngemm = 0;
+    for (size_t si : G.steps) if (h0->seq[si].kind == 0) ++ngemm;
+    G.gemms.assign(ngemm, BatchGroup());
+    int gi = 0;
+    ensure_smem_attr(SMEM_TC_GROUPED);
+    for (size_t si : G.steps) {
+        const Step& s0 = h0->seq[si];
+        GLaunch gl;
+        switch (s0.kind) {
+            case 0: {
+                const int cfg = gi < (int)cfgs.size() ? cfgs[gi] : h0->gemms[s0.idx].cfg;
+                if ((rc = group_gemm_descriptors(G, G.gemms[gi], si, cfg, st, own_split))) return rc;
+                const BatchGroup* bg = &G.gemms[gi];
+                gl.gemm = gi;
+                gl.launches = (bg->total > 0 ? 1 : 0) + (bg->reduce ? 1 : 0);
+                gl.fn = [bg, fp32, n](cudaStream_t s) { launch_gemm_group(*bg, fp32, s, n); };
+                ++gi;
+                break;
+            }
+            case 1: case 2: case 3: case 4: case 7: case 9: case 11: case 12: {
+                // elementwise steps
+                std::vector<long long> blocks;
+                auto build = [&](auto make, auto count) {
+                    using Op = decltype(make(G.m[0]));
+                    std::vector<Op> ops;
+                    for (ccsd_ctx* h : G.m) { ops.push_back(make(h)); blocks.push_back(grid_blocks(ew_grid(count(h)))); }
+                    return make_grouped(G, ops, blocks, st, gl);
+                };
+                if (s0.kind == 1)
+                    rc = build([&](ccsd_ctx* h) { return copy_op(h, h->copies[h->seq[si].idx]); },
+                               [&](ccsd_ctx* h) { return h->copies[h->seq[si].idx].n; });
+                else if (s0.kind == 2)
+                    rc = build([&](ccsd_ctx* h) { return perm_op(h, h->perms[h->seq[si].idx]); },
+                               [&](ccsd_ctx* h) {
+                                   const Perm4& q = h->perms[h->seq[si].idx].p;
+                                   return (long long)q.nbatch * q.n0 * q.n1 * q.n2 * q.n3;
+                               });
+                else if (s0.kind == 3)
+                    rc = build([&](ccsd_ctx* h) { return tau_op(h); }, [&](ccsd_ctx* h) { return h->n2; });
+                else if (s0.kind == 4)
+                    rc = build([&](ccsd_ctx* h) { return AntisymOp{h->buf[B_R2], h->buf[B_ZR], h->kb_of, h->N, h->o, h->v}; },
+                               [&](ccsd_ctx* h) { return h->n2; });
+                else if (s0.kind == 7)
+                    rc = build([&](ccsd_ctx* h) { return ZeroOp{h->buf[h->seq[si].idx], h->bufsize[h->seq[si].idx]}; },
+                               [&](ccsd_ctx* h) { return h->bufsize[h->seq[si].idx]; });
+                else if (s0.kind == 9)
+                    rc = build([&](ccsd_ctx* h) {
+                                   const int bi = h->seq[si].idx;
+                                   return ToC64Op{h->shadow[bi], h->buf[bi], h->bufsize[bi]};
+                               },
+                               [&](ccsd_ctx* h) { return h->bufsize[h->seq[si].idx]; });
+                else if (s0.kind == 11)
+                    rc = build([&](ccsd_ctx* h) { return fock_terms_op(h); }, [&](ccsd_ctx* h) { return h->n2; });
+                else
+                    rc = build([&](ccsd_ctx* h) {
+                                   const int bi = h->seq[si].idx;
+                                   return ToC64TOp{h->shadow[bi], h->buf[bi], h->N, h->v};
+                               },
+                               [&](ccsd_ctx* h) { return h->bufsize[h->seq[si].idx]; });
+                if (rc) return rc;
+                break;
+            }
+            case 5: {
+                std::vector<EmbedArgs> ops;
+                std::vector<long long> blocks;
+                for (ccsd_ctx* h : G.m) {
+                    const EmbedPlan& e = h->embeds[h->seq[si].idx];
+                    if (e.oz) { refuse("grouped launches run split-TF32 and FP64 steps only"); return CCSD_ERR_INVALID; }
+                    ops.push_back(embed_op(h, e));
+                    blocks.push_back(row_blocks((long long)e.a.nblk * e.a.R));
+                }
+                if ((rc = make_grouped(G, ops, blocks, st, gl))) return rc;
+                break;
+            }
+            case 10: {
+                std::vector<WprimeListArgs> ops;
+                std::vector<long long> blocks;
+                for (ccsd_ctx* h : G.m) {
+                    const WListPlan& w = h->wlists[h->seq[si].idx];
+                    if (w.oz) { refuse("grouped launches run split-TF32 and FP64 steps only"); return CCSD_ERR_INVALID; }
+                    ops.push_back(wprime_op(h, w));
+                    blocks.push_back(row_blocks((long long)w.a.nblk * w.a.ngrp));
+                }
+                if ((rc = make_grouped(G, ops, blocks, st, gl))) return rc;
+                break;
+            }
+            case 6: {
+                std::vector<CUtensorMap> maps;
+                std::vector<TcArgs> args;
+                std::vector<long long> prefix(1, 0);
+                for (ccsd_ctx* h : G.m) {
+                    const TcPlan& t = h->tcs[h->seq[si].idx];
+                    if (t.oz) { refuse("grouped launches run split-TF32 and FP64 steps only"); return CCSD_ERR_INVALID; }
+                    maps.push_back(t.mA_big); maps.push_back(t.mA_small);
+                    maps.push_back(t.mB_big); maps.push_back(t.mB_small);
+                    TcArgs a = t.a;
+                    a.C = h->buf[t.c];
+                    a.err = G.d_err;
+                    args.push_back(a);
+                    prefix.push_back(prefix.back() + t.blocks);
+                }
+                const long long total = prefix.back();
+                if (total > 2147483647LL) { refuse("a grouped launch exceeds 2^31 - 1 blocks"); return CCSD_ERR_INVALID; }
+                const CUtensorMap* d_maps = group_upload(G, maps, st, &rc);
+                if (rc) return rc;
+                const TcArgs* d_args = group_upload(G, args, st, &rc);
+                if (rc) return rc;
+                const long long* d_prefix = group_upload(G, prefix, st, &rc);
+                if (rc) return rc;
+                gl.launches = total > 0 ? 1 : 0;
+                gl.fn = [d_maps, d_args, d_prefix, n, total](cudaStream_t s) {
+                    if (total > 0)
+                        tc_gemm_grouped_kernel<<<(unsigned)total, TC_THREADS, TC_SMEM_BYTES, s>>>(d_maps, d_args, d_prefix, n);
+                };
+                break;
+            }
+            default:
+                refuse("a plan step kind has no grouped launch");
+                return CCSD_ERR_INVALID;
+        }
+        G.res.push_back(gl);
+    }
+    // max|R| of every member, then the update of those not converged
+    {
+        std::vector<MaxabsOp> mx;
+        std::vector<FinalMaxOp> fm;
+        std::vector<UpdateOp> up;
+        std::vector<long long> bm, bf, bu;
+        for (int i = 0; i < n; ++i) {
+            ccsd_ctx* h = G.m[i];
+            const long long nn = h->n1 + h->n2;
+            mx.push_back(MaxabsOp{h->res, nn, h->red});
+            bm.push_back(h->red_blocks);
+            fm.push_back(FinalMaxOp{h->red, h->red_blocks, d_norms + i});
+            bf.push_back(1);
+            up.push_back(update_op(h, d_skip ? d_skip + i : nullptr));
+            bu.push_back(grid_blocks(ew_grid(nn)));
+        }
+        GLaunch a1, a2;
+        if ((rc = make_grouped(G, mx, bm, st, a1)) || (rc = make_grouped(G, fm, bf, st, a2)) ||
+            (rc = make_grouped(G, up, bu, st, G.update)))
+            return rc;
+        G.norms.launches = a1.launches + a2.launches;
+        G.norms.fn = [a1, a2](cudaStream_t s) { a1.fn(s); a2.fn(s); };
+    }
+    CK(cudaStreamSynchronize(st));
+    return 0;
+}
+
+void group_residual(const Group& G, cudaStream_t st) {
+    for (const GLaunch& gl : G.res) gl.fn(st);
+}
+
+int group_launches(const Group& G, bool with_update) {
+    int n = G.norms.launches + (with_update ? G.update.launches : 0);
+    for (const GLaunch& gl : G.res) n += gl.launches;
+    return n;
+}
+
+// Reads and clears the group's tensor-core error word (synchronizes st).
+int group_check_err(const Group& G, cudaStream_t st) {
+    if (!G.d_err) return 0;
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, G.d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (flag) {
+        snprintf(g_errbuf, sizeof g_errbuf, "tensor-core GEMM wait timed out (code %d)", flag);
+        CK(cudaMemsetAsync(G.d_err, 0, sizeof(int), st));
+        return CCSD_ERR_TIMEOUT;
+    }
+    return 0;
+}
 
 }  // namespace
 
+// ================================================================ batched form
+// n independent problems: members are partitioned into groups by plan signature;
+// one iteration (every group's residual, max|R| per member, update of the members
+// not converged) is captured once in a CUDA graph, each group on a stream of its own
+// (they run concurrently), and replayed.
 struct ccsd_batch {
     int n = 0;
     std::vector<ccsd_ctx*> m;
     cudaStream_t st = nullptr;
+    std::vector<cudaStream_t> gst;                 // one stream per group
+    std::vector<cudaEvent_t> gev;
     int fp32 = 0;
-    std::vector<std::vector<size_t>> gemm_steps;   // per member: seq index of each active GEMM
-    std::vector<BatchGroup> groups[2];             // [fp32]
-    int tuned[2] = {0, 0};
+    std::vector<std::unique_ptr<Group>> groups;   // held by pointer: launches keep pointers into them
+    int tuned = 0;
     std::vector<void*> owned;
     double* d_norms = nullptr;
     int* d_done = nullptr;
-    double2* d_energy = nullptr;
     std::vector<int> done;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    long long launches = 0;
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -2060,176 +2496,73 @@ int batch_alloc(ccsd_batch* B, size_t bytes, void** p) {
     return 0;
 }
 
-long long tiles_for(const GemmArgs& a, int cfg, int* tm, int* tn) {
-    *tm = (a.M + CFG_BM[cfg] - 1) / CFG_BM[cfg];
-    *tn = (a.N + CFG_BN[cfg] - 1) / CFG_BN[cfg];
-    return (long long)*tm * *tn * a.nbatch;
-}
-
-// (Re)builds the grouped launch descriptors of one precision with the tile
-// shapes in cfgs (one per group).
-int batch_build_groups(ccsd_batch* B, int fp32, const std::vector<int>& cfgs) {
-    const int ng = (int)B->gemm_steps[0].size();
-    std::vector<BatchGroup>& G = B->groups[fp32];
-    if ((int)G.size() != ng) G.assign(ng, BatchGroup());
-    for (int g = 0; g < ng; ++g) {
-        BatchGroup& bg = G[g];
-        bg.cfg = cfgs[g];
-        bg.args.clear();
-        bg.split_members.clear();
-        long long tot = 0;
-        std::vector<long long> prefix;
-        // group-wide split: only when the whole group cannot fill the GPU
-        long long plain = 0;
-        for (int i = 0; i < B->n; ++i) {
-            int tm, tn;
-            plain += tiles_for(B->m[i]->gemms[B->m[i]->seq[B->gemm_steps[i][g]].idx].args, bg.cfg, &tm, &tn);
-        }
-        const int want = plain < 2 * kSMs ? (int)((4 * kSMs + plain - 1) / std::max(1LL, plain)) : 1;
-        for (int i = 0; i < B->n; ++i) {
-            ccsd_ctx* h = B->m[i];
-            const GemmPlan& p = h->gemms[h->seq[B->gemm_steps[i][g]].idx];
-            GemmArgs a = p.args;
-            int tm, tn;
-            tiles_for(a, bg.cfg, &tm, &tn);
-            a.tiles_m = tm; a.tiles_n = tn;
-            const int ns = std::max(1, std::min(want, a.nchunk));
-            a.chunks_per_split = (a.nchunk + ns - 1) / ns;
-            a.nsplit = (a.nchunk + a.chunks_per_split - 1) / a.chunks_per_split;
-            if (a.nbatch == 0) a.nsplit = 1;
-            if (a.nsplit > 1) {
-                const size_t need = (size_t)a.nsplit * a.nbatch * a.M * a.N;
-                if (need > h->work_elems) {
-                    void* w = nullptr;
-                    int rc = batch_alloc(B, need * 16, &w);
-                    if (rc) return rc;
-                    h->work = (double2*)w;
-                    h->work_elems = need;
-                }
-                bg.split_members.push_back(i);
-            }
-            a.A = h->buf[p.a]; a.B = h->buf[p.b]; a.C = h->buf[p.c]; a.work = h->work;
-            a.A32 = (fp32 || h->in32[p.a]) ? h->shadow[p.a] : nullptr;
-            a.B32 = (fp32 || h->in32[p.b]) ? h->shadow[p.b] : nullptr;
-            prefix.push_back(tot);
-            tot += (long long)tm * tn * a.nbatch * a.nsplit;
-            bg.args.push_back(a);
-        }
-        prefix.push_back(tot);
-        bg.total = tot;
-        if (!bg.d_args) {
-            void* x = nullptr;
-            int rc = batch_alloc(B, sizeof(GemmArgs) * B->n, &x);
-            if (rc) return rc;
-            bg.d_args = (GemmArgs*)x;
-            if ((rc = batch_alloc(B, sizeof(long long) * (B->n + 1), &x))) return rc;
-            bg.d_prefix = (long long*)x;
-        }
-        CK(cudaMemcpyAsync(bg.d_args, bg.args.data(), sizeof(GemmArgs) * B->n, cudaMemcpyHostToDevice, B->st));
-        CK(cudaMemcpyAsync(bg.d_prefix, prefix.data(), sizeof(long long) * (B->n + 1), cudaMemcpyHostToDevice, B->st));
-    }
-    CK(cudaStreamSynchronize(B->st));
-    return 0;
-}
-
-template <int BM, int BN, int TM, int TN>
-void grouped_launch(ccsd_batch* B, const BatchGroup& bg, int fp32) {
-    const long long ctas = std::min<long long>(bg.total, (long long)kSMs * 8);
-    if (fp32)
-        zgemm_grouped_kernel<BM, BN, 8, TM, TN, float><<<(unsigned)ctas, 256, 0, B->st>>>(bg.d_args, bg.d_prefix, B->n, bg.total);
-    else
-        zgemm_grouped_kernel<BM, BN, 8, TM, TN, double><<<(unsigned)ctas, 256, 0, B->st>>>(bg.d_args, bg.d_prefix, B->n, bg.total);
-}
-
-void launch_group(ccsd_batch* B, const BatchGroup& bg, int fp32) {
-    if (bg.total <= 0 || !bg.d_args) return;
-    switch (bg.cfg) {
-        case CFG_64x64: grouped_launch<64, 64, 4, 4>(B, bg, fp32); break;
-        case CFG_64x32: grouped_launch<64, 32, 4, 2>(B, bg, fp32); break;
-        case CFG_128x16: grouped_launch<128, 16, 8, 1>(B, bg, fp32); break;
-        case CFG_32x16: grouped_launch<32, 16, 2, 1>(B, bg, fp32); break;
-        default: grouped_launch<16, 16, 1, 1>(B, bg, fp32); break;
-    }
-    ++B->launches;
-    for (int i : bg.split_members) {
-        const GemmArgs& a = bg.args[i];
-        zgemm_split_reduce<<<ew_grid((long long)a.nbatch * a.M * a.N), 256, 0, B->st>>>(a);
-        ++B->launches;
-    }
-}
-
-// One residual of every member, contractions grouped.
-void batch_residual(ccsd_batch* B) {
-    const int fp32 = B->fp32;
-    const int ng = (int)B->gemm_steps[0].size();
-    std::vector<size_t> pos((size_t)B->n, 0);
-    for (int g = 0; g <= ng; ++g) {
-        for (int i = 0; i < B->n; ++i) {
-            ccsd_ctx* h = B->m[i];
-            const size_t end = g < ng ? B->gemm_steps[i][g] : h->seq.size();
-            for (size_t si = pos[i]; si < end; ++si)
-                if (step_active(h, h->seq[si]) && h->seq[si].kind != 0) { launch_step(h, si); ++B->launches; }
-            pos[i] = end + 1;
-        }
-        if (g < ng && g < (int)B->groups[fp32].size()) launch_group(B, B->groups[fp32][g], fp32);
-    }
-}
-
-// Residual, per-member max|R| into d_norms, update of unconverged members.
+// Residual of every member, max|R| into d_norms, update of unconverged members; the
+// groups run on their own streams, forked from and joined into B->st.
 void batch_iteration_body(ccsd_batch* B) {
-    batch_residual(B);
-    for (int i = 0; i < B->n; ++i) {
-        ccsd_ctx* h = B->m[i];
-        const long long nn = h->n1 + h->n2;
-        maxabs_partial<<<h->red_blocks, 256, 0, B->st>>>(h->res, nn, h->red);
-        final_max<<<1, 32, 0, B->st>>>(h->red, h->red_blocks, B->d_norms + i);
-        update_kernel<<<ew_grid(nn), 256, 0, B->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_R1], h->buf[B_R2],
-                                                      h->eo, h->ev, h->kb_of, h->N, h->o, h->v, nullptr, nullptr,
-                                                      B->d_done + i);
-        B->launches += 3;
+    cudaEventRecord(B->fork, B->st);
+    for (size_t g = 0; g < B->groups.size(); ++g) {
+        cudaStreamWaitEvent(B->gst[g], B->fork, 0);
+        group_residual(*B->groups[g], B->gst[g]);
+        B->groups[g]->norms.fn(B->gst[g]);
+        B->groups[g]->update.fn(B->gst[g]);
+        cudaEventRecord(B->gev[g], B->gst[g]);
+        cudaStreamWaitEvent(B->st, B->gev[g], 0);
     }
 }
 
-// Autotuner: time every tile shape on every grouped contraction and keep the
+// Autotuner: times every tile shape on every grouped contraction and keeps the
 // fastest.  Safe at any time: each residual re-initializes what it accumulates.
-int batch_autotune(ccsd_batch* B, int fp32) {
-    const int ng = (int)B->gemm_steps[0].size();
+int batch_autotune(ccsd_batch* B) {
     const int cands[5] = {CFG_64x64, CFG_64x32, CFG_128x16, CFG_32x16, CFG_16x16};
-    std::vector<int> best(ng, CFG_64x64);
-    std::vector<float> best_ms(ng, 1e30f);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    for (int c : cands) {
-        std::vector<int> cf(ng, c);
-        int rc = batch_build_groups(B, fp32, cf);
-        if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
-        for (int g = 0; g < ng; ++g) {
-            launch_group(B, B->groups[fp32][g], fp32);     // warm
-            CK(cudaEventRecord(e0, B->st));
-            launch_group(B, B->groups[fp32][g], fp32);
-            CK(cudaEventRecord(e1, B->st));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best_ms[g]) { best_ms[g] = ms; best[g] = c; }
+    int rc = 0;
+    for (auto& gp : B->groups) {
+        Group& G = *gp;
+        const int n = (int)G.m.size();
+        size_t gi = 0;
+        for (size_t k = 0; k < G.res.size() && !rc; ++k) {
+            if (G.res[k].gemm < 0) continue;
+            BatchGroup& bg = G.gemms[G.res[k].gemm];
+            const size_t si = G.steps[k];
+            int best = bg.cfg;
+            float best_ms = 1e30f;
+            for (int c : cands) {
+                if ((rc = group_gemm_descriptors(G, bg, si, c, B->st))) break;
+                launch_gemm_group(bg, B->fp32, B->st, n);     // warm
+                cudaEventRecord(e0, B->st);
+                launch_gemm_group(bg, B->fp32, B->st, n);
+                cudaEventRecord(e1, B->st);
+                float ms = 0.f;
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    last_err(cudaGetLastError());
+                    rc = CCSD_ERR_CUDA;
+                    break;
+                }
+                if (ms < best_ms) { best_ms = ms; best = c; }
+            }
+            if (!rc) rc = group_gemm_descriptors(G, bg, si, best, B->st);
+            G.res[k].launches = (bg.total > 0 ? 1 : 0) + (bg.reduce ? 1 : 0);
+            ++gi;
         }
+        if (rc) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int rc = batch_build_groups(B, fp32, best);
     if (rc) return rc;
-    B->tuned[fp32] = 1;
+    CK(cudaStreamSynchronize(B->st));
+    B->tuned = 1;
     return 0;
 }
 
-int batch_capture(ccsd_batch* B, int fp32) {
+int batch_capture(ccsd_batch* B) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(B->st, cudaStreamCaptureModeThreadLocal));
     batch_iteration_body(B);
     cudaError_t e = cudaStreamEndCapture(B->st, &g);
     if (e != cudaSuccess) { last_err(e); return CCSD_ERR_CUDA; }
-    e = cudaGraphInstantiate(&B->graph[fp32], g, 0);
+    e = cudaGraphInstantiate(&B->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) { last_err(e); return CCSD_ERR_CUDA; }
     return 0;
@@ -2454,7 +2787,7 @@ int iter_begin(ccsd_ctx* h) {
     int rc = run_residual_async(h);
     if (rc) return rc;
     const long long n = h->n1 + h->n2;
-    maxabs_partial<<<h->red_blocks, 256, 0, h->st>>>(h->res, n, h->red);
+    maxabs_partial<<<h->red_blocks, 256, 0, h->st>>>(MaxabsOp{h->res, n, h->red});
     final_max<<<1, 32, 0, h->st>>>(h->red, h->red_blocks, h->red_out);
     h->launches += 2;
     CK(cudaMemcpyAsync(h->norm_host, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->st));
@@ -2464,6 +2797,8 @@ int iter_begin(ccsd_ctx* h) {
 
 // Second half: waits for the norm, then the convergence test and the update
 // t <- t + R/D (plus DIIS) unless converged.
+int iter_finish(ccsd_ctx* h, double mr, int* done);
+
 int iter_end(ccsd_ctx* h, int* done, double* max_resid) {
     *done = 0;
     CK(cudaEventSynchronize(h->ev_norm));
@@ -2471,16 +2806,24 @@ int iter_end(ccsd_ctx* h, int* done, double* max_resid) {
     if (rc) return rc;
     if (h->trace && (rc = trace_collect(h, 0, h->seq.size()))) return rc;
     const double mr = *h->norm_host;
-    const long long n = h->n1 + h->n2;
     *max_resid = mr;
+    return iter_finish(h, mr, done);
+}
+
+// The convergence test on max|R| = mr and, unless converged, the update t <- t + R/D
+// with DIIS extrapolation (enqueued on the handle's stream; the DIIS inner products
+// synchronize it).
+int iter_finish(ccsd_ctx* h, double mr, int* done) {
+    int rc = 0;
+    *done = 0;
+    const long long n = h->n1 + h->n2;
     if (!std::isfinite(mr)) { refuse("max|R| is not finite: the iteration diverged"); return CCSD_ERR_DIVERGED; }
     if (mr < h->cfg.conv_tol) { *done = 1; return CCSD_OK; }
     const int depth = h->cfg.diis_depth;
     const size_t tu = h->seq.size();     // trace slot of the update
     if (h->trace) cudaEventRecord(h->ev0[tu], h->st);
     if (depth == 0) {
-        update_kernel<<<ew_grid(n), 256, 0, h->st>>>(h->buf[B_T1], h->buf[B_T2], h->buf[B_R1], h->buf[B_R2],
-                                                     h->eo, h->ev, h->kb_of, h->N, h->o, h->v, nullptr, nullptr);
+        update_kernel<<<ew_grid(n), 256, 0, h->st>>>(update_op(h, nullptr));
         ++h->launches;
         if (h->trace) { cudaEventRecord(h->ev1[tu], h->st); if ((rc = trace_collect(h, tu, tu + 1))) return rc; }
     } else {
@@ -2525,12 +2868,18 @@ int iter_end(ccsd_ctx* h, int* done, double* max_resid) {
 
 
 // ================================================================ serving form
-// A host thread admits submitted solves by device-memory footprint, gives each
-// admitted solve its own stream and handle (integrals and amplitudes stay
-// resident until it finishes), and advances all admitted solves in rounds: it
-// first enqueues one iteration of every solve (so their kernels run
-// concurrently on the GPU), then completes them one by one.  Converged solves
-// retire, free their memory and make room for the queue.
+// A host thread admits submitted solves by device-memory footprint (each gets a
+// handle whose integrals and amplitudes stay resident until it finishes) and
+// advances all admitted solves in rounds.  A round is one iteration of every
+// admitted solve: the solves are partitioned into groups of equal plan signature,
+// precision state and contraction tile shapes, every step of the residual is ONE
+// grouped launch per group (the groups on streams of their own, forked from the
+// server's stream), all max|R| come back in one copy, and then each solve takes its
+// convergence test and update (with DIIS).  Group members keep the split-K choices
+// of their own plans, so a solve's iterates are bitwise those it has alone.  Solves
+// in the Ozaki arithmetic run their residual on their own.  Converged solves retire,
+// free their memory and make room for the queue; a group is rebuilt only when its
+// membership changes.
 namespace {
 
 struct ServerReq {
@@ -2544,7 +2893,6 @@ struct ServerReq {
     double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
     size_t bytes = 0;
     ccsd_t h = nullptr;
-    cudaStream_t st = nullptr;
 };
 
 }  // namespace
@@ -2553,6 +2901,8 @@ struct ccsd_server {
     size_t budget = 0, used = 0;
     int max_slots = 1;
     int device = 0;
+    cudaStream_t st = nullptr;     // every device operation of the server
+    bool own_stream = false;
     std::mutex mu;
     std::condition_variable cv;
     std::deque<ServerReq*> pending;
@@ -2562,6 +2912,13 @@ struct ccsd_server {
     bool stop = false;
     std::thread th;
     std::chrono::steady_clock::time_point t0;
+    // grouped rounds (touched by the loop thread only)
+    std::map<std::vector<long long>, std::unique_ptr<Group>> groups;
+    std::vector<cudaStream_t> gst;
+    std::vector<cudaEvent_t> gev;
+    cudaEvent_t fork = nullptr;
+    double* h_norms = nullptr;     // pinned, max_slots
+    long long rounds = 0, grouped_launches = 0;
 };
 
 namespace {
@@ -2589,13 +2946,88 @@ void server_finish(ccsd_server* S, ServerReq* r, int state) {
         ccsd_destroy(r->h);
         r->h = nullptr;
     }
-    if (r->st) { cudaStreamDestroy(r->st); r->st = nullptr; }
     std::lock_guard<std::mutex> lock(S->mu);
     r->e_re = e_re;
     r->e_im = e_im;
     r->t_done = server_now(S);
     r->state = state;
     S->used -= r->bytes;
+}
+
+// Grouping key of a solve in its current arithmetic: solves with equal keys share every
+// grouped launch of a round.
+std::vector<long long> server_key(const ccsd_ctx* h) {
+    std::vector<long long> k{h->fp32, h->oz_on, h->cfg.precision};
+    for (const Step& st : h->seq) {
+        k.push_back(st.kind * 16 + st.mode);
+        if (st.kind == 0) k.push_back(h->gemms[st.idx].cfg);
+    }
+    return k;
+}
+
+// Builds the groups of this round's solves (reusing those whose membership is
+// unchanged); Ozaki-arithmetic solves go to `solo`.
+int server_groups(ccsd_server* S, const std::vector<ServerReq*>& act,
+                  std::vector<std::pair<Group*, std::vector<ServerReq*>>>& out, std::vector<ServerReq*>& solo) {
+    std::map<std::vector<long long>, std::vector<ServerReq*>> parts;
+    for (ServerReq* r : act) {
+        if (r->h->oz_on) solo.push_back(r);
+        else parts[server_key(r->h)].push_back(r);
+    }
+    std::map<std::vector<long long>, std::unique_ptr<Group>> next;
+    int rc = 0;
+    for (auto& kv : parts) {
+        std::vector<ccsd_ctx*> hs;
+        for (ServerReq* r : kv.second) hs.push_back(r->h);
+        auto it = S->groups.find(kv.first);
+        if (it != S->groups.end() && it->second->m == hs) {
+            next[kv.first] = std::move(it->second);
+        } else {
+            std::unique_ptr<Group> G(new (std::nothrow) Group());
+            if (!G) return CCSD_ERR_OOM;
+            G->m = hs;
+            if ((rc = group_build(*G, hs[0]->fp32, {}, nullptr, nullptr, S->st, true))) { group_free(*G); return rc; }
+            next[kv.first] = std::move(G);
+        }
+        out.emplace_back(next[kv.first].get(), kv.second);
+    }
+    for (auto& kv : S->groups) if (kv.second) group_free(*kv.second);
+    S->groups = std::move(next);
+    while (S->gst.size() < out.size()) {
+        cudaStream_t gs = nullptr;
+        cudaEvent_t ge = nullptr;
+        if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return CCSD_ERR_CUDA; }
+        S->gst.push_back(gs);
+        if (cudaEventCreateWithFlags(&ge, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); return CCSD_ERR_CUDA; }
+        S->gev.push_back(ge);
+    }
+    return 0;
+}
+
+// Completes one solve's iteration from its max|R| (convergence test, update, phase
+// changes); false if the request finished.
+bool server_complete(ccsd_server* S, ServerReq* r, int rc, int done, double mr) {
+    int iters = 0;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        r->max_resid = mr;
+        if (!rc && !done) iters = ++r->iters;
+    }
+    if (rc) { server_finish(S, r, rc); return false; }
+    if (!done) {
+        if (iters >= r->cfg.max_iter) { server_finish(S, r, CCSD_ERR_NOT_CONVERGED); return false; }
+        if (r->phase == 1 && --r->polish_left <= 0) { server_finish(S, r, 2); return false; }
+        return true;
+    }
+    if (r->phase == 0 && r->polish_left > 0) {    // mixed phase done: FP64 (or Ozaki) polish
+        r->phase = 1;
+        const int prc = ccsd_set_precision(r->h, r->cfg.polish_precision == CCSD_OZAKI ? CCSD_OZAKI : CCSD_FP64);
+        if (prc) { server_finish(S, r, prc); return false; }
+        r->h->cfg.conv_tol = r->cfg.conv_tol;
+        return true;
+    }
+    server_finish(S, r, 2);
+    return false;
 }
 
 void server_loop(ccsd_server* S) {
@@ -2606,7 +3038,7 @@ void server_loop(ccsd_server* S) {
             std::unique_lock<std::mutex> lock(S->mu);
             if (S->active.empty())
                 S->cv.wait(lock, [&] { return S->stop || !S->pending.empty(); });
-            if (S->stop && S->active.empty() && S->pending.empty()) return;
+            if (S->stop && S->active.empty() && S->pending.empty()) break;
             if (S->stop) {                         // cancel what has not started
                 for (ServerReq* r : S->pending) { r->state = CCSD_ERR_INVALID; r->t_done = server_now(S); }
                 S->pending.clear();
@@ -2626,9 +3058,7 @@ void server_loop(ccsd_server* S) {
             }
         }
         for (ServerReq* r : admit) {
-            int rc = CCSD_OK;
-            if (cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); rc = CCSD_ERR_CUDA; }
-            if (!rc) rc = ccsd_create(&r->cfg, &r->in, r->st, &r->h);
+            int rc = ccsd_create(&r->cfg, &r->in, S->st, &r->h);
             if (rc) { server_finish(S, r, rc); continue; }
             r->polish_left = r->cfg.precision == CCSD_MIXED ? r->cfg.polish_iters : 0;
             if (r->cfg.precision == CCSD_MIXED) r->h->cfg.conv_tol = std::max(r->cfg.mixed_tol, r->cfg.conv_tol);
@@ -2637,43 +3067,62 @@ void server_loop(ccsd_server* S) {
             r->state = 1;
             S->active.push_back(r);
         }
-        // one round: enqueue an iteration of every active solve, then complete each
         std::vector<ServerReq*> act;
         { std::lock_guard<std::mutex> lock(S->mu); act = S->active; }
-        std::vector<int> began(act.size(), 0);
-        for (size_t i = 0; i < act.size(); ++i) began[i] = iter_begin(act[i]->h);
+        if (act.empty()) continue;
+        // one round: grouped residuals and norms of every group, one copy of the norms
+        std::vector<std::pair<Group*, std::vector<ServerReq*>>> grp;
+        std::vector<ServerReq*> solo;
+        int grc = server_groups(S, act, grp, solo);
         std::vector<ServerReq*> keep;
-        for (size_t i = 0; i < act.size(); ++i) {
-            ServerReq* r = act[i];
+        if (grc) {                                 // groups could not be built: fail the round's solves
+            for (ServerReq* r : act) server_finish(S, r, grc);
+            std::lock_guard<std::mutex> lock(S->mu);
+            S->active.clear();
+            continue;
+        }
+        cudaEventRecord(S->fork, S->st);
+        int slot = 0;
+        std::vector<int> first(grp.size(), 0);
+        for (size_t g = 0; g < grp.size(); ++g) {
+            Group& G = *grp[g].first;
+            cudaStreamWaitEvent(S->gst[g], S->fork, 0);
+            group_residual(G, S->gst[g]);
+            G.norms.fn(S->gst[g]);
+            first[g] = slot;
+            cudaMemcpyAsync(S->h_norms + slot, G.d_norms, sizeof(double) * G.m.size(), cudaMemcpyDeviceToHost, S->gst[g]);
+            slot += (int)G.m.size();
+            cudaEventRecord(S->gev[g], S->gst[g]);
+            cudaStreamWaitEvent(S->st, S->gev[g], 0);
+            S->grouped_launches += group_launches(G, false);
+        }
+        std::vector<int> began(solo.size(), 0);
+        for (size_t i = 0; i < solo.size(); ++i) began[i] = iter_begin(solo[i]->h);
+        int src = cudaStreamSynchronize(S->st) == cudaSuccess ? 0 : CCSD_ERR_CUDA;
+        if (src) last_err(cudaGetLastError());
+        ++S->rounds;
+        for (size_t g = 0; g < grp.size(); ++g) {
+            int rc = src ? src : group_check_err(*grp[g].first, S->st);
+            for (size_t i = 0; i < grp[g].second.size(); ++i) {
+                ServerReq* r = grp[g].second[i];
+                int done = 0;
+                const double mr = S->h_norms[first[g] + i];
+                int frc = rc ? rc : iter_finish(r->h, mr, &done);
+                if (server_complete(S, r, frc, done, mr)) keep.push_back(r);
+            }
+        }
+        for (size_t i = 0; i < solo.size(); ++i) {
+            ServerReq* r = solo[i];
             int done = 0, rc = began[i];
             double mr = 0.0;
             if (!rc) rc = iter_end(r->h, &done, &mr);
-            int iters = 0;
-            {
-                std::lock_guard<std::mutex> lock(S->mu);
-                r->max_resid = mr;
-                if (!rc && !done) iters = ++r->iters;
-            }
-            if (rc) { server_finish(S, r, rc); continue; }
-            if (!done) {
-                if (iters >= r->cfg.max_iter) { server_finish(S, r, CCSD_ERR_NOT_CONVERGED); continue; }
-                if (r->phase == 1 && --r->polish_left <= 0) { server_finish(S, r, 2); continue; }
-                keep.push_back(r);
-                continue;
-            }
-            if (r->phase == 0 && r->polish_left > 0) {    // mixed phase done: FP64 polish
-                r->phase = 1;
-                const int prc = ccsd_set_precision(r->h, r->cfg.polish_precision == CCSD_OZAKI ? CCSD_OZAKI : CCSD_FP64);
-                if (prc) { server_finish(S, r, prc); continue; }
-                r->h->cfg.conv_tol = r->cfg.conv_tol;
-                keep.push_back(r);
-                continue;
-            }
-            server_finish(S, r, 2);
+            if (server_complete(S, r, rc, done, mr)) keep.push_back(r);
         }
         std::lock_guard<std::mutex> lock(S->mu);
         S->active = keep;
     }
+    for (auto& kv : S->groups) if (kv.second) group_free(*kv.second);
+    S->groups.clear();
 }
 
 }  // namespace
@@ -3110,6 +3559,7 @@ int ccsd_batch_create(int n, const ccsd_config* cfgs, const ccsd_inputs* inputs,
     B->n = n;
     auto fail = [&](int code) { ccsd_batch_destroy(B); return code; };
     if (cudaStreamCreateWithFlags(&B->st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); B->st = nullptr; return fail(CCSD_ERR_CUDA); }
+    if (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); B->fork = nullptr; return fail(CCSD_ERR_CUDA); }
     for (int i = 0; i < n; ++i) {
         ccsd_t h = nullptr;
         int rc = ccsd_create(&cfgs[i], &inputs[i], B->st, &h);
@@ -3117,26 +3567,41 @@ int ccsd_batch_create(int n, const ccsd_config* cfgs, const ccsd_inputs* inputs,
         B->m.push_back(h);
     }
     B->fp32 = cfgs[0].precision == CCSD_MIXED ? 1 : 0;
-    for (int i = 0; i < n; ++i) {
-        std::vector<size_t> gs;
-        for (size_t si = 0; si < B->m[i]->seq.size(); ++si)
-            if (B->m[i]->seq[si].kind == 0 && step_active(B->m[i], B->m[i]->seq[si])) gs.push_back(si);
-        if (i > 0 && gs.size() != B->gemm_steps[0].size()) {
-            refuse("batch members have different contraction sequences");
-            return fail(CCSD_ERR_INVALID);
-        }
-        B->gemm_steps.push_back(gs);
-    }
     void* p = nullptr;
     int rc;
     if ((rc = batch_alloc(B, sizeof(double) * n, &p))) return fail(rc);
     B->d_norms = (double*)p;
     if ((rc = batch_alloc(B, sizeof(int) * n, &p))) return fail(rc);
     B->d_done = (int*)p;
-    if ((rc = batch_alloc(B, sizeof(double2) * n, &p))) return fail(rc);
-    B->d_energy = (double2*)p;
     B->done.assign(n, 0);
     if (cudaMemsetAsync(B->d_done, 0, sizeof(int) * n, B->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
+    // groups of members with equal plan signatures (their members' norms and done flags
+    // are contiguous slices of d_norms / d_done)
+    std::vector<std::pair<std::vector<std::pair<int, int>>, std::vector<int>>> classes;
+    for (int i = 0; i < n; ++i) {
+        const auto sig = plan_signature(B->m[i]);
+        size_t c = 0;
+        while (c < classes.size() && classes[c].first != sig) ++c;
+        if (c == classes.size()) classes.push_back({sig, {}});
+        classes[c].second.push_back(i);
+    }
+    // the members are renumbered group by group so that each group's slice is contiguous;
+    // `order` maps a slot of d_norms back to the caller's member index
+    int slot = 0;
+    for (auto& cl : classes) {
+        B->groups.emplace_back(new (std::nothrow) Group());
+        if (!B->groups.back()) return fail(CCSD_ERR_OOM);
+        Group& g = *B->groups.back();
+        for (int i : cl.second) { g.m.push_back(B->m[i]); g.ids.push_back(i); }
+        if ((rc = group_build(g, B->fp32, {}, B->d_norms + slot, B->d_done + slot, B->st))) return fail(rc);
+        slot += (int)cl.second.size();
+        cudaStream_t gs = nullptr;
+        cudaEvent_t ge = nullptr;
+        if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return fail(CCSD_ERR_CUDA); }
+        B->gst.push_back(gs);
+        if (cudaEventCreateWithFlags(&ge, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); return fail(CCSD_ERR_CUDA); }
+        B->gev.push_back(ge);
+    }
     if (cudaStreamSynchronize(B->st) != cudaSuccess) return fail(CCSD_ERR_CUDA);
     *out = B;
     return CCSD_OK;
@@ -3145,24 +3610,24 @@ int ccsd_batch_create(int n, const ccsd_config* cfgs, const ccsd_inputs* inputs,
 int ccsd_batch_iterate(ccsd_batch_t B, int n_iter, int* done, double* max_resid) {
     ApiScope api_scope_;
     if (!B || n_iter < 0) return CCSD_ERR_INVALID;
-    const int f = B->fp32;
     int rc;
-    if (!B->tuned[f]) {
-        // start from each step's own tile shape (first member), warm every kernel, then tune
-        std::vector<int> cf;
-        for (size_t g = 0; g < B->gemm_steps[0].size(); ++g)
-            cf.push_back(B->m[0]->gemms[B->m[0]->seq[B->gemm_steps[0][g]].idx].cfg);
-        if ((rc = batch_build_groups(B, f, cf))) return rc;
-        batch_residual(B);
+    if (!B->tuned) {
+        // warm every kernel with one residual of each group, then tune the contractions
+        for (auto& g : B->groups) group_residual(*g, B->st);
         CK(cudaStreamSynchronize(B->st));
-        if ((rc = batch_autotune(B, f))) return rc;
+        if ((rc = batch_autotune(B))) return rc;
     }
-    if (!B->graph[f] && (rc = batch_capture(B, f))) return rc;
+    if (!B->graph && (rc = batch_capture(B))) return rc;
+    std::vector<double> slots((size_t)B->n, 0.0);
     std::vector<double> norms((size_t)B->n, 0.0);
     for (int it = 0; it < n_iter; ++it) {
-        CK(cudaGraphLaunch(B->graph[f], B->st));
-        CK(cudaMemcpyAsync(norms.data(), B->d_norms, sizeof(double) * B->n, cudaMemcpyDeviceToHost, B->st));
+        CK(cudaGraphLaunch(B->graph, B->st));
+        CK(cudaMemcpyAsync(slots.data(), B->d_norms, sizeof(double) * B->n, cudaMemcpyDeviceToHost, B->st));
         CK(cudaStreamSynchronize(B->st));
+        for (auto& g : B->groups) if ((rc = group_check_err(*g, B->st))) return rc;
+        // slot order -> member order
+        int slot = 0;
+        for (auto& g : B->groups) for (int id : g->ids) norms[id] = slots[slot++];
         bool changed = false, all = true;
         for (int i = 0; i < B->n; ++i) {
             if (!std::isfinite(norms[i])) { refuse("a batch member's max|R| is not finite: it diverged"); return CCSD_ERR_DIVERGED; }
@@ -3170,7 +3635,10 @@ int ccsd_batch_iterate(ccsd_batch_t B, int n_iter, int* done, double* max_resid)
             all = all && B->done[i];
         }
         if (changed) {
-            CK(cudaMemcpyAsync(B->d_done, B->done.data(), sizeof(int) * B->n, cudaMemcpyHostToDevice, B->st));
+            std::vector<int> flags((size_t)B->n);
+            slot = 0;
+            for (auto& g : B->groups) for (int id : g->ids) flags[slot++] = B->done[id];
+            CK(cudaMemcpyAsync(B->d_done, flags.data(), sizeof(int) * B->n, cudaMemcpyHostToDevice, B->st));
             CK(cudaStreamSynchronize(B->st));
         }
         if (all) break;
@@ -3207,15 +3675,14 @@ int ccsd_batch_stats(ccsd_batch_t B, long long* launches_per_iteration, int* til
     if (!B) return CCSD_ERR_INVALID;
     if (launches_per_iteration) {
         long long n = 0;
-        for (int i = 0; i < B->n; ++i) {
-            for (const Step& st : B->m[i]->seq) if (step_active(B->m[i], st) && st.kind != 0) ++n;
-            n += 3;
-        }
-        for (const BatchGroup& g : B->groups[B->fp32]) n += 1 + (long long)g.split_members.size();
+        for (auto& g : B->groups) n += group_launches(*g, true);
         *launches_per_iteration = n;
     }
-    if (tile_cfgs)
-        for (int g = 0; g < max_cfgs && g < (int)B->groups[B->fp32].size(); ++g) tile_cfgs[g] = B->groups[B->fp32][g].cfg;
+    if (tile_cfgs) {
+        int k = 0;
+        for (auto& g : B->groups)
+            for (const BatchGroup& bg : g->gemms) if (k < max_cfgs) tile_cfgs[k++] = bg.cfg;
+    }
     return CCSD_OK;
 }
 
@@ -3223,15 +3690,19 @@ int ccsd_batch_destroy(ccsd_batch_t B) {
     ApiScope api_scope_;
     if (!B) return CCSD_ERR_INVALID;
     if (B->st) cudaStreamSynchronize(B->st);
-    for (int f = 0; f < 2; ++f) if (B->graph[f]) cudaGraphExecDestroy(B->graph[f]);
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    for (auto& g : B->groups) if (g) group_free(*g);
     for (ccsd_ctx* h : B->m) ccsd_destroy(h);
     for (void* p : B->owned) cudaFree(p);
+    for (cudaStream_t s : B->gst) cudaStreamDestroy(s);
+    for (cudaEvent_t e : B->gev) cudaEventDestroy(e);
+    if (B->fork) cudaEventDestroy(B->fork);
     if (B->st) cudaStreamDestroy(B->st);
     delete B;
     return CCSD_OK;
 }
 
-int ccsd_server_create(size_t hbm_budget_bytes, int max_slots, ccsd_server_t* out) {
+int ccsd_server_create(size_t hbm_budget_bytes, int max_slots, void* stream, ccsd_server_t* out) {
     ApiScope api_scope_;
     if (!out || max_slots < 1 || max_slots > 1024 || hbm_budget_bytes == 0) return CCSD_ERR_INVALID;
     ccsd_server* S = new (std::nothrow) ccsd_server();
@@ -3239,12 +3710,25 @@ int ccsd_server_create(size_t hbm_budget_bytes, int max_slots, ccsd_server_t* ou
     S->budget = hbm_budget_bytes;
     S->max_slots = max_slots;
     S->t0 = std::chrono::steady_clock::now();
-    if (cudaGetDevice(&S->device) != cudaSuccess) { cudaGetLastError(); delete S; return CCSD_ERR_CUDA; }
+    auto fail = [&](int code) {
+        if (S->fork) cudaEventDestroy(S->fork);
+        if (S->h_norms) cudaFreeHost(S->h_norms);
+        if (S->own_stream && S->st) cudaStreamDestroy(S->st);
+        delete S;
+        return code;
+    };
+    if (cudaGetDevice(&S->device) != cudaSuccess) { cudaGetLastError(); return fail(CCSD_ERR_CUDA); }
+    S->st = (cudaStream_t)stream;
+    if (!S->st) {
+        if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); S->st = nullptr; return fail(CCSD_ERR_CUDA); }
+        S->own_stream = true;
+    }
+    if (cudaEventCreateWithFlags(&S->fork, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); S->fork = nullptr; return fail(CCSD_ERR_CUDA); }
+    if (cudaMallocHost(&S->h_norms, sizeof(double) * max_slots) != cudaSuccess) { cudaGetLastError(); S->h_norms = nullptr; return fail(CCSD_ERR_OOM); }
     try {
         S->th = std::thread(server_loop, S);
     } catch (...) {
-        delete S;
-        return CCSD_ERR_OOM;
+        return fail(CCSD_ERR_OOM);
     }
     *out = S;
     return CCSD_OK;
@@ -3308,6 +3792,12 @@ int ccsd_server_destroy(ccsd_server_t S) {
     S->cv.notify_one();
     if (S->th.joinable()) S->th.join();
     for (auto& kv : S->all) delete kv.second;
+    if (S->st) cudaStreamSynchronize(S->st);
+    for (cudaStream_t g : S->gst) cudaStreamDestroy(g);
+    for (cudaEvent_t e : S->gev) cudaEventDestroy(e);
+    if (S->fork) cudaEventDestroy(S->fork);
+    if (S->h_norms) cudaFreeHost(S->h_norms);
+    if (S->own_stream) cudaStreamDestroy(S->st);
     delete S;
     return CCSD_OK;
 }

@@ -24,53 +24,57 @@ __device__ __forceinline__ double2 ldz(const float2* p) { const float2 f = *p; r
 // Mixed form: t2_32 / taut_32 (when set) receive complex64 copies of t2 and tau~
 // for the FP32 contractions (a double->float conversion issues on GB300's FP64
 // pipe, so each element is converted once here instead of in every GEMM).
-__global__ void tau_kernel(const double2* __restrict__ t1, const double2* __restrict__ t2,
-                           double2* __restrict__ tau, double2* __restrict__ taut,
-                           const int* __restrict__ kb_of, int N, int o, int v,
-                           float2* __restrict__ t2_32 = nullptr, float2* __restrict__ taut_32 = nullptr)
-{
-    const long long blk = (long long)o * o * v * v;
-    const long long total = (long long)N * N * N * blk;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long kk = e / blk;
-        int r = (int)(e % blk);
-        const int b = r % v; r /= v;
-        const int a = r % v; r /= v;
-        const int j = r % o; const int i = r / o;
-        const int ka = (int)(kk % N), kj = (int)((kk / N) % N), ki = (int)(kk / ((long long)N * N));
-        const int kb = kb_of[kk];
-        double2 x = make_double2(0.0, 0.0);
-        if (ki == ka) {
-            const double2 p = cmul(t1[((long long)ki * o + i) * v + a], t1[((long long)kj * o + j) * v + b]);
-            x.x += p.x; x.y += p.y;
-        }
-        if (ki == kb) {
-            const double2 p = cmul(t1[((long long)ki * o + i) * v + b], t1[((long long)kj * o + j) * v + a]);
-            x.x -= p.x; x.y -= p.y;
-        }
-        const double2 t = t2[e];
-        tau[e] = make_double2(t.x + x.x, t.y + x.y);
-        const double2 tt = make_double2(t.x + 0.5 * x.x, t.y + 0.5 * x.y);
-        taut[e] = tt;
-        if (t2_32) {
-            t2_32[e] = make_float2((float)t.x, (float)t.y);
-            taut_32[e] = make_float2((float)tt.x, (float)tt.y);
+struct TauOp {
+    const double2* t1; const double2* t2;
+    double2* tau; double2* taut;
+    const int* kb_of; int N, o, v;
+    float2* t2_32; float2* taut_32;
+    // vb, nvb: this block's index and the block count of its (virtual) grid
+    __device__ void run(long long vb, long long nvb) const {
+        const long long blk = (long long)o * o * v * v;
+        const long long total = (long long)N * N * N * blk;
+        for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
+            const long long kk = e / blk;
+            int r = (int)(e % blk);
+            const int b = r % v; r /= v;
+            const int a = r % v; r /= v;
+            const int j = r % o; const int i = r / o;
+            const int ka = (int)(kk % N), kj = (int)((kk / N) % N), ki = (int)(kk / ((long long)N * N));
+            const int kb = kb_of[kk];
+            double2 x = make_double2(0.0, 0.0);
+            if (ki == ka) {
+                const double2 p = cmul(t1[((long long)ki * o + i) * v + a], t1[((long long)kj * o + j) * v + b]);
+                x.x += p.x; x.y += p.y;
+            }
+            if (ki == kb) {
+                const double2 p = cmul(t1[((long long)ki * o + i) * v + b], t1[((long long)kj * o + j) * v + a]);
+                x.x -= p.x; x.y -= p.y;
+            }
+            const double2 t = t2[e];
+            tau[e] = make_double2(t.x + x.x, t.y + x.y);
+            const double2 tt = make_double2(t.x + 0.5 * x.x, t.y + 0.5 * x.y);
+            taut[e] = tt;
+            if (t2_32) {
+                t2_32[e] = make_float2((float)t.x, (float)t.y);
+                taut_32[e] = make_float2((float)tt.x, (float)tt.y);
+            }
         }
     }
-}
+};
+__global__ void tau_kernel(const TauOp op) { op.run(blockIdx.x, gridDim.x); }
 
-// dst = conj(src) or dst = src, n elements
-template <typename TS>
-__global__ void copy_kernel(double2* __restrict__ dst, const TS* __restrict__ src, long long n, int conj)
-{
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
-        double2 s = ldz(src + e);
-        if (conj) s.y = -s.y;
-        dst[e] = s;
+// dst = conj(src) or dst = src, n elements; src is complex128, or complex64 (src32 set)
+struct CopyOp {
+    double2* dst; const double2* src; const float2* src32; long long n; int conj;
+    __device__ void run(long long vb, long long nvb) const {
+        for (long long e = vb * blockDim.x + threadIdx.x; e < n; e += nvb * blockDim.x) {
+            double2 s = src32 ? ldz(src32 + e) : ldz(src + e);
+            if (conj) s.y = -s.y;
+            dst[e] = s;
+        }
     }
-}
+};
+__global__ void copy_kernel(const CopyOp op) { op.run(blockIdx.x, gridDim.x); }
 
 // Batched 4-index permuted copy:
 //   dst[offD[b] + i0*d0 + i1*d1 + i2*d2 + i3*d3] = src[offS[b] + i0*s0 + i1*s1 + i2*s2 + i3*s3]
@@ -80,121 +84,142 @@ struct Perm4 {
     int d0, d1, d2, d3, s0, s1, s2, s3;
     int nbatch;
 };
-template <typename TS>
-__global__ void permute4_kernel(double2* __restrict__ dst, const TS* __restrict__ src, const Perm4 p)
-{
-    const long long blk = (long long)p.n0 * p.n1 * p.n2 * p.n3;
-    const long long total = blk * p.nbatch;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long b = e / blk;
-        int r = (int)(e % blk);
-        const int i3 = r % p.n3; r /= p.n3;
-        const int i2 = r % p.n2; r /= p.n2;
-        const int i1 = r % p.n1; const int i0 = r / p.n1;
-        dst[p.offD[b] + (long long)i0 * p.d0 + (long long)i1 * p.d1 + (long long)i2 * p.d2 + (long long)i3 * p.d3] =
-            ldz(src + p.offS[b] + (long long)i0 * p.s0 + (long long)i1 * p.s1 + (long long)i2 * p.s2 + (long long)i3 * p.s3);
+struct PermOp {
+    double2* dst; const double2* src; const float2* src32; Perm4 p;
+    __device__ void run(long long vb, long long nvb) const {
+        const long long blk = (long long)p.n0 * p.n1 * p.n2 * p.n3;
+        const long long total = blk * p.nbatch;
+        for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
+            const long long b = e / blk;
+            int r = (int)(e % blk);
+            const int i3 = r % p.n3; r /= p.n3;
+            const int i2 = r % p.n2; r /= p.n2;
+            const int i1 = r % p.n1; const int i0 = r / p.n1;
+            const long long so = p.offS[b] + (long long)i0 * p.s0 + (long long)i1 * p.s1 + (long long)i2 * p.s2 +
+                                 (long long)i3 * p.s3;
+            dst[p.offD[b] + (long long)i0 * p.d0 + (long long)i1 * p.d1 + (long long)i2 * p.d2 + (long long)i3 * p.d3] =
+                src32 ? ldz(src32 + so) : ldz(src + so);
+        }
     }
-}
+};
+__global__ void permute4_kernel(const PermOp op) { op.run(blockIdx.x, gridDim.x); }
 
 // R2 += Zr - Zr(i<->j) - Zr(a<->b) + Zr(both): the P_-(ij)P_-(ab) of Eq. ori_EqDouble
 // (operator of Sec. 2; swapping an index swaps its momentum too).  The terms under
 // P_-(ab) or P_-(ij) alone enter Zr at half weight (they are antisymmetric in the
 // other index pair), so this one sum applies all three operators.
-__global__ void antisym_kernel(double2* __restrict__ R2, const double2* __restrict__ Zr,
-                               const int* __restrict__ kb_of, int N, int o, int v)
-{
-    const long long blk = (long long)o * o * v * v;
-    const long long total = (long long)N * N * N * blk;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long kk = e / blk;
-        int r = (int)(e % blk);
-        const int b = r % v; r /= v;
-        const int a = r % v; r /= v;
-        const int j = r % o; const int i = r / o;
-        const int ka = (int)(kk % N), kj = (int)((kk / N) % N), ki = (int)(kk / ((long long)N * N));
-        const int kb = kb_of[kk];
-        // (ki,kj,ka)(i,j,a,b) ; (i<->j): (kj,ki,ka)(j,i,a,b) ; (a<->b): (ki,kj,kb)(i,j,b,a)
-        const long long e_ij = (((long long)kj * N + ki) * N + ka) * blk + (((long long)j * o + i) * v + a) * v + b;
-        const long long e_ab = (((long long)ki * N + kj) * N + kb) * blk + (((long long)i * o + j) * v + b) * v + a;
-        const long long e_2 = (((long long)kj * N + ki) * N + kb) * blk + (((long long)j * o + i) * v + b) * v + a;
-        const double2 z0 = Zr[e], z1 = Zr[e_ij], z2 = Zr[e_ab], z3 = Zr[e_2];
-        double2 out = R2[e];
-        out.x += z0.x - z1.x - z2.x + z3.x;
-        out.y += z0.y - z1.y - z2.y + z3.y;
-        R2[e] = out;
-    }
-}
-
-// Block-wise max |R| partials over an array (grid-stride; fixed per-thread order).
-__global__ void maxabs_partial(const double2* __restrict__ x, long long n, double* __restrict__ part)
-{
-    __shared__ double sm[256];
-    double m = 0.0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
-        const double2 z = x[e];
-        const double a = sqrt(z.x * z.x + z.y * z.y);
-        m = (a > m || a != a) ? a : m;     // NaN propagates
-    }
-    sm[threadIdx.x] = m;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            const double o2 = sm[threadIdx.x + s];
-            if (o2 > sm[threadIdx.x] || o2 != o2) sm[threadIdx.x] = o2;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
-}
-
-// t1 += R1 / D1, t2 += R2 / D2 (paper Sec. 4.4.19), D from the Fock diagonal
-// eo[k][i], ev[k][a].  When err != nullptr also stores e = R / D (DIIS error).
-__global__ void update_kernel(double2* __restrict__ t1, double2* __restrict__ t2,
-                              const double2* __restrict__ R1, const double2* __restrict__ R2,
-                              const double* __restrict__ eo, const double* __restrict__ ev,
-                              const int* __restrict__ kb_of, int N, int o, int v,
-                              double2* __restrict__ err1, double2* __restrict__ err2,
-                              const int* __restrict__ skip = nullptr)   // batched form: converged member
-{
-    if (skip && *skip) return;
-    const long long n1 = (long long)N * o * v;
-    const long long blk = (long long)o * o * v * v;
-    const long long total = n1 + (long long)N * N * N * blk;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        if (e < n1) {
-            const int a = (int)(e % v);
-            const int i = (int)((e / v) % o);
-            const int k = (int)(e / ((long long)o * v));
-            const double d = eo[k * o + i] - ev[k * v + a];
-            const double2 r = R1[e];
-            const double2 q = make_double2(r.x / d, r.y / d);
-            double2 t = t1[e];
-            t.x += q.x; t.y += q.y;
-            t1[e] = t;
-            if (err1) err1[e] = q;
-        } else {
-            const long long f = e - n1;
-            const long long kk = f / blk;
-            int r = (int)(f % blk);
+struct AntisymOp {
+    double2* R2; const double2* Zr; const int* kb_of; int N, o, v;
+    __device__ void run(long long vb, long long nvb) const {
+        const long long blk = (long long)o * o * v * v;
+        const long long total = (long long)N * N * N * blk;
+        for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
+            const long long kk = e / blk;
+            int r = (int)(e % blk);
             const int b = r % v; r /= v;
             const int a = r % v; r /= v;
             const int j = r % o; const int i = r / o;
             const int ka = (int)(kk % N), kj = (int)((kk / N) % N), ki = (int)(kk / ((long long)N * N));
             const int kb = kb_of[kk];
-            const double d = eo[ki * o + i] + eo[kj * o + j] - ev[ka * v + a] - ev[kb * v + b];
-            const double2 rr = R2[f];
-            const double2 q = make_double2(rr.x / d, rr.y / d);
-            double2 t = t2[f];
-            t.x += q.x; t.y += q.y;
-            t2[f] = t;
-            if (err2) err2[f] = q;
+            // (ki,kj,ka)(i,j,a,b) ; (i<->j): (kj,ki,ka)(j,i,a,b) ; (a<->b): (ki,kj,kb)(i,j,b,a)
+            const long long e_ij = (((long long)kj * N + ki) * N + ka) * blk + (((long long)j * o + i) * v + a) * v + b;
+            const long long e_ab = (((long long)ki * N + kj) * N + kb) * blk + (((long long)i * o + j) * v + b) * v + a;
+            const long long e_2 = (((long long)kj * N + ki) * N + kb) * blk + (((long long)j * o + i) * v + b) * v + a;
+            const double2 z0 = Zr[e], z1 = Zr[e_ij], z2 = Zr[e_ab], z3 = Zr[e_2];
+            double2 out = R2[e];
+            out.x += z0.x - z1.x - z2.x + z3.x;
+            out.y += z0.y - z1.y - z2.y + z3.y;
+            R2[e] = out;
         }
     }
-}
+};
+__global__ void antisym_kernel(const AntisymOp op) { op.run(blockIdx.x, gridDim.x); }
+
+// Block-wise max |R| partials over an array (grid-stride; fixed per-thread order).
+// part[vb] = max over this block's elements (blocks of 256 threads).
+struct MaxabsOp {
+    const double2* x; long long n; double* part;
+    __device__ void run(long long vb, long long nvb) const {
+        __shared__ double sm[256];
+        double m = 0.0;
+        for (long long e = vb * blockDim.x + threadIdx.x; e < n; e += nvb * blockDim.x) {
+            const double2 z = x[e];
+            const double a = sqrt(z.x * z.x + z.y * z.y);
+            m = (a > m || a != a) ? a : m;     // NaN propagates
+        }
+        sm[threadIdx.x] = m;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                const double o2 = sm[threadIdx.x + s];
+                if (o2 > sm[threadIdx.x] || o2 != o2) sm[threadIdx.x] = o2;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[vb] = sm[0];
+    }
+};
+__global__ void maxabs_partial(const MaxabsOp op) { op.run(blockIdx.x, gridDim.x); }
+
+// *out = max of n partials, in a fixed order (one thread of one block).
+struct FinalMaxOp {
+    const double* part; int n; double* out;
+    __device__ void run(long long vb, long long) const {
+        if (threadIdx.x == 0 && vb == 0) {
+            double m = 0.0;
+            for (int i = 0; i < n; ++i) { const double x = part[i]; if (x > m || x != x) m = x; }
+            *out = m;
+        }
+    }
+};
+
+// t1 += R1 / D1, t2 += R2 / D2 (paper Sec. 4.4.19), D from the Fock diagonal
+// eo[k][i], ev[k][a].  When err != nullptr also stores e = R / D (DIIS error).
+struct UpdateOp {
+    double2* t1; double2* t2;
+    const double2* R1; const double2* R2;
+    const double* eo; const double* ev;
+    const int* kb_of; int N, o, v;
+    double2* err1; double2* err2;
+    const int* skip;          // batched form: a converged member (its flag set) is not updated
+    __device__ void run(long long vb, long long nvb) const {
+        if (skip && *skip) return;
+        const long long n1 = (long long)N * o * v;
+        const long long blk = (long long)o * o * v * v;
+        const long long total = n1 + (long long)N * N * N * blk;
+        for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
+            if (e < n1) {
+                const int a = (int)(e % v);
+                const int i = (int)((e / v) % o);
+                const int k = (int)(e / ((long long)o * v));
+                const double d = eo[k * o + i] - ev[k * v + a];
+                const double2 r = R1[e];
+                const double2 q = make_double2(r.x / d, r.y / d);
+                double2 t = t1[e];
+                t.x += q.x; t.y += q.y;
+                t1[e] = t;
+                if (err1) err1[e] = q;
+            } else {
+                const long long f = e - n1;
+                const long long kk = f / blk;
+                int r = (int)(f % blk);
+                const int b = r % v; r /= v;
+                const int a = r % v; r /= v;
+                const int j = r % o; const int i = r / o;
+                const int ka = (int)(kk % N), kj = (int)((kk / N) % N), ki = (int)(kk / ((long long)N * N));
+                const int kb = kb_of[kk];
+                const double d = eo[ki * o + i] + eo[kj * o + j] - ev[ka * v + a] - ev[kb * v + b];
+                const double2 rr = R2[f];
+                const double2 q = make_double2(rr.x / d, rr.y / d);
+                double2 t = t2[f];
+                t.x += q.x; t.y += q.y;
+                t2[f] = t;
+                if (err2) err2[f] = q;
+            }
+        }
+    }
+};
+__global__ void update_kernel(const UpdateOp op) { op.run(blockIdx.x, gridDim.x); }
 
 // Energy partial sums: sum f_ia t_i^a + 1/4 sum <ij||ab> t_ij^ab
 //                    + 1/2 sum_{ki,kj} <i ki j kj||a ki b kj> t_i^a t_j^b.
@@ -244,11 +269,7 @@ __global__ void energy_partial(const double2* __restrict__ t1, const double2* __
 // Fixed-order final reductions (one block).
 __global__ void final_max(const double* __restrict__ part, int n, double* __restrict__ out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double m = 0.0;
-        for (int i = 0; i < n; ++i) { const double x = part[i]; if (x > m || x != x) m = x; }
-        *out = m;
-    }
+    FinalMaxOp{part, n, out}.run(blockIdx.x, gridDim.x);
 }
 __global__ void final_sum(const double* __restrict__ part, int n, double* __restrict__ out)
 {
@@ -295,64 +316,65 @@ __device__ __forceinline__ float2 cfma_conjb(float2 a, float2 b, float2 c) {
 }
 
 // dst[k][c][r] = (complex64) src[k][r][c] for nk blocks of n x n
-__global__ void to_c64_transpose_kernel(float2* __restrict__ dst, const double2* __restrict__ src, int nk, int n)
-{
-    const long long total = (long long)nk * n * n;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long k = e / ((long long)n * n);
-        const int rc = (int)(e % ((long long)n * n));
-        const int c = rc / n, r = rc % n;
-        const double2 z = src[(k * n + r) * n + c];
-        dst[e] = make_float2((float)z.x, (float)z.y);
+struct ToC64TOp {
+    float2* dst; const double2* src; int nk, n;
+    __device__ void run(long long vb, long long nvb) const {
+        const long long total = (long long)nk * n * n;
+        for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
+            const long long k = e / ((long long)n * n);
+            const int rc = (int)(e % ((long long)n * n));
+            const int c = rc / n, r = rc % n;
+            const double2 z = src[(k * n + r) * n + c];
+            dst[e] = make_float2((float)z.x, (float)z.y);
+        }
     }
-}
+};
+__global__ void to_c64_transpose_kernel(const ToC64TOp op) { op.run(blockIdx.x, gridDim.x); }
 
 // fvvpT is F'^{bf} transposed per k: fvvpT[kb][f][b], so that the threads of a warp
 // (consecutive b) read consecutive elements.
-__global__ void fock_terms_kernel(double2* __restrict__ Zr, const float2* __restrict__ t2,
-                                  const float2* __restrict__ t1, const float2* __restrict__ fvvpT,
-                                  const float2* __restrict__ foop, const float2* __restrict__ ooov,
-                                  const float2* __restrict__ ovvv, const int* __restrict__ kb_of,
-                                  int N, int o, int v)
-{
-    const long long blk = (long long)o * o * v * v;
-    const long long total = (long long)N * N * N * blk;
-    const long long vv = (long long)v * v, ov3 = (long long)o * v * vv, o3v = (long long)o * o * o * v;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long kk = e / blk;
-        int r = (int)(e % blk);
-        const int b = r % v; r /= v;
-        const int a = r % v; r /= v;
-        const int j = r % o; const int i = r / o;
-        const int ka = (int)(kk % N), kj = (int)((kk / N) % N), ki = (int)(kk / ((long long)N * N));
-        const int kb = kb_of[kk];
-        const float2* tb = t2 + kk * blk;
-        float2 p = make_float2(0.f, 0.f), q = make_float2(0.f, 0.f);
-        const float2* trow = tb + (((long long)i * o + j) * v + a) * v;             // t_ij^{a f}
-        const float2* fcol = fvvpT + (long long)kb * v * v + b;                     // F'^{b f}(kb) at f v
+struct FockTermsOp {
+    double2* Zr; const float2* t2; const float2* t1; const float2* fvvpT; const float2* foop;
+    const float2* ooov; const float2* ovvv; const int* kb_of; int N, o, v;
+    __device__ void run(long long vb, long long nvb) const {
+        const long long blk = (long long)o * o * v * v;
+        const long long total = (long long)N * N * N * blk;
+        const long long vv = (long long)v * v, ov3 = (long long)o * v * vv, o3v = (long long)o * o * o * v;
+        for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
+            const long long kk = e / blk;
+            int r = (int)(e % blk);
+            const int b = r % v; r /= v;
+            const int a = r % v; r /= v;
+            const int j = r % o; const int i = r / o;
+            const int ka = (int)(kk % N), kj = (int)((kk / N) % N), ki = (int)(kk / ((long long)N * N));
+            const int kb = kb_of[kk];
+            const float2* tb = t2 + kk * blk;
+            float2 p = make_float2(0.f, 0.f), q = make_float2(0.f, 0.f);
+            const float2* trow = tb + (((long long)i * o + j) * v + a) * v;             // t_ij^{a f}
+            const float2* fcol = fvvpT + (long long)kb * v * v + b;                     // F'^{b f}(kb) at f v
 #pragma unroll 4
-        for (int f = 0; f < v; ++f) p = cfma(trow[f], fcol[(long long)f * v], p);
-        const float2* oo = ooov + kk * o3v + ((long long)i * o + j) * o * v + b;    // <ij||r b>
-        const float2* ta = t1 + (long long)ka * o * v + a;                          // t_r^a(ka)
+            for (int f = 0; f < v; ++f) p = cfma(trow[f], fcol[(long long)f * v], p);
+            const float2* oo = ooov + kk * o3v + ((long long)i * o + j) * o * v + b;    // <ij||r b>
+            const float2* ta = t1 + (long long)ka * o * v + a;                          // t_r^a(ka)
 #pragma unroll 4
-        for (int rr = 0; rr < o; ++rr) q = cfma_conjb(ta[rr * v], oo[(long long)rr * v], q);
-        const float2* tn = tb + ((long long)i * o * v + a) * v + b;                 // t_in^{ab}, n stride v^2
-        const float2* fo = foop + (long long)kj * o * o + j;                        // F'_{n j}(kj)
+            for (int rr = 0; rr < o; ++rr) q = cfma_conjb(ta[rr * v], oo[(long long)rr * v], q);
+            const float2* tn = tb + ((long long)i * o * v + a) * v + b;                 // t_in^{ab}, n stride v^2
+            const float2* fo = foop + (long long)kj * o * o + j;                        // F'_{n j}(kj)
 #pragma unroll 4
-        for (int n = 0; n < o; ++n) q = cfma(tn[(long long)n * vv], fo[n * o], q);
-        const long long kjia = ((long long)kj * N + ki) * N + ka;
-        const float2* vb = ovvv + kjia * ov3 + (long long)j * v * vv + (long long)a * v + b;   // <j c||a b>
-        const float2* ti = t1 + ((long long)ki * o + i) * v;                        // t_i^c(ki)
+            for (int n = 0; n < o; ++n) q = cfma(tn[(long long)n * vv], fo[n * o], q);
+            const long long kjia = ((long long)kj * N + ki) * N + ka;
+            const float2* vbp = ovvv + kjia * ov3 + (long long)j * v * vv + (long long)a * v + b;   // <j c||a b>
+            const float2* ti = t1 + ((long long)ki * o + i) * v;                        // t_i^c(ki)
 #pragma unroll 4
-        for (int c = 0; c < v; ++c) q = cfma_conjb(ti[c], vb[(long long)c * vv], q);
-        double2 z = Zr[e];
-        z.x += 0.5 * ((double)p.x - (double)q.x);
-        z.y += 0.5 * ((double)p.y - (double)q.y);
-        Zr[e] = z;
+            for (int c = 0; c < v; ++c) q = cfma_conjb(ti[c], vbp[(long long)c * vv], q);
+            double2 z = Zr[e];
+            z.x += 0.5 * ((double)p.x - (double)q.x);
+            z.y += 0.5 * ((double)p.y - (double)q.y);
+            Zr[e] = z;
+        }
     }
-}
+};
+__global__ void fock_terms_kernel(const FockTermsOp op) { op.run(blockIdx.x, gridDim.x); }
 
 // ---------------------------------------------------------------------------
 // DIIS history on canonical momentum blocks.  t2 is antisymmetric under

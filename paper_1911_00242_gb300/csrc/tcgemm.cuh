@@ -158,10 +158,12 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
 //                   partial, adds them into FP32 registers, frees the buffer
 //                   (acc_empty), and at the end adds alpha * sum into the FP64 C.
 // Every wait is bounded; a timeout sets g.err and the CTA unwinds.
-__global__ void __launch_bounds__(TC_THREADS, 1)
-tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_constant__ CUtensorMap mapA_small,
-               const __grid_constant__ CUtensorMap mapB_big, const __grid_constant__ CUtensorMap mapB_small,
-               const TcArgs g)
+// `bid` is the CTA's tile index within its GEMM (tile + batch * tiles); the tensor maps
+// sit in kernel-parameter space (one GEMM per launch) or in global memory (grouped
+// launches of the batched form), written before the launch.
+__device__ __forceinline__ void tc_gemm_body(const CUtensorMap* mapA_big, const CUtensorMap* mapA_small,
+                                             const CUtensorMap* mapB_big, const CUtensorMap* mapB_small,
+                                             const TcArgs& g, long long bid)
 {
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte alignment for the swizzled stages
@@ -179,8 +181,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntile = g.tiles_m * g.tiles_n;
-    const int tile = blockIdx.x % ntile;
-    const long long b = blockIdx.x / ntile;
+    const int tile = (int)(bid % ntile);
+    const long long b = bid / ntile;
     const int m0 = (tile % g.tiles_m) * TC_BM;
     const int n0 = (tile / g.tiles_m) * TC_BN;
 
@@ -229,8 +231,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
                     break;
                 }
                 if (s != g.skip_stage) {                   // a skipped stage is never completed
-                    const CUtensorMap* mA = (term == 2) ? &mapA_small : &mapA_big;
-                    const CUtensorMap* mB = (term == 1) ? &mapB_small : &mapB_big;
+                    const CUtensorMap* mA = (term == 2) ? mapA_small : mapA_big;
+                    const CUtensorMap* mB = (term == 1) ? mapB_small : mapB_big;
                     const uint32_t full = full0 + 8 * st;
                     mbar_expect_tx(full, TC_STAGE_BYTES);
                     tma_load_2d(sA0 + st * TC_A_BYTES, mA, kx, ra, full);
@@ -378,6 +380,33 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_consta
     }
 }
 
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_big, const __grid_constant__ CUtensorMap mapA_small,
+               const __grid_constant__ CUtensorMap mapB_big, const __grid_constant__ CUtensorMap mapB_small,
+               const TcArgs g)
+{
+    tc_gemm_body(&mapA_big, &mapA_small, &mapB_big, &mapB_small, g, blockIdx.x);
+}
+
+// Grouped form (batched form, serving rounds): one launch covers the same plan step of
+// many independent problems.  CTA w works on member m with prefix[m] <= w < prefix[m+1],
+// tile w - prefix[m] of that member's GEMM, with its arguments args[m] and its four
+// tensor maps maps[4 m .. 4 m + 3] (A big, A small, B big, B small) from global memory.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc_gemm_grouped_kernel(const CUtensorMap* __restrict__ maps, const TcArgs* __restrict__ args,
+                       const long long* __restrict__ prefix, int nmem)
+{
+    const long long w = blockIdx.x;
+    int lo = 0, hi = nmem - 1;
+    while (lo < hi) {                       // last member whose prefix <= w
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    const TcArgs g = args[lo];
+    const CUtensorMap* m = maps + 4 * lo;
+    tc_gemm_body(m, m + 1, m + 2, m + 3, g, w - prefix[lo]);
+}
+
 }  // namespace ccsdk
 
 namespace ccsdk {
@@ -395,15 +424,17 @@ struct EmbedArgs {
     const long long* srcoff; const int* srow; const int* scol;
     float* big; float* small;
     int nblk, R, Kc, Kpad, mode;
+    // One block per operand row (b, r) of the (virtual) grid of nvb blocks: its threads
+    // sweep the row's column pairs, so the per-element index arithmetic is one 32-bit add.
+    __device__ void run(long long vb, long long nvb) const;
 };
 
-// One CTA per operand row (b, r): its threads sweep the row's column pairs, so
-// the per-element index arithmetic is one 32-bit add.
-__global__ void embed_kernel(const EmbedArgs e)
+__device__ inline void EmbedArgs::run(long long vb, long long nvb) const
 {
+    const EmbedArgs& e = *this;
     const int kh = e.Kpad / 2;                       // column pairs, padding included
     const long long rows = (long long)e.nblk * e.R;
-    for (long long br = blockIdx.x; br < rows; br += gridDim.x) {
+    for (long long br = vb; br < rows; br += nvb) {
         const int r = (int)(br % e.R);
         const long long b = br / e.R;
         const long long base = e.srcoff[b] + (long long)e.srow[r];
@@ -439,19 +470,23 @@ __global__ void embed_kernel(const EmbedArgs e)
     }
 }
 
+__global__ void embed_kernel(const EmbedArgs e) { e.run(blockIdx.x, gridDim.x); }
+
 }  // namespace ccsdk
 
 namespace ccsdk {
 
 // dst = (complex64) src, n elements
-__global__ void to_c64_kernel(float2* __restrict__ dst, const double2* __restrict__ src, long long n)
-{
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
-        const double2 z = src[e];
-        dst[e] = make_float2((float)z.x, (float)z.y);
+struct ToC64Op {
+    float2* dst; const double2* src; long long n;
+    __device__ void run(long long vb, long long nvb) const {
+        for (long long e = vb * blockDim.x + threadIdx.x; e < n; e += nvb * blockDim.x) {
+            const double2 z = src[e];
+            dst[e] = make_float2((float)z.x, (float)z.y);
+        }
     }
-}
+};
+__global__ void to_c64_kernel(const ToC64Op op) { op.run(blockIdx.x, gridDim.x); }
 
 }  // namespace ccsdk
 
@@ -471,6 +506,7 @@ struct WprimeListArgs {
     const int* blk; const int* abl; const int* efl;
     const int* grp;           // [ngrp][2]: first index into abl and count (<= WP_GROUP) of rows sharing a
     int nblk, nab, nef, N, o, v, Kpad, ngrp;
+    __device__ void run(long long vb, long long nvb) const;
 };
 
 constexpr int WP_GROUP = 4;   // rows (pairs a b with one a) that share the ovvv row of a
@@ -478,13 +514,14 @@ constexpr int WP_GROUP = 4;   // rows (pairs a b with one a) that share the ovvv
 // One CTA per group of up to WP_GROUP output row pairs of one block bi whose pairs (a, b)
 // share a: the ovvv row of a and t_r^a are loaded once for the group, and its threads
 // sweep the (e, f) list.
-__global__ void wprime_list_kernel(const WprimeListArgs w)
+__device__ inline void WprimeListArgs::run(long long vb, long long nvb) const
 {
+    const WprimeListArgs& w = *this;
     const int N = w.N, o = w.o, v = w.v;
     const long long vv = (long long)v * v, v4 = vv * vv, ov3 = (long long)o * v * vv;
     const int kh = w.Kpad / 2;                       // column pairs, padding included
     const long long units = (long long)w.nblk * w.ngrp;
-    for (long long unit = blockIdx.x; unit < units; unit += gridDim.x) {
+    for (long long unit = vb; unit < units; unit += nvb) {
         const long long bi = unit / w.ngrp;
         const int gi = (int)(unit - bi * w.ngrp);
         const int a0i = w.grp[2 * gi], cnt = w.grp[2 * gi + 1];
@@ -547,5 +584,7 @@ __global__ void wprime_list_kernel(const WprimeListArgs w)
         }
     }
 }
+
+__global__ void wprime_list_kernel(const WprimeListArgs w) { w.run(blockIdx.x, gridDim.x); }
 
 }  // namespace ccsdk

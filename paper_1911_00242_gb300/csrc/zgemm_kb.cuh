@@ -250,29 +250,31 @@ zgemm_grouped_kernel(const GemmArgs* __restrict__ gs, const long long* __restric
 }
 
 // Deterministic split-K reduction: C_b (+)= alpha * sum_s work[s][b] in split order.
-__global__ void zgemm_split_reduce(const GemmArgs g)
-{
-    const long long total = (long long)g.nbatch * g.M * g.N;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long b = e / ((long long)g.M * g.N);
-        const int mn = (int)(e % ((long long)g.M * g.N));
-        const int m = mn / g.N, n = mn % g.N;
-        double re = 0.0, im = 0.0;
-        for (int s = 0; s < g.nsplit; ++s) {
-            const double2 w = g.work[((long long)s * g.nbatch + b) * (long long)g.M * g.N + mn];
-            re += w.x; im += w.y;
-        }
-        double2* p = g.C + g.offC[b] + (long long)g.rowC[m] + g.colC[n];
-        const double r2 = g.alpha_re * re - g.alpha_im * im;
-        const double i2 = g.alpha_re * im + g.alpha_im * re;
-        if (g.accumulate) { double2 o = *p; o.x += r2; o.y += i2; *p = o; }
-        else *p = make_double2(r2, i2);
-        if (g.offC2) {
-            double2* q = g.C + g.offC2[b] + (long long)g.rowC[m] + g.colC2[n];
-            double2 o = *q; o.x -= r2; o.y -= i2; *q = o;
+struct SplitReduceOp {
+    GemmArgs g;
+    __device__ void run(long long vb, long long nvb) const {
+        const long long total = (long long)g.nbatch * g.M * g.N;
+        for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
+            const long long b = e / ((long long)g.M * g.N);
+            const int mn = (int)(e % ((long long)g.M * g.N));
+            const int m = mn / g.N, n = mn % g.N;
+            double re = 0.0, im = 0.0;
+            for (int s = 0; s < g.nsplit; ++s) {
+                const double2 w = g.work[((long long)s * g.nbatch + b) * (long long)g.M * g.N + mn];
+                re += w.x; im += w.y;
+            }
+            double2* p = g.C + g.offC[b] + (long long)g.rowC[m] + g.colC[n];
+            const double r2 = g.alpha_re * re - g.alpha_im * im;
+            const double i2 = g.alpha_re * im + g.alpha_im * re;
+            if (g.accumulate) { double2 o = *p; o.x += r2; o.y += i2; *p = o; }
+            else *p = make_double2(r2, i2);
+            if (g.offC2) {
+                double2* q = g.C + g.offC2[b] + (long long)g.rowC[m] + g.colC2[n];
+                double2 o = *q; o.x -= r2; o.y -= i2; *q = o;
+            }
         }
     }
-}
+};
+__global__ void zgemm_split_reduce(const GemmArgs g) { SplitReduceOp{g}.run(blockIdx.x, gridDim.x); }
 
 }  // namespace ccsdk
