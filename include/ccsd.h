@@ -262,18 +262,23 @@ int ccsd_batch_destroy(ccsd_batch_t b);
 /* ---------------------------------------------------------------- serving form
  * A request loop on its own host thread.  Submitted solves wait in FIFO order
  * until their device-memory footprint fits in hbm_budget_bytes and one of
- * max_slots slots is free; each admitted solve gets a stream and a handle whose
- * integrals and amplitudes stay resident until it finishes.  All admitted
- * solves advance together: each round enqueues one iteration of every solve
- * (their kernels run concurrently) and then completes them.  Converged solves
- * retire and free their memory for the queue.  A solve runs like ccsd_solve
- * (mixed iterations, then polish_iters iterations in polish_precision, for
- * CCSD_MIXED).
- * The inputs a request points to must stay valid until it is done (host
- * inputs are copied when the request is admitted). */
+ * max_slots slots is free; each admitted solve gets a handle whose integrals and
+ * amplitudes stay resident until it finishes.  All admitted solves advance
+ * together, one iteration each per round: solves with the same plan signature,
+ * arithmetic and contraction tile shapes form a group, and every step of their
+ * residual is one grouped launch (the groups run concurrently); all max|R| come
+ * back in one copy, then each solve takes its convergence test and update.  A
+ * solve's iterates are bitwise those it has alone.  Converged solves retire and
+ * free their memory for the queue.  A solve runs like ccsd_solve (mixed
+ * iterations, then polish_iters iterations in polish_precision, for CCSD_MIXED).
+ * The inputs a request points to must stay valid until it is done (host inputs
+ * are copied when the request is admitted). */
 typedef struct ccsd_server* ccsd_server_t;
-/* Starts the loop on the current device: hbm_budget_bytes > 0, 1 <= max_slots <= 1024. */
-int ccsd_server_create(size_t hbm_budget_bytes, int max_slots, ccsd_server_t* out);
+/* Starts the loop on the current device: hbm_budget_bytes > 0, 1 <= max_slots <= 1024.
+ * `stream` (a cudaStream_t) carries every device operation of the server, and the
+ * server's group streams fork from and join into it; NULL: the server creates a
+ * non-blocking stream of its own.  A given stream must outlive the server. */
+int ccsd_server_create(size_t hbm_budget_bytes, int max_slots, void* stream, ccsd_server_t* out);
 /* Queues one solve (config and input pointers are copied into the request; the
  * data they point to is not) and returns its id.  CCSD_ERR_INVALID for a bad
  * config or after ccsd_server_destroy began. */

@@ -82,7 +82,8 @@ SYMBOLS = {
     "ccsd_batch_stats": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
                           ctypes.c_int], ctypes.c_int),
     "ccsd_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
-    "ccsd_server_create": ([ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "ccsd_server_create": ([ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
+                           ctypes.c_int),
     "ccsd_submit": ([ctypes.c_void_p, ctypes.POINTER(ccsd_config), ctypes.POINTER(ccsd_inputs),
                      ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "ccsd_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
@@ -379,10 +380,11 @@ class BatchSolver:
 class Server:
     """The serving loop: submit solves, poll for results (see ccsd_server_* in include/ccsd.h)."""
 
-    def __init__(self, hbm_budget_bytes, max_slots):
+    def __init__(self, hbm_budget_bytes, max_slots, stream=None):
         self.lib = load()
         h = ctypes.c_void_p()
-        check(self.lib.ccsd_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)), "ccsd_server_create")
+        check(self.lib.ccsd_server_create(int(hbm_budget_bytes), int(max_slots), stream, ctypes.byref(h)),
+              "ccsd_server_create")
         self.h = h
         self._keep = {}
 

@@ -101,3 +101,30 @@ def test_admission_by_footprint(lib):
     st = wait_all(srv, [i])[i][0]
     srv.close()
     assert st == -2
+
+
+def test_served_energies_match_oracle(lib):
+    """Served solves against the oracle (paper Sec. 4.4 iteration, DIIS(6)): two FP64
+    solves and one mixed solve with its FP64 polish, converged to max|R| < 1e-7 (the
+    serving tolerance) in one mix on a caller-given stream; each energy per cell is
+    within 1e-7 Ha of the oracle's energy converged to 1e-10."""
+    from oracle import ccsd_k, driver
+    from paper_1911_00242_gb300.binding import CCSD_MIXED, Server
+    reqs = [(SPECS[0], 0), (SPECS[2], 0), (SPECS[3], CCSD_MIXED)]
+    inps = [cs.generate(s) for s, _ in reqs]
+    stream = torch.cuda.Stream()
+    srv = Server(64 << 30, 8, stream=stream.cuda_stream)
+    ids = [srv.submit(s.grid, s.nocc, s.nvir, inp, conv_tol=1e-7, diis_depth=6, max_iter=100, precision=p,
+                      mixed_tol=1e-7, polish_iters=2)
+           for (s, p), inp in zip(reqs, inps)]
+    res = wait_all(srv, ids)
+    srv.close()
+    for (s, p), inp, i in zip(reqs, inps, ids):
+        st, e, t, it = res[i]
+        assert st == 2, (s, st)
+        P = ccsd_k.Problem(s.grid, s.nocc, s.nvir, inp)
+        ref = driver.solve(P, tol=1e-10, max_iter=200, diis_depth=6)
+        assert ref["converged"]
+        de = abs(e - ref["energies"][-1].real / s.nk)
+        print(f"served {s.grid} o{s.nocc} v{s.nvir} precision {p}: |dE| vs oracle {de:.1e}")
+        assert de < 1e-7, (s, p, e, de)
