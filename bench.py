@@ -395,11 +395,14 @@ def run_batch(args, local):
     for _ in range(max(0, args.warmup - 1)):
         B.iterate(1)
     torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         B.iterate(1)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    clk = clocks.stop()
     launches, cfgs = B.stats()
     fl = sum(flops_per_iteration(s) for s in specs)
     B.close()
@@ -410,6 +413,8 @@ def run_batch(args, local):
             "config": {"workload": "batch64", "members": 64, "precision": args.precision,
                        "nk": [s.nk for s in specs], "nocc": [s.nocc for s in specs], "nvir": [s.nvir for s in specs]},
             "aggregate_tflops": fl * args.steps / dt / 1e12, "gpu_launches_per_step": launches,
+            "gpu_launches": launches * args.steps, "clocks": clk,
+            "timing": "host clock around the graph replays (each iteration ends with a copy of the member norms)",
             "autotune_and_capture_s": t_setup, "tile_cfgs": cfgs[:40]}
 
 
@@ -427,6 +432,8 @@ def run_serve(args, local):
     picks = [(big if rng.random() < 0.1 else pool[int(rng.integers(0, len(pool)))]) for _ in arrivals]
     cfg = dict(conv_tol=1e-7, diis_depth=6, max_iter=200, precision=CCSD_MIXED, mixed_tol=1e-7, polish_iters=0)
     srv = Server(200 << 30, 32)
+    clocks = ClockSampler(local)
+    clocks.start()
     ids, t_start = [], time.perf_counter()
     peak_bytes = peak_active = 0
     for t_arr, (s, arr) in zip(arrivals, picks):
@@ -446,6 +453,7 @@ def run_serve(args, local):
         peak_bytes, peak_active = max(peak_bytes, b), max(peak_active, a)
         time.sleep(0.005)
     elapsed = time.perf_counter() - t_start
+    clk = clocks.stop()
     srv.close()
     ok = [v for v in done.values() if v[0] == 2]
     ts = np.array([v[1] for v in ok])
@@ -463,7 +471,7 @@ def run_serve(args, local):
             "p50_large_s": q(tl, 50), "p99_large_s": q(tl, 99),
             "solves_per_s": len(ok) / elapsed, "submitted": len(ids), "completed": len(ok),
             "failed": len(ids) - len(ok), "elapsed_s": elapsed, "peak_admitted_gb": peak_bytes / 2**30,
-            "peak_active": peak_active}
+            "peak_active": peak_active, "clocks": clk}
 
 
 def run_grid333(args, local):
@@ -702,6 +710,99 @@ def run_grid333_ozaki(args, local):
     }
 
 
+def grid333_block(args, local):
+    """The mixed-precision workload inside the default line: 3x3x3 grid (N_k = 27), o 8,
+    v 24, integrals stored complex64 (vvvv 52 GB), DIIS(6).  One handle carries the
+    mixed form and its Ozaki polish.  Timed: `args.steps` mixed iterations (CUDA events,
+    clocks sampled) after `args.warmup`; then the rest of the solve (mixed iterations to
+    max|R| < 1e-7, Ozaki polish iterations to 1e-8); then the same handle switched to
+    native FP64 runs one timed iteration from the polished amplitudes, whose max|R| and
+    energy change give the distance to the FP64 fixed point."""
+    import torch
+    from paper_1911_00242_gb300.binding import CCSD_FP64, CCSD_MIXED, CCSD_OZAKI, Solver
+    spec = cs.spec_for("grid333_o8_v24_c64")
+    device = f"cuda:{local}"
+    t0 = time.perf_counter()
+    dev = cs.generate_torch(spec, device)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    torch.cuda.empty_cache()
+    depth = WORKLOADS["grid333_o8_v24_c64"]["diis_depth"]
+    t_create0 = time.perf_counter()
+    S = Solver(spec.grid, spec.nocc, spec.nvir, dev, precision=CCSD_MIXED, diis_depth=depth, max_iter=300,
+               conv_tol=1e-8, mixed_tol=1e-7, polish_iters=6, polish_precision=CCSD_OZAKI)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t_create0
+    free_b, total_b = torch.cuda.mem_get_info()
+    stream = torch.cuda.current_stream()
+    t_solve0 = time.perf_counter()
+    for _ in range(args.warmup):
+        S.iterate(1)
+    torch.cuda.synchronize()
+    S.trace(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        S.iterate(1)
+        launches += S.launches()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    steps = S.trace_steps()
+    S.trace(False)
+    ok, its, mr = S.solve()                  # mixed iterations to 1e-7, then the Ozaki polish
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t_solve0
+    iters = args.warmup + args.steps + its
+    e_mixed = S.energy()
+    S.set_precision(CCSD_FP64)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    d64, mr64 = S.iterate(1)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = f0.elapsed_time(f1)
+    e_fp64 = S.energy()
+    S.close()
+    del S, dev
+    torch.cuda.empty_cache()
+    tc = [x for x in steps if x[3] > 0 and x[1] > 0 and x[3] / (x[2] / x[1] / 1e3) > 20e12]
+    dom = max(tc, key=lambda x: x[2])
+    name, calls, tot_ms, fl, by = dom
+    avg_s = tot_ms / calls / 1e3
+    bf16 = measured_peaks().get("bf16_tflops")
+    peak = (bf16 or 1900.0) * TF32_NOMINAL_RATIO
+    achieved = fl / avg_s / 1e12
+    return {
+        "workload": "grid333_o8_v24_c64", "nk_grid": list(spec.grid), "nocc": spec.nocc, "nvir": spec.nvir,
+        "int_dtype": "c64", "diis": depth, "input_synthesis_s": t_gen, "create_s": t_create,
+        "device_gb_in_use": (total_b - free_b) / 1e9,
+        "value": 1e3 / ms, "unit": "iter/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+        "gpu_launches": launches, "clocks": clk,
+        "precision": "tcgen05 split-TF32 contractions, FP32 CUDA cores elsewhere, FP64 update/DIIS/energy",
+        "contraction_tflops": flops_per_iteration(spec) / (ms / 1e3) / 1e12,
+        "roofline": {"kernel": f"tc_gemm_kernel ({name})", "bound": "tensor", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "executed_frac": 3.0 * achieved / peak,
+                     "peak_source": ("measured bf16 %.0f TFLOP/s x nominal TF32/BF16 ratio" % bf16) if bf16
+                     else "fallback 1.9 PFLOP/s bf16 x nominal TF32/BF16 ratio",
+                     "flops_per_launch": fl, "launch_ms": avg_s * 1e3},
+        "solve": {"converged": ok, "iterations_incl_polish": iters, "polish": "Ozaki (FP64-accurate)",
+                  "max_resid": mr, "seconds": t_solve, "e_per_cell": e_mixed.real},
+        "fp64": {"ms_per_iter": fp64_ms, "speedup_per_iter_mixed_vs_fp64": fp64_ms / ms,
+                 "max_resid_at_mixed_solution": mr64, "e_per_cell_after_fp64_iteration": e_fp64.real,
+                 "abs_dE_mixed_vs_fp64_iteration": abs(e_mixed.real - e_fp64.real),
+                 "solve_seconds_estimate": iters * fp64_ms / 1e3,
+                 "solve_estimate_basis": "the mixed solve's iteration count at the measured FP64 time per iteration",
+                 "speedup_solve_estimate": iters * fp64_ms / 1e3 / t_solve},
+    }
+
+
 def grid333_cpu_baseline(spec):
     """The block oracle on a bounded sample: the F~ intermediates (all k) and one R2
     block, scaled to a full iteration (N_k^3 blocks) -- the full oracle does not fit
@@ -736,6 +837,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-form comparison")
     ap.add_argument("--no-ozaki", action="store_true", help="skip the Ozaki-form comparison")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-solution comparison")
+    ap.add_argument("--no-grid333", action="store_true", help="skip the 3x3x3 mixed-precision block")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "ozaki"],
                     help="batch64: member precision (fp64, mixed); grid333_o8_v24_c64: ozaki runs that form")
     ap.add_argument("--rate", type=float, default=5.0, help="serve: requests per second")
@@ -879,13 +981,13 @@ def main():
     if not args.no_ozaki:
         result["ozaki"] = run_ozaki(args, spec, dev, depth, result.get("fp64_solve"), ms / args.steps)
 
+    S.close()
     if not args.no_e2e:
         # end to end through the C ABI from pinned host buffers: create (copies
         # the integrals host->device), K iterations, energy, amplitudes back.
         host = {k: torch.from_numpy(v).pin_memory() for k, v in inp.items()}
         h1 = torch.empty(zeros1.shape, dtype=torch.complex128).pin_memory()
         h2 = torch.empty(zeros2.shape, dtype=torch.complex128).pin_memory()
-        del S
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -901,6 +1003,18 @@ def main():
         d2h = h1.numel() * 16 + h2.numel() * 16
         result["e2e"] = {"value": world * args.steps / dt, "unit": "iter/s",
                          "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+
+    if not args.no_grid333 and world == 1:
+        # the mixed-precision workload (3x3x3, complex64 integrals) needs about 280 GB: the
+        # FP64 workload's inputs are released first
+        del dev, inp, zeros1, zeros2
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        free_b, total_b = torch.cuda.mem_get_info()
+        if total_b >= 250e9:
+            result["grid333_mixed"] = grid333_block(args, local)
+        else:
+            result["grid333_mixed"] = {"skipped": "needs a GPU with about 280 GB of device memory"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         secs, desc = cpu_oracle_iteration(args.workload)
