@@ -166,6 +166,11 @@ struct ccsd_ctx {
     int oz_slices = 7;               // slices per operand row (CCSD_OZAKI)
     long long oz_work_elems = 0;     // split partials of the Ozaki GEMMs (complex elements)
     df2* ovvv_df = nullptr;          // Ozaki form, complex128 ovvv: its double-float copy
+    df2* ooov_df = nullptr;          // the same for complex128 ooov (fused Fock terms)
+    df2* t2_df = nullptr;            // Ozaki iterations: double-float copies for the fused Fock
+    df2* t1_df = nullptr;            // terms (t2_df aliases the idle B operand pool in the
+    df2* fvvpT_df = nullptr;         // pooled layout)
+    df2* foop_df = nullptr;
     double2* oz_work = nullptr;
     long long wab_cap_bytes = 12LL << 30;   // bound of the ladder's W' slab buffer
     // mixed and Ozaki forms: tensor-core operands (TF32 big/small parts, or BF16 slice
@@ -258,10 +263,12 @@ struct GemmSpec {
     double ar = 1.0, ai = 0.0;
 };
 
-// Tile configurations: (BM, BN, BK, TM, TN), 256 threads each.
-enum { CFG_64x64 = 0, CFG_64x32 = 1, CFG_128x16 = 2, CFG_16x16 = 3, CFG_32x16 = 4 };
-const int CFG_BM[5] = {64, 64, 128, 16, 32};
-const int CFG_BN[5] = {64, 32, 16, 16, 16};
+// Tile configurations: (BM, BN, BK, TM, TN[, KS]), 256 threads each.  The two K-split
+// shapes (KS thread groups share each K step) serve skinny contractions with K >= 32.
+enum { CFG_64x64 = 0, CFG_64x32 = 1, CFG_128x16 = 2, CFG_16x16 = 3, CFG_32x16 = 4, CFG_16x16K = 5, CFG_32x16K = 6,
+       CFG_COUNT = 7 };
+const int CFG_BM[CFG_COUNT] = {64, 64, 128, 16, 32, 16, 32};
+const int CFG_BN[CFG_COUNT] = {64, 32, 16, 16, 16, 16, 16};
 
 const int kSMs = 152;
 
@@ -328,8 +335,8 @@ int finalize_gemm(ccsd_ctx* h, Alloc& al, GemmSpec s, size_t& work_need) {
     if (s.N >= 48) p.cfg = CFG_64x64;
     else if (s.N > 16) p.cfg = CFG_64x32;
     else if (s.M > 64) p.cfg = CFG_128x16;
-    else if (s.M > 16) p.cfg = CFG_32x16;
-    else p.cfg = CFG_16x16;
+    else if (s.M > 16) p.cfg = s.K >= 32 ? CFG_32x16K : CFG_32x16;
+    else p.cfg = s.K >= 32 ? CFG_16x16K : CFG_16x16;
     GemmArgs& g = p.args;
     g.M = s.M; g.N = s.N; g.K = s.K; g.nbatch = s.nbatch; g.nchunk = s.nchunk;
     g.conjA = s.conjA; g.conjB = s.conjB; g.accumulate = s.acc ? 1 : 0;
@@ -416,7 +423,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
     return fn;
 }
 
-// 2D fp32 tensor [rows][kpad] with a (32 x box_rows) box and 128-byte swizzle.
+// 2D fp32 tensor [rows][kpad] with a (TC_BK x box_rows) box and 64-byte swizzle.
 int encode_map(CUtensorMap* m, const float* base, long long rows, int kpad, int box_rows) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
     if (!enc) return CCSD_ERR_CUDA;
@@ -425,7 +432,7 @@ int encode_map(CUtensorMap* m, const float* base, long long rows, int kpad, int 
     cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : CCSD_ERR_CUDA;
 }
@@ -798,6 +805,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
     long long pool_ae = 0, pool_be = 0, pool_ar = 0, pool_br = 0;   // Ozaki capacity: elements, scale rows
     float* pool_asc = nullptr;
     float* pool_bsc = nullptr;    // Ozaki pools: row scales
+    long long pool_b_bytes = 0;
     const long long nlt_vv = (long long)v * (v - 1) / 2;
     if (tcp) {
         const long long N3l = (long long)N * N * N;
@@ -893,6 +901,7 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
             }
             pool_a = (float*)al.get((size_t)bytes_a);
             pool_b = (float*)al.get((size_t)bytes_b);
+            pool_b_bytes = bytes_b;
             if (al.err) return al.err;
             for (TcSet& T : sets) {
                 // elements per part / plane the pools hold for this set
@@ -1735,6 +1744,32 @@ int build_plan(ccsd_ctx* h, Alloc& al, size_t& work_need) {
         s1.mode = s2.mode = s3.mode = 3;
         h->seq.push_back(s1); h->seq.push_back(s2); h->seq.push_back(s3);
     }
+    if (h->has_oz) {
+        // Ozaki iterations: the four GEMMs above become one fused double-float pass
+        // (fock_terms_df_kernel) over double-float copies; the GEMMs stay for FP64 iterations
+        for (size_t i = fock_first; i < h->seq.size(); ++i)
+            if (h->seq[i].kind == 0) h->seq[i].mode = 1;
+        if (!h->in32[B_OOOV]) {
+            h->ooov_df = (df2*)al.get((size_t)h->bufsize[B_OOOV] * sizeof(df2));
+            if (al.err) return al.err;
+            if (!al.dry)
+                to_df2_kernel<<<ew_grid(h->bufsize[B_OOOV]), 256, 0, h->st>>>(h->ooov_df, h->buf[B_OOOV],
+                                                                             h->bufsize[B_OOOV]);
+        }
+        if (pooled && pool_b_bytes >= (long long)sizeof(df2) * h->n2) {
+            h->t2_df = (df2*)pool_b;          // idle between the last tensor-core GEMM and the next residual
+        } else {
+            h->t2_df = (df2*)al.get((size_t)h->n2 * sizeof(df2));
+        }
+        h->t1_df = (df2*)al.get((size_t)h->n1 * sizeof(df2));
+        h->fvvpT_df = (df2*)al.get((size_t)h->bufsize[B_FVVP] * sizeof(df2));
+        h->foop_df = (df2*)al.get((size_t)h->bufsize[B_FOOP] * sizeof(df2));
+        if (al.err) return al.err;
+        Step s1{14, 0, h->cur_name, 0.0, 32.0 * (double)(h->n2 + h->n1)};
+        Step s2{13, 0, h->cur_name, 8.0 * 2.0 * (o + v) * (double)h->n2, 16.0 * 4.0 * h->n2};
+        s1.mode = s2.mode = 5;
+        h->seq.push_back(s1); h->seq.push_back(s2);
+    }
     h->seq.push_back({4, 0, "antisym_R2", 0.0, 16.0 * 3.0 * h->n2});
     h->cur_oz = true;
     if (oz && (rc = oz_convert_gemms(h, al, oz_specs, pooled, pool_a, pool_b, pool_ae, pool_be, pool_asc, pool_bsc,
@@ -1775,28 +1810,38 @@ int launch_gemm(ccsd_ctx* h, GemmPlan& p) {
     g.A32 = (h->fp32 || h->in32[p.a]) ? h->shadow[p.a] : nullptr;
     g.B32 = (h->fp32 || h->in32[p.b]) ? h->shadow[p.b] : nullptr;
     dim3 grid((unsigned)p.blocks, (unsigned)g.nsplit);
+    // the K-split tile shapes pay off in FP32 only (measured on GB300: the double-float
+    // instance ran slower with them, the FP64 one no faster); the other instances take
+    // the plain shape with the same tile, so the plan's tiling and split-K stand
+    const int cfg = h->fp32 ? p.cfg : p.cfg == CFG_16x16K ? CFG_16x16 : p.cfg == CFG_32x16K ? CFG_32x16 : p.cfg;
     if (h->oz_on) {         // Ozaki form: the GEMMs left off the tensor cores run in double-float
-        switch (p.cfg) {
+        switch (cfg) {
             case CFG_64x64:  zgemm_kb_kernel<64, 64, 8, 4, 4, df><<<grid, 256, 0, h->st>>>(g); break;
             case CFG_64x32:  zgemm_kb_kernel<64, 32, 8, 4, 2, df><<<grid, 256, 0, h->st>>>(g); break;
             case CFG_128x16: zgemm_kb_kernel<128, 16, 8, 8, 1, df><<<grid, 256, 0, h->st>>>(g); break;
             case CFG_32x16:  zgemm_kb_kernel<32, 16, 8, 2, 1, df><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_32x16K: zgemm_kb_kernel<32, 16, 32, 2, 2, df, 2><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_16x16K: zgemm_kb_kernel<16, 16, 32, 2, 2, df, 4><<<grid, 256, 0, h->st>>>(g); break;
             default:         zgemm_kb_kernel<16, 16, 8, 1, 1, df><<<grid, 256, 0, h->st>>>(g); break;
         }
     } else if (h->fp32) {
-        switch (p.cfg) {
+        switch (cfg) {
             case CFG_64x64:  zgemm_kb_kernel<64, 64, 8, 4, 4, float><<<grid, 256, 0, h->st>>>(g); break;
             case CFG_64x32:  zgemm_kb_kernel<64, 32, 8, 4, 2, float><<<grid, 256, 0, h->st>>>(g); break;
             case CFG_128x16: zgemm_kb_kernel<128, 16, 8, 8, 1, float><<<grid, 256, 0, h->st>>>(g); break;
             case CFG_32x16:  zgemm_kb_kernel<32, 16, 8, 2, 1, float><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_32x16K: zgemm_kb_kernel<32, 16, 32, 2, 2, float, 2><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_16x16K: zgemm_kb_kernel<16, 16, 32, 2, 2, float, 4><<<grid, 256, 0, h->st>>>(g); break;
             default:         zgemm_kb_kernel<16, 16, 8, 1, 1, float><<<grid, 256, 0, h->st>>>(g); break;
         }
     } else {
-        switch (p.cfg) {
+        switch (cfg) {
             case CFG_64x64:  zgemm_kb_kernel<64, 64, 8, 4, 4><<<grid, 256, 0, h->st>>>(g); break;
             case CFG_64x32:  zgemm_kb_kernel<64, 32, 8, 4, 2><<<grid, 256, 0, h->st>>>(g); break;
             case CFG_128x16: zgemm_kb_kernel<128, 16, 8, 8, 1><<<grid, 256, 0, h->st>>>(g); break;
             case CFG_32x16:  zgemm_kb_kernel<32, 16, 8, 2, 1><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_32x16K: zgemm_kb_kernel<32, 16, 32, 2, 2, double, 2><<<grid, 256, 0, h->st>>>(g); break;
+            case CFG_16x16K: zgemm_kb_kernel<16, 16, 32, 2, 2, double, 4><<<grid, 256, 0, h->st>>>(g); break;
             default:         zgemm_kb_kernel<16, 16, 8, 1, 1><<<grid, 256, 0, h->st>>>(g); break;
         }
     }
@@ -2000,6 +2045,19 @@ void launch_step(ccsd_ctx* h, size_t si) {
                 ++h->launches;
                 break;
             }
+            case 13:  // Ozaki iterations: fused double-float Fock terms into ZR
+                fock_terms_df_kernel<<<ew_grid(h->n2), 256, 0, h->st>>>(FockTermsDfOp{
+                    h->buf[B_ZR], h->t2_df, h->t1_df, h->fvvpT_df, h->foop_df,
+                    h->ooov_df, h->in32[B_OOOV] ? h->shadow[B_OOOV] : nullptr,
+                    h->ovvv_df, h->in32[B_OVVV] ? h->shadow[B_OVVV] : nullptr, h->kb_of, N, o, v});
+                ++h->launches;
+                break;
+            case 14:  // their double-float copies
+                to_df_kernel<<<ew_grid(h->n2 + h->n1), 256, 0, h->st>>>(ToDfOp{
+                    h->t2_df, h->buf[B_T2], h->n2, h->t1_df, h->buf[B_T1], h->n1,
+                    h->fvvpT_df, h->buf[B_FVVP], h->foop_df, h->buf[B_FOOP], N, o, v});
+                ++h->launches;
+                break;
             case 12:  // complex64 copy of F'vv, transposed per k (fused Fock terms)
                 to_c64_transpose_kernel<<<ew_grid(h->bufsize[s.idx]), 256, 0, h->st>>>(ToC64TOp{h->shadow[s.idx], h->buf[s.idx], N, v});
                 ++h->launches;
@@ -2250,23 +2308,26 @@ int group_gemm_descriptors(Group& G, BatchGroup& bg, size_t si, int cfg, cudaStr
     return 0;
 }
 
-template <int BM, int BN, int TM, int TN>
+template <int BM, int BN, int BK, int TM, int TN, int KS = 1>
 void grouped_gemm_launch(const BatchGroup& bg, int fp32, cudaStream_t st, int n) {
     const long long ctas = std::min<long long>(bg.total, (long long)kSMs * 8);
     if (fp32)
-        zgemm_grouped_kernel<BM, BN, 8, TM, TN, float><<<(unsigned)ctas, 256, 0, st>>>(bg.d_args, bg.d_prefix, n, bg.total);
+        zgemm_grouped_kernel<BM, BN, BK, TM, TN, float, KS><<<(unsigned)ctas, 256, 0, st>>>(bg.d_args, bg.d_prefix, n, bg.total);
     else
-        zgemm_grouped_kernel<BM, BN, 8, TM, TN, double><<<(unsigned)ctas, 256, 0, st>>>(bg.d_args, bg.d_prefix, n, bg.total);
+        zgemm_grouped_kernel<BM, BN, BK, TM, TN, double, KS><<<(unsigned)ctas, 256, 0, st>>>(bg.d_args, bg.d_prefix, n, bg.total);
 }
 
 void launch_gemm_group(const BatchGroup& bg, int fp32, cudaStream_t st, int n) {
     if (bg.total <= 0 || !bg.d_args) return;
-    switch (bg.cfg) {
-        case CFG_64x64: grouped_gemm_launch<64, 64, 4, 4>(bg, fp32, st, n); break;
-        case CFG_64x32: grouped_gemm_launch<64, 32, 4, 2>(bg, fp32, st, n); break;
-        case CFG_128x16: grouped_gemm_launch<128, 16, 8, 1>(bg, fp32, st, n); break;
-        case CFG_32x16: grouped_gemm_launch<32, 16, 2, 1>(bg, fp32, st, n); break;
-        default: grouped_gemm_launch<16, 16, 1, 1>(bg, fp32, st, n); break;
+    const int cfg = fp32 ? bg.cfg : bg.cfg == CFG_16x16K ? CFG_16x16 : bg.cfg == CFG_32x16K ? CFG_32x16 : bg.cfg;
+    switch (cfg) {
+        case CFG_64x64: grouped_gemm_launch<64, 64, 8, 4, 4>(bg, fp32, st, n); break;
+        case CFG_64x32: grouped_gemm_launch<64, 32, 8, 4, 2>(bg, fp32, st, n); break;
+        case CFG_128x16: grouped_gemm_launch<128, 16, 8, 8, 1>(bg, fp32, st, n); break;
+        case CFG_32x16: grouped_gemm_launch<32, 16, 8, 2, 1>(bg, fp32, st, n); break;
+        case CFG_32x16K: grouped_gemm_launch<32, 16, 32, 2, 2, 2>(bg, fp32, st, n); break;
+        case CFG_16x16K: grouped_gemm_launch<16, 16, 32, 2, 2, 4>(bg, fp32, st, n); break;
+        default: grouped_gemm_launch<16, 16, 8, 1, 1>(bg, fp32, st, n); break;
     }
     if (bg.reduce) bg.reduce(st);
 }
@@ -2430,11 +2491,59 @@ int group_build(Group& G, int fp32, const std::vector<int>& cfgs, double* d_norm
             bu.push_back(grid_blocks(ew_grid(nn)));
         }
         GLaunch a1, a2;
-        if ((rc = make_grouped(G, mx, bm, st, a1)) || (rc = make_grouped(G, fm, bf, st, a2)) ||
-            (rc = make_grouped(G, up, bu, st, G.update)))
+        if ((rc = make_grouped(G, mx, bm, st, a1)) || (rc = make_grouped(G, fm, bf, st, a2)))
             return rc;
         G.norms.launches = a1.launches + a2.launches;
         G.norms.fn = [a1, a2](cudaStream_t s) { a1.fn(s); a2.fn(s); };
+        const int depth = h0->cfg.diis_depth;
+        for (ccsd_ctx* h : G.m)
+            if (h->cfg.diis_depth != depth) { refuse("the members of a group share one DIIS depth"); return CCSD_ERR_INVALID; }
+        if (depth == 0) {
+            if ((rc = make_grouped(G, up, bu, st, G.update))) return rc;
+        } else {
+            // device-resident DIIS: pack, inner products, Pulay solve, extrapolation
+            std::vector<DiisState> init((size_t)n);
+            long long nparts = 0;
+            for (int i = 0; i < n; ++i) {
+                ccsd_ctx* h = G.m[i];
+                DiisState& d = init[(size_t)i];
+                memset(&d, 0, sizeof d);
+                d.depth = depth;
+                for (int j = 0; j < depth; ++j) { d.hx[j] = h->hx[(size_t)j]; d.he[j] = h->he[(size_t)j]; }
+                nparts += (long long)depth * h->red_blocks;
+            }
+            DiisState* d_ds = group_upload(G, init, st, &rc);
+            if (rc) return rc;
+            double* d_part = nullptr;
+            if ((rc = group_alloc(G, sizeof(double) * nparts, (void**)&d_part))) return rc;
+            std::vector<DiisPackOp> pk;
+            std::vector<DiisDotOp> dt;
+            std::vector<DiisSolveOp> sv;
+            std::vector<DiisComboOp> cb;
+            std::vector<long long> bp, bd, bs, bc;
+            long long off = 0;
+            for (int i = 0; i < n; ++i) {
+                ccsd_ctx* h = G.m[i];
+                const int* skip = d_skip ? d_skip + i : nullptr;
+                const long long blk = (long long)h->o * h->o * h->v * h->v;
+                pk.push_back(DiisPackOp{h->amp, h->res, d_ds + i, h->d_cblk, h->nc, h->eo, h->ev, h->kb_of,
+                                        h->N, h->o, h->v, skip});
+                bp.push_back(grid_blocks(ew_grid(h->n1 + h->nc * blk)));
+                dt.push_back(DiisDotOp{d_ds + i, h->n1, blk, h->nc, h->d_cw, d_part + off, h->red_blocks, skip});
+                bd.push_back((long long)depth * h->red_blocks);
+                sv.push_back(DiisSolveOp{d_ds + i, d_part + off, h->red_blocks, skip});
+                bs.push_back(1);
+                cb.push_back(DiisComboOp{h->amp, d_ds + i, h->d_cmap, h->N, h->o, h->v, skip});
+                bc.push_back(grid_blocks(ew_grid(h->n1 + h->n2)));
+                off += (long long)depth * h->red_blocks;
+            }
+            GLaunch g1, g2, g3, g4;
+            if ((rc = make_grouped(G, pk, bp, st, g1)) || (rc = make_grouped(G, dt, bd, st, g2)) ||
+                (rc = make_grouped(G, sv, bs, st, g3)) || (rc = make_grouped(G, cb, bc, st, g4)))
+                return rc;
+            G.update.launches = g1.launches + g2.launches + g3.launches + g4.launches;
+            G.update.fn = [g1, g2, g3, g4](cudaStream_t s) { g1.fn(s); g2.fn(s); g3.fn(s); g4.fn(s); };
+        }
     }
     CK(cudaStreamSynchronize(st));
     return 0;
@@ -2513,7 +2622,7 @@ void batch_iteration_body(ccsd_batch* B) {
 // Autotuner: times every tile shape on every grouped contraction and keeps the
 // fastest.  Safe at any time: each residual re-initializes what it accumulates.
 int batch_autotune(ccsd_batch* B) {
-    const int cands[5] = {CFG_64x64, CFG_64x32, CFG_128x16, CFG_32x16, CFG_16x16};
+    const int cands[CFG_COUNT] = {CFG_64x64, CFG_64x32, CFG_128x16, CFG_32x16, CFG_16x16, CFG_32x16K, CFG_16x16K};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -3549,9 +3658,9 @@ int ccsd_batch_create(int n, const ccsd_config* cfgs, const ccsd_inputs* inputs,
     if (!out || n < 1 || n > 4096 || !cfgs || !inputs) return CCSD_ERR_INVALID;
     *out = nullptr;
     for (int i = 0; i < n; ++i)
-        if (cfgs[i].precision != cfgs[0].precision || cfgs[i].diis_depth != 0 || cfgs[i].precision == CCSD_OZAKI ||
-            cfgs[i].polish_precision != CCSD_FP64) {
-            refuse("batch members share one precision (FP64 or mixed, FP64 polish) and use diis_depth 0");
+        if (cfgs[i].precision != cfgs[0].precision || cfgs[i].diis_depth != cfgs[0].diis_depth ||
+            cfgs[i].precision == CCSD_OZAKI || cfgs[i].polish_precision != CCSD_FP64) {
+            refuse("batch members share one precision (FP64 or mixed, FP64 polish) and one DIIS depth");
             return CCSD_ERR_INVALID;
         }
     ccsd_batch* B = new (std::nothrow) ccsd_batch();

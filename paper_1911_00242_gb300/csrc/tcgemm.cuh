@@ -9,14 +9,15 @@
 // so C'[m][2n] = Re c_mn and C'[m][2n+1] = Im c_mn (8 real flops per complex
 // multiply-add, as 4M).  The split-TF32 option writes x = x_big + x_small with
 // both parts TF32-exact and sums big*big + big*small + small*big (each product
-// to about 2^-22 relative); the three terms are three passes over K.
+// to about 2^-22 relative); the three products of a K slice run on one staged copy
+// of both parts.
 //
 // Accumulation.  The tensor core's FP32 accumulation truncates, so a long sum
 // in one TMEM accumulator drifts by about half an ulp per MMA (1e-4 relative
-// at K = 4096).  Every TC_PROMOTE_STAGES stages (16 MMAs) the partial is
+// at K = 4096).  Every TC_PROMOTE_STAGES stages (18 MMAs) the partial is
 // promoted: accumulator warps add it into FP32 registers (rounding to nearest)
 // while the MMAs continue in the second TMEM accumulator.  Measured split-TF32
-// error: 4e-7 .. 9e-7 of max|C| for K = 16 .. 4096.
+// error with promotion every 16 MMAs: 4e-7 .. 9e-7 of max|C| for K = 16 .. 4096.
 //
 // Batch b and chunk c (a contracted momentum) select operand rows through
 // tables: rows [rowA[b,c] + m0, +128) of the 2D TMA view of A', rows
@@ -25,9 +26,11 @@
 // mirror offC2 / colC2 when given).
 //
 // One CTA computes one 128 x 256 tile (cta_group::1, M = 128, N = 256), 10 warps:
-//   warp 0 / lane 0 issues TMA loads into a 4-stage ring (48 KiB per stage),
-//   warp 1 / lane 0 issues 4 MMAs (K = 8 each) per stage into TMEM buffer
-//   (segment & 1), warps 2..9 promote segments and run the epilogue.
+//   warp 0 / lane 0 issues TMA loads into a 4-stage ring (48 KiB per stage: a K
+//   slice of 16 of both parts of A' and B', 64-byte swizzle),
+//   warp 1 / lane 0 issues 6 MMAs (K = 8 each: two K steps of the three products)
+//   per stage into TMEM buffer (segment & 1), warps 2..9 promote segments and run
+//   the epilogue.
 // Every mbarrier wait is bounded; on timeout the CTA records an error code,
 // stops issuing, waits (bounded) for its copies and MMAs in flight, frees its
 // TMEM and returns.
@@ -42,24 +45,27 @@ namespace ccsdk {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BN = 256;
-constexpr int TC_BK = 32;                                // fp32 elements per stage row (128 B)
+constexpr int TC_BK = 16;                                // fp32 elements per stage row (64 B, 64-byte swizzle)
 constexpr int TC_STAGES = 4;
 static_assert((TC_STAGES & (TC_STAGES - 1)) == 0, "the ring index is s & (TC_STAGES - 1)");
-static_assert(TC_BK == 4 * 8, "the MMA issuer issues four K = 8 MMAs per stage");
-constexpr int TC_A_BYTES = TC_BM * TC_BK * 4;            // 16 KiB
-constexpr int TC_B_BYTES = TC_BN * TC_BK * 4;            // 32 KiB
-constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;  // 48 KiB
+static_assert(TC_BK == 2 * 8, "the MMA issuer issues two K = 8 MMAs per term and stage");
+constexpr int TC_A_BYTES = TC_BM * TC_BK * 4;            // 8 KiB: one part (big or small) of the A tile
+constexpr int TC_B_BYTES = TC_BN * TC_BK * 4;            // 16 KiB: one part of the B tile
+// A stage holds both parts of both tiles, [A big | A small | B big | B small], so the
+// three split-TF32 products of a K slice (big big, big small, small big) share one load:
+// 6 MMAs per 48 KiB, where staging one term at a time needs 72 KiB for them.
+constexpr int TC_STAGE_BYTES = 2 * (TC_A_BYTES + TC_B_BYTES);   // 48 KiB
 constexpr int TC_SMEM_BYTES = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
 // Two TMEM accumulators of TC_BN columns: the MMAs fill one while the
 // accumulator warps drain the other.
 constexpr int TC_TMEM_COLS = 2 * TC_BN;
-// Stages (4 MMAs of K = 8 each) summed in TMEM before the partial is promoted
-// into the FP32 register accumulator.  The tensor core's FP32 accumulation
+// Stages (6 MMAs of K = 8 each with split TF32) summed in TMEM before the partial is
+// promoted into the FP32 register accumulator.  The tensor core's FP32 accumulation
 // truncates: its error grows by about half an ulp of the running sum per MMA
 // (measured with ccsd_tc_selftest: relative 2.6e-5 at K = 1024 complex, 1e-4 at
-// K = 4096 with one TMEM sum per tile).  Promoting every 16 MMAs caps that bias
-// at the partial of K = 128 reals; the register sums round to nearest.
-constexpr int TC_PROMOTE_STAGES = 4;
+// K = 4096 with one TMEM sum per tile).  Promoting every 18 MMAs caps that bias
+// at the partial of K = 48 reals per term; the register sums round to nearest.
+constexpr int TC_PROMOTE_STAGES = 3;
 constexpr int TC_ACC_WARPS = 8;                          // two per TMEM lane quarter, 128 columns each
 constexpr int TC_THREADS = 64 + 32 * TC_ACC_WARPS;       // producer warp, MMA warp, accumulator warps
 constexpr long long TC_SPIN_LIMIT = 1LL << 24;           // polls before a wait gives up (> 0.1 s)
@@ -121,6 +127,17 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 
 // Shared-memory matrix descriptor, K-major, 128-byte swizzle: 8-row atoms of
 // 1024 bytes (stride byte offset 1024), leading byte offset unused (1).
+// The same for 64-byte swizzle: 8-row atoms of 512 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);            // start address
+    d |= (uint64_t)1 << 16;                             // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;                    // stride byte offset
+    d |= (uint64_t)1 << 46;                             // descriptor version (tcgen05)
+    d |= (uint64_t)4 << 61;                             // layout: SWIZZLE_64B
+    return d;
+}
+
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFF) >> 4);            // start address
@@ -149,7 +166,7 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
 }
 
 // One 128 x 256 output tile of one batch: C[rows m][cols n] += alpha * sum over the
-// batch's chunks, terms and K stages of A'(rows) . B'(rows)^T.
+// batch's chunks, K stages and split terms of A'(rows) . B'(rows)^T.
 //   warp 0, lane 0: TMA producer into a TC_STAGES ring (full/empty mbarriers)
 //   warp 1, lane 0: MMA issuer; segment g of TC_PROMOTE_STAGES stages accumulates
 //                   in TMEM buffer g & 1, then commits to acc_full[g & 1]
@@ -168,8 +185,6 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* mapA_big, const 
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte alignment for the swizzled stages
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* stA = smem;                                        // [STAGES][16 KiB]
-    uint8_t* stB = smem + TC_STAGES * TC_A_BYTES;               // [STAGES][32 KiB]
     uint64_t* bars = (uint64_t*)(smem + TC_STAGES * TC_STAGE_BYTES);
     // bars[0..S): full, bars[S..2S): empty, bars[2S + 0/1]: acc_full, bars[2S + 2/3]: acc_empty,
     // bars[2S + 4]: drain (abort path only)
@@ -209,18 +224,20 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* mapA_big, const 
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    const int per_chunk = g.nterms * g.kstages;
-    const int total = (g.nchunk_b ? g.nchunk_b[b] : g.nchunk) * per_chunk;
+    // one stage = one K slice of both parts of A and B; all terms of the slice run on it
+    const bool split3 = g.nterms == 3;
+    const int total = (g.nchunk_b ? g.nchunk_b[b] : g.nchunk) * g.kstages;
     const int nseg = (total + TC_PROMOTE_STAGES - 1) / TC_PROMOTE_STAGES;
     int issued = 0;
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- producer: TMA loads.  Chunk, term and K offset advance
-            // incrementally (no divisions): this single thread's issue rate bounds the pipeline.
-            const uint32_t sA0 = smem_u32(stA), sB0 = smem_u32(stB);
+            // ---------------- producer: TMA loads.  Chunk and K offset advance incrementally
+            // (no divisions): this single thread's issue rate bounds the pipeline.
+            const uint32_t s0 = smem_u32(smem);
             const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[TC_STAGES]);
-            int c = 0, term = 0, kx = 0;
+            const uint32_t stage_tx = split3 ? TC_STAGE_BYTES : TC_A_BYTES + TC_B_BYTES;
+            int c = 0, kx = 0;
             int ra = g.rowA[b * g.nchunk] + m0, rb = g.rowB[b * g.nchunk] + n0;
             for (int s = 0; s < total; ++s) {
                 const int st = s & (TC_STAGES - 1);
@@ -231,33 +248,33 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* mapA_big, const 
                     break;
                 }
                 if (s != g.skip_stage) {                   // a skipped stage is never completed
-                    const CUtensorMap* mA = (term == 2) ? mapA_small : mapA_big;
-                    const CUtensorMap* mB = (term == 1) ? mapB_small : mapB_big;
+                    const uint32_t base = s0 + st * TC_STAGE_BYTES;
                     const uint32_t full = full0 + 8 * st;
-                    mbar_expect_tx(full, TC_STAGE_BYTES);
-                    tma_load_2d(sA0 + st * TC_A_BYTES, mA, kx, ra, full);
-                    tma_load_2d(sB0 + st * TC_B_BYTES, mB, kx, rb, full);
+                    mbar_expect_tx(full, stage_tx);
+                    tma_load_2d(base, mapA_big, kx, ra, full);
+                    tma_load_2d(base + 2 * TC_A_BYTES, mapB_big, kx, rb, full);
+                    if (split3) {
+                        tma_load_2d(base + TC_A_BYTES, mapA_small, kx, ra, full);
+                        tma_load_2d(base + 2 * TC_A_BYTES + TC_B_BYTES, mapB_small, kx, rb, full);
+                    }
                     issued = s + 1;
                 }
                 kx += TC_BK;
                 if (kx == g.kstages * TC_BK) {
                     kx = 0;
-                    if (++term == g.nterms) {
-                        term = 0;
-                        if (++c < g.nchunk) {
-                            ra = g.rowA[b * g.nchunk + c] + m0;
-                            rb = g.rowB[b * g.nchunk + c] + n0;
-                        }
+                    if (++c < g.nchunk) {
+                        ra = g.rowA[b * g.nchunk + c] + m0;
+                        rb = g.rowB[b * g.nchunk + c] + n0;
                     }
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---------------- MMA issuer.  Stage descriptors: the stage-0 ones plus the
-            // stage offset (their start-address field is the shared address / 16, below 2^14).
+            // ---------------- MMA issuer.  Stage descriptors: the stage-0 one plus the stage
+            // and part offsets (the start-address field is the shared address / 16, below 2^14).
             const uint32_t idesc = tc_idesc_tf32();
-            const uint64_t da0 = smem_desc_sw128(smem_u32(stA)), db0 = smem_desc_sw128(smem_u32(stB));
+            const uint64_t d0 = smem_desc_sw64(smem_u32(smem));
             const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[TC_STAGES]);
             for (int s = 0; s < total; ++s) {
                 const int seg = s / TC_PROMOTE_STAGES;
@@ -280,13 +297,20 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* mapA_big, const 
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t da = da0 + (uint64_t)(st * (TC_A_BYTES >> 4));
-                const uint64_t db = db0 + (uint64_t)(st * (TC_B_BYTES >> 4));
+                const uint64_t dab = d0 + (uint64_t)(st * (TC_STAGE_BYTES >> 4));   // A big
+                const uint64_t das = dab + (uint64_t)(TC_A_BYTES >> 4);              // A small
+                const uint64_t dbb = dab + (uint64_t)((2 * TC_A_BYTES) >> 4);        // B big
+                const uint64_t dbs = dbb + (uint64_t)(TC_B_BYTES >> 4);              // B small
                 const uint32_t dst = tmem + (uint32_t)(buf * TC_BN);
-                tc_mma(dst, da, db, idesc, seg_first ? 0u : 1u);    // K = 8 tf32 (32 bytes) each
-                tc_mma(dst, da + 2, db + 2, idesc, 1u);
-                tc_mma(dst, da + 4, db + 4, idesc, 1u);
-                tc_mma(dst, da + 6, db + 6, idesc, 1u);
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {                                     // K = 8 tf32 (32 bytes) each
+                    const uint64_t o = (uint64_t)(2 * kk);
+                    tc_mma(dst, dab + o, dbb + o, idesc, (seg_first && kk == 0) ? 0u : 1u);
+                    if (split3) {
+                        tc_mma(dst, dab + o, dbs + o, idesc, 1u);
+                        tc_mma(dst, das + o, dbb + o, idesc, 1u);
+                    }
+                }
                 tc_commit(empty0 + 8 * st);                      // stage free once these MMAs have read it
                 if ((s % TC_PROMOTE_STAGES) == TC_PROMOTE_STAGES - 1 || s == total - 1)
                     tc_commit(smem_u32(&acc_full[buf]));        // segment complete
