@@ -141,10 +141,11 @@ int ccsd_plan_check(const ccsd_config* cfg, long long* n_launches, size_t* table
  * each of its *n_steps steps (at most max_steps are written; arrays may be NULL)
  * the step kind (0 FP64/FP32 GEMM, 1 copy, 2 permutation, 3 tau, 4 antisymmetrize,
  * 5 tensor-core operand embedding, 6 tensor-core GEMM, 7 zero, 9 complex64 copy,
- * 10 W' formation, 11 fused Fock terms, 12 transposed F'vv), the iterations it
+ * 10 W' formation, 11 fused Fock terms, 12 transposed F'vv, 13 fused double-float
+ * Fock terms, 14 their double-float copies), the iterations it
  * runs in (mode 0 all; 1 without tensor cores; 2 split-TF32 tensor-core steps of
  * mixed iterations; 3 mixed iterations only; 4 all but mixed iterations; 5 Ozaki
- * tensor-core steps of Ozaki iterations), its algorithmic real flops and its
+ * iterations only), its algorithmic real flops and its
  * name (static strings owned by the library). */
 int ccsd_plan_describe(const ccsd_config* cfg, int max_steps, int* kinds, int* modes, double* flops,
                        const char** names, int* n_steps);
@@ -237,15 +238,19 @@ int ccsd_trace_step(ccsd_t h, int i, const char** name, long long* calls, double
 int ccsd_destroy(ccsd_t h);
 
 /* ---------------------------------------------------------------- batched form
- * n independent problems (any mix of grids and orbital counts, one precision,
- * CCSD_FP64 or CCSD_MIXED, plain successive substitution: diis_depth must be 0)
- * iterate together on a
- * stream the batch owns.  Every contraction step of all members is one grouped
- * persistent kernel launch whose tile shape an autotuner picks on the first
- * iteration (one timing pass per candidate shape); an iteration -- residuals,
- * per-member max|R|, update of the members not yet converged -- is replayed as
- * one CUDA graph.  Members stop updating once their max|R| < conv_tol.
- * The problem data follow the rules of ccsd_create (device inputs borrowed). */
+ * n independent problems (any mix of grids and orbital counts; one precision,
+ * CCSD_FP64 or CCSD_MIXED, and one diis_depth) iterate together on a stream the
+ * batch owns.  Members whose plans have the same step sequence form a group; every
+ * step of a group's iteration is one grouped launch over its members (contractions
+ * in a persistent grouped kernel whose tile shape an autotuner picks on the first
+ * iteration; tensor-core contractions, elementwise steps, norms and updates in one
+ * launch each), and the groups run concurrently.  An iteration -- residuals,
+ * per-member max|R|, update of the members not yet converged, DIIS extrapolation
+ * with its history, Gram matrix and Pulay solve kept in device memory -- is
+ * replayed as one CUDA graph.  Members stop updating once their max|R| < conv_tol.
+ * The problem data follow the rules of ccsd_create (device inputs borrowed).  The
+ * batch's DIIS history is its own: ccsd_iterate on a member handle afterwards
+ * starts a fresh history. */
 typedef struct ccsd_batch* ccsd_batch_t;
 int ccsd_batch_create(int n, const ccsd_config* cfgs, const ccsd_inputs* inputs, ccsd_batch_t* out);
 /* Up to n_iter iterations; done[i] / max_resid[i] per member (arrays of n, may be NULL). */

@@ -8,6 +8,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
+#include "diis.h"
+
 namespace ccsdk {
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -377,6 +380,100 @@ struct FockTermsOp {
 __global__ void fock_terms_kernel(const FockTermsOp op) { op.run(blockIdx.x, gridDim.x); }
 
 // ---------------------------------------------------------------------------
+// Ozaki form: the same fused P(ab)-only / P(ij)-only terms in double-float arithmetic
+// (about 48 bits, on the FP32 pipe), from double-float copies of t2, t1, F'vv
+// (transposed per k), F'oo and ooov, and of ovvv (or complex64 integrals, which
+// widen exactly):
+//   Zr += 1/2 sum_f t_ij^af F'^{bf}(kb) - 1/2 sum_r t_r^a(ka) <ij||rb>^*
+//       - 1/2 sum_n t_in^ab F'_nj(kj)   - 1/2 sum_c t_i^c(ki) <jc||ab>^*
+// One thread per Zr element; the four short sums accumulate in double-float and
+// Zr receives their FP64 sum.
+__device__ __forceinline__ void cfma_df(const df2& a, const df2& b, df2& c) {
+    c.x = fma(a.x, b.x, c.x); c.x = fma(-a.y, b.y, c.x);
+    c.y = fma(a.x, b.y, c.y); c.y = fma(a.y, b.x, c.y);
+}
+__device__ __forceinline__ void cfma_conjb_df(const df2& a, const df2& b, df2& c) {
+    c.x = fma(a.x, b.x, c.x); c.x = fma(a.y, b.y, c.x);
+    c.y = fma(-a.x, b.y, c.y); c.y = fma(a.y, b.x, c.y);
+}
+struct FockTermsDfOp {
+    double2* Zr; const df2* t2; const df2* t1; const df2* fvvpT; const df2* foop;
+    const df2* ooov; const float2* ooov32;       // double-float copy, or complex64 input
+    const df2* ovvv; const float2* ovvv32;
+    const int* kb_of; int N, o, v;
+    __device__ void run(long long vb, long long nvb) const {
+        const long long blk = (long long)o * o * v * v;
+        const long long total = (long long)N * N * N * blk;
+        const long long vv = (long long)v * v, ov3 = (long long)o * v * vv, o3v = (long long)o * o * o * v;
+        for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
+            const long long kk = e / blk;
+            int r = (int)(e % blk);
+            const int b = r % v; r /= v;
+            const int a = r % v; r /= v;
+            const int j = r % o; const int i = r / o;
+            const int ka = (int)(kk % N), kj = (int)((kk / N) % N), ki = (int)(kk / ((long long)N * N));
+            const int kb = kb_of[kk];
+            const df2* tb = t2 + kk * blk;
+            df2 p{df(0.f, 0.f), df(0.f, 0.f)}, q{df(0.f, 0.f), df(0.f, 0.f)};
+            const df2* trow = tb + (((long long)i * o + j) * v + a) * v;              // t_ij^{a f}
+            const df2* fcol = fvvpT + (long long)kb * v * v + b;                      // F'^{b f}(kb) at f v
+            for (int f = 0; f < v; ++f) cfma_df(trow[f], fcol[(long long)f * v], p);
+            const long long oo_off = kk * o3v + ((long long)i * o + j) * o * v + b;   // <ij||r b>
+            const df2* ta = t1 + (long long)ka * o * v + a;                           // t_r^a(ka)
+            for (int rr = 0; rr < o; ++rr) {
+                const df2 w = ooov32 ? ld_df2(ooov32 + oo_off + (long long)rr * v) : ooov[oo_off + (long long)rr * v];
+                cfma_conjb_df(ta[rr * v], w, q);
+            }
+            const df2* tn = tb + ((long long)i * o * v + a) * v + b;                  // t_in^{ab}, n stride v^2
+            const df2* fo = foop + (long long)kj * o * o + j;                         // F'_{n j}(kj)
+            for (int n = 0; n < o; ++n) cfma_df(tn[(long long)n * vv], fo[n * o], q);
+            const long long kjia = ((long long)kj * N + ki) * N + ka;
+            const long long vb_off = kjia * ov3 + (long long)j * v * vv + (long long)a * v + b;   // <j c||a b>
+            const df2* ti = t1 + ((long long)ki * o + i) * v;                         // t_i^c(ki)
+            for (int c = 0; c < v; ++c) {
+                const df2 w = ovvv32 ? ld_df2(ovvv32 + vb_off + (long long)c * vv) : ovvv[vb_off + (long long)c * vv];
+                cfma_conjb_df(ti[c], w, q);
+            }
+            const df2 d{p.x - q.x, p.y - q.y};
+            double2 z = Zr[e];
+            z.x += 0.5 * (double)d.x;
+            z.y += 0.5 * (double)d.y;
+            Zr[e] = z;
+        }
+    }
+};
+__global__ void fock_terms_df_kernel(const FockTermsDfOp op) { op.run(blockIdx.x, gridDim.x); }
+
+// Double-float copies for fock_terms_df_kernel: t2 (n2 elements) into t2_df; t1 into
+// t1_df, F'vv transposed per k into fvvpT_df, F'oo into foop_df.  Each element is split
+// once (the split costs FP64 operations).
+struct ToDfOp {
+    df2* t2_df; const double2* t2; long long n2;
+    df2* t1_df; const double2* t1; long long n1;
+    df2* fvvpT_df; const double2* fvvp; df2* foop_df; const double2* foop; int N, o, v;
+    __device__ void run(long long vb, long long nvb) const {
+        const long long nv = (long long)N * v * v, no = (long long)N * o * o;
+        const long long total = n2 + n1 + nv + no;
+        for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
+            if (e < n2) { t2_df[e] = ld_df2(t2 + e); continue; }
+            long long f = e - n2;
+            if (f < n1) { t1_df[f] = ld_df2(t1 + f); continue; }
+            f -= n1;
+            if (f < nv) {
+                const long long k = f / ((long long)v * v);
+                const int rc = (int)(f % ((long long)v * v));
+                const int c = rc / v, r = rc % v;
+                fvvpT_df[f] = ld_df2(fvvp + (k * v + r) * v + c);
+                continue;
+            }
+            f -= nv;
+            foop_df[f] = ld_df2(foop + f);
+        }
+    }
+};
+__global__ void to_df_kernel(const ToDfOp op) { op.run(blockIdx.x, gridDim.x); }
+
+// ---------------------------------------------------------------------------
 // DIIS history on canonical momentum blocks.  t2 is antisymmetric under
 // (ki,i) <-> (kj,j) and under (ka,a) <-> (kb,b), so the blocks with ki <= kj and
 // ka <= kb determine all others; history vectors hold t1 followed by those
@@ -477,5 +574,166 @@ __global__ void combo_unpack(double2* __restrict__ out, const Combo cb, const in
         out[e] = make_double2(sg * re, sg * im);
     }
 }
+
+// ---------------------------------------------------------------------------
+// Device-resident DIIS (grouped iterations of the batched form): the same steps as
+// ccsd_iterate's host-driven DIIS -- pack x = t + R/D and e = R/D on the canonical
+// blocks into history slot `next`, the weighted inner products of e with every
+// filled slot, the Pulay solve, x = sum c_h x_h expanded to every block -- with the
+// history ring, the Gram matrix and the coefficients kept in device memory, so that
+// an iteration needs no host round trip and can be replayed from a CUDA graph.
+struct DiisState {
+    double2* hx[DIIS_MAX];    // history: amplitudes after the update (canonical blocks)
+    double2* he[DIIS_MAX];    // history: errors R / D
+    double gram[DIIS_MAX][DIIS_MAX];
+    double coef[DIIS_MAX];
+    int depth, next, count, m;
+    int singular;             // a solve met a zero pivot (that iteration took the plain update)
+};
+
+// pack into slot ds->next (diis_pack_update's body), skipped for converged members
+struct DiisPackOp {
+    const double2* amp; const double2* res; DiisState* ds;
+    const int* cblk; long long nc;
+    const double* eo; const double* ev; const int* kb_of; int N, o, v;
+    const int* skip;
+    __device__ void run(long long vb, long long nvb) const {
+        if (skip && *skip) return;
+        const int slot = ds->next;
+        double2* x_out = ds->hx[slot];
+        double2* e_out = ds->he[slot];
+        const long long n1 = (long long)N * o * v;
+        const long long blk = (long long)o * o * v * v;
+        const long long total = n1 + nc * blk;
+        for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
+            long long q;
+            double d;
+            if (e < n1) {
+                const int a = (int)(e % v);
+                const int i = (int)((e / v) % o);
+                const int k = (int)(e / ((long long)o * v));
+                d = eo[k * o + i] - ev[k * v + a];
+                q = e;
+            } else {
+                const long long pe = e - n1;
+                const long long f = cblk[pe / blk];
+                int r = (int)(pe % blk);
+                q = n1 + f * blk + r;
+                const int b = r % v; r /= v;
+                const int a = r % v; r /= v;
+                const int j = r % o; const int i = r / o;
+                const int ka = (int)(f % N), kj = (int)((f / N) % N), ki = (int)(f / ((long long)N * N));
+                const int kb = kb_of[f];
+                d = eo[ki * o + i] + eo[kj * o + j] - ev[ka * v + a] - ev[kb * v + b];
+            }
+            const double2 rq = res[q];
+            const double2 step = make_double2(rq.x / d, rq.y / d);
+            const double2 t = amp[q];
+            x_out[e] = make_double2(t.x + step.x, t.y + step.y);
+            e_out[e] = step;
+        }
+    }
+};
+
+// Partial sums of w-weighted Re <e_next | e_j> for every slot j of the history
+// (j >= the filled slots: zero): block vb = j * nred + r of a grid of depth * nred.
+struct DiisDotOp {
+    const DiisState* ds; long long n1, blk, nc; const double* cw;
+    double* part; int nred;
+    const int* skip;
+    __device__ void run(long long vb, long long) const {
+        if (skip && *skip) return;
+        __shared__ double sm[256];
+        const int j = (int)(vb / nred), r = (int)(vb % nred);
+        const int m = min(ds->count + 1, ds->depth);
+        double s = 0.0;
+        if (j < m) {
+            const double2* x = ds->he[ds->next];
+            const double2* y = ds->he[j];
+            const long long n = n1 + nc * blk;
+            for (long long e = (long long)r * blockDim.x + threadIdx.x; e < n; e += (long long)nred * blockDim.x) {
+                const double2 a = x[e], b = y[e];
+                const double w = e < n1 ? 1.0 : cw[(e - n1) / blk];
+                s += w * (a.x * b.x + a.y * b.y);
+            }
+        }
+        sm[threadIdx.x] = s;
+        __syncthreads();
+        for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+            if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[vb] = sm[0];
+    }
+};
+
+// One thread: the Gram row of the new slot (partials summed in a fixed order), the
+// Pulay solve over the filled slots, and the ring advance.
+struct DiisSolveOp {
+    DiisState* ds; const double* part; int nred;
+    const int* skip;
+    __device__ void run(long long vb, long long) const {
+        if ((skip && *skip) || vb != 0 || threadIdx.x != 0) return;
+        const int slot = ds->next;
+        const int m = min(ds->count + 1, ds->depth);
+        for (int j = 0; j < m; ++j) {
+            double d = 0.0;
+            for (int r = 0; r < nred; ++r) d += part[j * nred + r];
+            ds->gram[slot][j] = d;
+            ds->gram[j][slot] = d;
+        }
+        ds->count = m;
+        ds->next = (slot + 1) % ds->depth;
+        ds->m = m;
+        for (int j = 0; j < DIIS_MAX; ++j) ds->coef[j] = 0.0;
+        if (m < 2) { ds->coef[slot] = 1.0; return; }
+        double c[DIIS_MAX];
+        if (diis_solve(ds->gram, m, c)) {
+            for (int j = 0; j < m; ++j) ds->coef[j] = c[j];
+        } else {                  // singular: this iteration keeps the plain update
+            ds->singular = 1;
+            ds->coef[slot] = 1.0;
+        }
+    }
+};
+
+// amp = sum_h coef_h hx_h over the filled slots, expanded to every block with the
+// antisymmetry signs (combo_unpack's body).
+struct DiisComboOp {
+    double2* out; const DiisState* ds; const int* cmap; int N, o, v;
+    const int* skip;
+    __device__ void run(long long vb, long long nvb) const {
+        if (skip && *skip) return;
+        const int m = ds->m;
+        const long long n1 = (long long)N * o * v;
+        const long long blk = (long long)o * o * v * v;
+        const long long total = n1 + (long long)N * N * N * blk;
+        for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
+            long long src;
+            double sg = 1.0;
+            if (e < n1) {
+                src = e;
+            } else {
+                const long long f = (e - n1) / blk;
+                int r = (int)((e - n1) % blk);
+                const int b = r % v; r /= v;
+                const int a = r % v; r /= v;
+                const int j = r % o; const int i = r / o;
+                const int mm = cmap[f];
+                const int sij = (mm >> 1) & 1, sab = mm & 1;
+                const int i2 = sij ? j : i, j2 = sij ? i : j, a2 = sab ? b : a, b2 = sab ? a : b;
+                src = n1 + (long long)(mm >> 2) * blk + (((long long)i2 * o + j2) * v + a2) * v + b2;
+                if (sij != sab) sg = -1.0;
+            }
+            double re = 0.0, im = 0.0;
+            for (int h = 0; h < m; ++h) {
+                const double2 z = ds->hx[h][src];
+                re += ds->coef[h] * z.x;
+                im += ds->coef[h] * z.y;
+            }
+            out[e] = make_double2(sg * re, sg * im);
+        }
+    }
+};
 
 }  // namespace ccsdk

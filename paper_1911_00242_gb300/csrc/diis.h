@@ -1,13 +1,13 @@
-// DIIS host code: the canonical blocks of the history and the Pulay
-// extrapolation coefficients.
+// DIIS code: the canonical blocks of the history (host) and the Pulay
+// extrapolation coefficients (host and device).
 //
 // Pulay (DIIS) extrapolation coefficients.  Given the Gram matrix
 // B_ij = Re <e_i|e_j> of the last m update errors, the coefficients c minimise
 // |sum_i c_i e_i| subject to sum_i c_i = 1; with a Lagrange multiplier l they solve
 //   [ B  -1 ] [c]   [ 0]
 //   [-1   0 ] [l] = [-1],
-// here by Gaussian elimination with partial pivoting.  Host-only, so that the CPU
-// tests check this code itself.
+// here by Gaussian elimination with partial pivoting.  The CPU tests build this
+// header for the host and check this code itself.
 #pragma once
 #include <cmath>
 #include <utility>
@@ -53,35 +53,58 @@ inline bool diis_canonical_blocks(const KGrid& kg, std::vector<int>& cblk, std::
     return true;
 }
 
-// gram[i][j] for i, j < m (any row-indexable type); c receives m coefficients.
-// Returns false if the system is exactly singular (a zero pivot).
-template <class Gram>
-bool diis_coefficients(const Gram& gram, int m, double* c) {
+#ifdef __CUDACC__
+#define CCSD_HD __host__ __device__
+#else
+#define CCSD_HD
+#endif
+
+constexpr int DIIS_MAX = 8;     // deepest history
+
+// gram[i][j] for i, j < m <= DIIS_MAX; c receives m coefficients.  Returns false if
+// the system is exactly singular (a zero pivot).  The same code runs on the host
+// (ccsd_iterate) and on the device (grouped iterations of the batched form).
+CCSD_HD inline bool diis_solve(const double (*gram)[DIIS_MAX], int m, double* c) {
     const int S = m + 1;
-    std::vector<double> A((size_t)S * S, 0.0), b((size_t)S, 0.0);
-    for (int i = 0; i < m; ++i) for (int j = 0; j < m; ++j) A[(size_t)i * S + j] = gram[i][j];
-    for (int i = 0; i < m; ++i) { A[(size_t)i * S + m] = -1.0; A[(size_t)m * S + i] = -1.0; }
-    b[(size_t)m] = -1.0;
+    double A[DIIS_MAX + 1][DIIS_MAX + 1], b[DIIS_MAX + 1], xs[DIIS_MAX + 1];
+    for (int i = 0; i < S; ++i) { b[i] = 0.0; for (int j = 0; j < S; ++j) A[i][j] = 0.0; }
+    for (int i = 0; i < m; ++i) for (int j = 0; j < m; ++j) A[i][j] = gram[i][j];
+    for (int i = 0; i < m; ++i) { A[i][m] = -1.0; A[m][i] = -1.0; }
+    b[m] = -1.0;
     for (int col = 0; col < S; ++col) {
         int p = col;
-        for (int r = col + 1; r < S; ++r) if (std::fabs(A[(size_t)r * S + col]) > std::fabs(A[(size_t)p * S + col])) p = r;
-        if (p != col) { for (int k = 0; k < S; ++k) std::swap(A[(size_t)col * S + k], A[(size_t)p * S + k]); std::swap(b[col], b[p]); }
-        const double piv = A[(size_t)col * S + col];
+        for (int r = col + 1; r < S; ++r) {
+            const double x = A[r][col] < 0 ? -A[r][col] : A[r][col];
+            const double y = A[p][col] < 0 ? -A[p][col] : A[p][col];
+            if (x > y) p = r;
+        }
+        if (p != col) {
+            for (int k = 0; k < S; ++k) { const double t = A[col][k]; A[col][k] = A[p][k]; A[p][k] = t; }
+            const double t = b[col]; b[col] = b[p]; b[p] = t;
+        }
+        const double piv = A[col][col];
         if (piv == 0.0) return false;
         for (int r = col + 1; r < S; ++r) {
-            const double f = A[(size_t)r * S + col] / piv;
-            for (int k = col; k < S; ++k) A[(size_t)r * S + k] -= f * A[(size_t)col * S + k];
+            const double f = A[r][col] / piv;
+            for (int k = col; k < S; ++k) A[r][k] -= f * A[col][k];
             b[r] -= f * b[col];
         }
     }
-    std::vector<double> xs((size_t)S, 0.0);
     for (int r = S - 1; r >= 0; --r) {
         double s = b[r];
-        for (int k = r + 1; k < S; ++k) s -= A[(size_t)r * S + k] * xs[k];
-        xs[r] = s / A[(size_t)r * S + r];
+        for (int k = r + 1; k < S; ++k) s -= A[r][k] * xs[k];
+        xs[r] = s / A[r][r];
     }
     for (int j = 0; j < m; ++j) c[j] = xs[j];
     return true;
+}
+
+// The host entry: gram is any row-indexable type (m <= DIIS_MAX).
+template <class Gram>
+bool diis_coefficients(const Gram& gram, int m, double* c) {
+    double g[DIIS_MAX][DIIS_MAX];
+    for (int i = 0; i < m; ++i) for (int j = 0; j < m; ++j) g[i][j] = gram[i][j];
+    return diis_solve(g, m, c);
 }
 
 }  // namespace ccsdk

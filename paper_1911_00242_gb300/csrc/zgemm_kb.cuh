@@ -71,18 +71,28 @@ struct ZgemmSmem {
 // and br + bi are formed once per element when the tile is staged).  The FP32
 // instance keeps the four-product form, whose imaginary part has no
 // cancellation (its operands are already rounded to FP32).
-template <int BM, int BN, int BK, int TM, int TN, typename T>
+//
+// KS > 1 (skinny contractions: few outputs, long K): the CTA's threads form KS groups
+// of (BM / TM) (BN / TN) threads; all of them stage each K step, group q multiplies
+// its BK / KS rows of it, and at the end the groups' partial sums are added in group
+// order (deterministic) before the epilogue.  A tile then keeps KS times more
+// independent accumulators and loads in flight per barrier.
+template <int BM, int BN, int BK, int TM, int TN, typename T, int KS = 1>
 __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long long b, int split,
                                            ZgemmSmem<BM, BN, BK, T>& sm)
 {
     using V = typename Cplx<T>::V;
     constexpr bool k3M = sizeof(T) == 8;         // double and double-float: 3M products
-    constexpr int NT = (BM / TM) * (BN / TN);
+    constexpr int NT1 = (BM / TM) * (BN / TN);   // threads of one K group
+    constexpr int NT = NT1 * KS;
     constexpr int TX = BN / TN;
+    constexpr int KG = BK / KS;                  // K rows of a stage per group
+    static_assert(BK % KS == 0, "each K group takes an equal share of a stage");
     const int m0 = (tile % g.tiles_m) * BM;
     const int n0 = (tile / g.tiles_m) * BN;
     const int tid = threadIdx.x;
-    const int tx = tid % TX, ty = tid / TX;
+    const int kgrp = tid / NT1;
+    const int tx = (tid % NT1) % TX, ty = (tid % NT1) / TX;
     auto& As = sm.A;
     auto& Bs = sm.B;
 
@@ -137,7 +147,8 @@ __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long lon
             }
             __syncthreads();
 #pragma unroll
-            for (int kk = 0; kk < BK; ++kk) {
+            for (int kq = 0; kq < KG; ++kq) {
+                const int kk = kgrp * KG + kq;
                 V a[TM], bb[TN];
 #pragma unroll
                 for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
@@ -173,6 +184,41 @@ __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long lon
         }
     }
 
+    if constexpr (KS > 1) {
+        // the groups' partial sums, added in group order by group 0 (the stage buffers
+        // are free: the last K step ended with a barrier)
+        constexpr int NV = TM * TN * (k3M ? 3 : 2);
+        static_assert(sizeof(ZgemmSmem<BM, BN, BK, T>) >= sizeof(T) * NV * NT1 * (KS > 1 ? KS - 1 : 1),
+                      "the partial sums of the K groups fit the stage buffers");
+        T* red = (T*)&sm;
+        const int t1 = tid % NT1;
+        if (kgrp > 0) {
+            T* dst = red + ((long long)(kgrp - 1) * NT1 + t1) * NV;
+            int q = 0;
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    dst[q++] = cr[i][j];
+                    dst[q++] = ci[i][j];
+                    if (k3M) dst[q++] = cs[i][k3M ? j : 0];
+                }
+        }
+        __syncthreads();
+        if (kgrp > 0) return;
+        for (int gq = 1; gq < KS; ++gq) {
+            const T* src = red + ((long long)(gq - 1) * NT1 + t1) * NV;
+            int q = 0;
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    cr[i][j] = cr[i][j] + src[q++];
+                    ci[i][j] = ci[i][j] + src[q++];
+                    if (k3M) cs[i][k3M ? j : 0] = cs[i][k3M ? j : 0] + src[q++];
+                }
+        }
+    }
     if (k3M) {
 #pragma unroll
         for (int i = 0; i < TM; ++i)
@@ -215,21 +261,21 @@ __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long lon
         }
 }
 
-template <int BM, int BN, int BK, int TM, int TN, typename T = double>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+template <int BM, int BN, int BK, int TM, int TN, typename T = double, int KS = 1>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN) * KS)
 zgemm_kb_kernel(const GemmArgs g)
 {
     __shared__ ZgemmSmem<BM, BN, BK, T> sm;
     const int ntile = g.tiles_m * g.tiles_n;
-    zgemm_tile<BM, BN, BK, TM, TN, T>(g, blockIdx.x % ntile, blockIdx.x / ntile, blockIdx.y, sm);
+    zgemm_tile<BM, BN, BK, TM, TN, T, KS>(g, blockIdx.x % ntile, blockIdx.x / ntile, blockIdx.y, sm);
 }
 
 // Grouped persistent form (batched solves): one launch covers the same plan
 // step of many independent problems.  Work item w of the flattened list
 // [member][split][batch][tile] maps to member i with prefix[i] <= w < prefix[i+1];
 // every CTA strides through the list.  All members use this launch's tile shape.
-template <int BM, int BN, int BK, int TM, int TN, typename T = double>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+template <int BM, int BN, int BK, int TM, int TN, typename T = double, int KS = 1>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN) * KS)
 zgemm_grouped_kernel(const GemmArgs* __restrict__ gs, const long long* __restrict__ prefix, int nmem, long long total)
 {
     __shared__ ZgemmSmem<BM, BN, BK, T> sm;
@@ -245,7 +291,8 @@ zgemm_grouped_kernel(const GemmArgs* __restrict__ gs, const long long* __restric
         const long long per_split = ntile * g.nbatch;
         const int split = (int)(local / per_split);
         const long long r = local % per_split;
-        zgemm_tile<BM, BN, BK, TM, TN, T>(g, (int)(r % ntile), r / ntile, split, sm);
+        zgemm_tile<BM, BN, BK, TM, TN, T, KS>(g, (int)(r % ntile), r / ntile, split, sm);
+        if (KS > 1) __syncthreads();        // the next item reuses the stage buffers
     }
 }
 

@@ -90,3 +90,42 @@ def test_mixed_batch_complex64_members(lib):
         ref = driver.solve(P, tol=1e-10, max_iter=200)
         assert abs(e.real - ref["energies"][-1].real / s.nk) < 1e-6
     B.close()
+
+
+def test_batch_diis_members_match_standalone(lib):
+    """DIIS(6) inside the batch (device-resident history, Gram matrix and Pulay solve)
+    against each member run alone with the host-driven DIIS: energies after 6
+    extrapolated updates within 1e-11 Ha (the coefficient solve may round in a
+    different order on the device)."""
+    from paper_1911_00242_gb300.binding import BatchSolver, Solver
+    specs = SPECS[:4]
+    inps = [cs.generate(s) for s in specs]
+    devs = [dev(i) for i in inps]
+    B = BatchSolver([(s.grid, s.nocc, s.nvir, d) for s, d in zip(specs, devs)], conv_tol=1e-30, diis_depth=6)
+    B.iterate(6)
+    eb = B.energies()
+    for s, d, e in zip(specs, devs, eb):
+        S = Solver(s.grid, s.nocc, s.nvir, d, conv_tol=1e-30, diis_depth=6)
+        S.iterate(6)
+        assert abs(S.energy() - e) < 1e-11, (s, S.energy(), e)
+        S.close()
+    B.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_diis_converges_to_oracle(lib, precision):
+    """Members with DIIS(6) converge to the oracle's DIIS(6) energies: FP64 members
+    to 1e-8 Ha, mixed members (no polish inside the batch) to 1e-6 Ha."""
+    from paper_1911_00242_gb300.binding import BatchSolver
+    specs = SPECS[:4]
+    inps = [cs.generate(s) for s in specs]
+    B = BatchSolver([(s.grid, s.nocc, s.nvir, dev(i)) for s, i in zip(specs, inps)], conv_tol=1e-9 if precision == 0
+                    else 1e-7, diis_depth=6, precision=precision)
+    done, mr = B.iterate(100)
+    assert all(done), (done, mr)
+    eb = B.energies()
+    for s, inp, e in zip(specs, inps, eb):
+        P = ccsd_k.Problem(s.grid, s.nocc, s.nvir, inp)
+        ref = driver.solve(P, tol=1e-10, max_iter=200, diis_depth=6)
+        assert abs(e.real - ref["energies"][-1].real / s.nk) < (1e-8 if precision == 0 else 1e-6)
+    B.close()
