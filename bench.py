@@ -454,6 +454,7 @@ def run_serve(args, local):
         time.sleep(0.005)
     elapsed = time.perf_counter() - t_start
     clk = clocks.stop()
+    prof = srv.profile()
     srv.close()
     ok = [v for v in done.values() if v[0] == 2]
     ts = np.array([v[1] for v in ok])
@@ -471,7 +472,8 @@ def run_serve(args, local):
             "p50_large_s": q(tl, 50), "p99_large_s": q(tl, 99),
             "solves_per_s": len(ok) / elapsed, "submitted": len(ids), "completed": len(ok),
             "failed": len(ids) - len(ok), "elapsed_s": elapsed, "peak_admitted_gb": peak_bytes / 2**30,
-            "peak_active": peak_active, "clocks": clk}
+            "peak_active": peak_active, "clocks": clk,
+            "server": prof}
 
 
 def run_grid333(args, local):

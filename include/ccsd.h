@@ -186,9 +186,11 @@ int ccsd_residual(ccsd_t h, const void* t1, const void* t2, void* r1, void* r2);
 /* Up to n_iter iterations on the handle's amplitudes.  Each computes R(t);
  * if max(max|R1|, max|R2|) < conv_tol it sets *done = 1 and stops without
  * updating; otherwise t <- t + R/D (paper Sec. 4.4.19, D from the Fock
- * diagonal), followed by DIIS extrapolation when diis_depth > 0.
- * *max_resid receives the last max|R| (may be NULL).  Returns
- * CCSD_ERR_DIVERGED if R is not finite. */
+ * diagonal), followed by DIIS extrapolation when diis_depth > 0 (history, Gram
+ * matrix and Pulay solve in device memory; an iteration whose DIIS system is
+ * singular keeps the plain update).  The only host synchronization of an iteration
+ * is the read of max|R|.  *max_resid receives the last max|R| (may be NULL).
+ * Returns CCSD_ERR_DIVERGED if R is not finite. */
 int ccsd_iterate(ccsd_t h, int n_iter, int* done, double* max_resid);
 
 /* Iterates until convergence or cfg->max_iter updates; CCSD_ERR_NOT_CONVERGED
@@ -248,9 +250,8 @@ int ccsd_destroy(ccsd_t h);
  * per-member max|R|, update of the members not yet converged, DIIS extrapolation
  * with its history, Gram matrix and Pulay solve kept in device memory -- is
  * replayed as one CUDA graph.  Members stop updating once their max|R| < conv_tol.
- * The problem data follow the rules of ccsd_create (device inputs borrowed).  The
- * batch's DIIS history is its own: ccsd_iterate on a member handle afterwards
- * starts a fresh history. */
+ * The problem data follow the rules of ccsd_create (device inputs borrowed).  Each
+ * member extrapolates with its own handle's DIIS history, as ccsd_iterate does. */
 typedef struct ccsd_batch* ccsd_batch_t;
 int ccsd_batch_create(int n, const ccsd_config* cfgs, const ccsd_inputs* inputs, ccsd_batch_t* out);
 /* Up to n_iter iterations; done[i] / max_resid[i] per member (arrays of n, may be NULL). */
@@ -268,21 +269,25 @@ int ccsd_batch_destroy(ccsd_batch_t b);
  * A request loop on its own host thread.  Submitted solves wait in FIFO order
  * until their device-memory footprint fits in hbm_budget_bytes and one of
  * max_slots slots is free; each admitted solve gets a handle whose integrals and
- * amplitudes stay resident until it finishes.  All admitted solves advance
- * together, one iteration each per round: solves with the same plan signature,
- * arithmetic and contraction tile shapes form a group, and every step of their
- * residual is one grouped launch (the groups run concurrently); all max|R| come
- * back in one copy, then each solve takes its convergence test and update.  A
- * solve's iterates are bitwise those it has alone.  Converged solves retire and
- * free their memory for the queue.  A solve runs like ccsd_solve (mixed
+ * amplitudes stay resident until it finishes.  Admitted solves advance in rounds,
+ * one iteration each per round, in lanes by the order of magnitude of their
+ * iteration's work: every lane has a stream of its own and runs its rounds at its own
+ * pace, so small solves do not wait for the iterations of large ones.  Within a
+ * lane's round, solves with the same plan signature, arithmetic and contraction tile
+ * shapes form a group, and every step of their residual is one grouped launch (the
+ * groups run concurrently); all max|R| come back in one copy, each solve takes its
+ * convergence test, and one grouped update (with DIIS) advances the solves that go
+ * on.  A solve's iterates are bitwise those it has alone.  Converged solves retire
+ * and free their memory for the queue.  A solve runs like ccsd_solve (mixed
  * iterations, then polish_iters iterations in polish_precision, for CCSD_MIXED).
  * The inputs a request points to must stay valid until it is done (host inputs
  * are copied when the request is admitted). */
 typedef struct ccsd_server* ccsd_server_t;
 /* Starts the loop on the current device: hbm_budget_bytes > 0, 1 <= max_slots <= 1024.
- * `stream` (a cudaStream_t) carries every device operation of the server, and the
- * server's group streams fork from and join into it; NULL: the server creates a
- * non-blocking stream of its own.  A given stream must outlive the server. */
+ * `stream` (a cudaStream_t; NULL: the server creates a non-blocking stream of its
+ * own) orders the server with the caller's work: the lanes start after the work
+ * queued on it before this call, and it waits for the lanes' work when the server
+ * is destroyed.  A given stream must outlive the server. */
 int ccsd_server_create(size_t hbm_budget_bytes, int max_slots, void* stream, ccsd_server_t* out);
 /* Queues one solve (config and input pointers are copied into the request; the
  * data they point to is not) and returns its id.  CCSD_ERR_INVALID for a bad
@@ -294,6 +299,13 @@ int ccsd_submit(ccsd_server_t s, const ccsd_config* cfg, const ccsd_inputs* in, 
 int ccsd_poll(ccsd_server_t s, uint64_t id, int* state, double* e_corr, double* t_converge_s, int* iterations);
 /* Running solves, queued solves and the device bytes admitted solves hold. */
 int ccsd_server_stats(ccsd_server_t s, int* active, int* queued, size_t* admitted_bytes);
+/* Statistics of the loop so far: rounds run (over all lanes), groups built (a group
+ * is rebuilt when its solves change), the host seconds spent in rounds and, within
+ * them, in building groups, and over the admitted solves that finished the mean wait
+ * from submission to admission and the mean time from admission to completion.  Any
+ * pointer may be NULL.  The paper has no counterpart. */
+int ccsd_server_profile(ccsd_server_t s, long long* rounds, long long* group_builds, double* round_seconds,
+                        double* build_seconds, double* mean_wait_s, double* mean_run_s);
 /* Finishes the admitted solves, cancels the queued ones, joins the thread. */
 int ccsd_server_destroy(ccsd_server_t s);
 

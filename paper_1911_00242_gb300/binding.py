@@ -90,6 +90,8 @@ SYMBOLS = {
                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "ccsd_server_stats": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "ccsd_server_profile": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+                            + [ctypes.POINTER(ctypes.c_double)] * 4, ctypes.c_int),
     "ccsd_server_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "ccsd_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "ccsd_last_error": ([], ctypes.c_char_p),
@@ -414,6 +416,16 @@ class Server:
         b = ctypes.c_size_t(0)
         check(self.lib.ccsd_server_stats(self.h, ctypes.byref(a), ctypes.byref(q), ctypes.byref(b)), "ccsd_server_stats")
         return a.value, q.value, b.value
+
+    def profile(self):
+        """dict: rounds, group builds, seconds in rounds and in building groups, and the
+        mean wait for admission and mean run time of the finished solves."""
+        r, b = ctypes.c_longlong(0), ctypes.c_longlong(0)
+        x = [ctypes.c_double(0.0) for _ in range(4)]
+        check(self.lib.ccsd_server_profile(self.h, ctypes.byref(r), ctypes.byref(b), *[ctypes.byref(v) for v in x]),
+              "ccsd_server_profile")
+        return {"rounds": r.value, "group_builds": b.value, "round_s": x[0].value, "group_build_s": x[1].value,
+                "mean_wait_s": x[2].value, "mean_run_s": x[3].value}
 
     def close(self):
         if getattr(self, "h", None):

@@ -150,8 +150,9 @@ struct ccsd_ctx {
     int* d_cblk = nullptr;           // full block index of each canonical block
     double* d_cw = nullptr;          // its weight: the number of blocks it stands for
     int* d_cmap = nullptr;           // per full block: 4 * canonical index + 2 swap_ij + swap_ab
-    std::vector<std::vector<double>> gram;
-    int diis_count = 0, diis_next = 0;
+    DiisState* d_diis = nullptr;     // DIIS state on the device (history ring, Gram matrix, coefficients)
+    double* d_diis_part = nullptr;   // [depth][red_blocks] inner-product partials
+    DiisState diis_init{};           // its initial value (empty history), for resets
     std::vector<GemmPlan> gemms;
     std::vector<CopyPlan> copies;
     std::vector<PermPlan> perms;
@@ -271,6 +272,7 @@ const int CFG_BM[CFG_COUNT] = {64, 64, 128, 16, 32, 16, 32};
 const int CFG_BN[CFG_COUNT] = {64, 32, 16, 16, 16, 16, 16};
 
 const int kSMs = 152;
+const int kRedBlocks = kSMs * 4;    // blocks of the reductions (max|R|, inner products, energy)
 
 // Momentum pairs (ka <= kb) whose ladder W' blocks one slab holds: as many as fit in
 // cap bytes, at least one.  The slab buffer holds that many pairs x N blocks of v^4.
@@ -332,6 +334,22 @@ int finalize_gemm(ccsd_ctx* h, Alloc& al, GemmSpec s, size_t& work_need) {
     }
     GemmPlan p{};
     p.a = s.a; p.b = s.b; p.c = s.c;
+    // affine tables: the index arithmetic replaces the table loads in the kernel
+    auto affine = [](const std::vector<int>& t, int& stride) {
+        if (t.size() < 2) { stride = 0; return true; }
+        const long long d = (long long)t[1] - t[0];
+        if (d < INT_MIN || d > INT_MAX) return false;
+        for (size_t i = 2; i < t.size(); ++i) if ((long long)t[i] - t[i - 1] != d) return false;
+        stride = (int)d;
+        return true;
+    };
+    {
+        GemmArgs& g0 = p.args;
+        g0.affA = affine(s.rowA, g0.rAs) && affine(s.colA, g0.cAs) ? 1 : 0;
+        g0.affB = affine(s.rowB, g0.rBs) && affine(s.colB, g0.cBs) ? 1 : 0;
+        g0.a0 = g0.affA ? (long long)s.rowA[0] + s.colA[0] : 0;
+        g0.b0 = g0.affB ? (long long)s.rowB[0] + s.colB[0] : 0;
+    }
     if (s.N >= 48) p.cfg = CFG_64x64;
     else if (s.N > 16) p.cfg = CFG_64x32;
     else if (s.M > 64) p.cfg = CFG_128x16;
@@ -2138,15 +2156,22 @@ struct GLaunch {
 
 struct Group {
     std::vector<ccsd_ctx*> m;
-    std::vector<int> ids;             // caller's member indices
+    std::vector<int> ids;             // caller's member indices (batched form)
+    std::vector<uint64_t> rids;       // request ids of the members (serving form): a handle's
+                                      // address can be reused by a later request, an id is not
     int fp32 = 0;
     std::vector<size_t> steps;        // active plan steps, the same in every member
     std::vector<GLaunch> res;         // the residual, in plan order
     std::vector<BatchGroup> gemms;
     GLaunch norms, update;
     double* d_norms = nullptr;        // max|R| of each member (a caller's slice, or owned)
+    int* d_skip = nullptr;            // serving form: per member, 1 = no update this round
     int* d_err = nullptr;             // shared error word of the grouped tensor-core launches
-    std::vector<void*> owned;
+    std::vector<void*> owned;         // device allocations of this group
+    struct ChunkPool* pool = nullptr; // chunks for the tables (null: allocated per group)
+    std::vector<void*> chunks;        // chunks taken from the pool
+    char* chunk = nullptr;
+    size_t chunk_used = 0;
 };
 
 // Step signature of a plan: members with equal signatures share every grouped launch.
@@ -2156,9 +2181,44 @@ std::vector<std::pair<int, int>> plan_signature(const ccsd_ctx* h) {
     return sig;
 }
 
+// Device memory of a group's tables: 256-byte aligned pieces of 4 MiB chunks.  A
+// serving loop rebuilds groups whenever its admitted solves change, so the chunks
+// come from a pool that outlives the groups (no cudaMalloc or cudaFree per rebuild).
+constexpr size_t kChunkBytes = 4u << 20;
+
+struct ChunkPool {
+    std::vector<void*> free_chunks, all;
+    ~ChunkPool() { for (void* p : all) cudaFree(p); }
+    void* get() {
+        if (!free_chunks.empty()) { void* p = free_chunks.back(); free_chunks.pop_back(); return p; }
+        void* p = nullptr;
+        if (cudaMalloc(&p, kChunkBytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        all.push_back(p);
+        return p;
+    }
+};
+
 int group_alloc(Group& G, size_t bytes, void** p) {
-    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) { cudaGetLastError(); return CCSD_ERR_OOM; }
-    G.owned.push_back(*p);
+    bytes = (std::max<size_t>(bytes, 16) + 255) / 256 * 256;
+    if (bytes > kChunkBytes) {            // a table larger than a chunk: its own allocation
+        if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); return CCSD_ERR_OOM; }
+        G.owned.push_back(*p);
+        return 0;
+    }
+    if (!G.chunk || G.chunk_used + bytes > kChunkBytes) {
+        void* c = G.pool ? G.pool->get() : nullptr;
+        if (!G.pool) {
+            if (cudaMalloc(&c, kChunkBytes) != cudaSuccess) { cudaGetLastError(); c = nullptr; }
+            else G.owned.push_back(c);
+        } else if (c) {
+            G.chunks.push_back(c);
+        }
+        if (!c) return CCSD_ERR_OOM;
+        G.chunk = (char*)c;
+        G.chunk_used = 0;
+    }
+    *p = G.chunk + G.chunk_used;
+    G.chunk_used += bytes;
     return 0;
 }
 
@@ -2176,7 +2236,10 @@ T* group_upload(Group& G, const std::vector<T>& v, cudaStream_t st, int* rc) {
 
 void group_free(Group& G) {
     for (void* p : G.owned) cudaFree(p);
+    if (G.pool) for (void* c : G.chunks) G.pool->free_chunks.push_back(c);
+    ChunkPool* pool = G.pool;
     G = Group();
+    G.pool = pool;
 }
 
 long long grid_blocks(const dim3& g) { return (long long)g.x; }
@@ -2501,41 +2564,28 @@ int group_build(Group& G, int fp32, const std::vector<int>& cfgs, double* d_norm
         if (depth == 0) {
             if ((rc = make_grouped(G, up, bu, st, G.update))) return rc;
         } else {
-            // device-resident DIIS: pack, inner products, Pulay solve, extrapolation
-            std::vector<DiisState> init((size_t)n);
-            long long nparts = 0;
-            for (int i = 0; i < n; ++i) {
-                ccsd_ctx* h = G.m[i];
-                DiisState& d = init[(size_t)i];
-                memset(&d, 0, sizeof d);
-                d.depth = depth;
-                for (int j = 0; j < depth; ++j) { d.hx[j] = h->hx[(size_t)j]; d.he[j] = h->he[(size_t)j]; }
-                nparts += (long long)depth * h->red_blocks;
-            }
-            DiisState* d_ds = group_upload(G, init, st, &rc);
-            if (rc) return rc;
-            double* d_part = nullptr;
-            if ((rc = group_alloc(G, sizeof(double) * nparts, (void**)&d_part))) return rc;
+            // DIIS on the device, on each member's own history (the handle's DIIS state):
+            // pack, inner products, Pulay solve, extrapolation -- the kernels and grids of
+            // ccsd_iterate, so a member's iterates are those it has alone
             std::vector<DiisPackOp> pk;
             std::vector<DiisDotOp> dt;
             std::vector<DiisSolveOp> sv;
             std::vector<DiisComboOp> cb;
             std::vector<long long> bp, bd, bs, bc;
-            long long off = 0;
             for (int i = 0; i < n; ++i) {
                 ccsd_ctx* h = G.m[i];
+                if (!h->d_diis) { refuse("a group member has no DIIS state"); return CCSD_ERR_INVALID; }
                 const int* skip = d_skip ? d_skip + i : nullptr;
                 const long long blk = (long long)h->o * h->o * h->v * h->v;
-                pk.push_back(DiisPackOp{h->amp, h->res, d_ds + i, h->d_cblk, h->nc, h->eo, h->ev, h->kb_of,
+                pk.push_back(DiisPackOp{h->amp, h->res, h->d_diis, h->d_cblk, h->nc, h->eo, h->ev, h->kb_of,
                                         h->N, h->o, h->v, skip});
                 bp.push_back(grid_blocks(ew_grid(h->n1 + h->nc * blk)));
-                dt.push_back(DiisDotOp{d_ds + i, h->n1, blk, h->nc, h->d_cw, d_part + off, h->red_blocks, skip});
+                dt.push_back(DiisDotOp{h->d_diis, h->n1, blk, h->nc, h->d_cw, h->d_diis_part, h->red_blocks, skip});
                 bd.push_back((long long)depth * h->red_blocks);
-                sv.push_back(DiisSolveOp{d_ds + i, d_part + off, h->red_blocks, skip});
+                sv.push_back(DiisSolveOp{h->d_diis, h->d_diis_part, h->red_blocks, skip});
                 bs.push_back(1);
-                cb.push_back(DiisComboOp{h->amp, d_ds + i, h->d_cmap, h->N, h->o, h->v, skip});
+                cb.push_back(DiisComboOp{h->amp, h->d_diis, h->d_cmap, h->N, h->o, h->v, skip});
                 bc.push_back(grid_blocks(ew_grid(h->n1 + h->n2)));
-                off += (long long)depth * h->red_blocks;
             }
             GLaunch g1, g2, g3, g4;
             if ((rc = make_grouped(G, pk, bp, st, g1)) || (rc = make_grouped(G, dt, bd, st, g2)) ||
@@ -2808,9 +2858,16 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
             h->hx.push_back(dalloc(np));
             h->he.push_back(dalloc(np));
         }
+        h->d_diis = (DiisState*)al.get(sizeof(DiisState));
+        h->d_diis_part = (double*)al.get(sizeof(double) * (size_t)h->cfg.diis_depth * kRedBlocks);
+        if (al.err) return al.err;
+        memset(&h->diis_init, 0, sizeof h->diis_init);
+        h->diis_init.depth = h->cfg.diis_depth;
+        for (int d = 0; d < h->cfg.diis_depth; ++d) { h->diis_init.hx[d] = h->hx[(size_t)d]; h->diis_init.he[d] = h->he[(size_t)d]; }
+        if (!al.dry && cudaMemcpyAsync(h->d_diis, &h->diis_init, sizeof(DiisState), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+            return CCSD_ERR_CUDA;
     }
     if (al.err) return al.err;
-    h->gram.assign(h->cfg.diis_depth, std::vector<double>(h->cfg.diis_depth, 0.0));
     if (!al.dry && cudaMemsetAsync(h->amp, 0, (size_t)(h->n1 + h->n2) * 16, h->st) != cudaSuccess) return CCSD_ERR_CUDA;
 
     // Fock diagonals and the fourth momentum of doubles blocks
@@ -2850,7 +2907,7 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
     if (work_need) { h->work = dalloc((long long)work_need); if (!h->work) return al.err; }
     if (h->oz_work_elems) { h->oz_work = dalloc(h->oz_work_elems); if (!h->oz_work) return al.err; }
     h->work_elems = work_need;
-    h->red_blocks = 152 * 4;
+    h->red_blocks = kRedBlocks;
     h->red = (double*)al.get(sizeof(double) * h->red_blocks);
     h->red_out = (double*)al.get(sizeof(double) * 4);
     h->cred = (double2*)al.get(sizeof(double2) * h->red_blocks);
@@ -2908,6 +2965,15 @@ int iter_begin(ccsd_ctx* h) {
 // t <- t + R/D (plus DIIS) unless converged.
 int iter_finish(ccsd_ctx* h, double mr, int* done);
 
+// The convergence test alone: CCSD_ERR_DIVERGED for a non-finite max|R|, *done when
+// max|R| < conv_tol.
+int iter_test(const ccsd_ctx* h, double mr, int* done) {
+    *done = 0;
+    if (!std::isfinite(mr)) { refuse("max|R| is not finite: the iteration diverged"); return CCSD_ERR_DIVERGED; }
+    if (mr < h->cfg.conv_tol) *done = 1;
+    return CCSD_OK;
+}
+
 int iter_end(ccsd_ctx* h, int* done, double* max_resid) {
     *done = 0;
     CK(cudaEventSynchronize(h->ev_norm));
@@ -2923,11 +2989,9 @@ int iter_end(ccsd_ctx* h, int* done, double* max_resid) {
 // with DIIS extrapolation (enqueued on the handle's stream; the DIIS inner products
 // synchronize it).
 int iter_finish(ccsd_ctx* h, double mr, int* done) {
-    int rc = 0;
-    *done = 0;
+    int rc = iter_test(h, mr, done);
+    if (rc || *done) return rc;
     const long long n = h->n1 + h->n2;
-    if (!std::isfinite(mr)) { refuse("max|R| is not finite: the iteration diverged"); return CCSD_ERR_DIVERGED; }
-    if (mr < h->cfg.conv_tol) { *done = 1; return CCSD_OK; }
     const int depth = h->cfg.diis_depth;
     const size_t tu = h->seq.size();     // trace slot of the update
     if (h->trace) cudaEventRecord(h->ev0[tu], h->st);
@@ -2936,39 +3000,19 @@ int iter_finish(ccsd_ctx* h, double mr, int* done) {
         ++h->launches;
         if (h->trace) { cudaEventRecord(h->ev1[tu], h->st); if ((rc = trace_collect(h, tu, tu + 1))) return rc; }
     } else {
-        const int slot = h->diis_next;
-        double2* x = h->hx[slot];
-        double2* e = h->he[slot];
+        // DIIS on the device: pack x = t + R/D and e = R/D into the history, inner products
+        // of e with the filled slots, the Pulay solve, the extrapolation (no host round trip)
         const long long blk = (long long)h->o * h->o * h->v * h->v;
         const long long np = h->n1 + h->nc * blk;
-        diis_pack_update<<<ew_grid(np), 256, 0, h->st>>>(h->amp, h->res, x, e, h->d_cblk, h->nc, h->eo, h->ev,
-                                                         h->kb_of, h->N, h->o, h->v);
-        ++h->launches;
+        op_kernel<DiisPackOp><<<ew_grid(np), 256, 0, h->st>>>(DiisPackOp{h->amp, h->res, h->d_diis, h->d_cblk, h->nc,
+                                                                          h->eo, h->ev, h->kb_of, h->N, h->o, h->v, nullptr});
+        op_kernel<DiisDotOp><<<(unsigned)(depth * h->red_blocks), 256, 0, h->st>>>(
+            DiisDotOp{h->d_diis, h->n1, blk, h->nc, h->d_cw, h->d_diis_part, h->red_blocks, nullptr});
+        op_kernel<DiisSolveOp><<<1, 32, 0, h->st>>>(DiisSolveOp{h->d_diis, h->d_diis_part, h->red_blocks, nullptr});
+        op_kernel<DiisComboOp><<<ew_grid(n), 256, 0, h->st>>>(DiisComboOp{h->amp, h->d_diis, h->d_cmap, h->N, h->o, h->v,
+                                                                          nullptr});
+        h->launches += 4;
         if (h->trace) { cudaEventRecord(h->ev1[tu], h->st); if ((rc = trace_collect(h, tu, tu + 1))) return rc; }
-        h->diis_next = (slot + 1) % depth;
-        if (h->diis_count < depth) ++h->diis_count;
-        const int m = h->diis_count;
-        for (int j = 0; j < m; ++j) {
-            redot_w_partial<<<h->red_blocks, 256, 0, h->st>>>(e, h->he[j], h->n1, blk, h->nc, h->d_cw, h->red);
-            final_sum<<<1, 32, 0, h->st>>>(h->red, h->red_blocks, h->red_out + 0);
-            h->launches += 2;
-            double d = 0.0;
-            CK(cudaMemcpyAsync(&d, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-            CK(cudaStreamSynchronize(h->st));
-            h->gram[slot][j] = h->gram[j][slot] = d;
-        }
-        Combo cb{};
-        if (m < 2) {
-            cb.m = 1; cb.x[0] = x; cb.c[0] = 1.0;
-        } else {
-            // Pulay: [B -1; -1 0][c; l] = [0; -1]
-            double cs[8];
-            if (!diis_coefficients(h->gram, m, cs)) { refuse("the DIIS system is singular"); return CCSD_ERR_DIVERGED; }
-            cb.m = m;
-            for (int j = 0; j < m; ++j) { cb.x[j] = h->hx[j]; cb.c[j] = cs[j]; }
-        }
-        combo_unpack<<<ew_grid(n), 256, 0, h->st>>>(h->amp, cb, h->d_cmap, h->N, h->o, h->v);
-        ++h->launches;
     }
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) { last_err(ce); return CCSD_ERR_CUDA; }
@@ -3001,8 +3045,32 @@ struct ServerReq {
     double e_re = 0.0, e_im = 0.0, max_resid = 0.0;
     double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
     size_t bytes = 0;
+    int lane = 0;                  // cost class of one iteration (its lane of rounds)
     ccsd_t h = nullptr;
 };
+
+// A lane runs rounds over the solves of one cost class, on a stream of its own, at its
+// own pace: a round of small solves does not wait for the iteration of a large one.
+struct Lane {
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;    // recorded after the round's norms are copied out
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaStream_t> gst; // one stream per group of the round
+    std::vector<cudaEvent_t> gev;
+    std::vector<ServerReq*> active;
+    std::map<std::vector<long long>, std::unique_ptr<Group>> groups;
+    // the round in flight
+    bool in_flight = false;
+    std::vector<std::pair<Group*, std::vector<ServerReq*>>> grp;
+    std::vector<int> first;
+    std::vector<ServerReq*> solo;
+    std::vector<int> began;
+    double* h_norms = nullptr;     // pinned, one per slot
+    double t0 = 0.0, t_built = 0.0;
+    long long builds = 0;
+};
+
+constexpr int kLanes = 4;
 
 }  // namespace
 
@@ -3021,13 +3089,12 @@ struct ccsd_server {
     bool stop = false;
     std::thread th;
     std::chrono::steady_clock::time_point t0;
-    // grouped rounds (touched by the loop thread only)
-    std::map<std::vector<long long>, std::unique_ptr<Group>> groups;
-    std::vector<cudaStream_t> gst;
-    std::vector<cudaEvent_t> gev;
-    cudaEvent_t fork = nullptr;
-    double* h_norms = nullptr;     // pinned, max_slots
-    long long rounds = 0, grouped_launches = 0;
+    // lanes of grouped rounds (touched by the loop thread only)
+    Lane lanes[kLanes];
+    cudaEvent_t start = nullptr;   // the lanes' streams wait on it: work queued on st before
+    ChunkPool pool;                // device chunks of the groups' tables
+    long long rounds = 0, grouped_launches = 0, rebuilds = 0, finished = 0;
+    double round_s = 0.0, rebuild_s = 0.0, wait_s = 0.0, run_s = 0.0;
 };
 
 namespace {
@@ -3061,6 +3128,11 @@ void server_finish(ccsd_server* S, ServerReq* r, int state) {
     r->t_done = server_now(S);
     r->state = state;
     S->used -= r->bytes;
+    if (r->t_admit > 0.0) {
+        S->finished += 1;
+        S->wait_s += r->t_admit - r->t_submit;
+        S->run_s += r->t_done - r->t_admit;
+    }
 }
 
 // Grouping key of a solve in its current arithmetic: solves with equal keys share every
@@ -3074,12 +3146,12 @@ std::vector<long long> server_key(const ccsd_ctx* h) {
     return k;
 }
 
-// Builds the groups of this round's solves (reusing those whose membership is
-// unchanged); Ozaki-arithmetic solves go to `solo`.
-int server_groups(ccsd_server* S, const std::vector<ServerReq*>& act,
-                  std::vector<std::pair<Group*, std::vector<ServerReq*>>>& out, std::vector<ServerReq*>& solo) {
+// Builds the groups of a lane's round (reusing those whose membership is unchanged);
+// Ozaki-arithmetic solves go to `solo`.
+int lane_groups(ccsd_server* S, Lane& L, std::vector<std::pair<Group*, std::vector<ServerReq*>>>& out,
+                std::vector<ServerReq*>& solo, long long* builds) {
     std::map<std::vector<long long>, std::vector<ServerReq*>> parts;
-    for (ServerReq* r : act) {
+    for (ServerReq* r : L.active) {
         if (r->h->oz_on) solo.push_back(r);
         else parts[server_key(r->h)].push_back(r);
     }
@@ -3087,28 +3159,38 @@ int server_groups(ccsd_server* S, const std::vector<ServerReq*>& act,
     int rc = 0;
     for (auto& kv : parts) {
         std::vector<ccsd_ctx*> hs;
-        for (ServerReq* r : kv.second) hs.push_back(r->h);
-        auto it = S->groups.find(kv.first);
-        if (it != S->groups.end() && it->second->m == hs) {
+        std::vector<uint64_t> ids;
+        for (ServerReq* r : kv.second) { hs.push_back(r->h); ids.push_back(r->id); }
+        // a group is reused only for exactly the same requests: its device tables hold
+        // their buffers' addresses
+        auto it = L.groups.find(kv.first);
+        if (it != L.groups.end() && it->second->rids == ids && it->second->m == hs) {
             next[kv.first] = std::move(it->second);
         } else {
             std::unique_ptr<Group> G(new (std::nothrow) Group());
             if (!G) return CCSD_ERR_OOM;
+            G->pool = &S->pool;
             G->m = hs;
-            if ((rc = group_build(*G, hs[0]->fp32, {}, nullptr, nullptr, S->st, true))) { group_free(*G); return rc; }
+            G->rids = ids;
+            ++*builds;
+            if ((rc = group_alloc(*G, sizeof(int) * hs.size(), (void**)&G->d_skip)) ||
+                (rc = group_build(*G, hs[0]->fp32, {}, nullptr, G->d_skip, L.st, true))) {
+                group_free(*G);
+                return rc;
+            }
             next[kv.first] = std::move(G);
         }
         out.emplace_back(next[kv.first].get(), kv.second);
     }
-    for (auto& kv : S->groups) if (kv.second) group_free(*kv.second);
-    S->groups = std::move(next);
-    while (S->gst.size() < out.size()) {
+    for (auto& kv : L.groups) if (kv.second) group_free(*kv.second);
+    L.groups = std::move(next);
+    while (L.gst.size() < out.size()) {
         cudaStream_t gs = nullptr;
         cudaEvent_t ge = nullptr;
         if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return CCSD_ERR_CUDA; }
-        S->gst.push_back(gs);
+        L.gst.push_back(gs);
         if (cudaEventCreateWithFlags(&ge, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); return CCSD_ERR_CUDA; }
-        S->gev.push_back(ge);
+        L.gev.push_back(ge);
     }
     return 0;
 }
@@ -3139,15 +3221,109 @@ bool server_complete(ccsd_server* S, ServerReq* r, int rc, int done, double mr) 
     return false;
 }
 
+// Lane of a solve: the order of magnitude of its iteration's flops (four classes).
+int lane_of(const ccsd_config& c) {
+    const double N = (double)c.nk_dims[0] * c.nk_dims[1] * c.nk_dims[2], o = c.nocc, v = c.nvir;
+    const double fl = 8.0 * N * N * N * N * (o * o * v * v * v * v + 2 * o * o * o * v * v * v + 2 * o * o * o * o * v * v);
+    const int l = (int)std::floor(std::log10(std::max(fl, 1.0))) - 9;
+    return std::max(0, std::min(kLanes - 1, l));
+}
+
+// Launches one round of lane L (residuals and norms of every solve; no host wait).
+void lane_launch(ccsd_server* S, Lane& L) {
+    L.grp.clear();
+    L.solo.clear();
+    L.first.clear();
+    L.builds = 0;
+    L.t0 = server_now(S);
+    int grc = lane_groups(S, L, L.grp, L.solo, &L.builds);
+    L.t_built = server_now(S) - L.t0;
+    if (grc) {                                 // groups could not be built: fail the lane's solves
+        for (ServerReq* r : L.active) server_finish(S, r, grc);
+        L.active.clear();
+        L.grp.clear();
+        L.solo.clear();
+        return;
+    }
+    cudaEventRecord(L.fork, L.st);
+    int slot = 0;
+    for (size_t g = 0; g < L.grp.size(); ++g) {
+        Group& G = *L.grp[g].first;
+        cudaStreamWaitEvent(L.gst[g], L.fork, 0);
+        group_residual(G, L.gst[g]);
+        G.norms.fn(L.gst[g]);
+        L.first.push_back(slot);
+        cudaMemcpyAsync(L.h_norms + slot, G.d_norms, sizeof(double) * G.m.size(), cudaMemcpyDeviceToHost, L.gst[g]);
+        slot += (int)G.m.size();
+        cudaEventRecord(L.gev[g], L.gst[g]);
+        cudaStreamWaitEvent(L.st, L.gev[g], 0);
+        S->grouped_launches += group_launches(G, false);
+    }
+    L.began.assign(L.solo.size(), 0);
+    for (size_t i = 0; i < L.solo.size(); ++i) L.began[i] = iter_begin(L.solo[i]->h);
+    cudaEventRecord(L.done, L.st);
+    L.in_flight = true;
+}
+
+// Completes lane L's round once its norms have arrived: each solve's convergence test,
+// one grouped update of the solves that go on, retirements.
+void lane_complete(ccsd_server* S, Lane& L) {
+    L.in_flight = false;
+    int src = cudaEventSynchronize(L.done) == cudaSuccess ? 0 : CCSD_ERR_CUDA;
+    if (src) last_err(cudaGetLastError());
+    std::vector<ServerReq*> keep;
+    for (size_t g = 0; g < L.grp.size(); ++g) {
+        Group& G = *L.grp[g].first;
+        const int rc = src ? src : group_check_err(G, L.st);
+        const size_t nm = L.grp[g].second.size();
+        std::vector<int> frc(nm, 0), done(nm, 0), skip(nm, 1);
+        for (size_t i = 0; i < nm; ++i) {
+            const double mr = L.h_norms[L.first[g] + i];
+            frc[i] = rc ? rc : iter_test(L.grp[g].second[i]->h, mr, &done[i]);
+            skip[i] = (frc[i] || done[i]) ? 1 : 0;
+        }
+        int urc = rc;
+        if (!urc && cudaMemcpyAsync(G.d_skip, skip.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, L.st) != cudaSuccess) {
+            last_err(cudaGetLastError());
+            urc = CCSD_ERR_CUDA;
+        }
+        if (!urc) {
+            G.update.fn(L.st);
+            if (cudaGetLastError() != cudaSuccess) urc = CCSD_ERR_CUDA;
+        }
+        for (size_t i = 0; i < nm; ++i) {
+            ServerReq* r = L.grp[g].second[i];
+            const int code = frc[i] ? frc[i] : (urc && !done[i]) ? urc : 0;
+            if (server_complete(S, r, code, done[i], L.h_norms[L.first[g] + i])) keep.push_back(r);
+        }
+    }
+    for (size_t i = 0; i < L.solo.size(); ++i) {
+        ServerReq* r = L.solo[i];
+        int done = 0, rc = L.began[i];
+        double mr = 0.0;
+        if (!rc) rc = iter_end(r->h, &done, &mr);
+        if (server_complete(S, r, rc, done, mr)) keep.push_back(r);
+    }
+    L.active = keep;
+    L.grp.clear();
+    L.solo.clear();
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->rounds += 1;
+    S->rebuilds += L.builds;
+    S->rebuild_s += L.t_built;
+    S->round_s += server_now(S) - L.t0;
+}
+
 void server_loop(ccsd_server* S) {
     cudaSetDevice(S->device);
     for (;;) {
         std::vector<ServerReq*> admit;
+        bool busy = false;
+        for (const Lane& L : S->lanes) busy = busy || !L.active.empty() || L.in_flight;
         {
             std::unique_lock<std::mutex> lock(S->mu);
-            if (S->active.empty())
-                S->cv.wait(lock, [&] { return S->stop || !S->pending.empty(); });
-            if (S->stop && S->active.empty() && S->pending.empty()) break;
+            if (!busy) S->cv.wait(lock, [&] { return S->stop || !S->pending.empty(); });
+            if (S->stop && !busy && S->pending.empty()) break;
             if (S->stop) {                         // cancel what has not started
                 for (ServerReq* r : S->pending) { r->state = CCSD_ERR_INVALID; r->t_done = server_now(S); }
                 S->pending.clear();
@@ -3167,71 +3343,42 @@ void server_loop(ccsd_server* S) {
             }
         }
         for (ServerReq* r : admit) {
-            int rc = ccsd_create(&r->cfg, &r->in, S->st, &r->h);
+            r->lane = lane_of(r->cfg);
+            int rc = ccsd_create(&r->cfg, &r->in, S->lanes[r->lane].st, &r->h);
             if (rc) { server_finish(S, r, rc); continue; }
             r->polish_left = r->cfg.precision == CCSD_MIXED ? r->cfg.polish_iters : 0;
             if (r->cfg.precision == CCSD_MIXED) r->h->cfg.conv_tol = std::max(r->cfg.mixed_tol, r->cfg.conv_tol);
+            S->lanes[r->lane].active.push_back(r);
             std::lock_guard<std::mutex> lock(S->mu);
             r->t_admit = server_now(S);
             r->state = 1;
             S->active.push_back(r);
         }
-        std::vector<ServerReq*> act;
-        { std::lock_guard<std::mutex> lock(S->mu); act = S->active; }
-        if (act.empty()) continue;
-        // one round: grouped residuals and norms of every group, one copy of the norms
-        std::vector<std::pair<Group*, std::vector<ServerReq*>>> grp;
-        std::vector<ServerReq*> solo;
-        int grc = server_groups(S, act, grp, solo);
-        std::vector<ServerReq*> keep;
-        if (grc) {                                 // groups could not be built: fail the round's solves
-            for (ServerReq* r : act) server_finish(S, r, grc);
-            std::lock_guard<std::mutex> lock(S->mu);
-            S->active.clear();
-            continue;
-        }
-        cudaEventRecord(S->fork, S->st);
-        int slot = 0;
-        std::vector<int> first(grp.size(), 0);
-        for (size_t g = 0; g < grp.size(); ++g) {
-            Group& G = *grp[g].first;
-            cudaStreamWaitEvent(S->gst[g], S->fork, 0);
-            group_residual(G, S->gst[g]);
-            G.norms.fn(S->gst[g]);
-            first[g] = slot;
-            cudaMemcpyAsync(S->h_norms + slot, G.d_norms, sizeof(double) * G.m.size(), cudaMemcpyDeviceToHost, S->gst[g]);
-            slot += (int)G.m.size();
-            cudaEventRecord(S->gev[g], S->gst[g]);
-            cudaStreamWaitEvent(S->st, S->gev[g], 0);
-            S->grouped_launches += group_launches(G, false);
-        }
-        std::vector<int> began(solo.size(), 0);
-        for (size_t i = 0; i < solo.size(); ++i) began[i] = iter_begin(solo[i]->h);
-        int src = cudaStreamSynchronize(S->st) == cudaSuccess ? 0 : CCSD_ERR_CUDA;
-        if (src) last_err(cudaGetLastError());
-        ++S->rounds;
-        for (size_t g = 0; g < grp.size(); ++g) {
-            int rc = src ? src : group_check_err(*grp[g].first, S->st);
-            for (size_t i = 0; i < grp[g].second.size(); ++i) {
-                ServerReq* r = grp[g].second[i];
-                int done = 0;
-                const double mr = S->h_norms[first[g] + i];
-                int frc = rc ? rc : iter_finish(r->h, mr, &done);
-                if (server_complete(S, r, frc, done, mr)) keep.push_back(r);
+        // every lane at its own pace: complete the rounds whose norms have arrived, start
+        // the next round of every idle lane with solves
+        bool progressed = !admit.empty();
+        for (Lane& L : S->lanes) {
+            if (L.in_flight) {
+                const cudaError_t q = cudaEventQuery(L.done);
+                if (q == cudaErrorNotReady) continue;
+                if (q != cudaSuccess) cudaGetLastError();
+                lane_complete(S, L);
+                progressed = true;
             }
+            if (!L.in_flight && !L.active.empty()) { lane_launch(S, L); progressed = true; }
         }
-        for (size_t i = 0; i < solo.size(); ++i) {
-            ServerReq* r = solo[i];
-            int done = 0, rc = began[i];
-            double mr = 0.0;
-            if (!rc) rc = iter_end(r->h, &done, &mr);
-            if (server_complete(S, r, rc, done, mr)) keep.push_back(r);
+        {
+            std::lock_guard<std::mutex> lock(S->mu);
+            std::vector<ServerReq*> act;
+            for (const Lane& L : S->lanes) act.insert(act.end(), L.active.begin(), L.active.end());
+            S->active = act;
         }
-        std::lock_guard<std::mutex> lock(S->mu);
-        S->active = keep;
+        if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
-    for (auto& kv : S->groups) if (kv.second) group_free(*kv.second);
-    S->groups.clear();
+    for (Lane& L : S->lanes) {
+        for (auto& kv : L.groups) if (kv.second) group_free(*kv.second);
+        L.groups.clear();
+    }
 }
 
 }  // namespace
@@ -3566,8 +3713,7 @@ int ccsd_set_precision(ccsd_t h, int precision) {
     else if (precision == CCSD_MIXED && h->cfg.precision == CCSD_MIXED) { h->fp32 = 1; h->oz_on = 0; }
     else if (precision == CCSD_OZAKI && h->has_oz) { h->fp32 = 0; h->oz_on = 1; }
     else return CCSD_ERR_INVALID;
-    h->diis_count = 0;
-    h->diis_next = 0;
+    if (h->d_diis) CK(cudaMemcpyAsync(h->d_diis, &h->diis_init, sizeof(DiisState), cudaMemcpyHostToDevice, h->st));
     return CCSD_OK;
 }
 
@@ -3603,7 +3749,7 @@ int ccsd_set_amplitudes(ccsd_t h, const void* t1, const void* t2) {
     if (!h || !t1 || !t2) return CCSD_ERR_INVALID;
     CK(cudaMemcpyAsync(h->buf[B_T1], t1, (size_t)h->n1 * 16, cudaMemcpyDefault, h->st));
     CK(cudaMemcpyAsync(h->buf[B_T2], t2, (size_t)h->n2 * 16, cudaMemcpyDefault, h->st));
-    h->diis_count = 0; h->diis_next = 0;
+    if (h->d_diis) CK(cudaMemcpyAsync(h->d_diis, &h->diis_init, sizeof(DiisState), cudaMemcpyHostToDevice, h->st));
     CK(cudaStreamSynchronize(h->st));
     return CCSD_OK;
 }
@@ -3811,6 +3957,35 @@ int ccsd_batch_destroy(ccsd_batch_t B) {
     return CCSD_OK;
 }
 
+namespace {
+
+void server_release(ccsd_server* S) {
+    for (Lane& L : S->lanes) {
+        if (L.st) cudaStreamSynchronize(L.st);
+        for (cudaStream_t g : L.gst) cudaStreamDestroy(g);
+        for (cudaEvent_t e : L.gev) cudaEventDestroy(e);
+        if (L.done) cudaEventDestroy(L.done);
+        if (L.fork) cudaEventDestroy(L.fork);
+        if (L.h_norms) cudaFreeHost(L.h_norms);
+        if (L.st) {
+            // the caller's stream waits for everything the lane did
+            cudaEvent_t e = nullptr;
+            if (S->st && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+                cudaEventRecord(e, L.st);
+                cudaStreamWaitEvent(S->st, e, 0);
+                cudaEventDestroy(e);
+            }
+            cudaStreamDestroy(L.st);
+        }
+        L = Lane();
+    }
+    if (S->start) cudaEventDestroy(S->start);
+    if (S->own_stream && S->st) cudaStreamDestroy(S->st);
+    cudaGetLastError();
+}
+
+}  // namespace
+
 int ccsd_server_create(size_t hbm_budget_bytes, int max_slots, void* stream, ccsd_server_t* out) {
     ApiScope api_scope_;
     if (!out || max_slots < 1 || max_slots > 1024 || hbm_budget_bytes == 0) return CCSD_ERR_INVALID;
@@ -3819,21 +3994,22 @@ int ccsd_server_create(size_t hbm_budget_bytes, int max_slots, void* stream, ccs
     S->budget = hbm_budget_bytes;
     S->max_slots = max_slots;
     S->t0 = std::chrono::steady_clock::now();
-    auto fail = [&](int code) {
-        if (S->fork) cudaEventDestroy(S->fork);
-        if (S->h_norms) cudaFreeHost(S->h_norms);
-        if (S->own_stream && S->st) cudaStreamDestroy(S->st);
-        delete S;
-        return code;
-    };
+    auto fail = [&](int code) { server_release(S); delete S; return code; };
     if (cudaGetDevice(&S->device) != cudaSuccess) { cudaGetLastError(); return fail(CCSD_ERR_CUDA); }
     S->st = (cudaStream_t)stream;
     if (!S->st) {
         if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); S->st = nullptr; return fail(CCSD_ERR_CUDA); }
         S->own_stream = true;
     }
-    if (cudaEventCreateWithFlags(&S->fork, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); S->fork = nullptr; return fail(CCSD_ERR_CUDA); }
-    if (cudaMallocHost(&S->h_norms, sizeof(double) * max_slots) != cudaSuccess) { cudaGetLastError(); S->h_norms = nullptr; return fail(CCSD_ERR_OOM); }
+    if (cudaEventCreateWithFlags(&S->start, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); S->start = nullptr; return fail(CCSD_ERR_CUDA); }
+    if (cudaEventRecord(S->start, S->st) != cudaSuccess) { cudaGetLastError(); return fail(CCSD_ERR_CUDA); }
+    for (Lane& L : S->lanes) {
+        if (cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); L.st = nullptr; return fail(CCSD_ERR_CUDA); }
+        if (cudaStreamWaitEvent(L.st, S->start, 0) != cudaSuccess ||
+            cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); return fail(CCSD_ERR_CUDA); }
+        if (cudaMallocHost(&L.h_norms, sizeof(double) * max_slots) != cudaSuccess) { cudaGetLastError(); L.h_norms = nullptr; return fail(CCSD_ERR_OOM); }
+    }
     try {
         S->th = std::thread(server_loop, S);
     } catch (...) {
@@ -3891,6 +4067,20 @@ int ccsd_server_stats(ccsd_server_t S, int* active, int* queued, size_t* admitte
     return CCSD_OK;
 }
 
+int ccsd_server_profile(ccsd_server_t S, long long* rounds, long long* group_builds, double* round_seconds,
+                        double* build_seconds, double* mean_wait_s, double* mean_run_s) {
+    ApiScope api_scope_;
+    if (!S) return CCSD_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (rounds) *rounds = S->rounds;
+    if (group_builds) *group_builds = S->rebuilds;
+    if (round_seconds) *round_seconds = S->round_s;
+    if (build_seconds) *build_seconds = S->rebuild_s;
+    if (mean_wait_s) *mean_wait_s = S->finished ? S->wait_s / (double)S->finished : 0.0;
+    if (mean_run_s) *mean_run_s = S->finished ? S->run_s / (double)S->finished : 0.0;
+    return CCSD_OK;
+}
+
 int ccsd_server_destroy(ccsd_server_t S) {
     ApiScope api_scope_;
     if (!S) return CCSD_ERR_INVALID;
@@ -3901,12 +4091,7 @@ int ccsd_server_destroy(ccsd_server_t S) {
     S->cv.notify_one();
     if (S->th.joinable()) S->th.join();
     for (auto& kv : S->all) delete kv.second;
-    if (S->st) cudaStreamSynchronize(S->st);
-    for (cudaStream_t g : S->gst) cudaStreamDestroy(g);
-    for (cudaEvent_t e : S->gev) cudaEventDestroy(e);
-    if (S->fork) cudaEventDestroy(S->fork);
-    if (S->h_norms) cudaFreeHost(S->h_norms);
-    if (S->own_stream) cudaStreamDestroy(S->st);
+    server_release(S);
     delete S;
     return CCSD_OK;
 }

@@ -28,6 +28,10 @@ __global__ void __launch_bounds__(256) grouped_op_kernel(const Op* __restrict__ 
     op.run(w - prefix[lo], prefix[lo + 1] - prefix[lo]);
 }
 
+// A plain launch of one operation: block b of the grid runs op.run(b, gridDim.x).
+template <class Op>
+__global__ void __launch_bounds__(256) op_kernel(const Op op) { op.run(blockIdx.x, gridDim.x); }
+
 // Zeroes n complex elements (the batched counterpart of a memset step).
 struct ZeroOp {
     double2* p; long long n;

@@ -44,6 +44,13 @@ struct GemmArgs {
     int conjA, conjB, accumulate;
     double alpha_re, alpha_im;
     int tiles_m, tiles_n;
+    // Affine operand tables (set on the host when every entry fits): element (m, k) of A
+    // at offA + a0 + m * rAs + k * cAs, element (k, n) of B at offB + b0 + k * rBs + n * cBs.
+    // Gathers then skip the table loads, and an operand whose K index is contiguous is
+    // staged K-fastest (consecutive threads read consecutive elements).
+    int affA, affB;
+    long long a0, b0;
+    int rAs, cAs, rBs, cBs;
 };
 
 template <typename T> struct Cplx;
@@ -120,13 +127,15 @@ __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long lon
         const float2* Bb32 = g.B32 ? g.B32 + ob : nullptr;
         const double2* Ab = Ab32 ? nullptr : g.A + oa;
         const double2* Bb = Bb32 ? nullptr : g.B + ob;
+        const bool kfA = g.affA && g.cAs == 1, kfB = g.affB && g.rBs == 1;
         for (int k0 = 0; k0 < g.K; k0 += BK) {
             for (int e = tid; e < BM * BK; e += NT) {
-                const int mm = e % BM, kk = e / BM;
+                const int mm = kfA ? e / BK : e % BM, kk = kfA ? e % BK : e / BM;
                 const int m = m0 + mm, k = k0 + kk;
                 V v; v.x = T(0); v.y = T(0);
                 if (m < g.M && k < g.K) {
-                    const long long q = (long long)g.rowA[m] + g.colA[k];
+                    const long long q = g.affA ? g.a0 + (long long)m * g.rAs + (long long)k * g.cAs
+                                               : (long long)g.rowA[m] + g.colA[k];
                     if (Ab32) { const float2 w = __ldg(Ab32 + q); v.x = T(w.x); v.y = T(w.y) * sa; }
                     else { const double2 w = __ldg(Ab + q); v.x = T(w.x); v.y = T(w.y) * sa; }
                 }
@@ -134,11 +143,12 @@ __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long lon
                 if (k3M) sm.As[kk][mm] = v.x + v.y;
             }
             for (int e = tid; e < BN * BK; e += NT) {
-                const int nn = e % BN, kk = e / BN;
+                const int nn = kfB ? e / BK : e % BN, kk = kfB ? e % BK : e / BN;
                 const int n = n0 + nn, k = k0 + kk;
                 V v; v.x = T(0); v.y = T(0);
                 if (n < g.N && k < g.K) {
-                    const long long q = (long long)g.rowB[k] + g.colB[n];
+                    const long long q = g.affB ? g.b0 + (long long)k * g.rBs + (long long)n * g.cBs
+                                               : (long long)g.rowB[k] + g.colB[n];
                     if (Bb32) { const float2 w = __ldg(Bb32 + q); v.x = T(w.x); v.y = T(w.y) * sb; }
                     else { const double2 w = __ldg(Bb + q); v.x = T(w.x); v.y = T(w.y) * sb; }
                 }

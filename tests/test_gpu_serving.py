@@ -128,3 +128,22 @@ def test_served_energies_match_oracle(lib):
         de = abs(e - ref["energies"][-1].real / s.nk)
         print(f"served {s.grid} o{s.nocc} v{s.nvir} precision {p}: |dE| vs oracle {de:.1e}")
         assert de < 1e-7, (s, p, e, de)
+
+
+def test_sequential_requests_rebuild_their_groups(lib):
+    """One slot: each request is admitted only after the previous one retired, so a new
+    request can get the address of a retired handle.  Its round groups must be built
+    for it (they are keyed by request id), and every result equals the solve alone."""
+    from paper_1911_00242_gb300.binding import Server
+    specs = [cs.SynthSpec((2, 1, 1), o, v, 3100 + i) for i, (o, v) in enumerate([(3, 5), (2, 4), (4, 6), (3, 7)])]
+    inps = [cs.generate(s) for s in specs]
+    cfg = dict(conv_tol=1e-8, diis_depth=6, max_iter=100)
+    srv = Server(64 << 30, 1)
+    ids = [srv.submit(s.grid, s.nocc, s.nvir, inp, **cfg) for s, inp in zip(specs, inps)]
+    res = wait_all(srv, ids)
+    srv.close()
+    for s, inp, i in zip(specs, inps, ids):
+        st, e, t, it = res[i]
+        assert st == 2, (s, st)
+        ok, e_alone = standalone(s, inp, **cfg)
+        assert e == e_alone, (s, e, e_alone)
