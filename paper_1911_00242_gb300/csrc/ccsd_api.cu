@@ -1900,6 +1900,9 @@ WprimeListArgs wprime_op(const ccsd_ctx* h, const WListPlan& w) {
     return a;
 }
 
+// The tiled W' kernel serves o <= WPT_OMAX and v <= 128 (its t1 tables in shared memory).
+bool wprime_tiled(const WprimeListArgs& a) { return a.o <= WPT_OMAX && a.v <= 128; }
+
 EmbedArgs embed_op(const ccsd_ctx* h, const EmbedPlan& e) {
     EmbedArgs a = e.a;
     a.src = h->buf[e.src];
@@ -2054,7 +2057,12 @@ void launch_step(ccsd_ctx* h, size_t si) {
                     break;
                 }
                 const WprimeListArgs a = wprime_op(h, h->wlists[s.idx]);
-                wprime_list_kernel<<<row_grid((long long)a.nblk * a.ngrp), 256, 0, h->st>>>(a);
+                if (wprime_tiled(a)) {
+                    const WprimeTileOp op{a, a.nab != a.v * a.v ? 1 : 0};
+                    wprime_tile_kernel<<<row_grid((long long)a.nblk * ((a.v + WPT_A - 1) / WPT_A)), 256, 0, h->st>>>(op);
+                } else {
+                    wprime_list_kernel<<<row_grid((long long)a.nblk * a.ngrp), 256, 0, h->st>>>(a);
+                }
                 ++h->launches;
                 break;
             }
@@ -2491,14 +2499,20 @@ int group_build(Group& G, int fp32, const std::vector<int>& cfgs, double* d_norm
             }
             case 10: {
                 std::vector<WprimeListArgs> ops;
-                std::vector<long long> blocks;
+                std::vector<WprimeTileOp> tops;
+                std::vector<long long> blocks, tblocks;
+                bool tiled = true;
                 for (ccsd_ctx* h : G.m) {
                     const WListPlan& w = h->wlists[h->seq[si].idx];
                     if (w.oz) { refuse("grouped launches run split-TF32 and FP64 steps only"); return CCSD_ERR_INVALID; }
-                    ops.push_back(wprime_op(h, w));
-                    blocks.push_back(row_blocks((long long)w.a.nblk * w.a.ngrp));
+                    const WprimeListArgs a = wprime_op(h, w);
+                    ops.push_back(a);
+                    blocks.push_back(row_blocks((long long)a.nblk * a.ngrp));
+                    tops.push_back(WprimeTileOp{a, a.nab != a.v * a.v ? 1 : 0});
+                    tblocks.push_back(row_blocks((long long)a.nblk * ((a.v + WPT_A - 1) / WPT_A)));
+                    tiled = tiled && wprime_tiled(a);
                 }
-                if ((rc = make_grouped(G, ops, blocks, st, gl))) return rc;
+                if ((rc = tiled ? make_grouped(G, tops, tblocks, st, gl) : make_grouped(G, ops, blocks, st, gl))) return rc;
                 break;
             }
             case 6: {
@@ -3058,6 +3072,7 @@ struct Lane {
     std::vector<cudaStream_t> gst; // one stream per group of the round
     std::vector<cudaEvent_t> gev;
     std::vector<ServerReq*> active;
+    std::vector<ServerReq*> incoming;  // admitted while a round was in flight: join the next one
     std::map<std::vector<long long>, std::unique_ptr<Group>> groups;
     // the round in flight
     bool in_flight = false;
@@ -3304,6 +3319,8 @@ void lane_complete(ccsd_server* S, Lane& L) {
         if (!rc) rc = iter_end(r->h, &done, &mr);
         if (server_complete(S, r, rc, done, mr)) keep.push_back(r);
     }
+    keep.insert(keep.end(), L.incoming.begin(), L.incoming.end());
+    L.incoming.clear();
     L.active = keep;
     L.grp.clear();
     L.solo.clear();
@@ -3319,7 +3336,7 @@ void server_loop(ccsd_server* S) {
     for (;;) {
         std::vector<ServerReq*> admit;
         bool busy = false;
-        for (const Lane& L : S->lanes) busy = busy || !L.active.empty() || L.in_flight;
+        for (const Lane& L : S->lanes) busy = busy || !L.active.empty() || !L.incoming.empty() || L.in_flight;
         {
             std::unique_lock<std::mutex> lock(S->mu);
             if (!busy) S->cv.wait(lock, [&] { return S->stop || !S->pending.empty(); });
@@ -3348,7 +3365,8 @@ void server_loop(ccsd_server* S) {
             if (rc) { server_finish(S, r, rc); continue; }
             r->polish_left = r->cfg.precision == CCSD_MIXED ? r->cfg.polish_iters : 0;
             if (r->cfg.precision == CCSD_MIXED) r->h->cfg.conv_tol = std::max(r->cfg.mixed_tol, r->cfg.conv_tol);
-            S->lanes[r->lane].active.push_back(r);
+            Lane& L = S->lanes[r->lane];
+            (L.in_flight ? L.incoming : L.active).push_back(r);
             std::lock_guard<std::mutex> lock(S->mu);
             r->t_admit = server_now(S);
             r->state = 1;
@@ -3370,7 +3388,10 @@ void server_loop(ccsd_server* S) {
         {
             std::lock_guard<std::mutex> lock(S->mu);
             std::vector<ServerReq*> act;
-            for (const Lane& L : S->lanes) act.insert(act.end(), L.active.begin(), L.active.end());
+            for (const Lane& L : S->lanes) {
+                act.insert(act.end(), L.active.begin(), L.active.end());
+                act.insert(act.end(), L.incoming.begin(), L.incoming.end());
+            }
             S->active = act;
         }
         if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(50));

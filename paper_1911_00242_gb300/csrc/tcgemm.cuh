@@ -611,4 +611,113 @@ __device__ inline void WprimeListArgs::run(long long vb, long long nvb) const
 
 __global__ void wprime_list_kernel(const WprimeListArgs w) { w.run(blockIdx.x, gridDim.x); }
 
+// The same W' rows, tiled for reuse: one unit is a tile of WPT_A consecutive a of one
+// block and all their (a, b) pairs.  Per (e, f) column a thread keeps the ovvv rows of
+// its a's (o values each) in registers and loads the ovvv row of every b once for the
+// whole tile, where the grouped form above loads it once per (a, b) pair; t1 sits in
+// shared memory.  Output rows are the pairs' positions in the list (all pairs, or
+// a < b for the diagonal blocks ka = kb, both ordered by a then b).  o <= WPT_OMAX.
+constexpr int WPT_A = 2;
+constexpr int WPT_OMAX = 8;
+
+struct WprimeTileOp {
+    WprimeListArgs w;
+    int lt;                   // the pair list holds a < b only (diagonal blocks)
+    __device__ void run(long long vb, long long nvb) const {
+        const int N = w.N, o = w.o, v = w.v;
+        const long long vv = (long long)v * v, v4 = vv * vv, ov3 = (long long)o * v * vv;
+        const int kh = w.Kpad / 2;
+        const int ntile = (v + WPT_A - 1) / WPT_A;
+        const long long units = (long long)w.nblk * ntile;
+        __shared__ float2 tka[WPT_A * WPT_OMAX];                 // t_r^a(ka) of the tile's a
+        __shared__ float2 tkb[WPT_OMAX * 128];                   // t_r^b(kb), b < 128
+        for (long long unit = vb; unit < units; unit += nvb) {
+            const long long bi = unit / ntile;
+            const int a0 = (int)(unit - bi * ntile) * WPT_A;
+            const int ka = w.blk[3 * bi], kb = w.blk[3 * bi + 1], ke = w.blk[3 * bi + 2];
+            const long long blk_ab = ((long long)ka * N + kb) * N + ke;
+            const long long blk_ba = ((long long)kb * N + ka) * N + ke;
+            __syncthreads();                                       // the previous unit's reads are done
+            // every entry the unrolled r loops read is written: r >= o reads as zero
+            for (int q = threadIdx.x; q < WPT_A * WPT_OMAX; q += blockDim.x) {
+                const int ta = q / WPT_OMAX, r = q % WPT_OMAX;
+                tka[q] = (r < o && a0 + ta < v) ? w.t1[(long long)ka * o * v + (long long)r * v + a0 + ta]
+                                                : make_float2(0.f, 0.f);
+            }
+            for (int q = threadIdx.x; q < WPT_OMAX * v; q += blockDim.x) {
+                const int r = q % WPT_OMAX, b = q / WPT_OMAX;
+                tkb[r * 128 + b] = r < o ? w.t1[(long long)kb * o * v + (long long)r * v + b] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            // first pair index of each a of the tile in the list
+            int rowa[WPT_A];
+#pragma unroll
+            for (int ta = 0; ta < WPT_A; ++ta) {
+                const int a = a0 + ta;
+                rowa[ta] = lt ? a * v - a * (a + 1) / 2 - a - 1 : a * v;    // index of (a, b) = rowa + b
+            }
+            for (int ei = threadIdx.x; ei < kh; ei += blockDim.x) {
+                if (ei >= w.nef) {                                 // padding columns of every row of the tile
+                    for (int ta = 0; ta < WPT_A; ++ta) {
+                        const int a = a0 + ta;
+                        if (a >= v) break;
+                        for (int b = lt ? a + 1 : 0; b < v; ++b) {
+                            const long long o0 = (bi * 2 * w.nab + 2LL * (rowa[ta] + b)) * (long long)w.Kpad + 2LL * ei;
+                            const long long o1 = o0 + w.Kpad;
+                            *(float2*)(w.big + o0) = make_float2(0.f, 0.f);
+                            *(float2*)(w.big + o1) = make_float2(0.f, 0.f);
+                            *(float2*)(w.small + o0) = make_float2(0.f, 0.f);
+                            *(float2*)(w.small + o1) = make_float2(0.f, 0.f);
+                        }
+                    }
+                    continue;
+                }
+                const int ef = w.efl[ei];
+                float2 P[WPT_A][WPT_OMAX];                         // ovvv[kb,ka,ke](r, a, ef)
+#pragma unroll
+                for (int ta = 0; ta < WPT_A; ++ta)
+#pragma unroll
+                    for (int r = 0; r < WPT_OMAX; ++r)
+                        P[ta][r] = (r < o && a0 + ta < v)
+                                       ? w.ovvv[blk_ba * ov3 + (long long)r * v * vv + (long long)(a0 + ta) * vv + ef]
+                                       : make_float2(0.f, 0.f);
+                for (int b = lt ? a0 + 1 : 0; b < v; ++b) {
+                    float2 Q[WPT_OMAX];                            // ovvv[ka,kb,ke](r, b, ef)
+#pragma unroll
+                    for (int r = 0; r < WPT_OMAX; ++r)
+                        Q[r] = r < o ? w.ovvv[blk_ab * ov3 + (long long)r * v * vv + (long long)b * vv + ef]
+                                     : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int ta = 0; ta < WPT_A; ++ta) {
+                        const int a = a0 + ta;
+                        if (a >= v || (lt && a >= b)) continue;
+                        // + t_r^b(kb) ovvv[kb,ka,ke](r,a,e,f) - t_r^a(ka) ovvv[ka,kb,ke](r,b,e,f)
+                        float sr = 0.f, si = 0.f;
+#pragma unroll
+                        for (int r = 0; r < WPT_OMAX; ++r) {
+                            const float2 tb = tkb[r * 128 + b], t_a = tka[ta * WPT_OMAX + r];
+                            sr = fmaf(tb.x, P[ta][r].x, fmaf(-tb.y, P[ta][r].y, sr));
+                            si = fmaf(tb.x, P[ta][r].y, fmaf(tb.y, P[ta][r].x, si));
+                            sr = fmaf(-t_a.x, Q[r].x, fmaf(t_a.y, Q[r].y, sr));
+                            si = fmaf(-t_a.x, Q[r].y, fmaf(-t_a.y, Q[r].x, si));
+                        }
+                        const float2 gv = w.vvvv[blk_ab * v4 + ((long long)a * v + b) * vv + ef];
+                        float rb, rs, ib, is;
+                        split_tf32f(gv.x + sr, rb, rs);
+                        split_tf32f(gv.y + si, ib, is);
+                        const long long o0 = (bi * 2 * w.nab + 2LL * (rowa[ta] + b)) * (long long)w.Kpad + 2LL * ei;
+                        const long long o1 = o0 + w.Kpad;
+                        *(float2*)(w.big + o0) = make_float2(rb, -ib);
+                        *(float2*)(w.big + o1) = make_float2(ib, rb);
+                        *(float2*)(w.small + o0) = make_float2(rs, -is);
+                        *(float2*)(w.small + o1) = make_float2(is, rs);
+                    }
+                }
+            }
+        }
+    }
+};
+__global__ void __launch_bounds__(256, 2) wprime_tile_kernel(const WprimeTileOp op) { op.run(blockIdx.x, gridDim.x); }
+
+
 }  // namespace ccsdk

@@ -93,10 +93,9 @@ def test_mixed_batch_complex64_members(lib):
 
 
 def test_batch_diis_members_match_standalone(lib):
-    """DIIS(6) inside the batch (device-resident history, Gram matrix and Pulay solve)
-    against each member run alone with the host-driven DIIS: energies after 6
-    extrapolated updates within 1e-11 Ha (the coefficient solve may round in a
-    different order on the device)."""
+    """DIIS(6) inside the batch (grouped launches of the device-resident history, Gram
+    matrix and Pulay solve) against each member run alone: energies after 6
+    extrapolated updates within 1e-11 Ha."""
     from paper_1911_00242_gb300.binding import BatchSolver, Solver
     specs = SPECS[:4]
     inps = [cs.generate(s) for s in specs]
