@@ -601,9 +601,9 @@ int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M,
         z.rowC = rowC.empty() ? nullptr : upload(al, rowC, h->st);
         if (al.err) return al.err;
         z.nbatch = nbatch;
-        // too few tiles for the 152 SMs: split each tile's (chunk, diagonal) units over CTAs
+        // too few tiles for the 152 SMs: split each tile's (chunk, window) units over CTAs
         const long long tiles = (long long)z.tiles_m * z.tiles_n * nbatch;
-        const int units = nchunk * h->oz_slices;
+        const int units = nchunk * oz_nwin(z.kstages, h->oz_slices);
         z.nsplit = 1;
         if (tiles < 2 * 152) z.nsplit = (int)std::min<long long>(std::min(units, 16), (2 * 152 + tiles - 1) / tiles);
         t.blocks = (int)(tiles * z.nsplit);

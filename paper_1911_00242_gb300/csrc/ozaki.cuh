@@ -20,26 +20,31 @@
 // Products.  With row scales 2^Ea (A') and 2^Eb (B'),
 //   (A' B'^T)_mn = 2^{Ea_m + Eb_n} sum_{p,q} 2^{-7(p+q+2)} (V_p W_q^T)_mn.
 // The pairs with p + q <= s - 1 are formed (s (s + 1) / 2 of them); the others
-// lie below 2^{-7(s+1)} of 2^{Ea+Eb} per product.  A TMEM accumulator sums one
-// chunk's products of pairs with the same d = p + q over at most oz_win(d) stages
-// (d = 0: 1024 products of magnitude <= 2^14; d > 0: every pair has a slice with
-// |v| <= 64, so 2048 products of magnitude <= 2^13), so every partial sum is an
-// integer of magnitude <= 2^24, which FP32 holds exactly: the tensor-core
-// accumulation is exact.  Each such window is multiplied by
-// its power of two (exact) and added into (hi, lo) with TwoSum (Knuth), so the
-// only roundings after the split are those of the double-float sum.  The window
-// factors are taken relative to the largest row scales of the output's chunks
-// (RA for its A' rows, RB for its B' rows), so (hi, lo) stay near unit magnitude
-// whatever the data's range; the epilogue multiplies by RA RB in FP64.
+// lie below 2^{-7(s+1)} of 2^{Ea+Eb} per product.  Diagonal d = p + q has its own
+// TMEM accumulator, which sums the products of all its pairs over one window of
+// oz_kwin(s) K slices of one chunk; the window is short enough that every partial
+// sum is an integer of magnitude <= 2^24, which FP32 holds exactly: the tensor-core
+// accumulation is exact.  Each window sum is multiplied by its power of two (exact)
+// and added into (hi, lo) with TwoSum (Knuth), so the only roundings after the
+// split are those of the double-float sum.  The window factors are taken relative
+// to the largest row scales of the output's chunks (RA for its A' rows, RB for its
+// B' rows), so (hi, lo) stay near unit magnitude whatever the data's range; the
+// epilogue multiplies by RA RB in FP64.
 //
-// One CTA computes a 128 x 128 tile, 18 warps: warp 0 / lane 0 issues TMA loads
-// into a 6-stage ring (32 KiB per stage: 64 BF16 of K for 128 rows of A' and of
-// B'), warp 1 / lane 0 issues 4 MMAs (kind::f16, BF16 inputs, K = 16) per stage
-// into TMEM buffer (window & 1), warps 2..17 promote windows and run the epilogue
-// (32 columns of one TMEM lane quarter each; hi and lo live in TMEM as well, so a
-// thread holds only 8 columns at a time).  A launch with too few tiles for the SMs
-// splits each tile's (chunk, diagonal) units over several CTAs, whose partials
-// oz_split_reduce adds in a fixed order.
+// One CTA computes a 128 x 64 tile (128 rows of A', 64 rows of B').  A stage is one
+// K slice of 64: all s slices of the B tile (s x 8 KiB, in one of two B slots) and,
+// one after another, the s slices of the A tile (16 KiB each, in a ring of A slots).
+// Slice p of A meets slices q = 0 .. s-1-p of B, which lie side by side in the B slot,
+// so one MMA of N = 64 n covers n consecutive q and writes the n adjacent diagonal
+// accumulators p + q (TMEM columns 64 d).  Each staged byte thus feeds s / 2 products
+// on average (one in a layout that stages one pair at a time), which keeps the shared
+// memory's bandwidth, shared by the copies and the MMA operand reads, from bounding
+// the tensor pipe.  Warp 0 / lane 0 issues the TMA loads, warp 1 / lane 0 the MMAs;
+// warps 2..17 promote each diagonal's window as soon as its last product is in
+// (diagonal p is complete once slice p of A is done in the window's last K slice) and
+// keep (hi, lo) of 16 columns of one TMEM lane quarter in registers.  A launch with
+// too few tiles for the SMs splits each tile's (chunk, window) units over several
+// CTAs, whose partials oz_split_reduce adds in a fixed order.
 // Every mbarrier wait is bounded, as in the split-TF32 kernel.
 #pragma once
 #include "tcgemm.cuh"
@@ -49,22 +54,27 @@
 
 namespace ccsdk {
 
-constexpr int OZ_BM = 128;
-constexpr int OZ_BN = 128;
-constexpr int OZ_BK = 64;                                  // BF16 elements per stage row (128 B)
-static_assert(OZ_BK == 4 * 16, "the MMA issuer issues four K = 16 MMAs per stage");
-constexpr int OZ_STAGES = 6;
-constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;              // 16 KiB
-constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;              // 16 KiB
-constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;    // 32 KiB
-constexpr int OZ_LO_COL = 2 * OZ_BN;                       // TMEM columns of the lo accumulator
-constexpr int OZ_HI_COL = 3 * OZ_BN;                       // TMEM columns of the hi accumulator
-constexpr int OZ_TMEM_COLS = 4 * OZ_BN;                    // two windows, lo, hi
-constexpr int OZ_ACC_WARPS = 16;                           // four per TMEM lane quarter, 32 columns each
-constexpr int OZ_COLS = OZ_BN / (OZ_ACC_WARPS / 4);        // columns per accumulator thread
+constexpr int OZ_BM = 128;                                 // A' rows per tile (TMEM lanes)
+constexpr int OZ_BN = 64;                                  // B' rows per tile (TMEM columns per diagonal)
+constexpr int OZ_BK = 64;                                  // BF16 elements per K slice row (128 B)
+static_assert(OZ_BK == 4 * 16, "the MMA issuer issues four K = 16 MMAs per K slice");
+constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;              // 16 KiB: one slice of the A tile
+constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;              // 8 KiB: one slice of the B tile
+constexpr int OZ_RING_BYTES = 2 * OZ_MAX_SLICES * OZ_B_BYTES + 5 * OZ_A_BYTES;   // 208 KiB
+constexpr int OZ_A_SLOTS = 12;                             // most A slots (s = 1); s = 7: 6
+// A slices move in pairs of consecutive tiles of the load sequence (one full and one
+// empty barrier per pair), which halves the issuer's waits and commits.
+static_assert(OZ_MAX_SLICES * OZ_BN <= 512, "one TMEM accumulator per diagonal");
+constexpr int OZ_TMEM_COLS = 512;
+constexpr int OZ_ACC_WARPS = 16;                           // four per TMEM lane quarter
+constexpr int OZ_COLS = OZ_BN / (OZ_ACC_WARPS / 4);        // 16 columns per accumulator thread
+static_assert(OZ_COLS % 8 == 0 && OZ_COLS <= 32, "columns per thread: 8-column TMEM loads, one lane each");
 constexpr int OZ_THREADS = 64 + 32 * OZ_ACC_WARPS;
+constexpr int OZ_BAR_BYTES = 512;                          // mbarriers, TMEM address, abort flag
 constexpr int OZ_REF_BYTES = OZ_ACC_WARPS * 96 * 4;       // per accumulator warp: RB, 1 / RB, chunk column factors
-constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256 + OZ_REF_BYTES;
+constexpr int OZ_SMEM_BYTES = OZ_RING_BYTES + 1024 + OZ_BAR_BYTES + OZ_REF_BYTES;
+static_assert((4 + OZ_A_SLOTS + 2 * OZ_MAX_SLICES + 1) * 8 + 8 <= OZ_BAR_BYTES, "barrier area");
+static_assert(2 * OZ_COLS * (OZ_ACC_WARPS * 32) * 4 <= OZ_RING_BYTES, "epilogue park area");
 
 struct OzArgs {
     const int* rowA;          // [nbatch * nchunk] row of A' (within a slice plane) where chunk c of batch b starts
@@ -86,16 +96,16 @@ struct OzArgs {
     const long long* offC2;   // antisymmetric mirror (subtracted) or null
     const int* colC2;
     long long spin_limit;
-    int skip_stage;           // failure-detection self-test: this stage is never loaded (-1: none)
+    int skip_stage;           // failure-detection self-test: this pair of A-slice loads is never issued (-1: none)
     int overwrite;            // 1: C = alpha c (and -alpha c at the mirror) instead of C += ...
     int nbatch;
-    int nsplit;               // > 1: the (chunk, diagonal) units of a tile are split over nsplit CTAs
+    int nsplit;               // > 1: the (chunk, window) units of a tile are split over nsplit CTAs
     double2* work;            // nsplit > 1: partials [nsplit][nbatch][M][Nr / 2], summed by oz_split_reduce
 };
 
-// Instruction descriptor: D = F32, A = B = BF16 (kind::f16), both K-major, N = 128, M = 128.
-__host__ __device__ constexpr uint32_t oz_idesc_bf16() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
+// Instruction descriptor: D = F32, A = B = BF16 (kind::f16), both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t oz_idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
 }
 
 __device__ __forceinline__ void oz_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
@@ -103,6 +113,20 @@ __device__ __forceinline__ void oz_mma(uint32_t tmem_d, uint64_t adesc, uint64_t
                  "setp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
                  :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc) : "memory");
+}
+
+// The four K = 16 steps (32 bytes each) of one 64-wide K slice into one accumulator:
+// the first accumulates iff acc != 0, the others always.
+__device__ __forceinline__ void oz_mma4(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p, t;\n\t"
+                 "setp.ne.b32 p, %4, 0;\n\t"
+                 "setp.eq.b32 t, %4, %4;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %6, %3, t;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %7, %8, %3, t;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %9, %10, %3, t;\n\t}"
+                 :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc), "l"(adesc + 2), "l"(bdesc + 2),
+                    "l"(adesc + 4), "l"(bdesc + 4), "l"(adesc + 6), "l"(bdesc + 6) : "memory");
 }
 
 // 8 consecutive TMEM columns of this warp's lane quarter <-> registers (32x32b.x8).
@@ -125,18 +149,78 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
     lo += e;
 }
 
+// The MMAs of one K slice (the issuer of oz_gemm_kernel): for each A slice p (tile ja of
+// the load sequence, half ja & 1 of pair slot ps; a pair is waited for at its first tile
+// and released by one commit after its last), slices q0 .. q0+n-1 of B (adjacent in the
+// B slot at descriptor dbs) in MMAs of N = 64 n into the accumulators of diagonals
+// p + q0 .. (adjacent TMEM columns).  The first K step of p = 0 in a window's first K
+// slice overwrites every diagonal, after the previous window's promotion of it; all
+// later steps accumulate.  In the window's last K slice, diagonal p is complete after
+// slice p of A, and its acc_full barrier is committed.  SC > 0: the slice count is a
+// compile-time constant and the loops unroll; SC = 0: S at run time.  Returns 0, or the
+// error code of a wait that gave up.
+template <int SC>
+__device__ __forceinline__ int oz_issue_slice(int S_rt, uint32_t tmem, uint64_t da0, uint64_t dbs, uint32_t fA0,
+                                              uint32_t eA0, uint32_t accF0, uint32_t accE0, int nP, int totalA,
+                                              int& ja, int& ps, uint32_t& pph, bool wfirst, bool wlast, int w,
+                                              volatile int* abort_flag, long long spin_limit)
+{
+    const int S = SC > 0 ? SC : S_rt;
+    const uint32_t id4 = oz_idesc_bf16(4 * OZ_BN);
+#pragma unroll
+    for (int p = 0; p < (SC > 0 ? SC : OZ_MAX_SLICES); ++p) {
+        if (SC == 0 && p >= S) break;
+        const int h = ja & 1;
+        if (h == 0) {
+            if (!mbar_wait(fA0 + 8 * ps, pph, abort_flag, spin_limit)) return 2;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        const uint64_t da = da0 + (uint64_t)((2 * ps + h) * (OZ_A_BYTES >> 4));
+        const bool fresh = wfirst && p == 0;
+#pragma unroll
+        for (int q0 = 0; q0 < (SC > 0 ? SC : OZ_MAX_SLICES); q0 += 4) {
+            if (q0 >= S - p) break;
+            const int n = min(4, S - p - q0);
+            if (fresh && w > 0) {
+                // diagonals q0 .. q0+n-1 of the previous window have been promoted
+                for (int d = q0; d < q0 + n; ++d)
+                    if (!mbar_wait(accE0 + 8 * d, (uint32_t)((w - 1) & 1), abort_flag, spin_limit)) return 4;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            const uint64_t db = dbs + (uint64_t)(q0 * (OZ_B_BYTES >> 4));
+            const uint32_t dst = tmem + (uint32_t)(OZ_BN * (p + q0));
+            const uint32_t idesc = n == 4 ? id4 : oz_idesc_bf16(OZ_BN * n);
+            oz_mma4(dst, da, db, idesc, fresh ? 0u : 1u);
+        }
+        if (h == 1 || ja + 1 == totalA) {
+            tc_commit(eA0 + 8 * ps);
+            if (++ps == nP) { ps = 0; pph ^= 1u; }
+        }
+        ++ja;
+        if (wlast) tc_commit(accF0 + 8 * p);
+    }
+    return 0;
+}
+
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const OzArgs g)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* stA = smem;                                        // [STAGES][16 KiB]
-    uint8_t* stB = smem + OZ_STAGES * OZ_A_BYTES;               // [STAGES][16 KiB]
-    uint64_t* bars = (uint64_t*)(smem + OZ_STAGES * OZ_STAGE_BYTES);
-    uint64_t* acc_full = bars + 2 * OZ_STAGES;
-    uint64_t* acc_empty = bars + 2 * OZ_STAGES + 2;
-    uint64_t* drain = bars + 2 * OZ_STAGES + 4;
-    volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 2 * OZ_STAGES + 5);
+    const int S = g.slices;
+    const int bslot = S * OZ_B_BYTES;                           // all slices of one B tile
+    const int nA = min(OZ_A_SLOTS, (OZ_RING_BYTES - 2 * bslot) / OZ_A_BYTES) & ~1;   // whole pairs
+    uint8_t* stB = smem;                                        // [2][S][8 KiB]
+    uint8_t* stA = smem + 2 * bslot;                            // [nA][16 KiB]
+    const int nP = nA / 2;                                      // A pair slots
+    uint64_t* fullB = (uint64_t*)(smem + OZ_RING_BYTES);
+    uint64_t* emptyB = fullB + 2;
+    uint64_t* fullA = fullB + 4;                                // per pair slot
+    uint64_t* emptyA = fullA + OZ_A_SLOTS / 2;
+    uint64_t* acc_full = emptyA + OZ_A_SLOTS / 2;               // per diagonal
+    uint64_t* acc_empty = acc_full + OZ_MAX_SLICES;
+    uint64_t* drain = acc_empty + OZ_MAX_SLICES;
+    volatile uint32_t* tmem_slot = (volatile uint32_t*)(drain + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -148,13 +232,17 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     const int n0 = (tile / g.tiles_m) * OZ_BN;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < OZ_STAGES; ++s) {
-            mbar_init(smem_u32(&bars[s]), 1);
-            mbar_init(smem_u32(&bars[OZ_STAGES + s]), 1);
-        }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(smem_u32(&acc_full[i]), 1);
-            mbar_init(smem_u32(&acc_empty[i]), OZ_ACC_WARPS);
+            mbar_init(smem_u32(&fullB[i]), 1);
+            mbar_init(smem_u32(&emptyB[i]), 1);
+        }
+        for (int i = 0; i < OZ_A_SLOTS / 2; ++i) {
+            mbar_init(smem_u32(&fullA[i]), 1);
+            mbar_init(smem_u32(&emptyA[i]), 1);
+        }
+        for (int d = 0; d < OZ_MAX_SLICES; ++d) {
+            mbar_init(smem_u32(&acc_full[d]), 1);
+            mbar_init(smem_u32(&acc_empty[d]), OZ_ACC_WARPS);
         }
         mbar_init(smem_u32(drain), 1);
         *abort_flag = 0;
@@ -170,99 +258,113 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    const int S = g.slices;
     const int nch = g.nchunk_b ? g.nchunk_b[b] : g.nchunk;
+    const int W = oz_kwin(S), nw = oz_nwin(g.kstages, S);
     int u0, u1;
     oz_unit_range(nch, S, g.kstages, g.nsplit, split, u0, u1);
-    int issued = 0;
+    int nks = 0;                                                // K slices of this CTA
+    for (int u = u0; u < u1; ++u) {
+        const int k0 = (u % nw) * W;
+        nks += min(k0 + W, g.kstages) - k0;
+    }
+    const int totalA = nks * S;                                 // A tiles of this CTA
+    int issuedP = 0, issuedB = 0;                               // pairs / B slots loaded (warp 0 / lane 0)
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- producer: TMA loads.  The ring position (st, ph) advances
-            // incrementally: this single thread's issue rate bounds the pipeline.
+            // ---------------- producer: per K slice, the B tile's S slices into B slot
+            // (jb & 1), then the A tile's slices p = 0 .. S-1, pairs of consecutive tiles
+            // (ja, ja + 1) into pair slot ps with one barrier.  Slot indices and phases
+            // advance incrementally (no divisions in the loop).
             const uint32_t sA0 = smem_u32(stA), sB0 = smem_u32(stB);
-            const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[OZ_STAGES]);
-            int s = 0, st = 0;
-            uint32_t ph = 0;
-            bool run = true;
+            const uint32_t eA0 = smem_u32(&emptyA[0]), fA0 = smem_u32(&fullA[0]);
+            int ja = 0, jb = 0, ps = 0;
+            uint32_t pph = 0;
+            bool skip = false, run = true;
+            int open_x = 0, open_y = 0;                         // first tile of a half-loaded pair
             for (int u = u0; u < u1 && run; ++u) {
-                const int c = u / S, d = u - c * S;
+                const int c = u / nw, wi = u - c * nw;
                 const int ra = g.rowA[b * g.nchunk + c] + m0, rb = g.rowB[b * g.nchunk + c] + n0;
-                for (int p = 0; p <= d && run; ++p) {
-                    const int ya = p * g.rowsA + ra, yb = (d - p) * g.rowsB + rb;
-                    for (int kst = 0; kst < g.kstages; ++kst) {
-                        if (!mbar_wait(empty0 + 8 * st, ph ^ 1u, abort_flag, g.spin_limit)) {
-                            atomicCAS(g.err, 0, 1);
-                            *abort_flag = 1;
-                            run = false;
-                            break;
+                const int k1 = min((wi + 1) * W, g.kstages);
+                for (int kst = wi * W; kst < k1 && run; ++kst) {
+                    const int bs = jb & 1;
+                    if (!mbar_wait(smem_u32(&emptyB[bs]), (uint32_t)((jb >> 1) & 1) ^ 1u, abort_flag, g.spin_limit)) {
+                        run = false;
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&fullB[bs]);
+                    mbar_expect_tx(fb, (uint32_t)bslot);
+                    for (int q = 0; q < S; ++q)
+                        tma_load_2d(sB0 + bs * bslot + q * OZ_B_BYTES, &mapB, kst * OZ_BK, q * g.rowsB + rb, fb);
+                    issuedB = ++jb;
+                    for (int p = 0; p < S; ++p) {
+                        const int h = ja & 1;
+                        if (h == 0) {
+                            if (!mbar_wait(eA0 + 8 * ps, pph ^ 1u, abort_flag, g.spin_limit)) {
+                                run = false;
+                                break;
+                            }
+                            skip = (ja >> 1) == g.skip_stage;  // a skipped pair is never loaded
+                            if (!skip) {
+                                mbar_expect_tx(fA0 + 8 * ps, (ja + 1 < totalA ? 2 : 1) * OZ_A_BYTES);
+                                issuedP = (ja >> 1) + 1;
+                            }
+                            open_x = kst * OZ_BK;
+                            open_y = p * g.rowsA + ra;
                         }
-                        if (s != g.skip_stage) {           // a skipped stage is never completed
-                            const uint32_t full = full0 + 8 * st;
-                            mbar_expect_tx(full, OZ_STAGE_BYTES);
-                            tma_load_2d(sA0 + st * OZ_A_BYTES, &mapA, kst * OZ_BK, ya, full);
-                            tma_load_2d(sB0 + st * OZ_B_BYTES, &mapB, kst * OZ_BK, yb, full);
-                            issued = s + 1;
+                        if (!skip)
+                            tma_load_2d(sA0 + (2 * ps + h) * OZ_A_BYTES, &mapA, kst * OZ_BK, p * g.rowsA + ra, fA0 + 8 * ps);
+                        ++ja;
+                        if (h == 1 || ja == totalA) {
+                            if (++ps == nP) { ps = 0; pph ^= 1u; }
                         }
-                        ++s;
-                        if (++st == OZ_STAGES) { st = 0; ph ^= 1u; }
                     }
                 }
+            }
+            if (!run) {
+                atomicCAS(g.err, 0, 1);
+                *abort_flag = 1;
+                // a pair left with one tile loaded gets its second load (the first tile again),
+                // so that its barrier completes and teardown can wait for it
+                if ((ja & 1) && ja < totalA && !skip)
+                    tma_load_2d(sA0 + (2 * ps + 1) * OZ_A_BYTES, &mapA, open_x, open_y, fA0 + 8 * ps);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---------------- MMA issuer: window w accumulates in TMEM buffer w & 1.  The
-            // descriptors of stage st are the stage-0 ones plus the stage offset (their
-            // start-address field is the shared address / 16, below 2^14).
-            const uint32_t idesc = oz_idesc_bf16();
+            // ---------------- MMA issuer: per K slice, the B slot, then oz_issue_slice (the
+            // slice count 7, the default, compiled as a constant).  The descriptors are the
+            // slot-0 ones plus the slot offset (their start-address field is the shared
+            // address / 16, below 2^14); slots and phases advance incrementally.
             const uint64_t da0 = smem_desc_sw128(smem_u32(stA)), db0 = smem_desc_sw128(smem_u32(stB));
-            const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[OZ_STAGES]);
-            int w = 0, st = 0;
-            uint32_t ph = 0;
-            bool run = true;
-            for (int u = u0; u < u1 && run; ++u) {
-                const int d = u % S;
-                const int glen = (d + 1) * g.kstages;          // stages of this unit
-                const int win = oz_win(d);
-                int jw = 0;                                     // stage within the window
-                for (int j = 0; j < glen; ++j) {
-                    const bool first = jw == 0;
-                    const bool last = jw + 1 == win || j + 1 == glen;
-                    const int buf = w & 1;
-                    if (first && w >= 2) {
-                        if (!mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)((w - 2) >> 1) & 1u, abort_flag, g.spin_limit)) {
-                            atomicCAS(g.err, 0, 4);
-                            *abort_flag = 1;
-                            run = false;
-                            break;
-                        }
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    }
-                    if (!mbar_wait(full0 + 8 * st, ph, abort_flag, g.spin_limit)) {
-                        atomicCAS(g.err, 0, 2);
-                        *abort_flag = 1;
-                        run = false;
+            const uint32_t fA0 = smem_u32(&fullA[0]), eA0 = smem_u32(&emptyA[0]);
+            const uint32_t accF0 = smem_u32(&acc_full[0]), accE0 = smem_u32(&acc_empty[0]);
+            int ja = 0, ps = 0, bs = 0, w = 0;
+            uint32_t pph = 0, bph = 0;
+            int fail = 0;
+            for (int u = u0; u < u1 && !fail; ++u, ++w) {
+                const int k0 = (u % nw) * W, k1 = min(k0 + W, g.kstages);
+                for (int kst = k0; kst < k1; ++kst) {
+                    if (!mbar_wait(smem_u32(&fullB[bs]), bph, abort_flag, g.spin_limit)) {
+                        fail = 2;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint64_t da = da0 + (uint64_t)(st * (OZ_A_BYTES >> 4));
-                    const uint64_t db = db0 + (uint64_t)(st * (OZ_B_BYTES >> 4));
-                    const uint32_t dst = tmem + (uint32_t)(buf * OZ_BN);
-                    oz_mma(dst, da, db, idesc, first ? 0u : 1u);          // K = 16 BF16 (32 bytes) each
-                    oz_mma(dst, da + 2, db + 2, idesc, 1u);
-                    oz_mma(dst, da + 4, db + 4, idesc, 1u);
-                    oz_mma(dst, da + 6, db + 6, idesc, 1u);
-                    tc_commit(empty0 + 8 * st);
-                    if (last) {
-                        tc_commit(smem_u32(&acc_full[buf]));
-                        ++w;
-                        jw = 0;
-                    } else {
-                        ++jw;
-                    }
-                    if (++st == OZ_STAGES) { st = 0; ph ^= 1u; }
+                    const uint64_t dbs = db0 + (uint64_t)((bs * bslot) >> 4);
+                    const bool wfirst = kst == k0, wlast = kst + 1 == k1;
+                    fail = S == 7 ? oz_issue_slice<7>(S, tmem, da0, dbs, fA0, eA0, accF0, accE0, nP, totalA, ja, ps,
+                                                      pph, wfirst, wlast, w, abort_flag, g.spin_limit)
+                                  : oz_issue_slice<0>(S, tmem, da0, dbs, fA0, eA0, accF0, accE0, nP, totalA, ja, ps,
+                                                      pph, wfirst, wlast, w, abort_flag, g.spin_limit);
+                    if (fail) break;
+                    tc_commit(smem_u32(&emptyB[bs]));
+                    bs ^= 1;
+                    if (bs == 0) bph ^= 1u;
                 }
+            }
+            if (fail) {
+                atomicCAS(g.err, 0, fail);
+                *abort_flag = 1;
             }
             if (*abort_flag) {
                 tc_commit(smem_u32(drain));
@@ -270,33 +372,28 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             }
         }
     } else {
-        // ---------------- accumulator warps: exact windows -> (hi, lo), then the epilogue
-        const int qr = warp & 3;                                // TMEM lane quarter = rows 32 qr ..
-        const int half = (warp - 2) >> 2;                       // columns OZ_COLS half ..
+        // ---------------- accumulator warps: exact window sums -> (hi, lo) in registers,
+        // then the epilogue.  This thread: TMEM lane (row) 32 qr + lane, columns
+        // cg * OZ_COLS .. + OZ_COLS of every diagonal.
+        const int qr = warp & 3;
+        const int cg = (warp - 2) >> 2;
         const int row = m0 + qr * 32 + lane;
-        const uint32_t tlane = (uint32_t)(qr * 32) << 16;
-        const uint32_t tlo = tmem + tlane + (uint32_t)(OZ_LO_COL + half * OZ_COLS);   // this thread's lo
-        const uint32_t thi = tmem + tlane + (uint32_t)(OZ_HI_COL + half * OZ_COLS);   // and hi
+        const uint32_t tq = tmem + ((uint32_t)(qr * 32) << 16) + (uint32_t)(cg * OZ_COLS);
+        float hi[OZ_COLS], lo[OZ_COLS];
 #pragma unroll
-        for (int c0 = 0; c0 < OZ_COLS; c0 += 8) {
-            asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};"
-                         :: "r"(tlo + c0), "r"(0u) : "memory");
-            asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};"
-                         :: "r"(thi + c0), "r"(0u) : "memory");
-        }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        for (int i = 0; i < OZ_COLS; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
         // reference scales: RA over this row's chunks, RB over each column's (lane i: column i)
         float RA = 0.f, RBl = 0.f;
-        const int col_l = n0 + half * OZ_COLS + lane;
-        const int c_lo = u0 / S, c_hi = u1 > u0 ? (u1 - 1) / S + 1 : c_lo;
+        const int col_l = n0 + cg * OZ_COLS + lane;
+        const int c_lo = u0 / nw, c_hi = u1 > u0 ? (u1 - 1) / nw + 1 : c_lo;
         for (int c = c_lo; c < c_hi; ++c) {
             const int ra = g.rowA[b * g.nchunk + c] + row;
             if (row < g.M && ra < g.rowsA) RA = fmaxf(RA, g.scA[ra]);
             const int rb = g.rowB[b * g.nchunk + c] + col_l;
-            if (col_l < g.Nr && rb < g.rowsB) RBl = fmaxf(RBl, g.scB[rb]);
+            if (lane < OZ_COLS && col_l < g.Nr && rb < g.rowsB) RBl = fmaxf(RBl, g.scB[rb]);
         }
         const float inv_ra = RA > 0.f ? 1.0f / RA : 0.f;        // exact: powers of two
-        float* colref = (float*)(smem + OZ_STAGES * OZ_STAGE_BYTES + 256) + (warp - 2) * 96;
+        float* colref = (float*)(smem + OZ_RING_BYTES + OZ_BAR_BYTES) + (warp - 2) * 96;
         float* colfac = colref + 64;                            // this chunk's sb / RB per column
         colref[lane] = RBl;
         colref[32 + lane] = RBl > 0.f ? 1.0f / RBl : 0.f;
@@ -305,88 +402,48 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         bool ok = true;
         int w = 0;
         float sa = 0.f;
-        for (int u = u0; u < u1 && ok; ++u) {
-            const int c = u / S, d = u - c * S;
+        for (int u = u0; u < u1 && ok; ++u, ++w) {
+            const int c = u / nw;
             if (c != cur_c) {       // this row's factor; lane i: the factor of column i (one load each)
                 const int ra = g.rowA[b * g.nchunk + c] + row;
                 sa = (row < g.M && ra < g.rowsA) ? g.scA[ra] * inv_ra : 0.f;
-                const int rbase = g.rowB[b * g.nchunk + c] + n0 + half * OZ_COLS;
-                const int nvalid = min(g.Nr - (n0 + half * OZ_COLS), g.rowsB - rbase);
+                const int rbase = g.rowB[b * g.nchunk + c] + n0 + cg * OZ_COLS;
+                const int nvalid = min(g.Nr - (n0 + cg * OZ_COLS), g.rowsB - rbase);
                 __syncwarp();
-                colfac[lane] = lane < nvalid ? g.scB[rbase + lane] * colref[32 + lane] : 0.f;
+                colfac[lane] = (lane < OZ_COLS && lane < nvalid) ? g.scB[rbase + lane] * colref[32 + lane] : 0.f;
                 __syncwarp();
                 cur_c = c;
             }
-            {
+            for (int d = 0; d < S; ++d) {
+                bool got = mbar_wait(smem_u32(&acc_full[d]), (uint32_t)(w & 1), abort_flag, g.spin_limit);
+                got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+                if (!got) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const float fa = sa * __int_as_float((127 - OZ_SLICE_BITS * (d + 2)) << 23);  // * 2^{-7(d+2)}
-                const int nwin = ((d + 1) * g.kstages + oz_win(d) - 1) / oz_win(d);
-                for (int wi = 0; wi < nwin; ++wi, ++w) {
-                    const int buf = w & 1;
-                    bool got = mbar_wait(smem_u32(&acc_full[buf]), (uint32_t)(w >> 1) & 1u, abort_flag, g.spin_limit);
-                    got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
-                    if (!got) { ok = false; break; }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-                    for (int c0 = 0; c0 < OZ_COLS; c0 += 8) {
-                        uint32_t v[8], l[8], hh[8];
-                        tmem_ld8(tmem + tlane + (uint32_t)(buf * OZ_BN + half * OZ_COLS + c0), v);
-                        tmem_ld8(tlo + c0, l);
-                        tmem_ld8(thi + c0, hh);
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                for (int c0 = 0; c0 < OZ_COLS; c0 += 8) {
+                    uint32_t v[8];
+                    tmem_ld8(tq + (uint32_t)(OZ_BN * d + c0), v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const float sb = colfac[c0 + i];
-                            float lo = __uint_as_float(l[i]), hi = __uint_as_float(hh[i]);
-                            two_sum_acc(hi, lo, (__uint_as_float(v[i]) * sb) * fa);
-                            l[i] = __float_as_uint(lo);
-                            hh[i] = __float_as_uint(hi);
-                        }
-                        tmem_st8(tlo + c0, l);
-                        tmem_st8(thi + c0, hh);
-                    }
-                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&acc_empty[buf])) : "memory");
+                    for (int i = 0; i < 8; ++i)
+                        two_sum_acc(hi[c0 + i], lo[c0 + i], (__uint_as_float(v[i]) * colfac[c0 + i]) * fa);
                 }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&acc_empty[d])) : "memory");
             }
         }
         if (ok && !*abort_flag) {
-            // every MMA has completed: park (hi, lo) in the stage ring for the FP64 epilogue
-            constexpr int T = OZ_ACC_WARPS * 32;
-            float* park_hi = (float*)smem;                      // [OZ_COLS][T]
-            float* park_lo = park_hi + OZ_COLS * T;
-            const int t = (warp - 2) * 32 + lane;
-#pragma unroll
-            for (int c0 = 0; c0 < OZ_COLS; c0 += 8) {
-                uint32_t l[8], hh[8];
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 "
-                             "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                             : "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]),
-                               "=r"(l[6]), "=r"(l[7])
-                             : "r"(tlo + c0));
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 "
-                             "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                             : "=r"(hh[0]), "=r"(hh[1]), "=r"(hh[2]), "=r"(hh[3]), "=r"(hh[4]), "=r"(hh[5]),
-                               "=r"(hh[6]), "=r"(hh[7])
-                             : "r"(thi + c0));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    park_hi[(c0 + i) * T + t] = __uint_as_float(hh[i]);
-                    park_lo[(c0 + i) * T + t] = __uint_as_float(l[i]);
-                }
-            }
             if (row < g.M) {
                 const long long rb0 = g.rowC ? g.offC[b] + g.rowC[row] : g.offC[b * g.M + row];
                 const long long rb2 = !g.offC2 ? 0 : g.rowC ? g.offC2[b] + g.rowC[row] : g.offC2[b * g.M + row];
-#pragma unroll 1
+#pragma unroll
                 for (int qq = 0; qq < OZ_COLS / 2; ++qq) {
-                    const int nr = n0 + half * OZ_COLS + 2 * qq;
-                    if (nr >= g.Nr) break;
-                    const double xr = ((double)park_hi[(2 * qq) * T + t] + (double)park_lo[(2 * qq) * T + t]) *
-                                      ((double)RA * (double)colref[2 * qq]);
-                    const double xi = ((double)park_hi[(2 * qq + 1) * T + t] + (double)park_lo[(2 * qq + 1) * T + t]) *
+                    const int nr = n0 + cg * OZ_COLS + 2 * qq;
+                    if (nr >= g.Nr) continue;
+                    const double xr = ((double)hi[2 * qq] + (double)lo[2 * qq]) * ((double)RA * (double)colref[2 * qq]);
+                    const double xi = ((double)hi[2 * qq + 1] + (double)lo[2 * qq + 1]) *
                                       ((double)RA * (double)colref[2 * qq + 1]);
                     if (g.work) {       // partial of this split; oz_split_reduce applies alpha
                         g.work[(((long long)split * g.nbatch + b) * g.M + row) * (g.Nr / 2) + (nr >> 1)] =
@@ -395,10 +452,10 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     }
                     const double yr = g.alpha_re * xr - g.alpha_im * xi;
                     const double yi = g.alpha_re * xi + g.alpha_im * xr;
-                    double2* p = g.C + rb0 + g.colC[nr >> 1];
-                    double2 u = g.overwrite ? make_double2(0.0, 0.0) : *p;
-                    u.x += yr; u.y += yi;
-                    *p = u;
+                    double2* pc = g.C + rb0 + g.colC[nr >> 1];
+                    double2 uu = g.overwrite ? make_double2(0.0, 0.0) : *pc;
+                    uu.x += yr; uu.y += yi;
+                    *pc = uu;
                     if (g.offC2) {
                         double2* p2 = g.C + rb2 + g.colC2[nr >> 1];
                         double2 z = g.overwrite ? make_double2(0.0, 0.0) : *p2;
@@ -415,8 +472,11 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     // ---------------- teardown: copies in flight, TMEM
     __syncwarp();
     if (warp == 0 && lane == 0 && *abort_flag) {
-        for (int s = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); s < issued; ++s)
-            mbar_wait(smem_u32(&bars[s % OZ_STAGES]), (uint32_t)(s / OZ_STAGES) & 1u, nullptr, TC_DRAIN_LIMIT);
+        for (int j = (issuedP > nP ? issuedP - nP : 0); j < issuedP; ++j)
+            if (j != g.skip_stage)
+                mbar_wait(smem_u32(&fullA[j % nP]), (uint32_t)(j / nP) & 1u, nullptr, TC_DRAIN_LIMIT);
+        for (int j = (issuedB > 2 ? issuedB - 2 : 0); j < issuedB; ++j)
+            mbar_wait(smem_u32(&fullB[j & 1]), (uint32_t)(j >> 1) & 1u, nullptr, TC_DRAIN_LIMIT);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

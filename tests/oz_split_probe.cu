@@ -29,7 +29,7 @@ void probe_scales(int s, int E, double* fixed, float* row) {
     *row = oz_row_scale(E);
 }
 
-int probe_win(int d) { return oz_win(d); }
+int probe_kwin(int s) { return oz_kwin(s); }
 
 void probe_unit_range(int nch, int S, int kstages, int nsplit, int split, int* u0, int* u1) {
     oz_unit_range(nch, S, kstages, nsplit, split, *u0, *u1);

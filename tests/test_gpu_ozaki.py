@@ -50,10 +50,10 @@ def test_oz_gemm_exact_on_integer_operands(lib, M, Nc, K):
     assert np.array_equal(C, ref)
 
 
-def test_oz_gemm_exact_at_the_window_bound(lib):
-    """The largest exact window: every entry (1 - 2^-20)(1 +- i) has top slice 128, so each
-    TMEM window of 16 stages sums 1024 products of exactly 2^14 to 2^24, the largest
-    integer range FP32 holds; the product must still be exact."""
+def test_oz_gemm_exact_with_top_digits(lib):
+    """Every entry (1 - 2^-20)(1 +- i) has the digits (128, 0, -2, 0, 0): top digits of
+    the largest magnitude, and every dropped pair is zero, so the product is exact.  With
+    5 slices a window is 9 K slices (64 real K each), so the 1024 real K span two."""
     from paper_1911_00242_gb300.binding import oz_gemm
     x = 1.0 - 2.0 ** -20
     A = np.full((128, 512), x + 1j * x)
@@ -61,6 +61,20 @@ def test_oz_gemm_exact_at_the_window_bound(lib):
     C = oz_gemm(A, B, slices=5)
     assert np.array_equal(C, A @ B.T)
     assert C[0, 0] == 512 * 2 * x * x
+
+
+def test_oz_gemm_exact_at_the_window_bound(lib):
+    """The largest exact window: with 2 slices a window is 16 K slices, and the entries
+    (1 - 2^-14)(1 +- i) (digits (128, -1)) make diagonal 0 of the real column sum 1024
+    products of exactly 2^14 to 2^24, the largest integer range FP32 holds.  The result
+    is the scheme's truncated product, exactly: per real K the kept pairs give
+    128^2 2^-14 - 2 * 128 2^-21 = 1 - 2^-13 (the dropped pair (1, 1) is 2^-28)."""
+    from paper_1911_00242_gb300.binding import oz_gemm
+    x = 1.0 - 2.0 ** -14
+    A = np.full((128, 512), x + 1j * x)
+    B = np.full((64, 512), x - 1j * x)
+    C = oz_gemm(A, B, slices=2)
+    assert (C.real == 1024.0 - 0.125).all() and (C.imag == 0.0).all()
 
 
 @pytest.mark.parametrize("slices", [3, 5, 7, 8])

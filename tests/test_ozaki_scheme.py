@@ -5,9 +5,9 @@ cores (Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59 (2012) 95-118):
 
 * every operand row gets a power-of-two scale 2^E > max|x| and is cut into s balanced
   base-128 digits (BF16 integers);
-* the slice pairs (p, q) with p + q <= s - 1 are multiplied, and the products of one
-  diagonal d = p + q of one momentum chunk are summed in an FP32 TMEM window of at
-  most oz_win(d) stages of 64;
+* the slice pairs (p, q) with p + q <= s - 1 are multiplied; every diagonal d = p + q
+  has its own FP32 TMEM accumulator, which sums the products of all its pairs over a
+  window of at most oz_kwin(s) K slices of 64 of one momentum chunk;
 * each window is scaled by its power of two and added into a float pair (hi, lo) with
   TwoSum (Knuth); the FP64 epilogue multiplies hi + lo by the reference scales RA RB.
 
@@ -20,7 +20,7 @@ the form's accuracy rests on:
 2. every partial sum of a window is an integer of magnitude <= 2^24 (so the tensor
    core's FP32 accumulation is exact), and one more stage would break that;
 3. the truncated pair sum is within the bound derived below of the exact product;
-4. the schedule of units, stages and windows forms every kept pair exactly once, and
+4. the schedule of units, K slices and windows forms every kept pair exactly once, and
    the split of a tile's units over CTAs is a partition;
 5. the float-pair accumulation loses no more than its lo roundings.
 
@@ -55,16 +55,12 @@ def _kernel_constants():
         assert m, name
         return int(m.group(1))
 
-    m = re.search(r"oz_win\(int d\)\s*\{\s*return d == 0 \? (\d+) : (\d+);\s*\}", src)
-    assert m, "oz_win"
     return {
         "BK": const("OZ_BK"),
         "BITS": const("OZ_SLICE_BITS"),
         "MAX_SLICES": const("OZ_MAX_SLICES"),
         "EXP_MIN": const("OZ_EXP_MIN"),
         "EXP_MAX": const("OZ_EXP_MAX"),
-        "WIN0": int(m.group(1)),
-        "WIN": int(m.group(2)),
     }
 
 
@@ -74,8 +70,23 @@ BASE = 1 << BITS
 HALF = BASE >> 1
 
 
-def oz_win(d):
-    return K["WIN0"] if d == 0 else K["WIN"]
+def digit_bound(p):
+    """Largest |v_p|: the top digit reaches 2^7, the balanced low digits 2^6."""
+    return BASE if p == 0 else HALF
+
+
+def diagonal_bound(s, d):
+    """Largest |sum over the pairs of diagonal d of v_p w_q| for one K element."""
+    return sum(digit_bound(p) * digit_bound(d - p) for p in range(d + 1) if p < s and d - p < s)
+
+
+def oz_kwin(s):
+    """The longest window (K slices of 64) whose partial sums stay within 2^24 on every
+    kept diagonal, found by search from the digit bounds (not from the kernel's formula)."""
+    w = 0
+    while all((w + 1) * K["BK"] * diagonal_bound(s, d) <= 1 << 24 for d in range(s)) and w < 16:
+        w += 1
+    return w
 
 
 # ---------------------------------------------------------------- the split
@@ -162,8 +173,8 @@ def probe():
     lib.probe_row_exponent.restype = ctypes.c_int
     lib.probe_split.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint16)]
     lib.probe_scales.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_float)]
-    lib.probe_win.argtypes = [ctypes.c_int]
-    lib.probe_win.restype = ctypes.c_int
+    lib.probe_kwin.argtypes = [ctypes.c_int]
+    lib.probe_kwin.restype = ctypes.c_int
     ip = ctypes.POINTER(ctypes.c_int)
     lib.probe_unit_range.argtypes = [ctypes.c_int] * 5 + [ip, ip]
     return lib
@@ -217,42 +228,57 @@ def test_kernel_scales_are_the_powers_of_two(probe):
 
 
 # ---------------------------------------------------------------- exact windows
-def test_window_sizes_keep_fp32_exact_and_are_maximal():
+@pytest.mark.parametrize("s", range(1, K["MAX_SLICES"] + 1))
+def test_window_sizes_keep_fp32_exact_and_are_maximal(s):
     lim = 1 << 24
-    top, low = BASE, HALF
-    # d = 0: both digits are top digits
-    assert oz_win(0) * K["BK"] * top * top <= lim
-    assert (oz_win(0) + 1) * K["BK"] * top * top > lim
-    # d > 0: every pair holds at least one low digit
-    assert oz_win(1) * K["BK"] * top * low <= lim
-    assert (oz_win(1) + 1) * K["BK"] * top * low > lim
+    w = oz_kwin(s)
+    assert w >= 1
+    assert all(w * K["BK"] * diagonal_bound(s, d) <= lim for d in range(s))
+    # one more K slice breaks some diagonal, unless the 16-slice cap applies
+    assert w == 16 or any((w + 1) * K["BK"] * diagonal_bound(s, d) > lim for d in range(s))
 
 
-@pytest.mark.parametrize("d", [0, 1])
-def test_worst_case_window_sums_exactly_in_fp32(d):
-    """A full window of the largest digits sums to exactly 2^24; every FP32 prefix is exact."""
-    n = oz_win(d) * K["BK"]
-    prod = BASE * BASE if d == 0 else BASE * HALF
-    terms = np.full(n, prod, dtype=np.int64)
-    acc = np.float32(0.0)
-    for t in terms:
-        acc = np.float32(acc + np.float32(t))
-    assert int(acc) == int(terms.sum()) == 1 << 24
+def test_diagonal_bounds_by_hand():
+    """2^14 for diagonal 0; 2^12 (d + 3) for 1 <= d <= s - 1: pairs (0, d) and (d, 0) at
+    2^13, the d - 1 others at 2^12."""
+    for s in range(1, K["MAX_SLICES"] + 1):
+        assert diagonal_bound(s, 0) == 1 << 14
+        for d in range(1, s):
+            assert diagonal_bound(s, d) == (d + 3) << 12
+    assert [oz_kwin(s) for s in range(1, 9)] == [16, 16, 12, 10, 9, 8, 7, 6]
+
+
+@pytest.mark.parametrize("s", [2, 3, 7, 8])
+def test_worst_case_window_sums_exactly_in_fp32(s):
+    """A full window of the largest digits on the diagonal with the largest bound: every
+    FP32 prefix is exact, in pair-major (the MMA issue) and K-major order."""
+    w = oz_kwin(s)
+    d = max(range(s), key=lambda dd: diagonal_bound(s, dd))
+    per_k = [digit_bound(p) * digit_bound(d - p) for p in range(d + 1)]
+    n = w * K["BK"]
+    for terms in (np.repeat(per_k, n), np.tile(per_k, n)):
+        acc = np.float32(0.0)
+        tot = 0
+        for t in terms:
+            acc = np.float32(acc + np.float32(t))
+            tot += int(t)
+            assert int(acc) == tot
+        assert tot <= 1 << 24
 
 
 def test_random_window_prefixes_exact_in_fp32():
     rng = np.random.default_rng(6)
-    for d in (0, 1, 3):
-        n = oz_win(d) * K["BK"]
-        a = rng.integers(-BASE, BASE + 1, n) if d == 0 else rng.integers(-HALF, HALF, n)
-        b = rng.integers(-BASE, BASE + 1, n)
-        t = a * b
-        exact = np.cumsum(t)
-        assert np.max(np.abs(exact)) <= 1 << 24
-        acc = np.float32(0.0)
-        for i in range(n):
-            acc = np.float32(acc + np.float32(t[i]))
-            assert int(acc) == exact[i]
+    for s in (3, 7, 8):
+        n = oz_kwin(s) * K["BK"]
+        for d in (0, 1, s - 1):
+            acc, tot = np.float32(0.0), 0
+            for p in range(d + 1):
+                a = rng.integers(-BASE, BASE + 1, n) if p == 0 else rng.integers(-HALF, HALF, n)
+                bq = rng.integers(-BASE, BASE + 1, n) if d - p == 0 else rng.integers(-HALF, HALF, n)
+                for t in a * bq:
+                    acc = np.float32(acc + np.float32(t))
+                    tot += int(t)
+                    assert int(acc) == tot
 
 
 # ---------------------------------------------------------------- truncated products
@@ -299,17 +325,19 @@ def test_dropping_the_last_kept_diagonal_breaks_the_bound():
 
 # ---------------------------------------------------------------- the kernel's schedule
 def unit_range(nch, S, kstages, nsplit, split_idx):
-    """The units [u0, u1) of one CTA when a tile's units are split over nsplit CTAs by stage count."""
-    nunits = nch * S
+    """The units [u0, u1) of one CTA: units are (chunk, window) in order, each window
+    oz_kwin(S) K slices (the chunk's last one shorter); split by K-slice count."""
+    W = oz_kwin(S)
+    nw = -(-kstages // W)
+    nunits = nch * nw
     if nsplit <= 1:
         return 0, nunits
-    per_chunk = S * (S + 1) // 2 * kstages
-    total = per_chunk * nch
+    total = nch * kstages
     lo, hi = total * split_idx // nsplit, total * (split_idx + 1) // nsplit
     u0 = u1 = nunits
     for u in range(nunits):
-        c, d = divmod(u, S)
-        start = c * per_chunk + d * (d + 1) // 2 * kstages
+        c, wi = divmod(u, nw)
+        start = c * kstages + wi * W
         if start >= lo and u0 == nunits:
             u0 = u
         if start >= hi:
@@ -318,9 +346,10 @@ def unit_range(nch, S, kstages, nsplit, split_idx):
     return u0, max(u0, u1)
 
 
-@pytest.mark.parametrize("nch,S,kstages", [(1, 7, 1), (1, 7, 4), (3, 7, 8), (2, 3, 2), (5, 8, 3), (1, 1, 1)])
+@pytest.mark.parametrize("nch,S,kstages", [(1, 7, 1), (1, 7, 4), (3, 7, 8), (2, 3, 2), (5, 8, 3), (1, 1, 1),
+                                           (2, 7, 23)])
 def test_unit_split_is_a_partition(nch, S, kstages):
-    nunits = nch * S
+    nunits = nch * -(-kstages // oz_kwin(S))
     for nsplit in range(1, 17):
         covered = []
         prev = 0
@@ -333,43 +362,46 @@ def test_unit_split_is_a_partition(nch, S, kstages):
 
 
 def test_kernel_schedule_code_equals_the_model(probe):
-    """The GEMM kernel's window sizes and unit split (csrc/ozaki_schedule.cuh, built for
+    """The GEMM kernel's window lengths and unit split (csrc/ozaki_schedule.cuh, built for
     the host) equal the model's, and the kernel's split is a partition by itself."""
-    assert all(probe.probe_win(d) == oz_win(d) for d in range(K["MAX_SLICES"]))
+    assert all(probe.probe_kwin(s) == oz_kwin(s) for s in range(1, K["MAX_SLICES"] + 1))
     u0, u1 = ctypes.c_int(0), ctypes.c_int(0)
-    for nch, S, kst in [(1, 7, 1), (1, 7, 4), (3, 7, 8), (2, 3, 2), (5, 8, 3), (1, 1, 1), (27, 7, 6)]:
+    for nch, S, kst in [(1, 7, 1), (1, 7, 4), (3, 7, 8), (2, 3, 2), (5, 8, 3), (1, 1, 1), (27, 7, 6), (4, 7, 23)]:
+        nunits = nch * -(-kst // oz_kwin(S))
         for nsplit in range(1, 17):
             prev = 0
             for sp in range(nsplit):
                 probe.probe_unit_range(nch, S, kst, nsplit, sp, ctypes.byref(u0), ctypes.byref(u1))
                 assert (u0.value, u1.value) == unit_range(nch, S, kst, nsplit, sp)
-                assert u0.value == prev and u0.value <= u1.value <= nch * S
+                assert u0.value == prev and u0.value <= u1.value <= nunits
                 prev = u1.value
-            assert prev == nch * S
+            assert prev == nunits
 
 
 def schedule(nch, S, kstages):
-    """The MMA issuer's windows: lists of (chunk, p, q, kst) stages, per unit in order."""
+    """The MMA issuer's windows: per (chunk, window), for each diagonal d, the list of
+    (chunk, p, q, kst) products it sums, in issue order (K slice, then p)."""
+    W = oz_kwin(S)
     wins = []
-    for u in range(nch * S):
-        c, d = divmod(u, S)
-        stages = [(c, p, d - p, kst) for p in range(d + 1) for kst in range(kstages)]
-        w = oz_win(d)
-        wins.extend(stages[i:i + w] for i in range(0, len(stages), w))
+    for c in range(nch):
+        for k0 in range(0, kstages, W):
+            ks = range(k0, min(k0 + W, kstages))
+            wins.append({d: [(c, p, d - p, k) for k in ks for p in range(d + 1)] for d in range(S)})
     return wins
 
 
 @pytest.mark.parametrize("nch,S,kstages", [(1, 7, 40), (2, 7, 9), (3, 3, 17), (1, 8, 33)])
 def test_schedule_forms_each_kept_pair_once(nch, S, kstages):
     wins = schedule(nch, S, kstages)
-    seen = [st for w in wins for st in w]
+    seen = [st for w in wins for d in w for st in w[d]]
     want = [(c, p, q, k) for c in range(nch) for p in range(S) for q in range(S) if p + q <= S - 1
             for k in range(kstages)]
     assert sorted(seen) == sorted(want) and len(seen) == len(set(seen))
     for w in wins:
-        c, p, q, _ = w[0]
-        assert 0 < len(w) <= oz_win(p + q)
-        assert all(st[0] == c and st[1] + st[2] == p + q for st in w)
+        for d, sts in w.items():
+            ks = {st[3] for st in sts}
+            assert 0 < len(ks) <= oz_kwin(S)
+            assert all(st[0] == sts[0][0] and st[1] + st[2] == d for st in sts)
 
 
 def model_gemm(Ach, Bch, s):
@@ -393,36 +425,37 @@ def model_gemm(Ach, Bch, s):
             RB = max(2.0 ** Eb[c][n] for c in range(nch))
             hi, lo = np.float32(0.0), np.float32(0.0)
             xsum, lo_abs = Fraction(0), 0.0
-            for win in schedule(nch, s, kst):
-                c, p0, q0, _ = win[0]
-                d = p0 + q0
-                acc = 0
-                for (_, p, q, k) in win:
-                    sl = slice(k * K["BK"], (k + 1) * K["BK"])
-                    part = V[c][p][m, sl] * W[c][q][n, sl]
-                    acc_prefix = acc + np.cumsum(part)
-                    assert np.max(np.abs(acc_prefix)) <= 1 << 24
-                    acc = int(acc_prefix[-1])
-                v = np.float32(acc)
-                assert int(v) == acc
-                sa = np.float32(2.0 ** Ea[c][m] / RA)
-                sb = np.float32(2.0 ** Eb[c][n] / RB)
-                fa = np.float32(sa * np.float32(2.0 ** (-BITS * (d + 2))))
-                x = np.float32(np.float32(v * sb) * fa)
-                assert Fraction(float(x)) == Fraction(acc) * Fraction(float(sb)) * Fraction(float(fa))
-                xsum += Fraction(float(x))
-                t = np.float32(hi + x)
-                bp = np.float32(t - hi)
-                e = np.float32(np.float32(hi - np.float32(t - bp)) + np.float32(x - bp))
-                assert Fraction(float(t)) + Fraction(float(e)) == Fraction(float(hi)) + Fraction(float(x))
-                hi = t
-                lo = np.float32(lo + e)
-                lo_abs += abs(float(lo))
+            for wd in schedule(nch, s, kst):
+                for d in range(s):
+                    win = wd[d]             # the window's products of diagonal d
+                    c = win[0][0]
+                    acc = 0
+                    for (_, p, q, k) in win:
+                        sl = slice(k * K["BK"], (k + 1) * K["BK"])
+                        part = V[c][p][m, sl] * W[c][q][n, sl]
+                        acc_prefix = acc + np.cumsum(part)
+                        assert np.max(np.abs(acc_prefix)) <= 1 << 24
+                        acc = int(acc_prefix[-1])
+                    v = np.float32(acc)
+                    assert int(v) == acc
+                    sa = np.float32(2.0 ** Ea[c][m] / RA)
+                    sb = np.float32(2.0 ** Eb[c][n] / RB)
+                    fa = np.float32(sa * np.float32(2.0 ** (-BITS * (d + 2))))
+                    x = np.float32(np.float32(v * sb) * fa)
+                    assert Fraction(float(x)) == Fraction(acc) * Fraction(float(sb)) * Fraction(float(fa))
+                    xsum += Fraction(float(x))
+                    t = np.float32(hi + x)
+                    bp = np.float32(t - hi)
+                    e = np.float32(np.float32(hi - np.float32(t - bp)) + np.float32(x - bp))
+                    assert Fraction(float(t)) + Fraction(float(e)) == Fraction(float(hi)) + Fraction(float(x))
+                    hi = t
+                    lo = np.float32(lo + e)
+                    lo_abs += abs(float(lo))
             out[m, n] = (hi, lo, RA, RB, xsum, lo_abs, Ea, Eb)
     return out
 
 
-@pytest.mark.parametrize("s,nch,kst", [(7, 2, 2), (8, 1, 3), (5, 3, 1)])
+@pytest.mark.parametrize("s,nch,kst", [(7, 2, 2), (8, 1, 3), (5, 3, 1), (3, 1, 13), (7, 1, 9)])
 def test_kernel_model_matches_exact_product(s, nch, kst):
     rng = np.random.default_rng(400 + s)
     Kc = kst * K["BK"]
