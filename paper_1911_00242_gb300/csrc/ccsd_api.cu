@@ -605,7 +605,7 @@ int add_tc(ccsd_ctx* h, Alloc& al, const TcBuf& A, const TcBuf& B, int c, int M,
         const long long tiles = (long long)z.tiles_m * z.tiles_n * nbatch;
         const int units = nchunk * oz_nwin(z.kstages, h->oz_slices);
         z.nsplit = 1;
-        if (tiles < 2 * 152) z.nsplit = (int)std::min<long long>(std::min(units, 16), (2 * 152 + tiles - 1) / tiles);
+        if (tiles < 2 * kSMs) z.nsplit = (int)std::min<long long>(std::min(units, OZ_MAX_SPLIT), (2 * kSMs + tiles - 1) / tiles);
         t.blocks = (int)(tiles * z.nsplit);
         if (z.nsplit > 1)
             h->oz_work_elems = std::max(h->oz_work_elems, (long long)z.nsplit * nbatch * M * (Nr / 2));
@@ -648,11 +648,13 @@ dim3 row_grid(long long rows);
 // two buffers of at most OZ_GENERIC_CAP elements per slice plane are allocated here.
 constexpr double OZ_CONVERT_FLOPS = 5e8;
 // cost model of the conversion (measured on GB300: the per-CTA fixed cost of a launch of
-// oz_gemm_kernel, the time of one 128 x 128 x 64 stage, embedding bandwidth, FP64 GEMM rate)
+// oz_gemm_kernel, the time of one slice-pair product of a 128 x 64 tile over a K slice of
+// 64, embedding bandwidth, and the rate of the double-float GEMM engine on the skinny
+// shapes it is left with, 1.3 .. 2.4 TFLOP/s)
 constexpr double OZ_CTA_SECONDS = 8e-6;
-constexpr double OZ_STAGE_SECONDS = 0.35e-6;
+constexpr double OZ_PAIR_SECONDS = 0.11e-6;
 constexpr double OZ_EMBED_BPS = 2e12;
-constexpr double OZ_DF_FLOPS = 5e12;      // the double-float instance of the GEMM engine
+constexpr double OZ_DF_FLOPS = 1.5e12;
 constexpr long long OZ_GENERIC_CAP = 1LL << 28;
 
 int oz_convert_gemms(ccsd_ctx* h, Alloc& al, std::map<int, GemmSpec>& specs, bool pooled, float* pool_a,
@@ -666,8 +668,8 @@ int oz_convert_gemms(ccsd_ctx* h, Alloc& al, std::map<int, GemmSpec>& specs, boo
         auto it = specs.find(st.idx);
         if (it == specs.end() || it->second.nbatch == 0) continue;
         GemmSpec& s = it->second;
-        // orientation: C^T = B^T A^T when that needs fewer 128 x 128 tiles (rows M, real columns 2N)
-        auto tiles = [](long long m, long long n) { return ((m + 127) / 128) * ((2 * n + 127) / 128); };
+        // orientation: C^T = B^T A^T when that needs fewer tiles (rows M, real columns 2N)
+        auto tiles = [](long long m, long long n) { return ((m + OZ_BM - 1) / OZ_BM) * ((2 * n + OZ_BN - 1) / OZ_BN); };
         if (s.offC2.empty() && tiles(s.N, s.M) < tiles(s.M, s.N)) {
             std::swap(s.M, s.N);
             std::swap(s.a, s.b);
@@ -681,13 +683,20 @@ int oz_convert_gemms(ccsd_ctx* h, Alloc& al, std::map<int, GemmSpec>& specs, boo
         std::vector<long long> ua(s.offA), ub(s.offB);
         std::sort(ua.begin(), ua.end()); ua.erase(std::unique(ua.begin(), ua.end()), ua.end());
         std::sort(ub.begin(), ub.end()); ub.erase(std::unique(ub.begin(), ub.end()), ub.end());
-        // worth it?  Tensor-core estimate: per CTA a fixed cost plus its stages (all tiles,
-        // padding included), plus the operand embedding at HBM speed; the alternative is the
-        // double-float GEMM engine (algorithmic flops at its rate).
-        const double ctas = (double)tiles(s.M, s.N) * s.nbatch;
-        const double stages = (double)s.nchunk * (h->oz_slices * (h->oz_slices + 1) / 2) * (kpad / OZ_BK);
+        // worth it?  Tensor-core estimate: the launch's waves of CTAs (with the kernel's own
+        // split of small launches), each CTA a fixed cost plus its slice-pair products over
+        // its K slices (padding included), plus the operand embedding at HBM speed; the
+        // alternative is the double-float GEMM engine (algorithmic flops at its rate).
+        const long long ntile = tiles(s.M, s.N) * s.nbatch;
+        const int kst = kpad / OZ_BK;
+        const long long units = (long long)s.nchunk * oz_nwin(kst, h->oz_slices);
+        const long long nsplit = ntile < 2 * kSMs ? std::min<long long>(std::min<long long>(units, OZ_MAX_SPLIT),
+                                                                          (2 * kSMs + ntile - 1) / ntile) : 1;
+        const double waves = (double)((ntile * nsplit + kSMs - 1) / kSMs);
+        const double pairs = h->oz_slices * (h->oz_slices + 1) / 2;
+        const double per_cta = OZ_CTA_SECONDS + (double)s.nchunk * kst / nsplit * pairs * OZ_PAIR_SECONDS;
         const double emb = ((double)ua.size() * s.M + (double)ub.size() * 2 * s.N) * kpad * 2.0 * h->oz_slices;
-        const double t_tc = (ctas * OZ_CTA_SECONDS + ctas * stages * OZ_STAGE_SECONDS) / 152.0 + emb / OZ_EMBED_BPS;
+        const double t_tc = waves * per_cta + emb / OZ_EMBED_BPS;
         const double t_df = st.flops / OZ_DF_FLOPS;
         if (t_tc > 0.7 * t_df) continue;
         // the largest single batch must fit: its chunks' A blocks and B blocks

@@ -70,6 +70,7 @@ constexpr int OZ_ACC_WARPS = 16;                           // four per TMEM lane
 constexpr int OZ_COLS = OZ_BN / (OZ_ACC_WARPS / 4);        // 16 columns per accumulator thread
 static_assert(OZ_COLS % 8 == 0 && OZ_COLS <= 32, "columns per thread: 8-column TMEM loads, one lane each");
 constexpr int OZ_THREADS = 64 + 32 * OZ_ACC_WARPS;
+constexpr int OZ_MAX_SPLIT = 64;                           // most CTAs sharing one tile's units (small launches)
 constexpr int OZ_BAR_BYTES = 512;                          // mbarriers, TMEM address, abort flag
 constexpr int OZ_REF_BYTES = OZ_ACC_WARPS * 96 * 4;       // per accumulator warp: RB, 1 / RB, chunk column factors
 constexpr int OZ_SMEM_BYTES = OZ_RING_BYTES + 1024 + OZ_BAR_BYTES + OZ_REF_BYTES;
