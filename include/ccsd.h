@@ -172,8 +172,9 @@ int ccsd_tc_timeout_selftest(void);
  * K up to 8192.  CCSD_ERR_TIMEOUT if a bounded device wait gave up. */
 int ccsd_oz_gemm(int M, int Ncols, int K, int slices, const double* A, const double* B, double* C);
 
-/* Failure-detection self-test of the Ozaki GEMM, as ccsd_tc_timeout_selftest:
- * returns CCSD_ERR_TIMEOUT when the failure path works. */
+/* Failure-detection self-test of the Ozaki GEMM, as ccsd_tc_timeout_selftest (here
+ * the loader never fills one pair of A-slice stages): returns CCSD_ERR_TIMEOUT when
+ * the failure path works. */
 int ccsd_oz_timeout_selftest(void);
 
 /* One residual evaluation R(t) (paper Eqs. ori_EqSingle, ori_EqDouble with the
