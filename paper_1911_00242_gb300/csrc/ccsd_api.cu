@@ -149,7 +149,9 @@ struct ccsd_ctx {
     long long nc = 0;                // canonical t2 blocks (ki <= kj, ka <= kb)
     int* d_cblk = nullptr;           // full block index of each canonical block
     double* d_cw = nullptr;          // its weight: the number of blocks it stands for
-    int* d_cmap = nullptr;           // per full block: 4 * canonical index + 2 swap_ij + swap_ab
+    double* d_rden = nullptr;        // 1 / D of the history's elements (t1, canonical t2 blocks)
+    int* d_ctgt = nullptr;           // per canonical block: up to 4 full blocks it stands for,
+                                     // 4 * full index + 2 swap_ij + swap_ab (-1 past the last)
     DiisState* d_diis = nullptr;     // DIIS state on the device (history ring, Gram matrix, coefficients)
     double* d_diis_part = nullptr;   // [depth][red_blocks] inner-product partials
     DiisState diis_init{};           // its initial value (empty history), for resets
@@ -2600,15 +2602,15 @@ int group_build(Group& G, int fp32, const std::vector<int>& cfgs, double* d_norm
                 if (!h->d_diis) { refuse("a group member has no DIIS state"); return CCSD_ERR_INVALID; }
                 const int* skip = d_skip ? d_skip + i : nullptr;
                 const long long blk = (long long)h->o * h->o * h->v * h->v;
-                pk.push_back(DiisPackOp{h->amp, h->res, h->d_diis, h->d_cblk, h->nc, h->eo, h->ev, h->kb_of,
-                                        h->N, h->o, h->v, skip});
+                pk.push_back(DiisPackOp{h->amp, h->res, h->d_diis, h->d_cblk, h->nc, h->d_rden, h->N, h->o, h->v,
+                                        skip});
                 bp.push_back(grid_blocks(ew_grid(h->n1 + h->nc * blk)));
                 dt.push_back(DiisDotOp{h->d_diis, h->n1, blk, h->nc, h->d_cw, h->d_diis_part, h->red_blocks, skip});
-                bd.push_back((long long)depth * h->red_blocks);
+                bd.push_back(h->red_blocks);
                 sv.push_back(DiisSolveOp{h->d_diis, h->d_diis_part, h->red_blocks, skip});
                 bs.push_back(1);
-                cb.push_back(DiisComboOp{h->amp, h->d_diis, h->d_cmap, h->N, h->o, h->v, skip});
-                bc.push_back(grid_blocks(ew_grid(h->n1 + h->n2)));
+                cb.push_back(DiisComboOp{h->amp, h->d_diis, h->d_ctgt, h->nc, h->N, h->o, h->v, skip});
+                bc.push_back(std::min<long long>(cb.back().units(), 8LL * kSMs));
             }
             GLaunch g1, g2, g3, g4;
             if ((rc = make_grouped(G, pk, bp, st, g1)) || (rc = make_grouped(G, dt, bd, st, g2)) ||
@@ -2873,9 +2875,18 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
         std::vector<double> cw;
         if (!diis_canonical_blocks(h->kg, cblk, cw, cmap)) return CCSD_ERR_INVALID;
         h->nc = (long long)cblk.size();
+        // the inverse of cmap: the full blocks each canonical block is written to
+        std::vector<int> ctgt((size_t)h->nc * 4, -1);
+        for (size_t f = 0; f < cmap.size(); ++f) {
+            const int p = cmap[f] >> 2;
+            int t = 0;
+            while (t < 4 && ctgt[(size_t)p * 4 + t] >= 0) ++t;
+            if (t == 4) return CCSD_ERR_INVALID;
+            ctgt[(size_t)p * 4 + t] = (int)(4 * f) + (cmap[f] & 3);
+        }
         h->d_cblk = upload(al, cblk, h->st);
         h->d_cw = upload(al, cw, h->st);
-        h->d_cmap = upload(al, cmap, h->st);
+        h->d_ctgt = upload(al, ctgt, h->st);
         const long long np = h->n1 + h->nc * o * o * v * v;
         for (int d = 0; d < h->cfg.diis_depth; ++d) {
             h->hx.push_back(dalloc(np));
@@ -2914,6 +2925,15 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
             kb[(size_t)(((long long)ki * N + kj) * N + ka)] = h->kg.k4(ki, kj, ka);
         h->kb_of = upload(al, kb, h->st);
         if (al.err) return al.err;
+        if (h->cfg.diis_depth > 0) {
+            const long long np = h->n1 + h->nc * (long long)o * o * v * v;
+            h->d_rden = (double*)al.get((size_t)np * sizeof(double));
+            if (al.err) return al.err;
+            if (!al.dry)
+                op_kernel<DiisRdenOp><<<ew_grid(np), 256, 0, h->st>>>(DiisRdenOp{h->d_rden, h->d_cblk, h->nc, h->eo,
+                                                                                  h->ev, h->kb_of, (int)N, (int)o,
+                                                                                  (int)v});
+        }
     }
     set_sizes(h);
     size_t work_need = 0;
@@ -3028,12 +3048,12 @@ int iter_finish(ccsd_ctx* h, double mr, int* done) {
         const long long blk = (long long)h->o * h->o * h->v * h->v;
         const long long np = h->n1 + h->nc * blk;
         op_kernel<DiisPackOp><<<ew_grid(np), 256, 0, h->st>>>(DiisPackOp{h->amp, h->res, h->d_diis, h->d_cblk, h->nc,
-                                                                          h->eo, h->ev, h->kb_of, h->N, h->o, h->v, nullptr});
-        op_kernel<DiisDotOp><<<(unsigned)(depth * h->red_blocks), 256, 0, h->st>>>(
+                                                                          h->d_rden, h->N, h->o, h->v, nullptr});
+        op_kernel<DiisDotOp><<<(unsigned)h->red_blocks, 256, 0, h->st>>>(
             DiisDotOp{h->d_diis, h->n1, blk, h->nc, h->d_cw, h->d_diis_part, h->red_blocks, nullptr});
         op_kernel<DiisSolveOp><<<1, 32, 0, h->st>>>(DiisSolveOp{h->d_diis, h->d_diis_part, h->red_blocks, nullptr});
-        op_kernel<DiisComboOp><<<ew_grid(n), 256, 0, h->st>>>(DiisComboOp{h->amp, h->d_diis, h->d_cmap, h->N, h->o, h->v,
-                                                                          nullptr});
+        const DiisComboOp cb{h->amp, h->d_diis, h->d_ctgt, h->nc, h->N, h->o, h->v, nullptr};
+        op_kernel<DiisComboOp><<<(unsigned)std::min<long long>(cb.units(), 8LL * kSMs), 256, 0, h->st>>>(cb);
         h->launches += 4;
         if (h->trace) { cudaEventRecord(h->ev1[tu], h->st); if ((rc = trace_collect(h, tu, tu + 1))) return rc; }
     }

@@ -291,18 +291,6 @@ __global__ void final_csum(const double2* __restrict__ part, int n, double2* __r
     }
 }
 
-// x = sum_h c_h x_h over up to 8 history vectors (DIIS extrapolation).
-struct Combo { const double2* x[8]; double c[8]; int m; };
-__global__ void combo_kernel(double2* __restrict__ out, const Combo cb, long long n)
-{
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
-        double r = 0.0, im = 0.0;
-        for (int h = 0; h < cb.m; ++h) { const double2 z = cb.x[h][e]; r += cb.c[h] * z.x; im += cb.c[h] * z.y; }
-        out[e] = make_double2(r, im);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Mixed form: the P(ab)-only and P(ij)-only terms of R2 at half weight, fused
 // into one pass over Zr (FP32 products and sums, FP64 accumulation into Zr):
@@ -474,114 +462,15 @@ struct ToDfOp {
 __global__ void to_df_kernel(const ToDfOp op) { op.run(blockIdx.x, gridDim.x); }
 
 // ---------------------------------------------------------------------------
-// DIIS history on canonical momentum blocks.  t2 is antisymmetric under
-// (ki,i) <-> (kj,j) and under (ka,a) <-> (kb,b), so the blocks with ki <= kj and
-// ka <= kb determine all others; history vectors hold t1 followed by those
-// blocks only (about a quarter of t2).  cblk[p] is the full block index of
-// canonical block p, cw[p] the number of blocks it stands for (its weight in the
-// full inner product), cmap[f] = 4 p + 2 swap_ij + swap_ab for every full block f.
-// x = t + R/D and e = R/D on the canonical elements (t1 part first).
-__global__ void diis_pack_update(const double2* __restrict__ amp, const double2* __restrict__ res,
-                                 double2* __restrict__ x_out, double2* __restrict__ e_out,
-                                 const int* __restrict__ cblk, long long nc,
-                                 const double* __restrict__ eo, const double* __restrict__ ev,
-                                 const int* __restrict__ kb_of, int N, int o, int v)
-{
-    const long long n1 = (long long)N * o * v;
-    const long long blk = (long long)o * o * v * v;
-    const long long total = n1 + nc * blk;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        long long q;
-        double d;
-        if (e < n1) {
-            const int a = (int)(e % v);
-            const int i = (int)((e / v) % o);
-            const int k = (int)(e / ((long long)o * v));
-            d = eo[k * o + i] - ev[k * v + a];
-            q = e;
-        } else {
-            const long long pe = e - n1;
-            const long long f = cblk[pe / blk];
-            int r = (int)(pe % blk);
-            q = n1 + f * blk + r;
-            const int b = r % v; r /= v;
-            const int a = r % v; r /= v;
-            const int j = r % o; const int i = r / o;
-            const int ka = (int)(f % N), kj = (int)((f / N) % N), ki = (int)(f / ((long long)N * N));
-            const int kb = kb_of[f];
-            d = eo[ki * o + i] + eo[kj * o + j] - ev[ka * v + a] - ev[kb * v + b];
-        }
-        const double2 rq = res[q];
-        const double2 step = make_double2(rq.x / d, rq.y / d);
-        const double2 t = amp[q];
-        x_out[e] = make_double2(t.x + step.x, t.y + step.y);
-        e_out[e] = step;
-    }
-}
-
-// Weighted Re <x|y> partial sums over canonical vectors (the full inner product).
-__global__ void redot_w_partial(const double2* __restrict__ x, const double2* __restrict__ y, long long n1,
-                                long long blk, long long nc, const double* __restrict__ cw,
-                                double* __restrict__ part)
-{
-    __shared__ double sm[256];
-    double s = 0.0;
-    const long long n = n1 + nc * blk;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
-        const double2 a = x[e], b = y[e];
-        const double w = e < n1 ? 1.0 : cw[(e - n1) / blk];
-        s += w * (a.x * b.x + a.y * b.y);
-    }
-    sm[threadIdx.x] = s;
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
-}
-
-// amp = sum_h c_h x_h over canonical history vectors, expanded to every block
-// with the antisymmetry signs.
-__global__ void combo_unpack(double2* __restrict__ out, const Combo cb, const int* __restrict__ cmap,
-                             int N, int o, int v)
-{
-    const long long n1 = (long long)N * o * v;
-    const long long blk = (long long)o * o * v * v;
-    const long long total = n1 + (long long)N * N * N * blk;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        long long src;
-        double sg = 1.0;
-        if (e < n1) {
-            src = e;
-        } else {
-            const long long f = (e - n1) / blk;
-            int r = (int)((e - n1) % blk);
-            const int b = r % v; r /= v;
-            const int a = r % v; r /= v;
-            const int j = r % o; const int i = r / o;
-            const int m = cmap[f];
-            const int sij = (m >> 1) & 1, sab = m & 1;
-            const int i2 = sij ? j : i, j2 = sij ? i : j, a2 = sab ? b : a, b2 = sab ? a : b;
-            src = n1 + (long long)(m >> 2) * blk + (((long long)i2 * o + j2) * v + a2) * v + b2;
-            if (sij != sab) sg = -1.0;
-        }
-        double re = 0.0, im = 0.0;
-        for (int h = 0; h < cb.m; ++h) { const double2 z = cb.x[h][src]; re += cb.c[h] * z.x; im += cb.c[h] * z.y; }
-        out[e] = make_double2(sg * re, sg * im);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Device-resident DIIS (grouped iterations of the batched form): the same steps as
-// ccsd_iterate's host-driven DIIS -- pack x = t + R/D and e = R/D on the canonical
-// blocks into history slot `next`, the weighted inner products of e with every
-// filled slot, the Pulay solve, x = sum c_h x_h expanded to every block -- with the
-// history ring, the Gram matrix and the coefficients kept in device memory, so that
-// an iteration needs no host round trip and can be replayed from a CUDA graph.
+// DIIS on the device (every handle, alone or in a group).  t2 is antisymmetric under
+// (ki,i) <-> (kj,j) and under (ka,a) <-> (kb,b) (paper Sec. 2), so the blocks with
+// ki <= kj and ka <= kb determine all others; a history vector holds t1 followed by
+// those canonical blocks, and inner products weight each block by the number of
+// full blocks it stands for.  An update packs x = t + R/D and e = R/D into history
+// slot `next`, forms the weighted inner products of e with every filled slot, solves
+// the Pulay system and writes x = sum c_h x_h to every block with the antisymmetry
+// signs.  The history ring, the Gram matrix and the coefficients stay in device
+// memory, so an iteration needs no host round trip and can be replayed from a graph.
 struct DiisState {
     double2* hx[DIIS_MAX];    // history: amplitudes after the update (canonical blocks)
     double2* he[DIIS_MAX];    // history: errors R / D
@@ -591,11 +480,45 @@ struct DiisState {
     int singular;             // a solve met a zero pivot (that iteration took the plain update)
 };
 
-// pack into slot ds->next (diis_pack_update's body), skipped for converged members
+// The reciprocal orbital-energy denominators 1 / D of the history's elements (t1,
+// then the canonical t2 blocks; paper Sec. 4.4, Eqs. criterion_single and
+// criterion_double), formed once at creation: an update then multiplies, where a
+// division is a long sequence on the FP64 pipe (2 FMAs per clock and SM on GB300).
+struct DiisRdenOp {
+    double* rden; const int* cblk; long long nc;
+    const double* eo; const double* ev; const int* kb_of; int N, o, v;
+    __device__ void run(long long vb, long long nvb) const {
+        const long long n1 = (long long)N * o * v;
+        const long long blk = (long long)o * o * v * v;
+        const long long total = n1 + nc * blk;
+        for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
+            double d;
+            if (e < n1) {
+                const int a = (int)(e % v);
+                const int i = (int)((e / v) % o);
+                const int k = (int)(e / ((long long)o * v));
+                d = eo[k * o + i] - ev[k * v + a];
+            } else {
+                const long long pe = e - n1;
+                const long long f = cblk[pe / blk];
+                int r = (int)(pe % blk);
+                const int b = r % v; r /= v;
+                const int a = r % v; r /= v;
+                const int j = r % o; const int i = r / o;
+                const int ka = (int)(f % N), kj = (int)((f / N) % N), ki = (int)(f / ((long long)N * N));
+                const int kb = kb_of[f];
+                d = eo[ki * o + i] + eo[kj * o + j] - ev[ka * v + a] - ev[kb * v + b];
+            }
+            rden[e] = 1.0 / d;
+        }
+    }
+};
+
+// pack into slot ds->next, skipped for converged members: x = t + R / D, e = R / D on
+// the canonical elements (R and t read at their full-array positions)
 struct DiisPackOp {
     const double2* amp; const double2* res; DiisState* ds;
-    const int* cblk; long long nc;
-    const double* eo; const double* ev; const int* kb_of; int N, o, v;
+    const int* cblk; long long nc; const double* rden; int N, o, v;
     const int* skip;
     __device__ void run(long long vb, long long nvb) const {
         if (skip && *skip) return;
@@ -606,28 +529,14 @@ struct DiisPackOp {
         const long long blk = (long long)o * o * v * v;
         const long long total = n1 + nc * blk;
         for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
-            long long q;
-            double d;
-            if (e < n1) {
-                const int a = (int)(e % v);
-                const int i = (int)((e / v) % o);
-                const int k = (int)(e / ((long long)o * v));
-                d = eo[k * o + i] - ev[k * v + a];
-                q = e;
-            } else {
+            long long q = e;
+            if (e >= n1) {
                 const long long pe = e - n1;
-                const long long f = cblk[pe / blk];
-                int r = (int)(pe % blk);
-                q = n1 + f * blk + r;
-                const int b = r % v; r /= v;
-                const int a = r % v; r /= v;
-                const int j = r % o; const int i = r / o;
-                const int ka = (int)(f % N), kj = (int)((f / N) % N), ki = (int)(f / ((long long)N * N));
-                const int kb = kb_of[f];
-                d = eo[ki * o + i] + eo[kj * o + j] - ev[ka * v + a] - ev[kb * v + b];
+                q = n1 + (long long)cblk[pe / blk] * blk + pe % blk;
             }
+            const double rd = rden[e];
             const double2 rq = res[q];
-            const double2 step = make_double2(rq.x / d, rq.y / d);
+            const double2 step = make_double2(rq.x * rd, rq.y * rd);
             const double2 t = amp[q];
             x_out[e] = make_double2(t.x + step.x, t.y + step.y);
             e_out[e] = step;
@@ -636,7 +545,10 @@ struct DiisPackOp {
 };
 
 // Partial sums of w-weighted Re <e_next | e_j> for every slot j of the history
-// (j >= the filled slots: zero): block vb = j * nred + r of a grid of depth * nred.
+// (j >= the filled slots: zero).  Block r of nred takes the elements r * 256 + t
+// (stride nred * 256) and forms all the slots' sums in one pass, so e_next is read
+// once; part[j * nred + r] receives slot j's sum, each reduced over the block in the
+// same fixed tree.
 struct DiisDotOp {
     const DiisState* ds; long long n1, blk, nc; const double* cw;
     double* part; int nred;
@@ -644,26 +556,39 @@ struct DiisDotOp {
     __device__ void run(long long vb, long long) const {
         if (skip && *skip) return;
         __shared__ double sm[256];
-        const int j = (int)(vb / nred), r = (int)(vb % nred);
+        const int r = (int)vb;
         const int m = min(ds->count + 1, ds->depth);
-        double s = 0.0;
-        if (j < m) {
-            const double2* x = ds->he[ds->next];
-            const double2* y = ds->he[j];
-            const long long n = n1 + nc * blk;
-            for (long long e = (long long)r * blockDim.x + threadIdx.x; e < n; e += (long long)nred * blockDim.x) {
-                const double2 a = x[e], b = y[e];
-                const double w = e < n1 ? 1.0 : cw[(e - n1) / blk];
-                s += w * (a.x * b.x + a.y * b.y);
+        const double2* x = ds->he[ds->next];
+        const double2* y[DIIS_MAX];
+#pragma unroll
+        for (int j = 0; j < DIIS_MAX; ++j) y[j] = ds->he[j];
+        double s[DIIS_MAX];
+#pragma unroll
+        for (int j = 0; j < DIIS_MAX; ++j) s[j] = 0.0;
+        const long long n = n1 + nc * blk;
+        for (long long e = (long long)r * blockDim.x + threadIdx.x; e < n; e += (long long)nred * blockDim.x) {
+            const double2 a = x[e];
+            const double w = e < n1 ? 1.0 : cw[(e - n1) / blk];
+#pragma unroll
+            for (int j = 0; j < DIIS_MAX; ++j) {
+                if (j < m) {
+                    const double2 b = y[j][e];
+                    s[j] += w * (a.x * b.x + a.y * b.y);
+                }
             }
         }
-        sm[threadIdx.x] = s;
-        __syncthreads();
-        for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-            if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+#pragma unroll
+        for (int j = 0; j < DIIS_MAX; ++j) {
+            if (j >= ds->depth) break;
+            sm[threadIdx.x] = s[j];
+            __syncthreads();
+            for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+                if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) part[j * nred + r] = sm[0];
             __syncthreads();
         }
-        if (threadIdx.x == 0) part[vb] = sm[0];
     }
 };
 
@@ -673,14 +598,25 @@ struct DiisSolveOp {
     DiisState* ds; const double* part; int nred;
     const int* skip;
     __device__ void run(long long vb, long long) const {
-        if ((skip && *skip) || vb != 0 || threadIdx.x != 0) return;
+        if ((skip && *skip) || vb != 0 || threadIdx.x >= 32) return;
+        const int lane = threadIdx.x;
         const int slot = ds->next;
         const int m = min(ds->count + 1, ds->depth);
-        for (int j = 0; j < m; ++j) {
+        // the partials of each slot: lane l sums r = l, l + 32, ... in order, then a fixed
+        // shuffle tree over the lanes
+        double g[DIIS_MAX];
+#pragma unroll
+        for (int j = 0; j < DIIS_MAX; ++j) {
             double d = 0.0;
-            for (int r = 0; r < nred; ++r) d += part[j * nred + r];
-            ds->gram[slot][j] = d;
-            ds->gram[j][slot] = d;
+            if (j < m)
+                for (int r = lane; r < nred; r += 32) d += part[j * nred + r];
+            for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
+            g[j] = d;
+        }
+        if (lane != 0) return;
+        for (int j = 0; j < m; ++j) {
+            ds->gram[slot][j] = g[j];
+            ds->gram[j][slot] = g[j];
         }
         ds->count = m;
         ds->next = (slot + 1) % ds->depth;
@@ -697,41 +633,86 @@ struct DiisSolveOp {
     }
 };
 
-// amp = sum_h coef_h hx_h over the filled slots, expanded to every block with the
-// antisymmetry signs (combo_unpack's body).
+// amp = sum_h coef_h hx_h over the filled slots, written to every block.  The sum is
+// formed once per canonical element and stored at each of the up to four full blocks
+// the canonical block stands for (tgt[4 p + t] = 4 f + 2 swap_ij + swap_ab, -1 past the
+// last), with the swapped indices and the antisymmetry sign.  Work units: t1 in pieces
+// of 1024 elements, then 32 x 32 (a, b) tiles of every canonical (p, i, j) pair; a tile
+// is staged in shared memory so that the (a, b)-swapped targets are written row by row
+// as well (coalesced) instead of with a stride of v.
+constexpr int DIIS_TILE = 32;
 struct DiisComboOp {
-    double2* out; const DiisState* ds; const int* cmap; int N, o, v;
+    double2* out; const DiisState* ds; const int* tgt; long long nc; int N, o, v;
     const int* skip;
+    __host__ __device__ long long units() const {
+        const long long n1 = (long long)N * o * v;
+        const long long nt = (v + DIIS_TILE - 1) / DIIS_TILE;
+        return (n1 + 1023) / 1024 + nc * o * o * nt * nt;
+    }
     __device__ void run(long long vb, long long nvb) const {
         if (skip && *skip) return;
+        __shared__ double2 tile[DIIS_TILE][DIIS_TILE + 1];
         const int m = ds->m;
         const long long n1 = (long long)N * o * v;
         const long long blk = (long long)o * o * v * v;
-        const long long total = n1 + (long long)N * N * N * blk;
-        for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
-            long long src;
-            double sg = 1.0;
-            if (e < n1) {
-                src = e;
-            } else {
-                const long long f = (e - n1) / blk;
-                int r = (int)((e - n1) % blk);
-                const int b = r % v; r /= v;
-                const int a = r % v; r /= v;
-                const int j = r % o; const int i = r / o;
-                const int mm = cmap[f];
-                const int sij = (mm >> 1) & 1, sab = mm & 1;
-                const int i2 = sij ? j : i, j2 = sij ? i : j, a2 = sab ? b : a, b2 = sab ? a : b;
-                src = n1 + (long long)(mm >> 2) * blk + (((long long)i2 * o + j2) * v + a2) * v + b2;
-                if (sij != sab) sg = -1.0;
+        const long long u1 = (n1 + 1023) / 1024;
+        const int nt = (v + DIIS_TILE - 1) / DIIS_TILE;
+        const long long nu = u1 + nc * o * o * nt * nt;
+        for (long long u = vb; u < nu; u += nvb) {
+            if (u < u1) {                                   // t1: plain
+                for (long long e = u * 1024 + threadIdx.x; e < min(n1, (u + 1) * 1024); e += blockDim.x) {
+                    double re = 0.0, im = 0.0;
+                    for (int h = 0; h < m; ++h) {
+                        const double2 z = ds->hx[h][e];
+                        re += ds->coef[h] * z.x;
+                        im += ds->coef[h] * z.y;
+                    }
+                    out[e] = make_double2(re, im);
+                }
+                continue;
             }
-            double re = 0.0, im = 0.0;
-            for (int h = 0; h < m; ++h) {
-                const double2 z = ds->hx[h][src];
-                re += ds->coef[h] * z.x;
-                im += ds->coef[h] * z.y;
+            long long w = u - u1;
+            const int tb = (int)(w % nt); w /= nt;
+            const int ta = (int)(w % nt); w /= nt;
+            const int j = (int)(w % o); w /= o;
+            const int i = (int)(w % o);
+            const long long p = w / o;
+            const long long base = n1 + p * blk + ((long long)i * o + j) * v * v;   // canonical (i, j) plane
+            for (int q = threadIdx.x; q < DIIS_TILE * DIIS_TILE; q += blockDim.x) {
+                const int aa = q / DIIS_TILE, bb = q % DIIS_TILE;
+                const int a = ta * DIIS_TILE + aa, b = tb * DIIS_TILE + bb;
+                double re = 0.0, im = 0.0;
+                if (a < v && b < v) {
+                    const long long e = base + (long long)a * v + b;
+                    for (int h = 0; h < m; ++h) {
+                        const double2 z = ds->hx[h][e];
+                        re += ds->coef[h] * z.x;
+                        im += ds->coef[h] * z.y;
+                    }
+                }
+                tile[aa][bb] = make_double2(re, im);
             }
-            out[e] = make_double2(sg * re, sg * im);
+            __syncthreads();
+            for (int t = 0; t < 4; ++t) {
+                const int g = tgt[4 * p + t];
+                if (g < 0) break;
+                const int sij = (g >> 1) & 1, sab = g & 1;
+                const double sg = sij != sab ? -1.0 : 1.0;
+                const long long fbase = n1 + (long long)(g >> 2) * blk +
+                                        ((long long)(sij ? j : i) * o + (sij ? i : j)) * v * v;
+                // target element (a2, b2) of the plane, b2 fastest; it holds canonical
+                // (a, b) = (a2, b2), or (b2, a2) when the pair (a, b) is swapped
+                const int a0 = sab ? tb : ta, b0 = sab ? ta : tb;
+                for (int q = threadIdx.x; q < DIIS_TILE * DIIS_TILE; q += blockDim.x) {
+                    const int x = q / DIIS_TILE, y = q % DIIS_TILE;
+                    const int a2 = a0 * DIIS_TILE + x, b2 = b0 * DIIS_TILE + y;
+                    if (a2 < v && b2 < v) {
+                        const double2 z = sab ? tile[y][x] : tile[x][y];
+                        out[fbase + (long long)a2 * v + b2] = make_double2(sg * z.x, sg * z.y);
+                    }
+                }
+            }
+            __syncthreads();
         }
     }
 };
