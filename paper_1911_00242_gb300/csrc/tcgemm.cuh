@@ -506,7 +506,7 @@ struct ToC64Op {
     __device__ void run(long long vb, long long nvb) const {
         for (long long e = vb * blockDim.x + threadIdx.x; e < n; e += nvb * blockDim.x) {
             const double2 z = src[e];
-            dst[e] = make_float2((float)z.x, (float)z.y);
+            dst[e] = make_float2(f32_rn(z.x), f32_rn(z.y));    // integer rounding: no FP64 pipe
         }
     }
 };

@@ -18,4 +18,12 @@ void probe_split_tf32(const double* x, float* big, float* small, int n) {
     for (int i = 0; i < n; ++i) split_tf32(x[i], big[i], small[i]);
 }
 
+void probe_f32_rn(const double* x, float* out, int n) {
+    for (int i = 0; i < n; ++i) out[i] = f32_rn(x[i]);
+}
+
+void probe_f32_residual(const double* x, float* f, float* r, int* ok, int n) {
+    for (int i = 0; i < n; ++i) ok[i] = f32_round_with_residual(x[i], f[i], r[i]) ? 1 : 0;
+}
+
 }  // extern "C"
