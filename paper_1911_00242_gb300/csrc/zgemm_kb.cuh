@@ -26,6 +26,7 @@
 // FP64 pipe, so the complex64 copies matter for throughput, not only bytes.
 #pragma once
 #include "dfloat.cuh"
+#include "tf32_split.cuh"
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,6 +58,14 @@ template <typename T> struct Cplx;
 template <> struct Cplx<double> { using V = double2; };
 template <> struct Cplx<float> { using V = float2; };
 template <> struct Cplx<df> { using V = df2; };
+
+// A complex128 operand element in the instance's arithmetic.  The FP32 instance rounds
+// with integer operations (f32_rn; the double-float conversion does the same itself):
+// on GB300 every FP64 operation, a conversion included, issues on a pipe of 2 per clock
+// and SM.  The results are those of the plain conversions, bit for bit.
+template <typename T> __device__ __forceinline__ T from_f64(double x) { return T(x); }
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return f32_rn(x); }
+
 
 // Shared-memory staging of one K step: the complex tiles, and for the FP64
 // instance also Re + Im of every element (the third factor of the 3M product).
@@ -137,7 +146,7 @@ __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long lon
                     const long long q = g.affA ? g.a0 + (long long)m * g.rAs + (long long)k * g.cAs
                                                : (long long)g.rowA[m] + g.colA[k];
                     if (Ab32) { const float2 w = __ldg(Ab32 + q); v.x = T(w.x); v.y = T(w.y) * sa; }
-                    else { const double2 w = __ldg(Ab + q); v.x = T(w.x); v.y = T(w.y) * sa; }
+                    else { const double2 w = __ldg(Ab + q); v.x = from_f64<T>(w.x); v.y = from_f64<T>(w.y) * sa; }
                 }
                 As[kk][mm] = v;
                 if (k3M) sm.As[kk][mm] = v.x + v.y;
@@ -150,7 +159,7 @@ __device__ __forceinline__ void zgemm_tile(const GemmArgs& g, int tile, long lon
                     const long long q = g.affB ? g.b0 + (long long)k * g.rBs + (long long)n * g.cBs
                                                : (long long)g.rowB[k] + g.colB[n];
                     if (Bb32) { const float2 w = __ldg(Bb32 + q); v.x = T(w.x); v.y = T(w.y) * sb; }
-                    else { const double2 w = __ldg(Bb + q); v.x = T(w.x); v.y = T(w.y) * sb; }
+                    else { const double2 w = __ldg(Bb + q); v.x = from_f64<T>(w.x); v.y = from_f64<T>(w.y) * sb; }
                 }
                 Bs[kk][nn] = v;
                 if (k3M) sm.Bs[kk][nn] = v.x + v.y;
