@@ -332,11 +332,16 @@ struct FockTermsOp {
         const long long total = (long long)N * N * N * blk;
         const long long vv = (long long)v * v, ov3 = (long long)o * v * vv, o3v = (long long)o * o * o * v;
         for (long long e = vb * blockDim.x + threadIdx.x; e < total; e += nvb * blockDim.x) {
-            const long long kk = e / blk;
-            int r = (int)(e % blk);
-            const int b = r % v; r /= v;
-            const int a = r % v; r /= v;
-            const int j = r % o; const int i = r / o;
+            // thread order: b fastest, then i, a, j, the momentum block.  The o threads of
+            // one (block, j, a, b) are neighbours, so their ovvv, F' and t1 reads (the
+            // longest sum, over c) come from L1 after the first.
+            long long w = e;
+            const int b = (int)(w % v); w /= v;
+            const int i = (int)(w % o); w /= o;
+            const int a = (int)(w % v); w /= v;
+            const int j = (int)(w % o);
+            const long long kk = w / o;
+            const long long eo = kk * blk + (((long long)i * o + j) * v + a) * v + b;   // Zr position
             const int ka = (int)(kk % N), kj = (int)((kk / N) % N), ki = (int)(kk / ((long long)N * N));
             const int kb = kb_of[kk];
             const float2* tb = t2 + kk * blk;
@@ -358,10 +363,10 @@ struct FockTermsOp {
             const float2* ti = t1 + ((long long)ki * o + i) * v;                        // t_i^c(ki)
 #pragma unroll 4
             for (int c = 0; c < v; ++c) q = cfma_conjb(ti[c], vbp[(long long)c * vv], q);
-            double2 z = Zr[e];
+            double2 z = Zr[eo];
             z.x += 0.5 * ((double)p.x - (double)q.x);
             z.y += 0.5 * ((double)p.y - (double)q.y);
-            Zr[e] = z;
+            Zr[eo] = z;
         }
     }
 };
