@@ -2875,15 +2875,8 @@ int setup_handle(ccsd_ctx* h, Alloc& al, const void* const* ins, const bool* on_
         std::vector<double> cw;
         if (!diis_canonical_blocks(h->kg, cblk, cw, cmap)) return CCSD_ERR_INVALID;
         h->nc = (long long)cblk.size();
-        // the inverse of cmap: the full blocks each canonical block is written to
-        std::vector<int> ctgt((size_t)h->nc * 4, -1);
-        for (size_t f = 0; f < cmap.size(); ++f) {
-            const int p = cmap[f] >> 2;
-            int t = 0;
-            while (t < 4 && ctgt[(size_t)p * 4 + t] >= 0) ++t;
-            if (t == 4) return CCSD_ERR_INVALID;
-            ctgt[(size_t)p * 4 + t] = (int)(4 * f) + (cmap[f] & 3);
-        }
+        std::vector<int> ctgt;                 // the full blocks each canonical block is written to
+        if (!diis_canonical_targets(cmap, h->nc, ctgt)) return CCSD_ERR_INVALID;
         h->d_cblk = upload(al, cblk, h->st);
         h->d_cw = upload(al, cw, h->st);
         h->d_ctgt = upload(al, ctgt, h->st);

@@ -53,6 +53,24 @@ inline bool diis_canonical_blocks(const KGrid& kg, std::vector<int>& cblk, std::
     return true;
 }
 
+// The inverse of cmap: for canonical block p, ctgt[4 p + t] (t < 4) = 4 f + 2 swap_ij +
+// swap_ab for each full block f that is read from p (cmap[f] >> 2 == p), in increasing
+// f, and -1 past the last.  The device extrapolation writes each canonical element to
+// these blocks.  Returns false if some canonical block would stand for more than four
+// full blocks (not possible on a grid: its weight is at most 2 x 2).
+inline bool diis_canonical_targets(const std::vector<int>& cmap, long long nc, std::vector<int>& ctgt) {
+    ctgt.assign((size_t)nc * 4, -1);
+    for (size_t f = 0; f < cmap.size(); ++f) {
+        const long long p = cmap[f] >> 2;
+        if (p < 0 || p >= nc) return false;
+        int t = 0;
+        while (t < 4 && ctgt[(size_t)p * 4 + t] >= 0) ++t;
+        if (t == 4) return false;
+        ctgt[(size_t)p * 4 + t] = (int)(4 * f) + (cmap[f] & 3);
+    }
+    return true;
+}
+
 #ifdef __CUDACC__
 #define CCSD_HD __host__ __device__
 #else

@@ -22,3 +22,17 @@ extern "C" int probe_canonical(const int* dims, int* nc, int* cblk, double* cw, 
     for (size_t f = 0; f < m.size(); ++f) cmap[f] = m[f];
     return 1;
 }
+
+// The canonical blocks' targets (csrc/diis.h, the map the device extrapolation writes by);
+// ctgt has room for 4 N^3 entries.
+extern "C" int probe_targets(const int* dims, int* nc, int* ctgt) {
+    ccsdk::KGrid kg;
+    kg.init(dims);
+    std::vector<int> b, m, t;
+    std::vector<double> w;
+    if (!ccsdk::diis_canonical_blocks(kg, b, w, m)) return 0;
+    if (!ccsdk::diis_canonical_targets(m, (long long)b.size(), t)) return 0;
+    *nc = (int)b.size();
+    for (size_t i = 0; i < t.size(); ++i) ctgt[i] = t[i];
+    return 1;
+}

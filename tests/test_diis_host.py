@@ -35,6 +35,8 @@ def probe():
         ip = ctypes.POINTER(ctypes.c_int)
         _lib.probe_canonical.argtypes = [ip, ip, ip, d, ip]
         _lib.probe_canonical.restype = ctypes.c_int
+        _lib.probe_targets.argtypes = [ip, ip, ip]
+        _lib.probe_targets.restype = ctypes.c_int
     return _lib
 
 
@@ -159,3 +161,40 @@ def test_canonical_blocks_weights_dot_and_unpack():
             sign = -1.0 if sij != sab else 1.0
             # the 4-term antisymmetrizer above rounds differently per block: 1e-13, not bits
             np.testing.assert_allclose(sign * blk, Tf[f], rtol=0, atol=1e-13)
+
+
+def test_extrapolation_targets_write_every_block_once():
+    """The device extrapolation writes each canonical element to the full blocks listed
+    by diis_canonical_targets, with the swapped indices and the antisymmetry sign.  That
+    scatter must write every full block exactly once and reproduce the antisymmetric t2,
+    and list as many targets as the block's weight."""
+    rng = np.random.default_rng(10)
+    for grid in [(1, 1, 1), (2, 1, 1), (3, 1, 1), (4, 1, 1), (2, 2, 1), (3, 2, 1), (2, 2, 2), (3, 3, 1)]:
+        N = grid[0] * grid[1] * grid[2]
+        o, v = 2, 3
+        cblk, cw, cmap = canonical(grid)
+        dims = (ctypes.c_int * 3)(*grid)
+        nc = ctypes.c_int(0)
+        tg = (ctypes.c_int * (4 * N ** 3))()
+        assert probe().probe_targets(dims, ctypes.byref(nc), tg) == 1
+        assert nc.value == len(cblk)
+        ctgt = np.array(tg[:4 * nc.value]).reshape(nc.value, 4)
+        T = antisymmetric_t2(rng, grid, o, v)
+        Tf = T.reshape(N ** 3, o, o, v, v)
+        out = np.full_like(Tf, np.nan)
+        writes = np.zeros(N ** 3, int)
+        for p in range(nc.value):
+            listed = [g for g in ctgt[p] if g >= 0]
+            assert len(listed) == cw[p] and all(g >= 0 for g in ctgt[p][:len(listed)])
+            src = Tf[cblk[p]]
+            for g in listed:
+                f, sij, sab = g >> 2, (g >> 1) & 1, g & 1
+                blk = src
+                if sij:
+                    blk = blk.transpose(1, 0, 2, 3)
+                if sab:
+                    blk = blk.transpose(0, 1, 3, 2)
+                out[f] = (-1.0 if sij != sab else 1.0) * blk
+                writes[f] += 1
+        assert np.all(writes == 1)
+        np.testing.assert_allclose(out, Tf, rtol=0, atol=1e-13)
