@@ -259,7 +259,7 @@ def run_mixed(args, spec, dev, depth, local, fp64_solve, fp64_ms_per_iter):
     out = {
         "value": 1e3 / ms, "unit": "iter/s", "ms_per_step": ms, "steps": args.steps, "gpu_launches": launches,
         "step_ms": summ,
-        "precision": "tcgen05 split-TF32 (3 passes) for ladder and ring, FP32 CUDA cores elsewhere, FP64 update",
+        "precision": "tcgen05 split-TF32 (3 passes) for ladder, ring and hole-hole, FP32 CUDA cores elsewhere, FP64 update, DIIS and energy",
         "contraction_tflops": flops_per_iteration(spec) / (ms / 1e3) / 1e12,
         "speedup_per_iter_vs_fp64": fp64_ms_per_iter / ms,
         "roofline": {"kernel": f"tc_gemm_kernel ({name})", "bound": "tensor", "achieved": achieved,
@@ -352,8 +352,8 @@ def run_ozaki(args, spec, dev, depth, fp64_solve, fp64_ms_per_iter, slices=7):
         "value": 1e3 / ms, "unit": "iter/s", "ms_per_step": ms, "steps": args.steps, "gpu_launches": launches,
         "step_ms": summ, "slices": slices,
         "precision": (f"Ozaki scheme: {slices} BF16 slices per operand row, {pairs} slice-pair products per "
-                      "contraction on tcgen05 (exact FP32 windows, double-float sum) for ladder, ring and "
-                      "hole-hole; FP64 elsewhere"),
+                      "contraction on tcgen05 (exact FP32 windows, double-float sum) for ladder, ring, "
+                      "hole-hole and F~_vv; double-float GEMMs elsewhere; FP64 update, DIIS and energy"),
         "contraction_tflops": flops_per_iteration(spec) / (ms / 1e3) / 1e12,
         "speedup_per_iter_vs_fp64": fp64_ms_per_iter / ms,
         "roofline": {"kernel": f"oz_gemm_kernel ({name})", "bound": "tensor", "achieved": achieved,
@@ -609,7 +609,8 @@ def run_grid333(args, local):
 
 def run_grid333_ozaki(args, local):
     """The 3x3x3/o8/v24 workload (complex64 integrals) in the Ozaki form: FP64-accurate
-    contractions on the BF16 tensor cores, FP64 elsewhere.  One step = one Ozaki iteration;
+    contractions on the BF16 tensor cores, double-float elsewhere, FP64 update, DIIS and
+    energy.  One step = one Ozaki iteration;
     the timed steps are the first iterations of a solve from t = 0 to max|R| < 1e-8.  The
     same handle then runs one native FP64 iteration from the converged amplitudes: its
     max|R| and energy change show how far the Ozaki fixed point is from the FP64 one.
@@ -689,7 +690,7 @@ def run_grid333_ozaki(args, local):
     return {
         "metric": METRIC, "value": 1e3 / ms, "unit": "iter/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "ozaki: 7 bf16 slices, exact fp32 windows, double-float sums; fp64 elsewhere",
+        "vs_baseline": None, "dtype": "ozaki: 7 bf16 slices, exact fp32 windows, double-float sums; double-float and fp64 elsewhere",
         "data": "synthetic",
         "config": {"workload": "grid333_o8_v24_c64", "nk_grid": list(spec.grid), "nocc": spec.nocc,
                    "nvir": spec.nvir, "int_dtype": "c64", "precision": "ozaki", "diis": depth,
