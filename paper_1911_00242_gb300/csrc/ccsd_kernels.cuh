@@ -274,14 +274,6 @@ __global__ void final_max(const double* __restrict__ part, int n, double* __rest
 {
     FinalMaxOp{part, n, out}.run(blockIdx.x, gridDim.x);
 }
-__global__ void final_sum(const double* __restrict__ part, int n, double* __restrict__ out)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < n; ++i) s += part[i];
-        *out = s;
-    }
-}
 __global__ void final_csum(const double2* __restrict__ part, int n, double2* __restrict__ out)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
