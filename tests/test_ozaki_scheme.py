@@ -61,6 +61,7 @@ def _kernel_constants():
         "MAX_SLICES": const("OZ_MAX_SLICES"),
         "EXP_MIN": const("OZ_EXP_MIN"),
         "EXP_MAX": const("OZ_EXP_MAX"),
+        "MAX_SPLIT": const("OZ_MAX_SPLIT"),
     }
 
 
@@ -350,7 +351,7 @@ def unit_range(nch, S, kstages, nsplit, split_idx):
                                            (2, 7, 23)])
 def test_unit_split_is_a_partition(nch, S, kstages):
     nunits = nch * -(-kstages // oz_kwin(S))
-    for nsplit in range(1, 17):
+    for nsplit in range(1, K["MAX_SPLIT"] + 1):      # up to the most CTAs the kernel splits a tile over
         covered = []
         prev = 0
         for sp in range(nsplit):
@@ -368,7 +369,7 @@ def test_kernel_schedule_code_equals_the_model(probe):
     u0, u1 = ctypes.c_int(0), ctypes.c_int(0)
     for nch, S, kst in [(1, 7, 1), (1, 7, 4), (3, 7, 8), (2, 3, 2), (5, 8, 3), (1, 1, 1), (27, 7, 6), (4, 7, 23)]:
         nunits = nch * -(-kst // oz_kwin(S))
-        for nsplit in range(1, 17):
+        for nsplit in range(1, K["MAX_SPLIT"] + 1):      # up to the most CTAs the kernel splits a tile over
             prev = 0
             for sp in range(nsplit):
                 probe.probe_unit_range(nch, S, kst, nsplit, sp, ctypes.byref(u0), ctypes.byref(u1))
